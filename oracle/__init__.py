@@ -1,0 +1,224 @@
+"""FP64 CPU oracle of the chunked DAS operator chain -- TEST INFRASTRUCTURE.
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and ``bench.py``'s CPU-baseline
+leg may import this package.  The product library never loads it, and it
+shares no code with the CUDA path.  See ``filark_oracle.c`` for what each
+function computes and which passage of the paper it follows.
+
+Two builds of the same C source are made: ``ora_*`` (double) and ``orald_*``
+(long double, used only to bound the rounding error of the double build).
+"""
+from __future__ import annotations
+
+import ctypes as ct
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "filark_oracle.c")
+_OUT = os.path.join(_HERE, "_build")
+_LOCK = threading.Lock()
+_LIBS: dict = {}
+
+_dp = ct.POINTER(ct.c_double)
+_fp = ct.POINTER(ct.c_float)
+
+
+def _lib_path(long_double: bool) -> str:
+    return os.path.join(_OUT, "libfilark_oracle_ld.so" if long_double else "libfilark_oracle.so")
+
+
+def compile_source(src: str, out: str, long_double: bool = False) -> None:
+    """gcc a copy of the oracle source into a shared library (plain C11, no
+    target-specific flags, no floating-point contraction)."""
+    cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fno-fast-math", "-ffp-contract=off"]
+    if long_double:
+        cmd.append("-DORA_LONG_DOUBLE")
+    tmp = out + f".tmp{os.getpid()}"
+    cmd += ["-o", tmp, src, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, out)
+
+
+def build(force: bool = False) -> None:
+    """Compile both oracle builds."""
+    os.makedirs(_OUT, exist_ok=True)
+    for ld in (False, True):
+        out = _lib_path(ld)
+        if not force and os.path.exists(out) and os.path.getmtime(out) >= os.path.getmtime(_SRC):
+            continue
+        compile_source(_SRC, out, ld)
+
+
+def _bind(path: str, long_double: bool):
+    lib = ct.CDLL(path)
+    p = "orald_" if long_double else "ora_"
+    f = getattr(lib, p + "butter_bandpass")
+    f.argtypes = [ct.c_int, ct.c_double, ct.c_double, ct.c_double, _dp]
+    f.restype = ct.c_int
+    f = getattr(lib, p + "sosfilt")
+    f.argtypes = [_dp, ct.c_int, _dp, ct.c_long, _dp, _dp]
+    f.restype = None
+    f = getattr(lib, p + "chain_new")
+    f.argtypes = [ct.c_int, ct.c_int, _dp, ct.c_int, ct.c_int, ct.c_int]
+    f.restype = ct.c_void_p
+    for name in ("chain_free", "chain_reset"):
+        f = getattr(lib, p + name)
+        f.argtypes = [ct.c_void_p]
+        f.restype = None
+    f = getattr(lib, p + "chain_samples")
+    f.argtypes = [ct.c_void_p]
+    f.restype = ct.c_long
+    f = getattr(lib, p + "chain_push")
+    f.argtypes = [ct.c_void_p, _fp, ct.c_long, ct.c_long, _dp, _dp, _dp, ct.c_long]
+    f.restype = ct.c_int
+    f = getattr(lib, p + "chain_get_iir_state")
+    f.argtypes = [ct.c_void_p, _dp]
+    f.restype = None
+    f = getattr(lib, p + "stalta_naive")
+    f.argtypes = [_dp, ct.c_long, ct.c_int, ct.c_int, _dp]
+    f.restype = None
+    f = getattr(lib, p + "sos_adjoint")
+    f.argtypes = [_dp, ct.c_int, _dp, ct.c_long, _dp, _dp, _dp]
+    f.restype = None
+    return lib, p
+
+
+def _load(long_double: bool = False):
+    with _LOCK:
+        if long_double not in _LIBS:
+            build()
+            _LIBS[long_double] = _bind(_lib_path(long_double), long_double)
+        return _LIBS[long_double]
+
+
+class use_library:
+    """Context manager: route the double-precision API through another build of
+    the oracle source (the tests use it to run the pins on planted mistakes)."""
+
+    def __init__(self, path: str):
+        self._path = path
+
+    def __enter__(self):
+        with _LOCK:
+            self._saved = _LIBS.get(False)
+            _LIBS[False] = _bind(self._path, False)
+        return self
+
+    def __exit__(self, *exc):
+        with _LOCK:
+            if self._saved is None:
+                _LIBS.pop(False, None)
+            else:
+                _LIBS[False] = self._saved
+        return False
+
+
+def _fn(name: str, long_double: bool = False):
+    lib, p = _load(long_double)
+    return getattr(lib, p + name)
+
+
+def _ptr(a: np.ndarray | None, typ=_dp):
+    if a is None:
+        return ct.cast(None, typ)
+    return a.ctypes.data_as(typ)
+
+
+def butter_bandpass(order: int, f1: float, f2: float, fs: float, long_double: bool = False) -> np.ndarray:
+    """Butterworth bandpass as ``order`` SOS rows {b0,b1,b2,a0,a1,a2}."""
+    sos = np.zeros((order, 6), dtype=np.float64)
+    rc = _fn("butter_bandpass", long_double)(order, f1, f2, fs, _ptr(sos))
+    if rc != 0:
+        raise ValueError("invalid Butterworth bandpass parameters")
+    return sos
+
+
+def sosfilt(sos: np.ndarray, x: np.ndarray, zi: np.ndarray | None = None,
+            long_double: bool = False) -> tuple[np.ndarray, np.ndarray]:
+    """Filter one channel with the TDF-II cascade; returns (y, final state)."""
+    sos = np.ascontiguousarray(sos, dtype=np.float64)
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    S = sos.shape[0]
+    z = np.zeros(2 * S) if zi is None else np.array(zi, dtype=np.float64).copy()
+    y = np.empty_like(x)
+    _fn("sosfilt", long_double)(_ptr(sos), S, _ptr(x), x.shape[0], _ptr(y), _ptr(z))
+    return y, z
+
+
+class Chain:
+    """Stateful oracle chain: IIR -> spatial mean -> STA/LTA (all FP64)."""
+
+    def __init__(self, n_channels: int, sos: np.ndarray | None, spatial_width: int = 1,
+                 sta_len: int = 0, lta_len: int = 0, long_double: bool = False):
+        self._ld = long_double
+        sos = np.zeros((0, 6)) if sos is None else np.ascontiguousarray(sos, dtype=np.float64)
+        self._sos = sos
+        self.C = int(n_channels)
+        self.S = int(sos.shape[0])
+        self.detector = lta_len > 0
+        lib, p = _load(long_double)
+        self._f = {k: getattr(lib, p + k) for k in
+                   ("chain_new", "chain_free", "chain_reset", "chain_samples", "chain_push",
+                    "chain_get_iir_state")}
+        self._h = self._f["chain_new"](self.C, self.S, _ptr(sos if self.S else np.zeros(6)),
+                                       int(spatial_width), int(sta_len), int(lta_len))
+        if not self._h:
+            raise ValueError("invalid oracle chain configuration")
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h:
+            self._f["chain_free"](h)
+            self._h = None
+
+    def reset(self) -> None:
+        self._f["chain_reset"](self._h)
+
+    @property
+    def samples(self) -> int:
+        return int(self._f["chain_samples"](self._h))
+
+    def push(self, x: np.ndarray, want=("bp", "sp", "ratio")) -> dict:
+        """Push a time-major float32 chunk [T][C]; returns the requested outputs
+        as float64 arrays [T][C]."""
+        x = np.ascontiguousarray(x, dtype=np.float32)
+        if x.ndim != 2 or x.shape[1] != self.C:
+            raise ValueError("chunk must be [T][C]")
+        T = x.shape[0]
+        out = {k: np.zeros((T, self.C), dtype=np.float64) for k in want
+               if k != "ratio" or self.detector}
+        rc = self._f["chain_push"](self._h, _ptr(x, _fp), self.C, T,
+                                         _ptr(out.get("bp")), _ptr(out.get("sp")),
+                                         _ptr(out.get("ratio")), self.C)
+        if rc != 0:
+            raise ValueError("oracle push failed")
+        return out
+
+    def iir_state(self) -> np.ndarray:
+        z = np.zeros((self.C, 2 * self.S), dtype=np.float64)
+        self._f["chain_get_iir_state"](self._h, _ptr(z))
+        return z
+
+
+def stalta_naive(cf: np.ndarray, sta_len: int, lta_len: int, long_double: bool = False) -> np.ndarray:
+    """Literal-window STA/LTA of one channel's cf sequence (O(window) per sample)."""
+    cf = np.ascontiguousarray(cf, dtype=np.float64)
+    R = np.zeros_like(cf)
+    _fn("stalta_naive", long_double)(_ptr(cf), cf.shape[0], int(sta_len), int(lta_len), _ptr(R))
+    return R
+
+
+def sos_adjoint(sos: np.ndarray, x: np.ndarray, gy: np.ndarray, long_double: bool = False):
+    """Adjoint of the SOS cascade for one channel: returns (dL/dx, dL/dsos)."""
+    sos = np.ascontiguousarray(sos, dtype=np.float64)
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    gy = np.ascontiguousarray(gy, dtype=np.float64)
+    gx = np.zeros_like(x)
+    gs = np.zeros_like(sos)
+    _fn("sos_adjoint", long_double)(_ptr(sos), sos.shape[0], _ptr(x), x.shape[0], _ptr(gy),
+                                    _ptr(gx), _ptr(gs))
+    return gx, gs

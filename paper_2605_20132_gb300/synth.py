@@ -1,0 +1,171 @@
+"""Seeded synthetic DAS streams shaped like the paper's workloads.
+
+This module only makes inputs: Gaussian noise, 1/f (pink) noise and Ricker
+wavelets with linear moveout.  It holds none of the filter chain's arithmetic,
+and both the CUDA path's tests/benchmark and the oracle's tests draw their
+inputs from it, so the two sides always see identical float32 arrays.
+
+The paper's own recordings (three concatenated OOI ocean-cable files,
+Sec. 6.2) are not available; these streams stand in for them, with the channel
+counts and sampling rates of the paper's sizing example (6,000 channels at
+1,500 Hz, float32, Sec. 1).
+
+Layout of every array returned: time-major ``[n_samples][n_channels]`` float32
+(the ``nt_nc`` dimension order of the paper's Tape protocol, Sec. 3.5).
+"""
+from __future__ import annotations
+
+import numpy as np
+
+
+def ricker(t: np.ndarray, f: float) -> np.ndarray:
+    """Ricker wavelet (1 - 2 pi^2 f^2 t^2) exp(-pi^2 f^2 t^2), peak frequency f."""
+    a = (np.pi * f * t) ** 2
+    return (1.0 - 2.0 * a) * np.exp(-a)
+
+
+def add_ricker_events(x: np.ndarray, fs: float, t0: np.ndarray, c0: np.ndarray,
+                      f: np.ndarray, slope_s: np.ndarray, amp: np.ndarray,
+                      t_offset: float = 0.0) -> None:
+    """Add events in place.  Event e arrives on channel c at
+    t0[e] + slope_s[e] * (c - c0[e]) seconds; ``t_offset`` is the time of row 0
+    of ``x`` (so a long stream can be generated in pieces)."""
+    N, C = x.shape
+    ch = np.arange(C, dtype=np.float64)
+    for e in range(len(t0)):
+        arrival = t0[e] + slope_s[e] * (ch - c0[e])           # [C] seconds
+        half = 1.5 / f[e]                                      # support: |t| <= 1.5/f
+        lo = int(np.floor((arrival.min() - half - t_offset) * fs))
+        hi = int(np.ceil((arrival.max() + half - t_offset) * fs)) + 1
+        lo, hi = max(lo, 0), min(hi, N)
+        if lo >= hi:
+            continue
+        tt = (np.arange(lo, hi, dtype=np.float64) / fs + t_offset)[:, None] - arrival[None, :]
+        w = amp[e] * ricker(tt, f[e])
+        w[np.abs(tt) > half] = 0.0
+        x[lo:hi] += w.astype(np.float32)
+
+
+def pink_noise(rng: np.random.Generator, n_samples: int, n_channels: int,
+               block: int = 256) -> np.ndarray:
+    """Per channel: white Gaussian noise shaped by 1/sqrt(f) in the rFFT domain
+    (DC bin zeroed), scaled to unit standard deviation over the whole record."""
+    out = np.empty((n_samples, n_channels), dtype=np.float32)
+    k = np.arange(n_samples // 2 + 1, dtype=np.float64)
+    shape = np.zeros_like(k)
+    shape[1:] = 1.0 / np.sqrt(k[1:])
+    for c0 in range(0, n_channels, block):
+        c1 = min(n_channels, c0 + block)
+        w = rng.standard_normal((n_samples, c1 - c0))
+        W = np.fft.rfft(w, axis=0)
+        W *= shape[:, None]
+        p = np.fft.irfft(W, n=n_samples, axis=0)
+        p /= p.std(axis=0, keepdims=True)
+        out[:, c0:c1] = p
+    return out
+
+
+def noise_ricker_stream(n_channels: int, n_samples: int, fs: float, n_events: int,
+                        amp: float, f_range: tuple[float, float],
+                        slope_ms_range: tuple[float, float], seed: int,
+                        pink: bool = False, fixed_origin_channel: bool = False) -> np.ndarray:
+    """N(0,1) noise (+ optional unit-sigma pink noise) + seeded Ricker events."""
+    rng = np.random.default_rng(seed)
+    x = rng.standard_normal((n_samples, n_channels), dtype=np.float32)
+    if pink:
+        x += pink_noise(rng, n_samples, n_channels)
+    dur = n_samples / fs
+    t0 = rng.uniform(0.1 * dur, 0.9 * dur, n_events) if fixed_origin_channel else rng.uniform(0, dur, n_events)
+    c0 = np.zeros(n_events) if fixed_origin_channel else rng.uniform(0, n_channels, n_events)
+    f = rng.uniform(f_range[0], f_range[1], n_events)
+    slope = rng.uniform(slope_ms_range[0], slope_ms_range[1], n_events) * 1e-3
+    add_ricker_events(x, fs, t0, c0, f, slope, np.full(n_events, amp))
+    return x
+
+
+# --------------------------------------------------------------------------
+# The workloads.  Chain parameters are given in samples (windows) and as
+# Butterworth specs (prototype order N, band edges in Hz).
+# --------------------------------------------------------------------------
+
+SMALL = dict(name="small-64ch-1kHz", n_channels=64, n_samples=10_000, fs=1000.0, order=4,
+             band=(1.0, 50.0), chunk=1000, spatial_width=5, sta=50, lta=1000, seed=1)
+
+PAPER_SCALE = dict(name="paper-scale-6000ch-1500Hz", n_channels=6000, n_samples=90_000, fs=1500.0,
+                   order=8, band=(0.5, 100.0), chunk=1500, spatial_width=9, sta=150, lta=3000, seed=2)
+
+BATCH = dict(name="batch-32-streams", n_streams=32, channels=(500, 10_000), chunk=(200, 3000),
+             fs=1000.0, order=4, band=(1.0, 50.0), spatial_width=5, sta=50, lta=1000, seed=3)
+
+ADJOINT = dict(name="adjoint-2048ch-30k", n_channels=2048, n_samples=30_000, fs=1000.0, order=4,
+               band=(1.0, 50.0), checkpoint=3000, perturb=0.02, seed=4)
+
+PRECISION = dict(name="precision-10000ch-600s", n_channels=10_000, n_samples=900_000, fs=1500.0,
+                 order=8, band=(0.01, 1.0), chunk=1500, sine_hz=0.05, sine_amp=0.1, seed=5)
+
+
+def small_stream(n_channels: int = 64, n_samples: int = 10_000, seed: int = 1) -> np.ndarray:
+    """64 ch x 10,000 samples at 1 kHz: N(0,1) + 3 Ricker events (20 Hz peak,
+    amplitude 5, 0.5 ms/channel moveout) at seeded times."""
+    return noise_ricker_stream(n_channels, n_samples, 1000.0, 3, 5.0, (20.0, 20.0),
+                               (0.5, 0.5), seed, pink=False, fixed_origin_channel=True)
+
+
+def paper_scale_stream(n_channels: int = 6000, n_samples: int = 90_000, seed: int = 2,
+                       n_events: int = 200) -> np.ndarray:
+    """6,000 ch x 60 s at 1.5 kHz: N(0,1) + unit pink noise + 200 Ricker events
+    (amplitude 5, peak 5-80 Hz, moveout -1..1 ms/channel, seeded origin time and
+    channel)."""
+    return noise_ricker_stream(n_channels, n_samples, 1500.0, n_events, 5.0, (5.0, 80.0),
+                               (-1.0, 1.0), seed, pink=True)
+
+
+def precision_chunk(chunk_index: int, n_channels: int = 10_000, chunk: int = 1500,
+                    fs: float = 1500.0, seed: int = 5, sine_hz: float = 0.05,
+                    sine_amp: float = 0.1, channels: np.ndarray | None = None) -> np.ndarray:
+    """One chunk of the long precision-stress stream: N(0,1) noise plus a
+    0.05 Hz sinusoid of amplitude 0.1 with a seeded phase per channel.  Each
+    chunk is generated from its own seed, so any chunk (and any subset of
+    channels) can be made on its own."""
+    phase = np.random.default_rng([seed, 0]).uniform(0, 2 * np.pi, n_channels)
+    rng = np.random.default_rng([seed, 1, chunk_index])
+    x = rng.standard_normal((chunk, n_channels), dtype=np.float32)
+    t = (chunk_index * chunk + np.arange(chunk, dtype=np.float64)) / fs
+    if channels is not None:
+        x = x[:, channels]
+        phase = phase[channels]
+    x += (sine_amp * np.sin(2 * np.pi * sine_hz * t[:, None] + phase[None, :])).astype(np.float32)
+    return x
+
+
+def batch_streams(seed: int = 3, n_streams: int = 32, channels=(500, 10_000),
+                  chunk=(200, 3000)) -> list[dict]:
+    """Specs of the independent streams of the batching workload: a channel
+    count per stream and a generator of per-push chunk lengths."""
+    rng = np.random.default_rng(seed)
+    Cs = rng.integers(channels[0], channels[1] + 1, n_streams)
+    return [dict(n_channels=int(C), seed=int(seed * 1000 + i)) for i, C in enumerate(Cs)]
+
+
+def batch_chunk_lengths(seed: int, n_streams: int, n_pushes: int, chunk=(200, 3000)) -> np.ndarray:
+    """[n_pushes][n_streams] chunk lengths, uniform in [chunk[0], chunk[1]]."""
+    rng = np.random.default_rng([seed, 7])
+    return rng.integers(chunk[0], chunk[1] + 1, (n_pushes, n_streams))
+
+
+def perturb_sos(sos: np.ndarray, rel: float, seed: int, max_tries: int = 1000) -> np.ndarray:
+    """Multiply every coefficient except a0 by (1+u), u ~ U[-rel, rel]; a
+    section is redrawn until its poles lie strictly inside the unit circle."""
+    rng = np.random.default_rng(seed)
+    out = np.array(sos, dtype=np.float64).copy()
+    for s in range(out.shape[0]):
+        for _ in range(max_tries):
+            u = rng.uniform(-rel, rel, 6)
+            u[3] = 0.0
+            cand = sos[s] * (1.0 + u)
+            if np.all(np.abs(np.roots(cand[3:])) < 1.0):
+                out[s] = cand
+                break
+        else:
+            raise RuntimeError("could not draw a stable perturbed section")
+    return out
