@@ -1,0 +1,376 @@
+"""Benchmark of the chunked DAS chain on the paper-scale stream.
+
+Workload (one "step"): 6,000 channels x 60 s at 1.5 kHz, float32, pushed as 60
+chunks of 1,500 samples through the whole chain -- order-8 Butterworth bandpass
+0.5-100 Hz (8 SOS), 9-channel spatial mean, STA/LTA 150/3000 samples -- with
+the ratio written to device memory.  The input (2.16 GB) and output stay
+resident in HBM; a step re-pushes the same recording as a continuation of the
+stream (the state keeps carrying), so every step does identical work on inputs
+larger than L2.
+
+Prints one JSON line (rank 0).  `--impl reference` times the FP64 CPU oracle
+on the host cores instead (the reference arm; there is no published GPU code).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "channel-samples/s of chunked filter chain (device-timed), % of HBM roofline"
+UNIT = "channel-samples/s"
+
+
+def workload():
+    from paper_2605_20132_gb300 import synth
+    w = dict(synth.PAPER_SCALE)
+    return w
+
+
+def algorithmic_bytes_per_push(C: int, T: int, S: int, ns: int, nl: int) -> int:
+    """Bytes one push must move at minimum: input, ratio output, the cf values
+    written to the history ring, the exiting cf values read back from it
+    (min(T, nl) + min(T, ns) per channel), and the carried state (IIR state in
+    FP64 and the detector sums, read and written)."""
+    per_ch = 4 * T + 4 * T + 4 * min(T, nl) + 4 * (min(T, nl) + min(T, ns))
+    state = 2 * (8 * 2 * S + 8 * 4)
+    return C * (per_ch + state)
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons while it runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines: list[str] = []
+        self._t = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self._t = threading.Thread(target=self._read, daemon=True)
+            self._t.start()
+        except (OSError, ValueError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            if self._t:
+                self._t.join(timeout=2)
+        return False
+
+    def summary(self) -> dict:
+        sm, smax, reasons = [], None, set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peak_hbm() -> tuple[float, str]:
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+# ------------------------------------------------------------ oracle timing --
+
+def oracle_run(x: np.ndarray, sos, K: int, ns: int, nl: int, T: int, n_push: int, threads: int,
+               c_lo: int = 0, c_hi: int | None = None) -> float:
+    """Run the FP64 oracle (unmodified) over channels [c_lo, c_hi) of x for
+    n_push pushes of T samples, split into contiguous channel groups, one
+    oracle chain per host thread (each with its own halo).  Returns seconds."""
+    import concurrent.futures as cf
+    import ctypes as ct
+
+    import oracle
+    N, C = x.shape
+    c_hi = C if c_hi is None else c_hi
+    h = (K - 1) // 2
+    span = c_hi - c_lo
+    groups = [(c_lo + span * i // threads, c_lo + span * (i + 1) // threads) for i in range(threads)]
+    lib, pre = oracle._load(False)
+    push = getattr(lib, pre + "chain_push")
+
+    def work(g):
+        a, b = g
+        lo, hi = max(0, a - h), min(C, b + h)
+        ch = oracle.Chain(hi - lo, sos, K, ns, nl)
+        out = np.empty((T, hi - lo), dtype=np.float64)
+        base = x.ctypes.data
+        for p in range(n_push):
+            ptr = ct.cast(base + 4 * ((p * T) * C + lo), ct.POINTER(ct.c_float))
+            rc = push(ch._h, ptr, C, T, None, None, out.ctypes.data_as(ct.POINTER(ct.c_double)), hi - lo)
+            assert rc == 0
+        return None
+
+    t0 = time.perf_counter()
+    with cf.ThreadPoolExecutor(max_workers=threads) as ex:
+        list(ex.map(work, groups))
+    return time.perf_counter() - t0
+
+
+def host_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def run_reference(args, rank: int, world: int) -> None:
+    if rank != 0:
+        return
+    import oracle
+    w = workload()
+    from paper_2605_20132_gb300 import synth
+    x = synth.paper_scale_stream(w["n_channels"], w["n_samples"], w["seed"])
+    sos = oracle.butter_bandpass(w["order"], *w["band"], w["fs"])
+    C, T = w["n_channels"], w["chunk"]
+    cores = host_cores()
+    n_push = 6          # one step: every channel, 6 pushes of 1,500 samples
+    for _ in range(args.warmup):
+        oracle_run(x, sos, w["spatial_width"], w["sta"], w["lta"], T, n_push, cores)
+    secs = [oracle_run(x, sos, w["spatial_width"], w["sta"], w["lta"], T, n_push, cores)
+            for _ in range(args.steps)]
+    total = sum(secs)
+    units = C * T * n_push * args.steps
+    value = units / total
+    sample = f"{C} channels x {n_push} pushes of {T} samples per step, FP64 oracle, {cores} threads"
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": w["name"], "channels": C, "fs": w["fs"],
+                                        "chunk": T, "sections": w["order"], "spatial_width": w["spatial_width"],
+                                        "sta": w["sta"], "lta": w["lta"]},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------- GPU timing --
+
+def run_gpu(args, rank: int, world: int, dist) -> None:
+    import ctypes as ct
+
+    import torch
+
+    from paper_2605_20132_gb300 import abi, synth
+    from paper_2605_20132_gb300.chain import Chain, butter_bandpass
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    w = workload()
+    C, N, T = w["n_channels"], w["n_samples"], w["chunk"]
+    K, ns, nl = w["spatial_width"], w["sta"], w["lta"]
+    n_push = N // T
+    x_host = synth.paper_scale_stream(C, N, w["seed"])
+    sos = butter_bandpass(w["order"], *w["band"], w["fs"])
+    S = sos.shape[0]
+    lib = abi.load()
+    chain = Chain(C, sos, w["fs"], K, ns, nl, outputs=abi.FILARK_OUT_RATIO, max_chunk=T, device=local)
+    info = chain.info()
+    stream = torch.cuda.Stream(device=dev)
+    sh = stream.cuda_stream
+    xd = torch.from_numpy(x_host).to(dev)
+    rd = torch.empty((N, C), dtype=torch.float32, device=dev)
+    push = lib.filark_chain_push_chunk
+    h = chain._h
+    row = 4 * C
+    xp, rp = xd.data_ptr(), rd.data_ptr()
+    ptrs = [(xp + i * T * row, rp + i * T * row) for i in range(n_push)]
+
+    def step():
+        for xi, ri in ptrs:
+            st = push(h, xi, C, T, ri, None, None, C, sh)
+            if st:
+                abi.check(st, "push")
+
+    torch.cuda.synchronize()
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            step()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    sampler = ClockSampler(local)
+    with sampler:
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        ev0.record(stream)
+        for _ in range(args.steps):
+            step()
+        ev1.record(stream)
+        ev1.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    if dist:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    abi.check(abi.filark_chain_sync_status(h, sh), "sync")
+    launches_per_push = (T + 2047) // 2048
+    launches = args.steps * n_push * launches_per_push
+    units = C * N * args.steps * world
+    value = units / (ms / 1e3)
+
+    # ---- end to end through the host-buffer entry point (pinned host memory)
+    e2e_steps = max(1, min(args.steps, 3))
+    xh = torch.from_numpy(x_host).pin_memory()
+    rh = torch.empty((N, C), dtype=torch.float32).pin_memory()
+    push_h = lib.filark_chain_push_chunk_host
+    xhp, rhp = xh.data_ptr(), rh.data_ptr()
+
+    def step_host():
+        for i in range(n_push):
+            st = push_h(h, xhp + i * T * row, C, T, rhp + i * T * row, None, None, C, sh)
+            if st:
+                abi.check(st, "push_host")
+
+    step_host()
+    if dist:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        step_host()
+    e2e_s = time.perf_counter() - t0
+    if dist:
+        t = torch.tensor([e2e_s], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e_value = C * N * e2e_steps * world / e2e_s
+    chain.close()
+
+    if rank != 0:
+        return
+    # ---- roofline of the (only) kernel
+    bytes_push = algorithmic_bytes_per_push(C, T, S, ns, nl)
+    ms_launch = ms / launches
+    achieved = bytes_push / launches_per_push / (ms_launch / 1e3) / 1e9
+    peak, peak_kind = measured_peak_hbm()
+    traffic = None
+    tp = os.path.join(ROOT, "profiles", "chain_fwd_paper_scale_traffic.json")
+    if os.path.exists(tp):
+        try:
+            with open(tp) as f:
+                tj = json.load(f)
+            if tj.get("kernel_source_sha") == kernel_sha():
+                traffic = tj.get("dram_bytes_per_launch")
+        except (OSError, ValueError):
+            traffic = None
+
+    # ---- CPU baseline: the oracle on the host cores, bounded sample
+    cores = host_cores()
+    cpu_push = 6
+    cpu_s = oracle_run(x_host, sos, K, ns, nl, T, cpu_push, cores)
+    cpu_value = C * T * cpu_push / cpu_s
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic", "config": {
+            "workload": w["name"], "channels": C, "samples_per_step": N, "fs": w["fs"], "chunk": T,
+            "pushes_per_step": n_push, "sections": S, "spatial_width": K, "sta": ns, "lta": nl,
+            "precision": {1: "modal32", 2: "dense64", 3: "all32"}.get(info["precision"], "?"),
+            "l2": "inputs larger than L2 (2.16 GB per step)", "parallelism": "replicas" if world > 1 else "1 GPU"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
+                     "bytes_per_launch": bytes_push // launches_per_push,
+                     "ms_per_launch": ms_launch},
+        "cpu_baseline": {"value": cpu_value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"{C} channels x {cpu_push} pushes of {T} samples, FP64 oracle, {cores} threads"},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 4 * C * N,
+                "d2h_bytes_per_step": 4 * C * N},
+        "gpu_launches": launches,
+        "clocks": sampler.summary(),
+    }
+    print(json.dumps(line), flush=True)
+
+
+def kernel_sha() -> str:
+    import hashlib
+    hsh = hashlib.sha256()
+    for f in ("chain_kernel.cu", "filark_internal.h"):
+        with open(os.path.join(ROOT, "paper_2605_20132_gb300", "csrc", f), "rb") as fh:
+            hsh.update(fh.read())
+    return hsh.hexdigest()[:16]
+
+
+def main() -> None:
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="filark", choices=["filark", "reference"])
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3) if args.impl == "filark" else args.warmup
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist_mod
+        if args.impl == "reference":
+            dist_mod.init_process_group("gloo")
+        else:
+            import torch
+            torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+            dist_mod.init_process_group("nccl")
+        dist = dist_mod
+    try:
+        if args.impl == "reference":
+            run_reference(args, rank, world)
+        else:
+            run_gpu(args, rank, world, dist)
+    finally:
+        if dist is not None:
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,210 @@
+/*
+ * filark.h -- C-ABI of the GB300 chunked DAS filter chain.
+ *
+ * The chain is the streaming operator chain of FiLark (arxiv 2605.20132):
+ *   1. a causal IIR bandpass given as cascaded second-order sections (SOS),
+ *      each section in transposed direct form II, with the filter state carried
+ *      from one call to the next (Sec. 3.4: stateful-compatible operators and
+ *      the realtime SOS filter; Table 1, "IIR (offline & realtime SOS)");
+ *   2. a spatial running mean over the 2h+1 neighbouring channels, which needs
+ *      a halo of h channels on each side of every channel block (Sec. 3.4:
+ *      overlap-aware execution with halo regions; Table 1, "Spatial ... running
+ *      mean");
+ *   3. an energy detector, the classic STA/LTA ratio of cf = y^2 over trailing
+ *      windows, with running sums carried across calls (Sec. 3.4: threshold
+ *      energy detectors behind the monitor interface).
+ *
+ * Streaming contract (Sec. 3.4 and Sec. 6.2): the concatenation of the outputs
+ * of any sequence of pushes equals the output of one push of the whole
+ * recording, and every push returns exactly as many samples as it was given.
+ * The state after create/reset is zero (x[n<0] = y[n<0] = 0), which keeps the
+ * start-up transient of the first chunk that Sec. 6.2 describes.
+ *
+ * Data layout (every sample buffer, host or device): time-major float32,
+ * sample t of channel c at buf[t * ld + c], ld >= n_channels -- the paper's
+ * `nt_nc` dimension order (Sec. 3.5, custom loader listing).
+ *
+ * Exact definitions (the CPU oracle computes these in FP64):
+ *   IIR, per channel and section, coefficients divided by a0:
+ *       y = b0*u + z1;  z1 = b1*u - a1*y + z2;  z2 = b2*u - a2*y
+ *   spatial:  y_sp[n,c] = mean of y_bp[n,c'] over c' in [c-h, c+h] ∩ [0, C)
+ *   detector: cf = y_sp^2; STA[n] = (1/ns) sum_{k=n-ns+1..n} cf[k], LTA alike
+ *             with nl; R[n] = STA/LTA when n >= nl-1 and the long window holds
+ *             a nonzero cf, else 0.  n counts samples since create/reset.
+ *
+ * Threading: one chain must not be used from two threads at once.  Different
+ * chains are independent.  All calls that take a stream enqueue work on it and
+ * return without waiting, unless stated otherwise.  Error messages are kept
+ * per thread (filark_last_error_string).
+ */
+#ifndef FILARK_H
+#define FILARK_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define FILARK_ABI_VERSION 1u
+
+/* The same type as the CUDA runtime's cudaStream_t; NULL is the legacy
+   default stream. */
+typedef struct CUstream_st *filark_stream_t;
+
+typedef enum {
+    FILARK_OK = 0,
+    FILARK_EINVAL = 1,     /* an argument or configuration value is invalid   */
+    FILARK_ENOMEM = 2,     /* host or device allocation failed                */
+    FILARK_ECUDA = 3,      /* a CUDA runtime call or kernel launch failed     */
+    FILARK_EUNSTABLE = 4,  /* an SOS section has a pole on/outside |z| = 1    */
+    FILARK_ETIMEOUT = 5,   /* a bounded device-side wait gave up              */
+    FILARK_ESTATE = 6,     /* the chain is in an error state: reset it        */
+    FILARK_ENOSYS = 7      /* the configuration is valid but not supported    */
+} filark_status;
+
+/* Outputs a chain may be asked to write (bit mask, filark_chain_config.outputs) */
+enum {
+    FILARK_OUT_RATIO = 1u,     /* STA/LTA ratio R                  */
+    FILARK_OUT_BANDPASS = 2u,  /* bandpass output y_bp (stage 1)   */
+    FILARK_OUT_SPATIAL = 4u    /* spatial mean y_sp (stage 2)      */
+};
+
+/* How the IIR stage carries state between time blocks (see filark_chain_info) */
+enum {
+    FILARK_PREC_AUTO = 0,      /* planner picks and verifies a mode          */
+    FILARK_PREC_MODAL32 = 1,   /* per-pole 2x2 carries in FP32, FP64 across
+                                  thread blocks and chunks                   */
+    FILARK_PREC_DENSE64 = 2,   /* dense carry in FP64 (poles very near 1 or
+                                  repeated poles)                            */
+    FILARK_PREC_ALL32 = 3      /* modal carries in FP32 everywhere, including
+                                  the state kept between chunks (comparison
+                                  only)                                      */
+};
+
+typedef struct {
+    uint32_t abi_version;   /* must equal FILARK_ABI_VERSION                      */
+    int32_t n_channels;     /* C >= 1                                             */
+    double fs;              /* sampling rate in Hz (> 0); metadata only, all
+                               windows are given in samples                       */
+    int32_t n_sections;     /* S, 0 <= S <= FILARK_MAX_SECTIONS (0 = no IIR)      */
+    const double *sos;      /* host, S rows {b0,b1,b2,a0,a1,a2}; copied by create */
+    int32_t spatial_width;  /* K = 2h+1, odd, 1 <= K <= FILARK_MAX_SPATIAL_WIDTH;
+                               1 = no spatial stage                               */
+    int32_t sta_len;        /* ns in samples; 1 <= ns <= nl, or both 0 = detector
+                               off                                                */
+    int32_t lta_len;        /* nl in samples                                      */
+    uint32_t outputs;       /* FILARK_OUT_* mask of the outputs pushes may write  */
+    int32_t precision;      /* FILARK_PREC_*                                      */
+    int64_t max_chunk;      /* largest n_samples of one push (>= 1); sizes the
+                               detector's history ring                            */
+} filark_chain_config;
+
+#define FILARK_MAX_SECTIONS 8
+#define FILARK_MAX_SPATIAL_WIDTH 33
+
+typedef struct filark_chain filark_chain;
+
+/* Plan details, for diagnostics and benchmarks. */
+typedef struct {
+    int32_t precision;        /* mode in use (FILARK_PREC_MODAL32, ...)              */
+    int32_t block_len;        /* L: samples per time block                           */
+    int32_t blocks_per_cta;   /* time blocks per thread block                        */
+    int32_t tile_channels;    /* output channels per thread block                    */
+    int32_t halo;             /* h = (K-1)/2                                         */
+    int32_t n_slots;          /* 2x2 state slots per channel in the kernel           */
+    double modal_condition;   /* condition number of the modal basis (inf if none)   */
+    double probe_error;       /* planner's FP32-emulation error on its probe signal  */
+    int64_t ring_len;         /* detector history ring length in samples (0 = none)  */
+    int64_t device_bytes;     /* device memory the chain owns                        */
+    int64_t samples;          /* samples pushed since create/reset                   */
+} filark_chain_info;
+
+/*
+ * Create a chain on CUDA device `cuda_device`.  Validates the configuration
+ * (FILARK_EINVAL), checks that every section is stable (FILARK_EUNSTABLE),
+ * plans the kernel tables on the host in FP64, allocates the chain's device
+ * state and zeroes it.  On success *out receives the chain; on failure *out is
+ * set to NULL and nothing is leaked.  Synchronous.
+ */
+filark_status filark_chain_create(const filark_chain_config *cfg, int cuda_device,
+                                  filark_chain **out);
+
+/*
+ * Push n_samples new samples of every channel through the chain.
+ *   d_in       device, [n_samples][ld_in] float32, ld_in >= C; read only.
+ *   d_ratio    device, [n_samples][ld_out] float32, or NULL; STA/LTA ratio.
+ *   d_bandpass device, [n_samples][ld_out] float32, or NULL; stage-1 output.
+ *   d_spatial  device, [n_samples][ld_out] float32, or NULL; stage-2 output.
+ * An output may be non-NULL only if its bit is in cfg.outputs.  Inputs must not
+ * overlap outputs.  0 <= n_samples <= max_chunk; 0 is a no-op.  The work is
+ * enqueued on `stream`; the caller's buffers must stay valid until it
+ * completes.  Returns FILARK_ESTATE if an earlier device-side error was seen
+ * (the chain stays in that state until reset), FILARK_ECUDA if a launch fails.
+ */
+filark_status filark_chain_push_chunk(filark_chain *h, const float *d_in, int64_t ld_in,
+                                      int64_t n_samples, float *d_ratio, float *d_bandpass,
+                                      float *d_spatial, int64_t ld_out, filark_stream_t stream);
+
+/*
+ * As filark_chain_push_chunk, with HOST buffers (pinned memory is fastest).
+ * The chain copies the input to its own device staging buffer, runs the push
+ * and copies the requested outputs back, all on `stream`, and returns when the
+ * outputs are in host memory (synchronous).  Device staging is allocated on the
+ * first call (max_chunk samples per buffer).
+ */
+filark_status filark_chain_push_chunk_host(filark_chain *h, const float *h_in, int64_t ld_in,
+                                           int64_t n_samples, float *h_ratio, float *h_bandpass,
+                                           float *h_spatial, int64_t ld_out,
+                                           filark_stream_t stream);
+
+/* Zero the whole state (IIR, detector sums, history, sample count) on
+   `stream`, and clear a sticky error. */
+filark_status filark_chain_reset_state(filark_chain *h, filark_stream_t stream);
+
+/* Free everything the chain owns (waits for its work to finish).  NULL is
+   accepted. */
+filark_status filark_chain_destroy(filark_chain *h);
+
+/*
+ * Checkpoint: copy the chain's complete state to host memory.  With
+ * host_buf == NULL, *bytes receives the size needed.  The IIR state is written
+ * in the canonical layout (per channel, per section z1 then z2, FP64), followed
+ * by the detector sums and history.  Synchronous on `stream`.  Restoring it with
+ * filark_chain_set_state into a chain of the same configuration continues the
+ * stream exactly as if it had not stopped.
+ */
+filark_status filark_chain_get_state(filark_chain *h, void *host_buf, size_t *bytes,
+                                     filark_stream_t stream);
+filark_status filark_chain_set_state(filark_chain *h, const void *host_buf, size_t bytes,
+                                     filark_stream_t stream);
+
+/* Wait for the chain's work on `stream` and report any device-side error. */
+filark_status filark_chain_sync_status(filark_chain *h, filark_stream_t stream);
+
+/* Fill *out with the plan details (host only, no synchronisation). */
+filark_status filark_chain_get_info(const filark_chain *h, filark_chain_info *out);
+
+/*
+ * Butterworth bandpass design by the bilinear transform (host only).  `order`
+ * is the order N of the analog lowpass prototype (the bandpass has order 2N);
+ * 0 < f1 < f2 < fs/2.  Writes N SOS rows {b0,b1,b2,a0,a1,a2} to sos_out:
+ * conjugate-pole sections with zeros at z = +1 and z = -1, in ascending pole
+ * radius, gain spread evenly so that |H| = 1 at the image of the geometric band
+ * centre (and 1/sqrt(2) at f1 and f2).
+ */
+filark_status filark_butter_bandpass_sos(int order, double f1, double f2, double fs,
+                                         double *sos_out);
+
+/* Message for the last error returned to this thread ("" if none). */
+const char *filark_last_error_string(void);
+
+/* FILARK_ABI_VERSION of the loaded library. */
+uint32_t filark_abi_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FILARK_H */

@@ -1,0 +1,191 @@
+"""ctypes binding of libfilark (include/filark.h), same names as the C-ABI.
+
+Argument marshalling only: every step of the chain runs in the library's CUDA
+kernels.  There is no CPU fallback -- if the library cannot be loaded, the
+import of the functions below raises.
+"""
+from __future__ import annotations
+
+import ctypes as ct
+import os
+import threading
+
+from . import build as _build
+
+FILARK_ABI_VERSION = 1
+
+FILARK_OK = 0
+FILARK_EINVAL = 1
+FILARK_ENOMEM = 2
+FILARK_ECUDA = 3
+FILARK_EUNSTABLE = 4
+FILARK_ETIMEOUT = 5
+FILARK_ESTATE = 6
+FILARK_ENOSYS = 7
+STATUS_NAMES = {0: "FILARK_OK", 1: "FILARK_EINVAL", 2: "FILARK_ENOMEM", 3: "FILARK_ECUDA",
+                4: "FILARK_EUNSTABLE", 5: "FILARK_ETIMEOUT", 6: "FILARK_ESTATE", 7: "FILARK_ENOSYS"}
+
+FILARK_OUT_RATIO = 1
+FILARK_OUT_BANDPASS = 2
+FILARK_OUT_SPATIAL = 4
+
+FILARK_PREC_AUTO = 0
+FILARK_PREC_MODAL32 = 1
+FILARK_PREC_DENSE64 = 2
+FILARK_PREC_ALL32 = 3
+
+FILARK_MAX_SECTIONS = 8
+FILARK_MAX_SPATIAL_WIDTH = 33
+
+# Every function the header declares (the tests check the library exports them).
+EXPORTED = (
+    "filark_chain_create", "filark_chain_push_chunk", "filark_chain_push_chunk_host",
+    "filark_chain_reset_state", "filark_chain_destroy", "filark_chain_get_state",
+    "filark_chain_set_state", "filark_chain_sync_status", "filark_chain_get_info",
+    "filark_butter_bandpass_sos", "filark_last_error_string", "filark_abi_version",
+)
+
+
+class filark_chain_config(ct.Structure):
+    _fields_ = [
+        ("abi_version", ct.c_uint32),
+        ("n_channels", ct.c_int32),
+        ("fs", ct.c_double),
+        ("n_sections", ct.c_int32),
+        ("sos", ct.POINTER(ct.c_double)),
+        ("spatial_width", ct.c_int32),
+        ("sta_len", ct.c_int32),
+        ("lta_len", ct.c_int32),
+        ("outputs", ct.c_uint32),
+        ("precision", ct.c_int32),
+        ("max_chunk", ct.c_int64),
+    ]
+
+
+class filark_chain_info(ct.Structure):
+    _fields_ = [
+        ("precision", ct.c_int32),
+        ("block_len", ct.c_int32),
+        ("blocks_per_cta", ct.c_int32),
+        ("tile_channels", ct.c_int32),
+        ("halo", ct.c_int32),
+        ("n_slots", ct.c_int32),
+        ("modal_condition", ct.c_double),
+        ("probe_error", ct.c_double),
+        ("ring_len", ct.c_int64),
+        ("device_bytes", ct.c_int64),
+        ("samples", ct.c_int64),
+    ]
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True) -> ct.CDLL:
+    """Load libfilark.so (building it in-tree first if it is missing)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = _build.LIB
+        if not os.path.exists(path):
+            if not build_if_missing:
+                raise OSError(f"libfilark not built: {path}")
+            _build.build()
+        lib = ct.CDLL(path)
+        vp, i64, f_p = ct.c_void_p, ct.c_int64, ct.POINTER(ct.c_float)
+        sig = {
+            "filark_chain_create": ([ct.POINTER(filark_chain_config), ct.c_int, ct.POINTER(vp)], ct.c_int),
+            "filark_chain_push_chunk": ([vp, vp, i64, i64, vp, vp, vp, i64, vp], ct.c_int),
+            "filark_chain_push_chunk_host": ([vp, vp, i64, i64, vp, vp, vp, i64, vp], ct.c_int),
+            "filark_chain_reset_state": ([vp, vp], ct.c_int),
+            "filark_chain_destroy": ([vp], ct.c_int),
+            "filark_chain_get_state": ([vp, vp, ct.POINTER(ct.c_size_t), vp], ct.c_int),
+            "filark_chain_set_state": ([vp, vp, ct.c_size_t, vp], ct.c_int),
+            "filark_chain_sync_status": ([vp, vp], ct.c_int),
+            "filark_chain_get_info": ([vp, ct.POINTER(filark_chain_info)], ct.c_int),
+            "filark_butter_bandpass_sos": ([ct.c_int, ct.c_double, ct.c_double, ct.c_double,
+                                            ct.POINTER(ct.c_double)], ct.c_int),
+            "filark_last_error_string": ([], ct.c_char_p),
+            "filark_abi_version": ([], ct.c_uint32),
+        }
+        for name, (args, res) in sig.items():
+            f = getattr(lib, name)
+            f.argtypes = args
+            f.restype = res
+        del f_p
+        _lib = lib
+        return lib
+
+
+class FilarkError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        msg = load().filark_last_error_string().decode(errors="replace")
+        super().__init__(f"{where}: {STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+def check(status: int, where: str) -> None:
+    if status != FILARK_OK:
+        raise FilarkError(status, where)
+
+
+# Thin wrappers with the C names: raw pointers and sizes in, status out.
+def filark_chain_create(cfg: filark_chain_config, cuda_device: int) -> tuple[int, int | None]:
+    h = ct.c_void_p()
+    st = load().filark_chain_create(ct.byref(cfg), int(cuda_device), ct.byref(h))
+    return st, h.value
+
+
+def filark_chain_push_chunk(h, d_in, ld_in, n, d_ratio, d_bp, d_sp, ld_out, stream) -> int:
+    return load().filark_chain_push_chunk(h, d_in, ld_in, n, d_ratio, d_bp, d_sp, ld_out, stream)
+
+
+def filark_chain_push_chunk_host(h, h_in, ld_in, n, h_ratio, h_bp, h_sp, ld_out, stream) -> int:
+    return load().filark_chain_push_chunk_host(h, h_in, ld_in, n, h_ratio, h_bp, h_sp, ld_out, stream)
+
+
+def filark_chain_reset_state(h, stream) -> int:
+    return load().filark_chain_reset_state(h, stream)
+
+
+def filark_chain_destroy(h) -> int:
+    return load().filark_chain_destroy(h)
+
+
+def filark_chain_get_state(h, buf, nbytes: ct.c_size_t, stream) -> int:
+    return load().filark_chain_get_state(h, buf, ct.byref(nbytes), stream)
+
+
+def filark_chain_set_state(h, buf, nbytes: int, stream) -> int:
+    return load().filark_chain_set_state(h, buf, nbytes, stream)
+
+
+def filark_chain_sync_status(h, stream) -> int:
+    return load().filark_chain_sync_status(h, stream)
+
+
+def filark_chain_get_info(h) -> tuple[int, filark_chain_info]:
+    info = filark_chain_info()
+    st = load().filark_chain_get_info(h, ct.byref(info))
+    return st, info
+
+
+def filark_butter_bandpass_sos(order: int, f1: float, f2: float, fs: float):
+    import numpy as np
+    sos = np.zeros((order, 6), dtype=np.float64)
+    st = load().filark_butter_bandpass_sos(order, f1, f2, fs, sos.ctypes.data_as(ct.POINTER(ct.c_double)))
+    return st, sos
+
+
+def filark_last_error_string() -> str:
+    return load().filark_last_error_string().decode(errors="replace")
+
+
+def filark_abi_version() -> int:
+    return int(load().filark_abi_version())

@@ -1,0 +1,129 @@
+"""Convenience wrapper of the filark C-ABI for PyTorch users.
+
+PyTorch supplies device memory and streams; each call marshals pointers and
+sizes and goes straight to libfilark, where every step runs in CUDA kernels.
+"""
+from __future__ import annotations
+
+import ctypes as ct
+
+import numpy as np
+
+from . import abi
+
+
+def butter_bandpass(order: int, f1: float, f2: float, fs: float) -> np.ndarray:
+    """Butterworth bandpass SOS designed by the library (host code)."""
+    st, sos = abi.filark_butter_bandpass_sos(order, f1, f2, fs)
+    abi.check(st, "filark_butter_bandpass_sos")
+    return sos
+
+
+def _stream_handle(stream) -> int | None:
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream or None
+    if isinstance(stream, int):
+        return stream or None
+    return stream.cuda_stream or None
+
+
+def _ptr(t) -> int | None:
+    return None if t is None else int(t.data_ptr())
+
+
+class Chain:
+    """A stateful chain on one GPU: SOS bandpass -> spatial mean -> STA/LTA."""
+
+    def __init__(self, n_channels: int, sos: np.ndarray | None, fs: float = 1.0,
+                 spatial_width: int = 1, sta_len: int = 0, lta_len: int = 0,
+                 outputs: int = abi.FILARK_OUT_RATIO, precision: int = abi.FILARK_PREC_AUTO,
+                 max_chunk: int = 4096, device: int = 0):
+        abi.load()
+        self._sos = np.ascontiguousarray(np.zeros((0, 6)) if sos is None else sos, dtype=np.float64)
+        cfg = abi.filark_chain_config()
+        cfg.abi_version = abi.FILARK_ABI_VERSION
+        cfg.n_channels = int(n_channels)
+        cfg.fs = float(fs)
+        cfg.n_sections = int(self._sos.shape[0])
+        cfg.sos = self._sos.ctypes.data_as(ct.POINTER(ct.c_double)) if self._sos.size else None
+        cfg.spatial_width = int(spatial_width)
+        cfg.sta_len = int(sta_len)
+        cfg.lta_len = int(lta_len)
+        cfg.outputs = int(outputs)
+        cfg.precision = int(precision)
+        cfg.max_chunk = int(max_chunk)
+        self.cfg = cfg
+        self.n_channels = int(n_channels)
+        self.device = int(device)
+        st, h = abi.filark_chain_create(cfg, self.device)
+        abi.check(st, "filark_chain_create")
+        self._h = h
+
+    # -- lifetime
+    def close(self) -> None:
+        if getattr(self, "_h", None):
+            abi.check(abi.filark_chain_destroy(self._h), "filark_chain_destroy")
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+        return False
+
+    # -- streaming
+    def push(self, x, ratio=None, bandpass=None, spatial=None, stream=None) -> None:
+        """Enqueue one push.  x: CUDA float32 [T][ld_in] (row stride >= C);
+        outputs: CUDA float32 [T][ld_out] tensors or None."""
+        T = int(x.shape[0])
+        ld_in = int(x.stride(0)) if T > 0 else self.n_channels
+        outs = [o for o in (ratio, bandpass, spatial) if o is not None]
+        ld_out = int(outs[0].stride(0)) if outs else self.n_channels
+        st = abi.filark_chain_push_chunk(self._h, _ptr(x), ld_in, T, _ptr(ratio), _ptr(bandpass),
+                                         _ptr(spatial), ld_out, _stream_handle(stream))
+        abi.check(st, "filark_chain_push_chunk")
+
+    def push_host(self, x: np.ndarray, ratio: np.ndarray | None = None,
+                  bandpass: np.ndarray | None = None, spatial: np.ndarray | None = None,
+                  stream=None) -> None:
+        """Synchronous push from host arrays (pinned memory is fastest)."""
+        T = int(x.shape[0])
+        ld_in = int(x.strides[0] // 4) if T > 0 else self.n_channels
+        outs = [o for o in (ratio, bandpass, spatial) if o is not None]
+        ld_out = int(outs[0].strides[0] // 4) if outs else self.n_channels
+        p = lambda a: None if a is None else a.ctypes.data
+        st = abi.filark_chain_push_chunk_host(self._h, p(x), ld_in, T, p(ratio), p(bandpass), p(spatial),
+                                              ld_out, _stream_handle(stream))
+        abi.check(st, "filark_chain_push_chunk_host")
+
+    def reset(self, stream=None) -> None:
+        abi.check(abi.filark_chain_reset_state(self._h, _stream_handle(stream)), "filark_chain_reset_state")
+
+    def sync(self, stream=None) -> None:
+        abi.check(abi.filark_chain_sync_status(self._h, _stream_handle(stream)), "filark_chain_sync_status")
+
+    # -- checkpoint
+    def get_state(self, stream=None) -> bytes:
+        n = ct.c_size_t(0)
+        abi.check(abi.filark_chain_get_state(self._h, None, n, _stream_handle(stream)), "filark_chain_get_state")
+        buf = ct.create_string_buffer(n.value)
+        abi.check(abi.filark_chain_get_state(self._h, buf, n, _stream_handle(stream)), "filark_chain_get_state")
+        return buf.raw[: n.value]
+
+    def set_state(self, state: bytes, stream=None) -> None:
+        buf = ct.create_string_buffer(state, len(state))
+        abi.check(abi.filark_chain_set_state(self._h, buf, len(state), _stream_handle(stream)),
+                  "filark_chain_set_state")
+
+    def info(self) -> dict:
+        st, inf = abi.filark_chain_get_info(self._h)
+        abi.check(st, "filark_chain_get_info")
+        return {k: getattr(inf, k) for k, _ in inf._fields_}

@@ -1,0 +1,558 @@
+// C-ABI of the chunked DAS filter chain (see include/filark.h).
+//
+// Owns the chain's device state and drives the fused kernel.  Every push is
+// split into launches of at most kMaxLaunchSamples samples; each launch reads
+// the carried state from one of two buffers and writes the next state to the
+// other (the halo channels of a tile read a neighbour's state while that
+// neighbour writes its own), so consecutive launches simply alternate.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <set>
+#include <string>
+#include <vector>
+
+#include "filark_internal.h"
+
+using namespace filark;
+
+namespace {
+
+thread_local std::string g_err;
+
+filark_status fail(filark_status st, const std::string &msg) {
+    g_err = msg;
+    return st;
+}
+
+filark_status fail_cuda(cudaError_t e, const char *what) {
+    g_err = std::string(what) + ": " + cudaGetErrorString(e);
+    return FILARK_ECUDA;
+}
+
+// Restores the caller's current device on scope exit.
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = false;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        ok = cudaSetDevice(dev) == cudaSuccess;
+    }
+    ~DeviceGuard() {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+
+std::mutex g_cfg_mu;
+std::set<int> g_configured;
+
+constexpr uint32_t kStateMagic = 0x4B524C46u;   // "FLRK"
+constexpr uint32_t kStateVersion = 1u;
+
+struct StateHeader {
+    uint32_t magic, version;
+    int32_t C, S, ns, nl, K, reserved;
+    int64_t n;
+    int64_t hist_rows;
+};
+
+}  // namespace
+
+struct filark_chain {
+    filark_chain_config cfg{};
+    std::vector<double> sos;
+    Plan plan;
+    int device = 0;
+    int C = 0, K = 1, hw = 0, HP = 0, Wout = 0, n_tiles = 0;
+    bool det = false;
+    int ns = 0, nl = 0;
+    long long Q = 0, ldr = 0;
+    double *iir[2] = {nullptr, nullptr};
+    double *detst[2] = {nullptr, nullptr};
+    float *ring = nullptr;
+    int *status_host = nullptr;   // mapped pinned word written by kernels
+    int *status_dev = nullptr;
+    int parity = 0;
+    long long n = 0;
+    filark_status sticky = FILARK_OK;
+    float *stage[4] = {nullptr, nullptr, nullptr, nullptr};   // in, ratio, bp, sp
+    ChainParams base{};
+    int64_t device_bytes = 0;
+    int use_pdl = 1;
+};
+
+namespace {
+
+void free_chain(filark_chain *h) {
+    if (!h) return;
+    for (int i = 0; i < 2; ++i) {
+        if (h->iir[i]) cudaFree(h->iir[i]);
+        if (h->detst[i]) cudaFree(h->detst[i]);
+    }
+    if (h->ring) cudaFree(h->ring);
+    if (h->status_host) cudaFreeHost(h->status_host);
+    for (float *p : h->stage)
+        if (p) cudaFree(p);
+    delete h;
+}
+
+bool ranges_overlap(const void *a, size_t an, const void *b, size_t bn) {
+    const char *pa = (const char *)a, *pb = (const char *)b;
+    return pa < pb + bn && pb < pa + an;
+}
+
+filark_status zero_state(filark_chain *h, cudaStream_t stream) {
+    const int NS = h->plan.NS;
+    cudaError_t e = cudaSuccess;
+    for (int i = 0; i < 2 && e == cudaSuccess; ++i) {
+        if (h->iir[i]) e = cudaMemsetAsync(h->iir[i], 0, sizeof(double) * (size_t)h->C * (size_t)(2 * NS), stream);
+        if (e == cudaSuccess && h->detst[i]) e = cudaMemsetAsync(h->detst[i], 0, sizeof(double) * (size_t)h->C * 4, stream);
+    }
+    if (e == cudaSuccess && h->ring)
+        e = cudaMemsetAsync(h->ring, 0, sizeof(float) * (size_t)h->Q * (size_t)h->ldr, stream);
+    if (e != cudaSuccess) return fail_cuda(e, "reset: cudaMemsetAsync");
+    *(volatile int *)h->status_host = 0;
+    h->parity = 0;
+    h->n = 0;
+    h->sticky = FILARK_OK;
+    return FILARK_OK;
+}
+
+filark_status check_device_status(filark_chain *h) {
+    if (h->sticky != FILARK_OK) return fail(FILARK_ESTATE, "chain is in an error state; call filark_chain_reset_state");
+    int st = *(volatile int *)h->status_host;
+    if (st != 0) {
+        h->sticky = FILARK_ETIMEOUT;
+        return fail(FILARK_ESTATE, "a device-side error was reported (code " + std::to_string(st) + "); reset the chain");
+    }
+    return FILARK_OK;
+}
+
+filark_status push_device(filark_chain *h, const float *d_in, int64_t ld_in, int64_t T, float *d_ratio,
+                          float *d_bp, float *d_sp, int64_t ld_out, cudaStream_t stream) {
+    const int NS = h->plan.NS;
+    int64_t done = 0;
+    while (done < T) {
+        const int Tl = (int)std::min<int64_t>(T - done, kMaxLaunchSamples);
+        ChainParams p = h->base;
+        p.x = d_in + done * ld_in;
+        p.ldx = ld_in;
+        p.ratio = d_ratio ? d_ratio + done * ld_out : nullptr;
+        p.bp = d_bp ? d_bp + done * ld_out : nullptr;
+        p.sp = d_sp ? d_sp + done * ld_out : nullptr;
+        p.ldo = ld_out;
+        p.iir_in = h->iir[h->parity];
+        p.iir_out = h->iir[h->parity ^ 1];
+        p.det_in = h->detst[h->parity];
+        p.det_out = h->detst[h->parity ^ 1];
+        p.n0 = h->n;
+        p.T = Tl;
+        p.nblk = (Tl + kL - 1) / kL;
+        p.Lr = Tl - (p.nblk - 1) * kL;
+        p.R = (p.nblk + kNB - 1) / kNB;
+        if (NS > 0) {
+            const int nb_last = p.nblk - (p.R - 1) * kNB;
+            const double (*pl)[4] = h->plan.power_cached((nb_last - 1) * kL + p.Lr);
+            const double (*pr)[4] = h->plan.power_cached(p.Lr);
+            for (int s = 0; s < kMaxSlots; ++s)
+                for (int q = 0; q < 4; ++q) {
+                    p.PhiLast[s][q] = pl[s][q];
+                    p.Mr32[s][q] = (float)pr[s][q];
+                }
+        }
+        p.slot_n0 = h->Q > 0 ? (int)(h->n % h->Q) : 0;
+        p.pdl = h->use_pdl;
+        p.x_vec4 = (ld_in % 4 == 0) && (((uintptr_t)p.x & 15u) == 0);
+        bool ov = (ld_out % 4 == 0);
+        for (float *o : {p.ratio, p.bp, p.sp})
+            if (o && ((uintptr_t)o & 15u)) ov = false;
+        p.o_vec4 = ov;
+        cudaError_t e = launch_chain(p, NS, h->det, h->n_tiles, stream);
+        if (e != cudaSuccess) {
+            h->sticky = FILARK_ECUDA;
+            return fail_cuda(e, "push: kernel launch");
+        }
+        h->parity ^= 1;
+        h->n += Tl;
+        done += Tl;
+    }
+    return FILARK_OK;
+}
+
+filark_status validate_push(filark_chain *h, const void *in, int64_t ld_in, int64_t T, const void *ratio,
+                            const void *bp, const void *sp, int64_t ld_out) {
+    if (!h) return fail(FILARK_EINVAL, "chain is NULL");
+    if (T < 0 || T > h->cfg.max_chunk) return fail(FILARK_EINVAL, "n_samples must be in [0, max_chunk]");
+    if (T == 0) return FILARK_OK;
+    if (!in) return fail(FILARK_EINVAL, "input is NULL");
+    if (ld_in < h->C) return fail(FILARK_EINVAL, "ld_in < n_channels");
+    const bool any_out = ratio || bp || sp;
+    if (any_out && ld_out < h->C) return fail(FILARK_EINVAL, "ld_out < n_channels");
+    if (ratio && (!(h->cfg.outputs & FILARK_OUT_RATIO) || !h->det))
+        return fail(FILARK_EINVAL, "ratio output not enabled (outputs mask / detector off)");
+    if (bp && !(h->cfg.outputs & FILARK_OUT_BANDPASS)) return fail(FILARK_EINVAL, "bandpass output not enabled");
+    if (sp && !(h->cfg.outputs & FILARK_OUT_SPATIAL)) return fail(FILARK_EINVAL, "spatial output not enabled");
+    const size_t in_bytes = sizeof(float) * (size_t)((T - 1) * ld_in + h->C);
+    const size_t out_bytes = sizeof(float) * (size_t)((T - 1) * std::max<int64_t>(ld_out, 0) + h->C);
+    for (const void *o : {ratio, bp, sp})
+        if (o && ranges_overlap(in, in_bytes, o, out_bytes)) return fail(FILARK_EINVAL, "an output overlaps the input");
+    const void *outs[3] = {ratio, bp, sp};
+    for (int a = 0; a < 3; ++a)
+        for (int b = a + 1; b < 3; ++b)
+            if (outs[a] && outs[b] && ranges_overlap(outs[a], out_bytes, outs[b], out_bytes))
+                return fail(FILARK_EINVAL, "two outputs overlap");
+    return FILARK_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+uint32_t filark_abi_version(void) { return FILARK_ABI_VERSION; }
+
+const char *filark_last_error_string(void) { return g_err.c_str(); }
+
+filark_status filark_butter_bandpass_sos(int order, double f1, double f2, double fs, double *sos_out) {
+    std::string err;
+    filark_status st = design_butter_bandpass(order, f1, f2, fs, sos_out, &err);
+    if (st != FILARK_OK) return fail(st, err);
+    return FILARK_OK;
+}
+
+filark_status filark_chain_create(const filark_chain_config *cfg, int cuda_device, filark_chain **out) {
+    if (!out) return fail(FILARK_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!cfg) return fail(FILARK_EINVAL, "config is NULL");
+    if (cfg->abi_version != FILARK_ABI_VERSION) return fail(FILARK_EINVAL, "abi_version mismatch");
+    if (cfg->n_channels < 1) return fail(FILARK_EINVAL, "n_channels must be >= 1");
+    if (!(cfg->fs > 0) || !std::isfinite(cfg->fs)) return fail(FILARK_EINVAL, "fs must be > 0");
+    if (cfg->n_sections < 0) return fail(FILARK_EINVAL, "n_sections must be >= 0");
+    if (cfg->n_sections > FILARK_MAX_SECTIONS)
+        return fail(FILARK_ENOSYS, "more than FILARK_MAX_SECTIONS sections");
+    if (cfg->n_sections > 0 && !cfg->sos) return fail(FILARK_EINVAL, "sos is NULL");
+    if (cfg->spatial_width < 1 || cfg->spatial_width % 2 == 0)
+        return fail(FILARK_EINVAL, "spatial_width must be odd and >= 1");
+    if (cfg->spatial_width > FILARK_MAX_SPATIAL_WIDTH)
+        return fail(FILARK_ENOSYS, "spatial_width above FILARK_MAX_SPATIAL_WIDTH");
+    const bool det = cfg->lta_len > 0 || cfg->sta_len > 0;
+    if (det && (cfg->sta_len < 1 || cfg->lta_len < cfg->sta_len))
+        return fail(FILARK_EINVAL, "need 1 <= sta_len <= lta_len (or both 0)");
+    if (cfg->sta_len < 0 || cfg->lta_len < 0) return fail(FILARK_EINVAL, "negative window length");
+    if (cfg->outputs & ~(uint32_t)(FILARK_OUT_RATIO | FILARK_OUT_BANDPASS | FILARK_OUT_SPATIAL))
+        return fail(FILARK_EINVAL, "unknown output bits");
+    if ((cfg->outputs & FILARK_OUT_RATIO) && !det) return fail(FILARK_EINVAL, "ratio output needs the detector");
+    if (cfg->max_chunk < 1) return fail(FILARK_EINVAL, "max_chunk must be >= 1");
+    if (cfg->precision < FILARK_PREC_AUTO || cfg->precision > FILARK_PREC_ALL32)
+        return fail(FILARK_EINVAL, "unknown precision mode");
+    if (cfg->lta_len > (1 << 28)) return fail(FILARK_ENOSYS, "lta_len too large");
+
+    filark_chain *h = new (std::nothrow) filark_chain();
+    if (!h) return fail(FILARK_ENOMEM, "host allocation failed");
+    h->cfg = *cfg;
+    h->sos.assign(cfg->sos ? cfg->sos : (const double *)nullptr,
+                  cfg->sos ? cfg->sos + 6 * cfg->n_sections : (const double *)nullptr);
+    h->cfg.sos = h->sos.empty() ? nullptr : h->sos.data();
+    std::string err;
+    filark_status st = make_plan(h->sos.data(), cfg->n_sections, cfg->precision, &h->plan, &err);
+    if (st != FILARK_OK) {
+        delete h;
+        return fail(st, err);
+    }
+    h->device = cuda_device;
+    h->C = cfg->n_channels;
+    h->K = cfg->spatial_width;
+    h->hw = (h->K - 1) / 2;
+    h->HP = (h->hw + 3) / 4 * 4;
+    h->Wout = kWT - 2 * h->HP;
+    h->n_tiles = (h->C + h->Wout - 1) / h->Wout;
+    h->det = det;
+    h->ns = cfg->sta_len;
+    h->nl = cfg->lta_len;
+
+    DeviceGuard dg(cuda_device);
+    if (!dg.ok) {
+        delete h;
+        return fail(FILARK_ECUDA, "cudaSetDevice failed for device " + std::to_string(cuda_device));
+    }
+    {
+        std::lock_guard<std::mutex> lk(g_cfg_mu);
+        if (!g_configured.count(cuda_device)) {
+            cudaError_t e = configure_chain_kernels();
+            if (e != cudaSuccess) {
+                delete h;
+                return fail_cuda(e, "create: kernel attributes");
+            }
+            g_configured.insert(cuda_device);
+        }
+    }
+    const int NS = h->plan.NS;
+    auto alloc = [&](void **p, size_t bytes) -> bool {
+        if (bytes == 0) return true;
+        if (cudaMalloc(p, bytes) != cudaSuccess) {
+            cudaGetLastError();
+            return false;
+        }
+        h->device_bytes += (int64_t)bytes;
+        return true;
+    };
+    bool ok = true;
+    for (int i = 0; i < 2 && ok; ++i) {
+        if (NS > 0) ok = ok && alloc((void **)&h->iir[i], sizeof(double) * (size_t)h->C * (size_t)(2 * NS));
+        if (det) ok = ok && alloc((void **)&h->detst[i], sizeof(double) * (size_t)h->C * 4);
+    }
+    if (ok && det) {
+        h->Q = (long long)h->nl + std::min<int64_t>(cfg->max_chunk, kMaxLaunchSamples);
+        h->ldr = (h->C + 3) / 4 * 4;
+        ok = alloc((void **)&h->ring, sizeof(float) * (size_t)h->Q * (size_t)h->ldr);
+    }
+    if (ok) {
+        if (cudaHostAlloc((void **)&h->status_host, sizeof(int), cudaHostAllocMapped) != cudaSuccess ||
+            cudaHostGetDevicePointer((void **)&h->status_dev, h->status_host, 0) != cudaSuccess) {
+            cudaGetLastError();
+            ok = false;
+        }
+    }
+    if (!ok) {
+        free_chain(h);
+        return fail(FILARK_ENOMEM, "device allocation failed");
+    }
+    // kernel parameter template
+    ChainParams &b = h->base;
+    std::memset(&b, 0, sizeof(b));
+    b.tab = h->plan.tab;
+    h->plan.slot_power(kL * kNB, b.Phi);
+    h->plan.slot_power(kL, b.ML64);
+    b.ring = h->ring;
+    b.ldr = h->ldr;
+    b.Q = h->Q > 0 ? (int)h->Q : 1;
+    b.C = h->C;
+    b.hw = h->hw;
+    b.HP = h->HP;
+    b.Wout = h->Wout;
+    b.ns = h->ns;
+    b.nl = h->nl;
+    b.ratio_scale = det ? (float)((double)h->nl / (double)h->ns) : 0.f;
+    b.r_vec4 = 1;
+    b.all32 = h->plan.mode == FILARK_PREC_ALL32;
+    b.status = h->status_dev;
+
+    st = zero_state(h, nullptr);
+    if (st == FILARK_OK) {
+        cudaError_t e = cudaStreamSynchronize(nullptr);
+        if (e != cudaSuccess) st = fail_cuda(e, "create: synchronize");
+    }
+    if (st != FILARK_OK) {
+        free_chain(h);
+        return st;
+    }
+    *out = h;
+    return FILARK_OK;
+}
+
+filark_status filark_chain_destroy(filark_chain *h) {
+    if (!h) return FILARK_OK;
+    DeviceGuard dg(h->device);
+    cudaDeviceSynchronize();
+    free_chain(h);
+    return FILARK_OK;
+}
+
+filark_status filark_chain_reset_state(filark_chain *h, filark_stream_t stream) {
+    if (!h) return fail(FILARK_EINVAL, "chain is NULL");
+    DeviceGuard dg(h->device);
+    return zero_state(h, (cudaStream_t)stream);
+}
+
+filark_status filark_chain_push_chunk(filark_chain *h, const float *d_in, int64_t ld_in, int64_t n_samples,
+                                      float *d_ratio, float *d_bandpass, float *d_spatial, int64_t ld_out,
+                                      filark_stream_t stream) {
+    filark_status st = validate_push(h, d_in, ld_in, n_samples, d_ratio, d_bandpass, d_spatial, ld_out);
+    if (st != FILARK_OK) return st;
+    st = check_device_status(h);
+    if (st != FILARK_OK) return st;
+    if (n_samples == 0) return FILARK_OK;
+    DeviceGuard dg(h->device);
+    return push_device(h, d_in, ld_in, n_samples, d_ratio, d_bandpass, d_spatial, ld_out, (cudaStream_t)stream);
+}
+
+filark_status filark_chain_push_chunk_host(filark_chain *h, const float *h_in, int64_t ld_in, int64_t n_samples,
+                                           float *h_ratio, float *h_bandpass, float *h_spatial, int64_t ld_out,
+                                           filark_stream_t stream) {
+    filark_status st = validate_push(h, h_in, ld_in, n_samples, h_ratio, h_bandpass, h_spatial, ld_out);
+    if (st != FILARK_OK) return st;
+    st = check_device_status(h);
+    if (st != FILARK_OK) return st;
+    if (n_samples == 0) return FILARK_OK;
+    DeviceGuard dg(h->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t plane = sizeof(float) * (size_t)h->cfg.max_chunk * (size_t)h->C;
+    float *hosts[4] = {const_cast<float *>(h_in), h_ratio, h_bandpass, h_spatial};
+    for (int i = 0; i < 4; ++i) {
+        if (hosts[i] && !h->stage[i]) {
+            if (cudaMalloc((void **)&h->stage[i], plane) != cudaSuccess) {
+                cudaGetLastError();
+                return fail(FILARK_ENOMEM, "push_host: staging allocation failed");
+            }
+            h->device_bytes += (int64_t)plane;
+        }
+    }
+    const size_t row = sizeof(float) * (size_t)h->C;
+    cudaError_t e = cudaMemcpy2DAsync(h->stage[0], row, h_in, sizeof(float) * (size_t)ld_in, row,
+                                      (size_t)n_samples, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return fail_cuda(e, "push_host: input copy");
+    st = push_device(h, h->stage[0], h->C, n_samples, h_ratio ? h->stage[1] : nullptr,
+                     h_bandpass ? h->stage[2] : nullptr, h_spatial ? h->stage[3] : nullptr, h->C, s);
+    if (st != FILARK_OK) return st;
+    for (int i = 1; i < 4; ++i) {
+        if (!hosts[i]) continue;
+        e = cudaMemcpy2DAsync(hosts[i], sizeof(float) * (size_t)ld_out, h->stage[i], row, row, (size_t)n_samples,
+                              cudaMemcpyDeviceToHost, s);
+        if (e != cudaSuccess) return fail_cuda(e, "push_host: output copy");
+    }
+    e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return fail_cuda(e, "push_host: synchronize");
+    return check_device_status(h);
+}
+
+filark_status filark_chain_sync_status(filark_chain *h, filark_stream_t stream) {
+    if (!h) return fail(FILARK_EINVAL, "chain is NULL");
+    DeviceGuard dg(h->device);
+    cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+    if (e != cudaSuccess) {
+        h->sticky = FILARK_ECUDA;
+        return fail_cuda(e, "sync_status");
+    }
+    return check_device_status(h);
+}
+
+filark_status filark_chain_get_info(const filark_chain *h, filark_chain_info *out) {
+    if (!h || !out) return fail(FILARK_EINVAL, "NULL argument");
+    std::memset(out, 0, sizeof(*out));
+    out->precision = h->plan.mode;
+    out->block_len = kL;
+    out->blocks_per_cta = kNB;
+    out->tile_channels = h->Wout;
+    out->halo = h->hw;
+    out->n_slots = h->plan.NS;
+    out->modal_condition = h->plan.kappa;
+    out->probe_error = h->plan.probe_err;
+    out->ring_len = h->Q;
+    out->device_bytes = h->device_bytes;
+    out->samples = h->n;
+    return FILARK_OK;
+}
+
+filark_status filark_chain_get_state(filark_chain *h, void *host_buf, size_t *bytes, filark_stream_t stream) {
+    if (!h || !bytes) return fail(FILARK_EINVAL, "NULL argument");
+    const int S = h->plan.S, NS = h->plan.NS, C = h->C;
+    const int64_t hist = h->det ? std::min<int64_t>(h->n, h->nl) : 0;
+    const size_t need = sizeof(StateHeader) + sizeof(double) * (size_t)C * (size_t)(2 * S) +
+                        sizeof(double) * (size_t)C * 3 + sizeof(float) * (size_t)hist * (size_t)C;
+    if (!host_buf) {
+        *bytes = need;
+        return FILARK_OK;
+    }
+    if (*bytes < need) return fail(FILARK_EINVAL, "state buffer too small");
+    DeviceGuard dg(h->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return fail_cuda(e, "get_state: synchronize");
+    filark_status st = check_device_status(h);
+    if (st != FILARK_OK) return st;
+    char *p = (char *)host_buf;
+    StateHeader hd{kStateMagic, kStateVersion, C, S, h->ns, h->nl, h->K, 0, h->n, hist};
+    std::memcpy(p, &hd, sizeof(hd));
+    p += sizeof(hd);
+    if (S > 0) {
+        std::vector<double> m((size_t)C * (size_t)(2 * NS));
+        e = cudaMemcpy(m.data(), h->iir[h->parity], sizeof(double) * m.size(), cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return fail_cuda(e, "get_state: copy");
+        const int n2 = 2 * S;
+        std::vector<double> canon((size_t)C * (size_t)n2);
+        for (int c = 0; c < C; ++c)
+            for (int r = 0; r < n2; ++r) {
+                long double acc = 0;
+                for (int q = 0; q < n2; ++q)
+                    acc += h->plan.W[(size_t)r * n2 + q] * (long double)m[(size_t)c * (2 * NS) + q];
+                canon[(size_t)c * n2 + r] = (double)acc;
+            }
+        std::memcpy(p, canon.data(), sizeof(double) * canon.size());
+        p += sizeof(double) * canon.size();
+    }
+    std::vector<double> d((size_t)C * 4, 0.0);
+    if (h->det) {
+        e = cudaMemcpy(d.data(), h->detst[h->parity], sizeof(double) * d.size(), cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return fail_cuda(e, "get_state: copy");
+    }
+    for (int c = 0; c < C; ++c) std::memcpy(p + sizeof(double) * 3 * (size_t)c, &d[(size_t)c * 4], sizeof(double) * 3);
+    p += sizeof(double) * 3 * (size_t)C;
+    for (int64_t k = 0; k < hist; ++k) {
+        const long long nabs = h->n - hist + k;
+        const long long slot = nabs % h->Q;
+        e = cudaMemcpy(p, h->ring + slot * h->ldr, sizeof(float) * (size_t)C, cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return fail_cuda(e, "get_state: copy");
+        p += sizeof(float) * (size_t)C;
+    }
+    *bytes = need;
+    return FILARK_OK;
+}
+
+filark_status filark_chain_set_state(filark_chain *h, const void *host_buf, size_t bytes, filark_stream_t stream) {
+    if (!h || !host_buf) return fail(FILARK_EINVAL, "NULL argument");
+    if (bytes < sizeof(StateHeader)) return fail(FILARK_EINVAL, "state buffer too small");
+    StateHeader hd;
+    std::memcpy(&hd, host_buf, sizeof(hd));
+    const int S = h->plan.S, NS = h->plan.NS, C = h->C;
+    if (hd.magic != kStateMagic || hd.version != kStateVersion) return fail(FILARK_EINVAL, "not a filark state");
+    if (hd.C != C || hd.S != S || hd.ns != h->ns || hd.nl != h->nl || hd.K != h->K || hd.n < 0)
+        return fail(FILARK_EINVAL, "state does not match this chain's configuration");
+    const int64_t hist = h->det ? std::min<int64_t>(hd.n, h->nl) : 0;
+    if (hd.hist_rows != hist) return fail(FILARK_EINVAL, "state history length mismatch");
+    const size_t need = sizeof(StateHeader) + sizeof(double) * (size_t)C * (size_t)(2 * S) +
+                        sizeof(double) * (size_t)C * 3 + sizeof(float) * (size_t)hist * (size_t)C;
+    if (bytes < need) return fail(FILARK_EINVAL, "state buffer too small");
+    DeviceGuard dg(h->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    filark_status st = zero_state(h, s);
+    if (st != FILARK_OK) return st;
+    cudaError_t e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return fail_cuda(e, "set_state: synchronize");
+    const char *p = (const char *)host_buf + sizeof(StateHeader);
+    if (S > 0) {
+        const int n2 = 2 * S;
+        std::vector<double> canon((size_t)C * (size_t)n2);
+        std::memcpy(canon.data(), p, sizeof(double) * canon.size());
+        p += sizeof(double) * canon.size();
+        std::vector<double> m((size_t)C * (size_t)(2 * NS), 0.0);
+        for (int c = 0; c < C; ++c)
+            for (int r = 0; r < n2; ++r) {
+                long double acc = 0;
+                for (int q = 0; q < n2; ++q)
+                    acc += h->plan.Winv[(size_t)r * n2 + q] * (long double)canon[(size_t)c * n2 + q];
+                m[(size_t)c * (2 * NS) + r] = (double)acc;
+            }
+        e = cudaMemcpy(h->iir[0], m.data(), sizeof(double) * m.size(), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) return fail_cuda(e, "set_state: copy");
+    }
+    if (h->det) {
+        std::vector<double> d((size_t)C * 4, 0.0);
+        for (int c = 0; c < C; ++c) std::memcpy(&d[(size_t)c * 4], p + sizeof(double) * 3 * (size_t)c, sizeof(double) * 3);
+        e = cudaMemcpy(h->detst[0], d.data(), sizeof(double) * d.size(), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) return fail_cuda(e, "set_state: copy");
+    }
+    p += sizeof(double) * 3 * (size_t)C;
+    for (int64_t k = 0; k < hist; ++k) {
+        const long long nabs = hd.n - hist + k;
+        const long long slot = nabs % h->Q;
+        e = cudaMemcpy(h->ring + slot * h->ldr, p, sizeof(float) * (size_t)C, cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) return fail_cuda(e, "set_state: copy");
+        p += sizeof(float) * (size_t)C;
+    }
+    h->parity = 0;
+    h->n = hd.n;
+    return FILARK_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,555 @@
+// Fused chunked DAS chain kernel for sm_103a: causal SOS bandpass (block
+// state-space form, see plan.cpp), spatial running mean, STA/LTA detector.
+//
+// Work decomposition of one launch (<= 2048 samples of every channel):
+//   grid.x  = channel tiles; a tile is kWT = 64 consecutive channels of which
+//             Wout are outputs and HP on each side are halo (the spatial mean
+//             of an output channel needs its neighbours' bandpass output, so
+//             the halo channels' IIR is computed again by the neighbour tile --
+//             the overlap-aware halo expansion of Sec. 3.4);
+//   grid.y  = R time ranges of kNB blocks x kL samples; the R CTAs of a tile
+//             form one thread-block cluster and exchange their IIR carries and
+//             detector sums through distributed shared memory.
+//
+// Per CTA (512 threads):
+//   0. load the input tile [256 samples][64 channels] into shared memory;
+//   1. per (channel, block): local FIR response y_loc = T_L x and the block's
+//      end state e = K x from zero state (FP32, tables are FFMA constant
+//      operands);
+//   2. per (channel, slot): carry scan m_{j+1} = M m_j + e_j -- FP32 inside the
+//      CTA, FP64 across the CTAs of the cluster and across launches;
+//   3. fix-up y_bp = y_loc + G m_j, written back in place;
+//   4. spatial mean over the 2h+1 neighbouring columns, cf = y_sp^2, written to
+//      the detector's history ring and kept in place;
+//   5. STA/LTA: exact (compensated) block sums, FP64 scan across blocks and
+//      CTAs, then FP32 running sums inside each block and the ratio.
+//
+// Consecutive launches on a stream overlap through programmatic dependent
+// launch: phases 0-1 only read the caller's input, so a launch starts them
+// while the previous one drains, and waits for it before touching the state.
+#include <climits>
+
+#include <cooperative_groups.h>
+
+#include "filark_internal.h"
+
+namespace cg = cooperative_groups;
+
+namespace filark {
+
+namespace {
+
+__device__ __forceinline__ void cluster_sync_release_acquire() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n" ::: "memory");
+    asm volatile("barrier.cluster.wait.acquire.aligned;\n" ::: "memory");
+}
+
+__device__ __forceinline__ void pdl_launch_dependents() {
+    asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
+}
+
+__device__ __forceinline__ void pdl_wait() {
+    asm volatile("griddepcontrol.wait;\n" ::: "memory");
+}
+
+// s + v for s, v >= 0 with the rounding error kept in c (Fast2Sum on the larger
+// operand), so a block sum of non-negative values is carried as s + c with an
+// error of order eps^2 instead of eps.
+__device__ __forceinline__ void acc_nonneg(float &s, float &c, float v) {
+    const float t = s + v;
+    const float big = fmaxf(s, v), small = fminf(s, v);
+    c += small - (t - big);
+    s = t;
+}
+
+// shared memory carve-up (floats)
+constexpr int kTileFloats = kTileRows * kWT;                 // 16384
+constexpr int kEFloats = kNB * 2 * kMaxSlots * kWT;          // 8192
+constexpr int kERFloats = 2 * kMaxSlots * kWT;               // 1024
+constexpr int kAggFloats = 2 * kMaxSlots * kWT;              // 1024 (also holds 3 x 64 doubles)
+constexpr int kSmemFloats = kTileFloats + kEFloats + kERFloats + kAggFloats;
+
+// detector overlays on the E region (free after the IIR fix-up); offsets in floats
+constexpr int kDetDS = 0;                                    // double [kNB][kWT]
+constexpr int kDetDL = kDetDS + kNB * kWT * 2;               // double [kNB][kWT]
+constexpr int kDetBS = kDetDL + kNB * kWT * 2;               // double [kNB][kWT]
+constexpr int kDetBL = kDetBS + kNB * kWT * 2;               // double [kNB][kWT]
+constexpr int kDetLZ = kDetBL + kNB * kWT * 2;               // int [kNB][kWT] last nonzero row
+constexpr int kDetBZ = kDetLZ + kNB * kWT;                   // int [kNB][kWT] its running max
+static_assert(kDetBZ + kNB * kWT <= kEFloats, "detector overlays must fit in the E region");
+
+constexpr int kNoNonzero = INT_MIN / 2;   // "no nonzero cf" as a relative row index
+
+template <int NS, bool DET>
+__global__ void __launch_bounds__(kThreads, 2) chain_fwd_kernel(const __grid_constant__ ChainParams p) {
+    extern __shared__ __align__(16) float smem[];
+    float *tile = smem;                       // [kTileRows][kWT]
+    float *E = tile + kTileFloats;            // [kNB][2*NS][kWT]
+    float *ER = E + kEFloats;                 // [2*NS][kWT]
+    float *AGG = ER + kERFloats;              // [2*NS][kWT]; later 3 x kWT doubles
+
+    if (p.pdl) pdl_launch_dependents();
+
+    cg::cluster_group cluster = cg::this_cluster();
+    const int tid = threadIdx.x;
+    const int r = blockIdx.y;                 // time range within the launch = cluster rank
+    const int R = p.R;
+    const int c0 = blockIdx.x * p.Wout;       // first output channel of the tile
+    const int cbase = c0 - p.HP;              // channel of tile column 0
+    const int blk0 = r * kNB;
+    const int nb = min(kNB, p.nblk - blk0);   // blocks in this CTA (>= 1)
+    const int row0 = blk0 * kL;               // first launch row of this CTA
+    const int rows = min(nb * kL, p.T - row0);
+    const bool last_cta = (r == R - 1);
+
+    // ---------------------------------------------------------------- 0. load
+    {
+        const float *xb = p.x + (long long)row0 * p.ldx;
+        if (p.x_vec4) {
+#pragma unroll
+            for (int it = 0; it < kTileFloats / 4 / kThreads; ++it) {
+                const int f = tid + it * kThreads;
+                const int row = f >> 4, col = (f & 15) << 2;
+                const int cgl = cbase + col;
+                float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (row < rows) {
+                    const float *src = xb + (long long)row * p.ldx + cgl;
+                    if (cgl >= 0 && cgl + 3 < p.C) {
+                        v = __ldg(reinterpret_cast<const float4 *>(src));
+                    } else {
+                        if (cgl + 0 >= 0 && cgl + 0 < p.C) v.x = __ldg(src + 0);
+                        if (cgl + 1 >= 0 && cgl + 1 < p.C) v.y = __ldg(src + 1);
+                        if (cgl + 2 >= 0 && cgl + 2 < p.C) v.z = __ldg(src + 2);
+                        if (cgl + 3 >= 0 && cgl + 3 < p.C) v.w = __ldg(src + 3);
+                    }
+                }
+                *reinterpret_cast<float4 *>(&tile[row * kWT + col]) = v;
+            }
+        } else {
+            for (int f = tid; f < kTileFloats; f += kThreads) {
+                const int row = f / kWT, col = f % kWT;
+                const int cgl = cbase + col;
+                float v = 0.f;
+                if (row < rows && cgl >= 0 && cgl < p.C) v = __ldg(xb + (long long)row * p.ldx + cgl);
+                tile[f] = v;
+            }
+        }
+    }
+    __syncthreads();
+
+    // (channel, block) mapping: warps 2j, 2j+1 cover block j, columns 0-31 / 32-63
+    const int warp = tid >> 5, lane = tid & 31;
+    const int jb = warp >> 1;
+    const int col = ((warp & 1) << 5) | lane;
+    const int cgc = cbase + col;
+    const bool col_owned = col >= p.HP && col < p.HP + p.Wout && cgc < p.C;
+
+    // ------------------------------------------------ 1. local responses
+    if constexpr (NS > 0) {
+        if (jb < nb) {
+            const float *xc = tile + (jb * kL) * kWT + col;
+            if (blk0 + jb == p.nblk - 1 && p.Lr < kL) {
+                // ragged last block: its end state after Lr samples is K applied
+                // to the input right-aligned in the block
+                const int off = kL - p.Lr;
+                float e[2 * NS];
+#pragma unroll
+                for (int q = 0; q < 2 * NS; ++q) e[q] = 0.f;
+#pragma unroll
+                for (int i = 0; i < kL; ++i) {
+                    const float xi = (i >= off) ? xc[(i - off) * kWT] : 0.f;
+#pragma unroll
+                    for (int q = 0; q < 2 * NS; ++q) e[q] = fmaf(p.tab.K[i][q], xi, e[q]);
+                }
+#pragma unroll
+                for (int q = 0; q < 2 * NS; ++q) ER[q * kWT + col] = e[q];
+            }
+            float y[kL];
+            float e[2 * NS];
+#pragma unroll
+            for (int k = 0; k < kL; ++k) y[k] = 0.f;
+#pragma unroll
+            for (int q = 0; q < 2 * NS; ++q) e[q] = 0.f;
+#pragma unroll
+            for (int i = 0; i < kL; ++i) {
+                const float xi = xc[i * kWT];
+#pragma unroll
+                for (int k = i; k < kL; ++k) y[k] = fmaf(p.tab.h[k - i], xi, y[k]);
+#pragma unroll
+                for (int q = 0; q < 2 * NS; ++q) e[q] = fmaf(p.tab.K[i][q], xi, e[q]);
+            }
+#pragma unroll
+            for (int q = 0; q < 2 * NS; ++q) E[(jb * 2 * NS + q) * kWT + col] = e[q];
+            // the block's input is no longer needed: park y_loc in its place
+            float *xw = tile + (jb * kL) * kWT + col;
+#pragma unroll
+            for (int k = 0; k < kL; ++k) xw[k * kWT] = y[k];
+        }
+    }
+
+    // everything below reads state that the previous launch writes
+    if (p.pdl) pdl_wait();
+    __syncthreads();
+
+    if constexpr (NS > 0) {
+        // ------------------------------------------------ 2. carry scan
+        const int sc = tid % kWT, s = tid / kWT;
+        const bool act = s < NS;
+        const bool ragged_last = last_cta && p.Lr < kL;
+        if (act) {
+            // this CTA's aggregate: end state of its range from a zero start (FP32)
+            float a0 = 0.f, a1 = 0.f;
+            for (int j = 0; j < nb; ++j) {
+                float e0, e1, m00, m01, m10, m11;
+                if (ragged_last && j == nb - 1) {
+                    e0 = ER[(2 * s) * kWT + sc];
+                    e1 = ER[(2 * s + 1) * kWT + sc];
+                    m00 = p.Mr32[s][0]; m01 = p.Mr32[s][1]; m10 = p.Mr32[s][2]; m11 = p.Mr32[s][3];
+                } else {
+                    e0 = E[(j * 2 * NS + 2 * s) * kWT + sc];
+                    e1 = E[(j * 2 * NS + 2 * s + 1) * kWT + sc];
+                    m00 = p.tab.M[s][0]; m01 = p.tab.M[s][1]; m10 = p.tab.M[s][2]; m11 = p.tab.M[s][3];
+                }
+                const float t0 = fmaf(m00, a0, fmaf(m01, a1, e0));
+                const float t1 = fmaf(m10, a0, fmaf(m11, a1, e1));
+                a0 = t0;
+                a1 = t1;
+            }
+            AGG[(2 * s) * kWT + sc] = a0;
+            AGG[(2 * s + 1) * kWT + sc] = a1;
+        }
+        cluster_sync_release_acquire();
+        if (act) {
+            const int cgs = cbase + sc;
+            double d0 = 0.0, d1 = 0.0;
+            if (cgs >= 0 && cgs < p.C) {
+                d0 = p.iir_in[(long long)cgs * (2 * NS) + 2 * s];
+                d1 = p.iir_in[(long long)cgs * (2 * NS) + 2 * s + 1];
+            }
+            const double P00 = p.Phi[s][0], P01 = p.Phi[s][1], P10 = p.Phi[s][2], P11 = p.Phi[s][3];
+            for (int q = 0; q < r; ++q) {
+                const float *ragg = cluster.map_shared_rank(AGG, q);
+                const double g0 = ragg[(2 * s) * kWT + sc], g1 = ragg[(2 * s + 1) * kWT + sc];
+                double t0 = fma(P00, d0, fma(P01, d1, g0));
+                double t1 = fma(P10, d0, fma(P11, d1, g1));
+                if (p.all32) {
+                    t0 = (float)t0;
+                    t1 = (float)t1;
+                }
+                d0 = t0;
+                d1 = t1;
+            }
+            if (last_cta && sc >= p.HP && sc < p.HP + p.Wout && cgs < p.C) {
+                const double g0 = AGG[(2 * s) * kWT + sc], g1 = AGG[(2 * s + 1) * kWT + sc];
+                double u0 = fma(p.PhiLast[s][0], d0, fma(p.PhiLast[s][1], d1, g0));
+                double u1 = fma(p.PhiLast[s][2], d0, fma(p.PhiLast[s][3], d1, g1));
+                if (p.all32) {
+                    u0 = (float)u0;
+                    u1 = (float)u1;
+                }
+                p.iir_out[(long long)cgs * (2 * NS) + 2 * s] = u0;
+                p.iir_out[(long long)cgs * (2 * NS) + 2 * s + 1] = u1;
+            }
+            // block start states (FP32), written over the block end states
+            const float m00 = p.tab.M[s][0], m01 = p.tab.M[s][1], m10 = p.tab.M[s][2], m11 = p.tab.M[s][3];
+            float f0 = (float)d0, f1 = (float)d1;
+            for (int j = 0; j < nb; ++j) {
+                float *pe0 = &E[(j * 2 * NS + 2 * s) * kWT + sc];
+                float *pe1 = pe0 + kWT;
+                const float e0 = *pe0, e1 = *pe1;
+                *pe0 = f0;
+                *pe1 = f1;
+                const float t0 = fmaf(m00, f0, fmaf(m01, f1, e0));
+                const float t1 = fmaf(m10, f0, fmaf(m11, f1, e1));
+                f0 = t0;
+                f1 = t1;
+            }
+        }
+        __syncthreads();
+
+        // ------------------------------------------------ 3. fix-up
+        if (jb < nb) {
+            float m[2 * NS];
+#pragma unroll
+            for (int q = 0; q < 2 * NS; ++q) m[q] = E[(jb * 2 * NS + q) * kWT + col];
+            float *tc = tile + (jb * kL) * kWT + col;
+            const bool tap = p.bp && col_owned;
+            float *bpc = tap ? p.bp + (long long)(row0 + jb * kL) * p.ldo + cgc : nullptr;
+#pragma unroll
+            for (int k = 0; k < kL; ++k) {
+                float acc = tc[k * kWT];
+#pragma unroll
+                for (int q = 0; q < 2 * NS; ++q) acc = fmaf(p.tab.G[k][q], m[q], acc);
+                tc[k * kWT] = acc;
+                if (tap && jb * kL + k < rows) bpc[(long long)k * p.ldo] = acc;
+            }
+        }
+    } else {
+        // no IIR stage: the bandpass output is the input
+        if (p.bp && col_owned && jb < nb) {
+            for (int k = 0; k < kL; ++k) {
+                const int row = jb * kL + k;
+                if (row < rows) p.bp[(long long)(row0 + row) * p.ldo + cgc] = tile[row * kWT + col];
+            }
+        }
+    }
+    __syncthreads();
+
+    // ------------------------------------------------ 4. spatial mean, cf
+    // ring slot of tile row 0 (the host passes n0 mod Q; row0 < 2048 <= Q)
+    int slot_r0 = p.slot_n0 + row0;
+    if (slot_r0 >= p.Q) slot_r0 -= p.Q;
+    if (p.sp || DET) {
+        const int g = tid & 15, ro = tid >> 4;      // 4-column group, row offset
+        const int ngroups = p.Wout >> 2;
+        const int q0 = p.HP + 4 * g;                // first output column of the group
+        float cfv[kTileRows / 32][4];
+        const bool gact = g < ngroups;
+        // 1/|W| for the 4 channels (the window shrinks at the array ends)
+        float inv[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int cch = c0 + 4 * g + u;
+            const int lo = max(0, cch - p.hw), hi = min(p.C - 1, cch + p.hw);
+            inv[u] = 1.0f / (float)max(1, hi - lo + 1);
+        }
+#pragma unroll
+        for (int it = 0; it < kTileRows / 32; ++it) {
+            const int row = ro + 32 * it;
+            cfv[it][0] = cfv[it][1] = cfv[it][2] = cfv[it][3] = 0.f;
+            if (gact && row < rows) {
+                const float *tr = tile + row * kWT;
+                float sacc = 0.f;
+                for (int q = q0 - p.hw; q <= q0 + p.hw; ++q) sacc += tr[q];
+                float ysp[4];
+                ysp[0] = sacc * inv[0];
+#pragma unroll
+                for (int u = 1; u < 4; ++u) {
+                    sacc += tr[q0 + u + p.hw] - tr[q0 + u - 1 - p.hw];
+                    ysp[u] = sacc * inv[u];
+                }
+                const int cch = c0 + 4 * g;
+                const long long orow = row0 + row;
+                if (p.sp) {
+                    float *dst = p.sp + orow * p.ldo + cch;
+                    if (p.o_vec4 && cch + 3 < p.C) {
+                        *reinterpret_cast<float4 *>(dst) = make_float4(ysp[0], ysp[1], ysp[2], ysp[3]);
+                    } else {
+#pragma unroll
+                        for (int u = 0; u < 4; ++u)
+                            if (cch + u < p.C) dst[u] = ysp[u];
+                    }
+                }
+                if (DET) {
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) cfv[it][u] = ysp[u] * ysp[u];
+                    int slot = slot_r0 + row;
+                    if (slot >= p.Q) slot -= p.Q;
+                    float *dst = p.ring + (long long)slot * p.ldr + cch;
+                    if (p.r_vec4 && cch + 3 < p.C) {
+                        *reinterpret_cast<float4 *>(dst) = make_float4(cfv[it][0], cfv[it][1], cfv[it][2], cfv[it][3]);
+                    } else {
+#pragma unroll
+                        for (int u = 0; u < 4; ++u)
+                            if (cch + u < p.C) dst[u] = cfv[it][u];
+                    }
+                }
+            }
+        }
+        if (DET) {
+            __syncthreads();   // every thread has read its windows
+            if (gact) {
+#pragma unroll
+                for (int it = 0; it < kTileRows / 32; ++it) {
+                    const int row = ro + 32 * it;
+                    if (row < rows)
+                        *reinterpret_cast<float4 *>(&tile[row * kWT + q0]) =
+                            make_float4(cfv[it][0], cfv[it][1], cfv[it][2], cfv[it][3]);
+                }
+            }
+        }
+    }
+
+    if constexpr (DET) {
+        // ring writes of every CTA of the cluster become visible to the others
+        __threadfence();
+        cluster_sync_release_acquire();
+
+        // ------------------------------------------------ 5. STA/LTA
+        double *DS = reinterpret_cast<double *>(E + kDetDS);
+        double *DL = reinterpret_cast<double *>(E + kDetDL);
+        double *BS = reinterpret_cast<double *>(E + kDetBS);
+        double *BL = reinterpret_cast<double *>(E + kDetBL);
+        int *LZ = reinterpret_cast<int *>(E + kDetLZ);
+        int *BZ = reinterpret_cast<int *>(E + kDetBZ);
+        double *AGG2 = reinterpret_cast<double *>(AGG);     // [3][kWT]
+        const bool dact = col_owned && jb < nb;
+        const long long nrow0 = p.n0 + row0;                 // global index of tile row 0
+        const int rbeg = jb * kL;
+        // cf of tile row lr (< rows), from this tile or, for lr < 0, from the
+        // history ring (0 before the first sample)
+        auto cf_at = [&](int lr) -> float {
+            if (lr >= 0) return tile[lr * kWT + col];
+            if (nrow0 + lr < 0) return 0.f;
+            int slot = slot_r0 + lr;
+            if (slot < 0) slot += p.Q;
+            return __ldcg(p.ring + (long long)slot * p.ldr + cgc);
+        };
+        // pass a: exact block sums of cf and of the exiting values
+        if (dact) {
+            float cs = 0.f, cc = 0.f, ss = 0.f, sc2 = 0.f, ls = 0.f, lc = 0.f;
+            int lz = kNoNonzero;
+#pragma unroll 8
+            for (int k = 0; k < kL; ++k) {
+                const int row = rbeg + k;
+                if (row < rows) {
+                    const float cf = tile[row * kWT + col];
+                    const float es = cf_at(row - p.ns);
+                    const float el = cf_at(row - p.nl);
+                    acc_nonneg(cs, cc, cf);
+                    acc_nonneg(ss, sc2, es);
+                    acc_nonneg(ls, lc, el);
+                    if (cf != 0.f) lz = row;
+                }
+            }
+            const double tot = (double)cs + (double)cc;
+            DS[jb * kWT + col] = tot - ((double)ss + (double)sc2);
+            DL[jb * kWT + col] = tot - ((double)ls + (double)lc);
+            LZ[jb * kWT + col] = lz;
+        }
+        __syncthreads();
+        // exclusive scan over this CTA's blocks, one thread per column (FP64)
+        if (tid < kWT) {
+            const int c = tid;
+            const bool own = c >= p.HP && c < p.HP + p.Wout && cbase + c < p.C;
+            if (own) {
+                double bs = 0.0, bl = 0.0;
+                int bz = kNoNonzero;
+                for (int j = 0; j < nb; ++j) {
+                    BS[j * kWT + c] = bs;
+                    BL[j * kWT + c] = bl;
+                    BZ[j * kWT + c] = bz;
+                    bs += DS[j * kWT + c];
+                    bl += DL[j * kWT + c];
+                    bz = max(bz, LZ[j * kWT + c]);
+                }
+                AGG2[0 * kWT + c] = bs;
+                AGG2[1 * kWT + c] = bl;
+                AGG2[2 * kWT + c] = bz == kNoNonzero ? 0.0 : (double)(nrow0 + bz + 1);
+            }
+        }
+        cluster_sync_release_acquire();
+        if (tid < kWT) {
+            const int c = tid;
+            const int cgl = cbase + c;
+            const bool own = c >= p.HP && c < p.HP + p.Wout && cgl < p.C;
+            if (own) {
+                // state at the start of this CTA: carried state + earlier CTAs
+                double bS = p.det_in[(long long)cgl * 4 + 0];
+                double bL = p.det_in[(long long)cgl * 4 + 1];
+                double bz = p.det_in[(long long)cgl * 4 + 2];    // 1 + index of last nonzero, 0 = none
+                for (int q = 0; q < r; ++q) {
+                    const double *ra = cluster.map_shared_rank(AGG2, q);
+                    bS += ra[0 * kWT + c];
+                    bL += ra[1 * kWT + c];
+                    bz = fmax(bz, ra[2 * kWT + c]);
+                }
+                if (last_cta) {
+                    p.det_out[(long long)cgl * 4 + 0] = bS + AGG2[0 * kWT + c];
+                    p.det_out[(long long)cgl * 4 + 1] = bL + AGG2[1 * kWT + c];
+                    p.det_out[(long long)cgl * 4 + 2] = fmax(bz, AGG2[2 * kWT + c]);
+                    p.det_out[(long long)cgl * 4 + 3] = 0.0;
+                }
+                // relative row of the last nonzero before this CTA (clamped)
+                int bzr = kNoNonzero;
+                if (bz > 0.0) {
+                    const long long rel = (long long)bz - 1 - nrow0;
+                    bzr = rel < (long long)kNoNonzero ? kNoNonzero : (int)rel;
+                }
+                for (int j = 0; j < nb; ++j) {
+                    BS[j * kWT + c] += bS;
+                    BL[j * kWT + c] += bL;
+                    BZ[j * kWT + c] = max(BZ[j * kWT + c], bzr);
+                }
+            }
+        }
+        __syncthreads();
+        // pass b: running sums inside the block, ratio
+        if (dact) {
+            float fs = (float)BS[jb * kWT + col];
+            float fl = (float)BL[jb * kWT + col];
+            int lz = BZ[jb * kWT + col];
+            // warm-up: rows before global index nl - 1 give 0
+            const long long wl = (long long)(p.nl - 1) - nrow0;
+            const int warm = wl > 4096 ? 4096 : (wl < -4096 ? -4096 : (int)wl);
+            float *rp = p.ratio ? p.ratio + (long long)(row0 + rbeg) * p.ldo + cgc : nullptr;
+#pragma unroll 8
+            for (int k = 0; k < kL; ++k) {
+                const int row = rbeg + k;
+                if (row < rows) {
+                    const float cf = tile[row * kWT + col];
+                    const float es = cf_at(row - p.ns);
+                    const float el = cf_at(row - p.nl);
+                    fs += cf - es;
+                    fl += cf - el;
+                    if (cf != 0.f) lz = row;
+                    float Rv = 0.f;
+                    if (row >= warm && lz > row - p.nl) Rv = __fdividef(fs * p.ratio_scale, fl);
+                    if (rp) rp[(long long)k * p.ldo] = Rv;
+                }
+            }
+        }
+    }
+    // no CTA may exit while a peer can still read its shared memory
+    if (NS > 0 || DET) cluster_sync_release_acquire();
+}
+
+template <int NS, bool DET>
+cudaError_t configure_t() {
+    return cudaFuncSetAttribute(chain_fwd_kernel<NS, DET>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)chain_smem_bytes());
+}
+
+template <int NS, bool DET>
+cudaError_t launch_t(const ChainParams &p, int n_tiles, cudaStream_t stream) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)n_tiles, (unsigned)p.R, 1);
+    cfg.blockDim = dim3(kThreads, 1, 1);
+    cfg.dynamicSmemBytes = chain_smem_bytes();
+    cfg.stream = stream;
+    cudaLaunchAttribute attr[2];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 1;
+    attr[0].val.clusterDim.y = (unsigned)p.R;
+    attr[0].val.clusterDim.z = 1;
+    attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[1].val.programmaticStreamSerializationAllowed = p.pdl ? 1 : 0;
+    cfg.attrs = attr;
+    cfg.numAttrs = 2;
+    return cudaLaunchKernelEx(&cfg, chain_fwd_kernel<NS, DET>, p);
+}
+
+}  // namespace
+
+size_t chain_smem_bytes() { return (size_t)kSmemFloats * sizeof(float); }
+
+cudaError_t configure_chain_kernels() {
+    cudaError_t e = cudaSuccess;
+#define FILARK_CFG(NS, D) if (e == cudaSuccess) e = configure_t<NS, D>();
+    FILARK_CFG(0, false) FILARK_CFG(0, true) FILARK_CFG(2, false) FILARK_CFG(2, true)
+    FILARK_CFG(4, false) FILARK_CFG(4, true) FILARK_CFG(8, false) FILARK_CFG(8, true)
+#undef FILARK_CFG
+    return e;
+}
+
+cudaError_t launch_chain(const ChainParams &p, int NS, bool det, int n_tiles, cudaStream_t stream) {
+    switch (NS) {
+    case 0: return det ? launch_t<0, true>(p, n_tiles, stream) : launch_t<0, false>(p, n_tiles, stream);
+    case 2: return det ? launch_t<2, true>(p, n_tiles, stream) : launch_t<2, false>(p, n_tiles, stream);
+    case 4: return det ? launch_t<4, true>(p, n_tiles, stream) : launch_t<4, false>(p, n_tiles, stream);
+    case 8: return det ? launch_t<8, true>(p, n_tiles, stream) : launch_t<8, false>(p, n_tiles, stream);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace filark

@@ -1,0 +1,116 @@
+// Internal declarations shared by the host planner, the C-ABI layer and the
+// CUDA kernels of the chunked DAS filter chain.  Not part of the public API.
+#pragma once
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/filark.h"
+
+namespace filark {
+
+// ---------------------------------------------------------------------------
+// Kernel geometry.
+//
+// One thread block (CTA) owns a tile of kWT channels (output channels plus a
+// halo on both sides) and kNB time blocks of kL samples.  The IIR stage runs
+// one thread per (channel, time block); the CTAs of one tile that cover
+// consecutive time ranges of a launch form one thread-block cluster (at most
+// kMaxCluster CTAs), and pass their IIR carries and detector sums through
+// distributed shared memory.
+// ---------------------------------------------------------------------------
+constexpr int kL = 32;                    // samples per time block
+constexpr int kNB = 8;                    // time blocks per CTA
+constexpr int kWT = 64;                   // channels per CTA tile (incl. halo)
+constexpr int kThreads = kWT * kNB;       // 512 threads: one per (channel, block)
+constexpr int kTileRows = kL * kNB;       // 256 samples per CTA
+constexpr int kMaxCluster = 8;            // CTAs per cluster (time split)
+constexpr int kMaxLaunchSamples = kTileRows * kMaxCluster;  // 2048 samples per launch
+constexpr int kMaxSlots = 8;              // 2x2 state slots per channel (= sections)
+
+// FP32 tables of one chain.  They travel in the kernel parameter block, which
+// lives in the constant bank, so the fully unrolled contractions read them as
+// FFMA constant operands (no load instructions).
+struct Tables32 {
+    float h[kL];                        // impulse response h[0..L)
+    float K[kL][2 * kMaxSlots];         // K[i][r]: input i of a block -> end state r
+    float G[kL][2 * kMaxSlots];         // G[k][r]: start state r -> output k
+    float M[kMaxSlots][4];              // per slot, M^L as {m00, m01, m10, m11}
+};
+
+struct ChainParams {
+    Tables32 tab;
+    double Phi[kMaxSlots][4];           // M^(L*kNB): one full CTA, FP64
+    double ML64[kMaxSlots][4];          // M^L, FP64
+    double PhiLast[kMaxSlots][4];       // transition over the launch's last CTA, FP64
+    float Mr32[kMaxSlots][4];           // M^Lr of the ragged last block (Lr < L), FP32
+    const float *x;                     // launch input, row 0 = first sample
+    long long ldx;
+    float *ratio, *bp, *sp;             // launch outputs (row 0 = first sample)
+    long long ldo;
+    const double *iir_in;               // [C][2*NS] carried IIR state (internal basis)
+    double *iir_out;
+    const double *det_in;               // [C][4] {sta_sum, lta_sum, 1 + index of last nonzero cf (0 = none), 0}
+    double *det_out;
+    float *ring;                        // [Q][ldr] cf history
+    long long ldr;
+    int Q;                              // ring length in samples
+    int slot_n0;                        // n0 mod Q
+    long long n0;                       // global index of the launch's first sample
+    int C, T, nblk, Lr, R;
+    int hw, HP, Wout;
+    int ns, nl;
+    float ratio_scale;                  // nl / ns
+    int x_vec4, o_vec4, r_vec4;         // float4 access allowed (input, outputs, ring)
+    int all32;                          // keep carries in FP32 everywhere (comparison)
+    int pdl;                            // launched with programmatic stream serialization
+    int *status;                        // device error word (0 = ok)
+};
+
+// ---------------------------------------------------------------------------
+// Host planner.
+// ---------------------------------------------------------------------------
+struct Plan {
+    int S = 0;                // sections
+    int NS = 0;               // slots the kernel runs (S padded to 2, 4 or 8; 0 = no IIR)
+    int mode = FILARK_PREC_MODAL32;
+    double kappa = 0.0;       // condition number estimate of the modal basis
+    double probe_err = 0.0;   // FP32 emulation error on the probe signal
+    Tables32 tab{};
+    // Per slot: kind (0 = complex pair a +- ib, 1 = two real poles p, q).
+    int slot_kind[kMaxSlots] = {};
+    long double slot_a[kMaxSlots] = {}, slot_b[kMaxSlots] = {};
+    // Real modal basis: canonical state s = W m, m = Winv s (2S x 2S, row-major).
+    std::vector<long double> W, Winv;
+    // M^n per slot in FP64 (row-major 2x2), for any n >= 0.
+    void slot_power(int n, double out[kMaxSlots][4]) const;
+    // Memoised slot_power for 0 <= n <= kTileRows (the per-launch transitions).
+    const double (*power_cached(int n) const)[4];
+    mutable std::vector<double> pow_cache;     // (kTileRows + 1) x kMaxSlots x 4
+    mutable std::vector<char> pow_have;
+};
+
+// Validate and normalise the SOS (a0 != 0, finite, stable), and build the
+// plan.  Returns FILARK_OK or an error with a message in *err.
+filark_status make_plan(const double *sos, int S, int precision, Plan *plan, std::string *err);
+
+// Butterworth bandpass design (host, long double internally).
+filark_status design_butter_bandpass(int order, double f1, double f2, double fs, double *sos,
+                                     std::string *err);
+
+// ---------------------------------------------------------------------------
+// Kernel launch (chain_kernel.cu).  Enqueues one launch of <= kMaxLaunchSamples.
+// ---------------------------------------------------------------------------
+cudaError_t launch_chain(const ChainParams &p, int NS, bool detector, int n_tiles,
+                         cudaStream_t stream);
+
+size_t chain_smem_bytes();
+
+// Set the kernels' function attributes on the current device (call once per
+// device before the first launch).
+cudaError_t configure_chain_kernels();
+
+}  // namespace filark

@@ -28,55 +28,79 @@ def add_ricker_events(x: np.ndarray, fs: float, t0: np.ndarray, c0: np.ndarray,
                       f: np.ndarray, slope_s: np.ndarray, amp: np.ndarray,
                       t_offset: float = 0.0) -> None:
     """Add events in place.  Event e arrives on channel c at
-    t0[e] + slope_s[e] * (c - c0[e]) seconds; ``t_offset`` is the time of row 0
-    of ``x`` (so a long stream can be generated in pieces)."""
+    t0[e] + slope_s[e] * (c - c0[e]) seconds and lasts |t| <= 1.5 / f[e] around
+    it; ``t_offset`` is the time of row 0 of ``x``."""
     N, C = x.shape
-    ch = np.arange(C, dtype=np.float64)
+    ch = np.arange(C)
     for e in range(len(t0)):
-        arrival = t0[e] + slope_s[e] * (ch - c0[e])           # [C] seconds
-        half = 1.5 / f[e]                                      # support: |t| <= 1.5/f
-        lo = int(np.floor((arrival.min() - half - t_offset) * fs))
-        hi = int(np.ceil((arrival.max() + half - t_offset) * fs)) + 1
-        lo, hi = max(lo, 0), min(hi, N)
-        if lo >= hi:
-            continue
-        tt = (np.arange(lo, hi, dtype=np.float64) / fs + t_offset)[:, None] - arrival[None, :]
-        w = amp[e] * ricker(tt, f[e])
-        w[np.abs(tt) > half] = 0.0
-        x[lo:hi] += w.astype(np.float32)
+        half = 1.5 / f[e]
+        width = int(np.ceil(2 * half * fs)) + 2
+        arrival = t0[e] + slope_s[e] * (ch - c0[e]) - t_offset          # [C] seconds
+        start = np.floor((arrival - half) * fs).astype(np.int64)         # first row per channel
+        rows = start[None, :] + np.arange(width)[:, None]               # [width][C]
+        tt = (rows / fs - arrival[None, :]).astype(np.float32)
+        w = (amp[e] * ricker(tt, np.float32(f[e]))).astype(np.float32)
+        ok = (rows >= 0) & (rows < N) & (np.abs(tt) <= half)
+        cols = np.broadcast_to(ch[None, :], rows.shape)
+        x[rows[ok], cols[ok]] += w[ok]
 
 
-def pink_noise(rng: np.random.Generator, n_samples: int, n_channels: int,
-               block: int = 256) -> np.ndarray:
-    """Per channel: white Gaussian noise shaped by 1/sqrt(f) in the rFFT domain
-    (DC bin zeroed), scaled to unit standard deviation over the whole record."""
-    out = np.empty((n_samples, n_channels), dtype=np.float32)
-    k = np.arange(n_samples // 2 + 1, dtype=np.float64)
-    shape = np.zeros_like(k)
-    shape[1:] = 1.0 / np.sqrt(k[1:])
-    for c0 in range(0, n_channels, block):
-        c1 = min(n_channels, c0 + block)
-        w = rng.standard_normal((n_samples, c1 - c0))
+def _rfft_shaped_pink(w: np.ndarray, shape: np.ndarray) -> np.ndarray:
+    try:
+        import scipy.fft as sf
+        W = sf.rfft(w, axis=0, workers=1)
+        W *= shape[:, None].astype(W.real.dtype)
+        return sf.irfft(W, n=w.shape[0], axis=0, workers=1).astype(np.float32)
+    except ImportError:
         W = np.fft.rfft(w, axis=0)
         W *= shape[:, None]
-        p = np.fft.irfft(W, n=n_samples, axis=0)
+        return np.fft.irfft(W, n=w.shape[0], axis=0).astype(np.float32)
+
+
+def _noise_block(seed: int, b: int, n_samples: int, c0: int, c1: int, pink: bool,
+                 shape: np.ndarray | None, out: np.ndarray) -> None:
+    rng = np.random.default_rng([seed, 1, b])
+    blk = rng.standard_normal((n_samples, c1 - c0), dtype=np.float32)
+    if pink:
+        p = _rfft_shaped_pink(rng.standard_normal((n_samples, c1 - c0), dtype=np.float32), shape)
         p /= p.std(axis=0, keepdims=True)
-        out[:, c0:c1] = p
-    return out
+        blk += p
+    out[:, c0:c1] = blk
+
+
+NOISE_BLOCK = 128   # channels per independently seeded noise block
 
 
 def noise_ricker_stream(n_channels: int, n_samples: int, fs: float, n_events: int,
                         amp: float, f_range: tuple[float, float],
                         slope_ms_range: tuple[float, float], seed: int,
-                        pink: bool = False, fixed_origin_channel: bool = False) -> np.ndarray:
-    """N(0,1) noise (+ optional unit-sigma pink noise) + seeded Ricker events."""
-    rng = np.random.default_rng(seed)
-    x = rng.standard_normal((n_samples, n_channels), dtype=np.float32)
+                        pink: bool = False, fixed_origin_channel: bool = False,
+                        threads: int | None = None) -> np.ndarray:
+    """N(0,1) noise (+ unit-sigma pink noise per channel: white noise shaped by
+    1/sqrt(f) in the rFFT domain, DC zeroed, scaled to sigma = 1 over the whole
+    record) + seeded Ricker events.  Channel blocks of NOISE_BLOCK channels have
+    their own seeds, so the result does not depend on the thread count."""
+    import concurrent.futures as cf
+    import os
+    x = np.empty((n_samples, n_channels), dtype=np.float32)
+    shape = None
     if pink:
-        x += pink_noise(rng, n_samples, n_channels)
+        k = np.arange(n_samples // 2 + 1, dtype=np.float64)
+        shape = np.zeros_like(k)
+        shape[1:] = 1.0 / np.sqrt(k[1:])
+    blocks = [(b, c0, min(n_channels, c0 + NOISE_BLOCK)) for b, c0 in
+              enumerate(range(0, n_channels, NOISE_BLOCK))]
+    nthr = threads or min(len(blocks), os.cpu_count() or 1, 32)
+    with cf.ThreadPoolExecutor(max_workers=max(1, nthr)) as ex:
+        list(ex.map(lambda a: _noise_block(seed, a[0], n_samples, a[1], a[2], pink, shape, x), blocks))
+    rng = np.random.default_rng([seed, 2])
     dur = n_samples / fs
-    t0 = rng.uniform(0.1 * dur, 0.9 * dur, n_events) if fixed_origin_channel else rng.uniform(0, dur, n_events)
-    c0 = np.zeros(n_events) if fixed_origin_channel else rng.uniform(0, n_channels, n_events)
+    if fixed_origin_channel:
+        t0 = rng.uniform(0.1 * dur, 0.9 * dur, n_events)
+        c0 = np.zeros(n_events)
+    else:
+        t0 = rng.uniform(0, dur, n_events)
+        c0 = rng.uniform(0, n_channels, n_events)
     f = rng.uniform(f_range[0], f_range[1], n_events)
     slope = rng.uniform(slope_ms_range[0], slope_ms_range[1], n_events) * 1e-3
     add_ricker_events(x, fs, t0, c0, f, slope, np.full(n_events, amp))
