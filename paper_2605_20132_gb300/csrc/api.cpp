@@ -156,11 +156,19 @@ filark_status push_device(filark_chain *h, const float *d_in, int64_t ld_in, int
             const int nb_last = p.nblk - (p.R - 1) * kNB;
             const double (*pl)[4] = h->plan.power_cached((nb_last - 1) * kL + p.Lr);
             const double (*pr)[4] = h->plan.power_cached(p.Lr);
-            for (int s = 0; s < kMaxSlots; ++s)
+            const double (*pp)[4] = h->plan.power_cached_cta(p.R - 1);
+            for (int s = 0; s < kMaxSlots; ++s) {
                 for (int q = 0; q < 4; ++q) {
                     p.PhiLast[s][q] = pl[s][q];
                     p.Mr32[s][q] = (float)pr[s][q];
                 }
+                // PhiTot = PhiLast * Phi^(R-1) (2x2 per slot)
+                const double *a = pl[s], *b = pp[s];
+                p.PhiTot[s][0] = a[0] * b[0] + a[1] * b[2];
+                p.PhiTot[s][1] = a[0] * b[1] + a[1] * b[3];
+                p.PhiTot[s][2] = a[2] * b[0] + a[3] * b[2];
+                p.PhiTot[s][3] = a[2] * b[1] + a[3] * b[3];
+            }
         }
         p.slot_n0 = h->Q > 0 ? (int)(h->n % h->Q) : 0;
         p.pdl = h->use_pdl;
@@ -305,6 +313,10 @@ filark_status filark_chain_create(const filark_chain_config *cfg, int cuda_devic
     if (ok && det) {
         h->Q = (long long)h->nl + std::min<int64_t>(cfg->max_chunk, kMaxLaunchSamples);
         h->ldr = (h->C + 3) / 4 * 4;
+        if ((double)h->Q * (double)h->ldr >= 2147483647.0) {
+            free_chain(h);
+            return fail(FILARK_ENOSYS, "detector history ring above 2^31 elements (lta_len x channels too large)");
+        }
         ok = alloc((void **)&h->ring, sizeof(float) * (size_t)h->Q * (size_t)h->ldr);
     }
     if (ok) {
@@ -324,6 +336,9 @@ filark_status filark_chain_create(const filark_chain_config *cfg, int cuda_devic
     b.tab = h->plan.tab;
     h->plan.slot_power(kL * kNB, b.Phi);
     h->plan.slot_power(kL, b.ML64);
+    for (int r = 0; r < kMaxCluster; ++r) h->plan.slot_power(kL * kNB * r, b.PhiPow[r]);
+    for (int s = 0; s < kMaxSlots; ++s)
+        for (int q = 0; q < 4; ++q) b.Phi32[s][q] = (float)b.Phi[s][q];
     b.ring = h->ring;
     b.ldr = h->ldr;
     b.Q = h->Q > 0 ? (int)h->Q : 1;

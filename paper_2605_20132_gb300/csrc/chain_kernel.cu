@@ -80,6 +80,123 @@ static_assert(kDetBZ + kNB * kWT <= kEFloats, "detector overlays must fit in the
 
 constexpr int kNoNonzero = INT_MIN / 2;   // "no nonzero cf" as a relative row index
 
+
+// Stores of one 4-channel group of a row: the spatial tap and, with the
+// detector, cf = y_sp^2 into the history ring.
+template <bool DET>
+__device__ __forceinline__ void store_group(const ChainParams &p, int row, int row0, int cch, int slot_r0,
+                                            bool full_group, const float (&ysp)[4], float (&cf)[4]) {
+    if (p.sp) {
+        float *dst = p.sp + (long long)(row0 + row) * p.ldo + cch;
+        if (p.o_vec4 && full_group) {
+            *reinterpret_cast<float4 *>(dst) = make_float4(ysp[0], ysp[1], ysp[2], ysp[3]);
+        } else {
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                if (cch + u < p.C) dst[u] = ysp[u];
+        }
+    }
+    if (DET) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) cf[u] = ysp[u] * ysp[u];
+        int slot = slot_r0 + row;
+        if (slot >= p.Q) slot -= p.Q;
+        float *dst = p.ring + (long long)slot * p.ldr + cch;
+        if (full_group) {
+            *reinterpret_cast<float4 *>(dst) = make_float4(cf[0], cf[1], cf[2], cf[3]);
+        } else {
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                if (cch + u < p.C) dst[u] = cf[u];
+        }
+    }
+}
+
+// With the detector on, cf replaces y_bp in the tile once every thread has
+// read its windows (rows past the end get cf = 0).  Called by all threads.
+template <bool DET>
+__device__ __forceinline__ void store_cf_in_place(float *tile, int ro, int rows, int q0, bool gact,
+                                                  const float (&cfv)[kTileRows / 32][4]) {
+    if (!DET) return;
+    __syncthreads();
+    if (gact) {
+#pragma unroll
+        for (int it = 0; it < kTileRows / 32; ++it) {
+            const int row = ro + 32 * it;
+            *reinterpret_cast<float4 *>(&tile[row * kWT + q0]) = row < rows
+                ? make_float4(cfv[it][0], cfv[it][1], cfv[it][2], cfv[it][3])
+                : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+    }
+}
+
+// Spatial mean of 4 output columns q0..q0+3 for the rows ro, ro+32, ... of the
+// tile, window half-width HW <= 4 known at compile time (halo HP = 4, or 0 when
+// HW = 0): the 12 (or 4) columns around the group come in with aligned float4
+// loads, which are free of bank conflicts.
+template <int HW, bool DET>
+__device__ __forceinline__ void spatial_rows(const ChainParams &p, float *tile, int ro, int rows, int q0,
+                                             int row0, int cch, int slot_r0, bool full_group, bool gact,
+                                             const float (&inv)[4]) {
+    constexpr int H = HW == 0 ? 0 : 4;              // halo columns loaded on each side
+    float cfv[kTileRows / 32][4];
+#pragma unroll
+    for (int it = 0; it < kTileRows / 32; ++it) {
+        const int row = ro + 32 * it;
+        cfv[it][0] = cfv[it][1] = cfv[it][2] = cfv[it][3] = 0.f;
+        if (gact && row < rows) {
+            float v[4 + 2 * H];
+            const float4 *tr = reinterpret_cast<const float4 *>(tile + row * kWT + q0 - H);
+#pragma unroll
+            for (int f = 0; f < (4 + 2 * H) / 4; ++f) {
+                const float4 t = tr[f];
+                v[4 * f + 0] = t.x;
+                v[4 * f + 1] = t.y;
+                v[4 * f + 2] = t.z;
+                v[4 * f + 3] = t.w;
+            }
+            float sacc = 0.f;
+#pragma unroll
+            for (int q = H - HW; q <= H + HW; ++q) sacc += v[q];
+            float ysp[4];
+            ysp[0] = sacc * inv[0];
+#pragma unroll
+            for (int u = 1; u < 4; ++u) {
+                sacc += v[H + u + HW] - v[H + u - 1 - HW];
+                ysp[u] = sacc * inv[u];
+            }
+            store_group<DET>(p, row, row0, cch, slot_r0, full_group, ysp, cfv[it]);
+        }
+    }
+    store_cf_in_place<DET>(tile, ro, rows, q0, gact, cfv);
+}
+
+// Same for any halo width (hw runtime, columns read one by one).
+template <bool DET>
+__device__ __forceinline__ void spatial_rows_generic(const ChainParams &p, float *tile, int ro, int rows,
+                                                  int q0, int row0, int cch, int slot_r0, bool full_group,
+                                                  bool gact, const float (&inv)[4]) {
+    float cfv[kTileRows / 32][4];
+#pragma unroll
+    for (int it = 0; it < kTileRows / 32; ++it) {
+        const int row = ro + 32 * it;
+        cfv[it][0] = cfv[it][1] = cfv[it][2] = cfv[it][3] = 0.f;
+        if (gact && row < rows) {
+            const float *tr = tile + row * kWT;
+            float sacc = 0.f;
+            for (int q = q0 - p.hw; q <= q0 + p.hw; ++q) sacc += tr[q];
+            float ysp[4];
+            ysp[0] = sacc * inv[0];
+            for (int u = 1; u < 4; ++u) {
+                sacc += tr[q0 + u + p.hw] - tr[q0 + u - 1 - p.hw];
+                ysp[u] = sacc * inv[u];
+            }
+            store_group<DET>(p, row, row0, cch, slot_r0, full_group, ysp, cfv[it]);
+        }
+    }
+    store_cf_in_place<DET>(tile, ro, rows, q0, gact, cfv);
+}
+
 template <int NS, bool DET>
 __global__ void __launch_bounds__(kThreads, 2) chain_fwd_kernel(const __grid_constant__ ChainParams p) {
     extern __shared__ __align__(16) float smem[];
@@ -221,28 +338,38 @@ __global__ void __launch_bounds__(kThreads, 2) chain_fwd_kernel(const __grid_con
         cluster_sync_release_acquire();
         if (act) {
             const int cgs = cbase + sc;
-            double d0 = 0.0, d1 = 0.0;
-            if (cgs >= 0 && cgs < p.C) {
-                d0 = p.iir_in[(long long)cgs * (2 * NS) + 2 * s];
-                d1 = p.iir_in[(long long)cgs * (2 * NS) + 2 * s + 1];
-            }
-            const double P00 = p.Phi[s][0], P01 = p.Phi[s][1], P10 = p.Phi[s][2], P11 = p.Phi[s][3];
-            for (int q = 0; q < r; ++q) {
-                const float *ragg = cluster.map_shared_rank(AGG, q);
-                const double g0 = ragg[(2 * s) * kWT + sc], g1 = ragg[(2 * s + 1) * kWT + sc];
-                double t0 = fma(P00, d0, fma(P01, d1, g0));
-                double t1 = fma(P10, d0, fma(P11, d1, g1));
-                if (p.all32) {
-                    t0 = (float)t0;
-                    t1 = (float)t1;
+            // earlier CTAs of the cluster: g = sum_q Phi^(r-1-q) agg_q (FP32 chain)
+            float g0 = 0.f, g1 = 0.f;
+            {
+                const float P00 = p.Phi32[s][0], P01 = p.Phi32[s][1], P10 = p.Phi32[s][2], P11 = p.Phi32[s][3];
+                for (int q = 0; q < r; ++q) {
+                    const float *ragg = cluster.map_shared_rank(AGG, q);
+                    const float a0 = ragg[(2 * s) * kWT + sc], a1 = ragg[(2 * s + 1) * kWT + sc];
+                    const float t0 = fmaf(P00, g0, fmaf(P01, g1, a0));
+                    const float t1 = fmaf(P10, g0, fmaf(P11, g1, a1));
+                    g0 = t0;
+                    g1 = t1;
                 }
-                d0 = t0;
-                d1 = t1;
+            }
+            // carried state of the launch (FP64), advanced to this CTA's start
+            double c0d = 0.0, c1d = 0.0;
+            if (cgs >= 0 && cgs < p.C) {
+                c0d = p.iir_in[(long long)cgs * (2 * NS) + 2 * s];
+                c1d = p.iir_in[(long long)cgs * (2 * NS) + 2 * s + 1];
+            }
+            const double *Pr = p.PhiPow[r][s];
+            double d0 = fma(Pr[0], c0d, fma(Pr[1], c1d, (double)g0));
+            double d1 = fma(Pr[2], c0d, fma(Pr[3], c1d, (double)g1));
+            if (p.all32) {
+                d0 = (float)d0;
+                d1 = (float)d1;
             }
             if (last_cta && sc >= p.HP && sc < p.HP + p.Wout && cgs < p.C) {
-                const double g0 = AGG[(2 * s) * kWT + sc], g1 = AGG[(2 * s + 1) * kWT + sc];
-                double u0 = fma(p.PhiLast[s][0], d0, fma(p.PhiLast[s][1], d1, g0));
-                double u1 = fma(p.PhiLast[s][2], d0, fma(p.PhiLast[s][3], d1, g1));
+                // launch end state: PhiTot c + PhiLast g + own aggregate (FP64)
+                const double a0 = AGG[(2 * s) * kWT + sc], a1 = AGG[(2 * s + 1) * kWT + sc];
+                const double *PT = p.PhiTot[s], *PL = p.PhiLast[s];
+                double u0 = fma(PT[0], c0d, fma(PT[1], c1d, fma(PL[0], (double)g0, fma(PL[1], (double)g1, a0))));
+                double u1 = fma(PT[2], c0d, fma(PT[3], c1d, fma(PL[2], (double)g0, fma(PL[3], (double)g1, a1))));
                 if (p.all32) {
                     u0 = (float)u0;
                     u1 = (float)u1;
@@ -303,70 +430,24 @@ __global__ void __launch_bounds__(kThreads, 2) chain_fwd_kernel(const __grid_con
         const int g = tid & 15, ro = tid >> 4;      // 4-column group, row offset
         const int ngroups = p.Wout >> 2;
         const int q0 = p.HP + 4 * g;                // first output column of the group
-        float cfv[kTileRows / 32][4];
         const bool gact = g < ngroups;
+        const int cch = c0 + 4 * g;
         // 1/|W| for the 4 channels (the window shrinks at the array ends)
         float inv[4];
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
-            const int cch = c0 + 4 * g + u;
-            const int lo = max(0, cch - p.hw), hi = min(p.C - 1, cch + p.hw);
+            const int lo = max(0, cch + u - p.hw), hi = min(p.C - 1, cch + u + p.hw);
             inv[u] = 1.0f / (float)max(1, hi - lo + 1);
         }
-#pragma unroll
-        for (int it = 0; it < kTileRows / 32; ++it) {
-            const int row = ro + 32 * it;
-            cfv[it][0] = cfv[it][1] = cfv[it][2] = cfv[it][3] = 0.f;
-            if (gact && row < rows) {
-                const float *tr = tile + row * kWT;
-                float sacc = 0.f;
-                for (int q = q0 - p.hw; q <= q0 + p.hw; ++q) sacc += tr[q];
-                float ysp[4];
-                ysp[0] = sacc * inv[0];
-#pragma unroll
-                for (int u = 1; u < 4; ++u) {
-                    sacc += tr[q0 + u + p.hw] - tr[q0 + u - 1 - p.hw];
-                    ysp[u] = sacc * inv[u];
-                }
-                const int cch = c0 + 4 * g;
-                const long long orow = row0 + row;
-                if (p.sp) {
-                    float *dst = p.sp + orow * p.ldo + cch;
-                    if (p.o_vec4 && cch + 3 < p.C) {
-                        *reinterpret_cast<float4 *>(dst) = make_float4(ysp[0], ysp[1], ysp[2], ysp[3]);
-                    } else {
-#pragma unroll
-                        for (int u = 0; u < 4; ++u)
-                            if (cch + u < p.C) dst[u] = ysp[u];
-                    }
-                }
-                if (DET) {
-#pragma unroll
-                    for (int u = 0; u < 4; ++u) cfv[it][u] = ysp[u] * ysp[u];
-                    int slot = slot_r0 + row;
-                    if (slot >= p.Q) slot -= p.Q;
-                    float *dst = p.ring + (long long)slot * p.ldr + cch;
-                    if (p.r_vec4 && cch + 3 < p.C) {
-                        *reinterpret_cast<float4 *>(dst) = make_float4(cfv[it][0], cfv[it][1], cfv[it][2], cfv[it][3]);
-                    } else {
-#pragma unroll
-                        for (int u = 0; u < 4; ++u)
-                            if (cch + u < p.C) dst[u] = cfv[it][u];
-                    }
-                }
-            }
-        }
-        if (DET) {
-            __syncthreads();   // every thread has read its windows
-            if (gact) {
-#pragma unroll
-                for (int it = 0; it < kTileRows / 32; ++it) {
-                    const int row = ro + 32 * it;
-                    if (row < rows)
-                        *reinterpret_cast<float4 *>(&tile[row * kWT + q0]) =
-                            make_float4(cfv[it][0], cfv[it][1], cfv[it][2], cfv[it][3]);
-                }
-            }
+        const bool full_group = cch + 3 < p.C;
+        // every thread takes the same branch (hw and HP are launch constants)
+        switch (p.HP == 4 ? p.hw : (p.HP == 0 ? 0 : -1)) {
+        case 0: spatial_rows<0, DET>(p, tile, ro, rows, q0, row0, cch, slot_r0, full_group, gact, inv); break;
+        case 1: spatial_rows<1, DET>(p, tile, ro, rows, q0, row0, cch, slot_r0, full_group, gact, inv); break;
+        case 2: spatial_rows<2, DET>(p, tile, ro, rows, q0, row0, cch, slot_r0, full_group, gact, inv); break;
+        case 3: spatial_rows<3, DET>(p, tile, ro, rows, q0, row0, cch, slot_r0, full_group, gact, inv); break;
+        case 4: spatial_rows<4, DET>(p, tile, ro, rows, q0, row0, cch, slot_r0, full_group, gact, inv); break;
+        default: spatial_rows_generic<DET>(p, tile, ro, rows, q0, row0, cch, slot_r0, full_group, gact, inv); break;
         }
     }
 
@@ -386,30 +467,69 @@ __global__ void __launch_bounds__(kThreads, 2) chain_fwd_kernel(const __grid_con
         const bool dact = col_owned && jb < nb;
         const long long nrow0 = p.n0 + row0;                 // global index of tile row 0
         const int rbeg = jb * kL;
-        // cf of tile row lr (< rows), from this tile or, for lr < 0, from the
-        // history ring (0 before the first sample)
-        auto cf_at = [&](int lr) -> float {
-            if (lr >= 0) return tile[lr * kWT + col];
-            if (nrow0 + lr < 0) return 0.f;
-            int slot = slot_r0 + lr;
-            if (slot < 0) slot += p.Q;
-            return __ldcg(p.ring + (long long)slot * p.ldr + cgc);
+        // The exiting values cf[n - w] of a block's 32 samples are read from
+        // this tile when they all lie in it (mode 1), else from the history
+        // ring, which phase 4 has already filled for this launch: as one
+        // contiguous run (mode 0) or sample by sample with wrap-around and the
+        // zeros before the first sample (mode 2).  Modes are warp-uniform.
+        struct Exit {
+            int mode, off, s0, lr0;
         };
-        // pass a: exact block sums of cf and of the exiting values
+        auto make_exit = [&](int w) -> Exit {
+            Exit e;
+            e.lr0 = rbeg - w;
+            if (e.lr0 >= 0) {
+                e.mode = 1;
+                e.off = e.lr0 * kWT + col;
+                e.s0 = 0;
+                return e;
+            }
+            int slot = slot_r0 + e.lr0;          // > -Q
+            if (slot < 0) slot += p.Q;
+            e.s0 = slot;
+            e.off = slot * (int)p.ldr + cgc;
+            e.mode = (slot + kL - 1 < p.Q && nrow0 + e.lr0 >= 0) ? 0 : 2;
+            return e;
+        };
+        const Exit exS = make_exit(p.ns), exL = make_exit(p.nl);
+        const int ldr = (int)p.ldr;
+        // eight exits starting at block sample kb; samples past `rows` read 0
+        auto fetch8 = [&](const Exit &e, int kb, float (&v)[8]) {
+            if (e.mode == 0) {
+#pragma unroll
+                for (int u = 0; u < 8; ++u) v[u] = __ldcg(p.ring + (e.off + (kb + u) * ldr));
+            } else if (e.mode == 1) {
+#pragma unroll
+                for (int u = 0; u < 8; ++u) v[u] = tile[e.off + (kb + u) * kWT];
+            } else {
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    int slot = e.s0 + kb + u;
+                    slot = slot >= p.Q ? slot - p.Q : slot;
+                    const float t = __ldcg(p.ring + (slot * ldr + cgc));
+                    v[u] = (nrow0 + (e.lr0 + kb + u) >= 0) ? t : 0.f;
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < 8; ++u) v[u] = (rbeg + kb + u < rows) ? v[u] : 0.f;
+        };
+        // pass a: exact block sums of cf and of the exiting values (cf is 0 in
+        // the tile past `rows`)
         if (dact) {
             float cs = 0.f, cc = 0.f, ss = 0.f, sc2 = 0.f, ls = 0.f, lc = 0.f;
             int lz = kNoNonzero;
-#pragma unroll 8
-            for (int k = 0; k < kL; ++k) {
-                const int row = rbeg + k;
-                if (row < rows) {
-                    const float cf = tile[row * kWT + col];
-                    const float es = cf_at(row - p.ns);
-                    const float el = cf_at(row - p.nl);
+#pragma unroll 1
+            for (int kb = 0; kb < kL; kb += 8) {
+                float vs[8], vl[8];
+                fetch8(exS, kb, vs);
+                fetch8(exL, kb, vl);
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    const float cf = tile[(rbeg + kb + u) * kWT + col];
                     acc_nonneg(cs, cc, cf);
-                    acc_nonneg(ss, sc2, es);
-                    acc_nonneg(ls, lc, el);
-                    if (cf != 0.f) lz = row;
+                    acc_nonneg(ss, sc2, vs[u]);
+                    acc_nonneg(ls, lc, vl[u]);
+                    lz = cf != 0.f ? rbeg + kb + u : lz;
                 }
             }
             const double tot = (double)cs + (double)cc;
@@ -483,19 +603,22 @@ __global__ void __launch_bounds__(kThreads, 2) chain_fwd_kernel(const __grid_con
             const long long wl = (long long)(p.nl - 1) - nrow0;
             const int warm = wl > 4096 ? 4096 : (wl < -4096 ? -4096 : (int)wl);
             float *rp = p.ratio ? p.ratio + (long long)(row0 + rbeg) * p.ldo + cgc : nullptr;
-#pragma unroll 8
-            for (int k = 0; k < kL; ++k) {
-                const int row = rbeg + k;
-                if (row < rows) {
+            const float scale = p.ratio_scale;
+#pragma unroll 1
+            for (int kb = 0; kb < kL; kb += 8) {
+                float vs[8], vl[8];
+                fetch8(exS, kb, vs);
+                fetch8(exL, kb, vl);
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    const int row = rbeg + kb + u;
                     const float cf = tile[row * kWT + col];
-                    const float es = cf_at(row - p.ns);
-                    const float el = cf_at(row - p.nl);
-                    fs += cf - es;
-                    fl += cf - el;
-                    if (cf != 0.f) lz = row;
-                    float Rv = 0.f;
-                    if (row >= warm && lz > row - p.nl) Rv = __fdividef(fs * p.ratio_scale, fl);
-                    if (rp) rp[(long long)k * p.ldo] = Rv;
+                    fs += cf - vs[u];
+                    fl += cf - vl[u];
+                    lz = cf != 0.f ? row : lz;
+                    const bool valid = (row >= warm) & (lz > row - p.nl);
+                    const float Rv = valid ? __fdividef(fs * scale, fl) : 0.f;
+                    if (rp && row < rows) rp[(long long)(kb + u) * p.ldo] = Rv;
                 }
             }
         }

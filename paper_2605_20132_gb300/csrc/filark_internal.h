@@ -46,6 +46,9 @@ struct ChainParams {
     double Phi[kMaxSlots][4];           // M^(L*kNB): one full CTA, FP64
     double ML64[kMaxSlots][4];          // M^L, FP64
     double PhiLast[kMaxSlots][4];       // transition over the launch's last CTA, FP64
+    double PhiTot[kMaxSlots][4];        // PhiLast * Phi^(R-1): launch start -> launch end
+    double PhiPow[kMaxCluster][kMaxSlots][4];  // Phi^r = M^(L*kNB*r), FP64
+    float Phi32[kMaxSlots][4];          // Phi in FP32
     float Mr32[kMaxSlots][4];           // M^Lr of the ragged last block (Lr < L), FP32
     const float *x;                     // launch input, row 0 = first sample
     long long ldx;
@@ -91,6 +94,9 @@ struct Plan {
     const double (*power_cached(int n) const)[4];
     mutable std::vector<double> pow_cache;     // (kTileRows + 1) x kMaxSlots x 4
     mutable std::vector<char> pow_have;
+    // Phi^r = M^(L*kNB*r) for 0 <= r < kMaxCluster.
+    const double (*power_cached_cta(int r) const)[4];
+    mutable std::vector<double> cta_cache;
 };
 
 // Validate and normalise the SOS (a0 != 0, finite, stable), and build the

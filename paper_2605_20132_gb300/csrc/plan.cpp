@@ -296,6 +296,15 @@ const double (*Plan::power_cached(int n) const)[4] {
     return slot;
 }
 
+const double (*Plan::power_cached_cta(int r) const)[4] {
+    if (cta_cache.empty()) {
+        cta_cache.assign((size_t)kMaxCluster * kMaxSlots * 4, 0.0);
+        for (int q = 0; q < kMaxCluster; ++q)
+            slot_power(kL * kNB * q, reinterpret_cast<double (*)[4]>(&cta_cache[(size_t)q * kMaxSlots * 4]));
+    }
+    return reinterpret_cast<const double (*)[4]>(&cta_cache[(size_t)r * kMaxSlots * 4]);
+}
+
 filark_status make_plan(const double *sos, int S, int precision, Plan *pl, std::string *err) {
     *pl = Plan();
     pl->S = S;
