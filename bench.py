@@ -342,13 +342,39 @@ def kernel_sha() -> str:
     return hsh.hexdigest()[:16]
 
 
+def ncu_case() -> None:
+    """Small profiling case for ncu captures: the paper-scale chain on 6,000
+    channels, 4 pushes of 1,500 samples of Gaussian noise (144 MB of input,
+    larger than L2), ratio output only."""
+    import torch
+
+    from paper_2605_20132_gb300 import abi
+    from paper_2605_20132_gb300.chain import Chain, butter_bandpass
+    w = workload()
+    C, T, n_push = w["n_channels"], w["chunk"], 4
+    g = torch.Generator(device="cuda").manual_seed(0)
+    x = torch.randn((T * n_push, C), device="cuda", generator=g)
+    r = torch.empty_like(x)
+    ch = Chain(C, butter_bandpass(w["order"], *w["band"], w["fs"]), w["fs"], w["spatial_width"], w["sta"],
+               w["lta"], outputs=abi.FILARK_OUT_RATIO, max_chunk=T)
+    for i in range(n_push):
+        ch.push(x[i * T:(i + 1) * T], ratio=r[i * T:(i + 1) * T])
+    ch.sync()
+    ch.close()
+    print("ncu case done")
+
+
 def main() -> None:
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="filark", choices=["filark", "reference"])
+    ap.add_argument("--ncu-case", action="store_true", help="run the small profiling case only")
     args = ap.parse_args()
+    if args.ncu_case:
+        ncu_case()
+        return
     args.warmup = max(args.warmup, 3) if args.impl == "filark" else args.warmup
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

@@ -28,6 +28,7 @@
 // launch: phases 0-1 only read the caller's input, so a launch starts them
 // while the previous one drains, and waits for it before touching the state.
 #include <climits>
+#include <type_traits>
 
 #include <cooperative_groups.h>
 
@@ -400,15 +401,16 @@ __global__ void __launch_bounds__(kThreads, 2) chain_fwd_kernel(const __grid_con
 #pragma unroll
             for (int q = 0; q < 2 * NS; ++q) m[q] = E[(jb * 2 * NS + q) * kWT + col];
             float *tc = tile + (jb * kL) * kWT + col;
-            const bool tap = p.bp && col_owned;
-            float *bpc = tap ? p.bp + (long long)(row0 + jb * kL) * p.ldo + cgc : nullptr;
 #pragma unroll
             for (int k = 0; k < kL; ++k) {
                 float acc = tc[k * kWT];
 #pragma unroll
                 for (int q = 0; q < 2 * NS; ++q) acc = fmaf(p.tab.G[k][q], m[q], acc);
                 tc[k * kWT] = acc;
-                if (tap && jb * kL + k < rows) bpc[(long long)k * p.ldo] = acc;
+            }
+            if (p.bp && col_owned) {
+                float *bpc = p.bp + (long long)(row0 + jb * kL) * p.ldo + cgc;
+                for (int k = 0; k < kL && jb * kL + k < rows; ++k) bpc[(long long)k * p.ldo] = tc[k * kWT];
             }
         }
     } else {
@@ -493,11 +495,14 @@ __global__ void __launch_bounds__(kThreads, 2) chain_fwd_kernel(const __grid_con
         };
         const Exit exS = make_exit(p.ns), exL = make_exit(p.nl);
         const int ldr = (int)p.ldr;
-        // eight exits starting at block sample kb; samples past `rows` read 0
-        auto fetch8 = [&](const Exit &e, int kb, float (&v)[8]) {
+        const bool full_blk = rbeg + kL <= rows;      // warp-uniform
+        // eight exits starting at block sample kb (samples past `rows` read 0
+        // unless the block is known to be full)
+        auto fetch8 = [&](const Exit &e, int kb, float (&v)[8], auto full) {
             if (e.mode == 0) {
+                const float *gp = p.ring + (e.off + kb * ldr);
 #pragma unroll
-                for (int u = 0; u < 8; ++u) v[u] = __ldcg(p.ring + (e.off + (kb + u) * ldr));
+                for (int u = 0; u < 8; ++u) v[u] = __ldcg(gp + u * ldr);
             } else if (e.mode == 1) {
 #pragma unroll
                 for (int u = 0; u < 8; ++u) v[u] = tile[e.off + (kb + u) * kWT];
@@ -510,19 +515,21 @@ __global__ void __launch_bounds__(kThreads, 2) chain_fwd_kernel(const __grid_con
                     v[u] = (nrow0 + (e.lr0 + kb + u) >= 0) ? t : 0.f;
                 }
             }
+            if constexpr (!decltype(full)::value) {
 #pragma unroll
-            for (int u = 0; u < 8; ++u) v[u] = (rbeg + kb + u < rows) ? v[u] : 0.f;
+                for (int u = 0; u < 8; ++u) v[u] = (rbeg + kb + u < rows) ? v[u] : 0.f;
+            }
         };
         // pass a: exact block sums of cf and of the exiting values (cf is 0 in
         // the tile past `rows`)
-        if (dact) {
+        auto pass_a = [&](auto full) {
             float cs = 0.f, cc = 0.f, ss = 0.f, sc2 = 0.f, ls = 0.f, lc = 0.f;
             int lz = kNoNonzero;
 #pragma unroll 1
             for (int kb = 0; kb < kL; kb += 8) {
                 float vs[8], vl[8];
-                fetch8(exS, kb, vs);
-                fetch8(exL, kb, vl);
+                fetch8(exS, kb, vs, full);
+                fetch8(exL, kb, vl, full);
 #pragma unroll
                 for (int u = 0; u < 8; ++u) {
                     const float cf = tile[(rbeg + kb + u) * kWT + col];
@@ -536,6 +543,10 @@ __global__ void __launch_bounds__(kThreads, 2) chain_fwd_kernel(const __grid_con
             DS[jb * kWT + col] = tot - ((double)ss + (double)sc2);
             DL[jb * kWT + col] = tot - ((double)ls + (double)lc);
             LZ[jb * kWT + col] = lz;
+        };
+        if (dact) {
+            if (full_blk) pass_a(std::true_type{});
+            else pass_a(std::false_type{});
         }
         __syncthreads();
         // exclusive scan over this CTA's blocks, one thread per column (FP64)
@@ -604,21 +615,41 @@ __global__ void __launch_bounds__(kThreads, 2) chain_fwd_kernel(const __grid_con
             const int warm = wl > 4096 ? 4096 : (wl < -4096 ? -4096 : (int)wl);
             float *rp = p.ratio ? p.ratio + (long long)(row0 + rbeg) * p.ldo + cgc : nullptr;
             const float scale = p.ratio_scale;
+            // past the warm-up, with a nonzero cf inside every window of the
+            // block already known, no sample needs the validity test
+            const bool all_valid = full_blk && rbeg >= warm && lz > rbeg + kL - 1 - p.nl;
+            if (all_valid && rp) {
 #pragma unroll 1
-            for (int kb = 0; kb < kL; kb += 8) {
-                float vs[8], vl[8];
-                fetch8(exS, kb, vs);
-                fetch8(exL, kb, vl);
+                for (int kb = 0; kb < kL; kb += 8) {
+                    float vs[8], vl[8];
+                    fetch8(exS, kb, vs, std::true_type{});
+                    fetch8(exL, kb, vl, std::true_type{});
+                    float *rq = rp + (long long)kb * p.ldo;
 #pragma unroll
-                for (int u = 0; u < 8; ++u) {
-                    const int row = rbeg + kb + u;
-                    const float cf = tile[row * kWT + col];
-                    fs += cf - vs[u];
-                    fl += cf - vl[u];
-                    lz = cf != 0.f ? row : lz;
-                    const bool valid = (row >= warm) & (lz > row - p.nl);
-                    const float Rv = valid ? __fdividef(fs * scale, fl) : 0.f;
-                    if (rp && row < rows) rp[(long long)(kb + u) * p.ldo] = Rv;
+                    for (int u = 0; u < 8; ++u) {
+                        const float cf = tile[(rbeg + kb + u) * kWT + col];
+                        fs += cf - vs[u];
+                        fl += cf - vl[u];
+                        rq[(long long)u * p.ldo] = __fdividef(fs * scale, fl);
+                    }
+                }
+            } else {
+#pragma unroll 1
+                for (int kb = 0; kb < kL; kb += 8) {
+                    float vs[8], vl[8];
+                    fetch8(exS, kb, vs, std::false_type{});
+                    fetch8(exL, kb, vl, std::false_type{});
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) {
+                        const int row = rbeg + kb + u;
+                        const float cf = tile[row * kWT + col];
+                        fs += cf - vs[u];
+                        fl += cf - vl[u];
+                        lz = cf != 0.f ? row : lz;
+                        const bool valid = (row >= warm) & (lz > row - p.nl);
+                        const float Rv = valid ? __fdividef(fs * scale, fl) : 0.f;
+                        if (rp && row < rows) rp[(long long)(kb + u) * p.ldo] = Rv;
+                    }
                 }
             }
         }
