@@ -25,7 +25,9 @@
  *     coefficients, sections applied in array order.
  *   - Butterworth bandpass design (the filter the chain is configured with):
  *     analog prototype poles, bilinear transform with prewarped band edges,
- *     conjugate-pair sections, unit gain at the geometric band centre.
+ *     conjugate-pair sections whose double zeros face their poles (z = +1 for
+ *     the low half, z = -1 for the high half), unit gain at the geometric
+ *     band centre.
  *   - Spatial running mean (Table 1, "Spatial ... running mean"; Sec. 3.4,
  *     halo expansion across neighbouring channels): the mean over the channels
  *     c-h..c+h that exist (the window shrinks at the ends of the array).
@@ -51,6 +53,7 @@ typedef long double real;
 #define R_TAN tanl
 #define R_ATAN atanl
 #define R_POW powl
+#define R_ATAN2 atan2l
 #else
 typedef double real;
 #define ORA(name) ora_##name
@@ -61,6 +64,7 @@ typedef double real;
 #define R_TAN tan
 #define R_ATAN atan
 #define R_POW pow
+#define R_ATAN2 atan2
 #endif
 
 /* ------------------------------------------------------------------------- */
@@ -157,27 +161,50 @@ int ORA(butter_bandpass)(int N, double f1, double f2, double fs, double *sos)
             for (int q = 0; q < 3; ++q) { real t = den[j][q]; den[j][q] = den[j - 1][q]; den[j - 1][q] = t; }
         }
     }
+    /* numerators: the bandpass has N zeros at z = +1 (from s = 0) and N at
+       z = -1 (from s = infinity).  The N/2 sections whose poles have the
+       lowest frequency (smallest pole angle) take both zeros at z = +1,
+       b = (1, -2, 1); the N/2 highest take both at z = -1, b = (1, 2, 1); for
+       odd N the middle section takes one of each, b = (1, 0, -1).  Keeping the
+       zeros next to the poles they face keeps the TDF-II states of sections
+       with poles near z = 1 small (the transfer function is the same for any
+       pairing). */
+    real (*num)[3] = (real (*)[3])malloc(sizeof(real[3]) * (size_t)N);
+    real *ang = (real *)malloc(sizeof(real) * (size_t)N);
+    for (int s = 0; s < N; ++s) {
+        /* largest |angle| of the section's two poles z^2 + a1 z + a2 = 0 */
+        real disc = den[s][1] * den[s][1] - 4 * den[s][2];
+        ang[s] = disc < 0 ? R_ATAN2(R_SQRT(-disc), -den[s][1]) : (-den[s][1] < 0 ? (real)3.14159265358979323846264338327950288L : 0);
+    }
+    for (int s = 0; s < N; ++s) {
+        int rank = 0;            /* sections with a strictly smaller angle, ties by index */
+        for (int t = 0; t < N; ++t)
+            if (ang[t] < ang[s] || (ang[t] == ang[s] && t < s)) ++rank;
+        if (rank < N / 2) { num[s][0] = 1; num[s][1] = -2; num[s][2] = 1; }
+        else if ((N % 2) == 1 && rank == N / 2) { num[s][0] = 1; num[s][1] = 0; num[s][2] = -1; }
+        else { num[s][0] = 1; num[s][1] = 2; num[s][2] = 1; }
+    }
     /* gain: |H(e^{j w0})| = 1 at the digital image of the geometric centre,
-       spread equally over the sections; each numerator is g^(1/N) * (1 - z^-2)
-       (one zero at z = +1 from s = 0, one at z = -1 from s = infinity). */
+       spread equally over the sections. */
     const real w0 = 2 * R_ATAN(R_SQRT(W0sq) / two_fs);
     cplx zi = c_make(R_COS(w0), -R_SIN(w0));     /* z^-1 at w0 */
     cplx zi2 = c_mul(zi, zi);
     cplx H = c_make(1, 0);
     for (int s = 0; s < N; ++s) {
-        cplx num = c_sub(c_make(1, 0), zi2);
+        cplx nn = c_add(c_add(c_make(num[s][0], 0), c_scale(zi, num[s][1])), c_scale(zi2, num[s][2]));
         cplx dd = c_add(c_add(c_make(den[s][0], 0), c_scale(zi, den[s][1])), c_scale(zi2, den[s][2]));
-        H = c_mul(H, c_div(num, dd));
+        H = c_mul(H, c_div(nn, dd));
     }
     real g = R_POW(1 / c_abs(H), (real)1 / (real)N);
     for (int s = 0; s < N; ++s) {
-        sos[6 * s + 0] = (double)g;
-        sos[6 * s + 1] = 0.0;
-        sos[6 * s + 2] = (double)(-g);
+        sos[6 * s + 0] = (double)(g * num[s][0]);
+        sos[6 * s + 1] = (double)(g * num[s][1]);
+        sos[6 * s + 2] = (double)(g * num[s][2]);
         sos[6 * s + 3] = (double)den[s][0];
         sos[6 * s + 4] = (double)den[s][1];
         sos[6 * s + 5] = (double)den[s][2];
     }
+    free(num); free(ang);
     free(up); free(rp); free(rad); free(den);
     return 0;
 }

@@ -23,6 +23,7 @@
 // unit circle) far enough to change the filter by ~1e-3; the block tables do not
 // have that sensitivity, which is why this form is used.
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <complex>
 #include <cstring>
@@ -555,15 +556,37 @@ filark_status design_butter_bandpass(int order, double f1, double f2, double fs,
         return FILARK_EINVAL;
     }
     std::stable_sort(dens.begin(), dens.end(), [](const Den &a, const Den &b) { return a.radius < b.radius; });
+    // Zeros: N at z = +1 and N at z = -1.  The half of the sections with the
+    // lowest pole frequencies get (1 - z^-1)^2, the upper half (1 + z^-1)^2,
+    // a middle section (odd N) gets 1 - z^-2: each double zero faces the poles
+    // it sits next to, which keeps section states small for poles near z = 1.
+    std::vector<ld> freq((size_t)order);
+    for (int s = 0; s < order; ++s) {
+        const ld a1 = dens[(size_t)s].a1, a2 = dens[(size_t)s].a2;
+        const ld disc = a1 * a1 - 4 * a2;
+        freq[(size_t)s] = disc < 0 ? std::atan2(std::sqrt(-disc), -a1) : (a1 > 0 ? pi : (ld)0);
+    }
+    std::vector<int> idx((size_t)order);
+    for (int s = 0; s < order; ++s) idx[(size_t)s] = s;
+    std::stable_sort(idx.begin(), idx.end(), [&](int a, int b) { return freq[(size_t)a] < freq[(size_t)b]; });
+    std::vector<std::array<ld, 3>> num((size_t)order);
+    for (int rank = 0; rank < order; ++rank) {
+        const int s = idx[(size_t)rank];
+        if (rank < order / 2) num[(size_t)s] = {1, -2, 1};
+        else if (order % 2 == 1 && rank == order / 2) num[(size_t)s] = {1, 0, -1};
+        else num[(size_t)s] = {1, 2, 1};
+    }
     const ld wc = 2 * std::atan(std::sqrt(w0sq) / c);
     const cld zc = std::polar((ld)1, -wc);
     cld H = 1;
-    for (const Den &d : dens) H *= ((ld)1 - zc * zc) / ((ld)1 + d.a1 * zc + d.a2 * zc * zc);
+    for (int s = 0; s < order; ++s) {
+        const Den &d = dens[(size_t)s];
+        const auto &b = num[(size_t)s];
+        H *= (b[0] + b[1] * zc + b[2] * zc * zc) / ((ld)1 + d.a1 * zc + d.a2 * zc * zc);
+    }
     const ld g = std::pow(1 / std::abs(H), (ld)1 / (ld)order);
     for (int s = 0; s < order; ++s) {
-        sos[6 * s + 0] = (double)g;
-        sos[6 * s + 1] = 0.0;
-        sos[6 * s + 2] = (double)-g;
+        for (int q = 0; q < 3; ++q) sos[6 * s + q] = (double)(g * num[(size_t)s][(size_t)q]);
         sos[6 * s + 3] = 1.0;
         sos[6 * s + 4] = (double)dens[(size_t)s].a1;
         sos[6 * s + 5] = (double)dens[(size_t)s].a2;

@@ -157,11 +157,21 @@ def pin_butterworth_magnitude(ora):
         w0 = 2 * np.arctan(W0 / (2 * fs))
         worst = _worst(worst, abs(abs(sos_response(sos, [w0])[0]) - 1.0))
         worst = _worst(worst, abs(abs(sos_response(sos, [2 * np.pi * f1 / fs])[0]) - 2 ** -0.5))
-        # 2N poles, all strictly inside the unit circle; numerators are (1 - z^-2) * g
+        # 2N poles, all strictly inside the unit circle; N zeros at z = +1 and
+        # N at z = -1 (numerators g*(1,-2,1), g*(1,2,1), or one g*(1,0,-1))
+        nplus = nminus = 0
         for row in sos:
             if np.any(np.abs(np.roots(row[3:])) >= 1.0):
                 worst = _worst(worst, 1.0)
-            worst = _worst(worst, max(abs(row[1]) / abs(row[0]), abs(row[0] + row[2]) / abs(row[0])))
+            b = row[:3] / row[0]
+            for zero in np.roots(b):
+                if abs(zero - 1) < 1e-6:
+                    nplus += 1
+                elif abs(zero + 1) < 1e-6:
+                    nminus += 1
+                else:
+                    worst = _worst(worst, 1.0)
+        worst = _worst(worst, 0.0 if (nplus == N and nminus == N) else 1.0)
     return worst, 1e-9
 
 
