@@ -78,6 +78,7 @@ struct filark_chain {
     long long n = 0;
     filark_status sticky = FILARK_OK;
     float *stage[4] = {nullptr, nullptr, nullptr, nullptr};   // in, ratio, bp, sp
+    double *dense = nullptr;      // dense carry matrices (device)
     ChainParams base{};
     int64_t device_bytes = 0;
     int use_pdl = 1;
@@ -92,6 +93,7 @@ void free_chain(filark_chain *h) {
         if (h->detst[i]) cudaFree(h->detst[i]);
     }
     if (h->ring) cudaFree(h->ring);
+    if (h->dense) cudaFree(h->dense);
     if (h->status_host) cudaFreeHost(h->status_host);
     for (float *p : h->stage)
         if (p) cudaFree(p);
@@ -177,7 +179,7 @@ filark_status push_device(filark_chain *h, const float *d_in, int64_t ld_in, int
         for (float *o : {p.ratio, p.bp, p.sp})
             if (o && ((uintptr_t)o & 15u)) ov = false;
         p.o_vec4 = ov;
-        cudaError_t e = launch_chain(p, NS, h->det, h->n_tiles, stream);
+        cudaError_t e = launch_chain(p, NS, h->det, h->plan.dense, h->n_tiles, stream);
         if (e != cudaSuccess) {
             h->sticky = FILARK_ECUDA;
             return fail_cuda(e, "push: kernel launch");
@@ -319,6 +321,14 @@ filark_status filark_chain_create(const filark_chain_config *cfg, int cuda_devic
         }
         ok = alloc((void **)&h->ring, sizeof(float) * (size_t)h->Q * (size_t)h->ldr);
     }
+    if (ok && h->plan.dense) {
+        ok = alloc((void **)&h->dense, sizeof(double) * h->plan.dense_mats.size());
+        if (ok && cudaMemcpy(h->dense, h->plan.dense_mats.data(), sizeof(double) * h->plan.dense_mats.size(),
+                             cudaMemcpyHostToDevice) != cudaSuccess) {
+            cudaGetLastError();
+            ok = false;
+        }
+    }
     if (ok) {
         if (cudaHostAlloc((void **)&h->status_host, sizeof(int), cudaHostAllocMapped) != cudaSuccess ||
             cudaHostGetDevicePointer((void **)&h->status_dev, h->status_host, 0) != cudaSuccess) {
@@ -352,6 +362,7 @@ filark_status filark_chain_create(const filark_chain_config *cfg, int cuda_devic
     b.r_vec4 = 1;
     b.all32 = h->plan.mode == FILARK_PREC_ALL32;
     b.status = h->status_dev;
+    b.dense = h->dense;
 
     st = zero_state(h, nullptr);
     if (st == FILARK_OK) {

@@ -69,6 +69,11 @@ constexpr int kEFloats = kNB * 2 * kMaxSlots * kWT;          // 8192
 constexpr int kERFloats = 2 * kMaxSlots * kWT;               // 1024
 constexpr int kAggFloats = 2 * kMaxSlots * kWT;              // 1024 (also holds 3 x 64 doubles)
 constexpr int kSmemFloats = kTileFloats + kEFloats + kERFloats + kAggFloats;
+// the dense carry needs an FP64 aggregate [16][kWT] (in place of AGG) and a
+// double-buffered FP64 state [2][16][kWT] after it
+constexpr int kAggDenseFloats = kDenseDim * kWT * 2;          // 2048
+constexpr int kMVFloats = 2 * kDenseDim * kWT * 2;            // 4096
+constexpr int kSmemFloatsDense = kTileFloats + kEFloats + kERFloats + kAggDenseFloats + kMVFloats;
 
 // detector overlays on the E region (free after the IIR fix-up); offsets in floats
 constexpr int kDetDS = 0;                                    // double [kNB][kWT]
@@ -198,7 +203,36 @@ __device__ __forceinline__ void spatial_rows_generic(const ChainParams &p, float
     store_cf_in_place<DET>(tile, ro, rows, q0, gact, cfv);
 }
 
-template <int NS, bool DET>
+// One step of the dense carry for the column c and the rows r0, r0+1 this
+// thread owns: out = Mx * MV[cur] + add, written to MV[cur ^ 1].  All threads
+// of the block call it (it ends with a barrier).
+template <int NS>
+__device__ __forceinline__ void dense_step(double *MV, int &cur, const double *Mx, int c, int r0, bool act,
+                                           double add0, double add1, bool all32) {
+    constexpr int n = 2 * NS;
+    if (act) {
+        const double *v = MV + (size_t)cur * kDenseDim * kWT;
+        const double *row0 = Mx + (size_t)r0 * kDenseDim, *row1 = row0 + kDenseDim;
+        double a0 = add0, a1 = add1;
+#pragma unroll
+        for (int q = 0; q < n; ++q) {
+            const double vq = v[q * kWT + c];
+            a0 = fma(__ldg(row0 + q), vq, a0);
+            a1 = fma(__ldg(row1 + q), vq, a1);
+        }
+        if (all32) {
+            a0 = (float)a0;
+            a1 = (float)a1;
+        }
+        double *o = MV + (size_t)(cur ^ 1) * kDenseDim * kWT;
+        o[r0 * kWT + c] = a0;
+        o[(r0 + 1) * kWT + c] = a1;
+    }
+    cur ^= 1;
+    __syncthreads();
+}
+
+template <int NS, bool DET, bool DENSE>
 __global__ void __launch_bounds__(kThreads, 2) chain_fwd_kernel(const __grid_constant__ ChainParams p) {
     extern __shared__ __align__(16) float smem[];
     float *tile = smem;                       // [kTileRows][kWT]
@@ -311,6 +345,85 @@ __global__ void __launch_bounds__(kThreads, 2) chain_fwd_kernel(const __grid_con
 
     if constexpr (NS > 0) {
         // ------------------------------------------------ 2. carry scan
+        if constexpr (DENSE) {
+            // canonical basis, FP64 carry at every block; thread (c, rp) owns
+            // state rows 2rp, 2rp+1 of column c
+            double *AGGD = reinterpret_cast<double *>(AGG);                        // [16][kWT]
+            double *MV = AGGD + kDenseDim * kWT;                                   // [2][16][kWT]
+            const int c = tid % kWT, rp = tid / kWT, r0 = 2 * rp;
+            const bool act = r0 < 2 * NS;
+            const int cgs = cbase + c;
+            const bool ragged_last = last_cta && p.Lr < kL;
+            const double *AL = p.dense + (size_t)(kL - 1) * kDenseDim * kDenseDim;
+            const double *Ar = p.dense + (size_t)(p.Lr - 1) * kDenseDim * kDenseDim;
+            const double *Phi = p.dense + (size_t)(kL + 1) * kDenseDim * kDenseDim;
+            const double *PhiR = p.dense + (size_t)(kL + r) * kDenseDim * kDenseDim;
+            int cur = 0;
+            auto set_rows = [&](double v0, double v1) {
+                if (act) {
+                    MV[(size_t)cur * kDenseDim * kWT + r0 * kWT + c] = v0;
+                    MV[(size_t)cur * kDenseDim * kWT + (r0 + 1) * kWT + c] = v1;
+                }
+            };
+            // (a) aggregate of this CTA from a zero start (not needed by the last)
+            set_rows(0.0, 0.0);
+            __syncthreads();
+            if (!last_cta) {
+                for (int j = 0; j < nb; ++j) {
+                    const double e0 = act ? (double)E[(j * 2 * NS + r0) * kWT + c] : 0.0;
+                    const double e1 = act ? (double)E[(j * 2 * NS + r0 + 1) * kWT + c] : 0.0;
+                    dense_step<NS>(MV, cur, AL, c, r0, act, e0, e1, p.all32);
+                }
+                if (act) {
+                    AGGD[r0 * kWT + c] = MV[(size_t)cur * kDenseDim * kWT + r0 * kWT + c];
+                    AGGD[(r0 + 1) * kWT + c] = MV[(size_t)cur * kDenseDim * kWT + (r0 + 1) * kWT + c];
+                }
+            }
+            cluster_sync_release_acquire();
+            // (b) g = sum over earlier CTAs q of Phi^(r-1-q) agg_q
+            set_rows(0.0, 0.0);
+            __syncthreads();
+            for (int q = 0; q < r; ++q) {
+                const double *ragg = cluster.map_shared_rank(AGGD, q);
+                const double a0 = act ? ragg[r0 * kWT + c] : 0.0;
+                const double a1 = act ? ragg[(r0 + 1) * kWT + c] : 0.0;
+                dense_step<NS>(MV, cur, Phi, c, r0, act, a0, a1, p.all32);
+            }
+            double g0 = 0.0, g1 = 0.0;
+            if (act) {
+                g0 = MV[(size_t)cur * kDenseDim * kWT + r0 * kWT + c];
+                g1 = MV[(size_t)cur * kDenseDim * kWT + (r0 + 1) * kWT + c];
+            }
+            __syncthreads();
+            // (c) state at this CTA's start: Phi^r s_launch + g
+            {
+                double s0 = 0.0, s1 = 0.0;
+                if (act && cgs >= 0 && cgs < p.C) {
+                    s0 = p.iir_in[(long long)cgs * (2 * NS) + r0];
+                    s1 = p.iir_in[(long long)cgs * (2 * NS) + r0 + 1];
+                }
+                set_rows(s0, s1);
+                __syncthreads();
+                dense_step<NS>(MV, cur, PhiR, c, r0, act, g0, g1, p.all32);
+            }
+            // (d) block start states (FP32 into E) and, in the last CTA, the end state
+            for (int j = 0; j < nb; ++j) {
+                double e0 = 0.0, e1 = 0.0;
+                const bool rag = ragged_last && j == nb - 1;
+                if (act) {
+                    float *pe = &E[(j * 2 * NS + r0) * kWT + c];
+                    e0 = rag ? (double)ER[r0 * kWT + c] : (double)pe[0];
+                    e1 = rag ? (double)ER[(r0 + 1) * kWT + c] : (double)pe[kWT];
+                    pe[0] = (float)MV[(size_t)cur * kDenseDim * kWT + r0 * kWT + c];
+                    pe[kWT] = (float)MV[(size_t)cur * kDenseDim * kWT + (r0 + 1) * kWT + c];
+                }
+                if (last_cta || j < nb - 1) dense_step<NS>(MV, cur, rag ? Ar : AL, c, r0, act, e0, e1, p.all32);
+            }
+            if (last_cta && act && c >= p.HP && c < p.HP + p.Wout && cgs < p.C) {
+                p.iir_out[(long long)cgs * (2 * NS) + r0] = MV[(size_t)cur * kDenseDim * kWT + r0 * kWT + c];
+                p.iir_out[(long long)cgs * (2 * NS) + r0 + 1] = MV[(size_t)cur * kDenseDim * kWT + (r0 + 1) * kWT + c];
+            }
+        } else {
         const int sc = tid % kWT, s = tid / kWT;
         const bool act = s < NS;
         const bool ragged_last = last_cta && p.Lr < kL;
@@ -392,6 +505,7 @@ __global__ void __launch_bounds__(kThreads, 2) chain_fwd_kernel(const __grid_con
                 f0 = t0;
                 f1 = t1;
             }
+        }
         }
         __syncthreads();
 
@@ -658,18 +772,18 @@ __global__ void __launch_bounds__(kThreads, 2) chain_fwd_kernel(const __grid_con
     if (NS > 0 || DET) cluster_sync_release_acquire();
 }
 
-template <int NS, bool DET>
+template <int NS, bool DET, bool DENSE>
 cudaError_t configure_t() {
-    return cudaFuncSetAttribute(chain_fwd_kernel<NS, DET>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)chain_smem_bytes());
+    return cudaFuncSetAttribute(chain_fwd_kernel<NS, DET, DENSE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)chain_smem_bytes(DENSE));
 }
 
-template <int NS, bool DET>
+template <int NS, bool DET, bool DENSE>
 cudaError_t launch_t(const ChainParams &p, int n_tiles, cudaStream_t stream) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)n_tiles, (unsigned)p.R, 1);
     cfg.blockDim = dim3(kThreads, 1, 1);
-    cfg.dynamicSmemBytes = chain_smem_bytes();
+    cfg.dynamicSmemBytes = chain_smem_bytes(DENSE);
     cfg.stream = stream;
     cudaLaunchAttribute attr[2];
     attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -680,30 +794,38 @@ cudaError_t launch_t(const ChainParams &p, int n_tiles, cudaStream_t stream) {
     attr[1].val.programmaticStreamSerializationAllowed = p.pdl ? 1 : 0;
     cfg.attrs = attr;
     cfg.numAttrs = 2;
-    return cudaLaunchKernelEx(&cfg, chain_fwd_kernel<NS, DET>, p);
+    return cudaLaunchKernelEx(&cfg, chain_fwd_kernel<NS, DET, DENSE>, p);
 }
 
 }  // namespace
 
-size_t chain_smem_bytes() { return (size_t)kSmemFloats * sizeof(float); }
+size_t chain_smem_bytes(bool dense) {
+    return (size_t)(dense ? kSmemFloatsDense : kSmemFloats) * sizeof(float);
+}
 
 cudaError_t configure_chain_kernels() {
     cudaError_t e = cudaSuccess;
-#define FILARK_CFG(NS, D) if (e == cudaSuccess) e = configure_t<NS, D>();
-    FILARK_CFG(0, false) FILARK_CFG(0, true) FILARK_CFG(2, false) FILARK_CFG(2, true)
-    FILARK_CFG(4, false) FILARK_CFG(4, true) FILARK_CFG(8, false) FILARK_CFG(8, true)
+#define FILARK_CFG(NS, D, X) if (e == cudaSuccess) e = configure_t<NS, D, X>();
+    FILARK_CFG(0, false, false) FILARK_CFG(0, true, false)
+    FILARK_CFG(2, false, false) FILARK_CFG(2, true, false) FILARK_CFG(2, false, true) FILARK_CFG(2, true, true)
+    FILARK_CFG(4, false, false) FILARK_CFG(4, true, false) FILARK_CFG(4, false, true) FILARK_CFG(4, true, true)
+    FILARK_CFG(8, false, false) FILARK_CFG(8, true, false) FILARK_CFG(8, false, true) FILARK_CFG(8, true, true)
 #undef FILARK_CFG
     return e;
 }
 
-cudaError_t launch_chain(const ChainParams &p, int NS, bool det, int n_tiles, cudaStream_t stream) {
+cudaError_t launch_chain(const ChainParams &p, int NS, bool det, bool dense, int n_tiles, cudaStream_t stream) {
+#define FILARK_L(N) \
+    return dense ? (det ? launch_t<N, true, true>(p, n_tiles, stream) : launch_t<N, false, true>(p, n_tiles, stream)) \
+                 : (det ? launch_t<N, true, false>(p, n_tiles, stream) : launch_t<N, false, false>(p, n_tiles, stream));
     switch (NS) {
-    case 0: return det ? launch_t<0, true>(p, n_tiles, stream) : launch_t<0, false>(p, n_tiles, stream);
-    case 2: return det ? launch_t<2, true>(p, n_tiles, stream) : launch_t<2, false>(p, n_tiles, stream);
-    case 4: return det ? launch_t<4, true>(p, n_tiles, stream) : launch_t<4, false>(p, n_tiles, stream);
-    case 8: return det ? launch_t<8, true>(p, n_tiles, stream) : launch_t<8, false>(p, n_tiles, stream);
+    case 0: return det ? launch_t<0, true, false>(p, n_tiles, stream) : launch_t<0, false, false>(p, n_tiles, stream);
+    case 2: FILARK_L(2)
+    case 4: FILARK_L(4)
+    case 8: FILARK_L(8)
     default: return cudaErrorInvalidValue;
     }
+#undef FILARK_L
 }
 
 }  // namespace filark

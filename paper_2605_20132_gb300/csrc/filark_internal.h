@@ -30,6 +30,8 @@ constexpr int kTileRows = kL * kNB;       // 256 samples per CTA
 constexpr int kMaxCluster = 8;            // CTAs per cluster (time split)
 constexpr int kMaxLaunchSamples = kTileRows * kMaxCluster;  // 2048 samples per launch
 constexpr int kMaxSlots = 8;              // 2x2 state slots per channel (= sections)
+constexpr int kDenseDim = 2 * kMaxSlots;  // 16: dense state dimension
+constexpr int kDenseMats = kL + kMaxCluster;  // A^1..A^L, Phi^0..Phi^(kMaxCluster-1)
 
 // FP32 tables of one chain.  They travel in the kernel parameter block, which
 // lives in the constant bank, so the fully unrolled contractions read them as
@@ -70,6 +72,9 @@ struct ChainParams {
     int x_vec4, o_vec4, r_vec4;         // float4 access allowed (input, outputs, ring)
     int all32;                          // keep carries in FP32 everywhere (comparison)
     int pdl;                            // launched with programmatic stream serialization
+    // dense carry (FILARK_PREC_DENSE64, or ALL32 without a modal basis):
+    // [kDenseMats][16][16] FP64, entries 0..31 = A^1..A^32, 32..39 = Phi^0..Phi^7
+    const double *dense;
     int *status;                        // device error word (0 = ok)
 };
 
@@ -80,6 +85,9 @@ struct Plan {
     int S = 0;                // sections
     int NS = 0;               // slots the kernel runs (S padded to 2, 4 or 8; 0 = no IIR)
     int mode = FILARK_PREC_MODAL32;
+    bool dense = false;       // dense FP64 carry in the canonical basis
+    // dense matrices (see ChainParams::dense), host copy
+    std::vector<double> dense_mats;
     double kappa = 0.0;       // condition number estimate of the modal basis
     double probe_err = 0.0;   // FP32 emulation error on the probe signal
     Tables32 tab{};
@@ -110,10 +118,10 @@ filark_status design_butter_bandpass(int order, double f1, double f2, double fs,
 // ---------------------------------------------------------------------------
 // Kernel launch (chain_kernel.cu).  Enqueues one launch of <= kMaxLaunchSamples.
 // ---------------------------------------------------------------------------
-cudaError_t launch_chain(const ChainParams &p, int NS, bool detector, int n_tiles,
+cudaError_t launch_chain(const ChainParams &p, int NS, bool detector, bool dense, int n_tiles,
                          cudaStream_t stream);
 
-size_t chain_smem_bytes();
+size_t chain_smem_bytes(bool dense);
 
 // Set the kernels' function attributes on the current device (call once per
 // device before the first launch).

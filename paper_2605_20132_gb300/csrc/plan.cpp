@@ -250,6 +250,103 @@ double probe_modal(const Plan &pl, const std::vector<Section> &secs) {
     return den > 0 ? num / den : num;
 }
 
+// Same check for the dense carry: FP32 tables in the canonical basis, an FP64
+// carry at every block, the block start state rounded to FP32 for the fix-up.
+double probe_dense(const Plan &pl, const std::vector<Section> &secs, const std::vector<ld> &Acan) {
+    const int n = 2 * pl.S;
+    const int N = 6144;
+    std::vector<float> x((size_t)N);
+    uint64_t st = 0x2545F4914F6CDD1Dull;
+    for (int i = 0; i < N; ++i) {
+        st = st * 6364136223846793005ull + 1442695040888963407ull;
+        x[(size_t)i] = (float)((double)(st >> 11) * (1.0 / 9007199254740992.0) * 2.0 - 1.0);
+    }
+    x[0] = 8.0f;
+    std::vector<ld> z(2 * secs.size(), 0);
+    std::vector<double> yref((size_t)N), yemu((size_t)N);
+    for (int i = 0; i < N; ++i) yref[(size_t)i] = (double)cascade_step(secs, z, (ld)x[(size_t)i]);
+    // A^L in FP64
+    std::vector<double> AL((size_t)n * n);
+    {
+        std::vector<ld> P((size_t)n * n, 0), Q;
+        for (int i = 0; i < n; ++i) P[(size_t)i * n + i] = 1;
+        for (int k = 0; k < kL; ++k) {
+            Q.assign((size_t)n * n, 0);
+            for (int r = 0; r < n; ++r)
+                for (int c = 0; c < n; ++c)
+                    for (int q = 0; q < n; ++q) Q[(size_t)r * n + c] += Acan[(size_t)r * n + q] * P[(size_t)q * n + c];
+            P = Q;
+        }
+        for (size_t i = 0; i < AL.size(); ++i) AL[i] = (double)P[i];
+    }
+    const Tables32 &tb = pl.tab;
+    std::vector<double> m((size_t)n, 0.0);
+    for (int j = 0; j * kL < N; ++j) {
+        float mf[kDenseDim];
+        for (int r = 0; r < n; ++r) mf[r] = (float)m[(size_t)r];
+        float e[kDenseDim];
+        for (int r = 0; r < n; ++r) e[r] = 0.f;
+        for (int k = 0; k < kL; ++k) {
+            float acc = 0.f;
+            for (int i = 0; i <= k; ++i) acc = std::fmaf(tb.h[k - i], x[(size_t)(j * kL + i)], acc);
+            for (int r = 0; r < n; ++r) acc = std::fmaf(tb.G[k][r], mf[r], acc);
+            yemu[(size_t)(j * kL + k)] = acc;
+        }
+        for (int r = 0; r < n; ++r)
+            for (int i = 0; i < kL; ++i) e[r] = std::fmaf(tb.K[i][r], x[(size_t)(j * kL + i)], e[r]);
+        std::vector<double> nm((size_t)n, 0.0);
+        for (int r = 0; r < n; ++r) {
+            double acc = (double)e[r];
+            for (int q = 0; q < n; ++q) acc = std::fma(AL[(size_t)r * n + q], m[(size_t)q], acc);
+            nm[(size_t)r] = acc;
+        }
+        m = nm;
+    }
+    double num = 0, den = 0;
+    for (int i = 0; i < N; ++i) {
+        num = std::max(num, std::fabs(yemu[(size_t)i] - yref[(size_t)i]));
+        den = std::max(den, std::fabs(yref[(size_t)i]));
+    }
+    if (!(num == num)) return std::numeric_limits<double>::infinity();
+    return den > 0 ? num / den : num;
+}
+
+// Dense matrices for the kernel: A^1..A^L and Phi^0..Phi^(kMaxCluster-1),
+// Phi = A^(L*kNB), each padded to kDenseDim x kDenseDim.
+std::vector<double> dense_matrices(const std::vector<ld> &A, int n) {
+    const int D = kDenseDim;
+    std::vector<double> out((size_t)kDenseMats * D * D, 0.0);
+    auto mul = [&](const std::vector<ld> &X, const std::vector<ld> &Y) {
+        std::vector<ld> Z((size_t)n * n, 0);
+        for (int r = 0; r < n; ++r)
+            for (int c = 0; c < n; ++c) {
+                ld acc = 0;
+                for (int q = 0; q < n; ++q) acc += X[(size_t)r * n + q] * Y[(size_t)q * n + c];
+                Z[(size_t)r * n + c] = acc;
+            }
+        return Z;
+    };
+    auto put = [&](int slot, const std::vector<ld> &M) {
+        for (int r = 0; r < n; ++r)
+            for (int c = 0; c < n; ++c) out[((size_t)slot * D + r) * D + c] = (double)M[(size_t)r * n + c];
+    };
+    std::vector<ld> P = A;
+    for (int k = 1; k <= kL; ++k) {
+        put(k - 1, P);
+        if (k < kL) P = mul(P, A);
+    }
+    std::vector<ld> Phi = P;                       // A^L
+    for (int k = 0; k < 3; ++k) Phi = mul(Phi, Phi);  // A^(8L) = A^(L*kNB)
+    static_assert(kNB == 8, "Phi is built as (A^L)^8");
+    std::vector<ld> Q((size_t)n * n, 0);
+    for (int i = 0; i < n; ++i) Q[(size_t)i * n + i] = 1;
+    for (int r = 0; r < kMaxCluster; ++r) {
+        put(kL + r, Q);
+        Q = mul(Q, Phi);
+    }
+    return out;
+}
+
 }  // namespace
 
 void Plan::slot_power(int n, double out[kMaxSlots][4]) const {
@@ -404,15 +501,13 @@ filark_status make_plan(const double *sos, int S, int precision, Plan *pl, std::
     }
     std::vector<ld> Winv;
     if (modal_ok && !invert(W, n, Winv)) modal_ok = false;
-    if (!modal_ok) {
-        pl->kappa = std::numeric_limits<double>::infinity();
-        *err = "the IIR cascade has repeated poles (no modal basis); the dense carry is not available";
+    if (precision == FILARK_PREC_MODAL32 && !modal_ok) {
+        *err = "the IIR cascade has repeated poles (no modal basis)";
         return FILARK_ENOSYS;
     }
     // full tables in the canonical basis
     std::vector<ld> h((size_t)kL), Kf((size_t)n * kL), Gf((size_t)kL * n);
     {
-        std::vector<ld> v(B);          // A^(m-1) B
         h[0] = D;
         std::vector<std::vector<ld>> pw((size_t)kL);   // pw[m] = A^m B
         pw[0] = B;
@@ -440,80 +535,88 @@ filark_status make_plan(const double *sos, int S, int precision, Plan *pl, std::
             w = nw;
         }
     }
-    auto transform = [&](std::vector<ld> &Km, std::vector<ld> &Gm) {
-        Km.assign((size_t)n * kL, 0);
-        Gm.assign((size_t)kL * n, 0);
-        for (int r = 0; r < n; ++r)
-            for (int i = 0; i < kL; ++i) {
-                ld acc = 0;
-                for (int c = 0; c < n; ++c) acc += Winv[(size_t)r * n + c] * Kf[(size_t)c * kL + i];
-                Km[(size_t)r * kL + i] = acc;
-            }
-        for (int k = 0; k < kL; ++k)
-            for (int c = 0; c < n; ++c) {
-                ld acc = 0;
-                for (int r = 0; r < n; ++r) acc += Gf[(size_t)k * n + r] * W[(size_t)r * n + c];
-                Gm[(size_t)k * n + c] = acc;
-            }
-    };
-    std::vector<ld> Km, Gm;
-    transform(Km, Gm);
-    // balance each slot: equal largest entries in its K rows and G columns
-    for (int s = 0; s < S; ++s) {
-        ld nk = 0, ng = 0;
-        for (int rr = 2 * s; rr < 2 * s + 2; ++rr)
-            for (int i = 0; i < kL; ++i) nk = std::max(nk, std::fabs(Km[(size_t)rr * kL + i]));
-        for (int k = 0; k < kL; ++k)
-            for (int c = 2 * s; c < 2 * s + 2; ++c) ng = std::max(ng, std::fabs(Gm[(size_t)k * n + c]));
-        if (nk > 0 && ng > 0) {
-            ld sig = std::sqrt(nk / ng);
-            for (int r = 0; r < n; ++r) {
-                W[(size_t)r * n + 2 * s] *= sig;
-                W[(size_t)r * n + 2 * s + 1] *= sig;
-            }
-            for (int c = 0; c < n; ++c) {
-                Winv[(size_t)(2 * s) * n + c] /= sig;
-                Winv[(size_t)(2 * s + 1) * n + c] /= sig;
-            }
-        }
-    }
-    transform(Km, Gm);
-    pl->kappa = (double)(frob(W) * frob(Winv));
-    pl->W = W;
-    pl->Winv = Winv;
     Tables32 &tb = pl->tab;
-    std::memset(&tb, 0, sizeof(tb));
-    for (int k = 0; k < kL; ++k) tb.h[k] = (float)h[(size_t)k];
-    for (int i = 0; i < kL; ++i)
-        for (int r = 0; r < n; ++r) tb.K[i][r] = (float)Km[(size_t)r * kL + i];
-    for (int k = 0; k < kL; ++k)
-        for (int r = 0; r < n; ++r) tb.G[k][r] = (float)Gm[(size_t)k * n + r];
-    double ML[kMaxSlots][4];
-    pl->slot_power(kL, ML);
-    for (int s = 0; s < kMaxSlots; ++s)
-        for (int q = 0; q < 4; ++q) tb.M[s][q] = (float)ML[s][q];
-    pl->probe_err = probe_modal(*pl, secs);
-
-    switch (precision) {
-    case FILARK_PREC_AUTO:
-        if (pl->probe_err < 2e-6) {
-            pl->mode = FILARK_PREC_MODAL32;
-            return FILARK_OK;
+    auto fill_tables = [&](const std::vector<ld> &Km, const std::vector<ld> &Gm) {
+        std::memset(&tb, 0, sizeof(tb));
+        for (int k = 0; k < kL; ++k) tb.h[k] = (float)h[(size_t)k];
+        for (int i = 0; i < kL; ++i)
+            for (int r = 0; r < n; ++r) tb.K[i][r] = (float)Km[(size_t)r * kL + i];
+        for (int k = 0; k < kL; ++k)
+            for (int r = 0; r < n; ++r) tb.G[k][r] = (float)Gm[(size_t)k * n + r];
+    };
+    bool use_modal = false;
+    if (modal_ok) {
+        auto transform = [&](std::vector<ld> &Km, std::vector<ld> &Gm) {
+            Km.assign((size_t)n * kL, 0);
+            Gm.assign((size_t)kL * n, 0);
+            for (int r = 0; r < n; ++r)
+                for (int i = 0; i < kL; ++i) {
+                    ld acc = 0;
+                    for (int c = 0; c < n; ++c) acc += Winv[(size_t)r * n + c] * Kf[(size_t)c * kL + i];
+                    Km[(size_t)r * kL + i] = acc;
+                }
+            for (int k = 0; k < kL; ++k)
+                for (int c = 0; c < n; ++c) {
+                    ld acc = 0;
+                    for (int r = 0; r < n; ++r) acc += Gf[(size_t)k * n + r] * W[(size_t)r * n + c];
+                    Gm[(size_t)k * n + c] = acc;
+                }
+        };
+        std::vector<ld> Km, Gm;
+        transform(Km, Gm);
+        // balance each slot: equal largest entries in its K rows and G columns
+        for (int s = 0; s < S; ++s) {
+            ld nk = 0, ng = 0;
+            for (int rr = 2 * s; rr < 2 * s + 2; ++rr)
+                for (int i = 0; i < kL; ++i) nk = std::max(nk, std::fabs(Km[(size_t)rr * kL + i]));
+            for (int k = 0; k < kL; ++k)
+                for (int c = 2 * s; c < 2 * s + 2; ++c) ng = std::max(ng, std::fabs(Gm[(size_t)k * n + c]));
+            if (nk > 0 && ng > 0) {
+                ld sig = std::sqrt(nk / ng);
+                for (int r = 0; r < n; ++r) {
+                    W[(size_t)r * n + 2 * s] *= sig;
+                    W[(size_t)r * n + 2 * s + 1] *= sig;
+                }
+                for (int c = 0; c < n; ++c) {
+                    Winv[(size_t)(2 * s) * n + c] /= sig;
+                    Winv[(size_t)(2 * s + 1) * n + c] /= sig;
+                }
+            }
         }
-        *err = "FP32 modal tables are not accurate enough for this filter (probe error " +
-               std::to_string(pl->probe_err) + "); the dense FP64 carry is not available";
-        return FILARK_ENOSYS;
-    case FILARK_PREC_MODAL32:
-    case FILARK_PREC_ALL32:
-        pl->mode = precision;
+        transform(Km, Gm);
+        pl->kappa = (double)(frob(W) * frob(Winv));
+        fill_tables(Km, Gm);
+        double ML[kMaxSlots][4];
+        pl->slot_power(kL, ML);
+        for (int s = 0; s < kMaxSlots; ++s)
+            for (int q = 0; q < 4; ++q) tb.M[s][q] = (float)ML[s][q];
+        pl->probe_err = probe_modal(*pl, secs);
+        use_modal = precision == FILARK_PREC_MODAL32 ||
+                    ((precision == FILARK_PREC_AUTO || precision == FILARK_PREC_ALL32) && pl->probe_err < 2e-6);
+    } else {
+        pl->kappa = std::numeric_limits<double>::infinity();
+    }
+    if (use_modal) {
+        pl->W = W;
+        pl->Winv = Winv;
+        pl->dense = false;
+        pl->mode = precision == FILARK_PREC_ALL32 ? FILARK_PREC_ALL32 : FILARK_PREC_MODAL32;
         return FILARK_OK;
-    case FILARK_PREC_DENSE64:
-        *err = "FILARK_PREC_DENSE64 is not available in this build";
-        return FILARK_ENOSYS;
-    default:
+    }
+    if (precision != FILARK_PREC_AUTO && precision != FILARK_PREC_DENSE64 && precision != FILARK_PREC_ALL32) {
         *err = "unknown precision mode";
         return FILARK_EINVAL;
     }
+    // dense carry in the canonical basis (W = I)
+    pl->dense = true;
+    pl->mode = precision == FILARK_PREC_ALL32 ? FILARK_PREC_ALL32 : FILARK_PREC_DENSE64;
+    pl->W.assign((size_t)n * n, 0);
+    pl->Winv.assign((size_t)n * n, 0);
+    for (int i = 0; i < n; ++i) pl->W[(size_t)i * n + i] = pl->Winv[(size_t)i * n + i] = 1;
+    fill_tables(Kf, Gf);
+    pl->dense_mats = dense_matrices(A, n);
+    pl->probe_err = probe_dense(*pl, secs, A);
+    return FILARK_OK;
 }
 
 // ---------------------------------------------------------------------------

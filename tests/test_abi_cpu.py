@@ -129,10 +129,21 @@ def test_create_rejects_bad_sections(row, expect):
     assert st == expect and h is None
 
 
-def test_create_reports_repeated_poles_as_unsupported():
-    # two identical sections make the cascade matrix defective (no modal basis)
+def test_create_accepts_repeated_poles():
+    """Two identical sections make the cascade matrix defective (no modal
+    basis); the planner falls back to the dense FP64 carry instead of failing
+    (without a GPU the call then stops at the device step)."""
     sec = [1.0, 0.0, -1.0, 1.0, -1.2, 0.5]
     cfg, _keep = _cfg(sos=np.array([sec, sec]))
+    st, h = abi.filark_chain_create(cfg, 0)
+    assert st in (abi.FILARK_OK, abi.FILARK_ECUDA)
+    if h:
+        abi.filark_chain_destroy(h)
+
+
+def test_modal_request_with_repeated_poles_is_unsupported():
+    sec = [1.0, 0.0, -1.0, 1.0, -1.2, 0.5]
+    cfg, _keep = _cfg(sos=np.array([sec, sec]), precision=abi.FILARK_PREC_MODAL32)
     st, h = abi.filark_chain_create(cfg, 0)
     assert st == abi.FILARK_ENOSYS and h is None
 

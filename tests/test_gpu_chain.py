@@ -286,3 +286,60 @@ def test_paper_scale_parity_sampled(oracle_mod, paper_scale):
     lo_i, hi_i = (idx - h).clamp(min=0), (idx + h).clamp(max=C - 1)
     mean = (cs[:, hi_i + 1] - cs[:, lo_i]) / (hi_i - lo_i + 1).double()
     assert normwise(outs["sp"][rows].double().cpu().numpy(), mean.cpu().numpy()) <= TOL
+
+
+# --------------------------------------------------------------------------
+# Dense FP64 carry (canonical basis): forced on the small workload, chosen
+# automatically for a defective cascade (repeated poles) and for the
+# precision-stress bandpass 0.01-1 Hz at 1.5 kHz (poles 8e-6 from z = 1).
+# --------------------------------------------------------------------------
+
+def test_dense_mode_small_workload(oracle_mod):
+    x = synth.small_stream(64, 4000, seed=12)
+    sos = small_sos(oracle_mod)
+    got = run_gpu(x, [1000, 1, 999, 2000], sos, K=5, ns=50, nl=1000, precision=abi.FILARK_PREC_DENSE64)
+    ref = run_oracle(oracle_mod, x, sos, K=5, ns=50, nl=1000)
+    errs = compare(got, ref)
+    assert all(e <= TOL for e in errs.values()), errs
+
+
+def test_repeated_poles_use_dense_carry(oracle_mod):
+    from paper_2605_20132_gb300.chain import Chain
+    sec = [0.2, 0.0, -0.2, 1.0, -1.6, 0.8]
+    sos = np.array([sec, sec, sec])
+    ch = Chain(8, sos, 1000.0, 1, 0, 0, outputs=abi.FILARK_OUT_BANDPASS, max_chunk=3000)
+    assert ch.info()["precision"] == abi.FILARK_PREC_DENSE64
+    ch.close()
+    x = synth.small_stream(30, 3000, seed=13)
+    got = run_gpu(x, [1700, 1300], sos, K=3, ns=0, nl=0)
+    ref = run_oracle(oracle_mod, x, sos, K=3)
+    errs = compare(got, ref)
+    assert all(e <= TOL for e in errs.values()), errs
+
+
+def test_precision_stress_sampled(oracle_mod):
+    """Order-8 0.01-1 Hz bandpass at 1.5 kHz on 48 channels of the stress
+    stream (noise + 0.05 Hz sine), 120 pushes of 1 s: the planner picks the
+    dense FP64 carry and stays within 1e-5 of the FP64 oracle; carrying in
+    FP32 instead (the all-FP32 comparison mode) does not."""
+    from paper_2605_20132_gb300.chain import Chain
+    cfg = synth.PRECISION
+    sos = oracle_mod.butter_bandpass(cfg["order"], *cfg["band"], cfg["fs"])
+    chans = np.arange(0, 10_000, 10_000 // 48)[:48]
+    n_push = 120
+    x = np.concatenate([synth.precision_chunk(i, channels=chans) for i in range(n_push)])
+    ch = Chain(len(chans), sos, cfg["fs"], 1, 0, 0, outputs=abi.FILARK_OUT_BANDPASS, max_chunk=cfg["chunk"])
+    info = ch.info()
+    ch.close()
+    assert info["precision"] == abi.FILARK_PREC_DENSE64
+    chunks = [cfg["chunk"]] * n_push
+    got = run_gpu(x, chunks, sos, K=1)
+    ref = run_oracle(oracle_mod, x, sos, K=1)
+    err = normwise(got["bp"], ref["bp"])
+    got32 = run_gpu(x, chunks, sos, K=1, precision=abi.FILARK_PREC_ALL32)
+    err32 = normwise(got32["bp"], ref["bp"])
+    # per-chunk report (max over channels) of both modes
+    per_chunk = [normwise(got["bp"][i * 1500:(i + 1) * 1500], ref["bp"][i * 1500:(i + 1) * 1500]) for i in range(n_push)]
+    print(f"precision stress: dense FP64 carry {err:.2e} (worst chunk {max(per_chunk):.2e}), all-FP32 {err32:.2e}")
+    assert err <= TOL
+    assert err32 > err
