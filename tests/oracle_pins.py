@@ -386,6 +386,30 @@ def pin_adjoint_identity(ora):
     return abs(a - b) / max(abs(a), 1e-30), 1e-10
 
 
+def pin_stalta_naive_closed_forms(ora):
+    """The literal-window helper itself: constant cf gives R = 1 after the
+    warm-up; a single spike of height a at k0 gives STA = a/ns, LTA = a/nl
+    while it is inside both windows (R = nl/ns), R = 0 once it has left the
+    short window but not the long one, and 0 after both."""
+    ns, nl, N = 5, 17, 60
+    worst = 0.0
+    R = ora.stalta_naive(np.full(N, 2.25), ns, nl)
+    worst = _worst(worst, np.max(np.abs(R - np.where(np.arange(N) >= nl - 1, 1.0, 0.0))))
+    cf = np.zeros(N)
+    k0 = 20
+    cf[k0] = 3.0
+    R = ora.stalta_naive(cf, ns, nl)
+    for n in range(N):
+        if n < nl - 1 or n < k0 or n > k0 + nl - 1:
+            want = 0.0
+        elif n <= k0 + ns - 1:
+            want = nl / ns
+        else:
+            want = 0.0
+        worst = _worst(worst, abs(R[n] - want))
+    return worst, 1e-12
+
+
 ALL_PINS = [
     pin_biquad_closed_form,
     pin_bruteforce_convolution,
@@ -396,6 +420,7 @@ ALL_PINS = [
     pin_spatial_invariants,
     pin_stalta_closed_forms,
     pin_stalta_vs_literal_windows,
+    pin_stalta_naive_closed_forms,
     pin_adjoint_finite_differences,
     pin_adjoint_identity,
 ]
