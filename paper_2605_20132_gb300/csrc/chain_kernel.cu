@@ -63,6 +63,27 @@ __device__ __forceinline__ void acc_nonneg(float &s, float &c, float v) {
     s = t;
 }
 
+// Double-float (hi + lo) arithmetic for the detector's carried sums: exact
+// error-free additions (Knuth's TwoSum) keep ~48 significant bits without
+// the FP64 pipe.
+struct DF {
+    float hi, lo;
+};
+__device__ __forceinline__ DF df_add(DF a, DF b) {
+    const float s = a.hi + b.hi;
+    const float bb = s - a.hi;
+    const float err = (a.hi - (s - bb)) + (b.hi - bb);
+    const float lo = err + (a.lo + b.lo);
+    const float hi = s + lo;
+    return DF{hi, lo - (hi - s)};
+}
+__device__ __forceinline__ DF df_neg(DF a) { return DF{-a.hi, -a.lo}; }
+// a + c for a, c >= 0 held as compensated sums (s, comp): exact as DF
+__device__ __forceinline__ DF df_from_sum(float s, float comp) {
+    const float hi = s + comp;
+    return DF{hi, comp - (hi - s)};
+}
+
 // shared memory carve-up (floats)
 constexpr int kTileFloats = kTileRows * kWT;                 // 16384
 constexpr int kEFloats = kNB * 2 * kMaxSlots * kWT;          // 8192
@@ -76,10 +97,10 @@ constexpr int kMVFloats = 2 * kDenseDim * kWT * 2;            // 4096
 constexpr int kSmemFloatsDense = kTileFloats + kEFloats + kERFloats + kAggDenseFloats + kMVFloats;
 
 // detector overlays on the E region (free after the IIR fix-up); offsets in floats
-constexpr int kDetDS = 0;                                    // double [kNB][kWT]
-constexpr int kDetDL = kDetDS + kNB * kWT * 2;               // double [kNB][kWT]
-constexpr int kDetBS = kDetDL + kNB * kWT * 2;               // double [kNB][kWT]
-constexpr int kDetBL = kDetBS + kNB * kWT * 2;               // double [kNB][kWT]
+constexpr int kDetDS = 0;                                    // DF [kNB][kWT]
+constexpr int kDetDL = kDetDS + kNB * kWT * 2;               // DF [kNB][kWT]
+constexpr int kDetBS = kDetDL + kNB * kWT * 2;               // DF [kNB][kWT]
+constexpr int kDetBL = kDetBS + kNB * kWT * 2;               // DF [kNB][kWT]
 constexpr int kDetLZ = kDetBL + kNB * kWT * 2;               // int [kNB][kWT] last nonzero row
 constexpr int kDetBZ = kDetLZ + kNB * kWT;                   // int [kNB][kWT] its running max
 static_assert(kDetBZ + kNB * kWT <= kEFloats, "detector overlays must fit in the E region");
@@ -573,13 +594,12 @@ __global__ void __launch_bounds__(kThreads, 2) chain_fwd_kernel(const __grid_con
         cluster_sync_release_acquire();
 
         // ------------------------------------------------ 5. STA/LTA
-        double *DS = reinterpret_cast<double *>(E + kDetDS);
-        double *DL = reinterpret_cast<double *>(E + kDetDL);
-        double *BS = reinterpret_cast<double *>(E + kDetBS);
-        double *BL = reinterpret_cast<double *>(E + kDetBL);
+        DF *DS = reinterpret_cast<DF *>(E + kDetDS);
+        DF *DL = reinterpret_cast<DF *>(E + kDetDL);
+        DF *BS = reinterpret_cast<DF *>(E + kDetBS);
+        DF *BL = reinterpret_cast<DF *>(E + kDetBL);
         int *LZ = reinterpret_cast<int *>(E + kDetLZ);
         int *BZ = reinterpret_cast<int *>(E + kDetBZ);
-        double *AGG2 = reinterpret_cast<double *>(AGG);     // [3][kWT]
         const bool dact = col_owned && jb < nb;
         const long long nrow0 = p.n0 + row0;                 // global index of tile row 0
         const int rbeg = jb * kL;
@@ -653,9 +673,9 @@ __global__ void __launch_bounds__(kThreads, 2) chain_fwd_kernel(const __grid_con
                     lz = cf != 0.f ? rbeg + kb + u : lz;
                 }
             }
-            const double tot = (double)cs + (double)cc;
-            DS[jb * kWT + col] = tot - ((double)ss + (double)sc2);
-            DL[jb * kWT + col] = tot - ((double)ls + (double)lc);
+            const DF tot = df_from_sum(cs, cc);
+            DS[jb * kWT + col] = df_add(tot, df_neg(df_from_sum(ss, sc2)));
+            DL[jb * kWT + col] = df_add(tot, df_neg(df_from_sum(ls, lc)));
             LZ[jb * kWT + col] = lz;
         };
         if (dact) {
@@ -663,24 +683,30 @@ __global__ void __launch_bounds__(kThreads, 2) chain_fwd_kernel(const __grid_con
             else pass_a(std::false_type{});
         }
         __syncthreads();
-        // exclusive scan over this CTA's blocks, one thread per column (FP64)
+        // exclusive scan over this CTA's blocks, one thread per column
+        // (double-float); AGG2 holds the CTA totals for the later CTAs:
+        // [0..2) STA hi/lo, [2..4) LTA hi/lo, [4] 1 + last nonzero index (0 = none)
+        float *AGG2 = AGG;                                   // [5][kWT]
         if (tid < kWT) {
             const int c = tid;
             const bool own = c >= p.HP && c < p.HP + p.Wout && cbase + c < p.C;
             if (own) {
-                double bs = 0.0, bl = 0.0;
+                DF bs{0.f, 0.f}, bl{0.f, 0.f};
                 int bz = kNoNonzero;
                 for (int j = 0; j < nb; ++j) {
                     BS[j * kWT + c] = bs;
                     BL[j * kWT + c] = bl;
                     BZ[j * kWT + c] = bz;
-                    bs += DS[j * kWT + c];
-                    bl += DL[j * kWT + c];
+                    bs = df_add(bs, DS[j * kWT + c]);
+                    bl = df_add(bl, DL[j * kWT + c]);
                     bz = max(bz, LZ[j * kWT + c]);
                 }
-                AGG2[0 * kWT + c] = bs;
-                AGG2[1 * kWT + c] = bl;
-                AGG2[2 * kWT + c] = bz == kNoNonzero ? 0.0 : (double)(nrow0 + bz + 1);
+                AGG2[0 * kWT + c] = bs.hi;
+                AGG2[1 * kWT + c] = bs.lo;
+                AGG2[2 * kWT + c] = bl.hi;
+                AGG2[3 * kWT + c] = bl.lo;
+                // the last nonzero as an index relative to the launch start
+                AGG2[4 * kWT + c] = __int_as_float(bz == kNoNonzero ? kNoNonzero : row0 + bz);
             }
         }
         cluster_sync_release_acquire();
@@ -690,30 +716,38 @@ __global__ void __launch_bounds__(kThreads, 2) chain_fwd_kernel(const __grid_con
             const bool own = c >= p.HP && c < p.HP + p.Wout && cgl < p.C;
             if (own) {
                 // state at the start of this CTA: carried state + earlier CTAs
-                double bS = p.det_in[(long long)cgl * 4 + 0];
-                double bL = p.det_in[(long long)cgl * 4 + 1];
-                double bz = p.det_in[(long long)cgl * 4 + 2];    // 1 + index of last nonzero, 0 = none
+                const double sIn = p.det_in[(long long)cgl * 4 + 0];
+                const double lIn = p.det_in[(long long)cgl * 4 + 1];
+                const double zIn = p.det_in[(long long)cgl * 4 + 2];   // 1 + index of last nonzero, 0 = none
+                DF bS{(float)sIn, 0.f}, bL{(float)lIn, 0.f};
+                bS.lo = (float)(sIn - (double)bS.hi);
+                bL.lo = (float)(lIn - (double)bL.hi);
+                // last nonzero relative to the launch start (clamped)
+                int zl = kNoNonzero;
+                if (zIn > 0.0) {
+                    const long long rel = (long long)zIn - 1 - p.n0;
+                    zl = rel < (long long)kNoNonzero ? kNoNonzero : (int)rel;
+                }
                 for (int q = 0; q < r; ++q) {
-                    const double *ra = cluster.map_shared_rank(AGG2, q);
-                    bS += ra[0 * kWT + c];
-                    bL += ra[1 * kWT + c];
-                    bz = fmax(bz, ra[2 * kWT + c]);
+                    const float *ra = cluster.map_shared_rank(AGG2, q);
+                    bS = df_add(bS, DF{ra[0 * kWT + c], ra[1 * kWT + c]});
+                    bL = df_add(bL, DF{ra[2 * kWT + c], ra[3 * kWT + c]});
+                    zl = max(zl, __float_as_int(ra[4 * kWT + c]));
                 }
                 if (last_cta) {
-                    p.det_out[(long long)cgl * 4 + 0] = bS + AGG2[0 * kWT + c];
-                    p.det_out[(long long)cgl * 4 + 1] = bL + AGG2[1 * kWT + c];
-                    p.det_out[(long long)cgl * 4 + 2] = fmax(bz, AGG2[2 * kWT + c]);
+                    const DF eS = df_add(bS, DF{AGG2[0 * kWT + c], AGG2[1 * kWT + c]});
+                    const DF eL = df_add(bL, DF{AGG2[2 * kWT + c], AGG2[3 * kWT + c]});
+                    const int ez = max(zl, __float_as_int(AGG2[4 * kWT + c]));
+                    p.det_out[(long long)cgl * 4 + 0] = (double)eS.hi + (double)eS.lo;
+                    p.det_out[(long long)cgl * 4 + 1] = (double)eL.hi + (double)eL.lo;
+                    p.det_out[(long long)cgl * 4 + 2] = ez == kNoNonzero ? 0.0 : (double)(p.n0 + ez + 1);
                     p.det_out[(long long)cgl * 4 + 3] = 0.0;
                 }
-                // relative row of the last nonzero before this CTA (clamped)
-                int bzr = kNoNonzero;
-                if (bz > 0.0) {
-                    const long long rel = (long long)bz - 1 - nrow0;
-                    bzr = rel < (long long)kNoNonzero ? kNoNonzero : (int)rel;
-                }
+                // relative to this CTA's row 0
+                const int bzr = zl == kNoNonzero ? kNoNonzero : zl - row0;
                 for (int j = 0; j < nb; ++j) {
-                    BS[j * kWT + c] += bS;
-                    BL[j * kWT + c] += bL;
+                    BS[j * kWT + c] = df_add(BS[j * kWT + c], bS);
+                    BL[j * kWT + c] = df_add(BL[j * kWT + c], bL);
                     BZ[j * kWT + c] = max(BZ[j * kWT + c], bzr);
                 }
             }
@@ -721,8 +755,8 @@ __global__ void __launch_bounds__(kThreads, 2) chain_fwd_kernel(const __grid_con
         __syncthreads();
         // pass b: running sums inside the block, ratio
         if (dact) {
-            float fs = (float)BS[jb * kWT + col];
-            float fl = (float)BL[jb * kWT + col];
+            float fs = BS[jb * kWT + col].hi + BS[jb * kWT + col].lo;
+            float fl = BL[jb * kWT + col].hi + BL[jb * kWT + col].lo;
             int lz = BZ[jb * kWT + col];
             // warm-up: rows before global index nl - 1 give 0
             const long long wl = (long long)(p.nl - 1) - nrow0;
