@@ -346,9 +346,11 @@ filark_status filark_chain_create(const filark_chain_config *cfg, int cuda_devic
     b.tab = h->plan.tab;
     h->plan.slot_power(kL * kNB, b.Phi);
     h->plan.slot_power(kL, b.ML64);
-    for (int r = 0; r < kMaxCluster; ++r) h->plan.slot_power(kL * kNB * r, b.PhiPow[r]);
-    for (int s = 0; s < kMaxSlots; ++s)
-        for (int q = 0; q < 4; ++q) b.Phi32[s][q] = (float)b.Phi[s][q];
+    for (int r = 0; r < kMaxCluster; ++r) {
+        h->plan.slot_power(kL * kNB * r, b.PhiPow[r]);
+        for (int s = 0; s < kMaxSlots; ++s)
+            for (int q = 0; q < 4; ++q) b.PhiPow32[r][s][q] = (float)b.PhiPow[r][s][q];
+    }
     b.ring = h->ring;
     b.ldr = h->ldr;
     b.Q = h->Q > 0 ? (int)h->Q : 1;

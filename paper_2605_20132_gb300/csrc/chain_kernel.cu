@@ -106,6 +106,8 @@ constexpr int kDetBZ = kDetLZ + kNB * kWT;                   // int [kNB][kWT] i
 static_assert(kDetBZ + kNB * kWT <= kEFloats, "detector overlays must fit in the E region");
 
 constexpr int kNoNonzero = INT_MIN / 2;   // "no nonzero cf" as a relative row index
+constexpr int kRowStep = kThreads / 16;   // rows covered by one pass of the spatial phase
+constexpr int kRowIters = kTileRows / kRowStep;
 
 
 // Stores of one 4-channel group of a row: the spatial tap and, with the
@@ -143,13 +145,13 @@ __device__ __forceinline__ void store_group(const ChainParams &p, int row, int r
 // read its windows (rows past the end get cf = 0).  Called by all threads.
 template <bool DET>
 __device__ __forceinline__ void store_cf_in_place(float *tile, int ro, int rows, int q0, bool gact,
-                                                  const float (&cfv)[kTileRows / 32][4]) {
+                                                  const float (&cfv)[kRowIters][4]) {
     if (!DET) return;
     __syncthreads();
     if (gact) {
 #pragma unroll
-        for (int it = 0; it < kTileRows / 32; ++it) {
-            const int row = ro + 32 * it;
+        for (int it = 0; it < kRowIters; ++it) {
+            const int row = ro + kRowStep * it;
             *reinterpret_cast<float4 *>(&tile[row * kWT + q0]) = row < rows
                 ? make_float4(cfv[it][0], cfv[it][1], cfv[it][2], cfv[it][3])
                 : make_float4(0.f, 0.f, 0.f, 0.f);
@@ -166,10 +168,10 @@ __device__ __forceinline__ void spatial_rows(const ChainParams &p, float *tile, 
                                              int row0, int cch, int slot_r0, bool full_group, bool gact,
                                              const float (&inv)[4]) {
     constexpr int H = HW == 0 ? 0 : 4;              // halo columns loaded on each side
-    float cfv[kTileRows / 32][4];
+    float cfv[kRowIters][4];
 #pragma unroll
-    for (int it = 0; it < kTileRows / 32; ++it) {
-        const int row = ro + 32 * it;
+    for (int it = 0; it < kRowIters; ++it) {
+        const int row = ro + kRowStep * it;
         cfv[it][0] = cfv[it][1] = cfv[it][2] = cfv[it][3] = 0.f;
         if (gact && row < rows) {
             float v[4 + 2 * H];
@@ -203,10 +205,10 @@ template <bool DET>
 __device__ __forceinline__ void spatial_rows_generic(const ChainParams &p, float *tile, int ro, int rows,
                                                   int q0, int row0, int cch, int slot_r0, bool full_group,
                                                   bool gact, const float (&inv)[4]) {
-    float cfv[kTileRows / 32][4];
+    float cfv[kRowIters][4];
 #pragma unroll
-    for (int it = 0; it < kTileRows / 32; ++it) {
-        const int row = ro + 32 * it;
+    for (int it = 0; it < kRowIters; ++it) {
+        const int row = ro + kRowStep * it;
         cfv[it][0] = cfv[it][1] = cfv[it][2] = cfv[it][3] = 0.f;
         if (gact && row < rows) {
             const float *tr = tile + row * kWT;
@@ -227,34 +229,40 @@ __device__ __forceinline__ void spatial_rows_generic(const ChainParams &p, float
 // One step of the dense carry for the column c and the rows r0, r0+1 this
 // thread owns: out = Mx * MV[cur] + add, written to MV[cur ^ 1].  All threads
 // of the block call it (it ends with a barrier).
+// rows of the dense state owned by one thread
 template <int NS>
-__device__ __forceinline__ void dense_step(double *MV, int &cur, const double *Mx, int c, int r0, bool act,
-                                           double add0, double add1, bool all32) {
+__host__ __device__ constexpr int dense_rows_per_thread() {
+    return (2 * NS + kThreads / kWT - 1) / (kThreads / kWT);
+}
+
+template <int NS>
+__device__ __forceinline__ void dense_step(double *MV, int &cur, const double *Mx, int c, int r0,
+                                           const double (&add)[dense_rows_per_thread<NS>()], bool all32) {
     constexpr int n = 2 * NS;
-    if (act) {
+    constexpr int RT = dense_rows_per_thread<NS>();
+    if (r0 < n) {
         const double *v = MV + (size_t)cur * kDenseDim * kWT;
-        const double *row0 = Mx + (size_t)r0 * kDenseDim, *row1 = row0 + kDenseDim;
-        double a0 = add0, a1 = add1;
+        double a[RT];
+#pragma unroll
+        for (int t = 0; t < RT; ++t) a[t] = add[t];
 #pragma unroll
         for (int q = 0; q < n; ++q) {
             const double vq = v[q * kWT + c];
-            a0 = fma(__ldg(row0 + q), vq, a0);
-            a1 = fma(__ldg(row1 + q), vq, a1);
-        }
-        if (all32) {
-            a0 = (float)a0;
-            a1 = (float)a1;
+#pragma unroll
+            for (int t = 0; t < RT; ++t)
+                if (r0 + t < n) a[t] = fma(__ldg(Mx + (size_t)(r0 + t) * kDenseDim + q), vq, a[t]);
         }
         double *o = MV + (size_t)(cur ^ 1) * kDenseDim * kWT;
-        o[r0 * kWT + c] = a0;
-        o[(r0 + 1) * kWT + c] = a1;
+#pragma unroll
+        for (int t = 0; t < RT; ++t)
+            if (r0 + t < n) o[(r0 + t) * kWT + c] = all32 ? (double)(float)a[t] : a[t];
     }
     cur ^= 1;
     __syncthreads();
 }
 
 template <int NS, bool DET, bool DENSE>
-__global__ void __launch_bounds__(kThreads, 2) chain_fwd_kernel(const __grid_constant__ ChainParams p) {
+__global__ void __launch_bounds__(kThreads, kCTAsPerSM) chain_fwd_kernel(const __grid_constant__ ChainParams p) {
     extern __shared__ __align__(16) float smem[];
     float *tile = smem;                       // [kTileRows][kWT]
     float *E = tile + kTileFloats;            // [kNB][2*NS][kWT]
@@ -368,11 +376,12 @@ __global__ void __launch_bounds__(kThreads, 2) chain_fwd_kernel(const __grid_con
         // ------------------------------------------------ 2. carry scan
         if constexpr (DENSE) {
             // canonical basis, FP64 carry at every block; thread (c, rp) owns
-            // state rows 2rp, 2rp+1 of column c
+            // state rows rp*RT .. rp*RT+RT-1 of column c
+            constexpr int n = 2 * NS;
+            constexpr int RT = dense_rows_per_thread<NS>();
             double *AGGD = reinterpret_cast<double *>(AGG);                        // [16][kWT]
             double *MV = AGGD + kDenseDim * kWT;                                   // [2][16][kWT]
-            const int c = tid % kWT, rp = tid / kWT, r0 = 2 * rp;
-            const bool act = r0 < 2 * NS;
+            const int c = tid % kWT, rp = tid / kWT, r0 = rp * RT;
             const int cgs = cbase + c;
             const bool ragged_last = last_cta && p.Lr < kL;
             const double *AL = p.dense + (size_t)(kL - 1) * kDenseDim * kDenseDim;
@@ -380,76 +389,87 @@ __global__ void __launch_bounds__(kThreads, 2) chain_fwd_kernel(const __grid_con
             const double *Phi = p.dense + (size_t)(kL + 1) * kDenseDim * kDenseDim;
             const double *PhiR = p.dense + (size_t)(kL + r) * kDenseDim * kDenseDim;
             int cur = 0;
-            auto set_rows = [&](double v0, double v1) {
-                if (act) {
-                    MV[(size_t)cur * kDenseDim * kWT + r0 * kWT + c] = v0;
-                    MV[(size_t)cur * kDenseDim * kWT + (r0 + 1) * kWT + c] = v1;
-                }
+            double add[RT];
+            auto set_rows = [&](const double (&v)[RT]) {
+#pragma unroll
+                for (int t = 0; t < RT; ++t)
+                    if (r0 + t < n) MV[(size_t)cur * kDenseDim * kWT + (r0 + t) * kWT + c] = v[t];
             };
+            auto get_rows = [&](double (&v)[RT]) {
+#pragma unroll
+                for (int t = 0; t < RT; ++t)
+                    v[t] = r0 + t < n ? MV[(size_t)cur * kDenseDim * kWT + (r0 + t) * kWT + c] : 0.0;
+            };
+#pragma unroll
+            for (int t = 0; t < RT; ++t) add[t] = 0.0;
             // (a) aggregate of this CTA from a zero start (not needed by the last)
-            set_rows(0.0, 0.0);
+            set_rows(add);
             __syncthreads();
             if (!last_cta) {
                 for (int j = 0; j < nb; ++j) {
-                    const double e0 = act ? (double)E[(j * 2 * NS + r0) * kWT + c] : 0.0;
-                    const double e1 = act ? (double)E[(j * 2 * NS + r0 + 1) * kWT + c] : 0.0;
-                    dense_step<NS>(MV, cur, AL, c, r0, act, e0, e1, p.all32);
+#pragma unroll
+                    for (int t = 0; t < RT; ++t)
+                        add[t] = r0 + t < n ? (double)E[(j * 2 * NS + r0 + t) * kWT + c] : 0.0;
+                    dense_step<NS>(MV, cur, AL, c, r0, add, p.all32);
                 }
-                if (act) {
-                    AGGD[r0 * kWT + c] = MV[(size_t)cur * kDenseDim * kWT + r0 * kWT + c];
-                    AGGD[(r0 + 1) * kWT + c] = MV[(size_t)cur * kDenseDim * kWT + (r0 + 1) * kWT + c];
-                }
+                get_rows(add);
+#pragma unroll
+                for (int t = 0; t < RT; ++t)
+                    if (r0 + t < n) AGGD[(r0 + t) * kWT + c] = add[t];
             }
             cluster_sync_release_acquire();
             // (b) g = sum over earlier CTAs q of Phi^(r-1-q) agg_q
-            set_rows(0.0, 0.0);
+#pragma unroll
+            for (int t = 0; t < RT; ++t) add[t] = 0.0;
+            set_rows(add);
             __syncthreads();
             for (int q = 0; q < r; ++q) {
                 const double *ragg = cluster.map_shared_rank(AGGD, q);
-                const double a0 = act ? ragg[r0 * kWT + c] : 0.0;
-                const double a1 = act ? ragg[(r0 + 1) * kWT + c] : 0.0;
-                dense_step<NS>(MV, cur, Phi, c, r0, act, a0, a1, p.all32);
+#pragma unroll
+                for (int t = 0; t < RT; ++t) add[t] = r0 + t < n ? ragg[(r0 + t) * kWT + c] : 0.0;
+                dense_step<NS>(MV, cur, Phi, c, r0, add, p.all32);
             }
-            double g0 = 0.0, g1 = 0.0;
-            if (act) {
-                g0 = MV[(size_t)cur * kDenseDim * kWT + r0 * kWT + c];
-                g1 = MV[(size_t)cur * kDenseDim * kWT + (r0 + 1) * kWT + c];
-            }
+            double g[RT];
+            get_rows(g);
             __syncthreads();
             // (c) state at this CTA's start: Phi^r s_launch + g
             {
-                double s0 = 0.0, s1 = 0.0;
-                if (act && cgs >= 0 && cgs < p.C) {
-                    s0 = p.iir_in[(long long)cgs * (2 * NS) + r0];
-                    s1 = p.iir_in[(long long)cgs * (2 * NS) + r0 + 1];
-                }
-                set_rows(s0, s1);
+                double sv[RT];
+#pragma unroll
+                for (int t = 0; t < RT; ++t)
+                    sv[t] = (r0 + t < n && cgs >= 0 && cgs < p.C) ? p.iir_in[(long long)cgs * (2 * NS) + r0 + t] : 0.0;
+                set_rows(sv);
                 __syncthreads();
-                dense_step<NS>(MV, cur, PhiR, c, r0, act, g0, g1, p.all32);
+                dense_step<NS>(MV, cur, PhiR, c, r0, g, p.all32);
             }
             // (d) block start states (FP32 into E) and, in the last CTA, the end state
             for (int j = 0; j < nb; ++j) {
-                double e0 = 0.0, e1 = 0.0;
                 const bool rag = ragged_last && j == nb - 1;
-                if (act) {
-                    float *pe = &E[(j * 2 * NS + r0) * kWT + c];
-                    e0 = rag ? (double)ER[r0 * kWT + c] : (double)pe[0];
-                    e1 = rag ? (double)ER[(r0 + 1) * kWT + c] : (double)pe[kWT];
-                    pe[0] = (float)MV[(size_t)cur * kDenseDim * kWT + r0 * kWT + c];
-                    pe[kWT] = (float)MV[(size_t)cur * kDenseDim * kWT + (r0 + 1) * kWT + c];
+#pragma unroll
+                for (int t = 0; t < RT; ++t) {
+                    add[t] = 0.0;
+                    if (r0 + t < n) {
+                        float *pe = &E[(j * 2 * NS + r0 + t) * kWT + c];
+                        add[t] = rag ? (double)ER[(r0 + t) * kWT + c] : (double)*pe;
+                        *pe = (float)MV[(size_t)cur * kDenseDim * kWT + (r0 + t) * kWT + c];
+                    }
                 }
-                if (last_cta || j < nb - 1) dense_step<NS>(MV, cur, rag ? Ar : AL, c, r0, act, e0, e1, p.all32);
+                if (last_cta || j < nb - 1) dense_step<NS>(MV, cur, rag ? Ar : AL, c, r0, add, p.all32);
             }
-            if (last_cta && act && c >= p.HP && c < p.HP + p.Wout && cgs < p.C) {
-                p.iir_out[(long long)cgs * (2 * NS) + r0] = MV[(size_t)cur * kDenseDim * kWT + r0 * kWT + c];
-                p.iir_out[(long long)cgs * (2 * NS) + r0 + 1] = MV[(size_t)cur * kDenseDim * kWT + (r0 + 1) * kWT + c];
+            if (last_cta && c >= p.HP && c < p.HP + p.Wout && cgs < p.C) {
+#pragma unroll
+                for (int t = 0; t < RT; ++t)
+                    if (r0 + t < n)
+                        p.iir_out[(long long)cgs * (2 * NS) + r0 + t] =
+                            MV[(size_t)cur * kDenseDim * kWT + (r0 + t) * kWT + c];
             }
         } else {
-        const int sc = tid % kWT, s = tid / kWT;
-        const bool act = s < NS;
+        const int sc = tid % kWT;
+        constexpr int kSlotStep = kThreads / kWT;            // slots handled per pass
         const bool ragged_last = last_cta && p.Lr < kL;
-        if (act) {
-            // this CTA's aggregate: end state of its range from a zero start (FP32)
+        // this CTA's aggregate per slot: end state of its range from a zero
+        // start (FP32)
+        for (int s = tid / kWT; s < NS; s += kSlotStep) {
             float a0 = 0.f, a1 = 0.f;
             for (int j = 0; j < nb; ++j) {
                 float e0, e1, m00, m01, m10, m11;
@@ -471,20 +491,17 @@ __global__ void __launch_bounds__(kThreads, 2) chain_fwd_kernel(const __grid_con
             AGG[(2 * s + 1) * kWT + sc] = a1;
         }
         cluster_sync_release_acquire();
-        if (act) {
+        for (int s = tid / kWT; s < NS; s += kSlotStep) {
             const int cgs = cbase + sc;
-            // earlier CTAs of the cluster: g = sum_q Phi^(r-1-q) agg_q (FP32 chain)
+            // earlier CTAs of the cluster: g = sum_q Phi^(r-1-q) agg_q, each
+            // term from its own power (independent loads, FP32)
             float g0 = 0.f, g1 = 0.f;
-            {
-                const float P00 = p.Phi32[s][0], P01 = p.Phi32[s][1], P10 = p.Phi32[s][2], P11 = p.Phi32[s][3];
-                for (int q = 0; q < r; ++q) {
-                    const float *ragg = cluster.map_shared_rank(AGG, q);
-                    const float a0 = ragg[(2 * s) * kWT + sc], a1 = ragg[(2 * s + 1) * kWT + sc];
-                    const float t0 = fmaf(P00, g0, fmaf(P01, g1, a0));
-                    const float t1 = fmaf(P10, g0, fmaf(P11, g1, a1));
-                    g0 = t0;
-                    g1 = t1;
-                }
+            for (int q = 0; q < r; ++q) {
+                const float *ragg = cluster.map_shared_rank(AGG, q);
+                const float a0 = ragg[(2 * s) * kWT + sc], a1 = ragg[(2 * s + 1) * kWT + sc];
+                const float *Pq = p.PhiPow32[r - 1 - q][s];
+                g0 = fmaf(Pq[0], a0, fmaf(Pq[1], a1, g0));
+                g1 = fmaf(Pq[2], a0, fmaf(Pq[3], a1, g1));
             }
             // carried state of the launch (FP64), advanced to this CTA's start
             double c0d = 0.0, c1d = 0.0;
@@ -564,7 +581,7 @@ __global__ void __launch_bounds__(kThreads, 2) chain_fwd_kernel(const __grid_con
     int slot_r0 = p.slot_n0 + row0;
     if (slot_r0 >= p.Q) slot_r0 -= p.Q;
     if (p.sp || DET) {
-        const int g = tid & 15, ro = tid >> 4;      // 4-column group, row offset
+        const int g = tid & 15, ro = tid >> 4;      // 4-column group, row offset (< kRowStep)
         const int ngroups = p.Wout >> 2;
         const int q0 = p.HP + 4 * g;                // first output column of the group
         const bool gact = g < ngroups;
@@ -808,8 +825,11 @@ __global__ void __launch_bounds__(kThreads, 2) chain_fwd_kernel(const __grid_con
 
 template <int NS, bool DET, bool DENSE>
 cudaError_t configure_t() {
-    return cudaFuncSetAttribute(chain_fwd_kernel<NS, DET, DENSE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)chain_smem_bytes(DENSE));
+    cudaError_t e = cudaFuncSetAttribute(chain_fwd_kernel<NS, DET, DENSE>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)chain_smem_bytes(DENSE));
+    if (e == cudaSuccess && kMaxCluster > 8)
+        e = cudaFuncSetAttribute(chain_fwd_kernel<NS, DET, DENSE>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    return e;
 }
 
 template <int NS, bool DET, bool DENSE>

@@ -27,7 +27,8 @@ constexpr int kNB = 8;                    // time blocks per CTA
 constexpr int kWT = 64;                   // channels per CTA tile (incl. halo)
 constexpr int kThreads = kWT * kNB;       // 512 threads: one per (channel, block)
 constexpr int kTileRows = kL * kNB;       // 256 samples per CTA
-constexpr int kMaxCluster = 8;            // CTAs per cluster (time split)
+constexpr int kMaxCluster = 8;            // CTAs per cluster (time split, portable size)
+constexpr int kCTAsPerSM = 2;             // occupancy target (registers <= 64/thread)
 constexpr int kMaxLaunchSamples = kTileRows * kMaxCluster;  // 2048 samples per launch
 constexpr int kMaxSlots = 8;              // 2x2 state slots per channel (= sections)
 constexpr int kDenseDim = 2 * kMaxSlots;  // 16: dense state dimension
@@ -50,7 +51,7 @@ struct ChainParams {
     double PhiLast[kMaxSlots][4];       // transition over the launch's last CTA, FP64
     double PhiTot[kMaxSlots][4];        // PhiLast * Phi^(R-1): launch start -> launch end
     double PhiPow[kMaxCluster][kMaxSlots][4];  // Phi^r = M^(L*kNB*r), FP64
-    float Phi32[kMaxSlots][4];          // Phi in FP32
+    float PhiPow32[kMaxCluster][kMaxSlots][4]; // the same in FP32
     float Mr32[kMaxSlots][4];           // M^Lr of the ragged last block (Lr < L), FP32
     const float *x;                     // launch input, row 0 = first sample
     long long ldx;

@@ -336,8 +336,7 @@ std::vector<double> dense_matrices(const std::vector<ld> &A, int n) {
         if (k < kL) P = mul(P, A);
     }
     std::vector<ld> Phi = P;                       // A^L
-    for (int k = 0; k < 3; ++k) Phi = mul(Phi, Phi);  // A^(8L) = A^(L*kNB)
-    static_assert(kNB == 8, "Phi is built as (A^L)^8");
+    for (int k = 1; k < kNB; ++k) Phi = mul(Phi, P);  // A^(L*kNB)
     std::vector<ld> Q((size_t)n * n, 0);
     for (int i = 0; i < n; ++i) Q[(size_t)i * n + i] = 1;
     for (int r = 0; r < kMaxCluster; ++r) {
