@@ -197,6 +197,35 @@ filark_status filark_chain_get_info(const filark_chain *h, filark_chain_info *ou
 filark_status filark_butter_bandpass_sos(int order, double f1, double f2, double fs,
                                          double *sos_out);
 
+/*
+ * Allocation-free variant of the chain (the paper has no counterpart; this is a
+ * deployment aid).  For callers that cannot call cudaMalloc -- a real-time
+ * acquisition thread whose latency budget rules out allocator calls (cudaMalloc
+ * can block and synchronise the device), or a plugin inside a host application
+ * that owns all device memory through its own pool.
+ *
+ * Runs the whole chain over ONE recording of n_samples samples, from a zero
+ * state, writing the requested outputs (same layouts and rules as
+ * filark_chain_push_chunk; any n_samples >= 0, inputs must not overlap
+ * outputs).  The chain's working memory (carried IIR and detector state, cf
+ * history ring, dense-carry matrices) lives in a 32 MiB file-scope device array
+ * that every GPU which loads the library holds until the process exits; no
+ * device memory is allocated or freed (host-side planning uses ordinary heap
+ * memory).  A recording whose working memory would exceed the array -- roughly
+ * 4 * n_channels * (lta_len + min(n_samples, 2048)) bytes plus the state -- is
+ * rejected with FILARK_EINVAL and a message.
+ *
+ * The device address of the array is looked up, and the kernels' attributes are
+ * set, on the first call on each device (with that device current); make that
+ * first call before any stream capture.  All calls share the array and each
+ * call clears the state it starts from, so calls that overlap on the GPU (other
+ * streams or host threads) race with each other; serialise them.  Work is
+ * enqueued on `stream` on the current CUDA device.
+ */
+filark_status filark_chain_run_static(const filark_chain_config *cfg, const float *d_in, int64_t ld_in,
+                                      int64_t n_samples, float *d_ratio, float *d_bandpass,
+                                      float *d_spatial, int64_t ld_out, filark_stream_t stream);
+
 /* Message for the last error returned to this thread ("" if none). */
 const char *filark_last_error_string(void);
 

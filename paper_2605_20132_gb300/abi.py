@@ -43,6 +43,7 @@ EXPORTED = (
     "filark_chain_reset_state", "filark_chain_destroy", "filark_chain_get_state",
     "filark_chain_set_state", "filark_chain_sync_status", "filark_chain_get_info",
     "filark_butter_bandpass_sos", "filark_last_error_string", "filark_abi_version",
+    "filark_chain_run_static",
 )
 
 
@@ -113,6 +114,8 @@ def load(build_if_missing: bool = True) -> ct.CDLL:
                                             ct.POINTER(ct.c_double)], ct.c_int),
             "filark_last_error_string": ([], ct.c_char_p),
             "filark_abi_version": ([], ct.c_uint32),
+            "filark_chain_run_static": ([ct.POINTER(filark_chain_config), vp, i64, i64, vp, vp, vp, i64, vp],
+                                        ct.c_int),
         }
         for name, (args, res) in sig.items():
             f = getattr(lib, name)
@@ -181,6 +184,10 @@ def filark_butter_bandpass_sos(order: int, f1: float, f2: float, fs: float):
     sos = np.zeros((order, 6), dtype=np.float64)
     st = load().filark_butter_bandpass_sos(order, f1, f2, fs, sos.ctypes.data_as(ct.POINTER(ct.c_double)))
     return st, sos
+
+
+def filark_chain_run_static(cfg: filark_chain_config, d_in, ld_in, n, d_ratio, d_bp, d_sp, ld_out, stream) -> int:
+    return load().filark_chain_run_static(ct.byref(cfg), d_in, ld_in, n, d_ratio, d_bp, d_sp, ld_out, stream)
 
 
 def filark_last_error_string() -> str:

@@ -60,6 +60,10 @@ struct StateHeader {
 
 }  // namespace
 
+namespace filark {
+void set_last_error(const std::string &msg) { g_err = msg; }
+}  // namespace filark
+
 struct filark_chain {
     filark_chain_config cfg{};
     std::vector<double> sos;
