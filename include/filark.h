@@ -226,6 +226,54 @@ filark_status filark_chain_run_static(const filark_chain_config *cfg, const floa
                                       int64_t n_samples, float *d_ratio, float *d_bandpass,
                                       float *d_spatial, int64_t ld_out, filark_stream_t stream);
 
+/*
+ * Differentiable bandpass: the SOS cascade of the chain's first stage (Sec. 3.4,
+ * the SOS filter; Table 1, "IIR (offline & realtime SOS)") as a forward pass
+ * with state checkpoints plus its reverse-time adjoint, so that the filter can
+ * be fitted or inverted.  Whole records from a zero state (no carried state
+ * across calls).  Section s maps u_s to y_s = u_{s+1} by
+ *     a0 y[n] + a1 y[n-1] + a2 y[n-2] = b0 u[n] + b1 u[n-1] + b2 u[n-2].
+ * Given gy = dL/dy_{S-1}, the backward solves, backwards in time,
+ *     a0 w_s[n] + a1 w_s[n+1] + a2 w_s[n+2] = g_s[n]   (w = 0 past the end)
+ * and returns
+ *     dL/db_i = sum_m u_s[m] w_s[m+i],  dL/da_i = -sum_m y_s[m] w_s[m+i]
+ *     (i = 0, 1, 2; a0 included, through the division by a0),
+ *     dL/dx = g_0,  g_{s-1}[n] = b0 w_s[n] + b1 w_s[n+1] + b2 w_s[n+2].
+ *
+ * sos: host, n_sections rows {b0,b1,b2,a0,a1,a2} (raw, not normalised), read
+ * during the call only; all finite, a0 != 0; 1 <= n_sections <=
+ * FILARK_MAX_SECTIONS.  Signals are time-major float32 as everywhere else
+ * (buf[t * ld + c], ld >= n_channels).  Arithmetic is FP64 on the device.
+ *
+ * Checkpointing: the forward stores only the cascade state (2 * n_sections
+ * doubles per channel) at every multiple of ckpt_every samples, in the
+ * caller's d_ckpt buffer of filark_iir_ckpt_bytes(...) bytes.  The backward
+ * recomputes the section signals from those checkpoints, a piece of about
+ * sqrt(2 * ckpt_every) samples at a time, in the caller's d_work buffer of
+ * filark_iir_work_bytes(...) bytes -- about (ckpt_every / P * 2S + P * S + 8S)
+ * doubles per channel per checkpoint interval, P the piece length, rather than
+ * n_samples * n_sections doubles per channel for all intermediates.
+ * Both size queries return 0 for invalid sizes.
+ *
+ * Buffers are 8-byte aligned device memory owned by the caller; d_ckpt must
+ * hold the checkpoints of a forward with the same sos, sizes and input when the
+ * backward runs.  d_y and d_gx may be NULL (skipped).  d_gsos receives
+ * n_sections * 6 doubles (device).  Inputs must not overlap outputs.  Work is
+ * enqueued on `stream`; argument errors return FILARK_EINVAL before anything is
+ * enqueued, launch errors FILARK_ECUDA.
+ */
+size_t filark_iir_ckpt_bytes(int n_sections, int n_channels, int64_t n_samples, int64_t ckpt_every);
+size_t filark_iir_work_bytes(int n_sections, int n_channels, int64_t n_samples, int64_t ckpt_every);
+filark_status filark_iir_forward_ckpt(const double *sos, int n_sections, int n_channels, const float *d_x,
+                                      int64_t ld_x, int64_t n_samples, float *d_y, int64_t ld_y,
+                                      int64_t ckpt_every, void *d_ckpt, size_t ckpt_size,
+                                      filark_stream_t stream);
+filark_status filark_iir_backward(const double *sos, int n_sections, int n_channels, const float *d_x,
+                                  int64_t ld_x, int64_t n_samples, const float *d_gy, int64_t ld_gy,
+                                  int64_t ckpt_every, const void *d_ckpt, size_t ckpt_size, void *d_work,
+                                  size_t work_size, float *d_gx, int64_t ld_gx, double *d_gsos,
+                                  filark_stream_t stream);
+
 /* Message for the last error returned to this thread ("" if none). */
 const char *filark_last_error_string(void);
 

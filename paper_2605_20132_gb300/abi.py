@@ -43,7 +43,8 @@ EXPORTED = (
     "filark_chain_reset_state", "filark_chain_destroy", "filark_chain_get_state",
     "filark_chain_set_state", "filark_chain_sync_status", "filark_chain_get_info",
     "filark_butter_bandpass_sos", "filark_last_error_string", "filark_abi_version",
-    "filark_chain_run_static",
+    "filark_chain_run_static", "filark_iir_ckpt_bytes", "filark_iir_work_bytes",
+    "filark_iir_forward_ckpt", "filark_iir_backward",
 )
 
 
@@ -116,6 +117,12 @@ def load(build_if_missing: bool = True) -> ct.CDLL:
             "filark_abi_version": ([], ct.c_uint32),
             "filark_chain_run_static": ([ct.POINTER(filark_chain_config), vp, i64, i64, vp, vp, vp, i64, vp],
                                         ct.c_int),
+            "filark_iir_ckpt_bytes": ([ct.c_int, ct.c_int, i64, i64], ct.c_size_t),
+            "filark_iir_work_bytes": ([ct.c_int, ct.c_int, i64, i64], ct.c_size_t),
+            "filark_iir_forward_ckpt": ([vp, ct.c_int, ct.c_int, vp, i64, i64, vp, i64, i64, vp, ct.c_size_t, vp],
+                                        ct.c_int),
+            "filark_iir_backward": ([vp, ct.c_int, ct.c_int, vp, i64, i64, vp, i64, i64, vp, ct.c_size_t, vp,
+                                     ct.c_size_t, vp, i64, vp, vp], ct.c_int),
         }
         for name, (args, res) in sig.items():
             f = getattr(lib, name)
@@ -188,6 +195,29 @@ def filark_butter_bandpass_sos(order: int, f1: float, f2: float, fs: float):
 
 def filark_chain_run_static(cfg: filark_chain_config, d_in, ld_in, n, d_ratio, d_bp, d_sp, ld_out, stream) -> int:
     return load().filark_chain_run_static(ct.byref(cfg), d_in, ld_in, n, d_ratio, d_bp, d_sp, ld_out, stream)
+
+
+def filark_iir_ckpt_bytes(n_sections: int, n_channels: int, n_samples: int, ckpt_every: int) -> int:
+    return int(load().filark_iir_ckpt_bytes(n_sections, n_channels, n_samples, ckpt_every))
+
+
+def filark_iir_work_bytes(n_sections: int, n_channels: int, n_samples: int, ckpt_every: int) -> int:
+    return int(load().filark_iir_work_bytes(n_sections, n_channels, n_samples, ckpt_every))
+
+
+def filark_iir_forward_ckpt(sos_host, n_sections, n_channels, d_x, ld_x, n_samples, d_y, ld_y, ckpt_every,
+                            d_ckpt, ckpt_size, stream) -> int:
+    """sos_host: a C-contiguous float64 numpy array (n_sections, 6)."""
+    return load().filark_iir_forward_ckpt(sos_host.ctypes.data, n_sections, n_channels, d_x, ld_x, n_samples, d_y,
+                                          ld_y, ckpt_every, d_ckpt, ckpt_size, stream)
+
+
+def filark_iir_backward(sos_host, n_sections, n_channels, d_x, ld_x, n_samples, d_gy, ld_gy, ckpt_every, d_ckpt,
+                        ckpt_size, d_work, work_size, d_gx, ld_gx, d_gsos, stream) -> int:
+    """sos_host: a C-contiguous float64 numpy array (n_sections, 6)."""
+    return load().filark_iir_backward(sos_host.ctypes.data, n_sections, n_channels, d_x, ld_x, n_samples, d_gy,
+                                      ld_gy, ckpt_every, d_ckpt, ckpt_size, d_work, work_size, d_gx, ld_gx, d_gsos,
+                                      stream)
 
 
 def filark_last_error_string() -> str:

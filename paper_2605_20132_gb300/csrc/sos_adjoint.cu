@@ -1,0 +1,566 @@
+// Differentiable SOS cascade: a forward pass that keeps the cascade state at
+// checkpoints, and the reverse-time adjoint that gives the gradients with
+// respect to the input and to all six coefficients of every section, so the
+// bandpass of the chain can be fitted or inverted.
+//
+// Section s maps u_s -> y_s = u_{s+1} by
+//     a0 y[n] + a1 y[n-1] + a2 y[n-2] = b0 u[n] + b1 u[n-1] + b2 u[n-2]
+// from zero state, evaluated in transposed direct form II with the
+// coefficients divided by a0 (Sec. 3.4, the SOS filter).  For a loss L with
+// g = dL/dy_{S-1}, the adjoint w_s of section s solves, backwards in time,
+//     a0 w[n] + a1 w[n+1] + a2 w[n+2] = g_s[n],   w = 0 after the last sample,
+// and
+//     dL/db_i  =  sum_m u_s[m] w_s[m+i],
+//     dL/da_i  = -sum_m y_s[m] w_s[m+i],
+//     g_{s-1}[n] = dL/du_s[n] = b0 w_s[n] + b1 w_s[n+1] + b2 w_s[n+2].
+//
+// Arithmetic is FP64 throughout.  The per-section signals of poles a few 1e-3
+// from z = 1 are not accurate in FP32: rounding the coefficients alone moves
+// the poles by ~1e-5 and the resonance gain by ~1e-3.
+//
+// Parallelism over time as well as channels.  The record is cut into segments
+// of `ckpt` samples; one thread owns one (segment, channel) pair.  Both the
+// forward state and the adjoint state are linear in their inputs, so each
+// pass runs in three steps: every thread runs its segment from a zero state
+// and keeps only the final state; one thread per channel chains the segments,
+// state_next = T * state + local (T = the transition over ckpt samples of
+// zero input, computed on the host in long double); every thread reruns its
+// segment from the true state.
+//
+// Memory: the forward keeps only the cascade state at each segment start (the
+// checkpoints).  The backward recomputes a segment's section signals piece by
+// piece: a first sweep stores the state every P ~ sqrt(2 ckpt) samples, then
+// the pieces are recomputed in reverse order into a P-sample buffer and
+// consumed by the adjoint.  The workspace holds ~(ckpt/P * 2S + P * S) doubles
+// per (segment, channel) instead of ckpt * S.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <string>
+
+#include "filark_internal.h"
+
+namespace filark {
+void set_last_error(const std::string &msg);
+}
+
+namespace {
+
+using filark::set_last_error;
+
+constexpr int kMaxS = FILARK_MAX_SECTIONS;
+constexpr int kMaxState = 2 * kMaxS;
+constexpr int kAdjThreads = 128;
+
+struct SosCoef {
+    double b[kMaxS][3];   // numerators as given
+    double a[kMaxS][3];   // denominators as given (a0 included)
+    double nb[kMaxS][3];  // b / a0
+    double na[kMaxS][2];  // a1 / a0, a2 / a0
+    double ia0[kMaxS];    // 1 / a0
+};
+
+struct Transition {
+    double T[kMaxState][kMaxState];  // row-major, first 2S x 2S used
+};
+
+struct Geometry {
+    long long N, ckpt, P;  // samples, segment length, piece length
+    long long nseg, npiece;
+    int C;
+    long long NT;  // nseg * C threads
+};
+
+// ---- forward recursion (one TDF-II step of section s) ----------------------
+
+template <typename R>
+__host__ __device__ __forceinline__ R tdf2_step(const SosCoef &k, int s, R u, R &z1, R &z2) {
+    const R y = (R)k.nb[s][0] * u + z1;
+    z1 = (R)k.nb[s][1] * u - (R)k.na[s][0] * y + z2;
+    z2 = (R)k.nb[s][2] * u - (R)k.na[s][1] * y;
+    return y;
+}
+
+// ---- adjoint recursion (one reverse-time step of section s) ----------------
+// w1 = w[n+1], w2 = w[n+2] on entry; returns g_{s-1}[n] and shifts the state.
+
+template <typename R>
+__host__ __device__ __forceinline__ R adj_step(const SosCoef &k, int s, R g, R &w1, R &w2, R &w) {
+    w = (g - (R)k.a[s][1] * w1 - (R)k.a[s][2] * w2) * (R)k.ia0[s];
+    const R gprev = (R)k.b[s][0] * w + (R)k.b[s][1] * w1 + (R)k.b[s][2] * w2;
+    w2 = w1;
+    w1 = w;
+    return gprev;
+}
+
+__device__ __forceinline__ void seg_range(const Geometry &g, long long seg, long long &t0, long long &t1) {
+    t0 = seg * g.ckpt;
+    t1 = t0 + g.ckpt < g.N ? t0 + g.ckpt : g.N;
+}
+
+// state arrays are [row][NT] with the thread index fastest (coalesced)
+__device__ __forceinline__ double &at(double *base, long long row, long long NT, long long T) {
+    return base[row * NT + T];
+}
+
+// F1: final state of each segment (except the last) from a zero start, stored
+// in the checkpoint slot of the next segment.
+template <int S>
+__global__ void __launch_bounds__(kAdjThreads) fwd_local_kernel(const __grid_constant__ SosCoef k,
+                                                                const __grid_constant__ Geometry g,
+                                                                const float *__restrict__ x, long long ldx,
+                                                                double *__restrict__ ckpt) {
+    const long long T = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (T >= g.NT) return;
+    const long long seg = T / g.C;
+    const int c = (int)(T - seg * g.C);
+    if (seg == g.nseg - 1) return;
+    long long t0, t1;
+    seg_range(g, seg, t0, t1);
+    double z[S][2];
+#pragma unroll
+    for (int s = 0; s < S; ++s) z[s][0] = z[s][1] = 0.0;
+    for (long long n = t0; n < t1; ++n) {
+        double u = (double)x[n * ldx + c];
+#pragma unroll
+        for (int s = 0; s < S; ++s) u = tdf2_step(k, s, u, z[s][0], z[s][1]);
+    }
+    const long long Tn = T + g.C;  // (seg + 1, c)
+#pragma unroll
+    for (int s = 0; s < S; ++s) {
+        at(ckpt, 2 * s, g.NT, Tn) = z[s][0];
+        at(ckpt, 2 * s + 1, g.NT, Tn) = z[s][1];
+    }
+}
+
+// F2 / B2: one thread per channel chains the segments.
+//   forward : st[0] = 0,         st[j+1] += T st[j]        (j ascending)
+//   backward: st[nseg-1] = 0,    st[j-1] += T st[j]        (j descending)
+template <int S>
+__global__ void __launch_bounds__(kAdjThreads) chain_segments_kernel(const __grid_constant__ Transition tr,
+                                                                     const __grid_constant__ Geometry g,
+                                                                     double *__restrict__ st, int backward) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= g.C) return;
+    constexpr int D = 2 * S;
+    double v[D];
+    const long long first = backward ? g.nseg - 1 : 0;
+#pragma unroll
+    for (int i = 0; i < D; ++i) {
+        v[i] = 0.0;
+        at(st, i, g.NT, first * g.C + c) = 0.0;
+    }
+    for (long long j = 1; j < g.nseg; ++j) {
+        const long long seg = backward ? g.nseg - 1 - j : j;
+        const long long T = seg * g.C + c;
+        double nv[D];
+#pragma unroll
+        for (int i = 0; i < D; ++i) {
+            double acc = at(st, i, g.NT, T);
+#pragma unroll
+            for (int q = 0; q < D; ++q) acc += tr.T[i][q] * v[q];
+            nv[i] = acc;
+        }
+#pragma unroll
+        for (int i = 0; i < D; ++i) {
+            v[i] = nv[i];
+            at(st, i, g.NT, T) = nv[i];
+        }
+    }
+}
+
+// F3: rerun every segment from its checkpoint, writing y.
+template <int S>
+__global__ void __launch_bounds__(kAdjThreads) fwd_run_kernel(const __grid_constant__ SosCoef k,
+                                                              const __grid_constant__ Geometry g,
+                                                              const float *__restrict__ x, long long ldx,
+                                                              const double *__restrict__ ckpt,
+                                                              float *__restrict__ y, long long ldy) {
+    const long long T = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (T >= g.NT) return;
+    const long long seg = T / g.C;
+    const int c = (int)(T - seg * g.C);
+    long long t0, t1;
+    seg_range(g, seg, t0, t1);
+    double z[S][2];
+#pragma unroll
+    for (int s = 0; s < S; ++s) {
+        z[s][0] = ckpt[(2 * s) * g.NT + T];
+        z[s][1] = ckpt[(2 * s + 1) * g.NT + T];
+    }
+    for (long long n = t0; n < t1; ++n) {
+        double u = (double)x[n * ldx + c];
+#pragma unroll
+        for (int s = 0; s < S; ++s) u = tdf2_step(k, s, u, z[s][0], z[s][1]);
+        y[n * ldy + c] = (float)u;
+    }
+}
+
+// B1: adjoint state at the start of each segment (except the first) from a
+// zero adjoint state at its end, stored in the slot of the previous segment.
+// The adjoint state of section s is (w_s[n+1], w_s[n+2]).
+template <int S>
+__global__ void __launch_bounds__(kAdjThreads) adj_local_kernel(const __grid_constant__ SosCoef k,
+                                                                const __grid_constant__ Geometry g,
+                                                                const float *__restrict__ gy, long long ldg,
+                                                                double *__restrict__ beta) {
+    const long long T = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (T >= g.NT) return;
+    const long long seg = T / g.C;
+    const int c = (int)(T - seg * g.C);
+    if (seg == 0) return;
+    long long t0, t1;
+    seg_range(g, seg, t0, t1);
+    double w1[S], w2[S];
+#pragma unroll
+    for (int s = 0; s < S; ++s) w1[s] = w2[s] = 0.0;
+    for (long long n = t1 - 1; n >= t0; --n) {
+        double gg = (double)gy[n * ldg + c], w;
+#pragma unroll
+        for (int s = S - 1; s >= 0; --s) gg = adj_step(k, s, gg, w1[s], w2[s], w);
+    }
+    const long long Tp = T - g.C;  // (seg - 1, c)
+#pragma unroll
+    for (int s = 0; s < S; ++s) {
+        at(beta, 2 * s, g.NT, Tp) = w1[s];
+        at(beta, 2 * s + 1, g.NT, Tp) = w2[s];
+    }
+}
+
+// B3: gradients.  Sweep 1 stores the forward state every P samples; then the
+// pieces are handled last to first: recompute the piece's section outputs
+// into `sig` ([p][s][NT]), run the adjoint over it backwards from the true
+// adjoint state, accumulate the coefficient gradients, write dL/dx.
+template <int S>
+__global__ void __launch_bounds__(kAdjThreads) adj_run_kernel(const __grid_constant__ SosCoef k,
+                                                              const __grid_constant__ Geometry g,
+                                                              const float *__restrict__ x, long long ldx,
+                                                              const float *__restrict__ gy, long long ldg,
+                                                              const double *__restrict__ ckpt,
+                                                              const double *__restrict__ beta,
+                                                              double *__restrict__ sub, double *__restrict__ sig,
+                                                              float *__restrict__ gx, long long ldgx,
+                                                              double *__restrict__ gpart) {
+    const long long T = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (T >= g.NT) return;
+    const long long seg = T / g.C;
+    const int c = (int)(T - seg * g.C);
+    const long long NT = g.NT;
+    long long t0, t1;
+    seg_range(g, seg, t0, t1);
+    const long long npiece = (t1 - t0 + g.P - 1) / g.P;
+
+    // sweep 1: piece start states
+    {
+        double z[S][2];
+#pragma unroll
+        for (int s = 0; s < S; ++s) {
+            z[s][0] = ckpt[(2 * s) * NT + T];
+            z[s][1] = ckpt[(2 * s + 1) * NT + T];
+        }
+        for (long long p = 0; p < npiece; ++p) {
+#pragma unroll
+            for (int s = 0; s < S; ++s) {
+                at(sub, p * (2 * S) + 2 * s, NT, T) = z[s][0];
+                at(sub, p * (2 * S) + 2 * s + 1, NT, T) = z[s][1];
+            }
+            if (p == npiece - 1) break;
+            const long long a = t0 + p * g.P;
+            for (long long n = a; n < a + g.P; ++n) {
+                double u = (double)x[n * ldx + c];
+#pragma unroll
+                for (int s = 0; s < S; ++s) u = tdf2_step(k, s, u, z[s][0], z[s][1]);
+            }
+        }
+    }
+
+    double w1[S], w2[S], gb[S][3], ga[S][3];
+#pragma unroll
+    for (int s = 0; s < S; ++s) {
+        w1[s] = beta[(2 * s) * NT + T];
+        w2[s] = beta[(2 * s + 1) * NT + T];
+#pragma unroll
+        for (int i = 0; i < 3; ++i) gb[s][i] = ga[s][i] = 0.0;
+    }
+    for (long long p = npiece - 1; p >= 0; --p) {
+        const long long a = t0 + p * g.P;
+        const long long b = a + g.P < t1 ? a + g.P : t1;
+        {
+            double z[S][2];
+#pragma unroll
+            for (int s = 0; s < S; ++s) {
+                z[s][0] = at(sub, p * (2 * S) + 2 * s, NT, T);
+                z[s][1] = at(sub, p * (2 * S) + 2 * s + 1, NT, T);
+            }
+            for (long long n = a; n < b; ++n) {
+                double u = (double)x[n * ldx + c];
+#pragma unroll
+                for (int s = 0; s < S; ++s) {
+                    u = tdf2_step(k, s, u, z[s][0], z[s][1]);
+                    at(sig, (n - a) * S + s, NT, T) = u;
+                }
+            }
+        }
+        for (long long n = b - 1; n >= a; --n) {
+            double gg = (double)gy[n * ldg + c];
+#pragma unroll
+            for (int s = S - 1; s >= 0; --s) {
+                const double ys = at(sig, (n - a) * S + s, NT, T);
+                const double us = s == 0 ? (double)x[n * ldx + c] : at(sig, (n - a) * S + s - 1, NT, T);
+                const double wn1 = w1[s], wn2 = w2[s];
+                double w;
+                gg = adj_step(k, s, gg, w1[s], w2[s], w);
+                gb[s][0] += us * w;
+                gb[s][1] += us * wn1;
+                gb[s][2] += us * wn2;
+                ga[s][0] -= ys * w;
+                ga[s][1] -= ys * wn1;
+                ga[s][2] -= ys * wn2;
+            }
+            if (gx) gx[n * ldgx + c] = (float)gg;
+        }
+    }
+#pragma unroll
+    for (int s = 0; s < S; ++s)
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            at(gpart, 6 * s + i, NT, T) = gb[s][i];
+            at(gpart, 6 * s + 3 + i, NT, T) = ga[s][i];
+        }
+}
+
+// B4: dL/dsos[j] = sum over all (segment, channel) partials, FP64, fixed order.
+__global__ void __launch_bounds__(256) sum_partials_kernel(const double *__restrict__ gpart, long long NT,
+                                                           double *__restrict__ gsos) {
+    __shared__ double part[256];
+    const int j = blockIdx.x;
+    double acc = 0.0;
+    for (long long t = threadIdx.x; t < NT; t += blockDim.x) acc += gpart[j * NT + t];
+    part[threadIdx.x] = acc;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) part[threadIdx.x] += part[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) gsos[j] = part[0];
+}
+
+// ---- host side ---------------------------------------------------------------
+
+bool load_coef(const double *sos, int S, SosCoef &k) {
+    std::memset(&k, 0, sizeof(k));
+    for (int s = 0; s < S; ++s) {
+        const double *r = sos + 6 * s;
+        for (int i = 0; i < 6; ++i)
+            if (!std::isfinite(r[i])) return false;
+        if (r[3] == 0.0) return false;
+        for (int i = 0; i < 3; ++i) {
+            k.b[s][i] = r[i];
+            k.a[s][i] = r[3 + i];
+            k.nb[s][i] = r[i] / r[3];
+        }
+        k.na[s][0] = r[4] / r[3];
+        k.na[s][1] = r[5] / r[3];
+        k.ia0[s] = 1.0 / r[3];
+    }
+    return true;
+}
+
+// The kernels' own zero-input recursions, one step, in long double: column q
+// of the one-step matrix is the step applied to unit vector q.
+void one_step_matrix(const SosCoef &k, int S, bool adjoint, long double M[kMaxState][kMaxState]) {
+    const int D = 2 * S;
+    for (int q = 0; q < D; ++q) {
+        long double v[kMaxState] = {};
+        v[q] = 1.0L;
+        if (!adjoint) {
+            long double u = 0.0L;
+            for (int s = 0; s < S; ++s) u = tdf2_step<long double>(k, s, u, v[2 * s], v[2 * s + 1]);
+        } else {
+            long double gg = 0.0L, w;
+            for (int s = S - 1; s >= 0; --s) gg = adj_step<long double>(k, s, gg, v[2 * s], v[2 * s + 1], w);
+        }
+        for (int i = 0; i < D; ++i) M[i][q] = v[i];
+    }
+}
+
+void mat_mul(int D, const long double A[kMaxState][kMaxState], const long double B[kMaxState][kMaxState],
+             long double R[kMaxState][kMaxState]) {
+    long double t[kMaxState][kMaxState];
+    for (int i = 0; i < D; ++i)
+        for (int j = 0; j < D; ++j) {
+            long double acc = 0.0L;
+            for (int q = 0; q < D; ++q) acc += A[i][q] * B[q][j];
+            t[i][j] = acc;
+        }
+    for (int i = 0; i < D; ++i)
+        for (int j = 0; j < D; ++j) R[i][j] = t[i][j];
+}
+
+// transition over n steps of zero input, by repeated squaring
+void transition(const SosCoef &k, int S, bool adjoint, long long n, Transition &out) {
+    const int D = 2 * S;
+    long double M[kMaxState][kMaxState], R[kMaxState][kMaxState];
+    one_step_matrix(k, S, adjoint, M);
+    for (int i = 0; i < D; ++i)
+        for (int j = 0; j < D; ++j) R[i][j] = i == j ? 1.0L : 0.0L;
+    while (n > 0) {
+        if (n & 1) mat_mul(D, R, M, R);
+        n >>= 1;
+        if (n) mat_mul(D, M, M, M);
+    }
+    std::memset(&out, 0, sizeof(out));
+    for (int i = 0; i < D; ++i)
+        for (int j = 0; j < D; ++j) out.T[i][j] = (double)R[i][j];
+}
+
+long long piece_len(long long ckpt) {
+    long long P = (long long)std::ceil(std::sqrt(2.0 * (double)ckpt));
+    return std::max(1LL, std::min(P, ckpt));
+}
+
+bool make_geometry(int S, int C, long long N, long long ckpt, Geometry &g) {
+    if (S < 1 || S > kMaxS || C < 1 || N < 1 || ckpt < 1) return false;
+    g.N = N;
+    g.C = C;
+    g.ckpt = ckpt;
+    g.P = piece_len(ckpt);
+    g.nseg = (N + ckpt - 1) / ckpt;
+    g.npiece = (std::min(ckpt, N) + g.P - 1) / g.P;
+    g.NT = g.nseg * (long long)C;
+    return true;
+}
+
+size_t ckpt_doubles(const Geometry &g, int S) { return (size_t)g.NT * (size_t)(2 * S); }
+
+// workspace: beta [2S][NT], sub [npiece*2S][NT], sig [P*S][NT], gpart [6S][NT]
+size_t work_doubles(const Geometry &g, int S) {
+    return (size_t)g.NT * (size_t)(2 * S + g.npiece * 2 * S + g.P * S + 6 * S);
+}
+
+bool check_sos(const double *sos, int S, SosCoef &k) {
+    if (!sos || !load_coef(sos, S, k)) {
+        set_last_error("sos: NULL, a non-finite coefficient, or a0 == 0");
+        return false;
+    }
+    return true;
+}
+
+filark_status launch_status(const char *where) {
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        set_last_error(std::string(where) + ": " + cudaGetErrorString(e));
+        return FILARK_ECUDA;
+    }
+    return FILARK_OK;
+}
+
+template <int S>
+void launch_forward(const SosCoef &k, const Transition &tr, const Geometry &g, const float *x, long long ldx,
+                    float *y, long long ldy, double *ckpt, cudaStream_t st) {
+    const unsigned nb = (unsigned)((g.NT + kAdjThreads - 1) / kAdjThreads);
+    const unsigned nc = (unsigned)((g.C + kAdjThreads - 1) / kAdjThreads);
+    fwd_local_kernel<S><<<nb, kAdjThreads, 0, st>>>(k, g, x, ldx, ckpt);
+    chain_segments_kernel<S><<<nc, kAdjThreads, 0, st>>>(tr, g, ckpt, 0);
+    if (y) fwd_run_kernel<S><<<nb, kAdjThreads, 0, st>>>(k, g, x, ldx, ckpt, y, ldy);
+}
+
+template <int S>
+void launch_backward(const SosCoef &k, const Transition &tr, const Geometry &g, const float *x, long long ldx,
+                     const float *gy, long long ldg, const double *ckpt, double *work, float *gx, long long ldgx,
+                     double *gsos, cudaStream_t st) {
+    const unsigned nb = (unsigned)((g.NT + kAdjThreads - 1) / kAdjThreads);
+    const unsigned nc = (unsigned)((g.C + kAdjThreads - 1) / kAdjThreads);
+    double *beta = work;
+    double *sub = beta + (size_t)g.NT * (2 * S);
+    double *sig = sub + (size_t)g.NT * (size_t)(g.npiece * 2 * S);
+    double *gpart = sig + (size_t)g.NT * (size_t)(g.P * S);
+    adj_local_kernel<S><<<nb, kAdjThreads, 0, st>>>(k, g, gy, ldg, beta);
+    chain_segments_kernel<S><<<nc, kAdjThreads, 0, st>>>(tr, g, beta, 1);
+    adj_run_kernel<S><<<nb, kAdjThreads, 0, st>>>(k, g, x, ldx, gy, ldg, ckpt, beta, sub, sig, gx, ldgx, gpart);
+    sum_partials_kernel<<<6 * S, 256, 0, st>>>(gpart, g.NT, gsos);
+}
+
+}  // namespace
+
+extern "C" size_t filark_iir_ckpt_bytes(int n_sections, int n_channels, int64_t n_samples, int64_t ckpt_every) {
+    Geometry g;
+    if (!make_geometry(n_sections, n_channels, n_samples, ckpt_every, g)) return 0;
+    return sizeof(double) * ckpt_doubles(g, n_sections);
+}
+
+extern "C" size_t filark_iir_work_bytes(int n_sections, int n_channels, int64_t n_samples, int64_t ckpt_every) {
+    Geometry g;
+    if (!make_geometry(n_sections, n_channels, n_samples, ckpt_every, g)) return 0;
+    return sizeof(double) * work_doubles(g, n_sections);
+}
+
+extern "C" filark_status filark_iir_forward_ckpt(const double *sos, int n_sections, int n_channels,
+                                                 const float *d_x, int64_t ld_x, int64_t n_samples, float *d_y,
+                                                 int64_t ld_y, int64_t ckpt_every, void *d_ckpt, size_t ckpt_size,
+                                                 filark_stream_t stream) {
+    Geometry g;
+    if (!make_geometry(n_sections, n_channels, n_samples, ckpt_every, g)) {
+        set_last_error("need 1 <= n_sections <= FILARK_MAX_SECTIONS, n_channels >= 1, n_samples >= 1, ckpt_every >= 1");
+        return FILARK_EINVAL;
+    }
+    SosCoef k;
+    if (!check_sos(sos, n_sections, k)) return FILARK_EINVAL;
+    if (!d_x || !d_ckpt || ld_x < n_channels || (d_y && ld_y < n_channels)) {
+        set_last_error("iir_forward_ckpt: NULL input or checkpoint buffer, or a leading dimension < n_channels");
+        return FILARK_EINVAL;
+    }
+    if (ckpt_size < sizeof(double) * ckpt_doubles(g, n_sections) || ((uintptr_t)d_ckpt & 7)) {
+        set_last_error("iir_forward_ckpt: checkpoint buffer smaller than filark_iir_ckpt_bytes or not 8-byte aligned");
+        return FILARK_EINVAL;
+    }
+    Transition tr;
+    transition(k, n_sections, false, g.ckpt, tr);
+    cudaStream_t st = (cudaStream_t)stream;
+    double *ck = (double *)d_ckpt;
+    switch (n_sections) {
+#define FWD_CASE(S_) \
+    case S_: launch_forward<S_>(k, tr, g, d_x, ld_x, d_y, ld_y, ck, st); break;
+        FWD_CASE(1) FWD_CASE(2) FWD_CASE(3) FWD_CASE(4) FWD_CASE(5) FWD_CASE(6) FWD_CASE(7) FWD_CASE(8)
+#undef FWD_CASE
+    }
+    return launch_status("iir_forward_ckpt");
+}
+
+extern "C" filark_status filark_iir_backward(const double *sos, int n_sections, int n_channels, const float *d_x,
+                                             int64_t ld_x, int64_t n_samples, const float *d_gy, int64_t ld_gy,
+                                             int64_t ckpt_every, const void *d_ckpt, size_t ckpt_size, void *d_work,
+                                             size_t work_size, float *d_gx, int64_t ld_gx, double *d_gsos,
+                                             filark_stream_t stream) {
+    Geometry g;
+    if (!make_geometry(n_sections, n_channels, n_samples, ckpt_every, g)) {
+        set_last_error("need 1 <= n_sections <= FILARK_MAX_SECTIONS, n_channels >= 1, n_samples >= 1, ckpt_every >= 1");
+        return FILARK_EINVAL;
+    }
+    SosCoef k;
+    if (!check_sos(sos, n_sections, k)) return FILARK_EINVAL;
+    if (!d_x || !d_gy || !d_ckpt || !d_work || !d_gsos || ld_x < n_channels || ld_gy < n_channels ||
+        (d_gx && ld_gx < n_channels)) {
+        set_last_error("iir_backward: NULL buffer or a leading dimension < n_channels");
+        return FILARK_EINVAL;
+    }
+    if (ckpt_size < sizeof(double) * ckpt_doubles(g, n_sections) ||
+        work_size < sizeof(double) * work_doubles(g, n_sections) || ((uintptr_t)d_ckpt & 7) ||
+        ((uintptr_t)d_work & 7) || ((uintptr_t)d_gsos & 7)) {
+        set_last_error("iir_backward: checkpoint or work buffer too small (filark_iir_ckpt_bytes, "
+                       "filark_iir_work_bytes) or not 8-byte aligned");
+        return FILARK_EINVAL;
+    }
+    Transition tr;
+    transition(k, n_sections, true, g.ckpt, tr);
+    cudaStream_t st = (cudaStream_t)stream;
+    const double *ck = (const double *)d_ckpt;
+    double *wk = (double *)d_work;
+    switch (n_sections) {
+#define BWD_CASE(S_) \
+    case S_: launch_backward<S_>(k, tr, g, d_x, ld_x, d_gy, ld_gy, ck, wk, d_gx, ld_gx, d_gsos, st); break;
+        BWD_CASE(1) BWD_CASE(2) BWD_CASE(3) BWD_CASE(4) BWD_CASE(5) BWD_CASE(6) BWD_CASE(7) BWD_CASE(8)
+#undef BWD_CASE
+    }
+    return launch_status("iir_backward");
+}

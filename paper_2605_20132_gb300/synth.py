@@ -144,6 +144,14 @@ def paper_scale_stream(n_channels: int = 6000, n_samples: int = 90_000, seed: in
                                (-1.0, 1.0), seed, pink=True)
 
 
+def adjoint_stream(n_channels: int = 2048, n_samples: int = 30_000, seed: int = 4) -> np.ndarray:
+    """Input of the differentiation workload: 1 kHz float32 N(0,1) noise plus
+    Ricker events (amplitude 5, peak 5-50 Hz, moveout -1..1 ms/channel), one
+    event per 64 channels."""
+    return noise_ricker_stream(n_channels, n_samples, 1000.0, max(1, n_channels // 64), 5.0, (5.0, 50.0),
+                               (-1.0, 1.0), seed, pink=False)
+
+
 def precision_chunk(chunk_index: int, n_channels: int = 10_000, chunk: int = 1500,
                     fs: float = 1500.0, seed: int = 5, sine_hz: float = 0.05,
                     sine_amp: float = 0.1, channels: np.ndarray | None = None) -> np.ndarray:

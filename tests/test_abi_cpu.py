@@ -150,3 +150,61 @@ def test_modal_request_with_repeated_poles_is_unsupported():
 
 def test_destroy_null_is_ok():
     assert abi.filark_chain_destroy(None) == abi.FILARK_OK
+
+
+# ---- differentiable bandpass: host-side sizes and argument checks ----------
+
+def _piece(ckpt):
+    import math
+    return max(1, min(math.ceil(math.sqrt(2.0 * ckpt)), ckpt))
+
+
+@pytest.mark.parametrize("S,C,N,ckpt", [(4, 2048, 30000, 3000), (1, 1, 1, 1), (8, 37, 777, 100), (4, 16, 2000, 5000)])
+def test_iir_buffer_sizes(S, C, N, ckpt):
+    """Checkpoints: 2S doubles per channel per segment; work: the adjoint
+    states, piece states, one piece of section signals and the gradient
+    partials per (segment, channel)."""
+    nseg = -(-N // ckpt)
+    P = _piece(ckpt)
+    npiece = -(-min(ckpt, N) // P)
+    assert abi.filark_iir_ckpt_bytes(S, C, N, ckpt) == 8 * nseg * C * 2 * S
+    assert abi.filark_iir_work_bytes(S, C, N, ckpt) == 8 * nseg * C * (2 * S + npiece * 2 * S + P * S + 6 * S)
+
+
+@pytest.mark.parametrize("args", [(0, 4, 10, 5), (9, 4, 10, 5), (4, 0, 10, 5), (4, 4, 0, 5), (4, 4, 10, 0)])
+def test_iir_buffer_sizes_reject_invalid(args):
+    assert abi.filark_iir_ckpt_bytes(*args) == 0
+    assert abi.filark_iir_work_bytes(*args) == 0
+
+
+def test_iir_checkpoint_memory_is_far_below_all_intermediates():
+    """The differentiation workload keeps well under a tenth of the memory that
+    storing every section signal in FP64 would take."""
+    S, C, N, ckpt = 4, 2048, 30000, 3000
+    full = 8 * S * C * N
+    kept = abi.filark_iir_ckpt_bytes(S, C, N, ckpt) + abi.filark_iir_work_bytes(S, C, N, ckpt)
+    assert kept < full / 10
+
+
+def test_iir_calls_reject_bad_arguments_before_any_launch():
+    """Argument errors return FILARK_EINVAL without touching the device (the
+    pointers below are never dereferenced)."""
+    sos = np.array([[1.0, 0.0, -1.0, 1.0, -1.9, 0.95]])
+    fake = 0x1000
+    nb = abi.filark_iir_ckpt_bytes(1, 4, 10, 5)
+    wb = abi.filark_iir_work_bytes(1, 4, 10, 5)
+    bad_sos = np.array([[1.0, 0.0, -1.0, 0.0, -1.9, 0.95]])
+    nan_sos = np.array([[1.0, np.nan, -1.0, 1.0, -1.9, 0.95]])
+    for q in (bad_sos, nan_sos):
+        assert abi.filark_iir_forward_ckpt(q, 1, 4, fake, 4, 10, fake, 4, 5, fake, nb, None) == abi.FILARK_EINVAL
+    assert abi.filark_iir_forward_ckpt(sos, 1, 4, fake, 3, 10, fake, 4, 5, fake, nb, None) == abi.FILARK_EINVAL
+    assert abi.filark_iir_forward_ckpt(sos, 1, 4, fake, 4, 10, fake, 4, 5, fake, nb - 8, None) == abi.FILARK_EINVAL
+    assert abi.filark_iir_forward_ckpt(sos, 1, 4, None, 4, 10, fake, 4, 5, fake, nb, None) == abi.FILARK_EINVAL
+    assert abi.filark_iir_forward_ckpt(sos, 1, 4, fake, 4, 10, fake, 4, 0, fake, nb, None) == abi.FILARK_EINVAL
+    assert abi.filark_iir_backward(sos, 1, 4, fake, 4, 10, fake, 4, 5, fake, nb, fake, wb - 8, fake, 4, fake,
+                                   None) == abi.FILARK_EINVAL
+    assert abi.filark_iir_backward(sos, 1, 4, fake, 4, 10, fake, 4, 5, fake, nb, None, wb, fake, 4, fake,
+                                   None) == abi.FILARK_EINVAL
+    assert abi.filark_iir_backward(sos, 1, 4, fake, 4, 10, fake, 4, 5, fake, nb, fake, wb, fake, 4, fake + 4,
+                                   None) == abi.FILARK_EINVAL
+    assert "aligned" in abi.filark_last_error_string()
