@@ -336,7 +336,7 @@ def run_gpu(args, rank: int, world: int, dist) -> None:
 def kernel_sha() -> str:
     import hashlib
     hsh = hashlib.sha256()
-    for f in ("chain_kernel.cu", "filark_internal.h"):
+    for f in ("chain_body.cuh", "chain_kernel.cu", "filark_internal.h"):
         with open(os.path.join(ROOT, "paper_2605_20132_gb300", "csrc", f), "rb") as fh:
             hsh.update(fh.read())
     return hsh.hexdigest()[:16]

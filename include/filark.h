@@ -274,6 +274,79 @@ filark_status filark_iir_backward(const double *sos, int n_sections, int n_chann
                                   size_t work_size, float *d_gx, int64_t ld_gx, double *d_gsos,
                                   filark_stream_t stream);
 
+/*
+ * Batched chains: many independent streams with the same chain configuration
+ * (filter, spatial width, detector windows, outputs, precision, max_chunk) but
+ * their own channel count, chunk lengths and carried state -- the many
+ * concurrent DAS recordings a production deployment serves at once (Sec. 6.2
+ * streams one recording; this serves many).  Each push of all streams is ONE
+ * persistent kernel: a grid of thread-block clusters walks the (stream,
+ * channel tile) work items, longest chunk first, and runs every stream's push
+ * with the same arithmetic as filark_chain_push_chunk.  The descriptor upload
+ * and the launch are captured once in a CUDA graph and replayed per push.
+ *
+ * The launch geometry -- time ranges per cluster (the scan blocks one cluster
+ * combines, 1, 2, 4 or 8 x 256 samples) and the number of resident clusters --
+ * is chosen by filark_batch_tune, which times the candidates on a caller-given
+ * push; until then a fixed default is used.
+ */
+typedef struct filark_batch filark_batch;
+
+/* One stream's part of a batched push; the same rules as the arguments of
+   filark_chain_push_chunk (n_samples may be 0: the stream is skipped). */
+typedef struct {
+    const float *d_in;
+    int64_t ld_in;
+    int64_t n_samples;
+    float *d_ratio, *d_bandpass, *d_spatial;
+    int64_t ld_out;
+} filark_chunk_desc;
+
+typedef struct {
+    int32_t n_streams;
+    int32_t cluster;          /* CTAs (time ranges of 256 samples) per cluster */
+    int32_t n_clusters;       /* persistent grid, in clusters                  */
+    int32_t use_graph;        /* 1: pushes replay a captured CUDA graph         */
+    int64_t n_tiles;          /* work items of a push that feeds every stream  */
+    int64_t device_bytes;     /* state, rings, descriptors                     */
+    int32_t n_tuned;          /* candidates timed by the last filark_batch_tune */
+    int32_t tune_cluster[16];
+    int32_t tune_clusters[16];
+    double tune_ms[16];       /* mean ms per push of each candidate            */
+} filark_batch_info;
+
+/* cfg is the configuration every stream shares; its n_channels is ignored and
+   n_channels[i] (>= 1) is used for stream i.  n_streams >= 1.  Allocates every
+   stream's state like filark_chain_create, plus the descriptor buffers and two
+   captured graphs. */
+filark_status filark_batch_create(const filark_chain_config *cfg, int n_streams, const int32_t *n_channels,
+                                  int cuda_device, filark_batch **out);
+
+/* Push descs[0 .. n_streams) (host array, read during the call) on `stream`:
+   one launch for all streams.  Returns after enqueueing; the host may block
+   briefly until the descriptor upload of the push before last has run. */
+filark_status filark_batch_push(filark_batch *b, const filark_chunk_desc *descs, filark_stream_t stream);
+
+/* Time each launch geometry on the push `descs` (warm-up pushes, then
+   timed_pushes >= 1 timed ones, CUDA events on `stream`), keep the fastest,
+   and reset every stream's state (the trial pushes advance it).  Blocks until
+   done.  The outputs of descs are overwritten. */
+filark_status filark_batch_tune(filark_batch *b, const filark_chunk_desc *descs, int timed_pushes,
+                                filark_stream_t stream);
+
+/* Set the launch geometry by hand: cluster in {1, 2, 4, 8}; n_clusters <= 0
+   takes the occupancy limit; use_graph 0 launches without a graph. */
+filark_status filark_batch_set_launch(filark_batch *b, int cluster, int n_clusters, int use_graph);
+
+filark_status filark_batch_reset_state(filark_batch *b, filark_stream_t stream);
+filark_status filark_batch_sync_status(filark_batch *b, filark_stream_t stream);
+filark_status filark_batch_get_info(const filark_batch *b, filark_batch_info *out);
+/* Stream i's chain (owned by the batch; valid until filark_batch_destroy):
+   for filark_chain_get_state / get_info.  Pushing it directly is allowed
+   between batched pushes. */
+filark_status filark_batch_stream(filark_batch *b, int i, filark_chain **out);
+filark_status filark_batch_destroy(filark_batch *b);   /* NULL ok */
+
 /* Message for the last error returned to this thread ("" if none). */
 const char *filark_last_error_string(void);
 

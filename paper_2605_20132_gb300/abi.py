@@ -45,6 +45,9 @@ EXPORTED = (
     "filark_butter_bandpass_sos", "filark_last_error_string", "filark_abi_version",
     "filark_chain_run_static", "filark_iir_ckpt_bytes", "filark_iir_work_bytes",
     "filark_iir_forward_ckpt", "filark_iir_backward",
+    "filark_batch_create", "filark_batch_push", "filark_batch_tune", "filark_batch_set_launch",
+    "filark_batch_reset_state", "filark_batch_sync_status", "filark_batch_get_info", "filark_batch_stream",
+    "filark_batch_destroy",
 )
 
 
@@ -77,6 +80,33 @@ class filark_chain_info(ct.Structure):
         ("ring_len", ct.c_int64),
         ("device_bytes", ct.c_int64),
         ("samples", ct.c_int64),
+    ]
+
+
+class filark_chunk_desc(ct.Structure):
+    _fields_ = [
+        ("d_in", ct.c_void_p),
+        ("ld_in", ct.c_int64),
+        ("n_samples", ct.c_int64),
+        ("d_ratio", ct.c_void_p),
+        ("d_bandpass", ct.c_void_p),
+        ("d_spatial", ct.c_void_p),
+        ("ld_out", ct.c_int64),
+    ]
+
+
+class filark_batch_info(ct.Structure):
+    _fields_ = [
+        ("n_streams", ct.c_int32),
+        ("cluster", ct.c_int32),
+        ("n_clusters", ct.c_int32),
+        ("use_graph", ct.c_int32),
+        ("n_tiles", ct.c_int64),
+        ("device_bytes", ct.c_int64),
+        ("n_tuned", ct.c_int32),
+        ("tune_cluster", ct.c_int32 * 16),
+        ("tune_clusters", ct.c_int32 * 16),
+        ("tune_ms", ct.c_double * 16),
     ]
 
 
@@ -117,6 +147,16 @@ def load(build_if_missing: bool = True) -> ct.CDLL:
             "filark_abi_version": ([], ct.c_uint32),
             "filark_chain_run_static": ([ct.POINTER(filark_chain_config), vp, i64, i64, vp, vp, vp, i64, vp],
                                         ct.c_int),
+            "filark_batch_create": ([ct.POINTER(filark_chain_config), ct.c_int, ct.POINTER(ct.c_int32), ct.c_int,
+                                     ct.POINTER(vp)], ct.c_int),
+            "filark_batch_push": ([vp, ct.POINTER(filark_chunk_desc), vp], ct.c_int),
+            "filark_batch_tune": ([vp, ct.POINTER(filark_chunk_desc), ct.c_int, vp], ct.c_int),
+            "filark_batch_set_launch": ([vp, ct.c_int, ct.c_int, ct.c_int], ct.c_int),
+            "filark_batch_reset_state": ([vp, vp], ct.c_int),
+            "filark_batch_sync_status": ([vp, vp], ct.c_int),
+            "filark_batch_get_info": ([vp, ct.POINTER(filark_batch_info)], ct.c_int),
+            "filark_batch_stream": ([vp, ct.c_int, ct.POINTER(vp)], ct.c_int),
+            "filark_batch_destroy": ([vp], ct.c_int),
             "filark_iir_ckpt_bytes": ([ct.c_int, ct.c_int, i64, i64], ct.c_size_t),
             "filark_iir_work_bytes": ([ct.c_int, ct.c_int, i64, i64], ct.c_size_t),
             "filark_iir_forward_ckpt": ([vp, ct.c_int, ct.c_int, vp, i64, i64, vp, i64, i64, vp, ct.c_size_t, vp],
@@ -218,6 +258,50 @@ def filark_iir_backward(sos_host, n_sections, n_channels, d_x, ld_x, n_samples, 
     return load().filark_iir_backward(sos_host.ctypes.data, n_sections, n_channels, d_x, ld_x, n_samples, d_gy,
                                       ld_gy, ckpt_every, d_ckpt, ckpt_size, d_work, work_size, d_gx, ld_gx, d_gsos,
                                       stream)
+
+
+def filark_batch_create(cfg: filark_chain_config, n_channels, cuda_device: int) -> tuple[int, int | None]:
+    arr = (ct.c_int32 * len(n_channels))(*[int(c) for c in n_channels])
+    h = ct.c_void_p()
+    st = load().filark_batch_create(ct.byref(cfg), len(n_channels), arr, int(cuda_device), ct.byref(h))
+    return st, h.value
+
+
+def filark_batch_push(b, descs, stream) -> int:
+    """descs: a ctypes array of filark_chunk_desc, one per stream."""
+    return load().filark_batch_push(b, descs, stream)
+
+
+def filark_batch_tune(b, descs, timed_pushes: int, stream) -> int:
+    return load().filark_batch_tune(b, descs, int(timed_pushes), stream)
+
+
+def filark_batch_set_launch(b, cluster: int, n_clusters: int, use_graph: int) -> int:
+    return load().filark_batch_set_launch(b, int(cluster), int(n_clusters), int(use_graph))
+
+
+def filark_batch_reset_state(b, stream) -> int:
+    return load().filark_batch_reset_state(b, stream)
+
+
+def filark_batch_sync_status(b, stream) -> int:
+    return load().filark_batch_sync_status(b, stream)
+
+
+def filark_batch_get_info(b) -> tuple[int, filark_batch_info]:
+    info = filark_batch_info()
+    st = load().filark_batch_get_info(b, ct.byref(info))
+    return st, info
+
+
+def filark_batch_stream(b, i: int) -> tuple[int, int | None]:
+    h = ct.c_void_p()
+    st = load().filark_batch_stream(b, int(i), ct.byref(h))
+    return st, h.value
+
+
+def filark_batch_destroy(b) -> int:
+    return load().filark_batch_destroy(b)
 
 
 def filark_last_error_string() -> str:

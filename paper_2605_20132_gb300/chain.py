@@ -127,3 +127,92 @@ class Chain:
         st, inf = abi.filark_chain_get_info(self._h)
         abi.check(st, "filark_chain_get_info")
         return {k: getattr(inf, k) for k, _ in inf._fields_}
+
+
+class Batch:
+    """Many independent chains with one configuration (own channel counts,
+    chunk lengths and state), pushed together by one persistent launch."""
+
+    def __init__(self, n_channels, sos: np.ndarray | None, fs: float = 1.0, spatial_width: int = 1,
+                 sta_len: int = 0, lta_len: int = 0, outputs: int = abi.FILARK_OUT_RATIO,
+                 precision: int = abi.FILARK_PREC_AUTO, max_chunk: int = 4096, device: int = 0):
+        abi.load()
+        self._sos = np.ascontiguousarray(np.zeros((0, 6)) if sos is None else sos, dtype=np.float64)
+        cfg = abi.filark_chain_config()
+        cfg.abi_version = abi.FILARK_ABI_VERSION
+        cfg.n_channels = 1
+        cfg.fs = float(fs)
+        cfg.n_sections = int(self._sos.shape[0])
+        cfg.sos = self._sos.ctypes.data_as(ct.POINTER(ct.c_double)) if self._sos.size else None
+        cfg.spatial_width = int(spatial_width)
+        cfg.sta_len = int(sta_len)
+        cfg.lta_len = int(lta_len)
+        cfg.outputs = int(outputs)
+        cfg.precision = int(precision)
+        cfg.max_chunk = int(max_chunk)
+        self.cfg = cfg
+        self.n_channels = [int(c) for c in n_channels]
+        self.device = int(device)
+        st, h = abi.filark_batch_create(cfg, self.n_channels, self.device)
+        abi.check(st, "filark_batch_create")
+        self._h = h
+        self._descs = (abi.filark_chunk_desc * len(self.n_channels))()
+
+    def close(self) -> None:
+        if getattr(self, "_h", None):
+            abi.check(abi.filark_batch_destroy(self._h), "filark_batch_destroy")
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _fill(self, xs, ratios=None, bandpasses=None, spatials=None):
+        n = len(self.n_channels)
+        ratios = ratios or [None] * n
+        bandpasses = bandpasses or [None] * n
+        spatials = spatials or [None] * n
+        for i in range(n):
+            d = self._descs[i]
+            x = xs[i]
+            T = 0 if x is None else int(x.shape[0])
+            d.n_samples = T
+            d.d_in = _ptr(x) if T else None
+            d.ld_in = int(x.stride(0)) if T else self.n_channels[i]
+            outs = [o for o in (ratios[i], bandpasses[i], spatials[i]) if o is not None]
+            d.ld_out = int(outs[0].stride(0)) if (outs and T) else self.n_channels[i]
+            d.d_ratio = _ptr(ratios[i]) if T else None
+            d.d_bandpass = _ptr(bandpasses[i]) if T else None
+            d.d_spatial = _ptr(spatials[i]) if T else None
+        return self._descs
+
+    def push(self, xs, ratios=None, bandpasses=None, spatials=None, stream=None) -> None:
+        """xs[i]: CUDA float32 [T_i][ld] (or None for no samples); outputs alike."""
+        d = self._fill(xs, ratios, bandpasses, spatials)
+        abi.check(abi.filark_batch_push(self._h, d, _stream_handle(stream)), "filark_batch_push")
+
+    def tune(self, xs, ratios=None, bandpasses=None, spatials=None, timed_pushes: int = 5, stream=None) -> dict:
+        d = self._fill(xs, ratios, bandpasses, spatials)
+        abi.check(abi.filark_batch_tune(self._h, d, timed_pushes, _stream_handle(stream)), "filark_batch_tune")
+        return self.info()
+
+    def set_launch(self, cluster: int, n_clusters: int = 0, use_graph: bool = True) -> None:
+        abi.check(abi.filark_batch_set_launch(self._h, cluster, n_clusters, int(use_graph)),
+                  "filark_batch_set_launch")
+
+    def reset(self, stream=None) -> None:
+        abi.check(abi.filark_batch_reset_state(self._h, _stream_handle(stream)), "filark_batch_reset_state")
+
+    def sync(self, stream=None) -> None:
+        abi.check(abi.filark_batch_sync_status(self._h, _stream_handle(stream)), "filark_batch_sync_status")
+
+    def info(self) -> dict:
+        st, inf = abi.filark_batch_get_info(self._h)
+        abi.check(st, "filark_batch_get_info")
+        out = {k: getattr(inf, k) for k, _ in inf._fields_ if not k.startswith("tune_")}
+        n = inf.n_tuned
+        out["tuned"] = [dict(cluster=inf.tune_cluster[i], n_clusters=inf.tune_clusters[i], ms=inf.tune_ms[i])
+                        for i in range(n)]
+        return out

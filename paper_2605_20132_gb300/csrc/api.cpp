@@ -14,7 +14,7 @@
 #include <string>
 #include <vector>
 
-#include "filark_internal.h"
+#include "chain_object.h"
 
 using namespace filark;
 
@@ -63,30 +63,6 @@ struct StateHeader {
 namespace filark {
 void set_last_error(const std::string &msg) { g_err = msg; }
 }  // namespace filark
-
-struct filark_chain {
-    filark_chain_config cfg{};
-    std::vector<double> sos;
-    Plan plan;
-    int device = 0;
-    int C = 0, K = 1, hw = 0, HP = 0, Wout = 0, n_tiles = 0;
-    bool det = false;
-    int ns = 0, nl = 0;
-    long long Q = 0, ldr = 0;
-    double *iir[2] = {nullptr, nullptr};
-    double *detst[2] = {nullptr, nullptr};
-    float *ring = nullptr;
-    int *status_host = nullptr;   // mapped pinned word written by kernels
-    int *status_dev = nullptr;
-    int parity = 0;
-    long long n = 0;
-    filark_status sticky = FILARK_OK;
-    float *stage[4] = {nullptr, nullptr, nullptr, nullptr};   // in, ratio, bp, sp
-    double *dense = nullptr;      // dense carry matrices (device)
-    ChainParams base{};
-    int64_t device_bytes = 0;
-    int use_pdl = 1;
-};
 
 namespace {
 
@@ -143,46 +119,26 @@ filark_status push_device(filark_chain *h, const float *d_in, int64_t ld_in, int
     while (done < T) {
         const int Tl = (int)std::min<int64_t>(T - done, kMaxLaunchSamples);
         ChainParams p = h->base;
-        p.x = d_in + done * ld_in;
-        p.ldx = ld_in;
-        p.ratio = d_ratio ? d_ratio + done * ld_out : nullptr;
-        p.bp = d_bp ? d_bp + done * ld_out : nullptr;
-        p.sp = d_sp ? d_sp + done * ld_out : nullptr;
-        p.ldo = ld_out;
-        p.iir_in = h->iir[h->parity];
-        p.iir_out = h->iir[h->parity ^ 1];
-        p.det_in = h->detst[h->parity];
-        p.det_out = h->detst[h->parity ^ 1];
-        p.n0 = h->n;
-        p.T = Tl;
-        p.nblk = (Tl + kL - 1) / kL;
-        p.Lr = Tl - (p.nblk - 1) * kL;
-        p.R = (p.nblk + kNB - 1) / kNB;
-        if (NS > 0) {
-            const int nb_last = p.nblk - (p.R - 1) * kNB;
-            const double (*pl)[4] = h->plan.power_cached((nb_last - 1) * kL + p.Lr);
-            const double (*pr)[4] = h->plan.power_cached(p.Lr);
-            const double (*pp)[4] = h->plan.power_cached_cta(p.R - 1);
-            for (int s = 0; s < kMaxSlots; ++s) {
-                for (int q = 0; q < 4; ++q) {
-                    p.PhiLast[s][q] = pl[s][q];
-                    p.Mr32[s][q] = (float)pr[s][q];
-                }
-                // PhiTot = PhiLast * Phi^(R-1) (2x2 per slot)
-                const double *a = pl[s], *b = pp[s];
-                p.PhiTot[s][0] = a[0] * b[0] + a[1] * b[2];
-                p.PhiTot[s][1] = a[0] * b[1] + a[1] * b[3];
-                p.PhiTot[s][2] = a[2] * b[0] + a[3] * b[2];
-                p.PhiTot[s][3] = a[2] * b[1] + a[3] * b[3];
-            }
-        }
-        p.slot_n0 = h->Q > 0 ? (int)(h->n % h->Q) : 0;
+        ChainUnit &u = p.u;
+        u.x = d_in + done * ld_in;
+        u.ldx = ld_in;
+        u.ratio = d_ratio ? d_ratio + done * ld_out : nullptr;
+        u.bp = d_bp ? d_bp + done * ld_out : nullptr;
+        u.sp = d_sp ? d_sp + done * ld_out : nullptr;
+        u.ldo = ld_out;
+        u.iir_in = h->iir[h->parity];
+        u.iir_out = h->iir[h->parity ^ 1];
+        u.det_in = h->detst[h->parity];
+        u.det_out = h->detst[h->parity ^ 1];
+        u.n0 = h->n;
+        set_unit_geometry(h->plan, Tl, u);
+        u.slot_n0 = h->Q > 0 ? (int)(h->n % h->Q) : 0;
         p.pdl = h->use_pdl;
-        p.x_vec4 = (ld_in % 4 == 0) && (((uintptr_t)p.x & 15u) == 0);
+        u.x_vec4 = (ld_in % 4 == 0) && (((uintptr_t)u.x & 15u) == 0);
         bool ov = (ld_out % 4 == 0);
-        for (float *o : {p.ratio, p.bp, p.sp})
+        for (float *o : {u.ratio, u.bp, u.sp})
             if (o && ((uintptr_t)o & 15u)) ov = false;
-        p.o_vec4 = ov;
+        u.o_vec4 = ov;
         cudaError_t e = launch_chain(p, NS, h->det, h->plan.dense, h->n_tiles, stream);
         if (e != cudaSuccess) {
             h->sticky = FILARK_ECUDA;
@@ -221,6 +177,15 @@ filark_status validate_push(filark_chain *h, const void *in, int64_t ld_in, int6
 }
 
 }  // namespace
+
+namespace filark {
+filark_status chain_zero_state(filark_chain *h, cudaStream_t stream) { return zero_state(h, stream); }
+filark_status chain_check_status(filark_chain *h) { return check_device_status(h); }
+filark_status chain_validate_push(filark_chain *h, const void *in, int64_t ld_in, int64_t T, const void *ratio,
+                                  const void *bp, const void *sp, int64_t ld_out) {
+    return validate_push(h, in, ld_in, T, ratio, bp, sp, ld_out);
+}
+}  // namespace filark
 
 extern "C" {
 
@@ -346,29 +311,11 @@ filark_status filark_chain_create(const filark_chain_config *cfg, int cuda_devic
     }
     // kernel parameter template
     ChainParams &b = h->base;
-    std::memset(&b, 0, sizeof(b));
-    b.tab = h->plan.tab;
-    h->plan.slot_power(kL * kNB, b.Phi);
-    h->plan.slot_power(kL, b.ML64);
-    for (int r = 0; r < kMaxCluster; ++r) {
-        h->plan.slot_power(kL * kNB * r, b.PhiPow[r]);
-        for (int s = 0; s < kMaxSlots; ++s)
-            for (int q = 0; q < 4; ++q) b.PhiPow32[r][s][q] = (float)b.PhiPow[r][s][q];
-    }
-    b.ring = h->ring;
-    b.ldr = h->ldr;
-    b.Q = h->Q > 0 ? (int)h->Q : 1;
-    b.C = h->C;
-    b.hw = h->hw;
-    b.HP = h->HP;
-    b.Wout = h->Wout;
-    b.ns = h->ns;
-    b.nl = h->nl;
-    b.ratio_scale = det ? (float)((double)h->nl / (double)h->ns) : 0.f;
-    b.r_vec4 = 1;
-    b.all32 = h->plan.mode == FILARK_PREC_ALL32;
-    b.status = h->status_dev;
-    b.dense = h->dense;
+    set_static_params(h->plan, h->hw, h->HP, h->Wout, h->ns, h->nl, h->dense, b);
+    b.u.ring = h->ring;
+    b.u.ldr = h->ldr;
+    b.u.Q = h->Q > 0 ? (int)h->Q : 1;
+    b.u.C = h->C;
 
     st = zero_state(h, nullptr);
     if (st == FILARK_OK) {

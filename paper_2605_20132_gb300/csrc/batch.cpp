@@ -1,0 +1,476 @@
+// Batched chains (include/filark.h, filark_batch_*): many independent streams
+// that share one chain configuration, pushed together by ONE persistent
+// kernel launch per push.
+//
+// Each stream is an ordinary chain object (its own carried IIR and detector
+// state, history ring, sample counter).  A batched push cuts every stream's
+// chunk into units of at most cluster x 256 samples -- the same per-launch
+// records filark_chain_push_chunk would enqueue one by one -- and lists one
+// work item per (stream, channel tile).  Items are ordered longest chunk first
+// and the clusters of a persistent grid take them from a device counter; a
+// cluster runs an item's units in order, so each unit reads the state the
+// previous one wrote (the tile carries its halo columns' state itself between
+// units, since the neighbouring tiles may not have reached that point).  The unit and item tables travel in one pinned staging buffer (two,
+// alternating) whose upload and the kernel launch are captured once in a CUDA
+// graph per staging buffer; a push fills the tables and replays the graph.
+#include <algorithm>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "chain_object.h"
+
+using namespace filark;
+
+namespace {
+
+constexpr size_t kAlign = 256;
+constexpr int kClusterChoices[] = {1, 2, 4, 8};
+constexpr int kDefaultCluster = 8;   // the single-stream kernel's time split
+constexpr int kMaxTuned = 16;
+
+size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
+
+filark_status bfail(filark_status st, const std::string &msg) {
+    set_last_error(msg);
+    return st;
+}
+
+filark_status bfail_cuda(cudaError_t e, const char *what) {
+    cudaGetLastError();
+    set_last_error(std::string(what) + ": " + cudaGetErrorString(e));
+    return FILARK_ECUDA;
+}
+
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = false;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        ok = cudaSetDevice(dev) == cudaSuccess;
+    }
+    ~DeviceGuard() {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+
+}  // namespace
+
+struct filark_batch {
+    int device = 0;
+    std::vector<filark_chain *> chains;
+    ChainParams base{};          // static kernel parameters shared by the streams
+    int NS = 0;
+    bool det = false, dense = false;
+    int cluster = kDefaultCluster, n_clusters = 0, use_graph = 1;
+    int64_t max_units = 0, max_items = 0, n_tiles = 0;
+    size_t off_items = 0, off_units = 0, desc_bytes = 0;
+    char *d_desc = nullptr;                 // [count | items | units] on the device
+    char *h_stage[2] = {nullptr, nullptr};  // the same, pinned host staging
+    cudaEvent_t staged[2] = {nullptr, nullptr};
+    int next = 0;
+    cudaStream_t cap = nullptr;             // capture stream (graphs are built here)
+    cudaGraphExec_t exec[2] = {nullptr, nullptr};
+    filark_status sticky = FILARK_OK;
+    int64_t device_bytes = 0;
+    int n_tuned = 0;
+    int tune_cluster[kMaxTuned] = {}, tune_clusters[kMaxTuned] = {};
+    double tune_ms[kMaxTuned] = {};
+    std::vector<int> order;
+    std::vector<int> unit0, nunits;
+    std::vector<double *> halo;   // per stream: [2][tiles][kWT][2*NS] tile-private IIR state
+};
+
+namespace {
+
+void destroy_graphs(filark_batch *b) {
+    for (cudaGraphExec_t &g : b->exec)
+        if (g) {
+            cudaGraphExecDestroy(g);
+            g = nullptr;
+        }
+}
+
+void free_batch(filark_batch *b) {
+    if (!b) return;
+    destroy_graphs(b);
+    for (cudaEvent_t &e : b->staged)
+        if (e) cudaEventDestroy(e);
+    if (b->cap) cudaStreamDestroy(b->cap);
+    for (char *p : b->h_stage)
+        if (p) cudaFreeHost(p);
+    if (b->d_desc) cudaFree(b->d_desc);
+    for (double *p : b->halo)
+        if (p) cudaFree(p);
+    for (filark_chain *h : b->chains) filark_chain_destroy(h);
+    delete b;
+}
+
+const BatchItem *dev_items(const filark_batch *b) { return (const BatchItem *)(b->d_desc + b->off_items); }
+const ChainUnit *dev_units(const filark_batch *b) { return (const ChainUnit *)(b->d_desc + b->off_units); }
+int *dev_ctr(const filark_batch *b) { return (int *)b->d_desc; }
+
+cudaError_t enqueue_launch(filark_batch *b, cudaStream_t s) {
+    return launch_chain_batch(b->base, b->NS, b->det, b->dense, b->cluster, b->n_clusters, dev_items(b),
+                              dev_ctr(b), dev_units(b), s);
+}
+
+filark_status build_graphs(filark_batch *b) {
+    destroy_graphs(b);
+    if (!b->use_graph) return FILARK_OK;
+    for (int k = 0; k < 2; ++k) {
+        cudaError_t e = cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) return bfail_cuda(e, "batch: begin capture");
+        cudaError_t e1 = cudaMemcpyAsync(b->d_desc, b->h_stage[k], b->desc_bytes, cudaMemcpyHostToDevice, b->cap);
+        cudaError_t e2 = e1 == cudaSuccess ? enqueue_launch(b, b->cap) : e1;
+        cudaGraph_t g = nullptr;
+        e = cudaStreamEndCapture(b->cap, &g);
+        if (e2 != cudaSuccess || e != cudaSuccess) {
+            if (g) cudaGraphDestroy(g);
+            return bfail_cuda(e2 != cudaSuccess ? e2 : e, "batch: capture of upload + launch");
+        }
+        e = cudaGraphInstantiate(&b->exec[k], g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) {
+            b->exec[k] = nullptr;
+            return bfail_cuda(e, "batch: graph instantiate");
+        }
+    }
+    return FILARK_OK;
+}
+
+filark_status set_launch(filark_batch *b, int cluster, int n_clusters, int use_graph) {
+    if (std::find(std::begin(kClusterChoices), std::end(kClusterChoices), cluster) == std::end(kClusterChoices))
+        return bfail(FILARK_EINVAL, "batch: cluster must be 1, 2, 4 or 8");
+    int n = n_clusters;
+    if (n <= 0) n = batch_max_active_clusters(b->NS, b->det, b->dense, cluster);
+    if (n <= 0) return bfail(FILARK_ENOSYS, "batch: no cluster of this size fits on the device");
+    b->cluster = cluster;
+    b->n_clusters = n;
+    b->use_graph = use_graph ? 1 : 0;
+    return build_graphs(b);
+}
+
+// Fill the staging buffer k for one push; returns the item count.
+int stage_push(filark_batch *b, int k, const filark_chunk_desc *d) {
+    char *base = b->h_stage[k];
+    BatchItem *items = (BatchItem *)(base + b->off_items);
+    ChainUnit *units = (ChainUnit *)(base + b->off_units);
+    const int n = (int)b->chains.size();
+    const int span = kTileRows * b->cluster;
+    int nu = 0;
+    for (int i = 0; i < n; ++i) {
+        filark_chain *h = b->chains[(size_t)i];
+        const filark_chunk_desc &c = d[i];
+        b->unit0[(size_t)i] = nu;
+        b->nunits[(size_t)i] = 0;
+        const size_t hstride = (size_t)h->n_tiles * kWT * (size_t)(2 * b->NS);
+        double *hs = b->halo[(size_t)i];
+        for (int64_t done = 0; done < c.n_samples;) {
+            const int Tl = (int)std::min<int64_t>(c.n_samples - done, span);
+            const int j = b->nunits[(size_t)i];
+            ChainUnit &u = units[nu++];
+            u = h->base.u;   // ring, ldr, Q, C
+            // tile-private state between the units of this push (unit j reads
+            // what unit j-1 wrote; the first reads the per-channel state)
+            u.halo_in = (hs && j > 0) ? hs + (size_t)((j - 1) & 1) * hstride : nullptr;
+            u.halo_out = (hs && done + Tl < c.n_samples) ? hs + (size_t)(j & 1) * hstride : nullptr;
+            u.x = c.d_in + done * c.ld_in;
+            u.ldx = c.ld_in;
+            u.ratio = c.d_ratio ? c.d_ratio + done * c.ld_out : nullptr;
+            u.bp = c.d_bandpass ? c.d_bandpass + done * c.ld_out : nullptr;
+            u.sp = c.d_spatial ? c.d_spatial + done * c.ld_out : nullptr;
+            u.ldo = c.ld_out;
+            u.iir_in = h->iir[h->parity];
+            u.iir_out = h->iir[h->parity ^ 1];
+            u.det_in = h->detst[h->parity];
+            u.det_out = h->detst[h->parity ^ 1];
+            u.n0 = h->n;
+            set_unit_geometry(h->plan, Tl, u);
+            u.slot_n0 = h->Q > 0 ? (int)(h->n % h->Q) : 0;
+            u.x_vec4 = (c.ld_in % 4 == 0) && (((uintptr_t)u.x & 15u) == 0);
+            bool ov = (c.ld_out % 4 == 0);
+            for (float *o : {u.ratio, u.bp, u.sp})
+                if (o && ((uintptr_t)o & 15u)) ov = false;
+            u.o_vec4 = ov;
+            h->parity ^= 1;
+            h->n += Tl;
+            done += Tl;
+            b->nunits[(size_t)i]++;
+        }
+    }
+    // longest chunk first, then stream order
+    std::vector<int> &ord = b->order;
+    ord.resize((size_t)n);
+    for (int i = 0; i < n; ++i) ord[(size_t)i] = i;
+    std::stable_sort(ord.begin(), ord.end(), [&](int a, int c) { return d[a].n_samples > d[c].n_samples; });
+    int ni = 0;
+    for (int i : ord) {
+        if (b->nunits[(size_t)i] == 0) continue;
+        const filark_chain *h = b->chains[(size_t)i];
+        for (int t = 0; t < h->n_tiles; ++t) items[ni++] = BatchItem{b->unit0[(size_t)i], b->nunits[(size_t)i], t, 0};
+    }
+    ((int *)base)[0] = ni;
+    ((int *)base)[1] = 0;   // the kernel's work counter
+    return ni;
+}
+
+filark_status push(filark_batch *b, const filark_chunk_desc *descs, cudaStream_t stream) {
+    if (b->sticky != FILARK_OK) return bfail(FILARK_ESTATE, "batch is in an error state; reset it");
+    const int n = (int)b->chains.size();
+    for (int i = 0; i < n; ++i) {
+        filark_chain *h = b->chains[(size_t)i];
+        filark_status st = chain_check_status(h);
+        if (st != FILARK_OK) return st;
+        const filark_chunk_desc &c = descs[i];
+        st = chain_validate_push(h, c.d_in, c.ld_in, c.n_samples, c.d_ratio, c.d_bandpass, c.d_spatial, c.ld_out);
+        if (st != FILARK_OK) return bfail(st, "stream " + std::to_string(i) + ": " + filark_last_error_string());
+    }
+    const int k = b->next;
+    cudaError_t e = cudaEventSynchronize(b->staged[k]);   // the push before last has uploaded this buffer
+    if (e != cudaSuccess) return bfail_cuda(e, "batch: staging event");
+    const int ni = stage_push(b, k, descs);
+    if (ni == 0) return FILARK_OK;
+    if (b->use_graph) {
+        e = cudaGraphLaunch(b->exec[k], stream);
+    } else {
+        e = cudaMemcpyAsync(b->d_desc, b->h_stage[k], b->desc_bytes, cudaMemcpyHostToDevice, stream);
+        if (e == cudaSuccess) e = enqueue_launch(b, stream);
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(b->staged[k], stream);
+    if (e != cudaSuccess) {
+        b->sticky = FILARK_ECUDA;
+        for (filark_chain *h : b->chains) h->sticky = FILARK_ECUDA;
+        return bfail_cuda(e, "batch: launch");
+    }
+    b->next ^= 1;
+    return FILARK_OK;
+}
+
+filark_status reset(filark_batch *b, cudaStream_t stream) {
+    for (filark_chain *h : b->chains) {
+        filark_status st = chain_zero_state(h, stream);
+        if (st != FILARK_OK) return st;
+    }
+    b->sticky = FILARK_OK;
+    return FILARK_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+filark_status filark_batch_create(const filark_chain_config *cfg, int n_streams, const int32_t *n_channels,
+                                  int cuda_device, filark_batch **out) {
+    if (!out) return bfail(FILARK_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!cfg || !n_channels) return bfail(FILARK_EINVAL, "config or n_channels is NULL");
+    if (n_streams < 1) return bfail(FILARK_EINVAL, "n_streams must be >= 1");
+    filark_batch *b = new (std::nothrow) filark_batch();
+    if (!b) return bfail(FILARK_ENOMEM, "host allocation failed");
+    b->device = cuda_device;
+    for (int i = 0; i < n_streams; ++i) {
+        filark_chain_config c = *cfg;
+        c.n_channels = n_channels[i];
+        filark_chain *h = nullptr;
+        filark_status st = filark_chain_create(&c, cuda_device, &h);
+        if (st != FILARK_OK) {
+            const std::string msg = "stream " + std::to_string(i) + ": " + filark_last_error_string();
+            free_batch(b);
+            return bfail(st, msg);
+        }
+        h->use_pdl = 0;
+        b->chains.push_back(h);
+        b->device_bytes += h->device_bytes;
+        double *hs = nullptr;
+        if (h->plan.NS > 0) {
+            const size_t bytes = sizeof(double) * 2 * (size_t)h->n_tiles * kWT * (size_t)(2 * h->plan.NS);
+            DeviceGuard g(cuda_device);
+            if (cudaMalloc(&hs, bytes) != cudaSuccess) {
+                cudaGetLastError();
+                free_batch(b);
+                return bfail(FILARK_ENOMEM, "batch create: halo state allocation");
+            }
+            b->device_bytes += (int64_t)bytes;
+        }
+        b->halo.push_back(hs);
+        b->max_units += (std::min<int64_t>(cfg->max_chunk, INT32_MAX) + kTileRows - 1) / kTileRows;
+        b->max_items += h->n_tiles;
+    }
+    b->n_tiles = b->max_items;
+    const filark_chain *h0 = b->chains[0];
+    b->base = h0->base;
+    std::memset(&b->base.u, 0, sizeof(b->base.u));
+    b->base.pdl = 0;
+    b->NS = h0->plan.NS;
+    b->det = h0->det;
+    b->dense = h0->plan.dense;
+    b->unit0.assign((size_t)n_streams, 0);
+    b->nunits.assign((size_t)n_streams, 0);
+    b->off_items = kAlign;
+    b->off_units = align_up(b->off_items + sizeof(BatchItem) * (size_t)b->max_items);
+    b->desc_bytes = b->off_units + sizeof(ChainUnit) * (size_t)b->max_units;
+
+    DeviceGuard dg(cuda_device);
+    if (!dg.ok) {
+        free_batch(b);
+        return bfail(FILARK_ECUDA, "cudaSetDevice failed for device " + std::to_string(cuda_device));
+    }
+    cudaError_t e = cudaMalloc(&b->d_desc, b->desc_bytes);
+    for (int k = 0; k < 2 && e == cudaSuccess; ++k) e = cudaHostAlloc(&b->h_stage[k], b->desc_bytes, cudaHostAllocDefault);
+    for (int k = 0; k < 2 && e == cudaSuccess; ++k) e = cudaEventCreateWithFlags(&b->staged[k], cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+        free_batch(b);
+        return bfail_cuda(e, "batch create: allocation");
+    }
+    b->device_bytes += (int64_t)b->desc_bytes;
+    for (int k = 0; k < 2; ++k) std::memset(b->h_stage[k], 0, b->desc_bytes);
+    filark_status st = set_launch(b, kDefaultCluster, 0, 1);
+    if (st != FILARK_OK) {
+        const std::string msg = filark_last_error_string();
+        free_batch(b);
+        return bfail(st, msg);
+    }
+    *out = b;
+    return FILARK_OK;
+}
+
+filark_status filark_batch_push(filark_batch *b, const filark_chunk_desc *descs, filark_stream_t stream) {
+    if (!b) return bfail(FILARK_EINVAL, "batch is NULL");
+    if (!descs) return bfail(FILARK_EINVAL, "descs is NULL");
+    DeviceGuard dg(b->device);
+    if (!dg.ok) return bfail(FILARK_ECUDA, "cudaSetDevice failed");
+    return push(b, descs, (cudaStream_t)stream);
+}
+
+filark_status filark_batch_set_launch(filark_batch *b, int cluster, int n_clusters, int use_graph) {
+    if (!b) return bfail(FILARK_EINVAL, "batch is NULL");
+    DeviceGuard dg(b->device);
+    if (!dg.ok) return bfail(FILARK_ECUDA, "cudaSetDevice failed");
+    // the staging buffers may still be read by an earlier upload
+    for (cudaEvent_t ev : b->staged) {
+        cudaError_t e = cudaEventSynchronize(ev);
+        if (e != cudaSuccess) return bfail_cuda(e, "batch: staging event");
+    }
+    return set_launch(b, cluster, n_clusters, use_graph);
+}
+
+filark_status filark_batch_tune(filark_batch *b, const filark_chunk_desc *descs, int timed_pushes,
+                                filark_stream_t stream) {
+    if (!b || !descs) return bfail(FILARK_EINVAL, "batch or descs is NULL");
+    if (timed_pushes < 1) return bfail(FILARK_EINVAL, "timed_pushes must be >= 1");
+    DeviceGuard dg(b->device);
+    if (!dg.ok) return bfail(FILARK_ECUDA, "cudaSetDevice failed");
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaEvent_t t0 = nullptr, t1 = nullptr;
+    cudaError_t e = cudaEventCreate(&t0);
+    if (e == cudaSuccess) e = cudaEventCreate(&t1);
+    if (e != cudaSuccess) {
+        if (t0) cudaEventDestroy(t0);
+        return bfail_cuda(e, "tune: events");
+    }
+    filark_status st = FILARK_OK;
+    double best = 1e300;
+    int best_cluster = b->cluster, best_n = b->n_clusters;
+    b->n_tuned = 0;
+    for (int cl : kClusterChoices) {
+        const int occ = batch_max_active_clusters(b->NS, b->det, b->dense, cl);
+        if (occ <= 0) continue;
+        for (int mult : {1, 2}) {
+            if (b->n_tuned >= kMaxTuned) break;
+            for (cudaEvent_t ev : b->staged) cudaEventSynchronize(ev);
+            st = set_launch(b, cl, occ * mult, 1);
+            if (st == FILARK_OK) st = reset(b, s);
+            for (int w = 0; w < 2 && st == FILARK_OK; ++w) st = push(b, descs, s);
+            if (st == FILARK_OK && (e = cudaEventRecord(t0, s)) != cudaSuccess) st = bfail_cuda(e, "tune: record");
+            for (int r = 0; r < timed_pushes && st == FILARK_OK; ++r) st = push(b, descs, s);
+            if (st == FILARK_OK && (e = cudaEventRecord(t1, s)) != cudaSuccess) st = bfail_cuda(e, "tune: record");
+            if (st == FILARK_OK && (e = cudaEventSynchronize(t1)) != cudaSuccess) st = bfail_cuda(e, "tune: sync");
+            float ms = 0.f;
+            if (st == FILARK_OK && (e = cudaEventElapsedTime(&ms, t0, t1)) != cudaSuccess)
+                st = bfail_cuda(e, "tune: elapsed");
+            if (st != FILARK_OK) break;
+            const double per = (double)ms / timed_pushes;
+            b->tune_cluster[b->n_tuned] = cl;
+            b->tune_clusters[b->n_tuned] = occ * mult;
+            b->tune_ms[b->n_tuned] = per;
+            b->n_tuned++;
+            if (per < best) {
+                best = per;
+                best_cluster = cl;
+                best_n = occ * mult;
+            }
+        }
+        if (st != FILARK_OK) break;
+    }
+    cudaEventDestroy(t0);
+    cudaEventDestroy(t1);
+    if (st != FILARK_OK) return st;
+    for (cudaEvent_t ev : b->staged) cudaEventSynchronize(ev);
+    st = set_launch(b, best_cluster, best_n, 1);
+    if (st == FILARK_OK) st = reset(b, s);
+    if (st == FILARK_OK && (e = cudaStreamSynchronize(s)) != cudaSuccess) st = bfail_cuda(e, "tune: sync");
+    return st;
+}
+
+filark_status filark_batch_reset_state(filark_batch *b, filark_stream_t stream) {
+    if (!b) return bfail(FILARK_EINVAL, "batch is NULL");
+    DeviceGuard dg(b->device);
+    if (!dg.ok) return bfail(FILARK_ECUDA, "cudaSetDevice failed");
+    return reset(b, (cudaStream_t)stream);
+}
+
+filark_status filark_batch_sync_status(filark_batch *b, filark_stream_t stream) {
+    if (!b) return bfail(FILARK_EINVAL, "batch is NULL");
+    DeviceGuard dg(b->device);
+    if (!dg.ok) return bfail(FILARK_ECUDA, "cudaSetDevice failed");
+    cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+    if (e != cudaSuccess) {
+        b->sticky = FILARK_ECUDA;
+        return bfail_cuda(e, "batch: synchronize");
+    }
+    if (b->sticky != FILARK_OK) return bfail(FILARK_ESTATE, "batch is in an error state; reset it");
+    for (filark_chain *h : b->chains) {
+        filark_status st = chain_check_status(h);
+        if (st != FILARK_OK) return st;
+    }
+    return FILARK_OK;
+}
+
+filark_status filark_batch_get_info(const filark_batch *b, filark_batch_info *out) {
+    if (!b || !out) return bfail(FILARK_EINVAL, "batch or out is NULL");
+    std::memset(out, 0, sizeof(*out));
+    out->n_streams = (int32_t)b->chains.size();
+    out->cluster = b->cluster;
+    out->n_clusters = b->n_clusters;
+    out->use_graph = b->use_graph;
+    out->n_tiles = b->n_tiles;
+    out->device_bytes = b->device_bytes;
+    out->n_tuned = b->n_tuned;
+    for (int i = 0; i < b->n_tuned; ++i) {
+        out->tune_cluster[i] = b->tune_cluster[i];
+        out->tune_clusters[i] = b->tune_clusters[i];
+        out->tune_ms[i] = b->tune_ms[i];
+    }
+    return FILARK_OK;
+}
+
+filark_status filark_batch_stream(filark_batch *b, int i, filark_chain **out) {
+    if (!b || !out) return bfail(FILARK_EINVAL, "batch or out is NULL");
+    if (i < 0 || i >= (int)b->chains.size()) return bfail(FILARK_EINVAL, "stream index out of range");
+    *out = b->chains[(size_t)i];
+    return FILARK_OK;
+}
+
+filark_status filark_batch_destroy(filark_batch *b) {
+    if (!b) return FILARK_OK;
+    DeviceGuard dg(b->device);
+    for (cudaEvent_t ev : b->staged)
+        if (ev) cudaEventSynchronize(ev);
+    free_batch(b);
+    return FILARK_OK;
+}
+
+}  // extern "C"

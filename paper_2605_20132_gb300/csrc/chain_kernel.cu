@@ -1,826 +1,16 @@
-// Fused chunked DAS chain kernel for sm_103a: causal SOS bandpass (block
-// state-space form, see plan.cpp), spatial running mean, STA/LTA detector.
-//
-// Work decomposition of one launch (<= 2048 samples of every channel):
-//   grid.x  = channel tiles; a tile is kWT = 64 consecutive channels of which
-//             Wout are outputs and HP on each side are halo (the spatial mean
-//             of an output channel needs its neighbours' bandpass output, so
-//             the halo channels' IIR is computed again by the neighbour tile --
-//             the overlap-aware halo expansion of Sec. 3.4);
-//   grid.y  = R time ranges of kNB blocks x kL samples; the R CTAs of a tile
-//             form one thread-block cluster and exchange their IIR carries and
-//             detector sums through distributed shared memory.
-//
-// Per CTA (512 threads):
-//   0. load the input tile [256 samples][64 channels] into shared memory;
-//   1. per (channel, block): local FIR response y_loc = T_L x and the block's
-//      end state e = K x from zero state (FP32, tables are FFMA constant
-//      operands);
-//   2. per (channel, slot): carry scan m_{j+1} = M m_j + e_j -- FP32 inside the
-//      CTA, FP64 across the CTAs of the cluster and across launches;
-//   3. fix-up y_bp = y_loc + G m_j, written back in place;
-//   4. spatial mean over the 2h+1 neighbouring columns, cf = y_sp^2, written to
-//      the detector's history ring and kept in place;
-//   5. STA/LTA: exact (compensated) block sums, FP64 scan across blocks and
-//      CTAs, then FP32 running sums inside each block and the ratio.
-//
-// Consecutive launches on a stream overlap through programmatic dependent
-// launch: phases 0-1 only read the caller's input, so a launch starts them
-// while the previous one drains, and waits for it before touching the state.
-#include <climits>
-#include <type_traits>
-
-#include <cooperative_groups.h>
-
-#include "filark_internal.h"
-
-namespace cg = cooperative_groups;
+// Single-stream launch of the fused chain kernel (device code in
+// chain_body.cuh): one launch per <= 2048 samples of a push, grid.x =
+// channel tiles, grid.y = the cluster of time ranges.
+#include "chain_body.cuh"
 
 namespace filark {
 
 namespace {
 
-__device__ __forceinline__ void cluster_sync_release_acquire() {
-    asm volatile("barrier.cluster.arrive.release.aligned;\n" ::: "memory");
-    asm volatile("barrier.cluster.wait.acquire.aligned;\n" ::: "memory");
-}
-
-__device__ __forceinline__ void pdl_launch_dependents() {
-    asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
-}
-
-__device__ __forceinline__ void pdl_wait() {
-    asm volatile("griddepcontrol.wait;\n" ::: "memory");
-}
-
-// s + v for s, v >= 0 with the rounding error kept in c (Fast2Sum on the larger
-// operand), so a block sum of non-negative values is carried as s + c with an
-// error of order eps^2 instead of eps.
-__device__ __forceinline__ void acc_nonneg(float &s, float &c, float v) {
-    const float t = s + v;
-    const float big = fmaxf(s, v), small = fminf(s, v);
-    c += small - (t - big);
-    s = t;
-}
-
-// Double-float (hi + lo) arithmetic for the detector's carried sums: exact
-// error-free additions (Knuth's TwoSum) keep ~48 significant bits without
-// the FP64 pipe.
-struct DF {
-    float hi, lo;
-};
-__device__ __forceinline__ DF df_add(DF a, DF b) {
-    const float s = a.hi + b.hi;
-    const float bb = s - a.hi;
-    const float err = (a.hi - (s - bb)) + (b.hi - bb);
-    const float lo = err + (a.lo + b.lo);
-    const float hi = s + lo;
-    return DF{hi, lo - (hi - s)};
-}
-__device__ __forceinline__ DF df_neg(DF a) { return DF{-a.hi, -a.lo}; }
-// a + c for a, c >= 0 held as compensated sums (s, comp): exact as DF
-__device__ __forceinline__ DF df_from_sum(float s, float comp) {
-    const float hi = s + comp;
-    return DF{hi, comp - (hi - s)};
-}
-
-// shared memory carve-up (floats)
-constexpr int kTileFloats = kTileRows * kWT;                 // 16384
-constexpr int kEFloats = kNB * 2 * kMaxSlots * kWT;          // 8192
-constexpr int kERFloats = 2 * kMaxSlots * kWT;               // 1024
-constexpr int kAggFloats = 2 * kMaxSlots * kWT;              // 1024 (also holds 3 x 64 doubles)
-constexpr int kSmemFloats = kTileFloats + kEFloats + kERFloats + kAggFloats;
-// the dense carry needs an FP64 aggregate [16][kWT] (in place of AGG) and a
-// double-buffered FP64 state [2][16][kWT] after it
-constexpr int kAggDenseFloats = kDenseDim * kWT * 2;          // 2048
-constexpr int kMVFloats = 2 * kDenseDim * kWT * 2;            // 4096
-constexpr int kSmemFloatsDense = kTileFloats + kEFloats + kERFloats + kAggDenseFloats + kMVFloats;
-
-// detector overlays on the E region (free after the IIR fix-up); offsets in floats
-constexpr int kDetDS = 0;                                    // DF [kNB][kWT]
-constexpr int kDetDL = kDetDS + kNB * kWT * 2;               // DF [kNB][kWT]
-constexpr int kDetBS = kDetDL + kNB * kWT * 2;               // DF [kNB][kWT]
-constexpr int kDetBL = kDetBS + kNB * kWT * 2;               // DF [kNB][kWT]
-constexpr int kDetLZ = kDetBL + kNB * kWT * 2;               // int [kNB][kWT] last nonzero row
-constexpr int kDetBZ = kDetLZ + kNB * kWT;                   // int [kNB][kWT] its running max
-static_assert(kDetBZ + kNB * kWT <= kEFloats, "detector overlays must fit in the E region");
-
-constexpr int kNoNonzero = INT_MIN / 2;   // "no nonzero cf" as a relative row index
-constexpr int kRowStep = kThreads / 16;   // rows covered by one pass of the spatial phase
-constexpr int kRowIters = kTileRows / kRowStep;
-
-
-// Stores of one 4-channel group of a row: the spatial tap and, with the
-// detector, cf = y_sp^2 into the history ring.
-template <bool DET>
-__device__ __forceinline__ void store_group(const ChainParams &p, int row, int row0, int cch, int slot_r0,
-                                            bool full_group, const float (&ysp)[4], float (&cf)[4]) {
-    if (p.sp) {
-        float *dst = p.sp + (long long)(row0 + row) * p.ldo + cch;
-        if (p.o_vec4 && full_group) {
-            *reinterpret_cast<float4 *>(dst) = make_float4(ysp[0], ysp[1], ysp[2], ysp[3]);
-        } else {
-#pragma unroll
-            for (int u = 0; u < 4; ++u)
-                if (cch + u < p.C) dst[u] = ysp[u];
-        }
-    }
-    if (DET) {
-#pragma unroll
-        for (int u = 0; u < 4; ++u) cf[u] = ysp[u] * ysp[u];
-        int slot = slot_r0 + row;
-        if (slot >= p.Q) slot -= p.Q;
-        float *dst = p.ring + (long long)slot * p.ldr + cch;
-        if (full_group) {
-            *reinterpret_cast<float4 *>(dst) = make_float4(cf[0], cf[1], cf[2], cf[3]);
-        } else {
-#pragma unroll
-            for (int u = 0; u < 4; ++u)
-                if (cch + u < p.C) dst[u] = cf[u];
-        }
-    }
-}
-
-// With the detector on, cf replaces y_bp in the tile once every thread has
-// read its windows (rows past the end get cf = 0).  Called by all threads.
-template <bool DET>
-__device__ __forceinline__ void store_cf_in_place(float *tile, int ro, int rows, int q0, bool gact,
-                                                  const float (&cfv)[kRowIters][4]) {
-    if (!DET) return;
-    __syncthreads();
-    if (gact) {
-#pragma unroll
-        for (int it = 0; it < kRowIters; ++it) {
-            const int row = ro + kRowStep * it;
-            *reinterpret_cast<float4 *>(&tile[row * kWT + q0]) = row < rows
-                ? make_float4(cfv[it][0], cfv[it][1], cfv[it][2], cfv[it][3])
-                : make_float4(0.f, 0.f, 0.f, 0.f);
-        }
-    }
-}
-
-// Spatial mean of 4 output columns q0..q0+3 for the rows ro, ro+32, ... of the
-// tile, window half-width HW <= 4 known at compile time (halo HP = 4, or 0 when
-// HW = 0): the 12 (or 4) columns around the group come in with aligned float4
-// loads, which are free of bank conflicts.
-template <int HW, bool DET>
-__device__ __forceinline__ void spatial_rows(const ChainParams &p, float *tile, int ro, int rows, int q0,
-                                             int row0, int cch, int slot_r0, bool full_group, bool gact,
-                                             const float (&inv)[4]) {
-    constexpr int H = HW == 0 ? 0 : 4;              // halo columns loaded on each side
-    float cfv[kRowIters][4];
-#pragma unroll
-    for (int it = 0; it < kRowIters; ++it) {
-        const int row = ro + kRowStep * it;
-        cfv[it][0] = cfv[it][1] = cfv[it][2] = cfv[it][3] = 0.f;
-        if (gact && row < rows) {
-            float v[4 + 2 * H];
-            const float4 *tr = reinterpret_cast<const float4 *>(tile + row * kWT + q0 - H);
-#pragma unroll
-            for (int f = 0; f < (4 + 2 * H) / 4; ++f) {
-                const float4 t = tr[f];
-                v[4 * f + 0] = t.x;
-                v[4 * f + 1] = t.y;
-                v[4 * f + 2] = t.z;
-                v[4 * f + 3] = t.w;
-            }
-            float sacc = 0.f;
-#pragma unroll
-            for (int q = H - HW; q <= H + HW; ++q) sacc += v[q];
-            float ysp[4];
-            ysp[0] = sacc * inv[0];
-#pragma unroll
-            for (int u = 1; u < 4; ++u) {
-                sacc += v[H + u + HW] - v[H + u - 1 - HW];
-                ysp[u] = sacc * inv[u];
-            }
-            store_group<DET>(p, row, row0, cch, slot_r0, full_group, ysp, cfv[it]);
-        }
-    }
-    store_cf_in_place<DET>(tile, ro, rows, q0, gact, cfv);
-}
-
-// Same for any halo width (hw runtime, columns read one by one).
-template <bool DET>
-__device__ __forceinline__ void spatial_rows_generic(const ChainParams &p, float *tile, int ro, int rows,
-                                                  int q0, int row0, int cch, int slot_r0, bool full_group,
-                                                  bool gact, const float (&inv)[4]) {
-    float cfv[kRowIters][4];
-#pragma unroll
-    for (int it = 0; it < kRowIters; ++it) {
-        const int row = ro + kRowStep * it;
-        cfv[it][0] = cfv[it][1] = cfv[it][2] = cfv[it][3] = 0.f;
-        if (gact && row < rows) {
-            const float *tr = tile + row * kWT;
-            float sacc = 0.f;
-            for (int q = q0 - p.hw; q <= q0 + p.hw; ++q) sacc += tr[q];
-            float ysp[4];
-            ysp[0] = sacc * inv[0];
-            for (int u = 1; u < 4; ++u) {
-                sacc += tr[q0 + u + p.hw] - tr[q0 + u - 1 - p.hw];
-                ysp[u] = sacc * inv[u];
-            }
-            store_group<DET>(p, row, row0, cch, slot_r0, full_group, ysp, cfv[it]);
-        }
-    }
-    store_cf_in_place<DET>(tile, ro, rows, q0, gact, cfv);
-}
-
-// One step of the dense carry for the column c and the rows r0, r0+1 this
-// thread owns: out = Mx * MV[cur] + add, written to MV[cur ^ 1].  All threads
-// of the block call it (it ends with a barrier).
-// rows of the dense state owned by one thread
-template <int NS>
-__host__ __device__ constexpr int dense_rows_per_thread() {
-    return (2 * NS + kThreads / kWT - 1) / (kThreads / kWT);
-}
-
-template <int NS>
-__device__ __forceinline__ void dense_step(double *MV, int &cur, const double *Mx, int c, int r0,
-                                           const double (&add)[dense_rows_per_thread<NS>()], bool all32) {
-    constexpr int n = 2 * NS;
-    constexpr int RT = dense_rows_per_thread<NS>();
-    if (r0 < n) {
-        const double *v = MV + (size_t)cur * kDenseDim * kWT;
-        double a[RT];
-#pragma unroll
-        for (int t = 0; t < RT; ++t) a[t] = add[t];
-#pragma unroll
-        for (int q = 0; q < n; ++q) {
-            const double vq = v[q * kWT + c];
-#pragma unroll
-            for (int t = 0; t < RT; ++t)
-                if (r0 + t < n) a[t] = fma(__ldg(Mx + (size_t)(r0 + t) * kDenseDim + q), vq, a[t]);
-        }
-        double *o = MV + (size_t)(cur ^ 1) * kDenseDim * kWT;
-#pragma unroll
-        for (int t = 0; t < RT; ++t)
-            if (r0 + t < n) o[(r0 + t) * kWT + c] = all32 ? (double)(float)a[t] : a[t];
-    }
-    cur ^= 1;
-    __syncthreads();
-}
-
 template <int NS, bool DET, bool DENSE>
 __global__ void __launch_bounds__(kThreads, kCTAsPerSM) chain_fwd_kernel(const __grid_constant__ ChainParams p) {
-    extern __shared__ __align__(16) float smem[];
-    float *tile = smem;                       // [kTileRows][kWT]
-    float *E = tile + kTileFloats;            // [kNB][2*NS][kWT]
-    float *ER = E + kEFloats;                 // [2*NS][kWT]
-    float *AGG = ER + kERFloats;              // [2*NS][kWT]; later 3 x kWT doubles
-
     if (p.pdl) pdl_launch_dependents();
-
-    cg::cluster_group cluster = cg::this_cluster();
-    const int tid = threadIdx.x;
-    const int r = blockIdx.y;                 // time range within the launch = cluster rank
-    const int R = p.R;
-    const int c0 = blockIdx.x * p.Wout;       // first output channel of the tile
-    const int cbase = c0 - p.HP;              // channel of tile column 0
-    const int blk0 = r * kNB;
-    const int nb = min(kNB, p.nblk - blk0);   // blocks in this CTA (>= 1)
-    const int row0 = blk0 * kL;               // first launch row of this CTA
-    const int rows = min(nb * kL, p.T - row0);
-    const bool last_cta = (r == R - 1);
-
-    // ---------------------------------------------------------------- 0. load
-    {
-        const float *xb = p.x + (long long)row0 * p.ldx;
-        if (p.x_vec4) {
-#pragma unroll
-            for (int it = 0; it < kTileFloats / 4 / kThreads; ++it) {
-                const int f = tid + it * kThreads;
-                const int row = f >> 4, col = (f & 15) << 2;
-                const int cgl = cbase + col;
-                float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-                if (row < rows) {
-                    const float *src = xb + (long long)row * p.ldx + cgl;
-                    if (cgl >= 0 && cgl + 3 < p.C) {
-                        v = __ldg(reinterpret_cast<const float4 *>(src));
-                    } else {
-                        if (cgl + 0 >= 0 && cgl + 0 < p.C) v.x = __ldg(src + 0);
-                        if (cgl + 1 >= 0 && cgl + 1 < p.C) v.y = __ldg(src + 1);
-                        if (cgl + 2 >= 0 && cgl + 2 < p.C) v.z = __ldg(src + 2);
-                        if (cgl + 3 >= 0 && cgl + 3 < p.C) v.w = __ldg(src + 3);
-                    }
-                }
-                *reinterpret_cast<float4 *>(&tile[row * kWT + col]) = v;
-            }
-        } else {
-            for (int f = tid; f < kTileFloats; f += kThreads) {
-                const int row = f / kWT, col = f % kWT;
-                const int cgl = cbase + col;
-                float v = 0.f;
-                if (row < rows && cgl >= 0 && cgl < p.C) v = __ldg(xb + (long long)row * p.ldx + cgl);
-                tile[f] = v;
-            }
-        }
-    }
-    __syncthreads();
-
-    // (channel, block) mapping: warps 2j, 2j+1 cover block j, columns 0-31 / 32-63
-    const int warp = tid >> 5, lane = tid & 31;
-    const int jb = warp >> 1;
-    const int col = ((warp & 1) << 5) | lane;
-    const int cgc = cbase + col;
-    const bool col_owned = col >= p.HP && col < p.HP + p.Wout && cgc < p.C;
-
-    // ------------------------------------------------ 1. local responses
-    if constexpr (NS > 0) {
-        if (jb < nb) {
-            const float *xc = tile + (jb * kL) * kWT + col;
-            if (blk0 + jb == p.nblk - 1 && p.Lr < kL) {
-                // ragged last block: its end state after Lr samples is K applied
-                // to the input right-aligned in the block
-                const int off = kL - p.Lr;
-                float e[2 * NS];
-#pragma unroll
-                for (int q = 0; q < 2 * NS; ++q) e[q] = 0.f;
-#pragma unroll
-                for (int i = 0; i < kL; ++i) {
-                    const float xi = (i >= off) ? xc[(i - off) * kWT] : 0.f;
-#pragma unroll
-                    for (int q = 0; q < 2 * NS; ++q) e[q] = fmaf(p.tab.K[i][q], xi, e[q]);
-                }
-#pragma unroll
-                for (int q = 0; q < 2 * NS; ++q) ER[q * kWT + col] = e[q];
-            }
-            float y[kL];
-            float e[2 * NS];
-#pragma unroll
-            for (int k = 0; k < kL; ++k) y[k] = 0.f;
-#pragma unroll
-            for (int q = 0; q < 2 * NS; ++q) e[q] = 0.f;
-#pragma unroll
-            for (int i = 0; i < kL; ++i) {
-                const float xi = xc[i * kWT];
-#pragma unroll
-                for (int k = i; k < kL; ++k) y[k] = fmaf(p.tab.h[k - i], xi, y[k]);
-#pragma unroll
-                for (int q = 0; q < 2 * NS; ++q) e[q] = fmaf(p.tab.K[i][q], xi, e[q]);
-            }
-#pragma unroll
-            for (int q = 0; q < 2 * NS; ++q) E[(jb * 2 * NS + q) * kWT + col] = e[q];
-            // the block's input is no longer needed: park y_loc in its place
-            float *xw = tile + (jb * kL) * kWT + col;
-#pragma unroll
-            for (int k = 0; k < kL; ++k) xw[k * kWT] = y[k];
-        }
-    }
-
-    // everything below reads state that the previous launch writes
-    if (p.pdl) pdl_wait();
-    __syncthreads();
-
-    if constexpr (NS > 0) {
-        // ------------------------------------------------ 2. carry scan
-        if constexpr (DENSE) {
-            // canonical basis, FP64 carry at every block; thread (c, rp) owns
-            // state rows rp*RT .. rp*RT+RT-1 of column c
-            constexpr int n = 2 * NS;
-            constexpr int RT = dense_rows_per_thread<NS>();
-            double *AGGD = reinterpret_cast<double *>(AGG);                        // [16][kWT]
-            double *MV = AGGD + kDenseDim * kWT;                                   // [2][16][kWT]
-            const int c = tid % kWT, rp = tid / kWT, r0 = rp * RT;
-            const int cgs = cbase + c;
-            const bool ragged_last = last_cta && p.Lr < kL;
-            const double *AL = p.dense + (size_t)(kL - 1) * kDenseDim * kDenseDim;
-            const double *Ar = p.dense + (size_t)(p.Lr - 1) * kDenseDim * kDenseDim;
-            const double *Phi = p.dense + (size_t)(kL + 1) * kDenseDim * kDenseDim;
-            const double *PhiR = p.dense + (size_t)(kL + r) * kDenseDim * kDenseDim;
-            int cur = 0;
-            double add[RT];
-            auto set_rows = [&](const double (&v)[RT]) {
-#pragma unroll
-                for (int t = 0; t < RT; ++t)
-                    if (r0 + t < n) MV[(size_t)cur * kDenseDim * kWT + (r0 + t) * kWT + c] = v[t];
-            };
-            auto get_rows = [&](double (&v)[RT]) {
-#pragma unroll
-                for (int t = 0; t < RT; ++t)
-                    v[t] = r0 + t < n ? MV[(size_t)cur * kDenseDim * kWT + (r0 + t) * kWT + c] : 0.0;
-            };
-#pragma unroll
-            for (int t = 0; t < RT; ++t) add[t] = 0.0;
-            // (a) aggregate of this CTA from a zero start (not needed by the last)
-            set_rows(add);
-            __syncthreads();
-            if (!last_cta) {
-                for (int j = 0; j < nb; ++j) {
-#pragma unroll
-                    for (int t = 0; t < RT; ++t)
-                        add[t] = r0 + t < n ? (double)E[(j * 2 * NS + r0 + t) * kWT + c] : 0.0;
-                    dense_step<NS>(MV, cur, AL, c, r0, add, p.all32);
-                }
-                get_rows(add);
-#pragma unroll
-                for (int t = 0; t < RT; ++t)
-                    if (r0 + t < n) AGGD[(r0 + t) * kWT + c] = add[t];
-            }
-            cluster_sync_release_acquire();
-            // (b) g = sum over earlier CTAs q of Phi^(r-1-q) agg_q
-#pragma unroll
-            for (int t = 0; t < RT; ++t) add[t] = 0.0;
-            set_rows(add);
-            __syncthreads();
-            for (int q = 0; q < r; ++q) {
-                const double *ragg = cluster.map_shared_rank(AGGD, q);
-#pragma unroll
-                for (int t = 0; t < RT; ++t) add[t] = r0 + t < n ? ragg[(r0 + t) * kWT + c] : 0.0;
-                dense_step<NS>(MV, cur, Phi, c, r0, add, p.all32);
-            }
-            double g[RT];
-            get_rows(g);
-            __syncthreads();
-            // (c) state at this CTA's start: Phi^r s_launch + g
-            {
-                double sv[RT];
-#pragma unroll
-                for (int t = 0; t < RT; ++t)
-                    sv[t] = (r0 + t < n && cgs >= 0 && cgs < p.C) ? p.iir_in[(long long)cgs * (2 * NS) + r0 + t] : 0.0;
-                set_rows(sv);
-                __syncthreads();
-                dense_step<NS>(MV, cur, PhiR, c, r0, g, p.all32);
-            }
-            // (d) block start states (FP32 into E) and, in the last CTA, the end state
-            for (int j = 0; j < nb; ++j) {
-                const bool rag = ragged_last && j == nb - 1;
-#pragma unroll
-                for (int t = 0; t < RT; ++t) {
-                    add[t] = 0.0;
-                    if (r0 + t < n) {
-                        float *pe = &E[(j * 2 * NS + r0 + t) * kWT + c];
-                        add[t] = rag ? (double)ER[(r0 + t) * kWT + c] : (double)*pe;
-                        *pe = (float)MV[(size_t)cur * kDenseDim * kWT + (r0 + t) * kWT + c];
-                    }
-                }
-                if (last_cta || j < nb - 1) dense_step<NS>(MV, cur, rag ? Ar : AL, c, r0, add, p.all32);
-            }
-            if (last_cta && c >= p.HP && c < p.HP + p.Wout && cgs < p.C) {
-#pragma unroll
-                for (int t = 0; t < RT; ++t)
-                    if (r0 + t < n)
-                        p.iir_out[(long long)cgs * (2 * NS) + r0 + t] =
-                            MV[(size_t)cur * kDenseDim * kWT + (r0 + t) * kWT + c];
-            }
-        } else {
-        const int sc = tid % kWT;
-        constexpr int kSlotStep = kThreads / kWT;            // slots handled per pass
-        const bool ragged_last = last_cta && p.Lr < kL;
-        // this CTA's aggregate per slot: end state of its range from a zero
-        // start (FP32)
-        for (int s = tid / kWT; s < NS; s += kSlotStep) {
-            float a0 = 0.f, a1 = 0.f;
-            for (int j = 0; j < nb; ++j) {
-                float e0, e1, m00, m01, m10, m11;
-                if (ragged_last && j == nb - 1) {
-                    e0 = ER[(2 * s) * kWT + sc];
-                    e1 = ER[(2 * s + 1) * kWT + sc];
-                    m00 = p.Mr32[s][0]; m01 = p.Mr32[s][1]; m10 = p.Mr32[s][2]; m11 = p.Mr32[s][3];
-                } else {
-                    e0 = E[(j * 2 * NS + 2 * s) * kWT + sc];
-                    e1 = E[(j * 2 * NS + 2 * s + 1) * kWT + sc];
-                    m00 = p.tab.M[s][0]; m01 = p.tab.M[s][1]; m10 = p.tab.M[s][2]; m11 = p.tab.M[s][3];
-                }
-                const float t0 = fmaf(m00, a0, fmaf(m01, a1, e0));
-                const float t1 = fmaf(m10, a0, fmaf(m11, a1, e1));
-                a0 = t0;
-                a1 = t1;
-            }
-            AGG[(2 * s) * kWT + sc] = a0;
-            AGG[(2 * s + 1) * kWT + sc] = a1;
-        }
-        cluster_sync_release_acquire();
-        for (int s = tid / kWT; s < NS; s += kSlotStep) {
-            const int cgs = cbase + sc;
-            // earlier CTAs of the cluster: g = sum_q Phi^(r-1-q) agg_q, each
-            // term from its own power (independent loads, FP32)
-            float g0 = 0.f, g1 = 0.f;
-            for (int q = 0; q < r; ++q) {
-                const float *ragg = cluster.map_shared_rank(AGG, q);
-                const float a0 = ragg[(2 * s) * kWT + sc], a1 = ragg[(2 * s + 1) * kWT + sc];
-                const float *Pq = p.PhiPow32[r - 1 - q][s];
-                g0 = fmaf(Pq[0], a0, fmaf(Pq[1], a1, g0));
-                g1 = fmaf(Pq[2], a0, fmaf(Pq[3], a1, g1));
-            }
-            // carried state of the launch (FP64), advanced to this CTA's start
-            double c0d = 0.0, c1d = 0.0;
-            if (cgs >= 0 && cgs < p.C) {
-                c0d = p.iir_in[(long long)cgs * (2 * NS) + 2 * s];
-                c1d = p.iir_in[(long long)cgs * (2 * NS) + 2 * s + 1];
-            }
-            const double *Pr = p.PhiPow[r][s];
-            double d0 = fma(Pr[0], c0d, fma(Pr[1], c1d, (double)g0));
-            double d1 = fma(Pr[2], c0d, fma(Pr[3], c1d, (double)g1));
-            if (p.all32) {
-                d0 = (float)d0;
-                d1 = (float)d1;
-            }
-            if (last_cta && sc >= p.HP && sc < p.HP + p.Wout && cgs < p.C) {
-                // launch end state: PhiTot c + PhiLast g + own aggregate (FP64)
-                const double a0 = AGG[(2 * s) * kWT + sc], a1 = AGG[(2 * s + 1) * kWT + sc];
-                const double *PT = p.PhiTot[s], *PL = p.PhiLast[s];
-                double u0 = fma(PT[0], c0d, fma(PT[1], c1d, fma(PL[0], (double)g0, fma(PL[1], (double)g1, a0))));
-                double u1 = fma(PT[2], c0d, fma(PT[3], c1d, fma(PL[2], (double)g0, fma(PL[3], (double)g1, a1))));
-                if (p.all32) {
-                    u0 = (float)u0;
-                    u1 = (float)u1;
-                }
-                p.iir_out[(long long)cgs * (2 * NS) + 2 * s] = u0;
-                p.iir_out[(long long)cgs * (2 * NS) + 2 * s + 1] = u1;
-            }
-            // block start states (FP32), written over the block end states
-            const float m00 = p.tab.M[s][0], m01 = p.tab.M[s][1], m10 = p.tab.M[s][2], m11 = p.tab.M[s][3];
-            float f0 = (float)d0, f1 = (float)d1;
-            for (int j = 0; j < nb; ++j) {
-                float *pe0 = &E[(j * 2 * NS + 2 * s) * kWT + sc];
-                float *pe1 = pe0 + kWT;
-                const float e0 = *pe0, e1 = *pe1;
-                *pe0 = f0;
-                *pe1 = f1;
-                const float t0 = fmaf(m00, f0, fmaf(m01, f1, e0));
-                const float t1 = fmaf(m10, f0, fmaf(m11, f1, e1));
-                f0 = t0;
-                f1 = t1;
-            }
-        }
-        }
-        __syncthreads();
-
-        // ------------------------------------------------ 3. fix-up
-        if (jb < nb) {
-            float m[2 * NS];
-#pragma unroll
-            for (int q = 0; q < 2 * NS; ++q) m[q] = E[(jb * 2 * NS + q) * kWT + col];
-            float *tc = tile + (jb * kL) * kWT + col;
-#pragma unroll
-            for (int k = 0; k < kL; ++k) {
-                float acc = tc[k * kWT];
-#pragma unroll
-                for (int q = 0; q < 2 * NS; ++q) acc = fmaf(p.tab.G[k][q], m[q], acc);
-                tc[k * kWT] = acc;
-            }
-            if (p.bp && col_owned) {
-                float *bpc = p.bp + (long long)(row0 + jb * kL) * p.ldo + cgc;
-                for (int k = 0; k < kL && jb * kL + k < rows; ++k) bpc[(long long)k * p.ldo] = tc[k * kWT];
-            }
-        }
-    } else {
-        // no IIR stage: the bandpass output is the input
-        if (p.bp && col_owned && jb < nb) {
-            for (int k = 0; k < kL; ++k) {
-                const int row = jb * kL + k;
-                if (row < rows) p.bp[(long long)(row0 + row) * p.ldo + cgc] = tile[row * kWT + col];
-            }
-        }
-    }
-    __syncthreads();
-
-    // ------------------------------------------------ 4. spatial mean, cf
-    // ring slot of tile row 0 (the host passes n0 mod Q; row0 < 2048 <= Q)
-    int slot_r0 = p.slot_n0 + row0;
-    if (slot_r0 >= p.Q) slot_r0 -= p.Q;
-    if (p.sp || DET) {
-        const int g = tid & 15, ro = tid >> 4;      // 4-column group, row offset (< kRowStep)
-        const int ngroups = p.Wout >> 2;
-        const int q0 = p.HP + 4 * g;                // first output column of the group
-        const bool gact = g < ngroups;
-        const int cch = c0 + 4 * g;
-        // 1/|W| for the 4 channels (the window shrinks at the array ends)
-        float inv[4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            const int lo = max(0, cch + u - p.hw), hi = min(p.C - 1, cch + u + p.hw);
-            inv[u] = 1.0f / (float)max(1, hi - lo + 1);
-        }
-        const bool full_group = cch + 3 < p.C;
-        // every thread takes the same branch (hw and HP are launch constants)
-        switch (p.HP == 4 ? p.hw : (p.HP == 0 ? 0 : -1)) {
-        case 0: spatial_rows<0, DET>(p, tile, ro, rows, q0, row0, cch, slot_r0, full_group, gact, inv); break;
-        case 1: spatial_rows<1, DET>(p, tile, ro, rows, q0, row0, cch, slot_r0, full_group, gact, inv); break;
-        case 2: spatial_rows<2, DET>(p, tile, ro, rows, q0, row0, cch, slot_r0, full_group, gact, inv); break;
-        case 3: spatial_rows<3, DET>(p, tile, ro, rows, q0, row0, cch, slot_r0, full_group, gact, inv); break;
-        case 4: spatial_rows<4, DET>(p, tile, ro, rows, q0, row0, cch, slot_r0, full_group, gact, inv); break;
-        default: spatial_rows_generic<DET>(p, tile, ro, rows, q0, row0, cch, slot_r0, full_group, gact, inv); break;
-        }
-    }
-
-    if constexpr (DET) {
-        // ring writes of every CTA of the cluster become visible to the others
-        __threadfence();
-        cluster_sync_release_acquire();
-
-        // ------------------------------------------------ 5. STA/LTA
-        DF *DS = reinterpret_cast<DF *>(E + kDetDS);
-        DF *DL = reinterpret_cast<DF *>(E + kDetDL);
-        DF *BS = reinterpret_cast<DF *>(E + kDetBS);
-        DF *BL = reinterpret_cast<DF *>(E + kDetBL);
-        int *LZ = reinterpret_cast<int *>(E + kDetLZ);
-        int *BZ = reinterpret_cast<int *>(E + kDetBZ);
-        const bool dact = col_owned && jb < nb;
-        const long long nrow0 = p.n0 + row0;                 // global index of tile row 0
-        const int rbeg = jb * kL;
-        // The exiting values cf[n - w] of a block's 32 samples are read from
-        // this tile when they all lie in it (mode 1), else from the history
-        // ring, which phase 4 has already filled for this launch: as one
-        // contiguous run (mode 0) or sample by sample with wrap-around and the
-        // zeros before the first sample (mode 2).  Modes are warp-uniform.
-        struct Exit {
-            int mode, off, s0, lr0;
-        };
-        auto make_exit = [&](int w) -> Exit {
-            Exit e;
-            e.lr0 = rbeg - w;
-            if (e.lr0 >= 0) {
-                e.mode = 1;
-                e.off = e.lr0 * kWT + col;
-                e.s0 = 0;
-                return e;
-            }
-            int slot = slot_r0 + e.lr0;          // > -Q
-            if (slot < 0) slot += p.Q;
-            e.s0 = slot;
-            e.off = slot * (int)p.ldr + cgc;
-            e.mode = (slot + kL - 1 < p.Q && nrow0 + e.lr0 >= 0) ? 0 : 2;
-            return e;
-        };
-        const Exit exS = make_exit(p.ns), exL = make_exit(p.nl);
-        const int ldr = (int)p.ldr;
-        const bool full_blk = rbeg + kL <= rows;      // warp-uniform
-        // eight exits starting at block sample kb (samples past `rows` read 0
-        // unless the block is known to be full)
-        auto fetch8 = [&](const Exit &e, int kb, float (&v)[8], auto full) {
-            if (e.mode == 0) {
-                const float *gp = p.ring + (e.off + kb * ldr);
-#pragma unroll
-                for (int u = 0; u < 8; ++u) v[u] = __ldcg(gp + u * ldr);
-            } else if (e.mode == 1) {
-#pragma unroll
-                for (int u = 0; u < 8; ++u) v[u] = tile[e.off + (kb + u) * kWT];
-            } else {
-#pragma unroll
-                for (int u = 0; u < 8; ++u) {
-                    int slot = e.s0 + kb + u;
-                    slot = slot >= p.Q ? slot - p.Q : slot;
-                    const float t = __ldcg(p.ring + (slot * ldr + cgc));
-                    v[u] = (nrow0 + (e.lr0 + kb + u) >= 0) ? t : 0.f;
-                }
-            }
-            if constexpr (!decltype(full)::value) {
-#pragma unroll
-                for (int u = 0; u < 8; ++u) v[u] = (rbeg + kb + u < rows) ? v[u] : 0.f;
-            }
-        };
-        // pass a: exact block sums of cf and of the exiting values (cf is 0 in
-        // the tile past `rows`)
-        auto pass_a = [&](auto full) {
-            float cs = 0.f, cc = 0.f, ss = 0.f, sc2 = 0.f, ls = 0.f, lc = 0.f;
-            int lz = kNoNonzero;
-#pragma unroll 1
-            for (int kb = 0; kb < kL; kb += 8) {
-                float vs[8], vl[8];
-                fetch8(exS, kb, vs, full);
-                fetch8(exL, kb, vl, full);
-#pragma unroll
-                for (int u = 0; u < 8; ++u) {
-                    const float cf = tile[(rbeg + kb + u) * kWT + col];
-                    acc_nonneg(cs, cc, cf);
-                    acc_nonneg(ss, sc2, vs[u]);
-                    acc_nonneg(ls, lc, vl[u]);
-                    lz = cf != 0.f ? rbeg + kb + u : lz;
-                }
-            }
-            const DF tot = df_from_sum(cs, cc);
-            DS[jb * kWT + col] = df_add(tot, df_neg(df_from_sum(ss, sc2)));
-            DL[jb * kWT + col] = df_add(tot, df_neg(df_from_sum(ls, lc)));
-            LZ[jb * kWT + col] = lz;
-        };
-        if (dact) {
-            if (full_blk) pass_a(std::true_type{});
-            else pass_a(std::false_type{});
-        }
-        __syncthreads();
-        // exclusive scan over this CTA's blocks, one thread per column
-        // (double-float); AGG2 holds the CTA totals for the later CTAs:
-        // [0..2) STA hi/lo, [2..4) LTA hi/lo, [4] 1 + last nonzero index (0 = none)
-        float *AGG2 = AGG;                                   // [5][kWT]
-        if (tid < kWT) {
-            const int c = tid;
-            const bool own = c >= p.HP && c < p.HP + p.Wout && cbase + c < p.C;
-            if (own) {
-                DF bs{0.f, 0.f}, bl{0.f, 0.f};
-                int bz = kNoNonzero;
-                for (int j = 0; j < nb; ++j) {
-                    BS[j * kWT + c] = bs;
-                    BL[j * kWT + c] = bl;
-                    BZ[j * kWT + c] = bz;
-                    bs = df_add(bs, DS[j * kWT + c]);
-                    bl = df_add(bl, DL[j * kWT + c]);
-                    bz = max(bz, LZ[j * kWT + c]);
-                }
-                AGG2[0 * kWT + c] = bs.hi;
-                AGG2[1 * kWT + c] = bs.lo;
-                AGG2[2 * kWT + c] = bl.hi;
-                AGG2[3 * kWT + c] = bl.lo;
-                // the last nonzero as an index relative to the launch start
-                AGG2[4 * kWT + c] = __int_as_float(bz == kNoNonzero ? kNoNonzero : row0 + bz);
-            }
-        }
-        cluster_sync_release_acquire();
-        if (tid < kWT) {
-            const int c = tid;
-            const int cgl = cbase + c;
-            const bool own = c >= p.HP && c < p.HP + p.Wout && cgl < p.C;
-            if (own) {
-                // state at the start of this CTA: carried state + earlier CTAs
-                const double sIn = p.det_in[(long long)cgl * 4 + 0];
-                const double lIn = p.det_in[(long long)cgl * 4 + 1];
-                const double zIn = p.det_in[(long long)cgl * 4 + 2];   // 1 + index of last nonzero, 0 = none
-                DF bS{(float)sIn, 0.f}, bL{(float)lIn, 0.f};
-                bS.lo = (float)(sIn - (double)bS.hi);
-                bL.lo = (float)(lIn - (double)bL.hi);
-                // last nonzero relative to the launch start (clamped)
-                int zl = kNoNonzero;
-                if (zIn > 0.0) {
-                    const long long rel = (long long)zIn - 1 - p.n0;
-                    zl = rel < (long long)kNoNonzero ? kNoNonzero : (int)rel;
-                }
-                for (int q = 0; q < r; ++q) {
-                    const float *ra = cluster.map_shared_rank(AGG2, q);
-                    bS = df_add(bS, DF{ra[0 * kWT + c], ra[1 * kWT + c]});
-                    bL = df_add(bL, DF{ra[2 * kWT + c], ra[3 * kWT + c]});
-                    zl = max(zl, __float_as_int(ra[4 * kWT + c]));
-                }
-                if (last_cta) {
-                    const DF eS = df_add(bS, DF{AGG2[0 * kWT + c], AGG2[1 * kWT + c]});
-                    const DF eL = df_add(bL, DF{AGG2[2 * kWT + c], AGG2[3 * kWT + c]});
-                    const int ez = max(zl, __float_as_int(AGG2[4 * kWT + c]));
-                    p.det_out[(long long)cgl * 4 + 0] = (double)eS.hi + (double)eS.lo;
-                    p.det_out[(long long)cgl * 4 + 1] = (double)eL.hi + (double)eL.lo;
-                    p.det_out[(long long)cgl * 4 + 2] = ez == kNoNonzero ? 0.0 : (double)(p.n0 + ez + 1);
-                    p.det_out[(long long)cgl * 4 + 3] = 0.0;
-                }
-                // relative to this CTA's row 0
-                const int bzr = zl == kNoNonzero ? kNoNonzero : zl - row0;
-                for (int j = 0; j < nb; ++j) {
-                    BS[j * kWT + c] = df_add(BS[j * kWT + c], bS);
-                    BL[j * kWT + c] = df_add(BL[j * kWT + c], bL);
-                    BZ[j * kWT + c] = max(BZ[j * kWT + c], bzr);
-                }
-            }
-        }
-        __syncthreads();
-        // pass b: running sums inside the block, ratio
-        if (dact) {
-            float fs = BS[jb * kWT + col].hi + BS[jb * kWT + col].lo;
-            float fl = BL[jb * kWT + col].hi + BL[jb * kWT + col].lo;
-            int lz = BZ[jb * kWT + col];
-            // warm-up: rows before global index nl - 1 give 0
-            const long long wl = (long long)(p.nl - 1) - nrow0;
-            const int warm = wl > 4096 ? 4096 : (wl < -4096 ? -4096 : (int)wl);
-            float *rp = p.ratio ? p.ratio + (long long)(row0 + rbeg) * p.ldo + cgc : nullptr;
-            const float scale = p.ratio_scale;
-            // past the warm-up, with a nonzero cf inside every window of the
-            // block already known, no sample needs the validity test
-            const bool all_valid = full_blk && rbeg >= warm && lz > rbeg + kL - 1 - p.nl;
-            if (all_valid && rp) {
-#pragma unroll 1
-                for (int kb = 0; kb < kL; kb += 8) {
-                    float vs[8], vl[8];
-                    fetch8(exS, kb, vs, std::true_type{});
-                    fetch8(exL, kb, vl, std::true_type{});
-                    float *rq = rp + (long long)kb * p.ldo;
-#pragma unroll
-                    for (int u = 0; u < 8; ++u) {
-                        const float cf = tile[(rbeg + kb + u) * kWT + col];
-                        fs += cf - vs[u];
-                        fl += cf - vl[u];
-                        rq[(long long)u * p.ldo] = __fdividef(fs * scale, fl);
-                    }
-                }
-            } else {
-#pragma unroll 1
-                for (int kb = 0; kb < kL; kb += 8) {
-                    float vs[8], vl[8];
-                    fetch8(exS, kb, vs, std::false_type{});
-                    fetch8(exL, kb, vl, std::false_type{});
-#pragma unroll
-                    for (int u = 0; u < 8; ++u) {
-                        const int row = rbeg + kb + u;
-                        const float cf = tile[row * kWT + col];
-                        fs += cf - vs[u];
-                        fl += cf - vl[u];
-                        lz = cf != 0.f ? row : lz;
-                        const bool valid = (row >= warm) & (lz > row - p.nl);
-                        const float Rv = valid ? __fdividef(fs * scale, fl) : 0.f;
-                        if (rp && row < rows) rp[(long long)(kb + u) * p.ldo] = Rv;
-                    }
-                }
-            }
-        }
-    }
-    // no CTA may exit while a peer can still read its shared memory
-    if (NS > 0 || DET) cluster_sync_release_acquire();
+    chain_body<NS, DET, DENSE>(p, p.u, blockIdx.x, blockIdx.y);
 }
 
 template <int NS, bool DET, bool DENSE>
@@ -835,14 +25,14 @@ cudaError_t configure_t() {
 template <int NS, bool DET, bool DENSE>
 cudaError_t launch_t(const ChainParams &p, int n_tiles, cudaStream_t stream) {
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3((unsigned)n_tiles, (unsigned)p.R, 1);
+    cfg.gridDim = dim3((unsigned)n_tiles, (unsigned)p.u.R, 1);
     cfg.blockDim = dim3(kThreads, 1, 1);
     cfg.dynamicSmemBytes = chain_smem_bytes(DENSE);
     cfg.stream = stream;
     cudaLaunchAttribute attr[2];
     attr[0].id = cudaLaunchAttributeClusterDimension;
     attr[0].val.clusterDim.x = 1;
-    attr[0].val.clusterDim.y = (unsigned)p.R;
+    attr[0].val.clusterDim.y = (unsigned)p.u.R;
     attr[0].val.clusterDim.z = 1;
     attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
     attr[1].val.programmaticStreamSerializationAllowed = p.pdl ? 1 : 0;
@@ -865,6 +55,7 @@ cudaError_t configure_chain_kernels() {
     FILARK_CFG(4, false, false) FILARK_CFG(4, true, false) FILARK_CFG(4, false, true) FILARK_CFG(4, true, true)
     FILARK_CFG(8, false, false) FILARK_CFG(8, true, false) FILARK_CFG(8, false, true) FILARK_CFG(8, true, true)
 #undef FILARK_CFG
+    if (e == cudaSuccess) e = configure_batch_kernels();
     return e;
 }
 

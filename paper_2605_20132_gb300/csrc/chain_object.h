@@ -1,0 +1,39 @@
+// The chain object behind the C-ABI handle, shared by the single-stream API
+// (api.cpp) and the batched API (batch.cpp).  Not part of the public API.
+#pragma once
+
+#include "filark_internal.h"
+
+struct filark_chain {
+    filark_chain_config cfg{};
+    std::vector<double> sos;
+    filark::Plan plan;
+    int device = 0;
+    int C = 0, K = 1, hw = 0, HP = 0, Wout = 0, n_tiles = 0;
+    bool det = false;
+    int ns = 0, nl = 0;
+    long long Q = 0, ldr = 0;
+    double *iir[2] = {nullptr, nullptr};
+    double *detst[2] = {nullptr, nullptr};
+    float *ring = nullptr;
+    int *status_host = nullptr;   // mapped pinned word written by kernels
+    int *status_dev = nullptr;
+    int parity = 0;
+    long long n = 0;
+    filark_status sticky = FILARK_OK;
+    float *stage[4] = {nullptr, nullptr, nullptr, nullptr};   // in, ratio, bp, sp
+    double *dense = nullptr;      // dense carry matrices (device)
+    filark::ChainParams base{};
+    int64_t device_bytes = 0;
+    int use_pdl = 1;
+};
+
+namespace filark {
+// zero carried state, ring and counters (enqueued on `stream`)
+filark_status chain_zero_state(filark_chain *h, cudaStream_t stream);
+// sticky error state / device error word
+filark_status chain_check_status(filark_chain *h);
+// the argument checks of filark_chain_push_chunk
+filark_status chain_validate_push(filark_chain *h, const void *in, int64_t ld_in, int64_t T, const void *ratio,
+                                  const void *bp, const void *sp, int64_t ld_out);
+}  // namespace filark

@@ -130,71 +130,34 @@ extern "C" filark_status filark_chain_run_static(const filark_chain_config *cfg,
     if (e != cudaSuccess) return fail(FILARK_ECUDA, std::string("scratch clear: ") + cudaGetErrorString(e));
 
     ChainParams p;
-    std::memset(&p, 0, sizeof(p));
-    p.tab = plan.tab;
-    plan.slot_power(kL * kNB, p.Phi);
-    plan.slot_power(kL, p.ML64);
-    for (int r = 0; r < kMaxCluster; ++r) {
-        plan.slot_power(kL * kNB * r, p.PhiPow[r]);
-        for (int q = 0; q < kMaxSlots; ++q)
-            for (int t = 0; t < 4; ++t) p.PhiPow32[r][q][t] = (float)p.PhiPow[r][q][t];
-    }
-    p.ring = ring;
-    p.ldr = ldr;
-    p.Q = (int)Q;
-    p.C = C;
-    p.hw = hw;
-    p.HP = HP;
-    p.Wout = Wout;
-    p.ns = cfg->sta_len;
-    p.nl = cfg->lta_len;
-    p.ratio_scale = det ? (float)((double)cfg->lta_len / (double)cfg->sta_len) : 0.f;
-    p.r_vec4 = 1;
-    p.all32 = plan.mode == FILARK_PREC_ALL32;
-    p.status = nullptr;
-    p.dense = dense;
+    set_static_params(plan, hw, HP, Wout, cfg->sta_len, cfg->lta_len, dense, p);
     p.pdl = 1;
+    ChainUnit &u = p.u;
+    u.ring = ring;
+    u.ldr = ldr;
+    u.Q = (int)Q;
+    u.C = C;
     int parity = 0;
     for (int64_t done = 0; done < n_samples;) {
         const int Tl = (int)std::min<int64_t>(n_samples - done, kMaxLaunchSamples);
-        p.x = d_in + done * ld_in;
-        p.ldx = ld_in;
-        p.ratio = d_ratio ? d_ratio + done * ld_out : nullptr;
-        p.bp = d_bandpass ? d_bandpass + done * ld_out : nullptr;
-        p.sp = d_spatial ? d_spatial + done * ld_out : nullptr;
-        p.ldo = ld_out;
-        p.iir_in = iir[parity];
-        p.iir_out = iir[parity ^ 1];
-        p.det_in = dst[parity];
-        p.det_out = dst[parity ^ 1];
-        p.n0 = done;
-        p.T = Tl;
-        p.nblk = (Tl + kL - 1) / kL;
-        p.Lr = Tl - (p.nblk - 1) * kL;
-        p.R = (p.nblk + kNB - 1) / kNB;
-        if (NS > 0) {
-            const int nb_last = p.nblk - (p.R - 1) * kNB;
-            double PL[kMaxSlots][4], PR[kMaxSlots][4];
-            plan.slot_power((nb_last - 1) * kL + p.Lr, PL);
-            plan.slot_power(p.Lr, PR);
-            for (int q = 0; q < kMaxSlots; ++q) {
-                const double *a = PL[q], *b = p.PhiPow[p.R - 1][q];
-                for (int t = 0; t < 4; ++t) {
-                    p.PhiLast[q][t] = PL[q][t];
-                    p.Mr32[q][t] = (float)PR[q][t];
-                }
-                p.PhiTot[q][0] = a[0] * b[0] + a[1] * b[2];
-                p.PhiTot[q][1] = a[0] * b[1] + a[1] * b[3];
-                p.PhiTot[q][2] = a[2] * b[0] + a[3] * b[2];
-                p.PhiTot[q][3] = a[2] * b[1] + a[3] * b[3];
-            }
-        }
-        p.slot_n0 = (int)(done % Q);
-        p.x_vec4 = (ld_in % 4 == 0) && (((uintptr_t)p.x & 15u) == 0);
+        u.x = d_in + done * ld_in;
+        u.ldx = ld_in;
+        u.ratio = d_ratio ? d_ratio + done * ld_out : nullptr;
+        u.bp = d_bandpass ? d_bandpass + done * ld_out : nullptr;
+        u.sp = d_spatial ? d_spatial + done * ld_out : nullptr;
+        u.ldo = ld_out;
+        u.iir_in = iir[parity];
+        u.iir_out = iir[parity ^ 1];
+        u.det_in = dst[parity];
+        u.det_out = dst[parity ^ 1];
+        u.n0 = done;
+        set_unit_geometry(plan, Tl, u);
+        u.slot_n0 = (int)(done % Q);
+        u.x_vec4 = (ld_in % 4 == 0) && (((uintptr_t)u.x & 15u) == 0);
         bool ov = (ld_out % 4 == 0);
-        for (float *o : {p.ratio, p.bp, p.sp})
+        for (float *o : {u.ratio, u.bp, u.sp})
             if (o && ((uintptr_t)o & 15u)) ov = false;
-        p.o_vec4 = ov;
+        u.o_vec4 = ov;
         e = launch_chain(p, NS, det, plan.dense, n_tiles, s);
         if (e != cudaSuccess) return fail(FILARK_ECUDA, std::string("kernel launch: ") + cudaGetErrorString(e));
         parity ^= 1;

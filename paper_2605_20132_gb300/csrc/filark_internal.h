@@ -44,15 +44,10 @@ struct Tables32 {
     float M[kMaxSlots][4];              // per slot, M^L as {m00, m01, m10, m11}
 };
 
-struct ChainParams {
-    Tables32 tab;
-    double Phi[kMaxSlots][4];           // M^(L*kNB): one full CTA, FP64
-    double ML64[kMaxSlots][4];          // M^L, FP64
-    double PhiLast[kMaxSlots][4];       // transition over the launch's last CTA, FP64
-    double PhiTot[kMaxSlots][4];        // PhiLast * Phi^(R-1): launch start -> launch end
-    double PhiPow[kMaxCluster][kMaxSlots][4];  // Phi^r = M^(L*kNB*r), FP64
-    float PhiPow32[kMaxCluster][kMaxSlots][4]; // the same in FP32
-    float Mr32[kMaxSlots][4];           // M^Lr of the ragged last block (Lr < L), FP32
+// What changes from one launch to the next (and, in a batch, from one stream
+// to another): buffers, carried-state parity, position in the stream and the
+// launch geometry with its ragged-end transitions.
+struct ChainUnit {
     const float *x;                     // launch input, row 0 = first sample
     long long ldx;
     float *ratio, *bp, *sp;             // launch outputs (row 0 = first sample)
@@ -61,22 +56,46 @@ struct ChainParams {
     double *iir_out;
     const double *det_in;               // [C][4] {sta_sum, lta_sum, 1 + index of last nonzero cf (0 = none), 0}
     double *det_out;
+    // Batched pushes run a stream's units back to back in one cluster, so a
+    // tile cannot wait for its neighbours' end states: it carries the state of
+    // all kWT columns (halo included) itself, [tiles][kWT][2*NS], between the
+    // units of one push.  NULL: read iir_in / write only the owned channels.
+    const double *halo_in;
+    double *halo_out;
     float *ring;                        // [Q][ldr] cf history
     long long ldr;
+    long long n0;                       // global index of the launch's first sample
     int Q;                              // ring length in samples
     int slot_n0;                        // n0 mod Q
-    long long n0;                       // global index of the launch's first sample
     int C, T, nblk, Lr, R;
+    int x_vec4, o_vec4;                 // float4 access allowed (input, outputs)
+    double PhiLast[kMaxSlots][4];       // transition over the launch's last CTA, FP64
+    double PhiTot[kMaxSlots][4];        // PhiLast * Phi^(R-1): launch start -> launch end
+    float Mr32[kMaxSlots][4];           // M^Lr of the ragged last block (Lr < L), FP32
+};
+
+// Everything else is fixed for a chain (for a batch: shared by its streams).
+struct ChainParams {
+    Tables32 tab;
+    double Phi[kMaxSlots][4];           // M^(L*kNB): one full CTA, FP64
+    double ML64[kMaxSlots][4];          // M^L, FP64
+    double PhiPow[kMaxCluster][kMaxSlots][4];  // Phi^r = M^(L*kNB*r), FP64
+    float PhiPow32[kMaxCluster][kMaxSlots][4]; // the same in FP32
     int hw, HP, Wout;
     int ns, nl;
     float ratio_scale;                  // nl / ns
-    int x_vec4, o_vec4, r_vec4;         // float4 access allowed (input, outputs, ring)
     int all32;                          // keep carries in FP32 everywhere (comparison)
     int pdl;                            // launched with programmatic stream serialization
     // dense carry (FILARK_PREC_DENSE64, or ALL32 without a modal basis):
     // [kDenseMats][16][16] FP64, entries 0..31 = A^1..A^32, 32..39 = Phi^0..Phi^7
     const double *dense;
-    int *status;                        // device error word (0 = ok)
+    ChainUnit u;                        // the launch (single-stream kernel)
+};
+
+// One work item of the batched kernel: tile `tile` of one stream, whose push
+// is the units [unit0, unit0 + n_units) run in order by one cluster.
+struct BatchItem {
+    int unit0, n_units, tile, pad;
 };
 
 // ---------------------------------------------------------------------------
@@ -108,6 +127,9 @@ struct Plan {
     mutable std::vector<double> cta_cache;
 };
 
+// Message returned by filark_last_error_string on this thread.
+void set_last_error(const std::string &msg);
+
 // Validate and normalise the SOS (a0 != 0, finite, stable), and build the
 // plan.  Returns FILARK_OK or an error with a message in *err.
 filark_status make_plan(const double *sos, int S, int precision, Plan *plan, std::string *err);
@@ -116,6 +138,14 @@ filark_status make_plan(const double *sos, int S, int precision, Plan *plan, std
 filark_status design_butter_bandpass(int order, double f1, double f2, double fs, double *sos,
                                      std::string *err);
 
+// Fill the launch geometry of a unit of Tl samples (1 <= Tl <= kTileRows * Rmax,
+// Rmax <= kMaxCluster) and its ragged-end transitions from the plan.
+void set_unit_geometry(const Plan &plan, int Tl, ChainUnit &u);
+
+// Static kernel parameters of a chain (tables, transitions, geometry).
+void set_static_params(const Plan &plan, int hw, int HP, int Wout, int ns, int nl, const double *dense_dev,
+                       ChainParams &p);
+
 // ---------------------------------------------------------------------------
 // Kernel launch (chain_kernel.cu).  Enqueues one launch of <= kMaxLaunchSamples.
 // ---------------------------------------------------------------------------
@@ -123,6 +153,20 @@ cudaError_t launch_chain(const ChainParams &p, int NS, bool detector, bool dense
                          cudaStream_t stream);
 
 size_t chain_smem_bytes(bool dense);
+
+// The batched kernel: a persistent grid of `n_clusters` clusters of `cluster`
+// CTAs (time ranges) takes the items in order from a device counter.
+// d_ctr[0] = item count, d_ctr[1] = next item (0 at launch); both live in
+// device memory so that a captured graph can be replayed with other tables.
+cudaError_t launch_chain_batch(const ChainParams &p, int NS, bool detector, bool dense, int cluster,
+                               int n_clusters, const BatchItem *d_items, int *d_ctr,
+                               const ChainUnit *d_units, cudaStream_t stream);
+
+// Function attributes of the batched kernels (called by configure_chain_kernels).
+cudaError_t configure_batch_kernels();
+
+// Clusters of `cluster` CTAs that can be resident at once (0 if unknown).
+int batch_max_active_clusters(int NS, bool detector, bool dense, int cluster);
 
 // Set the kernels' function attributes on the current device (call once per
 // device before the first launch).

@@ -696,4 +696,53 @@ filark_status design_butter_bandpass(int order, double f1, double f2, double fs,
     return FILARK_OK;
 }
 
+void set_unit_geometry(const Plan &plan, int Tl, ChainUnit &u) {
+    u.T = Tl;
+    u.nblk = (Tl + kL - 1) / kL;
+    u.Lr = Tl - (u.nblk - 1) * kL;
+    u.R = (u.nblk + kNB - 1) / kNB;
+    if (plan.NS > 0) {
+        const int nb_last = u.nblk - (u.R - 1) * kNB;
+        const double (*pl)[4] = plan.power_cached((nb_last - 1) * kL + u.Lr);
+        const double (*pr)[4] = plan.power_cached(u.Lr);
+        const double (*pp)[4] = plan.power_cached_cta(u.R - 1);
+        for (int s = 0; s < kMaxSlots; ++s) {
+            for (int q = 0; q < 4; ++q) {
+                u.PhiLast[s][q] = pl[s][q];
+                u.Mr32[s][q] = (float)pr[s][q];
+            }
+            // PhiTot = PhiLast * Phi^(R-1) (2x2 per slot)
+            const double *a = pl[s], *b = pp[s];
+            u.PhiTot[s][0] = a[0] * b[0] + a[1] * b[2];
+            u.PhiTot[s][1] = a[0] * b[1] + a[1] * b[3];
+            u.PhiTot[s][2] = a[2] * b[0] + a[3] * b[2];
+            u.PhiTot[s][3] = a[2] * b[1] + a[3] * b[3];
+        }
+    }
+}
+
+void set_static_params(const Plan &plan, int hw, int HP, int Wout, int ns, int nl, const double *dense_dev,
+                       ChainParams &p) {
+    std::memset(&p, 0, sizeof(p));
+    p.tab = plan.tab;
+    plan.slot_power(kL * kNB, p.Phi);
+    plan.slot_power(kL, p.ML64);
+    for (int r = 0; r < kMaxCluster; ++r) {
+        const double (*pr)[4] = plan.power_cached_cta(r);
+        for (int s = 0; s < kMaxSlots; ++s)
+            for (int q = 0; q < 4; ++q) {
+                p.PhiPow[r][s][q] = pr[s][q];
+                p.PhiPow32[r][s][q] = (float)pr[s][q];
+            }
+    }
+    p.hw = hw;
+    p.HP = HP;
+    p.Wout = Wout;
+    p.ns = ns;
+    p.nl = nl;
+    p.ratio_scale = (nl > 0 && ns > 0) ? (float)((double)nl / (double)ns) : 0.f;
+    p.all32 = plan.mode == FILARK_PREC_ALL32;
+    p.dense = dense_dev;
+}
+
 }  // namespace filark

@@ -40,10 +40,6 @@
 
 #include "filark_internal.h"
 
-namespace filark {
-void set_last_error(const std::string &msg);
-}
-
 namespace {
 
 using filark::set_last_error;

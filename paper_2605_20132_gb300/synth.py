@@ -179,6 +179,14 @@ def batch_streams(seed: int = 3, n_streams: int = 32, channels=(500, 10_000),
     return [dict(n_channels=int(C), seed=int(seed * 1000 + i)) for i, C in enumerate(Cs)]
 
 
+def batch_stream_data(spec: dict, n_samples: int) -> np.ndarray:
+    """One stream of the batching workload: the small-workload recipe (1 kHz,
+    N(0,1) noise plus 3 Ricker events of 20 Hz peak, amplitude 5, moveout
+    0.5 ms/channel) at the stream's channel count and seed."""
+    return noise_ricker_stream(spec["n_channels"], n_samples, 1000.0, 3, 5.0, (20.0, 20.0), (0.5, 0.5),
+                               spec["seed"], pink=False, fixed_origin_channel=True)
+
+
 def batch_chunk_lengths(seed: int, n_streams: int, n_pushes: int, chunk=(200, 3000)) -> np.ndarray:
     """[n_pushes][n_streams] chunk lengths, uniform in [chunk[0], chunk[1]]."""
     rng = np.random.default_rng([seed, 7])
