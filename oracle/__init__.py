@@ -84,6 +84,23 @@ def _bind(path: str, long_double: bool):
     f = getattr(lib, p + "sos_adjoint")
     f.argtypes = [_dp, ct.c_int, _dp, ct.c_long, _dp, _dp, _dp]
     f.restype = None
+    if not long_double:
+        _lp = ct.POINTER(ct.c_long)
+        f = lib.ora_trig_new
+        f.argtypes = [ct.c_int, ct.c_double, ct.c_double]
+        f.restype = ct.c_void_p
+        f = lib.ora_trig_free
+        f.argtypes = [ct.c_void_p]
+        f.restype = None
+        f = lib.ora_trig_push
+        f.argtypes = [ct.c_void_p, _fp, ct.c_long, ct.c_long, _lp, _lp, _lp, ct.c_long]
+        f.restype = ct.c_long
+        f = lib.ora_trig_flush
+        f.argtypes = [ct.c_void_p, _lp, _lp, _lp, ct.c_long]
+        f.restype = ct.c_long
+        f = lib.ora_events_merge
+        f.argtypes = [_lp, _lp, _lp, ct.c_long, _lp]
+        f.restype = ct.c_long
     return lib, p
 
 
@@ -222,3 +239,66 @@ def sos_adjoint(sos: np.ndarray, x: np.ndarray, gy: np.ndarray, long_double: boo
     _fn("sos_adjoint", long_double)(_ptr(sos), sos.shape[0], _ptr(x), x.shape[0], _ptr(gy),
                                     _ptr(gx), _ptr(gs))
     return gx, gs
+
+
+# ------------------------------------------------------ triggers and events --
+
+_lp = ct.POINTER(ct.c_long)
+
+
+class Trigger:
+    """Per-channel on/off hysteresis on the detector ratio, carried across
+    pushes; reports each channel trigger [t_on, t_off) when it ends."""
+
+    def __init__(self, C: int, on: float, off: float):
+        lib, _ = _load(False)
+        self._f = {k: getattr(lib, "ora_" + k) for k in ("trig_new", "trig_free", "trig_push", "trig_flush")}
+        self.C = int(C)
+        self._h = self._f["trig_new"](self.C, float(on), float(off))
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h:
+            self._f["trig_free"](h)
+            self._h = None
+
+    @staticmethod
+    def _records(call, cap):
+        while True:
+            rc, ron, roff = (np.zeros(cap, dtype=np.int64) for _ in range(3))
+            n = call(rc, ron, roff, cap)
+            if n <= cap:
+                return np.stack([rc[:n], ron[:n], roff[:n]], axis=1)
+            cap = int(n)
+
+    def push(self, R: np.ndarray) -> np.ndarray:
+        """R: [T][C] float32.  Returns the triggers that ended, [k][3] =
+        (channel, t_on, t_off)."""
+        R = np.ascontiguousarray(R, dtype=np.float32)
+        if R.ndim != 2 or R.shape[1] != self.C:
+            raise ValueError("R must be [T][C]")
+        T = R.shape[0]
+        # at most one trigger can end per channel every second sample
+        cap = min(T * self.C // 2 + 16, 64 * self.C + 100_000)
+        rc, ron, roff = (np.zeros(cap, dtype=np.int64) for _ in range(3))
+        n = self._f["trig_push"](self._h, _ptr(R, _fp), self.C, T, _ptr(rc, _lp), _ptr(ron, _lp),
+                                 _ptr(roff, _lp), cap)
+        if n > cap:
+            raise RuntimeError("more triggers ended in one push than the oracle buffer holds")
+        return np.stack([rc[:n], ron[:n], roff[:n]], axis=1)
+
+    def flush(self) -> np.ndarray:
+        """The runs still open, with t_off = samples seen (state kept)."""
+        return self._records(lambda a, b, c, cap: self._f["trig_flush"](
+            self._h, _ptr(a, _lp), _ptr(b, _lp), _ptr(c, _lp), cap), max(16, self.C))
+
+
+def events_merge(records: np.ndarray) -> np.ndarray:
+    """Events from channel triggers [k][3] = (channel, t_on, t_off): rows
+    (t_on, t_off, c_min, c_max, n_triggers), sorted by (t_on, c_min, t_off,
+    c_max)."""
+    r = np.ascontiguousarray(records, dtype=np.int64).reshape(-1, 3)
+    rc, ron, roff = (np.ascontiguousarray(r[:, i]) for i in range(3))
+    ev = np.zeros((max(1, r.shape[0]), 5), dtype=np.int64)
+    m = _fn("events_merge")(_ptr(rc, _lp), _ptr(ron, _lp), _ptr(roff, _lp), r.shape[0], _ptr(ev, _lp))
+    return ev[:m].copy()

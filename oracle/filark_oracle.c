@@ -37,6 +37,11 @@
  *     and wherever the long window holds only zeros.
  *   - Adjoint of the SOS cascade (gradients with respect to the input and to
  *     every coefficient of every section), for the differentiable filter.
+ *   - Trigger and event extraction on the detector ratio (Sec. 3.4, threshold
+ *     detectors behind the monitor interface): a per-channel on/off
+ *     hysteresis state carried across pushes; every maximal run of the "on"
+ *     state is a channel trigger [t_on, t_off); triggers on neighbouring
+ *     channels whose time intervals overlap belong to the same event.
  */
 #include <math.h>
 #include <stdint.h>
@@ -484,3 +489,147 @@ void ORA(sos_adjoint)(const double *sos, int S, const double *x, long N,
     for (long n = 0; n < N; ++n) gx[n] = (double)g[n];
     free(sig); free(g); free(w);
 }
+
+
+/* ------------------------------------------------------------------------
+ * Triggers (per channel, hysteresis) and events (triggers merged across
+ * neighbouring channels).  Integer and comparison work only: the ratio is
+ * compared, as given (float), against the double thresholds.
+ *
+ *   s(-1) = 0;  s(n) = 1 if R(n) >= on,  0 if R(n) < off,  else s(n-1).
+ *   A channel trigger is a maximal run of s = 1: [t_on, t_off), t_off the
+ *   first sample after the run.  It is reported when the run ends (or, by a
+ *   flush, with t_off = samples seen so far and the OPEN flag).
+ * ------------------------------------------------------------------------ */
+#ifndef ORA_LONG_DOUBLE
+typedef struct {
+    int C;
+    double on, off;
+    long n;          /* samples seen */
+    int *s;          /* state per channel */
+    long *t_open;    /* start of the open run (valid while s = 1) */
+} ora_trig_t;
+
+void *ora_trig_new(int C, double on, double off)
+{
+    ora_trig_t *t = (ora_trig_t *)calloc(1, sizeof(ora_trig_t));
+    t->C = C;
+    t->on = on;
+    t->off = off;
+    t->s = (int *)calloc((size_t)C, sizeof(int));
+    t->t_open = (long *)calloc((size_t)C, sizeof(long));
+    return t;
+}
+
+void ora_trig_free(void *p)
+{
+    ora_trig_t *t = (ora_trig_t *)p;
+    if (!t) return;
+    free(t->s);
+    free(t->t_open);
+    free(t);
+}
+
+/* One push of T samples of R (time-major, row stride ld).  Appends the
+ * triggers that end in this push as (channel, t_on, t_off) to the arrays
+ * (at most cap); returns how many ended (which may exceed cap). */
+long ora_trig_push(void *p, const float *R, long ld, long T, long *rc, long *ron, long *roff, long cap)
+{
+    ora_trig_t *t = (ora_trig_t *)p;
+    long k = 0;
+    for (long i = 0; i < T; ++i) {
+        const long n = t->n + i;
+        for (int c = 0; c < t->C; ++c) {
+            const double r = (double)R[i * ld + c];
+            int s = t->s[c];
+            if (r >= t->on) s = 1;
+            else if (r < t->off) s = 0;
+            if (s == 1 && t->s[c] == 0) t->t_open[c] = n;
+            if (s == 0 && t->s[c] == 1) {
+                if (k < cap) {
+                    rc[k] = c;
+                    ron[k] = t->t_open[c];
+                    roff[k] = n;
+                }
+                ++k;
+            }
+            t->s[c] = s;
+        }
+    }
+    t->n += T;
+    return k;
+}
+
+/* Report the runs still open (t_off = samples seen); the state is kept. */
+long ora_trig_flush(void *p, long *rc, long *ron, long *roff, long cap)
+{
+    ora_trig_t *t = (ora_trig_t *)p;
+    long k = 0;
+    for (int c = 0; c < t->C; ++c) {
+        if (!t->s[c]) continue;
+        if (k < cap) {
+            rc[k] = c;
+            ron[k] = t->t_open[c];
+            roff[k] = t->n;
+        }
+        ++k;
+    }
+    return k;
+}
+
+static long uf_find(long *parent, long i)
+{
+    while (parent[i] != i) i = parent[i];
+    return i;
+}
+
+/* Events: connected components of the triggers, two triggers being joined
+ * when their channels differ by one and their intervals share a sample.
+ * ev receives 5 longs per event {t_on, t_off, c_min, c_max, n_triggers};
+ * events are returned sorted by (t_on, c_min, t_off, c_max).  Returns the
+ * number of events.  Quadratic in the number of triggers: for tests. */
+static int ev_cmp(const void *a, const void *b)
+{
+    const long *x = (const long *)a, *y = (const long *)b;
+    const int order[4] = {0, 2, 1, 3};
+    for (int i = 0; i < 4; ++i) {
+        if (x[order[i]] < y[order[i]]) return -1;
+        if (x[order[i]] > y[order[i]]) return 1;
+    }
+    return 0;
+}
+
+long ora_events_merge(const long *rc, const long *ron, const long *roff, long n, long *ev)
+{
+    long *parent = (long *)malloc(sizeof(long) * (size_t)(n > 0 ? n : 1));
+    for (long i = 0; i < n; ++i) parent[i] = i;
+    for (long i = 0; i < n; ++i)
+        for (long j = i + 1; j < n; ++j) {
+            const long dc = rc[i] - rc[j];
+            if (dc != 1 && dc != -1) continue;
+            const long lo = ron[i] > ron[j] ? ron[i] : ron[j];
+            const long hi = roff[i] < roff[j] ? roff[i] : roff[j];
+            if (lo >= hi) continue;
+            const long a = uf_find(parent, i), b = uf_find(parent, j);
+            if (a != b) parent[a < b ? b : a] = a < b ? a : b;
+        }
+    long m = 0;
+    for (long i = 0; i < n; ++i) {
+        if (uf_find(parent, i) != i) continue;
+        long *e = ev + 5 * m;
+        e[0] = ron[i]; e[1] = roff[i]; e[2] = rc[i]; e[3] = rc[i]; e[4] = 0;
+        for (long j = 0; j < n; ++j) {
+            if (uf_find(parent, j) != i) continue;
+            if (ron[j] < e[0]) e[0] = ron[j];
+            if (roff[j] > e[1]) e[1] = roff[j];
+            if (rc[j] < e[2]) e[2] = rc[j];
+            if (rc[j] > e[3]) e[3] = rc[j];
+            e[4] += 1;
+        }
+        ++m;
+    }
+    qsort(ev, (size_t)m, 5 * sizeof(long), ev_cmp);
+    free(parent);
+    return m;
+}
+#endif

@@ -24,8 +24,8 @@
 //   3. fix-up y_bp = y_loc + G m_j, written back in place;
 //   4. spatial mean over the 2h+1 neighbouring columns, cf = y_sp^2, written to
 //      the detector's history ring and kept in place;
-//   5. STA/LTA: exact (compensated) block sums, FP64 scan across blocks and
-//      CTAs, then FP32 running sums inside each block and the ratio.
+//   5. STA/LTA: exact (compensated) block sums, double-float scan across
+//      blocks and CTAs, then FP32 running sums inside each block and the ratio.
 //
 // Consecutive launches on a stream overlap through programmatic dependent
 // launch: phases 0-1 only read the caller's input, so a launch starts them
@@ -440,9 +440,9 @@ __device__ __forceinline__ void chain_body(const ChainParams &p, const ChainUnit
             // (c) state at this CTA's start: Phi^r s_launch + g
             {
                 double sv[RT];
-#pragma unroll
                 const double *src = cu.halo_in ? cu.halo_in + ((long long)tx * kWT + c) * (2 * NS)
                                                : cu.iir_in + (long long)cgs * (2 * NS);
+#pragma unroll
                 for (int t = 0; t < RT; ++t)
                     sv[t] = (r0 + t < n && cgs >= 0 && cgs < cu.C) ? src[r0 + t] : 0.0;
                 set_rows(sv);
@@ -630,7 +630,8 @@ __device__ __forceinline__ void chain_body(const ChainParams &p, const ChainUnit
 
     if constexpr (DET) {
         // ring writes of every CTA of the cluster become visible to the others
-        __threadfence();
+        // (release/acquire at cluster scope orders the global stores too; the
+        // next launch sees them at the kernel boundary)
         cluster_sync_release_acquire();
 
         // ------------------------------------------------ 5. STA/LTA

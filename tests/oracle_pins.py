@@ -326,6 +326,117 @@ def pin_stalta_vs_literal_windows(ora):
     return worst, 1e-11
 
 
+
+# ------------------------------------------------------ trigger / event pins --
+
+def _sorted_records(r):
+    r = np.asarray(r, dtype=np.int64).reshape(-1, 3)
+    return r[np.lexsort((r[:, 2], r[:, 1], r[:, 0]))] if r.size else r
+
+
+def pin_trigger_closed_forms(ora):
+    """Hand-built ratio sequences with known runs: a value equal to the on
+    threshold sets, equal to the off threshold keeps, just below it resets;
+    a run open at the end is reported only by the flush, and a run that spans
+    a push boundary keeps its start."""
+    on, off = 4.0, 1.5
+    lo = float(np.nextafter(np.float32(off), np.float32(0)))
+    R = np.zeros((12, 4), dtype=np.float32)
+    R[:, 0] = [0, 4, 2, 1.5, 1.5, lo, 0, 5, 0, 0, 0, 0]        # runs [1,5), [7,8)
+    R[:, 1] = [3.99, 3.99, 1, 4, 4, 4, 4, 4, 4, 4, 4, 4]       # open from 3
+    R[:, 2] = [9, 0, 9, 0, 9, 0, 9, 0, 9, 0, 9, 0]             # six unit runs
+    R[:, 3] = [0] * 12                                          # never
+    t = ora.Trigger(4, on, off)
+    got = np.concatenate([t.push(R[:4]), t.push(R[4:9]), t.push(R[9:])])
+    fl = t.flush()
+    want = [(0, 1, 5), (0, 7, 8)] + [(2, k, k + 1) for k in range(0, 12, 2)]
+    err = 0.0 if np.array_equal(_sorted_records(got), _sorted_records(want)) else 1.0
+    err += 0.0 if np.array_equal(_sorted_records(fl), _sorted_records([(1, 3, 12)])) else 1.0
+    return err, 0.0
+
+
+def pin_trigger_last_forcing_sample(ora):
+    """The recursion s(n) = set / reset / keep has a non-recursive form: s(n)
+    = 1 exactly when the latest sample k <= n with R(k) >= on or R(k) < off
+    exists and has R(k) >= on.  Runs of that image, on random ratios pushed
+    in random chunks, must equal the oracle's triggers (plus the flush)."""
+    rng = np.random.default_rng(31)
+    C, N, on, off = 7, 400, 2.0, 1.2
+    R = rng.choice(np.array([0.0, 1.0, 1.2, 1.5, 1.99, 2.0, 3.0], dtype=np.float32), size=(N, C),
+                   p=[0.15, 0.15, 0.1, 0.3, 0.1, 0.1, 0.1])
+    S = np.zeros((N, C), dtype=np.int64)
+    for c in range(C):
+        forcing = (R[:, c] >= on) | (R[:, c] < off)
+        idx = np.where(forcing, np.arange(N), -1)
+        last = np.maximum.accumulate(idx)
+        S[:, c] = np.where(last >= 0, R[np.maximum(last, 0), c] >= on, False)
+    want = []
+    for c in range(C):
+        d = np.diff(np.concatenate([[0], S[:, c], [0]]))
+        for a, b in zip(np.where(d == 1)[0], np.where(d == -1)[0]):
+            want.append((c, a, b))
+    t = ora.Trigger(C, on, off)
+    parts, pos = [], 0
+    while pos < N:
+        k = int(rng.integers(1, 60))
+        parts.append(t.push(R[pos:pos + k]))
+        pos += k
+    parts.append(t.flush())
+    got = np.concatenate(parts)
+    return (0.0 if np.array_equal(_sorted_records(got), _sorted_records(want)) else 1.0), 0.0
+
+
+def _flood_fill_events(S):
+    """4-connected components of the binary image S[n][c]: (t_on, t_off,
+    c_min, c_max, n_runs) with t_off one past the last sample."""
+    N, C = S.shape
+    seen = np.zeros_like(S, dtype=bool)
+    out = []
+    for n0 in range(N):
+        for c0 in range(C):
+            if not S[n0, c0] or seen[n0, c0]:
+                continue
+            stack, cells = [(n0, c0)], []
+            seen[n0, c0] = True
+            while stack:
+                n, c = stack.pop()
+                cells.append((n, c))
+                for dn, dc in ((1, 0), (-1, 0), (0, 1), (0, -1)):
+                    m, d = n + dn, c + dc
+                    if 0 <= m < N and 0 <= d < C and S[m, d] and not seen[m, d]:
+                        seen[m, d] = True
+                        stack.append((m, d))
+            ns = [n for n, _ in cells]
+            cs = [c for _, c in cells]
+            runs = sum(1 for n, c in cells if n == 0 or not S[n - 1, c])
+            out.append((min(ns), max(ns) + 1, min(cs), max(cs), runs))
+    out.sort(key=lambda e: (e[0], e[2], e[1], e[3]))
+    return np.array(out, dtype=np.int64).reshape(-1, 5)
+
+
+def pin_events_vs_flood_fill(ora):
+    """Events merged from channel triggers (neighbouring channels, intervals
+    sharing a sample) equal the 4-connected components of the trigger image
+    found by flood fill, on random blob-shaped ratio images."""
+    rng = np.random.default_rng(37)
+    worst = 0.0
+    for trial in range(6):
+        C, N = 24, 160
+        R = np.zeros((N, C), dtype=np.float32)
+        for _ in range(10):
+            c0, n0 = rng.integers(0, C), rng.integers(0, N)
+            w, h, slope = rng.integers(1, 6), rng.integers(3, 25), rng.integers(-2, 3)
+            for c in range(max(0, c0 - w), min(C, c0 + w + 1)):
+                a = n0 + slope * (c - c0)
+                R[max(0, a):max(0, min(N, a + h)), c] = 5.0
+        R[rng.random((N, C)) < 0.03] = 5.0
+        t = ora.Trigger(C, 3.0, 3.0)
+        recs = np.concatenate([t.push(R[:N // 3]), t.push(R[N // 3:]), t.flush()])
+        ev = ora.events_merge(recs)
+        ref = _flood_fill_events(R >= 3.0)
+        worst = max(worst, 0.0 if np.array_equal(ev, ref) else 1.0)
+    return worst, 0.0
+
 # ------------------------------------------------------------ adjoint pins --
 
 def _loss_and_grads(ora, sos, x, target):
@@ -423,4 +534,7 @@ ALL_PINS = [
     pin_stalta_naive_closed_forms,
     pin_adjoint_finite_differences,
     pin_adjoint_identity,
+    pin_trigger_closed_forms,
+    pin_trigger_last_forcing_sample,
+    pin_events_vs_flood_fill,
 ]

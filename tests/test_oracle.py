@@ -91,6 +91,12 @@ MUTANTS = [
     ("adjoint_sign_a", "ga[i] -= w[n] * y[n - i];", "ga[i] += w[n] * y[n - i];"),
     ("adjoint_index", "if (n + 1 < N) acc -= a1 * w[n + 1];", "if (n + 1 < N) acc -= a2 * w[n + 1];"),
     ("adjoint_input_grad_b", "if (n + 2 < N) acc += b2 * w[n + 2];", "if (n + 2 < N) acc += b1 * w[n + 2];"),
+    ("trigger_on_strict", "if (r >= t->on) s = 1;", "if (r > t->on) s = 1;"),
+    ("trigger_off_inclusive", "else if (r < t->off) s = 0;", "else if (r <= t->off) s = 0;"),
+    ("trigger_no_hysteresis", "else if (r < t->off) s = 0;", "else s = 0;"),
+    ("trigger_flush_end", "roff[k] = t->n;", "roff[k] = t->n - 1;"),
+    ("events_touching_merge", "if (lo >= hi) continue;", "if (lo > hi) continue;"),
+    ("events_skip_a_channel", "if (dc != 1 && dc != -1) continue;", "if (dc == 0 || dc < -2 || dc > 2) continue;"),
 ]
 
 
