@@ -347,6 +347,69 @@ filark_status filark_batch_get_info(const filark_batch *b, filark_batch_info *ou
 filark_status filark_batch_stream(filark_batch *b, int i, filark_chain **out);
 filark_status filark_batch_destroy(filark_batch *b);   /* NULL ok */
 
+/*
+ * Triggers and events on the detector ratio: the monitor stage behind the
+ * energy detector (Sec. 3.4, threshold-based energy detectors behind the
+ * monitor interface).
+ *
+ * Per channel, a hysteresis state carried across pushes (zero after create /
+ * reset):  s(n) = 1 if R(n) >= on, 0 if R(n) < off, else s(n-1).  Every
+ * maximal run of s = 1 is a channel trigger [t_on, t_off) (sample indices
+ * since create/reset, t_off one past the run).  A push reports the triggers
+ * that END in it; filark_trigger_flush reports the runs still open (t_off =
+ * samples so far, flag FILARK_TRIGGER_OPEN) and keeps the state.  R is
+ * compared exactly against the double thresholds.
+ *
+ * Triggers are appended at d_records[*d_count ...] with one device atomic per
+ * trigger: *d_count (device, the caller zeroes it) grows by the number of
+ * triggers even past `capacity`; records past capacity are dropped.  Order
+ * within a call is unspecified.  Work is enqueued on `stream`.
+ *
+ * Events: the connected components of a set of triggers, two triggers being
+ * joined when their channels differ by one and their intervals share a
+ * sample -- the 4-connected regions of the (channel, time) trigger image.
+ * Each event is (t_on = earliest start, t_off = latest end, c_min, c_max,
+ * n_triggers, flags = OR of the triggers' flags), in unspecified order.
+ * filark_events_merge needs a 256-byte aligned device workspace of
+ * filark_events_work_bytes(n_triggers, n_channels) bytes and blocks until it
+ * is done (it reads back an error flag).  FILARK_EINVAL if a trigger's channel
+ * lies outside [0, n_channels).
+ */
+#define FILARK_TRIGGER_OPEN 1
+
+typedef struct {
+    int64_t t_on, t_off;
+    int32_t channel;
+    int32_t flags;
+} filark_trigger_record;
+
+typedef struct {
+    int64_t t_on, t_off;
+    int32_t c_min, c_max;
+    int32_t n_triggers;
+    int32_t flags;
+} filark_event;
+
+typedef struct filark_trigger filark_trigger;
+
+/* off <= on, both finite; max_chunk: largest n_samples of one push. */
+filark_status filark_trigger_create(int n_channels, double on, double off, int64_t max_chunk, int cuda_device,
+                                    filark_trigger **out);
+/* d_ratio: device [n_samples][ld] float32, ld >= n_channels (e.g. a chain's
+   ratio output).  d_count: device, 64-bit. */
+filark_status filark_trigger_push(filark_trigger *t, const float *d_ratio, int64_t ld, int64_t n_samples,
+                                  filark_trigger_record *d_records, int64_t capacity,
+                                  unsigned long long *d_count, filark_stream_t stream);
+filark_status filark_trigger_flush(filark_trigger *t, filark_trigger_record *d_records, int64_t capacity,
+                                   unsigned long long *d_count, filark_stream_t stream);
+filark_status filark_trigger_reset(filark_trigger *t, filark_stream_t stream);
+filark_status filark_trigger_destroy(filark_trigger *t);   /* NULL ok */
+
+size_t filark_events_work_bytes(int64_t n_triggers, int n_channels);
+filark_status filark_events_merge(const filark_trigger_record *d_triggers, int64_t n_triggers, int n_channels,
+                                  filark_event *d_events, int64_t capacity, unsigned long long *d_n_events,
+                                  void *d_work, size_t work_bytes, filark_stream_t stream);
+
 /* Message for the last error returned to this thread ("" if none). */
 const char *filark_last_error_string(void);
 

@@ -48,7 +48,11 @@ EXPORTED = (
     "filark_batch_create", "filark_batch_push", "filark_batch_tune", "filark_batch_set_launch",
     "filark_batch_reset_state", "filark_batch_sync_status", "filark_batch_get_info", "filark_batch_stream",
     "filark_batch_destroy",
+    "filark_trigger_create", "filark_trigger_push", "filark_trigger_flush", "filark_trigger_reset",
+    "filark_trigger_destroy", "filark_events_work_bytes", "filark_events_merge",
 )
+
+FILARK_TRIGGER_OPEN = 1
 
 
 class filark_chain_config(ct.Structure):
@@ -110,6 +114,15 @@ class filark_batch_info(ct.Structure):
     ]
 
 
+class filark_trigger_record(ct.Structure):
+    _fields_ = [("t_on", ct.c_int64), ("t_off", ct.c_int64), ("channel", ct.c_int32), ("flags", ct.c_int32)]
+
+
+class filark_event(ct.Structure):
+    _fields_ = [("t_on", ct.c_int64), ("t_off", ct.c_int64), ("c_min", ct.c_int32), ("c_max", ct.c_int32),
+                ("n_triggers", ct.c_int32), ("flags", ct.c_int32)]
+
+
 _lock = threading.Lock()
 _lib = None
 
@@ -157,6 +170,14 @@ def load(build_if_missing: bool = True) -> ct.CDLL:
             "filark_batch_get_info": ([vp, ct.POINTER(filark_batch_info)], ct.c_int),
             "filark_batch_stream": ([vp, ct.c_int, ct.POINTER(vp)], ct.c_int),
             "filark_batch_destroy": ([vp], ct.c_int),
+            "filark_trigger_create": ([ct.c_int, ct.c_double, ct.c_double, i64, ct.c_int, ct.POINTER(vp)],
+                                      ct.c_int),
+            "filark_trigger_push": ([vp, vp, i64, i64, vp, i64, vp, vp], ct.c_int),
+            "filark_trigger_flush": ([vp, vp, i64, vp, vp], ct.c_int),
+            "filark_trigger_reset": ([vp, vp], ct.c_int),
+            "filark_trigger_destroy": ([vp], ct.c_int),
+            "filark_events_work_bytes": ([i64, ct.c_int], ct.c_size_t),
+            "filark_events_merge": ([vp, i64, ct.c_int, vp, i64, vp, vp, ct.c_size_t, vp], ct.c_int),
             "filark_iir_ckpt_bytes": ([ct.c_int, ct.c_int, i64, i64], ct.c_size_t),
             "filark_iir_work_bytes": ([ct.c_int, ct.c_int, i64, i64], ct.c_size_t),
             "filark_iir_forward_ckpt": ([vp, ct.c_int, ct.c_int, vp, i64, i64, vp, i64, i64, vp, ct.c_size_t, vp],
@@ -302,6 +323,39 @@ def filark_batch_stream(b, i: int) -> tuple[int, int | None]:
 
 def filark_batch_destroy(b) -> int:
     return load().filark_batch_destroy(b)
+
+
+def filark_trigger_create(n_channels: int, on: float, off: float, max_chunk: int, cuda_device: int):
+    h = ct.c_void_p()
+    st = load().filark_trigger_create(int(n_channels), float(on), float(off), int(max_chunk), int(cuda_device),
+                                      ct.byref(h))
+    return st, h.value
+
+
+def filark_trigger_push(t, d_ratio, ld, n, d_records, capacity, d_count, stream) -> int:
+    return load().filark_trigger_push(t, d_ratio, ld, n, d_records, capacity, d_count, stream)
+
+
+def filark_trigger_flush(t, d_records, capacity, d_count, stream) -> int:
+    return load().filark_trigger_flush(t, d_records, capacity, d_count, stream)
+
+
+def filark_trigger_reset(t, stream) -> int:
+    return load().filark_trigger_reset(t, stream)
+
+
+def filark_trigger_destroy(t) -> int:
+    return load().filark_trigger_destroy(t)
+
+
+def filark_events_work_bytes(n_triggers: int, n_channels: int) -> int:
+    return int(load().filark_events_work_bytes(int(n_triggers), int(n_channels)))
+
+
+def filark_events_merge(d_triggers, n_triggers, n_channels, d_events, capacity, d_n_events, d_work, work_bytes,
+                        stream) -> int:
+    return load().filark_events_merge(d_triggers, n_triggers, n_channels, d_events, capacity, d_n_events, d_work,
+                                      work_bytes, stream)
 
 
 def filark_last_error_string() -> str:

@@ -216,3 +216,82 @@ class Batch:
         out["tuned"] = [dict(cluster=inf.tune_cluster[i], n_clusters=inf.tune_clusters[i], ms=inf.tune_ms[i])
                         for i in range(n)]
         return out
+
+
+class Trigger:
+    """Per-channel hysteresis triggers on a ratio stream (device), with the
+    triggers collected in a device list of `capacity` records."""
+
+    RECORD_WORDS = 3  # int64 words of one filark_trigger_record (24 bytes)
+
+    def __init__(self, n_channels: int, on: float, off: float, max_chunk: int = 4096, capacity: int = 1 << 20,
+                 device: int = 0):
+        import torch
+        abi.load()
+        self.n_channels = int(n_channels)
+        self.capacity = int(capacity)
+        st, h = abi.filark_trigger_create(n_channels, on, off, max_chunk, device)
+        abi.check(st, "filark_trigger_create")
+        self._h = h
+        dev = torch.device("cuda", device)
+        self.records = torch.zeros((self.capacity, self.RECORD_WORDS), dtype=torch.int64, device=dev)
+        self.count = torch.zeros(1, dtype=torch.int64, device=dev)
+
+    def close(self) -> None:
+        if getattr(self, "_h", None):
+            abi.check(abi.filark_trigger_destroy(self._h), "filark_trigger_destroy")
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def push(self, ratio, stream=None) -> None:
+        T = int(ratio.shape[0])
+        ld = int(ratio.stride(0)) if T else self.n_channels
+        st = abi.filark_trigger_push(self._h, _ptr(ratio) if T else None, ld, T, _ptr(self.records), self.capacity,
+                                     _ptr(self.count), _stream_handle(stream))
+        abi.check(st, "filark_trigger_push")
+
+    def flush(self, stream=None) -> None:
+        abi.check(abi.filark_trigger_flush(self._h, _ptr(self.records), self.capacity, _ptr(self.count),
+                                           _stream_handle(stream)), "filark_trigger_flush")
+
+    def reset(self, stream=None) -> None:
+        abi.check(abi.filark_trigger_reset(self._h, _stream_handle(stream)), "filark_trigger_reset")
+        self.count.zero_()
+
+    def triggers(self) -> np.ndarray:
+        """[k][3] = (channel, t_on, t_off, flags folded out) as numpy int64."""
+        n = int(self.count.item())
+        if n > self.capacity:
+            raise RuntimeError(f"{n} triggers exceeded the capacity {self.capacity}")
+        raw = self.records[:n].cpu().numpy()
+        t_on, t_off = raw[:, 0], raw[:, 1]
+        chan = (raw[:, 2] & 0xFFFFFFFF).astype(np.int64)
+        flags = (raw[:, 2] >> 32).astype(np.int64)
+        return np.stack([chan, t_on, t_off, flags], axis=1)
+
+
+def merge_events(records_dev, n_triggers: int, n_channels: int, capacity: int | None = None, stream=None):
+    """Events of the first n_triggers records of a device record tensor (as
+    kept by Trigger): numpy rows (t_on, t_off, c_min, c_max, n_triggers,
+    flags), in the library's (unspecified) order."""
+    import torch
+    dev = records_dev.device
+    cap = int(capacity or max(1, n_triggers))
+    ev = torch.zeros((cap, 4), dtype=torch.int64, device=dev)
+    n_ev = torch.zeros(1, dtype=torch.int64, device=dev)
+    wb = abi.filark_events_work_bytes(n_triggers, n_channels)
+    work = torch.empty(wb + 256, dtype=torch.uint8, device=dev)
+    wp = (work.data_ptr() + 255) // 256 * 256
+    st = abi.filark_events_merge(_ptr(records_dev), n_triggers, n_channels, _ptr(ev), cap, _ptr(n_ev), wp, wb,
+                                 _stream_handle(stream))
+    abi.check(st, "filark_events_merge")
+    m = int(n_ev.item())
+    raw = ev[:min(m, cap)].cpu().numpy()
+    out = np.stack([raw[:, 0], raw[:, 1], raw[:, 2] & 0xFFFFFFFF, raw[:, 2] >> 32,
+                    raw[:, 3] & 0xFFFFFFFF, raw[:, 3] >> 32], axis=1).astype(np.int64)
+    return out, m
