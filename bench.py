@@ -342,6 +342,207 @@ def kernel_sha() -> str:
     return hsh.hexdigest()[:16]
 
 
+# ------------------------------------------------- other workloads (lines) --
+
+def _event_ms(fn, reps: int, stream=None) -> float:
+    import torch
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(reps):
+        fn()
+    e1.record(stream)
+    e1.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def run_batch_workload(args) -> None:
+    """32 independent streams (500..10,000 channels, 200..3,000 samples per
+    push, drawn per stream and push) through one persistent launch per push,
+    after the autotuner picked the launch geometry; against the same pushes
+    made stream by stream through single-stream chains."""
+    import torch
+
+    from paper_2605_20132_gb300 import abi, synth
+    from paper_2605_20132_gb300.chain import Batch, Chain, butter_bandpass
+    cfg = synth.BATCH
+    specs = synth.batch_streams(cfg["seed"], cfg["n_streams"], cfg["channels"], cfg["chunk"])
+    Cs = [s["n_channels"] for s in specs]
+    P = 6
+    T = synth.batch_chunk_lengths(cfg["seed"], cfg["n_streams"], P, cfg["chunk"])
+    sos = butter_bandpass(cfg["order"], *cfg["band"], cfg["fs"])
+    K, ns, nl = cfg["spatial_width"], cfg["sta"], cfg["lta"]
+    tot = T.sum(axis=0)
+    g = torch.Generator(device="cuda").manual_seed(cfg["seed"])
+    xs = [torch.randn((int(tot[i]), C), device="cuda", generator=g) for i, C in enumerate(Cs)]
+    rs = [torch.empty_like(x) for x in xs]
+    offs = np.vstack([np.zeros((1, len(Cs)), dtype=np.int64), np.cumsum(T, axis=0)])
+    views = [[(xs[i][offs[p, i]:offs[p + 1, i]], rs[i][offs[p, i]:offs[p + 1, i]]) for i in range(len(Cs))]
+             for p in range(P)]
+    b = Batch(Cs, sos, cfg["fs"], K, ns, nl, outputs=abi.FILARK_OUT_RATIO, max_chunk=cfg["chunk"][1])
+    info = b.tune([v[0] for v in views[0]], ratios=[v[1] for v in views[0]], timed_pushes=3)
+
+    def step_batch():
+        for p in range(P):
+            b.push([v[0] for v in views[p]], ratios=[v[1] for v in views[p]])
+
+    for _ in range(max(args.warmup, 3)):
+        step_batch()
+    sampler = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
+    with sampler:
+        ms = _event_ms(step_batch, args.steps)
+    b.sync()
+    b.close()
+    chains = [Chain(C, sos, cfg["fs"], K, ns, nl, outputs=abi.FILARK_OUT_RATIO, max_chunk=cfg["chunk"][1])
+              for C in Cs]
+
+    def step_single():
+        for p in range(P):
+            for i in range(len(Cs)):
+                chains[i].push(views[p][i][0], ratio=views[p][i][1])
+
+    for _ in range(3):
+        step_single()
+    ms_single = _event_ms(step_single, args.steps)
+    for c in chains:
+        c.close()
+    units = float((T * np.array(Cs)[None, :]).sum())
+    byts = float(sum(algorithmic_bytes_per_push(Cs[i], int(T[p, i]), sos.shape[0], ns, nl)
+                     for p in range(P) for i in range(len(Cs))))
+    peak, peak_kind = measured_peak_hbm()
+    achieved = byts / (ms / 1e3) / 1e9
+    line = {
+        "workload": cfg["name"], "metric": "channel-samples/s of batched pushes (device-timed)",
+        "value": units / (ms / 1e3), "unit": UNIT, "ms_per_step": ms, "steps": args.steps, "pushes_per_step": P,
+        "single_stream": {"value": units / (ms_single / 1e3), "unit": UNIT, "ms_per_step": ms_single,
+                          "launches_per_step": int(sum(-(-int(t) // 2048) for t in T.ravel() if t))},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                     "peak_kind": peak_kind},
+        "tuner": {"cluster": info["cluster"], "n_clusters": info["n_clusters"], "candidates": info["tuned"]},
+        "gpu_launches": args.steps * P, "dtype": "f32", "data": "synthetic N(0,1) noise generated on the device",
+        "config": {"streams": len(Cs), "channels": int(sum(Cs)), "chunk_range": list(cfg["chunk"]),
+                   "sections": int(sos.shape[0]), "spatial_width": K, "sta": ns, "lta": nl},
+        "clocks": sampler.summary(),
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_adjoint_workload(args) -> None:
+    """Forward with checkpoints + reverse-time adjoint through the order-4
+    bandpass on 2,048 channels x 30,000 samples (checkpoints every 3,000),
+    against the chain's plain forward bandpass on the same record."""
+    import torch
+
+    from paper_2605_20132_gb300 import abi, synth
+    from paper_2605_20132_gb300.chain import Chain, butter_bandpass
+    cfg = synth.ADJOINT
+    C, N, ck = cfg["n_channels"], cfg["n_samples"], cfg["checkpoint"]
+    sos = butter_bandpass(cfg["order"], *cfg["band"], cfg["fs"])
+    S = sos.shape[0]
+    x = torch.from_numpy(synth.adjoint_stream(C, N, cfg["seed"])).cuda()
+    gy = torch.randn_like(x)
+    nb, wb = abi.filark_iir_ckpt_bytes(S, C, N, ck), abi.filark_iir_work_bytes(S, C, N, ck)
+    ckb = torch.empty(nb, dtype=torch.uint8, device="cuda")
+    wk = torch.empty(wb, dtype=torch.uint8, device="cuda")
+    y, gx = torch.empty_like(x), torch.empty_like(x)
+    gs = torch.empty((S, 6), dtype=torch.float64, device="cuda")
+    sh = torch.cuda.current_stream().cuda_stream
+
+    def fwd():
+        abi.check(abi.filark_iir_forward_ckpt(sos, S, C, x.data_ptr(), C, N, y.data_ptr(), C, ck, ckb.data_ptr(),
+                                              nb, sh), "forward")
+
+    def bwd():
+        abi.check(abi.filark_iir_backward(sos, S, C, x.data_ptr(), C, N, gy.data_ptr(), C, ck, ckb.data_ptr(), nb,
+                                          wk.data_ptr(), wb, gx.data_ptr(), C, gs.data_ptr(), sh), "backward")
+
+    def both():
+        fwd()
+        bwd()
+
+    chain = Chain(C, sos, cfg["fs"], 1, 0, 0, outputs=abi.FILARK_OUT_BANDPASS, max_chunk=ck)
+
+    def plain():
+        for t in range(0, N, ck):
+            chain.push(x[t:t + ck], bandpass=y[t:t + ck])
+
+    for f in (fwd, bwd, plain):
+        for _ in range(3):
+            f()
+    sampler = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
+    with sampler:
+        ms_both = _event_ms(both, args.steps)
+    ms_fwd = _event_ms(fwd, args.steps)
+    ms_bwd = _event_ms(bwd, args.steps)
+    ms_plain = _event_ms(plain, args.steps)
+    chain.close()
+    units = C * N
+    line = {
+        "workload": cfg["name"], "metric": "channel-samples/s of forward + adjoint (device-timed)",
+        "value": units / (ms_both / 1e3), "unit": UNIT, "ms_per_step": ms_both, "steps": args.steps,
+        "forward_ckpt_ms": ms_fwd, "backward_ms": ms_bwd,
+        "plain_forward": {"value": units / (ms_plain / 1e3), "unit": UNIT, "ms": ms_plain,
+                          "what": "chain bandpass only, FP32 block scan, pushes of 3,000"},
+        "memory": {"checkpoint_bytes": nb, "work_bytes": wb, "all_intermediates_fp64_bytes": 8 * S * C * N},
+        "dtype": "f64", "data": "synthetic noise + Ricker events (seeded)",
+        "config": {"channels": C, "samples": N, "sections": S, "checkpoint": ck},
+        "clocks": sampler.summary(),
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_trigger_workload(args) -> None:
+    """Triggers (hysteresis 6 / 2) on the paper-scale chain's ratio, 60 pushes
+    of 1,500 samples x 6,000 channels, and the event merge of all of them."""
+    import torch
+
+    from paper_2605_20132_gb300 import abi, synth
+    from paper_2605_20132_gb300.chain import Chain, Trigger, butter_bandpass, merge_events
+    w = workload()
+    C, N, T = w["n_channels"], w["n_samples"], w["chunk"]
+    x = torch.from_numpy(synth.paper_scale_stream(C, N, w["seed"])).cuda()
+    r = torch.empty_like(x)
+    ch = Chain(C, butter_bandpass(w["order"], *w["band"], w["fs"]), w["fs"], w["spatial_width"], w["sta"],
+               w["lta"], outputs=abi.FILARK_OUT_RATIO, max_chunk=T)
+    for t in range(0, N, T):
+        ch.push(x[t:t + T], ratio=r[t:t + T])
+    ch.sync()
+    ch.close()
+    del x
+    tr = Trigger(C, 6.0, 2.0, max_chunk=T, capacity=1 << 22)
+
+    def step():
+        tr.reset()
+        for t in range(0, N, T):
+            tr.push(r[t:t + T])
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    ms = _event_ms(step, args.steps)
+    tr.flush()
+    n = int(tr.count.item())
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    _, m = merge_events(tr.records, n, C)
+    e1.record()
+    e1.synchronize()
+    ms_merge = e0.elapsed_time(e1)
+    tr.close()
+    peak, peak_kind = measured_peak_hbm()
+    byts = 4.0 * C * N   # the ratio is read once; the triggers are a few MB
+    achieved = byts / (ms / 1e3) / 1e9
+    line = {
+        "workload": "trigger-" + w["name"], "metric": "channel-samples/s of trigger extraction (device-timed)",
+        "value": C * N / (ms / 1e3), "unit": UNIT, "ms_per_step": ms, "steps": args.steps,
+        "triggers": n, "events": m, "event_merge_ms": ms_merge,
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                     "peak_kind": peak_kind, "bytes_per_step": byts},
+        "gpu_launches": 3 * (N // T) * args.steps, "dtype": "u8/i64 (comparisons, indices)",
+        "data": "the paper-scale chain's ratio on synthetic input", "config": {"on": 6.0, "off": 2.0},
+    }
+    print(json.dumps(line), flush=True)
+
+
 def ncu_case() -> None:
     """Small profiling case for ncu captures: the paper-scale chain on 6,000
     channels, 4 pushes of 1,500 samples of Gaussian noise (144 MB of input,
@@ -371,9 +572,17 @@ def main() -> None:
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="filark", choices=["filark", "reference"])
     ap.add_argument("--ncu-case", action="store_true", help="run the small profiling case only")
+    ap.add_argument("--workload", default="chain", choices=["chain", "batch", "adjoint", "trigger"],
+                    help="chain: the paper-scale chain (the benchmark line); the others print their own line")
     args = ap.parse_args()
     if args.ncu_case:
         ncu_case()
+        return
+    if args.workload != "chain":
+        import torch
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        {"batch": run_batch_workload, "adjoint": run_adjoint_workload,
+         "trigger": run_trigger_workload}[args.workload](args)
         return
     args.warmup = max(args.warmup, 3) if args.impl == "filark" else args.warmup
     world = int(os.environ.get("WORLD_SIZE", "1"))
