@@ -102,6 +102,25 @@ filark_status zero_state(filark_chain *h, cudaStream_t stream) {
     return FILARK_OK;
 }
 
+// The modal carries keep each state entry as a double-float {hi, lo} pair of
+// floats in its 8-byte slot; the checkpoint format is FP64.
+void decode_df_state(std::vector<double> &m) {
+    for (double &v : m) {
+        float hl[2];
+        std::memcpy(hl, &v, sizeof(hl));
+        v = (double)hl[0] + (double)hl[1];
+    }
+}
+
+void encode_df_state(std::vector<double> &m) {
+    for (double &v : m) {
+        float hl[2];
+        hl[0] = (float)v;
+        hl[1] = (float)(v - (double)hl[0]);
+        std::memcpy(&v, hl, sizeof(hl));
+    }
+}
+
 filark_status check_device_status(filark_chain *h) {
     if (h->sticky != FILARK_OK) return fail(FILARK_ESTATE, "chain is in an error state; call filark_chain_reset_state");
     int st = *(volatile int *)h->status_host;
@@ -448,6 +467,7 @@ filark_status filark_chain_get_state(filark_chain *h, void *host_buf, size_t *by
         std::vector<double> m((size_t)C * (size_t)(2 * NS));
         e = cudaMemcpy(m.data(), h->iir[h->parity], sizeof(double) * m.size(), cudaMemcpyDeviceToHost);
         if (e != cudaSuccess) return fail_cuda(e, "get_state: copy");
+        if (!h->plan.dense) decode_df_state(m);
         const int n2 = 2 * S;
         std::vector<double> canon((size_t)C * (size_t)n2);
         for (int c = 0; c < C; ++c)
@@ -512,6 +532,7 @@ filark_status filark_chain_set_state(filark_chain *h, const void *host_buf, size
                     acc += h->plan.Winv[(size_t)r * n2 + q] * (long double)canon[(size_t)c * n2 + q];
                 m[(size_t)c * (2 * NS) + r] = (double)acc;
             }
+        if (!h->plan.dense) encode_df_state(m);
         e = cudaMemcpy(h->iir[0], m.data(), sizeof(double) * m.size(), cudaMemcpyHostToDevice);
         if (e != cudaSuccess) return fail_cuda(e, "set_state: copy");
     }

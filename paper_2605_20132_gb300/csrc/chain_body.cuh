@@ -20,7 +20,8 @@
 //      end state e = K x from zero state (FP32, tables are FFMA constant
 //      operands);
 //   2. per (channel, slot): carry scan m_{j+1} = M m_j + e_j -- FP32 inside the
-//      CTA, FP64 across the CTAs of the cluster and across launches;
+//      CTA and from the CTAs of the cluster, double-float for the state carried
+//      across launches (the dense mode carries in FP64);
 //   3. fix-up y_bp = y_loc + G m_j, written back in place;
 //   4. spatial mean over the 2h+1 neighbouring columns, cf = y_sp^2, written to
 //      the detector's history ring and kept in place;
@@ -68,9 +69,9 @@ __device__ __forceinline__ void acc_nonneg(float &s, float &c, float v) {
     s = t;
 }
 
-// Double-float (hi + lo) arithmetic for the detector's carried sums: exact
-// error-free additions (Knuth's TwoSum) keep ~48 significant bits without
-// the FP64 pipe.
+// Double-float (hi + lo) arithmetic for the carried IIR state and the
+// detector's carried sums: error-free additions (Knuth's TwoSum) and FMA-based
+// products keep ~48 significant bits without the FP64 pipe (1/64 rate).
 struct DF {
     float hi, lo;
 };
@@ -83,6 +84,22 @@ __device__ __forceinline__ DF df_add(DF a, DF b) {
     return DF{hi, lo - (hi - s)};
 }
 __device__ __forceinline__ DF df_neg(DF a) { return DF{-a.hi, -a.lo}; }
+// a * b with the leading product exact (FMA), ~2^-46 relative
+__device__ __forceinline__ DF df_mul(DF a, DF b) {
+    const float p = a.hi * b.hi;
+    float e = fmaf(a.hi, b.hi, -p);
+    e = fmaf(a.hi, b.lo, e);
+    e = fmaf(a.lo, b.hi, e);
+    const float hi = p + e;
+    return DF{hi, e - (hi - p)};
+}
+__device__ __forceinline__ DF df_mul_f(DF a, float b) {
+    const float p = a.hi * b;
+    float e = fmaf(a.hi, b, -p);
+    e = fmaf(a.lo, b, e);
+    const float hi = p + e;
+    return DF{hi, e - (hi - p)};
+}
 // a + c for a, c >= 0 held as compensated sums (s, comp): exact as DF
 __device__ __forceinline__ DF df_from_sum(float s, float comp) {
     const float hi = s + comp;
@@ -517,44 +534,51 @@ __device__ __forceinline__ void chain_body(const ChainParams &p, const ChainUnit
                 g0 = fmaf(Pq[0], a0, fmaf(Pq[1], a1, g0));
                 g1 = fmaf(Pq[2], a0, fmaf(Pq[3], a1, g1));
             }
-            // carried state of the launch (FP64), advanced to this CTA's start
-            double c0d = 0.0, c1d = 0.0;
+            // carried state of the launch (double-float hi/lo pairs); the
+            // start of this CTA, Phi^r c + g, only feeds the FP32 block carries
+            float2 c0 = make_float2(0.f, 0.f), c1 = make_float2(0.f, 0.f);
             if (cgs >= 0 && cgs < cu.C) {
-                const double *src = cu.halo_in ? cu.halo_in + ((long long)tx * kWT + sc) * (2 * NS)
-                                               : cu.iir_in + (long long)cgs * (2 * NS);
-                c0d = src[2 * s];
-                c1d = src[2 * s + 1];
+                const float2 *src = reinterpret_cast<const float2 *>(
+                    cu.halo_in ? cu.halo_in + ((long long)tx * kWT + sc) * (2 * NS)
+                               : cu.iir_in + (long long)cgs * (2 * NS));
+                c0 = src[2 * s];
+                c1 = src[2 * s + 1];
             }
-            const double *Pr = p.PhiPow[r][s];
-            double d0 = fma(Pr[0], c0d, fma(Pr[1], c1d, (double)g0));
-            double d1 = fma(Pr[2], c0d, fma(Pr[3], c1d, (double)g1));
-            if (p.all32) {
-                d0 = (float)d0;
-                d1 = (float)d1;
-            }
+            const float *Pr = p.PhiPow32[r][s];
+            const float d0 = fmaf(Pr[0], c0.x, fmaf(Pr[1], c1.x, g0));
+            const float d1 = fmaf(Pr[2], c0.x, fmaf(Pr[3], c1.x, g1));
             const bool own = sc >= p.HP && sc < p.HP + p.Wout;
             if (last_cta && cgs >= 0 && cgs < cu.C && (own || cu.halo_out)) {
-                // launch end state: PhiTot c + PhiLast g + own aggregate (FP64)
-                const double a0 = AGG[(2 * s) * kWT + sc], a1 = AGG[(2 * s + 1) * kWT + sc];
-                const double *PT = cu.PhiTot[s], *PL = cu.PhiLast[s];
-                double u0 = fma(PT[0], c0d, fma(PT[1], c1d, fma(PL[0], (double)g0, fma(PL[1], (double)g1, a0))));
-                double u1 = fma(PT[2], c0d, fma(PT[3], c1d, fma(PL[2], (double)g0, fma(PL[3], (double)g1, a1))));
+                // launch end state: PhiTot c + PhiLast g + own aggregate, in
+                // double-float (~48 bits) on the FP32 pipe
+                const float a0 = AGG[(2 * s) * kWT + sc], a1 = AGG[(2 * s + 1) * kWT + sc];
+                const float *PTh = cu.PhiTotHi[s], *PTl = cu.PhiTotLo[s];
+                const float *PLh = cu.PhiLastHi[s], *PLl = cu.PhiLastLo[s];
+                const DF C0{c0.x, c0.y}, C1{c1.x, c1.y};
+                DF u0 = df_add(df_add(df_mul(DF{PTh[0], PTl[0]}, C0), df_mul(DF{PTh[1], PTl[1]}, C1)),
+                               df_add(df_add(df_mul_f(DF{PLh[0], PLl[0]}, g0), df_mul_f(DF{PLh[1], PLl[1]}, g1)),
+                                      DF{a0, 0.f}));
+                DF u1 = df_add(df_add(df_mul(DF{PTh[2], PTl[2]}, C0), df_mul(DF{PTh[3], PTl[3]}, C1)),
+                               df_add(df_add(df_mul_f(DF{PLh[2], PLl[2]}, g0), df_mul_f(DF{PLh[3], PLl[3]}, g1)),
+                                      DF{a1, 0.f}));
                 if (p.all32) {
-                    u0 = (float)u0;
-                    u1 = (float)u1;
+                    u0 = DF{u0.hi, 0.f};
+                    u1 = DF{u1.hi, 0.f};
                 }
                 if (own) {
-                    cu.iir_out[(long long)cgs * (2 * NS) + 2 * s] = u0;
-                    cu.iir_out[(long long)cgs * (2 * NS) + 2 * s + 1] = u1;
+                    float2 *dst = reinterpret_cast<float2 *>(cu.iir_out + (long long)cgs * (2 * NS));
+                    dst[2 * s] = make_float2(u0.hi, u0.lo);
+                    dst[2 * s + 1] = make_float2(u1.hi, u1.lo);
                 }
                 if (cu.halo_out) {
-                    cu.halo_out[((long long)tx * kWT + sc) * (2 * NS) + 2 * s] = u0;
-                    cu.halo_out[((long long)tx * kWT + sc) * (2 * NS) + 2 * s + 1] = u1;
+                    float2 *dst = reinterpret_cast<float2 *>(cu.halo_out + ((long long)tx * kWT + sc) * (2 * NS));
+                    dst[2 * s] = make_float2(u0.hi, u0.lo);
+                    dst[2 * s + 1] = make_float2(u1.hi, u1.lo);
                 }
             }
             // block start states (FP32), written over the block end states
             const float m00 = p.tab.M[s][0], m01 = p.tab.M[s][1], m10 = p.tab.M[s][2], m11 = p.tab.M[s][3];
-            float f0 = (float)d0, f1 = (float)d1;
+            float f0 = d0, f1 = d1;
             for (int j = 0; j < nb; ++j) {
                 float *pe0 = &E[(j * 2 * NS + 2 * s) * kWT + sc];
                 float *pe1 = pe0 + kWT;

@@ -52,7 +52,10 @@ struct ChainUnit {
     long long ldx;
     float *ratio, *bp, *sp;             // launch outputs (row 0 = first sample)
     long long ldo;
-    const double *iir_in;               // [C][2*NS] carried IIR state (internal basis)
+    // [C][2*NS] carried IIR state in the internal basis, 8 bytes per entry:
+    // modal carries store double-float {hi, lo} float pairs, the dense carry
+    // stores FP64
+    const double *iir_in;
     double *iir_out;
     const double *det_in;               // [C][4] {sta_sum, lta_sum, 1 + index of last nonzero cf (0 = none), 0}
     double *det_out;
@@ -69,18 +72,17 @@ struct ChainUnit {
     int slot_n0;                        // n0 mod Q
     int C, T, nblk, Lr, R;
     int x_vec4, o_vec4;                 // float4 access allowed (input, outputs)
-    double PhiLast[kMaxSlots][4];       // transition over the launch's last CTA, FP64
-    double PhiTot[kMaxSlots][4];        // PhiLast * Phi^(R-1): launch start -> launch end
+    // transition over the launch's last CTA, and PhiTot = PhiLast * Phi^(R-1)
+    // (launch start -> launch end), as double-float hi/lo pairs
+    float PhiLastHi[kMaxSlots][4], PhiLastLo[kMaxSlots][4];
+    float PhiTotHi[kMaxSlots][4], PhiTotLo[kMaxSlots][4];
     float Mr32[kMaxSlots][4];           // M^Lr of the ragged last block (Lr < L), FP32
 };
 
 // Everything else is fixed for a chain (for a batch: shared by its streams).
 struct ChainParams {
     Tables32 tab;
-    double Phi[kMaxSlots][4];           // M^(L*kNB): one full CTA, FP64
-    double ML64[kMaxSlots][4];          // M^L, FP64
-    double PhiPow[kMaxCluster][kMaxSlots][4];  // Phi^r = M^(L*kNB*r), FP64
-    float PhiPow32[kMaxCluster][kMaxSlots][4]; // the same in FP32
+    float PhiPow32[kMaxCluster][kMaxSlots][4]; // Phi^r = M^(L*kNB*r), FP32
     int hw, HP, Wout;
     int ns, nl;
     float ratio_scale;                  // nl / ns

@@ -138,8 +138,7 @@ double probe_modal(const Plan &pl, const std::vector<Section> &secs) {
     // emulation
     std::vector<double> yemu((size_t)N);
     std::vector<double> state((size_t)R2, 0.0);
-    double Phi[kMaxSlots][4], Mr[kMaxSlots][4];
-    pl.slot_power(kL * kNB, Phi);
+    double Mr[kMaxSlots][4];
     const Tables32 &tb = pl.tab;
     int base = 0;
     for (int T : launches) {
@@ -199,23 +198,34 @@ double probe_modal(const Plan &pl, const std::vector<Section> &secs) {
         }
         std::vector<float> mstart((size_t)nblk * R2);
         std::vector<double> newstate((size_t)R2);
+        const double (*PP)[4] = pl.power_cached_cta(R - 1);
         for (int rr = 0; rr < R; ++rr) {
             int j0 = rr * kNB, nb = std::min(kNB, nblk - j0);
+            const double (*Pr)[4] = pl.power_cached_cta(rr);
             for (int s = 0; s < NS; ++s) {
-                double d0 = state[(size_t)2 * s], d1 = state[(size_t)2 * s + 1];
+                // as the kernel: earlier CTAs' aggregates through their own FP32
+                // powers, the carried state's leading float through Phi^rr
+                float g0 = 0.f, g1 = 0.f;
                 for (int q = 0; q < rr; ++q) {
-                    double g0 = agg[(size_t)q * R2 + 2 * s], g1 = agg[(size_t)q * R2 + 2 * s + 1];
-                    double t0 = std::fma(Phi[s][0], d0, std::fma(Phi[s][1], d1, g0));
-                    double t1 = std::fma(Phi[s][2], d0, std::fma(Phi[s][3], d1, g1));
-                    d0 = t0;
-                    d1 = t1;
+                    const double (*Pq)[4] = pl.power_cached_cta(rr - 1 - q);
+                    const float a0 = agg[(size_t)q * R2 + 2 * s], a1 = agg[(size_t)q * R2 + 2 * s + 1];
+                    g0 = std::fmaf((float)Pq[s][0], a0, std::fmaf((float)Pq[s][1], a1, g0));
+                    g1 = std::fmaf((float)Pq[s][2], a0, std::fmaf((float)Pq[s][3], a1, g1));
                 }
+                const double c0 = state[(size_t)2 * s], c1 = state[(size_t)2 * s + 1];
+                const float c0h = (float)c0, c1h = (float)c1;
+                float f0 = std::fmaf((float)Pr[s][0], c0h, std::fmaf((float)Pr[s][1], c1h, g0));
+                float f1 = std::fmaf((float)Pr[s][2], c0h, std::fmaf((float)Pr[s][3], c1h, g1));
                 if (rr == R - 1) {
-                    double g0 = agg[(size_t)rr * R2 + 2 * s], g1 = agg[(size_t)rr * R2 + 2 * s + 1];
-                    newstate[(size_t)2 * s] = std::fma(PhiLast[s][0], d0, std::fma(PhiLast[s][1], d1, g0));
-                    newstate[(size_t)2 * s + 1] = std::fma(PhiLast[s][2], d0, std::fma(PhiLast[s][3], d1, g1));
+                    // end state PhiTot c + PhiLast g + own aggregate (double-float
+                    // in the kernel, double here)
+                    const double *a = PhiLast[s], *b = PP[s];
+                    const double T0 = a[0] * b[0] + a[1] * b[2], T1 = a[0] * b[1] + a[1] * b[3];
+                    const double T2 = a[2] * b[0] + a[3] * b[2], T3 = a[2] * b[1] + a[3] * b[3];
+                    const double o0 = agg[(size_t)rr * R2 + 2 * s], o1 = agg[(size_t)rr * R2 + 2 * s + 1];
+                    newstate[(size_t)2 * s] = T0 * c0 + T1 * c1 + (a[0] * g0 + a[1] * g1) + o0;
+                    newstate[(size_t)2 * s + 1] = T2 * c0 + T3 * c1 + (a[2] * g0 + a[3] * g1) + o1;
                 }
-                float f0 = (float)d0, f1 = (float)d1;
                 const float *M = tb.M[s];
                 for (int jj = 0; jj < nb; ++jj) {
                     int j = j0 + jj;
@@ -707,16 +717,17 @@ void set_unit_geometry(const Plan &plan, int Tl, ChainUnit &u) {
         const double (*pr)[4] = plan.power_cached(u.Lr);
         const double (*pp)[4] = plan.power_cached_cta(u.R - 1);
         for (int s = 0; s < kMaxSlots; ++s) {
-            for (int q = 0; q < 4; ++q) {
-                u.PhiLast[s][q] = pl[s][q];
-                u.Mr32[s][q] = (float)pr[s][q];
-            }
             // PhiTot = PhiLast * Phi^(R-1) (2x2 per slot)
             const double *a = pl[s], *b = pp[s];
-            u.PhiTot[s][0] = a[0] * b[0] + a[1] * b[2];
-            u.PhiTot[s][1] = a[0] * b[1] + a[1] * b[3];
-            u.PhiTot[s][2] = a[2] * b[0] + a[3] * b[2];
-            u.PhiTot[s][3] = a[2] * b[1] + a[3] * b[3];
+            const double tot[4] = {a[0] * b[0] + a[1] * b[2], a[0] * b[1] + a[1] * b[3],
+                                   a[2] * b[0] + a[3] * b[2], a[2] * b[1] + a[3] * b[3]};
+            for (int q = 0; q < 4; ++q) {
+                u.Mr32[s][q] = (float)pr[s][q];
+                u.PhiLastHi[s][q] = (float)pl[s][q];
+                u.PhiLastLo[s][q] = (float)(pl[s][q] - (double)u.PhiLastHi[s][q]);
+                u.PhiTotHi[s][q] = (float)tot[q];
+                u.PhiTotLo[s][q] = (float)(tot[q] - (double)u.PhiTotHi[s][q]);
+            }
         }
     }
 }
@@ -725,15 +736,10 @@ void set_static_params(const Plan &plan, int hw, int HP, int Wout, int ns, int n
                        ChainParams &p) {
     std::memset(&p, 0, sizeof(p));
     p.tab = plan.tab;
-    plan.slot_power(kL * kNB, p.Phi);
-    plan.slot_power(kL, p.ML64);
     for (int r = 0; r < kMaxCluster; ++r) {
         const double (*pr)[4] = plan.power_cached_cta(r);
         for (int s = 0; s < kMaxSlots; ++s)
-            for (int q = 0; q < 4; ++q) {
-                p.PhiPow[r][s][q] = pr[s][q];
-                p.PhiPow32[r][s][q] = (float)pr[s][q];
-            }
+            for (int q = 0; q < 4; ++q) p.PhiPow32[r][s][q] = (float)pr[s][q];
     }
     p.hw = hw;
     p.HP = HP;
