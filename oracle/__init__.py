@@ -101,6 +101,15 @@ def _bind(path: str, long_double: bool):
         f = lib.ora_events_merge
         f.argtypes = [_lp, _lp, _lp, ct.c_long, _lp]
         f.restype = ct.c_long
+        f = lib.ora_top_new
+        f.argtypes = [ct.c_int, ct.c_int, ct.c_int, _dp, ct.c_double]
+        f.restype = ct.c_void_p
+        f = lib.ora_top_free
+        f.argtypes = [ct.c_void_p]
+        f.restype = None
+        f = lib.ora_top_push
+        f.argtypes = [ct.c_void_p, _fp, ct.c_long, ct.c_long, _dp, ct.c_long]
+        f.restype = None
     return lib, p
 
 
@@ -302,3 +311,36 @@ def events_merge(records: np.ndarray) -> np.ndarray:
     ev = np.zeros((max(1, r.shape[0]), 5), dtype=np.int64)
     m = _fn("events_merge")(_ptr(rc, _lp), _ptr(ron, _lp), _ptr(roff, _lp), r.shape[0], _ptr(ev, _lp))
     return ev[:m].copy()
+
+
+# ------------------------------------------------------- temporal operators --
+
+TOP_FIR, TOP_MEAN, TOP_AGC, TOP_EMA = 0, 1, 2, 3
+
+
+class TemporalOp:
+    """Stateful temporal operator per channel (x before the stream start is 0):
+    FIR y = sum_k h[k] x[n-k]; MEAN y = window mean of x over the last w
+    samples; AGC y = x / (window mean of |x|) (0 if that mean is 0); EMA e =
+    (1-a) e + a x^2, y = x / sqrt(e) (0 if e = 0)."""
+
+    def __init__(self, C: int, kind: int, length: int = 1, taps=None, alpha: float = 0.0):
+        lib, _ = _load(False)
+        self._f = {k: getattr(lib, "ora_" + k) for k in ("top_new", "top_free", "top_push")}
+        self.C = int(C)
+        h = None if taps is None else np.ascontiguousarray(taps, dtype=np.float64)
+        self._h = self._f["top_new"](self.C, int(kind), int(length), _ptr(h), float(alpha))
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h:
+            self._f["top_free"](h)
+            self._h = None
+
+    def push(self, x: np.ndarray) -> np.ndarray:
+        x = np.ascontiguousarray(x, dtype=np.float32)
+        if x.ndim != 2 or x.shape[1] != self.C:
+            raise ValueError("x must be [T][C]")
+        y = np.zeros(x.shape, dtype=np.float64)
+        self._f["top_push"](self._h, _ptr(x, _fp), self.C, x.shape[0], _ptr(y), self.C)
+        return y

@@ -37,6 +37,10 @@
  *     and wherever the long window holds only zeros.
  *   - Adjoint of the SOS cascade (gradients with respect to the input and to
  *     every coefficient of every section), for the differentiable filter.
+ *   - Stateful temporal operators of the same streaming contract (Table 1,
+ *     temporal filters and amplitude operators): a realtime FIR with its input
+ *     history carried across pushes (overlap-save), a running mean and a
+ *     running AGC over a trailing window, and an EMA power equalisation.
  *   - Trigger and event extraction on the detector ratio (Sec. 3.4, threshold
  *     detectors behind the monitor interface): a per-channel on/off
  *     hysteresis state carried across pushes; every maximal run of the "on"
@@ -659,5 +663,93 @@ long ora_events_merge(const long *rc, const long *ron, const long *roff, long n,
     free(ord);
     free(root_ev);
     return m;
+}
+#endif
+
+
+/* ------------------------------------------------------------------------
+ * Temporal operators, per channel, x[n < 0] = 0, state carried across pushes:
+ *   FIR      y[n] = sum_{k=0}^{M-1} h[k] x[n-k]
+ *   MEAN     y[n] = (1/w) sum_{k=0}^{w-1} x[n-k]
+ *   AGC      g[n] = (1/w) sum_{k=0}^{w-1} |x[n-k]|;  y[n] = x[n] / g[n] (0 if g = 0)
+ *   EMA      e[n] = (1-a) e[n-1] + a x[n]^2, e[-1] = 0;
+ *            y[n] = x[n] / sqrt(e[n]) (0 if e = 0)
+ * ------------------------------------------------------------------------ */
+#ifndef ORA_LONG_DOUBLE
+typedef struct {
+    int C, kind, M;     /* kind 0 FIR, 1 MEAN, 2 AGC, 3 EMA; M = taps or window */
+    double a;           /* EMA coefficient */
+    double *h;          /* FIR taps */
+    double *hist;       /* [M][C] last M values of x (FIR, MEAN) or |x| (AGC), ring */
+    double *sum;        /* [C] window sums (MEAN, AGC) */
+    double *e;          /* [C] EMA state */
+    long n;
+} ora_top_t;
+
+void *ora_top_new(int C, int kind, int M, const double *h, double a)
+{
+    ora_top_t *t = (ora_top_t *)calloc(1, sizeof(ora_top_t));
+    t->C = C;
+    t->kind = kind;
+    t->M = M > 0 ? M : 1;
+    t->a = a;
+    t->h = (double *)calloc((size_t)t->M, sizeof(double));
+    if (h) memcpy(t->h, h, sizeof(double) * (size_t)t->M);
+    t->hist = (double *)calloc((size_t)t->M * (size_t)C, sizeof(double));
+    t->sum = (double *)calloc((size_t)C, sizeof(double));
+    t->e = (double *)calloc((size_t)C, sizeof(double));
+    return t;
+}
+
+void ora_top_free(void *p)
+{
+    ora_top_t *t = (ora_top_t *)p;
+    if (!t) return;
+    free(t->h); free(t->hist); free(t->sum); free(t->e);
+    free(t);
+}
+
+/* value of the history ring for sample m (0 before the stream start) */
+static double top_hist(const ora_top_t *t, int c, long m)
+{
+    if (m < 0) return 0;
+    return t->hist[(size_t)(m % t->M) * (size_t)t->C + (size_t)c];
+}
+
+void ora_top_push(void *p, const float *x, long ld, long T, double *y, long ldy)
+{
+    ora_top_t *t = (ora_top_t *)p;
+    for (long i = 0; i < T; ++i) {
+        const long n = t->n + i;
+        for (int c = 0; c < t->C; ++c) {
+            const double v = (double)x[i * ld + c];
+            double out = 0;
+            if (t->kind == 0) {
+                /* store first: the k = 0 term is the current sample */
+                t->hist[(size_t)(n % t->M) * (size_t)t->C + (size_t)c] = v;
+                double acc = 0;
+                for (int k = 0; k < t->M; ++k) acc += t->h[k] * top_hist(t, c, n - k);
+                out = acc;
+            } else if (t->kind == 1 || t->kind == 2) {
+                const double u = t->kind == 1 ? v : fabs(v);
+                const double old = top_hist(t, c, n - t->M);
+                t->hist[(size_t)(n % t->M) * (size_t)t->C + (size_t)c] = u;
+                t->sum[c] += u - old;
+                if (n % 4096 == 4095) {   /* re-sum the window exactly from time to time */
+                    double s = 0;
+                    for (long m = n - t->M + 1; m <= n; ++m) s += top_hist(t, c, m);
+                    t->sum[c] = s;
+                }
+                const double g = t->sum[c] / (double)t->M;
+                if (t->kind == 1) out = g;
+                else out = g > 0 ? v / g : 0;
+            } else {
+                t->e[c] = (1 - t->a) * t->e[c] + t->a * v * v;
+                out = t->e[c] > 0 ? v / sqrt(t->e[c]) : 0;
+            }
+            y[i * ldy + c] = out;
+        }
+    }
+    t->n += T;
 }
 #endif

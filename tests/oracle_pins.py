@@ -437,6 +437,103 @@ def pin_events_vs_flood_fill(ora):
         worst = max(worst, 0.0 if np.array_equal(ev, ref) else 1.0)
     return worst, 0.0
 
+
+# ----------------------------------------------------- temporal-op pins --
+
+def _top_run(ora, x, kind, length=1, taps=None, alpha=0.0, chunks=None):
+    op = ora.TemporalOp(x.shape[1], kind, length, taps, alpha)
+    if chunks is None:
+        return op.push(x)
+    out, pos = [], 0
+    for k in chunks:
+        out.append(op.push(x[pos:pos + k]))
+        pos += k
+    return np.concatenate(out)
+
+
+def pin_fir_vs_convolution(ora):
+    """Realtime FIR: impulses give the taps back, and random input pushed in
+    random chunks equals numpy's full convolution truncated to the input
+    length (brute force, independent code)."""
+    rng = np.random.default_rng(41)
+    worst = 0.0
+    for M in (1, 2, 7, 64):
+        h = rng.standard_normal(M)
+        x = np.zeros((3 * M + 5, 2), dtype=np.float32)
+        x[3, 0] = 1.0
+        y = _top_run(ora, x, ora.TOP_FIR, M, h)
+        worst = _worst(worst, float(np.max(np.abs(y[3:3 + M, 0] - h))))
+        worst = _worst(worst, float(np.max(np.abs(y[:3, 0]))) + float(np.max(np.abs(y[:, 1]))))
+        x = rng.standard_normal((500, 3)).astype(np.float32)
+        chunks, pos = [], 0
+        while pos < 500:
+            k = int(rng.integers(1, 90))
+            chunks.append(min(k, 500 - pos))
+            pos += chunks[-1]
+        y = _top_run(ora, x, ora.TOP_FIR, M, h, chunks=chunks)
+        for c in range(3):
+            ref = np.convolve(x[:, c].astype(np.float64), h)[:500]
+            worst = _worst(worst, normwise_err(y[:, c:c + 1], ref[:, None]))
+    return worst, 1e-13
+
+
+def pin_window_ops_literal(ora):
+    """Running mean and AGC against literal window sums on random input in
+    random chunks (past the re-summation period), plus closed forms for a
+    constant: mean ramps as c (n+1)/w then stays c; AGC of +-c is w/(n+1) in
+    magnitude during the ramp, then +-1."""
+    rng = np.random.default_rng(43)
+    worst = 0.0
+    N, w = 9000, 37
+    x = (rng.standard_normal((N, 2)) * rng.uniform(0.1, 3.0, (N, 1))).astype(np.float32)
+    x[5000:5100, 0] = 0.0
+    chunks = [int(k) for k in rng.integers(1, 700, 40)]
+    chunks = [k for k in np.diff(np.unique(np.r_[0, np.cumsum(chunks), N].clip(0, N)))]
+    mean = _top_run(ora, x, ora.TOP_MEAN, w, chunks=chunks)
+    agc = _top_run(ora, x, ora.TOP_AGC, w, chunks=chunks)
+    xd = x.astype(np.float64)
+    pad = np.vstack([np.zeros((w - 1, 2)), xd])
+    for n in range(0, N, 7):
+        win = pad[n:n + w]
+        m = win.sum(axis=0) / w
+        g = np.abs(win).sum(axis=0) / w
+        a = np.where(g > 0, xd[n] / np.where(g > 0, g, 1), 0.0)
+        worst = _worst(worst, float(np.max(np.abs(mean[n] - m))) / 3.0)
+        worst = _worst(worst, float(np.max(np.abs(agc[n] - a) / np.maximum(1.0, np.abs(a)))))
+    c = np.full((3 * w, 1), 2.5, dtype=np.float32)
+    c[1::2] *= -1
+    m = _top_run(ora, np.abs(c), ora.TOP_MEAN, w)[:, 0]
+    n = np.arange(3 * w)
+    worst = _worst(worst, float(np.max(np.abs(m - 2.5 * np.minimum(n + 1, w) / w))))
+    a = _top_run(ora, c, ora.TOP_AGC, w)[:, 0]
+    worst = _worst(worst, float(np.max(np.abs(np.abs(a) - w / np.minimum(n + 1, w)))))
+    worst = _worst(worst, float(np.max(np.abs(np.sign(a) - np.sign(c[:, 0])))))
+    return worst, 1e-11
+
+
+def pin_ema_closed_forms(ora):
+    """EMA power equalisation: a constant c gives e[n] = c^2 (1 - (1-a)^(n+1))
+    and y = 1 / sqrt(1 - (1-a)^(n+1)); an impulse gives y = 1/sqrt(a) then 0;
+    chunking does not change the output."""
+    worst = 0.0
+    for a in (0.5, 0.01, 1e-4):
+        n = np.arange(3000)
+        y = _top_run(ora, np.full((3000, 1), -1.7, dtype=np.float32), ora.TOP_EMA, alpha=a)[:, 0]
+        ref = -1.0 / np.sqrt(1.0 - (1.0 - a) ** (n + 1))
+        worst = _worst(worst, float(np.max(np.abs(y - ref) / np.abs(ref))))
+        x = np.zeros((50, 1), dtype=np.float32)
+        x[4] = 3.0
+        y = _top_run(ora, x, ora.TOP_EMA, alpha=a)[:, 0]
+        want = np.zeros(50)
+        want[4] = 1.0 / np.sqrt(a)
+        worst = _worst(worst, float(np.max(np.abs(y - want))) * np.sqrt(a))
+    rng = np.random.default_rng(47)
+    x = rng.standard_normal((2000, 3)).astype(np.float32)
+    whole = _top_run(ora, x, ora.TOP_EMA, alpha=0.003)
+    parts = _top_run(ora, x, ora.TOP_EMA, alpha=0.003, chunks=[1, 999, 3, 997])
+    worst = _worst(worst, 0.0 if np.array_equal(whole, parts) else 1.0)
+    return worst, 1e-12
+
 # ------------------------------------------------------------ adjoint pins --
 
 def _loss_and_grads(ora, sos, x, target):
@@ -537,4 +634,7 @@ ALL_PINS = [
     pin_trigger_closed_forms,
     pin_trigger_last_forcing_sample,
     pin_events_vs_flood_fill,
+    pin_fir_vs_convolution,
+    pin_window_ops_literal,
+    pin_ema_closed_forms,
 ]

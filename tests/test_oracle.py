@@ -98,6 +98,15 @@ MUTANTS = [
     ("events_touching_merge", "if (lo >= hi) continue;", "if (lo > hi) continue;"),
     ("events_skip_a_channel", "if (next >= n || rc[ord[next]] != rc[ord[a]] + 1) continue;",
      "if (next >= n || rc[ord[next]] != rc[ord[a]] + 2) continue;"),
+    ("fir_skip_current", "for (int k = 0; k < t->M; ++k) acc += t->h[k] * top_hist(t, c, n - k);",
+     "for (int k = 0; k < t->M; ++k) acc += t->h[k] * top_hist(t, c, n - k - 1);"),
+    ("window_exit_early", "const double old = top_hist(t, c, n - t->M);",
+     "const double old = top_hist(t, c, n - t->M + 1);"),
+    ("agc_no_abs", "const double u = t->kind == 1 ? v : fabs(v);", "const double u = v;"),
+    ("ema_swapped", "t->e[c] = (1 - t->a) * t->e[c] + t->a * v * v;",
+     "t->e[c] = t->a * t->e[c] + (1 - t->a) * v * v;"),
+    ("window_resum_short", "for (long m = n - t->M + 1; m <= n; ++m) s += top_hist(t, c, m);",
+     "for (long m = n - t->M + 2; m <= n; ++m) s += top_hist(t, c, m);"),
 ]
 
 
