@@ -410,6 +410,39 @@ filark_status filark_events_merge(const filark_trigger_record *d_triggers, int64
                                   filark_event *d_events, int64_t capacity, unsigned long long *d_n_events,
                                   void *d_work, size_t work_bytes, filark_stream_t stream);
 
+/*
+ * Stateful temporal operators on the same streaming contract as the chain
+ * (Sec. 3.4, stateful-compatible operators; Table 1, temporal filters and
+ * amplitude operators): per channel, x before the stream start is zero, the
+ * state is carried across pushes, and the outputs of any sequence of pushes
+ * equal one push of the whole recording.
+ *
+ *   FILARK_TOP_FIR   y[n] = sum_{k<M} h[k] x[n-k]   (realtime FIR; the last M-1
+ *                    inputs are carried, overlap-save); `length` = M <= 512,
+ *                    `taps` = h (host, M doubles, rounded to float)
+ *   FILARK_TOP_MEAN  y[n] = (1/w) sum_{k<w} x[n-k]  (running mean; `length` = w)
+ *   FILARK_TOP_AGC   y[n] = x[n] / ((1/w) sum_{k<w} |x[n-k]|), 0 where that mean
+ *                    is 0 (running AGC; `length` = w)
+ *   FILARK_TOP_EMA   e[n] = (1-a) e[n-1] + a x[n]^2, e[-1] = 0,
+ *                    y[n] = x[n] / sqrt(e[n]), 0 where e = 0 (EMA gain
+ *                    equalisation; `alpha` = a in (0, 1])
+ *
+ * Buffers: time-major float32 [n][ld], ld >= n_channels, device; the output
+ * must not overlap the input.  Window sums are kept as double-float running
+ * prefixes (about 48 significant bits), the EMA state likewise.  Pushes are
+ * asynchronous on `stream`; one operator must not be used concurrently.
+ */
+enum { FILARK_TOP_FIR = 0, FILARK_TOP_MEAN = 1, FILARK_TOP_AGC = 2, FILARK_TOP_EMA = 3 };
+
+typedef struct filark_top filark_top;
+
+filark_status filark_top_create(int kind, int n_channels, int length, const double *taps, double alpha,
+                                int64_t max_chunk, int cuda_device, filark_top **out);
+filark_status filark_top_push(filark_top *t, const float *d_in, int64_t ld_in, int64_t n_samples,
+                              float *d_out, int64_t ld_out, filark_stream_t stream);
+filark_status filark_top_reset(filark_top *t, filark_stream_t stream);
+filark_status filark_top_destroy(filark_top *t);   /* NULL ok */
+
 /* Message for the last error returned to this thread ("" if none). */
 const char *filark_last_error_string(void);
 

@@ -50,7 +50,10 @@ EXPORTED = (
     "filark_batch_destroy",
     "filark_trigger_create", "filark_trigger_push", "filark_trigger_flush", "filark_trigger_reset",
     "filark_trigger_destroy", "filark_events_work_bytes", "filark_events_merge",
+    "filark_top_create", "filark_top_push", "filark_top_reset", "filark_top_destroy",
 )
+
+FILARK_TOP_FIR, FILARK_TOP_MEAN, FILARK_TOP_AGC, FILARK_TOP_EMA = 0, 1, 2, 3
 
 FILARK_TRIGGER_OPEN = 1
 
@@ -178,6 +181,11 @@ def load(build_if_missing: bool = True) -> ct.CDLL:
             "filark_trigger_destroy": ([vp], ct.c_int),
             "filark_events_work_bytes": ([i64, ct.c_int], ct.c_size_t),
             "filark_events_merge": ([vp, i64, ct.c_int, vp, i64, vp, vp, ct.c_size_t, vp], ct.c_int),
+            "filark_top_create": ([ct.c_int, ct.c_int, ct.c_int, vp, ct.c_double, i64, ct.c_int, ct.POINTER(vp)],
+                                  ct.c_int),
+            "filark_top_push": ([vp, vp, i64, i64, vp, i64, vp], ct.c_int),
+            "filark_top_reset": ([vp, vp], ct.c_int),
+            "filark_top_destroy": ([vp], ct.c_int),
             "filark_iir_ckpt_bytes": ([ct.c_int, ct.c_int, i64, i64], ct.c_size_t),
             "filark_iir_work_bytes": ([ct.c_int, ct.c_int, i64, i64], ct.c_size_t),
             "filark_iir_forward_ckpt": ([vp, ct.c_int, ct.c_int, vp, i64, i64, vp, i64, i64, vp, ct.c_size_t, vp],
@@ -356,6 +364,27 @@ def filark_events_merge(d_triggers, n_triggers, n_channels, d_events, capacity, 
                         stream) -> int:
     return load().filark_events_merge(d_triggers, n_triggers, n_channels, d_events, capacity, d_n_events, d_work,
                                       work_bytes, stream)
+
+
+def filark_top_create(kind: int, n_channels: int, length: int, taps, alpha: float, max_chunk: int,
+                      cuda_device: int):
+    """taps: None or a C-contiguous float64 numpy array."""
+    h = ct.c_void_p()
+    st = load().filark_top_create(int(kind), int(n_channels), int(length), None if taps is None else taps.ctypes.data,
+                                  float(alpha), int(max_chunk), int(cuda_device), ct.byref(h))
+    return st, h.value
+
+
+def filark_top_push(t, d_in, ld_in, n, d_out, ld_out, stream) -> int:
+    return load().filark_top_push(t, d_in, ld_in, n, d_out, ld_out, stream)
+
+
+def filark_top_reset(t, stream) -> int:
+    return load().filark_top_reset(t, stream)
+
+
+def filark_top_destroy(t) -> int:
+    return load().filark_top_destroy(t)
 
 
 def filark_last_error_string() -> str:

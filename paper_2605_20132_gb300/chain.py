@@ -295,3 +295,38 @@ def merge_events(records_dev, n_triggers: int, n_channels: int, capacity: int | 
     out = np.stack([raw[:, 0], raw[:, 1], raw[:, 2] & 0xFFFFFFFF, raw[:, 2] >> 32,
                     raw[:, 3] & 0xFFFFFFFF, raw[:, 3] >> 32], axis=1).astype(np.int64)
     return out, m
+
+
+class TemporalOp:
+    """A stateful temporal operator on device streams: FIR, running mean,
+    running AGC or EMA gain equalisation (include/filark.h, filark_top_*)."""
+
+    def __init__(self, kind: int, n_channels: int, length: int = 1, taps=None, alpha: float = 0.0,
+                 max_chunk: int = 4096, device: int = 0):
+        abi.load()
+        self._taps = None if taps is None else np.ascontiguousarray(taps, dtype=np.float64)
+        st, h = abi.filark_top_create(kind, n_channels, length, self._taps, alpha, max_chunk, device)
+        abi.check(st, "filark_top_create")
+        self._h = h
+        self.n_channels = int(n_channels)
+
+    def close(self) -> None:
+        if getattr(self, "_h", None):
+            abi.check(abi.filark_top_destroy(self._h), "filark_top_destroy")
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def push(self, x, out, stream=None) -> None:
+        T = int(x.shape[0])
+        ld_in = int(x.stride(0)) if T else self.n_channels
+        ld_out = int(out.stride(0)) if T else self.n_channels
+        abi.check(abi.filark_top_push(self._h, _ptr(x) if T else None, ld_in, T, _ptr(out) if T else None, ld_out,
+                                      _stream_handle(stream)), "filark_top_push")
+
+    def reset(self, stream=None) -> None:
+        abi.check(abi.filark_top_reset(self._h, _stream_handle(stream)), "filark_top_reset")

@@ -304,6 +304,21 @@ __device__ __forceinline__ void chain_body(const ChainParams &p, const ChainUnit
     const int row0 = blk0 * kL;               // first launch row of this CTA
     const int rows = min(nb * kL, cu.T - row0);
     const bool last_cta = (r == R - 1);
+    if constexpr (DET) {
+        // The long window's exiting cf values come from ring rows written at
+        // least one launch ago: start their HBM -> L2 transfer now, behind the
+        // IIR phases (one 128-byte line per thread; L2 is coherent, so a row
+        // the previous launch is still writing is only fetched early).
+        const int k = tid >> 1;
+        if (k < rows && cu.n0 + row0 + k - p.nl >= 0) {
+            const int slot = (int)((cu.n0 + row0 + k - p.nl) % cu.Q);
+            const int cc = c0 + ((tid & 1) << 5);
+            if (cc < cu.C) {
+                const float *a = cu.ring + (long long)slot * cu.ldr + cc;
+                asm volatile("prefetch.global.L2 [%0];" ::"l"(a));
+            }
+        }
+    }
 
     // ---------------------------------------------------------------- 0. load
     {

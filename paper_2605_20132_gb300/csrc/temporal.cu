@@ -1,0 +1,478 @@
+// Stateful temporal operators on the chain's streaming contract
+// (include/filark.h, filark_top_*): the concatenation of the outputs of any
+// sequence of pushes equals one push of the whole recording, x before the
+// stream start is zero (Sec. 3.4, stateful-compatible operators; Table 1,
+// temporal filters and amplitude operators).
+//
+//   FIR   y[n] = sum_{k<M} h[k] x[n-k]: the last M-1 inputs of every channel
+//         are carried (overlap-save).  CTA = 32 channels x 256 outputs; the
+//         inputs with M-1 rows of history sit in shared memory; each thread
+//         makes 32 consecutive outputs of one channel from a 63-value register
+//         window per 32 taps (FFMA with the taps as constant-bank operands).
+//   MEAN  y[n] = (1/w) sum_{k<w} x[n-k]
+//   AGC   g[n] = (1/w) sum_{k<w} |x[n-k]|, y[n] = x[n] / g[n] (0 if g = 0)
+//         Window sums are differences of a running prefix P of x (or |x|) kept
+//         in double-float (~48 bits) in a ring of w + max_chunk rows: a prefix
+//         kernel (one CTA per 32 channels walks the push in slabs of 32 blocks
+//         x 32 samples: block sums, per-channel prefix over the blocks, the
+//         samples' prefixes) and an output kernel over all samples.
+//   EMA   e[n] = (1-a) e[n-1] + a x[n]^2, y[n] = x[n] / sqrt(e[n]) (0 if e = 0)
+//         One CTA per 32 channels: per 32-sample block the response from a
+//         zero start (FP32), block starts from the carried state through the
+//         powers (1-a)^(32 j), the carried state itself in double-float.
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "filark_internal.h"
+
+using namespace filark;
+
+namespace {
+
+constexpr int kTopCh = 32;          // channels per CTA
+constexpr int kFirRows = 256;       // FIR outputs per CTA
+constexpr int kFirThreads = 256;    // (channel, group of 32 outputs)
+constexpr int kFirMaxTaps = 512;
+constexpr int kScanBlocks = 32;     // blocks of 32 samples per slab (window / EMA kernels)
+constexpr int kScanThreads = kTopCh * kScanBlocks;   // 1024
+constexpr int kSlab = 32 * kScanBlocks;              // 1024 samples
+
+struct DF2 {
+    float hi, lo;
+};
+__device__ __forceinline__ DF2 d_add(DF2 a, DF2 b) {
+    const float s = a.hi + b.hi;
+    const float bb = s - a.hi;
+    const float err = (a.hi - (s - bb)) + (b.hi - bb);
+    const float lo = err + (a.lo + b.lo);
+    const float hi = s + lo;
+    return DF2{hi, lo - (hi - s)};
+}
+__device__ __forceinline__ DF2 d_add_f(DF2 a, float b) { return d_add(a, DF2{b, 0.f}); }
+__device__ __forceinline__ DF2 d_mul(DF2 a, DF2 b) {
+    const float p = a.hi * b.hi;
+    float e = fmaf(a.hi, b.hi, -p);
+    e = fmaf(a.hi, b.lo, e);
+    e = fmaf(a.lo, b.hi, e);
+    const float hi = p + e;
+    return DF2{hi, e - (hi - p)};
+}
+
+// ------------------------------------------------------------------- FIR --
+
+struct FirParams {
+    float h[kFirMaxTaps];   // taps, zero past M
+    int M, Mpad;            // taps; taps rounded up to 32
+};
+
+// history: [M-1][ldh] floats, row j = sample (push start - (M-1) + j)
+__global__ void __launch_bounds__(kFirThreads) fir_kernel(const __grid_constant__ FirParams fp,
+                                                          const float *__restrict__ x, long long ldx, int T, int C,
+                                                          const float *__restrict__ hist,
+                                                          float *__restrict__ y, long long ldy) {
+    extern __shared__ float xs[];   // [Mpad + kFirRows][kTopCh]; row OFF + r = input row t0 + r
+    const int OFF = fp.Mpad;
+    const int c0 = blockIdx.x * kTopCh, t0 = blockIdx.y * kFirRows;
+    const int tid = threadIdx.x;
+    const int nrows = OFF + kFirRows;
+    for (int f = tid; f < nrows * kTopCh; f += kFirThreads) {
+        const int s = f / kTopCh, ch = f % kTopCh;
+        const int r = s - OFF;                 // tile row, negative = earlier
+        const long long g = (long long)t0 + r;  // sample index within the push
+        const int c = c0 + ch;
+        float v = 0.f;
+        if (c < C && r > -fp.M && g < T) {
+            if (g >= 0) v = __ldg(x + g * ldx + c);
+            else v = __ldg(hist + (g + fp.M - 1) * (long long)C + c);
+        }
+        xs[f] = v;
+    }
+    __syncthreads();
+    const int ch = tid & 31, r0 = (tid >> 5) * 32;
+    float acc[32];
+#pragma unroll
+    for (int j = 0; j < 32; ++j) acc[j] = 0.f;
+    for (int k0 = 0; k0 < fp.Mpad; k0 += 32) {
+        // w[q] = input row r0 - k0 - 31 + q, q = 0..62
+        float w[63];
+        const float *base = xs + (OFF + r0 - k0 - 31) * kTopCh + ch;
+#pragma unroll
+        for (int q = 0; q < 63; ++q) w[q] = base[q * kTopCh];
+#pragma unroll
+        for (int kk = 0; kk < 32; ++kk) {
+            const float hk = fp.h[k0 + kk];
+#pragma unroll
+            for (int j = 0; j < 32; ++j) acc[j] = fmaf(hk, w[j - kk + 31], acc[j]);
+        }
+    }
+    const int c = c0 + ch;
+    if (c < C) {
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+            const int g = t0 + r0 + j;
+            if (g < T) y[(long long)g * ldy + c] = acc[j];
+        }
+    }
+}
+
+// next history = the last M-1 samples of (history, push)
+__global__ void fir_history_kernel(const float *__restrict__ x, long long ldx, int T, int C, int M,
+                                   const float *__restrict__ hist, float *__restrict__ hist_next) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long n = (long long)(M - 1) * C;
+    if (i >= n) return;
+    const int j = (int)(i / C), c = (int)(i % C);
+    const long long src = (long long)j + T;   // position in (history, push)
+    hist_next[i] = src >= M - 1 ? x[(src - (M - 1)) * ldx + c] : hist[src * C + c];
+}
+
+// ------------------------------------------------------ window sums (P) --
+
+// One CTA per 32 channels walks the push in slabs of 1024 samples and writes
+// the running prefix P[n] (double-float) of u = x (MEAN) or |x| (AGC).
+__global__ void __launch_bounds__(kScanThreads) prefix_kernel(const float *__restrict__ x, long long ldx, int T,
+                                                              int C, int absval, long long n0, int Q,
+                                                              float2 *__restrict__ ring,
+                                                              float2 *__restrict__ carry) {
+    __shared__ DF2 bs[kScanBlocks][kTopCh];
+    __shared__ DF2 cin[kTopCh];
+    const int ch = threadIdx.x & 31, blk = threadIdx.x >> 5;
+    const int c = blockIdx.x * kTopCh + ch;
+    if (blk == 0) cin[ch] = c < C ? DF2{carry[c].x, carry[c].y} : DF2{0.f, 0.f};
+    __syncthreads();
+    for (int s0 = 0; s0 < T; s0 += kSlab) {
+        const int a = s0 + blk * 32;
+        float u[32];
+        DF2 sum{0.f, 0.f};
+#pragma unroll
+        for (int i = 0; i < 32; ++i) {
+            float v = 0.f;
+            if (c < C && a + i < T) v = x[(long long)(a + i) * ldx + c];
+            u[i] = absval ? fabsf(v) : v;
+            sum = d_add_f(sum, u[i]);
+        }
+        bs[blk][ch] = sum;
+        __syncthreads();
+        DF2 p = cin[ch];
+        for (int j = 0; j < blk; ++j) p = d_add(p, bs[j][ch]);
+        if (c < C) {
+#pragma unroll
+            for (int i = 0; i < 32; ++i) {
+                if (a + i >= T) break;
+                p = d_add_f(p, u[i]);
+                ring[(size_t)((n0 + a + i) % Q) * C + c] = make_float2(p.hi, p.lo);
+            }
+        }
+        __syncthreads();
+        if (blk == 0) {
+            DF2 t = cin[ch];
+            for (int j = 0; j < kScanBlocks; ++j) t = d_add(t, bs[j][ch]);
+            cin[ch] = t;
+        }
+        __syncthreads();
+    }
+    if (blk == 0 && c < C) carry[c] = make_float2(cin[ch].hi, cin[ch].lo);
+}
+
+__global__ void window_out_kernel(const float *__restrict__ x, long long ldx, int T, int C, int w, int agc,
+                                  long long n0, int Q, const float2 *__restrict__ ring, float *__restrict__ y,
+                                  long long ldy) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (long long)T * C) return;
+    const int t = (int)(i / C), c = (int)(i % C);
+    const long long n = n0 + t;
+    const float2 pn = ring[(size_t)(n % Q) * C + c];
+    float2 pw = make_float2(0.f, 0.f);
+    if (n - w >= 0) pw = ring[(size_t)((n - w) % Q) * C + c];
+    const DF2 d = d_add(DF2{pn.x, pn.y}, DF2{-pw.x, -pw.y});
+    const float g = (d.hi + d.lo) / (float)w;
+    float out = g;
+    if (agc) {
+        const float v = x[(long long)t * ldx + c];
+        out = g > 0.f ? v / g : 0.f;
+    }
+    y[(long long)t * ldy + c] = out;
+}
+
+// ------------------------------------------------------------------- EMA --
+
+struct EmaParams {
+    float alpha;                  // a
+    float ac, ac_lo;              // 1 - a as a float pair: a float alone would move
+                                  // a slow EMA's time constant (1-a = 0.9999 to ~6e-8)
+    float pw32[kScanBlocks + 1];  // (1-a)^(32 j), FP32
+    float pw1[32];                // (1-a)^j, FP32
+    float p1024_hi, p1024_lo;     // (1-a)^1024, double-float (full slabs)
+    float plast_hi, plast_lo;     // (1-a)^(length of the push's last slab), double-float
+};
+
+__device__ __forceinline__ float ema_pow(const EmaParams &ep, int m) { return ep.pw32[m >> 5] * ep.pw1[m & 31]; }
+
+__global__ void __launch_bounds__(kScanThreads) ema_kernel(const __grid_constant__ EmaParams ep,
+                                                           const float *__restrict__ x, long long ldx, int T, int C,
+                                                           float2 *__restrict__ state, float *__restrict__ y,
+                                                           long long ldy) {
+    __shared__ float ls[kScanBlocks][kTopCh];
+    __shared__ DF2 es[kTopCh];
+    const int ch = threadIdx.x & 31, blk = threadIdx.x >> 5;
+    const int c = blockIdx.x * kTopCh + ch;
+    if (blk == 0) es[ch] = c < C ? DF2{state[c].x, state[c].y} : DF2{0.f, 0.f};
+    __syncthreads();
+    for (int s0 = 0; s0 < T; s0 += kSlab) {
+        const int slab = min(kSlab, T - s0);
+        const int a = s0 + blk * 32;
+        float v[32];
+        // this block's response at its last sample from a zero start (FP32)
+        float l = 0.f;
+#pragma unroll
+        for (int i = 0; i < 32; ++i) {
+            const bool in = c < C && a + i < T;
+            v[i] = in ? x[(long long)(a + i) * ldx + c] : 0.f;
+            if (in) l = fmaf(ep.ac, l, fmaf(ep.ac_lo, l, ep.alpha * v[i] * v[i]));
+        }
+        ls[blk][ch] = l;
+        __syncthreads();
+        // start of this block: (1-a)^(32 blk) E + sum_{j<blk} (1-a)^(32(blk-1-j)) l_j
+        const DF2 E = es[ch];
+        float e = ep.pw32[blk] * E.hi;
+        for (int j = 0; j < blk; ++j) e = fmaf(ep.pw32[blk - 1 - j], ls[j][ch], e);
+        if (c < C) {
+#pragma unroll
+            for (int i = 0; i < 32; ++i) {
+                if (a + i >= T) break;
+                e = fmaf(ep.ac, e, fmaf(ep.ac_lo, e, ep.alpha * v[i] * v[i]));
+                y[(long long)(a + i) * ldy + c] = e > 0.f ? v[i] * rsqrtf(e) : 0.f;
+            }
+        }
+        __syncthreads();
+        if (blk == 0) {
+            // state after the slab's last sample, double-float:
+            // (1-a)^slab E + sum_j (1-a)^(samples after block j) l_j
+            const int nb = (slab + 31) / 32;
+            DF2 t = d_mul(E, slab == kSlab ? DF2{ep.p1024_hi, ep.p1024_lo} : DF2{ep.plast_hi, ep.plast_lo});
+            float add = 0.f;
+            for (int j = 0; j < nb; ++j) {
+                const int after = j < nb - 1 ? slab - 32 * (j + 1) : 0;
+                add = fmaf(ema_pow(ep, after), ls[j][ch], add);
+            }
+            es[ch] = d_add_f(t, add);
+        }
+        __syncthreads();
+    }
+    if (blk == 0 && c < C) state[c] = make_float2(es[ch].hi, es[ch].lo);
+}
+
+// ------------------------------------------------------------------ host --
+
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = false;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        ok = cudaSetDevice(dev) == cudaSuccess;
+    }
+    ~DeviceGuard() {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+
+filark_status tfail(filark_status st, const std::string &m) {
+    set_last_error(m);
+    return st;
+}
+
+filark_status tcuda(cudaError_t e, const char *what) {
+    cudaGetLastError();
+    set_last_error(std::string(what) + ": " + cudaGetErrorString(e));
+    return FILARK_ECUDA;
+}
+
+size_t fir_smem(int Mpad) { return sizeof(float) * (size_t)(Mpad + kFirRows) * kTopCh; }
+
+}  // namespace
+
+struct filark_top {
+    int kind = 0, device = 0, C = 0, M = 1;
+    long long max_chunk = 0, n = 0;
+    FirParams fir{};
+    EmaParams ema{};
+    float *hist[2] = {nullptr, nullptr};
+    int parity = 0;
+    float2 *ring = nullptr;
+    long long Q = 0;
+    float2 *carry = nullptr;   // window prefix or EMA state
+};
+
+namespace {
+
+void free_top(filark_top *t) {
+    if (!t) return;
+    for (float *p : t->hist)
+        if (p) cudaFree(p);
+    if (t->ring) cudaFree(t->ring);
+    if (t->carry) cudaFree(t->carry);
+    delete t;
+}
+
+filark_status zero_top(filark_top *t, cudaStream_t s) {
+    cudaError_t e = cudaSuccess;
+    for (float *p : t->hist)
+        if (p && e == cudaSuccess) e = cudaMemsetAsync(p, 0, sizeof(float) * (size_t)(t->M - 1) * t->C, s);
+    if (t->carry && e == cudaSuccess) e = cudaMemsetAsync(t->carry, 0, sizeof(float2) * (size_t)t->C, s);
+    if (e != cudaSuccess) return tcuda(e, "temporal operator: reset");
+    t->n = 0;
+    t->parity = 0;
+    return FILARK_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+filark_status filark_top_create(int kind, int n_channels, int length, const double *taps, double alpha,
+                                int64_t max_chunk, int cuda_device, filark_top **out) {
+    if (!out) return tfail(FILARK_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (kind < FILARK_TOP_FIR || kind > FILARK_TOP_EMA) return tfail(FILARK_EINVAL, "unknown operator kind");
+    if (n_channels < 1) return tfail(FILARK_EINVAL, "n_channels must be >= 1");
+    if (max_chunk < 1 || max_chunk > (int64_t)1 << 30) return tfail(FILARK_EINVAL, "max_chunk out of range");
+    filark_top *t = new (std::nothrow) filark_top();
+    if (!t) return tfail(FILARK_ENOMEM, "host allocation failed");
+    t->kind = kind;
+    t->device = cuda_device;
+    t->C = n_channels;
+    t->max_chunk = max_chunk;
+    if (kind == FILARK_TOP_FIR) {
+        if (length < 1 || length > kFirMaxTaps || !taps) {
+            delete t;
+            return tfail(FILARK_EINVAL, "FIR needs 1 <= taps <= 512 and a taps array");
+        }
+        for (int k = 0; k < length; ++k)
+            if (!std::isfinite(taps[k])) {
+                delete t;
+                return tfail(FILARK_EINVAL, "non-finite tap");
+            }
+        t->M = length;
+        t->fir.M = length;
+        t->fir.Mpad = (length + 31) / 32 * 32;
+        for (int k = 0; k < length; ++k) t->fir.h[k] = (float)taps[k];
+    } else if (kind == FILARK_TOP_MEAN || kind == FILARK_TOP_AGC) {
+        if (length < 1 || length > (1 << 24)) {
+            delete t;
+            return tfail(FILARK_EINVAL, "window length must be in [1, 2^24]");
+        }
+        t->M = length;
+        t->Q = (long long)length + max_chunk;
+        if ((double)t->Q * n_channels > 2.0e9) {
+            delete t;
+            return tfail(FILARK_ENOSYS, "window ring above 2^31 entries");
+        }
+    } else {
+        if (!(alpha > 0.0) || !(alpha <= 1.0)) {
+            delete t;
+            return tfail(FILARK_EINVAL, "EMA coefficient must be in (0, 1]");
+        }
+        t->M = 1;
+        const double ac = 1.0 - alpha;
+        t->ema.alpha = (float)alpha;
+        t->ema.ac = (float)ac;
+        t->ema.ac_lo = (float)(ac - (double)t->ema.ac);
+        for (int j = 0; j <= kScanBlocks; ++j) t->ema.pw32[j] = (float)std::pow(ac, 32.0 * j);
+        for (int j = 0; j < 32; ++j) t->ema.pw1[j] = (float)std::pow(ac, (double)j);
+        const double p1024 = std::pow(ac, 1024.0);
+        t->ema.p1024_hi = (float)p1024;
+        t->ema.p1024_lo = (float)(p1024 - (double)t->ema.p1024_hi);
+    }
+    DeviceGuard dg(cuda_device);
+    if (!dg.ok) {
+        delete t;
+        return tfail(FILARK_ECUDA, "cudaSetDevice failed");
+    }
+    cudaError_t e = cudaSuccess;
+    if (kind == FILARK_TOP_FIR) {
+        if (t->M > 1)
+            for (int k = 0; k < 2 && e == cudaSuccess; ++k)
+                e = cudaMalloc(&t->hist[k], sizeof(float) * (size_t)(t->M - 1) * t->C);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(fir_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fir_smem(kFirMaxTaps));
+    } else {
+        e = cudaMalloc(&t->carry, sizeof(float2) * (size_t)t->C);
+        if (e == cudaSuccess && t->Q > 0) e = cudaMalloc(&t->ring, sizeof(float2) * (size_t)t->Q * t->C);
+    }
+    if (e != cudaSuccess) {
+        free_top(t);
+        return tcuda(e, "temporal operator create");
+    }
+    filark_status st = zero_top(t, nullptr);
+    if (st == FILARK_OK && (e = cudaStreamSynchronize(nullptr)) != cudaSuccess) st = tcuda(e, "create: sync");
+    if (st != FILARK_OK) {
+        free_top(t);
+        return st;
+    }
+    *out = t;
+    return FILARK_OK;
+}
+
+filark_status filark_top_push(filark_top *t, const float *d_in, int64_t ld_in, int64_t n_samples, float *d_out,
+                              int64_t ld_out, filark_stream_t stream) {
+    if (!t) return tfail(FILARK_EINVAL, "operator is NULL");
+    if (n_samples < 0 || n_samples > t->max_chunk) return tfail(FILARK_EINVAL, "n_samples must be in [0, max_chunk]");
+    if (n_samples == 0) return FILARK_OK;
+    if (!d_in || !d_out || ld_in < t->C || ld_out < t->C) return tfail(FILARK_EINVAL, "buffers NULL or ld < C");
+    const size_t in_bytes = sizeof(float) * (size_t)((n_samples - 1) * ld_in + t->C);
+    const size_t out_bytes = sizeof(float) * (size_t)((n_samples - 1) * ld_out + t->C);
+    const char *pi = (const char *)d_in, *po = (const char *)d_out;
+    if (pi < po + out_bytes && po < pi + in_bytes) return tfail(FILARK_EINVAL, "output overlaps the input");
+    DeviceGuard dg(t->device);
+    if (!dg.ok) return tfail(FILARK_ECUDA, "cudaSetDevice failed");
+    cudaStream_t s = (cudaStream_t)stream;
+    const int T = (int)n_samples, C = t->C;
+    const unsigned gch = (unsigned)((C + kTopCh - 1) / kTopCh);
+    if (t->kind == FILARK_TOP_FIR) {
+        const dim3 grid(gch, (unsigned)((T + kFirRows - 1) / kFirRows));
+        const float *h = t->M > 1 ? t->hist[t->parity] : nullptr;
+        fir_kernel<<<grid, kFirThreads, fir_smem(t->fir.Mpad), s>>>(t->fir, d_in, ld_in, T, C, h, d_out, ld_out);
+        if (t->M > 1) {
+            const long long n = (long long)(t->M - 1) * C;
+            fir_history_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(d_in, ld_in, T, C, t->M, h,
+                                                                           t->hist[t->parity ^ 1]);
+            t->parity ^= 1;
+        }
+    } else if (t->kind == FILARK_TOP_MEAN || t->kind == FILARK_TOP_AGC) {
+        const int agc = t->kind == FILARK_TOP_AGC;
+        prefix_kernel<<<gch, kScanThreads, 0, s>>>(d_in, ld_in, T, C, agc, t->n, (int)t->Q, t->ring, t->carry);
+        const long long n = (long long)T * C;
+        window_out_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(d_in, ld_in, T, C, t->M, agc, t->n,
+                                                                      (int)t->Q, t->ring, d_out, ld_out);
+    } else {
+        EmaParams ep = t->ema;
+        const int last = T - (T - 1) / kSlab * kSlab;   // length of the last slab
+        const double pl = std::pow((double)ep.ac + (double)ep.ac_lo, (double)last);
+        ep.plast_hi = (float)pl;
+        ep.plast_lo = (float)(pl - (double)ep.plast_hi);
+        ema_kernel<<<gch, kScanThreads, 0, s>>>(ep, d_in, ld_in, T, C, t->carry, d_out, ld_out);
+    }
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return tcuda(e, "temporal operator push");
+    t->n += n_samples;
+    return FILARK_OK;
+}
+
+filark_status filark_top_reset(filark_top *t, filark_stream_t stream) {
+    if (!t) return tfail(FILARK_EINVAL, "operator is NULL");
+    DeviceGuard dg(t->device);
+    if (!dg.ok) return tfail(FILARK_ECUDA, "cudaSetDevice failed");
+    return zero_top(t, (cudaStream_t)stream);
+}
+
+filark_status filark_top_destroy(filark_top *t) {
+    if (!t) return FILARK_OK;
+    DeviceGuard dg(t->device);
+    cudaDeviceSynchronize();
+    free_top(t);
+    return FILARK_OK;
+}
+
+}  // extern "C"
