@@ -443,6 +443,29 @@ filark_status filark_top_push(filark_top *t, const float *d_in, int64_t ld_in, i
 filark_status filark_top_reset(filark_top *t, filark_stream_t stream);
 filark_status filark_top_destroy(filark_top *t);   /* NULL ok */
 
+/*
+ * Overlap-add FFT filtering: the FFT-domain filtering mode the paper benchmarks
+ * on the GPU (Table 1, FFT-domain bandpass; Sec. 6.2, overlap-add chunked
+ * filtering), with the chain's streaming contract.  Computes
+ *     y[n] = sum_{k<M} h[k] x[n-k]   (x before the stream start is zero)
+ * for long filters (a windowed-sinc bandpass of thousands of taps): each push
+ * is cut into blocks of at most block_len samples, each block is convolved
+ * with h through an FFT of N >= block_len + M - 1 points (hand-written Stockham
+ * transform, two channels per complex transform), and the M-1 sample overlap
+ * tail is carried across blocks and pushes.  block_len <= 0 picks N = the
+ * power of two >= 2M.  N is limited to 8192 (FILARK_ENOSYS above).  taps: host,
+ * M doubles, rounded to float.  Buffers as for filark_top_push.
+ */
+typedef struct filark_fftfilt filark_fftfilt;
+
+filark_status filark_fftfilt_create(int n_channels, int n_taps, const double *taps, int block_len,
+                                    int64_t max_chunk, int cuda_device, filark_fftfilt **out);
+filark_status filark_fftfilt_push(filark_fftfilt *f, const float *d_in, int64_t ld_in, int64_t n_samples,
+                                  float *d_out, int64_t ld_out, filark_stream_t stream);
+filark_status filark_fftfilt_reset(filark_fftfilt *f, filark_stream_t stream);
+filark_status filark_fftfilt_get_info(const filark_fftfilt *f, int *fft_len, int *block_len);
+filark_status filark_fftfilt_destroy(filark_fftfilt *f);   /* NULL ok */
+
 /* Message for the last error returned to this thread ("" if none). */
 const char *filark_last_error_string(void);
 

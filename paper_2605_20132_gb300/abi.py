@@ -51,6 +51,8 @@ EXPORTED = (
     "filark_trigger_create", "filark_trigger_push", "filark_trigger_flush", "filark_trigger_reset",
     "filark_trigger_destroy", "filark_events_work_bytes", "filark_events_merge",
     "filark_top_create", "filark_top_push", "filark_top_reset", "filark_top_destroy",
+    "filark_fftfilt_create", "filark_fftfilt_push", "filark_fftfilt_reset", "filark_fftfilt_get_info",
+    "filark_fftfilt_destroy",
 )
 
 FILARK_TOP_FIR, FILARK_TOP_MEAN, FILARK_TOP_AGC, FILARK_TOP_EMA = 0, 1, 2, 3
@@ -186,6 +188,11 @@ def load(build_if_missing: bool = True) -> ct.CDLL:
             "filark_top_push": ([vp, vp, i64, i64, vp, i64, vp], ct.c_int),
             "filark_top_reset": ([vp, vp], ct.c_int),
             "filark_top_destroy": ([vp], ct.c_int),
+            "filark_fftfilt_create": ([ct.c_int, ct.c_int, vp, ct.c_int, i64, ct.c_int, ct.POINTER(vp)], ct.c_int),
+            "filark_fftfilt_push": ([vp, vp, i64, i64, vp, i64, vp], ct.c_int),
+            "filark_fftfilt_reset": ([vp, vp], ct.c_int),
+            "filark_fftfilt_get_info": ([vp, ct.POINTER(ct.c_int), ct.POINTER(ct.c_int)], ct.c_int),
+            "filark_fftfilt_destroy": ([vp], ct.c_int),
             "filark_iir_ckpt_bytes": ([ct.c_int, ct.c_int, i64, i64], ct.c_size_t),
             "filark_iir_work_bytes": ([ct.c_int, ct.c_int, i64, i64], ct.c_size_t),
             "filark_iir_forward_ckpt": ([vp, ct.c_int, ct.c_int, vp, i64, i64, vp, i64, i64, vp, ct.c_size_t, vp],
@@ -385,6 +392,32 @@ def filark_top_reset(t, stream) -> int:
 
 def filark_top_destroy(t) -> int:
     return load().filark_top_destroy(t)
+
+
+def filark_fftfilt_create(n_channels: int, taps, block_len: int, max_chunk: int, cuda_device: int):
+    """taps: a C-contiguous float64 numpy array."""
+    h = ct.c_void_p()
+    st = load().filark_fftfilt_create(int(n_channels), int(taps.shape[0]), taps.ctypes.data, int(block_len),
+                                      int(max_chunk), int(cuda_device), ct.byref(h))
+    return st, h.value
+
+
+def filark_fftfilt_push(f, d_in, ld_in, n, d_out, ld_out, stream) -> int:
+    return load().filark_fftfilt_push(f, d_in, ld_in, n, d_out, ld_out, stream)
+
+
+def filark_fftfilt_reset(f, stream) -> int:
+    return load().filark_fftfilt_reset(f, stream)
+
+
+def filark_fftfilt_get_info(f):
+    n, l = ct.c_int(), ct.c_int()
+    st = load().filark_fftfilt_get_info(f, ct.byref(n), ct.byref(l))
+    return st, n.value, l.value
+
+
+def filark_fftfilt_destroy(f) -> int:
+    return load().filark_fftfilt_destroy(f)
 
 
 def filark_last_error_string() -> str:

@@ -330,3 +330,38 @@ class TemporalOp:
 
     def reset(self, stream=None) -> None:
         abi.check(abi.filark_top_reset(self._h, _stream_handle(stream)), "filark_top_reset")
+
+
+class FFTFilter:
+    """Overlap-add FFT filtering with a long FIR (filark_fftfilt_*)."""
+
+    def __init__(self, n_channels: int, taps, block_len: int = 0, max_chunk: int = 4096, device: int = 0):
+        abi.load()
+        self._taps = np.ascontiguousarray(taps, dtype=np.float64)
+        st, h = abi.filark_fftfilt_create(n_channels, self._taps, block_len, max_chunk, device)
+        abi.check(st, "filark_fftfilt_create")
+        self._h = h
+        self.n_channels = int(n_channels)
+        st, self.fft_len, self.block_len = abi.filark_fftfilt_get_info(h)
+        abi.check(st, "filark_fftfilt_get_info")
+
+    def close(self) -> None:
+        if getattr(self, "_h", None):
+            abi.check(abi.filark_fftfilt_destroy(self._h), "filark_fftfilt_destroy")
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def push(self, x, out, stream=None) -> None:
+        T = int(x.shape[0])
+        ld_in = int(x.stride(0)) if T else self.n_channels
+        ld_out = int(out.stride(0)) if T else self.n_channels
+        abi.check(abi.filark_fftfilt_push(self._h, _ptr(x) if T else None, ld_in, T, _ptr(out) if T else None,
+                                          ld_out, _stream_handle(stream)), "filark_fftfilt_push")
+
+    def reset(self, stream=None) -> None:
+        abi.check(abi.filark_fftfilt_reset(self._h, _stream_handle(stream)), "filark_fftfilt_reset")

@@ -193,6 +193,15 @@ def batch_chunk_lengths(seed: int, n_streams: int, n_pushes: int, chunk=(200, 30
     return rng.integers(chunk[0], chunk[1] + 1, (n_pushes, n_streams))
 
 
+def windowed_sinc_bandpass(n_taps: int, f1: float, f2: float, fs: float) -> np.ndarray:
+    """Linear-phase FIR bandpass taps (Hamming-windowed ideal bandpass), the
+    long filter of the FFT-filtering workload; an input to the operators under
+    test, not part of their arithmetic."""
+    n = np.arange(n_taps) - (n_taps - 1) / 2.0
+    ideal = 2 * f2 / fs * np.sinc(2 * f2 / fs * n) - 2 * f1 / fs * np.sinc(2 * f1 / fs * n)
+    return ideal * np.hamming(n_taps)
+
+
 def perturb_sos(sos: np.ndarray, rel: float, seed: int, max_tries: int = 1000) -> np.ndarray:
     """Multiply every coefficient except a0 by (1+u), u ~ U[-rel, rel]; a
     section is redrawn until its poles lie strictly inside the unit circle."""

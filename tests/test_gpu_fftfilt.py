@@ -1,0 +1,72 @@
+"""Overlap-add FFT filtering against the FP64 oracle's direct FIR (the
+exact linear convolution), for filter lengths up to thousands of taps, block
+lengths that give every FFT size, odd channel counts (channel pairs share a
+transform) and random chunkings."""
+import numpy as np
+import pytest
+
+from gpu_helpers import TOL, normwise
+from paper_2605_20132_gb300 import abi, synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    abi.load()
+
+
+def run(x, taps, chunks, block_len=0):
+    import torch
+    from paper_2605_20132_gb300.chain import FFTFilter
+    N, C = x.shape
+    f = FFTFilter(C, taps, block_len, max_chunk=max(chunks))
+    xd = torch.from_numpy(x).cuda()
+    yd = torch.full_like(xd, float("nan"))
+    t = 0
+    for k in chunks:
+        f.push(xd[t:t + k], yd[t:t + k])
+        t += k
+    torch.cuda.synchronize()
+    info = (f.fft_len, f.block_len)
+    f.close()
+    return yd.cpu().numpy().astype(np.float64), info
+
+
+@pytest.mark.parametrize("M,block_len", [(1, 0), (31, 0), (257, 100), (257, 0), (1001, 0), (4001, 0),
+                                         (2000, 6000)])
+def test_fftfilt_matches_direct_fir(oracle_mod, M, block_len):
+    rng = np.random.default_rng(130 + M)
+    C = 9
+    x = synth.small_stream(C, 30000, seed=130 + M)
+    h = synth.windowed_sinc_bandpass(M, 1.0, 50.0, 1000.0) if M > 1 else np.array([0.7])
+    chunks = []
+    while sum(chunks) < 30000:
+        chunks.append(int(min(rng.integers(1, 9000), 30000 - sum(chunks))))
+    got, info = run(x, h, chunks, block_len)
+    ref = oracle_mod.TemporalOp(C, oracle_mod.TOP_FIR, M, h.astype(np.float32).astype(np.float64)).push(x)
+    err = normwise(got, ref)
+    print("fftfilt", M, block_len, info, err)
+    assert info[0] >= info[1] + M - 1
+    assert err <= TOL
+
+
+def test_fftfilt_reset_and_errors(oracle_mod):
+    import torch
+    from paper_2605_20132_gb300.chain import FFTFilter
+    h = synth.windowed_sinc_bandpass(401, 2.0, 40.0, 1000.0)
+    x = torch.from_numpy(synth.small_stream(4, 5000, seed=140)).cuda()
+    f = FFTFilter(4, h, max_chunk=5000)
+    y1, y2 = torch.empty_like(x), torch.empty_like(x)
+    f.push(x, y1)
+    f.reset()
+    f.push(x, y2)
+    torch.cuda.synchronize()
+    assert torch.equal(y1, y2)
+    assert abi.filark_fftfilt_push(f._h, x.data_ptr(), 4, 5001, y1.data_ptr(), 4, None) == abi.FILARK_EINVAL
+    f.close()
+    st, _ = abi.filark_fftfilt_create(4, np.ones(9000), 0, 100, 0)
+    assert st == abi.FILARK_ENOSYS
