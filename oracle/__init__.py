@@ -344,3 +344,61 @@ class TemporalOp:
         y = np.zeros(x.shape, dtype=np.float64)
         self._f["top_push"](self._h, _ptr(x, _fp), self.C, x.shape[0], _ptr(y), self.C)
         return y
+
+
+# ------------------------------------------------- headless display path --
+
+VIEW_DROP, VIEW_PEAK, VIEW_LINEAR = 0, 1, 2
+
+
+def _reduce_group(v: np.ndarray, mode: int) -> float:
+    """One display value from a group of samples (consecutive channels or
+    consecutive times): drop = the first; peak = the value of largest
+    magnitude (first on ties); linear = interpolation at the group's centre."""
+    n = v.shape[0]
+    if mode == VIEW_DROP:
+        return float(v[0])
+    if mode == VIEW_PEAK:
+        return float(v[int(np.argmax(np.abs(v)))])
+    p = (n - 1) / 2.0
+    i0 = int(np.floor(p))
+    f = p - i0
+    return float(v[i0]) if f == 0 else float((1 - f) * v[i0] + f * v[i0 + 1])
+
+
+class View:
+    """Streaming display buffer (test infrastructure): channels grouped by kc
+    into display rows, an optional causal SOS display filter on the rows at
+    the source rate (state carried), times grouped by kt into columns, the
+    last W columns kept in a ring; image() returns them oldest to newest, the
+    newest at the right, zeros before the first column."""
+
+    def __init__(self, C: int, kc: int, kt: int, W: int, mode: int, sos=None):
+        self.C, self.kc, self.kt, self.W, self.mode = int(C), int(kc), int(kt), int(W), int(mode)
+        self.H = -(-self.C // self.kc)
+        self.filt = None if sos is None else Chain(self.H, sos)
+        self.pending = np.zeros((0, self.H))
+        self.cols: list[np.ndarray] = []
+
+    def push(self, x: np.ndarray) -> None:
+        x = np.asarray(x, dtype=np.float32)
+        T = x.shape[0]
+        rows = np.zeros((T, self.H))
+        for n in range(T):
+            for r in range(self.H):
+                rows[n, r] = _reduce_group(x[n, r * self.kc:min(self.C, (r + 1) * self.kc)].astype(np.float64),
+                                           self.mode)
+        if self.filt is not None:
+            rows = self.filt.push(rows.astype(np.float32), want=("bp",))["bp"]
+        self.pending = np.vstack([self.pending, rows])
+        while self.pending.shape[0] >= self.kt:
+            grp = self.pending[:self.kt]
+            self.cols.append(np.array([_reduce_group(grp[:, r], self.mode) for r in range(self.H)]))
+            self.pending = self.pending[self.kt:]
+
+    def image(self) -> np.ndarray:
+        img = np.zeros((self.H, self.W))
+        last = self.cols[-self.W:]
+        for i, col in enumerate(last):
+            img[:, self.W - len(last) + i] = col
+        return img

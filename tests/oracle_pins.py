@@ -534,6 +534,75 @@ def pin_ema_closed_forms(ora):
     worst = _worst(worst, 0.0 if np.array_equal(whole, parts) else 1.0)
     return worst, 1e-12
 
+
+# ---------------------------------------------------------- display pins --
+
+def pin_view_closed_forms(ora):
+    """The headless display buffer on a linear field x[n][c] = 1000 n + c:
+    drop gives the group's first sample, linear interpolation the value at
+    the group's centre (exact on a linear field), both in the ring order
+    (newest column at the right, zeros before the first) for any chunking;
+    peak picks an isolated spike, negative or positive."""
+    worst = 0.0
+    C, N, kc, kt, W = 11, 700, 3, 7, 40
+    n = np.arange(N, dtype=np.float64)[:, None]
+    c = np.arange(C, dtype=np.float64)[None, :]
+    x = (1000.0 * n + c).astype(np.float32)
+    ncol = N // kt
+    H = -(-C // kc)
+    for mode in (ora.VIEW_DROP, ora.VIEW_LINEAR):
+        for chunks in ([N], [1, 13, 300, 386]):
+            v = ora.View(C, kc, kt, W, mode)
+            pos = 0
+            for k in chunks:
+                v.push(x[pos:pos + k])
+                pos += k
+            img = v.image()
+            want = np.zeros((H, W))
+            for i in range(W):
+                j = ncol - W + i
+                if j < 0:
+                    continue
+                for r in range(H):
+                    k_r = min(C, (r + 1) * kc) - r * kc
+                    if mode == ora.VIEW_DROP:
+                        want[r, i] = 1000.0 * j * kt + r * kc
+                    else:
+                        want[r, i] = 1000.0 * (j * kt + (kt - 1) / 2) + r * kc + (k_r - 1) / 2
+            worst = _worst(worst, float(np.max(np.abs(img - want))))
+    x = np.zeros((70, 9), dtype=np.float32)
+    x[12, 4] = -5.0
+    x[13, 3] = 4.0
+    x[40, 8] = 2.0
+    v = ora.View(9, 3, 10, 8, ora.VIEW_PEAK)
+    v.push(x)
+    img = v.image()
+    want = np.zeros((3, 8))
+    want[1, 8 - 7 + 1] = -5.0
+    want[2, 8 - 7 + 4] = 2.0
+    worst = _worst(worst, float(np.max(np.abs(img - want))))
+    return worst, 0.0
+
+
+def pin_view_display_filter(ora):
+    """With the causal display filter, drop-mode columns are the filtered
+    rows (per-channel SOS filtering of the dropped channels) sampled every kt
+    samples, across pushes."""
+    rng = np.random.default_rng(53)
+    sos = ora.butter_bandpass(2, 5.0, 80.0, 1000.0)
+    C, N, kc, kt, W = 8, 900, 2, 5, 200
+    x = rng.standard_normal((N, C)).astype(np.float32)
+    v = ora.View(C, kc, kt, W, ora.VIEW_DROP, sos)
+    for a in range(0, N, 250):
+        v.push(x[a:a + 250])
+    img = v.image()
+    worst = 0.0
+    for r in range(C // kc):
+        y, _ = ora.sosfilt(sos, x[:, r * kc].astype(np.float64))
+        cols = y[0:N - N % kt:kt]
+        worst = _worst(worst, normwise_err(img[r, W - len(cols):][:, None], cols[-W:][:, None]))
+    return worst, 1e-12
+
 # ------------------------------------------------------------ adjoint pins --
 
 def _loss_and_grads(ora, sos, x, target):
@@ -637,4 +706,6 @@ ALL_PINS = [
     pin_fir_vs_convolution,
     pin_window_ops_literal,
     pin_ema_closed_forms,
+    pin_view_closed_forms,
+    pin_view_display_filter,
 ]

@@ -131,3 +131,43 @@ def test_planted_mistake_is_caught(oracle_mod, tmp_path, name, old, new):
             if not ok:
                 failed.append(pin.__name__)
     assert failed, f"no pin caught mutant {name}"
+
+
+# The display-path oracle is numpy code: plant mistakes by swapping its group
+# reduction and check a pin fails.
+def _bad_linear(v, mode):
+    import numpy as _np
+    if mode == 2:
+        return float(v[(v.shape[0] - 1) // 2])          # no interpolation
+    return _ORIG_REDUCE(v, mode)
+
+
+def _bad_peak(v, mode):
+    import numpy as _np
+    if mode == 1:
+        return float(v[int(_np.argmax(v))])              # largest value, not magnitude
+    return _ORIG_REDUCE(v, mode)
+
+
+def _bad_drop(v, mode):
+    if mode == 0:
+        return float(v[-1])                              # last sample of the group
+    return _ORIG_REDUCE(v, mode)
+
+
+_ORIG_REDUCE = None
+
+
+@pytest.mark.parametrize("bad", [_bad_linear, _bad_peak, _bad_drop], ids=["linear", "peak", "drop"])
+def test_planted_display_mistake_is_caught(oracle_mod, monkeypatch, bad):
+    global _ORIG_REDUCE
+    _ORIG_REDUCE = oracle_mod._reduce_group
+    monkeypatch.setattr(oracle_mod, "_reduce_group", bad)
+    failed = False
+    for pin in (P.pin_view_closed_forms, P.pin_view_display_filter):
+        try:
+            err, bound = pin(oracle_mod)
+            failed |= not (err <= bound)
+        except Exception:
+            failed = True
+    assert failed
