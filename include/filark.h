@@ -466,6 +466,46 @@ filark_status filark_fftfilt_reset(filark_fftfilt *f, filark_stream_t stream);
 filark_status filark_fftfilt_get_info(const filark_fftfilt *f, int *fft_len, int *block_len);
 filark_status filark_fftfilt_destroy(filark_fftfilt *f);   /* NULL ok */
 
+/*
+ * Headless streaming display path: the paper's ring-buffer texture (Sec. 3.2,
+ * ring-buffer streaming visualization -- fixed-size buffer, only the newly
+ * exposed columns written, a ring offset for the logical start), the
+ * view-dependent downsampling modes of its I/O layer (Sec. 3.5: drop, peak,
+ * linear) and the render-time causal display filter whose state is kept
+ * across viewport updates (Sec. 3.2) -- as a device buffer, without a graphics
+ * API.
+ *
+ * Per push of n_samples x n_channels (time-major, device):
+ *   rows     channels are grouped channels_per_row at a time (the last group
+ *            may be shorter) into H = ceil(n_channels / channels_per_row)
+ *            display rows, per sample;
+ *   filter   with n_sections > 0, the causal SOS filter `sos` (as for the
+ *            chain, state carried) runs on the rows at the source rate;
+ *   columns  samples are grouped samples_per_column at a time into display
+ *            columns counted from the stream start; the samples of an
+ *            incomplete column wait for the next push;
+ *   ring     column j is stored at ring column j mod width.
+ * Group reduction: FILARK_VIEW_DROP the first value, FILARK_VIEW_PEAK the value
+ * of largest magnitude (first on ties), FILARK_VIEW_LINEAR the interpolation at
+ * the group's centre (the middle value, or the mean of the two middle values).
+ * filark_view_image writes the ring as an [H][ld_image] float32 image (device),
+ * oldest column at the left, newest at the right, zeros left of the first
+ * column.
+ */
+enum { FILARK_VIEW_DROP = 0, FILARK_VIEW_PEAK = 1, FILARK_VIEW_LINEAR = 2 };
+
+typedef struct filark_view filark_view;
+
+filark_status filark_view_create(int n_channels, int channels_per_row, int samples_per_column, int width, int mode,
+                                 int n_sections, const double *sos, int64_t max_chunk, int cuda_device,
+                                 filark_view **out);
+filark_status filark_view_push(filark_view *v, const float *d_in, int64_t ld_in, int64_t n_samples,
+                               filark_stream_t stream);
+filark_status filark_view_image(const filark_view *v, float *d_image, int64_t ld_image, filark_stream_t stream);
+filark_status filark_view_get_info(const filark_view *v, int *rows, int64_t *columns, int *ring_offset);
+filark_status filark_view_reset(filark_view *v, filark_stream_t stream);
+filark_status filark_view_destroy(filark_view *v);   /* NULL ok */
+
 /* Message for the last error returned to this thread ("" if none). */
 const char *filark_last_error_string(void);
 

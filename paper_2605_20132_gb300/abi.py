@@ -53,7 +53,11 @@ EXPORTED = (
     "filark_top_create", "filark_top_push", "filark_top_reset", "filark_top_destroy",
     "filark_fftfilt_create", "filark_fftfilt_push", "filark_fftfilt_reset", "filark_fftfilt_get_info",
     "filark_fftfilt_destroy",
+    "filark_view_create", "filark_view_push", "filark_view_image", "filark_view_get_info", "filark_view_reset",
+    "filark_view_destroy",
 )
+
+FILARK_VIEW_DROP, FILARK_VIEW_PEAK, FILARK_VIEW_LINEAR = 0, 1, 2
 
 FILARK_TOP_FIR, FILARK_TOP_MEAN, FILARK_TOP_AGC, FILARK_TOP_EMA = 0, 1, 2, 3
 
@@ -193,6 +197,13 @@ def load(build_if_missing: bool = True) -> ct.CDLL:
             "filark_fftfilt_reset": ([vp, vp], ct.c_int),
             "filark_fftfilt_get_info": ([vp, ct.POINTER(ct.c_int), ct.POINTER(ct.c_int)], ct.c_int),
             "filark_fftfilt_destroy": ([vp], ct.c_int),
+            "filark_view_create": ([ct.c_int, ct.c_int, ct.c_int, ct.c_int, ct.c_int, ct.c_int, vp, i64, ct.c_int,
+                                    ct.POINTER(vp)], ct.c_int),
+            "filark_view_push": ([vp, vp, i64, i64, vp], ct.c_int),
+            "filark_view_image": ([vp, vp, i64, vp], ct.c_int),
+            "filark_view_get_info": ([vp, ct.POINTER(ct.c_int), ct.POINTER(ct.c_int64), ct.POINTER(ct.c_int)], ct.c_int),
+            "filark_view_reset": ([vp, vp], ct.c_int),
+            "filark_view_destroy": ([vp], ct.c_int),
             "filark_iir_ckpt_bytes": ([ct.c_int, ct.c_int, i64, i64], ct.c_size_t),
             "filark_iir_work_bytes": ([ct.c_int, ct.c_int, i64, i64], ct.c_size_t),
             "filark_iir_forward_ckpt": ([vp, ct.c_int, ct.c_int, vp, i64, i64, vp, i64, i64, vp, ct.c_size_t, vp],

@@ -365,3 +365,56 @@ class FFTFilter:
 
     def reset(self, stream=None) -> None:
         abi.check(abi.filark_fftfilt_reset(self._h, _stream_handle(stream)), "filark_fftfilt_reset")
+
+
+class View:
+    """Headless streaming display buffer (filark_view_*)."""
+
+    def __init__(self, n_channels: int, channels_per_row: int, samples_per_column: int, width: int, mode: int,
+                 sos: np.ndarray | None = None, max_chunk: int = 4096, device: int = 0):
+        import torch
+        abi.load()
+        self._sos = None if sos is None else np.ascontiguousarray(sos, dtype=np.float64)
+        h = ct.c_void_p()
+        st = abi.load().filark_view_create(int(n_channels), int(channels_per_row), int(samples_per_column),
+                                           int(width), int(mode), 0 if self._sos is None else self._sos.shape[0],
+                                           None if self._sos is None else self._sos.ctypes.data, int(max_chunk),
+                                           int(device), ct.byref(h))
+        abi.check(st, "filark_view_create")
+        self._h = h.value
+        self.n_channels, self.width = int(n_channels), int(width)
+        self.rows = -(-int(n_channels) // int(channels_per_row))
+        self.device = torch.device("cuda", device)
+
+    def close(self) -> None:
+        if getattr(self, "_h", None):
+            abi.check(abi.load().filark_view_destroy(self._h), "filark_view_destroy")
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def push(self, x, stream=None) -> None:
+        T = int(x.shape[0])
+        ld = int(x.stride(0)) if T else self.n_channels
+        abi.check(abi.load().filark_view_push(self._h, _ptr(x) if T else None, ld, T, _stream_handle(stream)),
+                  "filark_view_push")
+
+    def image(self, stream=None):
+        import torch
+        img = torch.empty((self.rows, self.width), dtype=torch.float32, device=self.device)
+        abi.check(abi.load().filark_view_image(self._h, _ptr(img), self.width, _stream_handle(stream)),
+                  "filark_view_image")
+        return img
+
+    def info(self) -> dict:
+        r, c, o = ct.c_int(), ct.c_int64(), ct.c_int()
+        abi.check(abi.load().filark_view_get_info(self._h, ct.byref(r), ct.byref(c), ct.byref(o)),
+                  "filark_view_get_info")
+        return {"rows": r.value, "columns": c.value, "ring_offset": o.value}
+
+    def reset(self, stream=None) -> None:
+        abi.check(abi.load().filark_view_reset(self._h, _stream_handle(stream)), "filark_view_reset")
