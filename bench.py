@@ -484,7 +484,7 @@ def run_adjoint_workload(args) -> None:
         "plain_forward": {"value": units / (ms_plain / 1e3), "unit": UNIT, "ms": ms_plain,
                           "what": "chain bandpass only, FP32 block scan, pushes of 3,000"},
         "memory": {"checkpoint_bytes": nb, "work_bytes": wb, "all_intermediates_fp64_bytes": 8 * S * C * N},
-        "dtype": "f64", "data": "synthetic noise + Ricker events (seeded)",
+        "dtype": "f32x2 (double-float)", "data": "synthetic noise + Ricker events (seeded)",
         "config": {"channels": C, "samples": N, "sections": S, "checkpoint": ck},
         "clocks": sampler.summary(),
     }
@@ -543,6 +543,75 @@ def run_trigger_workload(args) -> None:
     print(json.dumps(line), flush=True)
 
 
+def run_ops_workload(args) -> None:
+    """The other streaming operators on the paper-scale shape (6,000 channels,
+    pushes of 1,500 samples at 1.5 kHz; 6 pushes per step, 216 MB of input,
+    larger than L2): realtime FIR (101 taps), running mean and AGC (3,000-sample
+    window), EMA equalisation, overlap-add FFT bandpass (4,001 taps), and the
+    display path (2,048 rows of 3 channels, 10 samples per column, display
+    filter = the paper-scale bandpass).  One line per operator."""
+    import torch
+
+    from paper_2605_20132_gb300 import abi, synth
+    from paper_2605_20132_gb300.chain import FFTFilter, TemporalOp, View, butter_bandpass
+    w = workload()
+    C, T, P = w["n_channels"], w["chunk"], 6
+    g = torch.Generator(device="cuda").manual_seed(9)
+    x = torch.randn((T * P, C), device="cuda", generator=g)
+    y = torch.empty_like(x)
+    peak, peak_kind = measured_peak_hbm()
+    sos = butter_bandpass(w["order"], *w["band"], w["fs"])
+    ops = [
+        ("fir-101", lambda: TemporalOp(abi.FILARK_TOP_FIR, C, 101,
+                                       synth.windowed_sinc_bandpass(101, 5.0, 100.0, w["fs"]), max_chunk=T), 8, 3),
+        ("running-mean-3000", lambda: TemporalOp(abi.FILARK_TOP_MEAN, C, 3000, max_chunk=T), 8, 2),
+        ("running-agc-3000", lambda: TemporalOp(abi.FILARK_TOP_AGC, C, 3000, max_chunk=T), 8, 2),
+        ("ema-equalisation", lambda: TemporalOp(abi.FILARK_TOP_EMA, C, alpha=1e-3, max_chunk=T), 8, 1),
+        ("fft-bandpass-4001", lambda: FFTFilter(C, synth.windowed_sinc_bandpass(4001, 0.5, 100.0, w["fs"]),
+                                                max_chunk=T), 8, 1),
+    ]
+    for name, make, bps, launches in ops:
+        op = make()
+
+        def step():
+            for i in range(P):
+                op.push(x[i * T:(i + 1) * T], y[i * T:(i + 1) * T])
+
+        for _ in range(3):
+            step()
+        ms = _event_ms(step, args.steps)
+        op.close()
+        achieved = bps * C * T * P / (ms / 1e3) / 1e9
+        print(json.dumps({
+            "workload": name + "-6000ch-1500", "metric": "channel-samples/s (device-timed)",
+            "value": C * T * P / (ms / 1e3), "unit": UNIT, "ms_per_step": ms, "steps": args.steps,
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "peak_kind": peak_kind,
+                         "bytes_per_channel_sample": bps, "note": "input read + output written"},
+            "gpu_launches": launches * P * args.steps, "dtype": "f32", "data": "synthetic N(0,1) on the device"}),
+            flush=True)
+    v = View(C, 3, 10, 2048, abi.FILARK_VIEW_PEAK, sos, max_chunk=T)
+
+    def vstep():
+        for i in range(P):
+            v.push(x[i * T:(i + 1) * T])
+        v.image()
+
+    for _ in range(3):
+        vstep()
+    ms = _event_ms(vstep, args.steps)
+    v.close()
+    achieved = 4 * C * T * P / (ms / 1e3) / 1e9
+    print(json.dumps({
+        "workload": "display-path-2000rows-6000ch-1500", "metric": "channel-samples/s (device-timed)",
+        "value": C * T * P / (ms / 1e3), "unit": UNIT, "ms_per_step": ms, "steps": args.steps,
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                     "peak_kind": peak_kind, "bytes_per_channel_sample": 4, "note": "input read once"},
+        "dtype": "f32", "data": "synthetic N(0,1) on the device",
+        "config": {"rows": 2000, "channels_per_row": 3, "samples_per_column": 10, "width": 2048, "mode": "peak",
+                   "display_filter": "order-8 0.5-100 Hz bandpass"}}), flush=True)
+
+
 def ncu_case() -> None:
     """Small profiling case for ncu captures: the paper-scale chain on 6,000
     channels, 4 pushes of 1,500 samples of Gaussian noise (144 MB of input,
@@ -572,7 +641,7 @@ def main() -> None:
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="filark", choices=["filark", "reference"])
     ap.add_argument("--ncu-case", action="store_true", help="run the small profiling case only")
-    ap.add_argument("--workload", default="chain", choices=["chain", "batch", "adjoint", "trigger"],
+    ap.add_argument("--workload", default="chain", choices=["chain", "batch", "adjoint", "trigger", "ops"],
                     help="chain: the paper-scale chain (the benchmark line); the others print their own line")
     args = ap.parse_args()
     if args.ncu_case:
@@ -582,7 +651,7 @@ def main() -> None:
         import torch
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
         {"batch": run_batch_workload, "adjoint": run_adjoint_workload,
-         "trigger": run_trigger_workload}[args.workload](args)
+         "trigger": run_trigger_workload, "ops": run_ops_workload}[args.workload](args)
         return
     args.warmup = max(args.warmup, 3) if args.impl == "filark" else args.warmup
     world = int(os.environ.get("WORLD_SIZE", "1"))

@@ -243,7 +243,7 @@ filark_status filark_chain_run_static(const filark_chain_config *cfg, const floa
  * sos: host, n_sections rows {b0,b1,b2,a0,a1,a2} (raw, not normalised), read
  * during the call only; all finite, a0 != 0; 1 <= n_sections <=
  * FILARK_MAX_SECTIONS.  Signals are time-major float32 as everywhere else
- * (buf[t * ld + c], ld >= n_channels).  Arithmetic is FP64 on the device.
+ * (buf[t * ld + c], ld >= n_channels).  Arithmetic is double-float (FP32 pairs, ~48 bits) on the device.
  *
  * Checkpointing: the forward stores only the cascade state (2 * n_sections
  * doubles per channel) at every multiple of ckpt_every samples, in the

@@ -14,9 +14,11 @@
 //     dL/da_i  = -sum_m y_s[m] w_s[m+i],
 //     g_{s-1}[n] = dL/du_s[n] = b0 w_s[n] + b1 w_s[n+1] + b2 w_s[n+2].
 //
-// Arithmetic is FP64 throughout.  The per-section signals of poles a few 1e-3
-// from z = 1 are not accurate in FP32: rounding the coefficients alone moves
-// the poles by ~1e-5 and the resonance gain by ~1e-3.
+// Arithmetic is double-float (FP32 pairs, ~48 significant bits) on the FP32
+// pipe -- GB300 runs FP64 at 1/64 of the FP32 rate.  Plain FP32 is not enough:
+// for poles a few 1e-3 from z = 1, rounding the coefficients alone moves the
+// poles by ~1e-5 and the resonance gain by ~1e-3.  The per-channel chaining of
+// segment states (a few steps) and the final reductions run in FP64.
 //
 // Parallelism over time as well as channels.  The record is cut into segments
 // of `ckpt` samples; one thread owns one (segment, channel) pair.  Both the
@@ -48,12 +50,52 @@ constexpr int kMaxS = FILARK_MAX_SECTIONS;
 constexpr int kMaxState = 2 * kMaxS;
 constexpr int kAdjThreads = 128;
 
+// A double-float number (hi + lo, ~48 significant bits) on the FP32 pipe:
+// FMA-exact products and TwoSum additions (the "sloppy" sum: error ~2^-44 of
+// the operands, far below what the recursions amplify to).
+struct dd {
+    float hi, lo;
+};
+__device__ __forceinline__ dd dd_norm(float s, float e) {
+    const float hi = s + e;
+    return dd{hi, e - (hi - s)};
+}
+__device__ __forceinline__ dd operator+(dd a, dd b) {
+    const float s = a.hi + b.hi;
+    const float bb = s - a.hi;
+    const float e = (a.hi - (s - bb)) + (b.hi - bb) + a.lo + b.lo;
+    return dd_norm(s, e);
+}
+__device__ __forceinline__ dd operator-(dd a) { return dd{-a.hi, -a.lo}; }
+__device__ __forceinline__ dd operator-(dd a, dd b) { return a + (-b); }
+__device__ __forceinline__ dd operator*(dd a, dd b) {
+    const float p = a.hi * b.hi;
+    float e = fmaf(a.hi, b.hi, -p);
+    e = fmaf(a.hi, b.lo, e);
+    e = fmaf(a.lo, b.hi, e);
+    return dd_norm(p, e);
+}
+__device__ __forceinline__ dd dd_f(float v) { return dd{v, 0.f}; }
+__device__ __forceinline__ float dd_to_f(dd v) { return v.hi + v.lo; }
+// storage: a double-float in an 8-byte slot of the double-typed buffers
+__device__ __forceinline__ dd ld_dd(const double *p) {
+    const float2 v = *reinterpret_cast<const float2 *>(p);
+    return dd{v.x, v.y};
+}
+__device__ __forceinline__ void st_dd(double *p, dd v) { *reinterpret_cast<float2 *>(p) = make_float2(v.hi, v.lo); }
+
+struct DDC {
+    float hi, lo;
+};
+
 struct SosCoef {
     double b[kMaxS][3];   // numerators as given
     double a[kMaxS][3];   // denominators as given (a0 included)
     double nb[kMaxS][3];  // b / a0
     double na[kMaxS][2];  // a1 / a0, a2 / a0
     double ia0[kMaxS];    // 1 / a0
+    // the same as double-float pairs for the kernels
+    DDC db[kMaxS][3], da[kMaxS][3], dnb[kMaxS][3], dna[kMaxS][2], dia0[kMaxS];
 };
 
 struct Transition {
@@ -89,15 +131,31 @@ __host__ __device__ __forceinline__ R adj_step(const SosCoef &k, int s, R g, R &
     return gprev;
 }
 
+__device__ __forceinline__ dd cf(const DDC &c) { return dd{c.hi, c.lo}; }
+
+__device__ __forceinline__ dd tdf2_dd(const SosCoef &k, int s, dd u, dd &z1, dd &z2) {
+    const dd y = cf(k.dnb[s][0]) * u + z1;
+    z1 = cf(k.dnb[s][1]) * u - cf(k.dna[s][0]) * y + z2;
+    z2 = cf(k.dnb[s][2]) * u - cf(k.dna[s][1]) * y;
+    return y;
+}
+
+__device__ __forceinline__ dd adj_dd(const SosCoef &k, int s, dd g, dd &w1, dd &w2, dd &w) {
+    w = (g - cf(k.da[s][1]) * w1 - cf(k.da[s][2]) * w2) * cf(k.dia0[s]);
+    const dd gprev = cf(k.db[s][0]) * w + cf(k.db[s][1]) * w1 + cf(k.db[s][2]) * w2;
+    w2 = w1;
+    w1 = w;
+    return gprev;
+}
+
 __device__ __forceinline__ void seg_range(const Geometry &g, long long seg, long long &t0, long long &t1) {
     t0 = seg * g.ckpt;
     t1 = t0 + g.ckpt < g.N ? t0 + g.ckpt : g.N;
 }
 
-// state arrays are [row][NT] with the thread index fastest (coalesced)
-__device__ __forceinline__ double &at(double *base, long long row, long long NT, long long T) {
-    return base[row * NT + T];
-}
+// State and signal buffers are [row][NT] with the thread index fastest
+// (coalesced); each 8-byte entry holds a double-float.
+__device__ __forceinline__ long long ix(long long row, long long NT, long long T) { return row * NT + T; }
 
 // F1: final state of each segment (except the last) from a zero start, stored
 // in the checkpoint slot of the next segment.
@@ -113,23 +171,23 @@ __global__ void __launch_bounds__(kAdjThreads) fwd_local_kernel(const __grid_con
     if (seg == g.nseg - 1) return;
     long long t0, t1;
     seg_range(g, seg, t0, t1);
-    double z[S][2];
+    dd z[S][2];
 #pragma unroll
-    for (int s = 0; s < S; ++s) z[s][0] = z[s][1] = 0.0;
+    for (int s = 0; s < S; ++s) z[s][0] = z[s][1] = dd_f(0.f);
     for (long long n = t0; n < t1; ++n) {
-        double u = (double)x[n * ldx + c];
+        dd u = dd_f(x[n * ldx + c]);
 #pragma unroll
-        for (int s = 0; s < S; ++s) u = tdf2_step(k, s, u, z[s][0], z[s][1]);
+        for (int s = 0; s < S; ++s) u = tdf2_dd(k, s, u, z[s][0], z[s][1]);
     }
     const long long Tn = T + g.C;  // (seg + 1, c)
 #pragma unroll
     for (int s = 0; s < S; ++s) {
-        at(ckpt, 2 * s, g.NT, Tn) = z[s][0];
-        at(ckpt, 2 * s + 1, g.NT, Tn) = z[s][1];
+        st_dd(ckpt + ix(2 * s, g.NT, Tn), z[s][0]);
+        st_dd(ckpt + ix(2 * s + 1, g.NT, Tn), z[s][1]);
     }
 }
 
-// F2 / B2: one thread per channel chains the segments.
+// F2 / B2: one thread per channel chains the segments (FP64: a few steps).
 //   forward : st[0] = 0,         st[j+1] += T st[j]        (j ascending)
 //   backward: st[nseg-1] = 0,    st[j-1] += T st[j]        (j descending)
 template <int S>
@@ -144,7 +202,7 @@ __global__ void __launch_bounds__(kAdjThreads) chain_segments_kernel(const __gri
 #pragma unroll
     for (int i = 0; i < D; ++i) {
         v[i] = 0.0;
-        at(st, i, g.NT, first * g.C + c) = 0.0;
+        st_dd(st + ix(i, g.NT, first * g.C + c), dd_f(0.f));
     }
     for (long long j = 1; j < g.nseg; ++j) {
         const long long seg = backward ? g.nseg - 1 - j : j;
@@ -152,7 +210,8 @@ __global__ void __launch_bounds__(kAdjThreads) chain_segments_kernel(const __gri
         double nv[D];
 #pragma unroll
         for (int i = 0; i < D; ++i) {
-            double acc = at(st, i, g.NT, T);
+            const dd loc = ld_dd(st + ix(i, g.NT, T));
+            double acc = (double)loc.hi + (double)loc.lo;
 #pragma unroll
             for (int q = 0; q < D; ++q) acc += tr.T[i][q] * v[q];
             nv[i] = acc;
@@ -160,7 +219,8 @@ __global__ void __launch_bounds__(kAdjThreads) chain_segments_kernel(const __gri
 #pragma unroll
         for (int i = 0; i < D; ++i) {
             v[i] = nv[i];
-            at(st, i, g.NT, T) = nv[i];
+            const float hi = (float)nv[i];
+            st_dd(st + ix(i, g.NT, T), dd{hi, (float)(nv[i] - (double)hi)});
         }
     }
 }
@@ -178,17 +238,17 @@ __global__ void __launch_bounds__(kAdjThreads) fwd_run_kernel(const __grid_const
     const int c = (int)(T - seg * g.C);
     long long t0, t1;
     seg_range(g, seg, t0, t1);
-    double z[S][2];
+    dd z[S][2];
 #pragma unroll
     for (int s = 0; s < S; ++s) {
-        z[s][0] = ckpt[(2 * s) * g.NT + T];
-        z[s][1] = ckpt[(2 * s + 1) * g.NT + T];
+        z[s][0] = ld_dd(ckpt + ix(2 * s, g.NT, T));
+        z[s][1] = ld_dd(ckpt + ix(2 * s + 1, g.NT, T));
     }
     for (long long n = t0; n < t1; ++n) {
-        double u = (double)x[n * ldx + c];
+        dd u = dd_f(x[n * ldx + c]);
 #pragma unroll
-        for (int s = 0; s < S; ++s) u = tdf2_step(k, s, u, z[s][0], z[s][1]);
-        y[n * ldy + c] = (float)u;
+        for (int s = 0; s < S; ++s) u = tdf2_dd(k, s, u, z[s][0], z[s][1]);
+        y[n * ldy + c] = dd_to_f(u);
     }
 }
 
@@ -207,19 +267,19 @@ __global__ void __launch_bounds__(kAdjThreads) adj_local_kernel(const __grid_con
     if (seg == 0) return;
     long long t0, t1;
     seg_range(g, seg, t0, t1);
-    double w1[S], w2[S];
+    dd w1[S], w2[S];
 #pragma unroll
-    for (int s = 0; s < S; ++s) w1[s] = w2[s] = 0.0;
+    for (int s = 0; s < S; ++s) w1[s] = w2[s] = dd_f(0.f);
     for (long long n = t1 - 1; n >= t0; --n) {
-        double gg = (double)gy[n * ldg + c], w;
+        dd gg = dd_f(gy[n * ldg + c]), w;
 #pragma unroll
-        for (int s = S - 1; s >= 0; --s) gg = adj_step(k, s, gg, w1[s], w2[s], w);
+        for (int s = S - 1; s >= 0; --s) gg = adj_dd(k, s, gg, w1[s], w2[s], w);
     }
     const long long Tp = T - g.C;  // (seg - 1, c)
 #pragma unroll
     for (int s = 0; s < S; ++s) {
-        at(beta, 2 * s, g.NT, Tp) = w1[s];
-        at(beta, 2 * s + 1, g.NT, Tp) = w2[s];
+        st_dd(beta + ix(2 * s, g.NT, Tp), w1[s]);
+        st_dd(beta + ix(2 * s + 1, g.NT, Tp), w2[s]);
     }
 }
 
@@ -248,80 +308,80 @@ __global__ void __launch_bounds__(kAdjThreads) adj_run_kernel(const __grid_const
 
     // sweep 1: piece start states
     {
-        double z[S][2];
+        dd z[S][2];
 #pragma unroll
         for (int s = 0; s < S; ++s) {
-            z[s][0] = ckpt[(2 * s) * NT + T];
-            z[s][1] = ckpt[(2 * s + 1) * NT + T];
+            z[s][0] = ld_dd(ckpt + ix(2 * s, NT, T));
+            z[s][1] = ld_dd(ckpt + ix(2 * s + 1, NT, T));
         }
         for (long long p = 0; p < npiece; ++p) {
 #pragma unroll
             for (int s = 0; s < S; ++s) {
-                at(sub, p * (2 * S) + 2 * s, NT, T) = z[s][0];
-                at(sub, p * (2 * S) + 2 * s + 1, NT, T) = z[s][1];
+                st_dd(sub + ix(p * (2 * S) + 2 * s, NT, T), z[s][0]);
+                st_dd(sub + ix(p * (2 * S) + 2 * s + 1, NT, T), z[s][1]);
             }
             if (p == npiece - 1) break;
             const long long a = t0 + p * g.P;
             for (long long n = a; n < a + g.P; ++n) {
-                double u = (double)x[n * ldx + c];
+                dd u = dd_f(x[n * ldx + c]);
 #pragma unroll
-                for (int s = 0; s < S; ++s) u = tdf2_step(k, s, u, z[s][0], z[s][1]);
+                for (int s = 0; s < S; ++s) u = tdf2_dd(k, s, u, z[s][0], z[s][1]);
             }
         }
     }
 
-    double w1[S], w2[S], gb[S][3], ga[S][3];
+    dd w1[S], w2[S], gb[S][3], ga[S][3];
 #pragma unroll
     for (int s = 0; s < S; ++s) {
-        w1[s] = beta[(2 * s) * NT + T];
-        w2[s] = beta[(2 * s + 1) * NT + T];
+        w1[s] = ld_dd(beta + ix(2 * s, NT, T));
+        w2[s] = ld_dd(beta + ix(2 * s + 1, NT, T));
 #pragma unroll
-        for (int i = 0; i < 3; ++i) gb[s][i] = ga[s][i] = 0.0;
+        for (int i = 0; i < 3; ++i) gb[s][i] = ga[s][i] = dd_f(0.f);
     }
     for (long long p = npiece - 1; p >= 0; --p) {
         const long long a = t0 + p * g.P;
         const long long b = a + g.P < t1 ? a + g.P : t1;
         {
-            double z[S][2];
+            dd z[S][2];
 #pragma unroll
             for (int s = 0; s < S; ++s) {
-                z[s][0] = at(sub, p * (2 * S) + 2 * s, NT, T);
-                z[s][1] = at(sub, p * (2 * S) + 2 * s + 1, NT, T);
+                z[s][0] = ld_dd(sub + ix(p * (2 * S) + 2 * s, NT, T));
+                z[s][1] = ld_dd(sub + ix(p * (2 * S) + 2 * s + 1, NT, T));
             }
             for (long long n = a; n < b; ++n) {
-                double u = (double)x[n * ldx + c];
+                dd u = dd_f(x[n * ldx + c]);
 #pragma unroll
                 for (int s = 0; s < S; ++s) {
-                    u = tdf2_step(k, s, u, z[s][0], z[s][1]);
-                    at(sig, (n - a) * S + s, NT, T) = u;
+                    u = tdf2_dd(k, s, u, z[s][0], z[s][1]);
+                    st_dd(sig + ix((n - a) * S + s, NT, T), u);
                 }
             }
         }
         for (long long n = b - 1; n >= a; --n) {
-            double gg = (double)gy[n * ldg + c];
+            dd gg = dd_f(gy[n * ldg + c]);
 #pragma unroll
             for (int s = S - 1; s >= 0; --s) {
-                const double ys = at(sig, (n - a) * S + s, NT, T);
-                const double us = s == 0 ? (double)x[n * ldx + c] : at(sig, (n - a) * S + s - 1, NT, T);
-                const double wn1 = w1[s], wn2 = w2[s];
-                double w;
-                gg = adj_step(k, s, gg, w1[s], w2[s], w);
-                gb[s][0] += us * w;
-                gb[s][1] += us * wn1;
-                gb[s][2] += us * wn2;
-                ga[s][0] -= ys * w;
-                ga[s][1] -= ys * wn1;
-                ga[s][2] -= ys * wn2;
+                const dd ys = ld_dd(sig + ix((n - a) * S + s, NT, T));
+                const dd us = s == 0 ? dd_f(x[n * ldx + c]) : ld_dd(sig + ix((n - a) * S + s - 1, NT, T));
+                const dd wn1 = w1[s], wn2 = w2[s];
+                dd w;
+                gg = adj_dd(k, s, gg, w1[s], w2[s], w);
+                gb[s][0] = gb[s][0] + us * w;
+                gb[s][1] = gb[s][1] + us * wn1;
+                gb[s][2] = gb[s][2] + us * wn2;
+                ga[s][0] = ga[s][0] - ys * w;
+                ga[s][1] = ga[s][1] - ys * wn1;
+                ga[s][2] = ga[s][2] - ys * wn2;
             }
-            if (gx) gx[n * ldgx + c] = (float)gg;
+            if (gx) gx[n * ldgx + c] = dd_to_f(gg);
         }
     }
 #pragma unroll
     for (int s = 0; s < S; ++s)
 #pragma unroll
         for (int i = 0; i < 3; ++i) {
-            at(gpart, 6 * s + i, NT, T) = gb[s][i];
-            at(gpart, 6 * s + 3 + i, NT, T) = ga[s][i];
+            gpart[ix(6 * s + i, NT, T)] = (double)gb[s][i].hi + (double)gb[s][i].lo;
+            gpart[ix(6 * s + 3 + i, NT, T)] = (double)ga[s][i].hi + (double)ga[s][i].lo;
         }
 }
 
@@ -358,6 +418,20 @@ bool load_coef(const double *sos, int S, SosCoef &k) {
         k.na[s][0] = r[4] / r[3];
         k.na[s][1] = r[5] / r[3];
         k.ia0[s] = 1.0 / r[3];
+        auto split = [](double v) {
+            DDC d;
+            d.hi = (float)v;
+            d.lo = (float)(v - (double)d.hi);
+            return d;
+        };
+        for (int i = 0; i < 3; ++i) {
+            k.db[s][i] = split(k.b[s][i]);
+            k.da[s][i] = split(k.a[s][i]);
+            k.dnb[s][i] = split(k.nb[s][i]);
+        }
+        k.dna[s][0] = split(k.na[s][0]);
+        k.dna[s][1] = split(k.na[s][1]);
+        k.dia0[s] = split(k.ia0[s]);
     }
     return true;
 }
