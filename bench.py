@@ -192,6 +192,22 @@ def run_reference(args, rank: int, world: int) -> None:
 
 # ------------------------------------------------------------- GPU timing --
 
+def max_over_ranks(value: float, dist, device=None) -> float:
+    """The slowest rank's time (every rank gets it); the value itself when
+    running alone."""
+    if not dist:
+        return float(value)
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank: float, world: int, seconds: float) -> float:
+    """Units all ranks processed per second of the slowest rank (weak scaling:
+    every rank runs its own replica of the workload)."""
+    return units_per_rank * world / seconds
+
 def run_gpu(args, rank: int, world: int, dist) -> None:
     import ctypes as ct
 
@@ -248,16 +264,11 @@ def run_gpu(args, rank: int, world: int, dist) -> None:
             step()
         ev1.record(stream)
         ev1.synchronize()
-    ms = ev0.elapsed_time(ev1)
-    if dist:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ev0.elapsed_time(ev1), dist, dev)
     abi.check(abi.filark_chain_sync_status(h, sh), "sync")
     launches_per_push = (T + 2047) // 2048
     launches = args.steps * n_push * launches_per_push
-    units = C * N * args.steps * world
-    value = units / (ms / 1e3)
+    value = whole_job_rate(C * N * args.steps, world, ms / 1e3)
 
     # ---- end to end through the host-buffer entry point (pinned host memory)
     e2e_steps = max(1, min(args.steps, 3))
@@ -278,12 +289,8 @@ def run_gpu(args, rank: int, world: int, dist) -> None:
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
         step_host()
-    e2e_s = time.perf_counter() - t0
-    if dist:
-        t = torch.tensor([e2e_s], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e_value = C * N * e2e_steps * world / e2e_s
+    e2e_s = max_over_ranks(time.perf_counter() - t0, dist, dev)
+    e2e_value = whole_job_rate(C * N * e2e_steps, world, e2e_s)
     chain.close()
 
     if rank != 0:
