@@ -568,14 +568,20 @@ def run_ops_workload(args) -> None:
     y = torch.empty_like(x)
     peak, peak_kind = measured_peak_hbm()
     sos = butter_bandpass(w["order"], *w["band"], w["fs"])
+    # algorithmic bytes per channel-sample: input read + output written, plus
+    # the state each operator must read and write per push (FIR history and
+    # FFT overlap tail: M - 1 samples per channel each way; running mean/AGC:
+    # the double-float prefix written and the exiting prefix read back)
+    state = lambda M: 8.0 * (M - 1) / T
     ops = [
         ("fir-101", lambda: TemporalOp(abi.FILARK_TOP_FIR, C, 101,
-                                       synth.windowed_sinc_bandpass(101, 5.0, 100.0, w["fs"]), max_chunk=T), 8, 3),
-        ("running-mean-3000", lambda: TemporalOp(abi.FILARK_TOP_MEAN, C, 3000, max_chunk=T), 8, 2),
-        ("running-agc-3000", lambda: TemporalOp(abi.FILARK_TOP_AGC, C, 3000, max_chunk=T), 8, 2),
+                                       synth.windowed_sinc_bandpass(101, 5.0, 100.0, w["fs"]), max_chunk=T),
+         8 + state(101), 3),
+        ("running-mean-3000", lambda: TemporalOp(abi.FILARK_TOP_MEAN, C, 3000, max_chunk=T), 24, 2),
+        ("running-agc-3000", lambda: TemporalOp(abi.FILARK_TOP_AGC, C, 3000, max_chunk=T), 24, 2),
         ("ema-equalisation", lambda: TemporalOp(abi.FILARK_TOP_EMA, C, alpha=1e-3, max_chunk=T), 8, 1),
         ("fft-bandpass-4001", lambda: FFTFilter(C, synth.windowed_sinc_bandpass(4001, 0.5, 100.0, w["fs"]),
-                                                max_chunk=T), 8, 1),
+                                                max_chunk=T), 8 + state(4001), 1),
     ]
     for name, make, bps, launches in ops:
         op = make()
@@ -594,7 +600,7 @@ def run_ops_workload(args) -> None:
             "value": C * T * P / (ms / 1e3), "unit": UNIT, "ms_per_step": ms, "steps": args.steps,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "peak_kind": peak_kind,
-                         "bytes_per_channel_sample": bps, "note": "input read + output written"},
+                         "bytes_per_channel_sample": bps, "note": "input read + output written + carried state"},
             "gpu_launches": launches * P * args.steps, "dtype": "f32", "data": "synthetic N(0,1) on the device"}),
             flush=True)
     v = View(C, 3, 10, 2048, abi.FILARK_VIEW_PEAK, sos, max_chunk=T)

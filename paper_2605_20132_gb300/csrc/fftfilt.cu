@@ -11,10 +11,19 @@
 // Two channels share one complex transform (x1 + i x2; h is real, so the
 // real and imaginary parts of the result are the two convolutions).
 //
-// FFT: radix-2 Stockham in shared memory, one CTA per channel pair and block,
-// log2(N) passes of N/2 butterflies, twiddles from a table made on the host in
-// double precision.  N <= 8192 (64 KB of complex floats, double-buffered in
-// 128 KB of shared memory).
+// FFT: Stockham autosort in shared memory, one CTA per channel pair and
+// block.  The log2(N) radix-2 steps are grouped into passes of radix 8 (one
+// radix 2 or radix 4 pass first when log2(N) is not a multiple of 3); each
+// thread does whole radix-R butterflies in registers.  The first forward pass
+// reads the input block straight from global memory, the last forward pass
+// multiplies by H, and the last inverse pass writes the outputs and the new
+// tail straight to global memory.  The tail is double-buffered (read from one
+// buffer, written to the other), so the epilogue needs no barrier.  Twiddles
+// come from a host table made in double precision; a butterfly's powers
+// w^2 .. w^7 are products of at most three table values' roundings.
+// N <= 8192 (64 KB of complex floats, double-buffered in 128 KB of shared
+// memory).
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -27,38 +36,57 @@ using namespace filark;
 
 namespace {
 
-constexpr int kFftThreads = 512;
+constexpr int kFftMaxThreads = 1024;
 constexpr int kFftMaxLog = 13;     // N <= 8192
 
 __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
     return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+// z * (d i), d = -1 forward, +1 inverse
+template <bool INV>
+__device__ __forceinline__ float2 rot(float2 z) {
+    return INV ? make_float2(-z.y, z.x) : make_float2(z.y, -z.x);
+}
 
-// Stockham radix-2 FFT of length N = 2^logN on buffers a <-> b in shared
-// memory; inverse = false: exp(-i...) (forward), true: exp(+i...) (unscaled).
-// tw[k] = exp(-2 pi i k / N), k < N/2.  Returns the buffer that holds the
-// result.  All threads of the CTA call it.
-__device__ float2 *fft_stockham(float2 *a, float2 *b, int logN, bool inverse, const float2 *__restrict__ tw) {
-    const int N = 1 << logN, half = N >> 1;
-    for (int s = 0; s < logN; ++s) {
-        const int m = 1 << s;           // length of the sub-transforms already done
-        for (int t = threadIdx.x; t < half; t += blockDim.x) {
-            const int j = t & (m - 1);  // position inside the sub-transform
-            const int k = t >> s;       // which pair of sub-transforms
-            // twiddle exp(-+ i pi j / m) = tw[j N / (2m)]
-            float2 w = __ldg(tw + (j << (logN - 1 - s)));
-            if (inverse) w.y = -w.y;
-            const float2 u = a[t];
-            const float2 v = cmul(w, a[t + half]);
-            b[2 * k * m + j] = make_float2(u.x + v.x, u.y + v.y);
-            b[2 * k * m + j + m] = make_float2(u.x - v.x, u.y - v.y);
-        }
-        __syncthreads();
-        float2 *tmp = a;
-        a = b;
-        b = tmp;
+// In-register DFT of size R: y_q = sum_r x_r exp(d 2 pi i r q / R).
+template <bool INV>
+__device__ __forceinline__ void dft4(float2 &a0, float2 &a1, float2 &a2, float2 &a3) {
+    const float2 s0 = cadd(a0, a2), s1 = csub(a0, a2), s2 = cadd(a1, a3), s3 = rot<INV>(csub(a1, a3));
+    a0 = cadd(s0, s2);
+    a2 = csub(s0, s2);
+    a1 = cadd(s1, s3);
+    a3 = csub(s1, s3);
+}
+
+template <int R, bool INV>
+__device__ __forceinline__ void dft(float2 (&x)[R]) {
+    if constexpr (R == 2) {
+        const float2 u = x[0];
+        x[0] = cadd(u, x[1]);
+        x[1] = csub(u, x[1]);
+    } else if constexpr (R == 4) {
+        dft4<INV>(x[0], x[1], x[2], x[3]);
+    } else {
+        // even / odd halves, then y_q = E_q + w8^q O_q, y_{q+4} = E_q - w8^q O_q
+        dft4<INV>(x[0], x[2], x[4], x[6]);
+        dft4<INV>(x[1], x[3], x[5], x[7]);
+        const float c = 0.70710678118654752f;
+        const float d = INV ? 1.f : -1.f;
+        const float2 o1 = make_float2(c * (x[3].x - d * x[3].y), c * (x[3].y + d * x[3].x));
+        const float2 o2 = rot<INV>(x[5]);
+        const float2 o3 = make_float2(c * (-x[7].x - d * x[7].y), c * (-x[7].y + d * x[7].x));
+        const float2 e0 = x[0], e1 = x[2], e2 = x[4], e3 = x[6], o0 = x[1];
+        x[0] = cadd(e0, o0);
+        x[4] = csub(e0, o0);
+        x[1] = cadd(e1, o1);
+        x[5] = csub(e1, o1);
+        x[2] = cadd(e2, o2);
+        x[6] = csub(e2, o2);
+        x[3] = cadd(e3, o3);
+        x[7] = csub(e3, o3);
     }
-    return a;
 }
 
 struct FftParams {
@@ -66,72 +94,198 @@ struct FftParams {
     float scale;        // 1 / N
 };
 
-// One CTA per (channel pair, block) of a launch; the blocks of one launch are
-// consecutive and independent given the tail, so a launch covers exactly one
-// block per channel pair and the host launches the blocks of a push in order.
-__global__ void __launch_bounds__(kFftThreads) fftfilt_block_kernel(const __grid_constant__ FftParams fp,
-                                                                    const float *__restrict__ x, long long ldx,
-                                                                    int len, int C,
-                                                                    const float2 *__restrict__ H,
-                                                                    const float2 *__restrict__ tw,
-                                                                    float *__restrict__ tail,   // [C][M-1]
-                                                                    float *__restrict__ y, long long ldy) {
-    extern __shared__ float2 sm[];
-    float2 *a = sm, *b = sm + fp.N;
-    const int c1 = 2 * blockIdx.x, c2 = c1 + 1;
-    const bool has2 = c2 < C;
-    for (int i = threadIdx.x; i < fp.N; i += blockDim.x) {
-        float re = 0.f, im = 0.f;
-        if (i < len) {
-            re = x[(long long)i * ldx + c1];
-            if (has2) im = x[(long long)i * ldx + c2];
+// Where a pass reads from and writes to.
+enum { SRC_SMEM = 0, SRC_GIN = 1 };
+enum { DST_SMEM = 0, DST_SMEM_H = 1, DST_GOUT = 2 };
+
+struct BlockIO {
+    const float *x;         // input block, time-major, row stride ldx
+    long long ldx;
+    int len;                // samples in this block
+    int c1;                 // first channel of the pair (c1 + 1 the second, if has2)
+    bool has2;
+    const float2 *H;        // [N] spectrum of the taps
+    const float *told;      // [C][M-1] tail before this block (NULL if M = 1)
+    float *tnew;            // [C][M-1] tail after this block
+    float *y;               // output block, row stride ldy
+    long long ldy;
+    int T1;                 // M - 1
+    float scale;
+};
+
+// One Stockham pass of radix R: sub-transforms of length m = 2^logm are
+// combined R at a time.  Butterfly t (< N/R) reads elements t + r N/R, scales
+// them by w^r with w = exp(d 2 pi i j / (R m)), j = t mod m, and writes the
+// radix-R DFT to (t - j) R + j + q m.
+template <int R, bool INV, int SRC, int DST>
+__device__ __forceinline__ void radix_pass(const float2 *__restrict__ a, float2 *__restrict__ b, int logN, int logm,
+                                           const float2 *__restrict__ tw, const BlockIO &io) {
+    constexpr int logR = R == 2 ? 1 : (R == 4 ? 2 : 3);
+    const int N = 1 << logN, stride = N >> logR, m = 1 << logm;
+    for (int t = threadIdx.x; t < stride; t += blockDim.x) {
+        const int j = t & (m - 1);
+        float2 x[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const int i = t + r * stride;
+            if constexpr (SRC == SRC_GIN) {
+                float re = 0.f, im = 0.f;
+                if (i < io.len) {
+                    re = __ldg(io.x + (long long)i * io.ldx + io.c1);
+                    if (io.has2) im = __ldg(io.x + (long long)i * io.ldx + io.c1 + 1);
+                }
+                x[r] = make_float2(re, im);
+            } else {
+                x[r] = a[i];
+            }
         }
-        a[i] = make_float2(re, im);
-    }
-    __syncthreads();
-    float2 *X = fft_stockham(a, b, fp.logN, false, tw);
-    float2 *other = X == a ? b : a;
-    for (int i = threadIdx.x; i < fp.N; i += blockDim.x) X[i] = cmul(X[i], H[i]);
-    __syncthreads();
-    float2 *z = fft_stockham(X, other, fp.logN, true, tw);
-    const int T1 = fp.M - 1;
-    // outputs, then the new tail (each index is read before it is written:
-    // outputs read tail[i] for i < len, the new tail entry i reads tail[i+len])
-    for (int i = threadIdx.x; i < len; i += blockDim.x) {
-        const float2 v = z[i];
-        const float t1 = i < T1 ? tail[(long long)c1 * T1 + i] : 0.f;
-        y[(long long)i * ldy + c1] = v.x * fp.scale + t1;
-        if (has2) {
-            const float t2 = i < T1 ? tail[(long long)c2 * T1 + i] : 0.f;
-            y[(long long)i * ldy + c2] = v.y * fp.scale + t2;
+        if (logm > 0) {
+            float2 w = __ldg(tw + (j << (logN - logm - logR)));
+            if (INV) w.y = -w.y;
+            if constexpr (R == 2) {
+                x[1] = cmul(x[1], w);
+            } else if constexpr (R == 4) {
+                const float2 w2 = cmul(w, w);
+                x[1] = cmul(x[1], w);
+                x[2] = cmul(x[2], w2);
+                x[3] = cmul(x[3], cmul(w2, w));
+            } else {
+                const float2 w2 = cmul(w, w), w4 = cmul(w2, w2), w3 = cmul(w2, w);
+                x[1] = cmul(x[1], w);
+                x[2] = cmul(x[2], w2);
+                x[3] = cmul(x[3], w3);
+                x[4] = cmul(x[4], w4);
+                x[5] = cmul(x[5], cmul(w4, w));
+                x[6] = cmul(x[6], cmul(w4, w2));
+                x[7] = cmul(x[7], cmul(w4, w3));
+            }
         }
-    }
-    __syncthreads();
-    // new tail in registers first (in-place shift), then stored
-    for (int base = 0; base < T1; base += blockDim.x) {
-        const int i = base + threadIdx.x;
-        float n1 = 0.f, n2 = 0.f;
-        if (i < T1) {
-            const float2 v = z[len + i];
-            n1 = v.x * fp.scale + (i + len < T1 ? tail[(long long)c1 * T1 + i + len] : 0.f);
-            if (has2) n2 = v.y * fp.scale + (i + len < T1 ? tail[(long long)c2 * T1 + i + len] : 0.f);
+        dft<R, INV>(x);
+        const int base = ((t - j) << logR) + j;
+#pragma unroll
+        for (int q = 0; q < R; ++q) {
+            const int i = base + (q << logm);
+            if constexpr (DST == DST_SMEM) {
+                b[i] = x[q];
+            } else if constexpr (DST == DST_SMEM_H) {
+                b[i] = cmul(x[q], __ldg(io.H + i));
+            } else {
+                // z[i] (scaled) plus the old tail gives output i (i < len) or
+                // new tail entry i - len (len <= i < len + M - 1)
+                if (i < io.len + io.T1) {
+                    float v1 = x[q].x * io.scale, v2 = x[q].y * io.scale;
+                    if (i < io.T1) {
+                        v1 += io.told[(long long)io.c1 * io.T1 + i];
+                        if (io.has2) v2 += io.told[(long long)(io.c1 + 1) * io.T1 + i];
+                    }
+                    if (i < io.len) {
+                        io.y[(long long)i * io.ldy + io.c1] = v1;
+                        if (io.has2) io.y[(long long)i * io.ldy + io.c1 + 1] = v2;
+                    } else {
+                        io.tnew[(long long)io.c1 * io.T1 + (i - io.len)] = v1;
+                        if (io.has2) io.tnew[(long long)(io.c1 + 1) * io.T1 + (i - io.len)] = v2;
+                    }
+                }
+            }
         }
-        __syncthreads();
-        if (i < T1) {
-            tail[(long long)c1 * T1 + i] = n1;
-            if (has2) tail[(long long)c2 * T1 + i] = n2;
-        }
-        __syncthreads();
     }
 }
 
-__global__ void fft_of_taps_kernel(const __grid_constant__ FftParams fp, const float *__restrict__ h,
-                                   const float2 *__restrict__ tw, float2 *__restrict__ H) {
+template <bool INV, int SRC, int DST>
+__device__ __forceinline__ void radix_pass_any(int logR, const float2 *a, float2 *b, int logN, int logm,
+                                               const float2 *tw, const BlockIO &io) {
+    if (logR == 1) radix_pass<2, INV, SRC, DST>(a, b, logN, logm, tw, io);
+    else if (logR == 2) radix_pass<4, INV, SRC, DST>(a, b, logN, logm, tw, io);
+    else radix_pass<8, INV, SRC, DST>(a, b, logN, logm, tw, io);
+}
+
+// Forward transform of the input block (read from global memory), times H
+// when io.H is set; the result is left in the returned buffer.
+__device__ float2 *fft_forward(float2 *a, float2 *b, int logN, const float2 *tw, const BlockIO &io) {
+    const int rem = logN % 3, npass = logN / 3 + (rem ? 1 : 0);
+    int logm = 0;
+    for (int p = 0; p < npass; ++p) {
+        const int logR = (p == 0 && rem) ? rem : 3;
+        const bool last = p == npass - 1;
+        if (p == 0) {
+            if (last && io.H) radix_pass_any<false, SRC_GIN, DST_SMEM_H>(logR, a, b, logN, logm, tw, io);
+            else radix_pass_any<false, SRC_GIN, DST_SMEM>(logR, a, b, logN, logm, tw, io);
+        } else {
+            if (last && io.H) radix_pass_any<false, SRC_SMEM, DST_SMEM_H>(logR, a, b, logN, logm, tw, io);
+            else radix_pass_any<false, SRC_SMEM, DST_SMEM>(logR, a, b, logN, logm, tw, io);
+        }
+        __syncthreads();
+        float2 *tmp = a;
+        a = b;
+        b = tmp;
+        logm += logR;
+    }
+    return a;
+}
+
+// Inverse transform of a (unscaled); the last pass writes outputs and tail.
+__device__ void fft_inverse_out(float2 *a, float2 *b, int logN, const float2 *tw, const BlockIO &io) {
+    const int rem = logN % 3, npass = logN / 3 + (rem ? 1 : 0);
+    int logm = 0;
+    for (int p = 0; p < npass; ++p) {
+        const int logR = (p == 0 && rem) ? rem : 3;
+        if (p == npass - 1) {
+            radix_pass_any<true, SRC_SMEM, DST_GOUT>(logR, a, b, logN, logm, tw, io);
+        } else {
+            radix_pass_any<true, SRC_SMEM, DST_SMEM>(logR, a, b, logN, logm, tw, io);
+            __syncthreads();
+            float2 *tmp = a;
+            a = b;
+            b = tmp;
+        }
+        logm += logR;
+    }
+}
+
+int fft_threads(int N) { return std::max(64, std::min(kFftMaxThreads, N / 8)); }
+
+// One CTA per (channel pair, block) of a launch; the blocks of one launch are
+// consecutive and independent given the tail, so a launch covers exactly one
+// block per channel pair and the host launches the blocks of a push in order.
+__global__ void __launch_bounds__(kFftMaxThreads) fftfilt_block_kernel(const __grid_constant__ FftParams fp,
+                                                                       const float *__restrict__ x, long long ldx,
+                                                                       int len, int C,
+                                                                       const float2 *__restrict__ H,
+                                                                       const float2 *__restrict__ tw,
+                                                                       const float *__restrict__ told,
+                                                                       float *__restrict__ tnew,
+                                                                       float *__restrict__ y, long long ldy) {
     extern __shared__ float2 sm[];
-    float2 *a = sm, *b = sm + fp.N;
-    for (int i = threadIdx.x; i < fp.N; i += blockDim.x) a[i] = make_float2(i < fp.M ? h[i] : 0.f, 0.f);
-    __syncthreads();
-    float2 *r = fft_stockham(a, b, fp.logN, false, tw);
+    BlockIO io;
+    io.x = x;
+    io.ldx = ldx;
+    io.len = len;
+    io.c1 = 2 * blockIdx.x;
+    io.has2 = io.c1 + 1 < C;
+    io.H = H;
+    io.told = told;
+    io.tnew = tnew;
+    io.y = y;
+    io.ldy = ldy;
+    io.T1 = fp.M - 1;
+    io.scale = fp.scale;
+    float2 *X = fft_forward(sm, sm + fp.N, fp.logN, tw, io);
+    fft_inverse_out(X, X == sm ? sm + fp.N : sm, fp.logN, tw, io);
+}
+
+__global__ void __launch_bounds__(kFftMaxThreads) fft_of_taps_kernel(const __grid_constant__ FftParams fp,
+                                                                     const float *__restrict__ h,
+                                                                     const float2 *__restrict__ tw,
+                                                                     float2 *__restrict__ H) {
+    extern __shared__ float2 sm[];
+    BlockIO io{};
+    io.x = h;
+    io.ldx = 1;
+    io.len = fp.M;
+    io.c1 = 0;
+    io.has2 = false;
+    io.H = nullptr;
+    const float2 *r = fft_forward(sm, sm + fp.N, fp.logN, tw, io);
     for (int i = threadIdx.x; i < fp.N; i += blockDim.x) H[i] = r[i];
 }
 
@@ -168,7 +322,8 @@ struct filark_fftfilt {
     FftParams fp{};
     float2 *H = nullptr;
     float2 *tw = nullptr;       // exp(-2 pi i k / N), k < N/2
-    float *tail = nullptr;
+    float *tail[2] = {nullptr, nullptr};   // [C][M-1] each; tail[cur] is current
+    int cur = 0;
 };
 
 extern "C" {
@@ -217,7 +372,9 @@ filark_status filark_fftfilt_create(int n_channels, int n_taps, const double *ta
     cudaError_t e = cudaMalloc(&f->H, sizeof(float2) * (size_t)f->fp.N);
     if (e == cudaSuccess) e = cudaMalloc(&f->tw, sizeof(float2) * twh.size());
     if (e == cudaSuccess) e = cudaMemcpy(f->tw, twh.data(), sizeof(float2) * twh.size(), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess && n_taps > 1) e = cudaMalloc(&f->tail, sizeof(float) * (size_t)n_channels * (n_taps - 1));
+    const size_t tail_bytes = sizeof(float) * (size_t)n_channels * (size_t)(n_taps - 1);
+    if (e == cudaSuccess && n_taps > 1) e = cudaMalloc(&f->tail[0], tail_bytes);
+    if (e == cudaSuccess && n_taps > 1) e = cudaMalloc(&f->tail[1], tail_bytes);
     if (e == cudaSuccess) e = cudaMalloc(&dh, sizeof(float) * (size_t)n_taps);
     if (e == cudaSuccess) e = cudaMemcpy(dh, hf.data(), sizeof(float) * hf.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess)
@@ -227,16 +384,17 @@ filark_status filark_fftfilt_create(int n_channels, int n_taps, const double *ta
         e = cudaFuncSetAttribute(fft_of_taps_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)fft_smem(1 << kFftMaxLog));
     if (e == cudaSuccess) {
-        fft_of_taps_kernel<<<1, kFftThreads, fft_smem(f->fp.N)>>>(f->fp, dh, f->tw, f->H);
+        fft_of_taps_kernel<<<1, fft_threads(f->fp.N), fft_smem(f->fp.N)>>>(f->fp, dh, f->tw, f->H);
         e = cudaGetLastError();
     }
-    if (e == cudaSuccess && f->tail) e = cudaMemset(f->tail, 0, sizeof(float) * (size_t)n_channels * (n_taps - 1));
+    if (e == cudaSuccess && f->tail[0]) e = cudaMemset(f->tail[0], 0, tail_bytes);
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     if (dh) cudaFree(dh);
     if (e != cudaSuccess) {
         if (f->H) cudaFree(f->H);
         if (f->tw) cudaFree(f->tw);
-        if (f->tail) cudaFree(f->tail);
+        if (f->tail[0]) cudaFree(f->tail[0]);
+        if (f->tail[1]) cudaFree(f->tail[1]);
         delete f;
         return fcuda(e, "fftfilt create");
     }
@@ -260,9 +418,10 @@ filark_status filark_fftfilt_push(filark_fftfilt *f, const float *d_in, int64_t 
     const unsigned pairs = (unsigned)((f->C + 1) / 2);
     for (int64_t t = 0; t < n_samples; t += f->fp.L) {
         const int len = (int)std::min<int64_t>(f->fp.L, n_samples - t);
-        fftfilt_block_kernel<<<pairs, kFftThreads, fft_smem(f->fp.N), s>>>(f->fp, d_in + t * ld_in, ld_in, len, f->C,
-                                                                           f->H, f->tw, f->tail, d_out + t * ld_out,
-                                                                           ld_out);
+        fftfilt_block_kernel<<<pairs, fft_threads(f->fp.N), fft_smem(f->fp.N), s>>>(
+            f->fp, d_in + t * ld_in, ld_in, len, f->C, f->H, f->tw, f->tail[f->cur], f->tail[1 - f->cur],
+            d_out + t * ld_out, ld_out);
+        f->cur = 1 - f->cur;
     }
     const cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? FILARK_OK : fcuda(e, "fftfilt push");
@@ -272,8 +431,8 @@ filark_status filark_fftfilt_reset(filark_fftfilt *f, filark_stream_t stream) {
     if (!f) return ffail(FILARK_EINVAL, "filter is NULL");
     DeviceGuard dg(f->device);
     if (!dg.ok) return ffail(FILARK_ECUDA, "cudaSetDevice failed");
-    if (!f->tail) return FILARK_OK;
-    const cudaError_t e = cudaMemsetAsync(f->tail, 0, sizeof(float) * (size_t)f->C * (f->fp.M - 1),
+    if (!f->tail[0]) return FILARK_OK;
+    const cudaError_t e = cudaMemsetAsync(f->tail[f->cur], 0, sizeof(float) * (size_t)f->C * (f->fp.M - 1),
                                           (cudaStream_t)stream);
     return e == cudaSuccess ? FILARK_OK : fcuda(e, "fftfilt reset");
 }
@@ -291,7 +450,8 @@ filark_status filark_fftfilt_destroy(filark_fftfilt *f) {
     cudaDeviceSynchronize();
     if (f->H) cudaFree(f->H);
     if (f->tw) cudaFree(f->tw);
-    if (f->tail) cudaFree(f->tail);
+    if (f->tail[0]) cudaFree(f->tail[0]);
+    if (f->tail[1]) cudaFree(f->tail[1]);
     delete f;
     return FILARK_OK;
 }

@@ -36,8 +36,8 @@ def run(x, taps, chunks, block_len=0):
     return yd.cpu().numpy().astype(np.float64), info
 
 
-@pytest.mark.parametrize("M,block_len", [(1, 0), (31, 0), (257, 100), (257, 0), (1001, 0), (4001, 0),
-                                         (2000, 6000)])
+@pytest.mark.parametrize("M,block_len", [(1, 0), (2, 0), (3, 0), (5, 0), (9, 0), (31, 0), (100, 0), (257, 100),
+                                         (257, 0), (1001, 0), (1500, 0), (4001, 0), (2000, 6000)])
 def test_fftfilt_matches_direct_fir(oracle_mod, M, block_len):
     rng = np.random.default_rng(130 + M)
     C = 9
