@@ -37,6 +37,8 @@ namespace {
 
 constexpr int kSeg = 32;          // samples per segment
 constexpr int kTrigThreads = 128;
+constexpr int kScanThreads = 32;   // one warp per CTA: the scan has only C threads
+constexpr int kScanBatch = 16;
 
 // packed segment summary: bits 0/1 final state from 0/1, bits 2/3 a run ends
 // inside when entering with 0/1, bits 4-9 / 10-15 last rise + 1 (0 = none)
@@ -70,24 +72,33 @@ __global__ void __launch_bounds__(kTrigThreads) trig_summary_kernel(const float 
 }
 
 // One thread per channel: state at each segment start, and the carried state.
-__global__ void __launch_bounds__(kTrigThreads) trig_scan_kernel(const unsigned *__restrict__ summ, int C, int nseg,
+__global__ void __launch_bounds__(kScanThreads) trig_scan_kernel(const unsigned *__restrict__ summ, int C, int nseg,
                                                                  long long n0, int *__restrict__ st_s,
                                                                  long long *__restrict__ st_t,
                                                                  int *__restrict__ seg_s,
                                                                  long long *__restrict__ seg_t) {
-    const int c = blockIdx.x * kTrigThreads + threadIdx.x;
+    const int c = blockIdx.x * kScanThreads + threadIdx.x;
     if (c >= C) return;
     int s = st_s[c];
     long long t = st_t[c];
-#pragma unroll 4
-    for (int g = 0; g < nseg; ++g) {
-        const unsigned m = summ[(size_t)g * C + c];
-        seg_s[(size_t)g * C + c] = s;
-        seg_t[(size_t)g * C + c] = t;
-        const int f = (m >> s) & 1;
-        const int rise = (int)((m >> (s ? 10 : 4)) & 63) - 1;
-        if (f) t = rise >= 0 ? n0 + (long long)g * kSeg + rise : t;
-        s = f;
+    // the summaries do not depend on the chained state: load them kScanBatch
+    // at a time, then chain in registers
+    for (int g0 = 0; g0 < nseg; g0 += kScanBatch) {
+        unsigned m[kScanBatch];
+#pragma unroll
+        for (int q = 0; q < kScanBatch; ++q) m[q] = g0 + q < nseg ? __ldcs(summ + (size_t)(g0 + q) * C + c) : 0u;
+#pragma unroll
+        for (int q = 0; q < kScanBatch; ++q) {
+            const int g = g0 + q;
+            if (g < nseg) {
+                seg_s[(size_t)g * C + c] = s;
+                seg_t[(size_t)g * C + c] = t;
+                const int f = (m[q] >> s) & 1;
+                const int rise = (int)((m[q] >> (s ? 10 : 4)) & 63) - 1;
+                if (f) t = rise >= 0 ? n0 + (long long)g * kSeg + rise : t;
+                s = f;
+            }
+        }
     }
     st_s[c] = s;
     st_t[c] = t;
@@ -121,13 +132,20 @@ __global__ void __launch_bounds__(kTrigThreads) trig_emit_kernel(const float *__
     int s = seg_s[idx];
     if (!((summ[idx] >> (2 + s)) & 1)) return;   // no run ends in this segment
     long long t = seg_t[idx];
-    const int a = seg * kSeg, b = min(a + kSeg, T);
-    for (int k = a; k < b; ++k) {
-        const float r = R[(long long)k * ld + c];
-        const int n = r >= on ? 1 : (r < off ? 0 : s);
-        if (n && !s) t = n0 + k;
-        if (!n && s) append_record(recs, cap, count, t, n0 + k, c, 0);
-        s = n;
+    const int a = seg * kSeg, nk = min(kSeg, T - a);
+    // all of the segment's samples in flight at once, then the automaton
+    float rv[kSeg];
+#pragma unroll
+    for (int k = 0; k < kSeg; ++k) rv[k] = k < nk ? __ldg(R + (long long)(a + k) * ld + c) : 0.f;
+#pragma unroll
+    for (int k = 0; k < kSeg; ++k) {
+        if (k < nk) {
+            const float r = rv[k];
+            const int n = r >= on ? 1 : (r < off ? 0 : s);
+            if (n && !s) t = n0 + a + k;
+            if (!n && s) append_record(recs, cap, count, t, n0 + a + k, c, 0);
+            s = n;
+        }
     }
 }
 
@@ -466,9 +484,9 @@ filark_status filark_trigger_push(filark_trigger *t, const float *d_ratio, int64
     const int T = (int)n_samples;
     const int nseg = (T + kSeg - 1) / kSeg;
     const dim3 grid2((unsigned)((t->C + kTrigThreads - 1) / kTrigThreads), (unsigned)nseg);
-    const unsigned grid1 = (unsigned)((t->C + kTrigThreads - 1) / kTrigThreads);
+    const unsigned grid1 = (unsigned)((t->C + kScanThreads - 1) / kScanThreads);
     trig_summary_kernel<<<grid2, kTrigThreads, 0, s>>>(d_ratio, ld, t->C, T, t->on_f, t->off_f, t->summ);
-    trig_scan_kernel<<<grid1, kTrigThreads, 0, s>>>(t->summ, t->C, nseg, t->n, t->st_s, t->st_t, t->seg_s,
+    trig_scan_kernel<<<grid1, kScanThreads, 0, s>>>(t->summ, t->C, nseg, t->n, t->st_s, t->st_t, t->seg_s,
                                                     t->seg_t);
     trig_emit_kernel<<<grid2, kTrigThreads, 0, s>>>(d_ratio, ld, t->C, T, t->on_f, t->off_f, t->n, t->summ,
                                                     t->seg_s, t->seg_t, d_records, capacity, d_count);
