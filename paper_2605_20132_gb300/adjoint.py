@@ -3,8 +3,8 @@
 The forward and the backward are the library's CUDA kernels
 (filark_iir_forward_ckpt / filark_iir_backward); this module only allocates
 the checkpoint and work buffers with torch and marshals pointers.  The
-forward keeps the cascade state every ``ckpt_every`` samples and nothing
-else; the backward recomputes the section signals from those checkpoints and
+forward keeps the cascade state at most ``ckpt_every`` samples apart (closer
+when the channels are too few to fill the GPU) and nothing else; the backward recomputes the section signals from those checkpoints and
 runs the reverse-time adjoint (Sec. 3.4, the SOS filter, differentiated).
 
 x: (n_samples, n_channels) float32 CUDA tensor, time-major (row stride >=

@@ -19,10 +19,11 @@
 // multiplies by H, and the last inverse pass writes the outputs and the new
 // tail straight to global memory.  The tail is double-buffered (read from one
 // buffer, written to the other), so the epilogue needs no barrier.  Twiddles
-// come from a host table made in double precision; a butterfly's powers
-// w^2 .. w^7 are products of at most three table values' roundings.
-// N <= 8192 (64 KB of complex floats, double-buffered in 128 KB of shared
-// memory).
+// come from a host table made in double precision, staged in shared memory;
+// a butterfly's powers w^2 .. w^7 are products of at most three table values'
+// roundings.  Shared arrays are padded by one element per 16 (element i at
+// i + i/16), which spreads the strided stores of the early passes over the
+// banks.  N <= 8192 (2 x 68 KB of complex floats plus 32 KB of twiddles).
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -38,6 +39,9 @@ namespace {
 
 constexpr int kFftMaxThreads = 1024;
 constexpr int kFftMaxLog = 13;     // N <= 8192
+
+// padded shared-memory position of element i
+__device__ __forceinline__ int pad(int i) { return i + (i >> 4); }
 
 __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
     return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
@@ -119,7 +123,7 @@ struct BlockIO {
 // radix-R DFT to (t - j) R + j + q m.
 template <int R, bool INV, int SRC, int DST>
 __device__ __forceinline__ void radix_pass(const float2 *__restrict__ a, float2 *__restrict__ b, int logN, int logm,
-                                           const float2 *__restrict__ tw, const BlockIO &io) {
+                                           const float2 *tw, const BlockIO &io) {
     constexpr int logR = R == 2 ? 1 : (R == 4 ? 2 : 3);
     const int N = 1 << logN, stride = N >> logR, m = 1 << logm;
     for (int t = threadIdx.x; t < stride; t += blockDim.x) {
@@ -136,11 +140,11 @@ __device__ __forceinline__ void radix_pass(const float2 *__restrict__ a, float2 
                 }
                 x[r] = make_float2(re, im);
             } else {
-                x[r] = a[i];
+                x[r] = a[pad(i)];
             }
         }
         if (logm > 0) {
-            float2 w = __ldg(tw + (j << (logN - logm - logR)));
+            float2 w = tw[j << (logN - logm - logR)];
             if (INV) w.y = -w.y;
             if constexpr (R == 2) {
                 x[1] = cmul(x[1], w);
@@ -166,9 +170,9 @@ __device__ __forceinline__ void radix_pass(const float2 *__restrict__ a, float2 
         for (int q = 0; q < R; ++q) {
             const int i = base + (q << logm);
             if constexpr (DST == DST_SMEM) {
-                b[i] = x[q];
+                b[pad(i)] = x[q];
             } else if constexpr (DST == DST_SMEM_H) {
-                b[i] = cmul(x[q], __ldg(io.H + i));
+                b[pad(i)] = cmul(x[q], __ldg(io.H + i));
             } else {
                 // z[i] (scaled) plus the old tail gives output i (i < len) or
                 // new tail entry i - len (len <= i < len + M - 1)
@@ -256,6 +260,9 @@ __global__ void __launch_bounds__(kFftMaxThreads) fftfilt_block_kernel(const __g
                                                                        float *__restrict__ tnew,
                                                                        float *__restrict__ y, long long ldy) {
     extern __shared__ float2 sm[];
+    const int NP = pad(fp.N);
+    float2 *stw = sm + 2 * NP;
+    for (int i = threadIdx.x; i < fp.N / 2; i += blockDim.x) stw[i] = __ldg(tw + i);
     BlockIO io;
     io.x = x;
     io.ldx = ldx;
@@ -269,8 +276,9 @@ __global__ void __launch_bounds__(kFftMaxThreads) fftfilt_block_kernel(const __g
     io.ldy = ldy;
     io.T1 = fp.M - 1;
     io.scale = fp.scale;
-    float2 *X = fft_forward(sm, sm + fp.N, fp.logN, tw, io);
-    fft_inverse_out(X, X == sm ? sm + fp.N : sm, fp.logN, tw, io);
+    __syncthreads();
+    float2 *X = fft_forward(sm, sm + NP, fp.logN, stw, io);
+    fft_inverse_out(X, X == sm ? sm + NP : sm, fp.logN, stw, io);
 }
 
 __global__ void __launch_bounds__(kFftMaxThreads) fft_of_taps_kernel(const __grid_constant__ FftParams fp,
@@ -278,6 +286,10 @@ __global__ void __launch_bounds__(kFftMaxThreads) fft_of_taps_kernel(const __gri
                                                                      const float2 *__restrict__ tw,
                                                                      float2 *__restrict__ H) {
     extern __shared__ float2 sm[];
+    const int NP = pad(fp.N);
+    float2 *stw = sm + 2 * NP;
+    for (int i = threadIdx.x; i < fp.N / 2; i += blockDim.x) stw[i] = __ldg(tw + i);
+    __syncthreads();
     BlockIO io{};
     io.x = h;
     io.ldx = 1;
@@ -285,8 +297,8 @@ __global__ void __launch_bounds__(kFftMaxThreads) fft_of_taps_kernel(const __gri
     io.c1 = 0;
     io.has2 = false;
     io.H = nullptr;
-    const float2 *r = fft_forward(sm, sm + fp.N, fp.logN, tw, io);
-    for (int i = threadIdx.x; i < fp.N; i += blockDim.x) H[i] = r[i];
+    const float2 *r = fft_forward(sm, sm + NP, fp.logN, stw, io);
+    for (int i = threadIdx.x; i < fp.N; i += blockDim.x) H[i] = r[pad(i)];
 }
 
 struct DeviceGuard {
@@ -312,7 +324,8 @@ filark_status fcuda(cudaError_t e, const char *what) {
     return FILARK_ECUDA;
 }
 
-size_t fft_smem(int N) { return sizeof(float2) * 2 * (size_t)N; }
+// two padded buffers and the twiddle table
+size_t fft_smem(int N) { return sizeof(float2) * (2 * (size_t)(N + (N >> 4)) + (size_t)(N / 2)); }
 
 }  // namespace
 

@@ -21,7 +21,11 @@
 // segment states (a few steps) and the final reductions run in FP64.
 //
 // Parallelism over time as well as channels.  The record is cut into segments
-// of `ckpt` samples; one thread owns one (segment, channel) pair.  Both the
+// of at most `ckpt` samples; one thread owns one (segment, channel) pair.  When
+// the channels times the segments of `ckpt` samples are too few threads to
+// fill the GPU (kTargetThreads), the segments are shortened (to no fewer than
+// kMinSegment samples) until they are enough: the checkpoints are then closer
+// than asked for, which the size queries account for.  Both the
 // forward state and the adjoint state are linear in their inputs, so each
 // pass runs in three steps: every thread runs its segment from a zero state
 // and keeps only the final state; one thread per channel chains the segments,
@@ -49,6 +53,9 @@ using filark::set_last_error;
 constexpr int kMaxS = FILARK_MAX_SECTIONS;
 constexpr int kMaxState = 2 * kMaxS;
 constexpr int kAdjThreads = 128;
+constexpr long long kTargetThreads = 1LL << 17;   // (segment, channel) pairs that fill the GPU
+constexpr long long kMinSegment = 128;
+constexpr int kChainThreads = 32;   // one warp per CTA: the chaining has only C threads (FP64, spread over SMs)
 
 // A double-float number (hi + lo, ~48 significant bits) on the FP32 pipe:
 // FMA-exact products and TwoSum additions (the "sloppy" sum: error ~2^-44 of
@@ -103,7 +110,7 @@ struct Transition {
 };
 
 struct Geometry {
-    long long N, ckpt, P;  // samples, segment length, piece length
+    long long N, ckpt, P;  // samples, segment length (<= the requested interval), piece length
     long long nseg, npiece;
     int C;
     long long NT;  // nseg * C threads
@@ -191,7 +198,7 @@ __global__ void __launch_bounds__(kAdjThreads) fwd_local_kernel(const __grid_con
 //   forward : st[0] = 0,         st[j+1] += T st[j]        (j ascending)
 //   backward: st[nseg-1] = 0,    st[j-1] += T st[j]        (j descending)
 template <int S>
-__global__ void __launch_bounds__(kAdjThreads) chain_segments_kernel(const __grid_constant__ Transition tr,
+__global__ void __launch_bounds__(kChainThreads) chain_segments_kernel(const __grid_constant__ Transition tr,
                                                                      const __grid_constant__ Geometry g,
                                                                      double *__restrict__ st, int backward) {
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
@@ -204,14 +211,28 @@ __global__ void __launch_bounds__(kAdjThreads) chain_segments_kernel(const __gri
         v[i] = 0.0;
         st_dd(st + ix(i, g.NT, first * g.C + c), dd_f(0.f));
     }
+    // the local states of step j + 1 are loaded while step j is combined
+    dd next[D];
+    if (g.nseg > 1) {
+        const long long T1 = (backward ? g.nseg - 2 : 1) * g.C + c;
+#pragma unroll
+        for (int i = 0; i < D; ++i) next[i] = ld_dd(st + ix(i, g.NT, T1));
+    }
     for (long long j = 1; j < g.nseg; ++j) {
         const long long seg = backward ? g.nseg - 1 - j : j;
         const long long T = seg * g.C + c;
+        dd loc[D];
+#pragma unroll
+        for (int i = 0; i < D; ++i) loc[i] = next[i];
+        if (j + 1 < g.nseg) {
+            const long long Tn = (backward ? g.nseg - 2 - j : j + 1) * g.C + c;
+#pragma unroll
+            for (int i = 0; i < D; ++i) next[i] = ld_dd(st + ix(i, g.NT, Tn));
+        }
         double nv[D];
 #pragma unroll
         for (int i = 0; i < D; ++i) {
-            const dd loc = ld_dd(st + ix(i, g.NT, T));
-            double acc = (double)loc.hi + (double)loc.lo;
+            double acc = (double)loc[i].hi + (double)loc[i].lo;
 #pragma unroll
             for (int q = 0; q < D; ++q) acc += tr.T[i][q] * v[q];
             nv[i] = acc;
@@ -385,16 +406,25 @@ __global__ void __launch_bounds__(kAdjThreads) adj_run_kernel(const __grid_const
         }
 }
 
-// B4: dL/dsos[j] = sum over all (segment, channel) partials, FP64, fixed order.
-__global__ void __launch_bounds__(256) sum_partials_kernel(const double *__restrict__ gpart, long long NT,
-                                                           double *__restrict__ gsos) {
-    __shared__ double part[256];
+// B4: dL/dsos[j] = sum over all (segment, channel) partials, FP64, fixed order
+// (each thread keeps 4 interleaved sums, combined in a fixed tree).
+constexpr int kSumThreads = 1024;
+__global__ void __launch_bounds__(kSumThreads) sum_partials_kernel(const double *__restrict__ gpart, long long NT,
+                                                                   double *__restrict__ gsos) {
+    __shared__ double part[kSumThreads];
     const int j = blockIdx.x;
-    double acc = 0.0;
-    for (long long t = threadIdx.x; t < NT; t += blockDim.x) acc += gpart[j * NT + t];
-    part[threadIdx.x] = acc;
+    const double *src = gpart + (long long)j * NT;
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    long long t = threadIdx.x;
+    for (; t + 3 * kSumThreads < NT; t += 4 * kSumThreads) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc[q] += src[t + q * kSumThreads];
+    }
+    for (int q = 0; q < 4; ++q, t += kSumThreads)
+        if (t < NT) acc[q] += src[t];
+    part[threadIdx.x] = (acc[0] + acc[1]) + (acc[2] + acc[3]);
     __syncthreads();
-    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    for (int w = kSumThreads / 2; w > 0; w >>= 1) {
         if ((int)threadIdx.x < w) part[threadIdx.x] += part[threadIdx.x + w];
         __syncthreads();
     }
@@ -493,10 +523,17 @@ bool make_geometry(int S, int C, long long N, long long ckpt, Geometry &g) {
     if (S < 1 || S > kMaxS || C < 1 || N < 1 || ckpt < 1) return false;
     g.N = N;
     g.C = C;
-    g.ckpt = ckpt;
-    g.P = piece_len(ckpt);
-    g.nseg = (N + ckpt - 1) / ckpt;
-    g.npiece = (std::min(ckpt, N) + g.P - 1) / g.P;
+    // shorten the segments while (segments x channels) is below the target
+    long long seg = ckpt;
+    const long long nt0 = ((N + ckpt - 1) / ckpt) * (long long)C;
+    if (nt0 < kTargetThreads) {
+        const long long f = (kTargetThreads + nt0 - 1) / nt0;
+        seg = std::max(std::min(ckpt, kMinSegment), (ckpt + f - 1) / f);
+    }
+    g.ckpt = seg;
+    g.P = piece_len(seg);
+    g.nseg = (N + seg - 1) / seg;
+    g.npiece = (std::min(seg, N) + g.P - 1) / g.P;
     g.NT = g.nseg * (long long)C;
     return true;
 }
@@ -529,9 +566,9 @@ template <int S>
 void launch_forward(const SosCoef &k, const Transition &tr, const Geometry &g, const float *x, long long ldx,
                     float *y, long long ldy, double *ckpt, cudaStream_t st) {
     const unsigned nb = (unsigned)((g.NT + kAdjThreads - 1) / kAdjThreads);
-    const unsigned nc = (unsigned)((g.C + kAdjThreads - 1) / kAdjThreads);
+    const unsigned nc = (unsigned)((g.C + kChainThreads - 1) / kChainThreads);
     fwd_local_kernel<S><<<nb, kAdjThreads, 0, st>>>(k, g, x, ldx, ckpt);
-    chain_segments_kernel<S><<<nc, kAdjThreads, 0, st>>>(tr, g, ckpt, 0);
+    chain_segments_kernel<S><<<nc, kChainThreads, 0, st>>>(tr, g, ckpt, 0);
     if (y) fwd_run_kernel<S><<<nb, kAdjThreads, 0, st>>>(k, g, x, ldx, ckpt, y, ldy);
 }
 
@@ -540,15 +577,15 @@ void launch_backward(const SosCoef &k, const Transition &tr, const Geometry &g, 
                      const float *gy, long long ldg, const double *ckpt, double *work, float *gx, long long ldgx,
                      double *gsos, cudaStream_t st) {
     const unsigned nb = (unsigned)((g.NT + kAdjThreads - 1) / kAdjThreads);
-    const unsigned nc = (unsigned)((g.C + kAdjThreads - 1) / kAdjThreads);
+    const unsigned nc = (unsigned)((g.C + kChainThreads - 1) / kChainThreads);
     double *beta = work;
     double *sub = beta + (size_t)g.NT * (2 * S);
     double *sig = sub + (size_t)g.NT * (size_t)(g.npiece * 2 * S);
     double *gpart = sig + (size_t)g.NT * (size_t)(g.P * S);
     adj_local_kernel<S><<<nb, kAdjThreads, 0, st>>>(k, g, gy, ldg, beta);
-    chain_segments_kernel<S><<<nc, kAdjThreads, 0, st>>>(tr, g, beta, 1);
+    chain_segments_kernel<S><<<nc, kChainThreads, 0, st>>>(tr, g, beta, 1);
     adj_run_kernel<S><<<nb, kAdjThreads, 0, st>>>(k, g, x, ldx, gy, ldg, ckpt, beta, sub, sig, gx, ldgx, gpart);
-    sum_partials_kernel<<<6 * S, 256, 0, st>>>(gpart, g.NT, gsos);
+    sum_partials_kernel<<<6 * S, kSumThreads, 0, st>>>(gpart, g.NT, gsos);
 }
 
 }  // namespace

@@ -159,16 +159,39 @@ def _piece(ckpt):
     return max(1, min(math.ceil(math.sqrt(2.0 * ckpt)), ckpt))
 
 
-@pytest.mark.parametrize("S,C,N,ckpt", [(4, 2048, 30000, 3000), (1, 1, 1, 1), (8, 37, 777, 100), (4, 16, 2000, 5000)])
+def _segment(C, N, ckpt):
+    """Segment length the library uses: the requested interval, shortened when
+    channels x segments are fewer than 2^17 threads, to no fewer than 128
+    samples (or the requested interval, if that is shorter)."""
+    nt0 = -(-N // ckpt) * C
+    if nt0 >= 1 << 17:
+        return ckpt
+    f = -(-(1 << 17) // nt0)
+    return max(min(ckpt, 128), -(-ckpt // f))
+
+
+@pytest.mark.parametrize("S,C,N,ckpt", [(4, 2048, 30000, 3000), (1, 1, 1, 1), (8, 37, 777, 100), (4, 16, 2000, 5000),
+                                        (4, 6000, 90000, 3000), (2, 100, 10**6, 1000)])
 def test_iir_buffer_sizes(S, C, N, ckpt):
     """Checkpoints: 2S doubles per channel per segment; work: the adjoint
     states, piece states, one piece of section signals and the gradient
     partials per (segment, channel)."""
-    nseg = -(-N // ckpt)
-    P = _piece(ckpt)
-    npiece = -(-min(ckpt, N) // P)
+    seg = _segment(C, N, ckpt)
+    assert seg <= ckpt
+    nseg = -(-N // seg)
+    P = _piece(seg)
+    npiece = -(-min(seg, N) // P)
     assert abi.filark_iir_ckpt_bytes(S, C, N, ckpt) == 8 * nseg * C * 2 * S
     assert abi.filark_iir_work_bytes(S, C, N, ckpt) == 8 * nseg * C * (2 * S + npiece * 2 * S + P * S + 6 * S)
+
+
+def test_iir_segments_fill_the_gpu_only_when_needed():
+    """Large problems keep the requested checkpoint interval; the paper-scale
+    differentiation workload (2048 x 30,000, every 3000) is cut finer."""
+    assert _segment(6000, 90000, 3000) == 3000
+    assert _segment(2048, 30000, 3000) == 429
+    assert abi.filark_iir_ckpt_bytes(4, 6000, 90000, 3000) == 8 * 30 * 6000 * 8
+    assert abi.filark_iir_ckpt_bytes(4, 2048, 30000, 3000) == 8 * 70 * 2048 * 8
 
 
 @pytest.mark.parametrize("args", [(0, 4, 10, 5), (9, 4, 10, 5), (4, 0, 10, 5), (4, 4, 0, 5), (4, 4, 10, 0)])
@@ -178,9 +201,14 @@ def test_iir_buffer_sizes_reject_invalid(args):
 
 
 def test_iir_checkpoint_memory_is_far_below_all_intermediates():
-    """The differentiation workload keeps well under a tenth of the memory that
-    storing every section signal in FP64 would take."""
+    """The differentiation workload keeps a fraction of the memory that storing
+    every section signal in FP64 would take: under a fifth with the segments
+    cut finer to fill the GPU, under a tenth at the requested interval."""
     S, C, N, ckpt = 4, 2048, 30000, 3000
+    full = 8 * S * C * N
+    kept = abi.filark_iir_ckpt_bytes(S, C, N, ckpt) + abi.filark_iir_work_bytes(S, C, N, ckpt)
+    assert kept < full / 5
+    S, C, N, ckpt = 4, 6000, 90000, 3000
     full = 8 * S * C * N
     kept = abi.filark_iir_ckpt_bytes(S, C, N, ckpt) + abi.filark_iir_work_bytes(S, C, N, ckpt)
     assert kept < full / 10
