@@ -55,7 +55,7 @@ constexpr int kMaxState = 2 * kMaxS;
 constexpr int kAdjThreads = 128;
 constexpr long long kTargetThreads = 1LL << 17;   // (segment, channel) pairs that fill the GPU
 constexpr long long kMinSegment = 128;
-constexpr int kChainThreads = 32;   // one warp per CTA: the chaining has only C threads (FP64, spread over SMs)
+constexpr int kChainThreads = 64;   // small CTAs: the chaining has only C x (2S rounded up) threads
 
 // A double-float number (hi + lo, ~48 significant bits) on the FP32 pipe:
 // FMA-exact products and TwoSum additions (the "sloppy" sum: error ~2^-44 of
@@ -194,54 +194,46 @@ __global__ void __launch_bounds__(kAdjThreads) fwd_local_kernel(const __grid_con
     }
 }
 
-// F2 / B2: one thread per channel chains the segments (FP64: a few steps).
+// F2 / B2: per channel, chain the segments (FP64: one D x D product per
+// segment).  A group of G >= D lanes serves one channel, lane i owning state
+// row i; the state vector is read across the group with shuffles.
 //   forward : st[0] = 0,         st[j+1] += T st[j]        (j ascending)
 //   backward: st[nseg-1] = 0,    st[j-1] += T st[j]        (j descending)
 template <int S>
+__host__ __device__ constexpr int chain_group() {
+    return 2 * S <= 2 ? 2 : (2 * S <= 4 ? 4 : (2 * S <= 8 ? 8 : 16));
+}
+
+template <int S>
 __global__ void __launch_bounds__(kChainThreads) chain_segments_kernel(const __grid_constant__ Transition tr,
-                                                                     const __grid_constant__ Geometry g,
-                                                                     double *__restrict__ st, int backward) {
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= g.C) return;
+                                                                       const __grid_constant__ Geometry g,
+                                                                       double *__restrict__ st, int backward) {
     constexpr int D = 2 * S;
-    double v[D];
+    constexpr int G = chain_group<S>();
+    const int i = threadIdx.x % G;                          // state row of this lane
+    const int gbase = (threadIdx.x & 31) - i;                // first lane of the group
+    const long long c = ((long long)blockIdx.x * blockDim.x + threadIdx.x) / G;
+    const bool row = c < g.C && i < D;                       // lanes past D or C only shuffle
+    double Trow[D];
+#pragma unroll
+    for (int q = 0; q < D; ++q) Trow[q] = i < D ? tr.T[i][q] : 0.0;
+    double v = 0.0;
     const long long first = backward ? g.nseg - 1 : 0;
-#pragma unroll
-    for (int i = 0; i < D; ++i) {
-        v[i] = 0.0;
-        st_dd(st + ix(i, g.NT, first * g.C + c), dd_f(0.f));
-    }
-    // the local states of step j + 1 are loaded while step j is combined
-    dd next[D];
-    if (g.nseg > 1) {
-        const long long T1 = (backward ? g.nseg - 2 : 1) * g.C + c;
-#pragma unroll
-        for (int i = 0; i < D; ++i) next[i] = ld_dd(st + ix(i, g.NT, T1));
-    }
+    if (row) st_dd(st + ix(i, g.NT, first * g.C + c), dd_f(0.f));
+    // the local state of step j + 1 is loaded while step j is combined
+    dd next = dd_f(0.f);
+    if (row && g.nseg > 1) next = ld_dd(st + ix(i, g.NT, (backward ? g.nseg - 2 : 1) * g.C + c));
     for (long long j = 1; j < g.nseg; ++j) {
         const long long seg = backward ? g.nseg - 1 - j : j;
-        const long long T = seg * g.C + c;
-        dd loc[D];
+        const dd loc = next;
+        if (row && j + 1 < g.nseg) next = ld_dd(st + ix(i, g.NT, (backward ? g.nseg - 2 - j : j + 1) * g.C + c));
+        double acc = (double)loc.hi + (double)loc.lo;
 #pragma unroll
-        for (int i = 0; i < D; ++i) loc[i] = next[i];
-        if (j + 1 < g.nseg) {
-            const long long Tn = (backward ? g.nseg - 2 - j : j + 1) * g.C + c;
-#pragma unroll
-            for (int i = 0; i < D; ++i) next[i] = ld_dd(st + ix(i, g.NT, Tn));
-        }
-        double nv[D];
-#pragma unroll
-        for (int i = 0; i < D; ++i) {
-            double acc = (double)loc[i].hi + (double)loc[i].lo;
-#pragma unroll
-            for (int q = 0; q < D; ++q) acc += tr.T[i][q] * v[q];
-            nv[i] = acc;
-        }
-#pragma unroll
-        for (int i = 0; i < D; ++i) {
-            v[i] = nv[i];
-            const float hi = (float)nv[i];
-            st_dd(st + ix(i, g.NT, T), dd{hi, (float)(nv[i] - (double)hi)});
+        for (int q = 0; q < D; ++q) acc += Trow[q] * __shfl_sync(0xffffffffu, v, gbase + q);
+        v = row ? acc : 0.0;
+        if (row) {
+            const float hi = (float)acc;
+            st_dd(st + ix(i, g.NT, seg * g.C + c), dd{hi, (float)(acc - (double)hi)});
         }
     }
 }
@@ -566,7 +558,7 @@ template <int S>
 void launch_forward(const SosCoef &k, const Transition &tr, const Geometry &g, const float *x, long long ldx,
                     float *y, long long ldy, double *ckpt, cudaStream_t st) {
     const unsigned nb = (unsigned)((g.NT + kAdjThreads - 1) / kAdjThreads);
-    const unsigned nc = (unsigned)((g.C + kChainThreads - 1) / kChainThreads);
+    const unsigned nc = (unsigned)((g.C * chain_group<S>() + kChainThreads - 1) / kChainThreads);
     fwd_local_kernel<S><<<nb, kAdjThreads, 0, st>>>(k, g, x, ldx, ckpt);
     chain_segments_kernel<S><<<nc, kChainThreads, 0, st>>>(tr, g, ckpt, 0);
     if (y) fwd_run_kernel<S><<<nb, kAdjThreads, 0, st>>>(k, g, x, ldx, ckpt, y, ldy);
@@ -577,7 +569,7 @@ void launch_backward(const SosCoef &k, const Transition &tr, const Geometry &g, 
                      const float *gy, long long ldg, const double *ckpt, double *work, float *gx, long long ldgx,
                      double *gsos, cudaStream_t st) {
     const unsigned nb = (unsigned)((g.NT + kAdjThreads - 1) / kAdjThreads);
-    const unsigned nc = (unsigned)((g.C + kChainThreads - 1) / kChainThreads);
+    const unsigned nc = (unsigned)((g.C * chain_group<S>() + kChainThreads - 1) / kChainThreads);
     double *beta = work;
     double *sub = beta + (size_t)g.NT * (2 * S);
     double *sig = sub + (size_t)g.NT * (size_t)(g.npiece * 2 * S);
