@@ -274,14 +274,17 @@ def run_gpu(args, rank: int, world: int, dist) -> None:
     e2e_steps = max(1, min(args.steps, 3))
     xh = torch.from_numpy(x_host).pin_memory()
     rh = torch.empty((N, C), dtype=torch.float32).pin_memory()
-    push_h = lib.filark_chain_push_chunk_host
+    push_h = lib.filark_chain_push_host_async
     xhp, rhp = xh.data_ptr(), rh.data_ptr()
 
     def step_host():
+        # pipelined: the copies of one push overlap the computation of the
+        # neighbouring pushes; the step ends when every ratio row is in host memory
         for i in range(n_push):
             st = push_h(h, xhp + i * T * row, C, T, rhp + i * T * row, None, None, C, sh)
             if st:
-                abi.check(st, "push_host")
+                abi.check(st, "push_host_async")
+        abi.check(lib.filark_chain_host_sync(h, sh), "host_sync")
 
     step_host()
     if dist:

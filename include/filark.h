@@ -159,6 +159,32 @@ filark_status filark_chain_push_chunk_host(filark_chain *h, const float *h_in, i
                                            float *h_spatial, int64_t ld_out,
                                            filark_stream_t stream);
 
+/*
+ * Pipelined host-buffer pushes (no counterpart in the paper, which reads its
+ * input on the host and moves it to the device one chunk at a time): the same
+ * computation as filark_chain_push_chunk_host, but the call only enqueues the
+ * work and returns.  Each push takes the next of FILARK_HOST_SLOTS device
+ * staging slots; its input copy runs on a copy stream of the chain, the chain
+ * on `stream`, the output copies on a second copy stream, ordered by events,
+ * so the copies of one push overlap the computation of its neighbours.  A slot
+ * is reused only after the computation and the output copies of its previous
+ * push are done.  The host buffers must be page-locked (cudaHostAlloc or
+ * registered; pageable memory works but does not overlap) and must stay valid
+ * and unmodified until filark_chain_host_sync returns; the outputs are in
+ * host memory only then.  Pushes are applied in call order; they may be mixed
+ * with filark_chain_push_chunk on the same `stream`.  Call
+ * filark_chain_host_sync before filark_chain_reset_state, set_state or reading
+ * the outputs.  Argument checks as filark_chain_push_chunk_host.
+ */
+#define FILARK_HOST_SLOTS 3
+filark_status filark_chain_push_host_async(filark_chain *h, const float *h_in, int64_t ld_in,
+                                           int64_t n_samples, float *h_ratio, float *h_bandpass,
+                                           float *h_spatial, int64_t ld_out,
+                                           filark_stream_t stream);
+/* Wait for all pipelined host pushes (and `stream`); returns the chain's
+   device status as filark_chain_sync_status does. */
+filark_status filark_chain_host_sync(filark_chain *h, filark_stream_t stream);
+
 /* Zero the whole state (IIR, detector sums, history, sample count) on
    `stream`, and clear a sticky error. */
 filark_status filark_chain_reset_state(filark_chain *h, filark_stream_t stream);

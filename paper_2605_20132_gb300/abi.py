@@ -40,6 +40,7 @@ FILARK_MAX_SPATIAL_WIDTH = 33
 # Every function the header declares (the tests check the library exports them).
 EXPORTED = (
     "filark_chain_create", "filark_chain_push_chunk", "filark_chain_push_chunk_host",
+    "filark_chain_push_host_async", "filark_chain_host_sync",
     "filark_chain_reset_state", "filark_chain_destroy", "filark_chain_get_state",
     "filark_chain_set_state", "filark_chain_sync_status", "filark_chain_get_info",
     "filark_butter_bandpass_sos", "filark_last_error_string", "filark_abi_version",
@@ -157,6 +158,8 @@ def load(build_if_missing: bool = True) -> ct.CDLL:
             "filark_chain_create": ([ct.POINTER(filark_chain_config), ct.c_int, ct.POINTER(vp)], ct.c_int),
             "filark_chain_push_chunk": ([vp, vp, i64, i64, vp, vp, vp, i64, vp], ct.c_int),
             "filark_chain_push_chunk_host": ([vp, vp, i64, i64, vp, vp, vp, i64, vp], ct.c_int),
+            "filark_chain_push_host_async": ([vp, vp, i64, i64, vp, vp, vp, i64, vp], ct.c_int),
+            "filark_chain_host_sync": ([vp, vp], ct.c_int),
             "filark_chain_reset_state": ([vp, vp], ct.c_int),
             "filark_chain_destroy": ([vp], ct.c_int),
             "filark_chain_get_state": ([vp, vp, ct.POINTER(ct.c_size_t), vp], ct.c_int),
@@ -245,6 +248,14 @@ def filark_chain_push_chunk(h, d_in, ld_in, n, d_ratio, d_bp, d_sp, ld_out, stre
 
 def filark_chain_push_chunk_host(h, h_in, ld_in, n, h_ratio, h_bp, h_sp, ld_out, stream) -> int:
     return load().filark_chain_push_chunk_host(h, h_in, ld_in, n, h_ratio, h_bp, h_sp, ld_out, stream)
+
+
+def filark_chain_push_host_async(h, h_in, ld_in, n, h_ratio, h_bp, h_sp, ld_out, stream) -> int:
+    return load().filark_chain_push_host_async(h, h_in, ld_in, n, h_ratio, h_bp, h_sp, ld_out, stream)
+
+
+def filark_chain_host_sync(h, stream) -> int:
+    return load().filark_chain_host_sync(h, stream)
 
 
 def filark_chain_reset_state(h, stream) -> int:

@@ -104,6 +104,24 @@ class Chain:
                                               ld_out, _stream_handle(stream))
         abi.check(st, "filark_chain_push_chunk_host")
 
+    def push_host_async(self, x: np.ndarray, ratio: np.ndarray | None = None,
+                        bandpass: np.ndarray | None = None, spatial: np.ndarray | None = None,
+                        stream=None) -> None:
+        """Pipelined push from host arrays (page-locked for overlap): enqueues
+        and returns; the arrays must stay alive and unmodified, and the
+        outputs are valid, only after host_sync()."""
+        T = int(x.shape[0])
+        ld_in = int(x.strides[0] // 4) if T > 0 else self.n_channels
+        outs = [o for o in (ratio, bandpass, spatial) if o is not None]
+        ld_out = int(outs[0].strides[0] // 4) if outs else self.n_channels
+        p = lambda a: None if a is None else a.ctypes.data
+        st = abi.filark_chain_push_host_async(self._h, p(x), ld_in, T, p(ratio), p(bandpass), p(spatial),
+                                              ld_out, _stream_handle(stream))
+        abi.check(st, "filark_chain_push_host_async")
+
+    def host_sync(self, stream=None) -> None:
+        abi.check(abi.filark_chain_host_sync(self._h, _stream_handle(stream)), "filark_chain_host_sync")
+
     def reset(self, stream=None) -> None:
         abi.check(abi.filark_chain_reset_state(self._h, _stream_handle(stream)), "filark_chain_reset_state")
 

@@ -77,6 +77,15 @@ void free_chain(filark_chain *h) {
     if (h->status_host) cudaFreeHost(h->status_host);
     for (float *p : h->stage)
         if (p) cudaFree(p);
+    for (int k = 0; k < FILARK_HOST_SLOTS; ++k) {
+        for (float *p : h->astage[k])
+            if (p) cudaFree(p);
+        if (h->ev_in[k]) cudaEventDestroy(h->ev_in[k]);
+        if (h->ev_comp[k]) cudaEventDestroy(h->ev_comp[k]);
+        if (h->ev_out[k]) cudaEventDestroy(h->ev_out[k]);
+    }
+    if (h->hcopy_in) cudaStreamDestroy(h->hcopy_in);
+    if (h->hcopy_out) cudaStreamDestroy(h->hcopy_out);
     delete h;
 }
 
@@ -411,6 +420,82 @@ filark_status filark_chain_push_chunk_host(filark_chain *h, const float *h_in, i
     }
     e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return fail_cuda(e, "push_host: synchronize");
+    return check_device_status(h);
+}
+
+filark_status filark_chain_push_host_async(filark_chain *h, const float *h_in, int64_t ld_in, int64_t n_samples,
+                                           float *h_ratio, float *h_bandpass, float *h_spatial, int64_t ld_out,
+                                           filark_stream_t stream) {
+    filark_status st = validate_push(h, h_in, ld_in, n_samples, h_ratio, h_bandpass, h_spatial, ld_out);
+    if (st != FILARK_OK) return st;
+    st = check_device_status(h);
+    if (st != FILARK_OK) return st;
+    if (n_samples == 0) return FILARK_OK;
+    DeviceGuard dg(h->device);
+    cudaError_t e = cudaSuccess;
+    if (!h->hcopy_in) {
+        e = cudaStreamCreateWithFlags(&h->hcopy_in, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->hcopy_out, cudaStreamNonBlocking);
+        for (int k = 0; k < FILARK_HOST_SLOTS && e == cudaSuccess; ++k) {
+            e = cudaEventCreateWithFlags(&h->ev_in[k], cudaEventDisableTiming);
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_comp[k], cudaEventDisableTiming);
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_out[k], cudaEventDisableTiming);
+        }
+        if (e != cudaSuccess) return fail_cuda(e, "push_host_async: stream/event creation");
+    }
+    const int k = h->aslot;
+    const size_t plane = sizeof(float) * (size_t)h->cfg.max_chunk * (size_t)h->C;
+    float *hosts[4] = {const_cast<float *>(h_in), h_ratio, h_bandpass, h_spatial};
+    for (int i = 0; i < 4; ++i) {
+        if (hosts[i] && !h->astage[k][i]) {
+            if (cudaMalloc((void **)&h->astage[k][i], plane) != cudaSuccess) {
+                cudaGetLastError();
+                return fail(FILARK_ENOMEM, "push_host_async: staging allocation failed");
+            }
+            h->device_bytes += (int64_t)plane;
+        }
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t row = sizeof(float) * (size_t)h->C;
+    // input copy, once the slot's previous push has read its input
+    if (h->slot_used[k]) e = cudaStreamWaitEvent(h->hcopy_in, h->ev_comp[k], 0);
+    if (e == cudaSuccess)
+        e = cudaMemcpy2DAsync(h->astage[k][0], row, h_in, sizeof(float) * (size_t)ld_in, row, (size_t)n_samples,
+                              cudaMemcpyHostToDevice, h->hcopy_in);
+    if (e == cudaSuccess) e = cudaEventRecord(h->ev_in[k], h->hcopy_in);
+    // the push, once the input is in and the slot's previous outputs are out
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, h->ev_in[k], 0);
+    if (e == cudaSuccess && h->slot_used[k]) e = cudaStreamWaitEvent(s, h->ev_out[k], 0);
+    if (e != cudaSuccess) return fail_cuda(e, "push_host_async: input copy");
+    st = push_device(h, h->astage[k][0], h->C, n_samples, h_ratio ? h->astage[k][1] : nullptr,
+                     h_bandpass ? h->astage[k][2] : nullptr, h_spatial ? h->astage[k][3] : nullptr, h->C, s);
+    if (st != FILARK_OK) return st;
+    e = cudaEventRecord(h->ev_comp[k], s);
+    // output copies
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(h->hcopy_out, h->ev_comp[k], 0);
+    for (int i = 1; i < 4 && e == cudaSuccess; ++i) {
+        if (!hosts[i]) continue;
+        e = cudaMemcpy2DAsync(hosts[i], sizeof(float) * (size_t)ld_out, h->astage[k][i], row, row, (size_t)n_samples,
+                              cudaMemcpyDeviceToHost, h->hcopy_out);
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(h->ev_out[k], h->hcopy_out);
+    if (e != cudaSuccess) return fail_cuda(e, "push_host_async: output copy");
+    h->slot_used[k] = true;
+    h->aslot = (k + 1) % FILARK_HOST_SLOTS;
+    return FILARK_OK;
+}
+
+filark_status filark_chain_host_sync(filark_chain *h, filark_stream_t stream) {
+    if (!h) return fail(FILARK_EINVAL, "chain is NULL");
+    DeviceGuard dg(h->device);
+    cudaError_t e = cudaSuccess;
+    if (h->hcopy_in) e = cudaStreamSynchronize(h->hcopy_in);
+    if (e == cudaSuccess) e = cudaStreamSynchronize((cudaStream_t)stream);
+    if (e == cudaSuccess && h->hcopy_out) e = cudaStreamSynchronize(h->hcopy_out);
+    if (e != cudaSuccess) {
+        h->sticky = FILARK_ECUDA;
+        return fail_cuda(e, "host_sync");
+    }
     return check_device_status(h);
 }
 

@@ -22,6 +22,13 @@ struct filark_chain {
     long long n = 0;
     filark_status sticky = FILARK_OK;
     float *stage[4] = {nullptr, nullptr, nullptr, nullptr};   // in, ratio, bp, sp
+    // pipelined host pushes: per slot staging {in, ratio, bp, sp} and the
+    // events that order the input copy, the push and the output copies
+    cudaStream_t hcopy_in = nullptr, hcopy_out = nullptr;
+    float *astage[FILARK_HOST_SLOTS][4] = {};
+    cudaEvent_t ev_in[FILARK_HOST_SLOTS] = {}, ev_comp[FILARK_HOST_SLOTS] = {}, ev_out[FILARK_HOST_SLOTS] = {};
+    bool slot_used[FILARK_HOST_SLOTS] = {};
+    int aslot = 0;
     double *dense = nullptr;      // dense carry matrices (device)
     filark::ChainParams base{};
     int64_t device_bytes = 0;

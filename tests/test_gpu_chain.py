@@ -206,6 +206,40 @@ def test_host_buffer_push_matches_device_push(oracle_mod):
     assert np.array_equal(r, dev["ratio"]) and np.array_equal(bp, dev["bp"]) and np.array_equal(sp, dev["sp"])
 
 
+@pytest.mark.parametrize("pinned", [True, False])
+def test_pipelined_host_push_matches_device_push(oracle_mod, pinned):
+    """Pipelined host pushes (three staging slots reused, chunks of mixed
+    lengths, outputs at a wider row stride) give bitwise the outputs of device
+    pushes, from page-locked and from pageable host memory."""
+    import torch
+    from paper_2605_20132_gb300.chain import Chain
+    x = synth.small_stream(64, 7000, seed=19)
+    sos = small_sos(oracle_mod)
+    chunks = [1000, 1, 999, 700, 1000, 300, 1000, 1000, 1000]
+    dev = run_gpu(x, chunks, sos, K=5, ns=50, nl=1000)
+    ch = Chain(64, sos, 1000.0, 5, 50, 1000, outputs=ALL_OUT, max_chunk=1000)
+    xt = torch.from_numpy(x)
+    outs = [torch.full((7000, 70), float("nan")) for _ in range(3)]
+    if pinned:
+        xt = xt.pin_memory()
+        outs = [o.pin_memory() for o in outs]
+    xn = xt.numpy()
+    r, bp, sp = (o.numpy() for o in outs)
+    for rep in range(2):      # twice, with a reset in between: slots are reused across resets
+        t = 0
+        for k in chunks:
+            ch.push_host_async(xn[t:t + k], ratio=r[t:t + k], bandpass=bp[t:t + k], spatial=sp[t:t + k])
+            t += k
+        ch.host_sync()
+        assert np.array_equal(r[:, :64], dev["ratio"]) and np.array_equal(bp[:, :64], dev["bp"])
+        assert np.array_equal(sp[:, :64], dev["sp"])
+        assert np.isnan(r[:, 64:]).all()
+        ch.reset()
+        for o in (r, bp, sp):
+            o[:, :64] = np.nan
+    ch.close()
+
+
 def test_abi_argument_errors(oracle_mod):
     import torch
     from paper_2605_20132_gb300.chain import Chain
