@@ -13,7 +13,7 @@
 //   AGC   g[n] = (1/w) sum_{k<w} |x[n-k]|, y[n] = x[n] / g[n] (0 if g = 0)
 //         Window sums are differences of a running prefix P of x (or |x|) kept
 //         in double-float (~48 bits) in a ring of w + max_chunk rows: a prefix
-//         kernel (one CTA per 32 channels walks the push in slabs of 32 blocks
+//         kernel (one CTA per 8 channels walks the push in slabs of 32 blocks
 //         x 32 samples: block sums, per-channel prefix over the blocks, the
 //         samples' prefixes) and an output kernel over all samples.
 //   EMA   e[n] = (1-a) e[n-1] + a x[n]^2, y[n] = x[n] / sqrt(e[n]) (0 if e = 0)
@@ -21,6 +21,7 @@
 //         zero start (FP32), block starts from the carried state through the
 //         powers (1-a)^(32 j), the carried state itself in double-float.
 #include <cmath>
+#include <cstdint>
 #include <cstring>
 #include <new>
 #include <string>
@@ -36,7 +37,11 @@ constexpr int kFirRows = 256;       // FIR outputs per CTA
 constexpr int kFirThreads = 256;    // (channel, group of 32 outputs)
 constexpr int kFirMaxTaps = 512;
 constexpr int kScanBlocks = 32;     // blocks of 32 samples per slab (window / EMA kernels)
-constexpr int kScanThreads = kTopCh * kScanBlocks;   // 1024
+constexpr int kScanCh = 8;          // channels per CTA of the window / EMA kernels: 32-byte rows,
+                                    // and enough CTAs (C / 8) to fill every SM
+constexpr int kScanThreads = kScanCh * kScanBlocks;  // 256
+constexpr int kEmaCh = 32;          // channels per CTA of the EMA kernel (measured faster than 8)
+constexpr int kEmaThreads = kEmaCh * kScanBlocks;    // 1024
 constexpr int kSlab = 32 * kScanBlocks;              // 1024 samples
 
 struct DF2 {
@@ -77,17 +82,34 @@ __global__ void __launch_bounds__(kFirThreads) fir_kernel(const __grid_constant_
     const int c0 = blockIdx.x * kTopCh, t0 = blockIdx.y * kFirRows;
     const int tid = threadIdx.x;
     const int nrows = OFF + kFirRows;
-    for (int f = tid; f < nrows * kTopCh; f += kFirThreads) {
-        const int s = f / kTopCh, ch = f % kTopCh;
-        const int r = s - OFF;                 // tile row, negative = earlier
-        const long long g = (long long)t0 + r;  // sample index within the push
-        const int c = c0 + ch;
-        float v = 0.f;
-        if (c < C && r > -fp.M && g < T) {
-            if (g >= 0) v = __ldg(x + g * ldx + c);
-            else v = __ldg(hist + (g + fp.M - 1) * (long long)C + c);
+    // 16-byte loads when every row of input and history starts 16-byte aligned
+    const bool vec4 = ((ldx | C) & 3) == 0 && (((uintptr_t)x | (uintptr_t)hist) & 15) == 0;
+    if (vec4) {
+        for (int f = tid; f < nrows * (kTopCh / 4); f += kFirThreads) {
+            const int s = f / (kTopCh / 4), q = f % (kTopCh / 4);
+            const int r = s - OFF;
+            const long long g = (long long)t0 + r;
+            const int c = c0 + 4 * q;
+            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (c < C && r > -fp.M && g < T) {   // C % 4 == 0: the whole quad is in range
+                if (g >= 0) v = __ldg(reinterpret_cast<const float4 *>(x + g * ldx + c));
+                else v = __ldg(reinterpret_cast<const float4 *>(hist + (g + fp.M - 1) * (long long)C + c));
+            }
+            *reinterpret_cast<float4 *>(&xs[s * kTopCh + 4 * q]) = v;
         }
-        xs[f] = v;
+    } else {
+        for (int f = tid; f < nrows * kTopCh; f += kFirThreads) {
+            const int s = f / kTopCh, ch = f % kTopCh;
+            const int r = s - OFF;                 // tile row, negative = earlier
+            const long long g = (long long)t0 + r;  // sample index within the push
+            const int c = c0 + ch;
+            float v = 0.f;
+            if (c < C && r > -fp.M && g < T) {
+                if (g >= 0) v = __ldg(x + g * ldx + c);
+                else v = __ldg(hist + (g + fp.M - 1) * (long long)C + c);
+            }
+            xs[f] = v;
+        }
     }
     __syncthreads();
     const int ch = tid & 31, r0 = (tid >> 5) * 32;
@@ -130,16 +152,16 @@ __global__ void fir_history_kernel(const float *__restrict__ x, long long ldx, i
 
 // ------------------------------------------------------ window sums (P) --
 
-// One CTA per 32 channels walks the push in slabs of 1024 samples and writes
+// One CTA per 8 channels walks the push in slabs of 1024 samples and writes
 // the running prefix P[n] (double-float) of u = x (MEAN) or |x| (AGC).
-__global__ void __launch_bounds__(kScanThreads) prefix_kernel(const float *__restrict__ x, long long ldx, int T,
+__global__ void __launch_bounds__(kScanThreads, 5) prefix_kernel(const float *__restrict__ x, long long ldx, int T,
                                                               int C, int absval, long long n0, int Q,
                                                               float2 *__restrict__ ring,
                                                               float2 *__restrict__ carry) {
-    __shared__ DF2 bs[kScanBlocks][kTopCh];
-    __shared__ DF2 cin[kTopCh];
-    const int ch = threadIdx.x & 31, blk = threadIdx.x >> 5;
-    const int c = blockIdx.x * kTopCh + ch;
+    __shared__ DF2 bs[kScanBlocks][kScanCh];
+    __shared__ DF2 cin[kScanCh];
+    const int ch = threadIdx.x % kScanCh, blk = threadIdx.x / kScanCh;
+    const int c = blockIdx.x * kScanCh + ch;
     if (blk == 0) cin[ch] = c < C ? DF2{carry[c].x, carry[c].y} : DF2{0.f, 0.f};
     __syncthreads();
     for (int s0 = 0; s0 < T; s0 += kSlab) {
@@ -210,14 +232,14 @@ struct EmaParams {
 
 __device__ __forceinline__ float ema_pow(const EmaParams &ep, int m) { return ep.pw32[m >> 5] * ep.pw1[m & 31]; }
 
-__global__ void __launch_bounds__(kScanThreads) ema_kernel(const __grid_constant__ EmaParams ep,
+__global__ void __launch_bounds__(kEmaThreads) ema_kernel(const __grid_constant__ EmaParams ep,
                                                            const float *__restrict__ x, long long ldx, int T, int C,
                                                            float2 *__restrict__ state, float *__restrict__ y,
                                                            long long ldy) {
-    __shared__ float ls[kScanBlocks][kTopCh];
-    __shared__ DF2 es[kTopCh];
-    const int ch = threadIdx.x & 31, blk = threadIdx.x >> 5;
-    const int c = blockIdx.x * kTopCh + ch;
+    __shared__ float ls[kScanBlocks][kEmaCh];
+    __shared__ DF2 es[kEmaCh];
+    const int ch = threadIdx.x % kEmaCh, blk = threadIdx.x / kEmaCh;
+    const int c = blockIdx.x * kEmaCh + ch;
     if (blk == 0) es[ch] = c < C ? DF2{state[c].x, state[c].y} : DF2{0.f, 0.f};
     __syncthreads();
     for (int s0 = 0; s0 < T; s0 += kSlab) {
@@ -430,6 +452,7 @@ filark_status filark_top_push(filark_top *t, const float *d_in, int64_t ld_in, i
     cudaStream_t s = (cudaStream_t)stream;
     const int T = (int)n_samples, C = t->C;
     const unsigned gch = (unsigned)((C + kTopCh - 1) / kTopCh);
+    const unsigned gscan = (unsigned)((C + kScanCh - 1) / kScanCh);
     if (t->kind == FILARK_TOP_FIR) {
         const dim3 grid(gch, (unsigned)((T + kFirRows - 1) / kFirRows));
         const float *h = t->M > 1 ? t->hist[t->parity] : nullptr;
@@ -442,7 +465,7 @@ filark_status filark_top_push(filark_top *t, const float *d_in, int64_t ld_in, i
         }
     } else if (t->kind == FILARK_TOP_MEAN || t->kind == FILARK_TOP_AGC) {
         const int agc = t->kind == FILARK_TOP_AGC;
-        prefix_kernel<<<gch, kScanThreads, 0, s>>>(d_in, ld_in, T, C, agc, t->n, (int)t->Q, t->ring, t->carry);
+        prefix_kernel<<<gscan, kScanThreads, 0, s>>>(d_in, ld_in, T, C, agc, t->n, (int)t->Q, t->ring, t->carry);
         const long long n = (long long)T * C;
         window_out_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(d_in, ld_in, T, C, t->M, agc, t->n,
                                                                       (int)t->Q, t->ring, d_out, ld_out);
@@ -452,7 +475,7 @@ filark_status filark_top_push(filark_top *t, const float *d_in, int64_t ld_in, i
         const double pl = std::pow((double)ep.ac + (double)ep.ac_lo, (double)last);
         ep.plast_hi = (float)pl;
         ep.plast_lo = (float)(pl - (double)ep.plast_hi);
-        ema_kernel<<<gch, kScanThreads, 0, s>>>(ep, d_in, ld_in, T, C, t->carry, d_out, ld_out);
+        ema_kernel<<<(unsigned)((C + kEmaCh - 1) / kEmaCh), kEmaThreads, 0, s>>>(ep, d_in, ld_in, T, C, t->carry, d_out, ld_out);
     }
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return tcuda(e, "temporal operator push");

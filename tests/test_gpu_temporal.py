@@ -62,6 +62,18 @@ def test_fir_matches_oracle(oracle_mod, M):
     assert err <= TOL
 
 
+@pytest.mark.parametrize("M", [7, 101, 300])
+def test_fir_aligned_rows_match_oracle(oracle_mod, M):
+    """Row strides and channel counts that are multiples of 4 (16-byte tile loads)."""
+    rng = np.random.default_rng(95 + M)
+    x = synth.small_stream(68, 5000, seed=95 + M)
+    h = rng.standard_normal(M) / np.sqrt(M)
+    chunks = random_chunks(rng, 5000, 1200)
+    got = run_gpu_op(abi.FILARK_TOP_FIR, x, chunks, M, h, ld_in=72, ld_out=76)
+    ref = run_oracle_op(oracle_mod, oracle_mod.TOP_FIR, x, M, h.astype(np.float32).astype(np.float64))
+    assert normwise(got, ref) <= TOL
+
+
 @pytest.mark.parametrize("kind", ["mean", "agc"])
 @pytest.mark.parametrize("w", [1, 50, 1000, 3000])
 def test_window_ops_match_oracle(oracle_mod, kind, w):
