@@ -19,9 +19,10 @@
 // multiplies by H, and the last inverse pass writes the outputs and the new
 // tail straight to global memory.  The tail is double-buffered (read from one
 // buffer, written to the other), so the epilogue needs no barrier.  Twiddles
-// come from a host table made in double precision, staged in shared memory;
-// a butterfly's powers w^2 .. w^7 are products of at most three table values'
-// roundings.  Shared arrays are padded by one element per 16 (element i at
+// come from a host table made in double precision, one run of m values per
+// pass (w_j = exp(-2 pi i j / (R m)), j < m, contiguous in j so that a warp
+// reads consecutive entries), staged in shared memory; a butterfly's powers
+// w^2 .. w^7 are products of at most three table values' roundings.  Shared arrays are padded by one element per 16 (element i at
 // i + i/16), which spreads the strided stores of the early passes over the
 // banks.  N <= 8192 (2 x 68 KB of complex floats plus 32 KB of twiddles).
 #include <algorithm>
@@ -95,6 +96,7 @@ __device__ __forceinline__ void dft(float2 (&x)[R]) {
 
 struct FftParams {
     int N, logN, L, M;
+    int twlen;          // entries of the per-pass twiddle table (<= N / 2)
     float scale;        // 1 / N
 };
 
@@ -119,8 +121,8 @@ struct BlockIO {
 
 // One Stockham pass of radix R: sub-transforms of length m = 2^logm are
 // combined R at a time.  Butterfly t (< N/R) reads elements t + r N/R, scales
-// them by w^r with w = exp(d 2 pi i j / (R m)), j = t mod m, and writes the
-// radix-R DFT to (t - j) R + j + q m.
+// them by w^r with w = exp(d 2 pi i j / (R m)) = tw[j] (this pass's run of
+// the table), j = t mod m, and writes the radix-R DFT to (t - j) R + j + q m.
 template <int R, bool INV, int SRC, int DST>
 __device__ __forceinline__ void radix_pass(const float2 *__restrict__ a, float2 *__restrict__ b, int logN, int logm,
                                            const float2 *tw, const BlockIO &io) {
@@ -128,6 +130,21 @@ __device__ __forceinline__ void radix_pass(const float2 *__restrict__ a, float2 
     const int N = 1 << logN, stride = N >> logR, m = 1 << logm;
     for (int t = threadIdx.x; t < stride; t += blockDim.x) {
         const int j = t & (m - 1);
+        // the old tail values this butterfly's outputs add (issued first: they
+        // do not depend on the transform)
+        float2 told_q[DST == DST_GOUT ? R : 1];
+        if constexpr (DST == DST_GOUT) {
+            const int base = ((t - j) << logR) + j;
+#pragma unroll
+            for (int q = 0; q < R; ++q) {
+                const int i = base + (q << logm);
+                told_q[q] = make_float2(0.f, 0.f);
+                if (i < io.T1) {
+                    told_q[q].x = __ldg(io.told + (long long)io.c1 * io.T1 + i);
+                    if (io.has2) told_q[q].y = __ldg(io.told + (long long)(io.c1 + 1) * io.T1 + i);
+                }
+            }
+        }
         float2 x[R];
 #pragma unroll
         for (int r = 0; r < R; ++r) {
@@ -144,7 +161,7 @@ __device__ __forceinline__ void radix_pass(const float2 *__restrict__ a, float2 
             }
         }
         if (logm > 0) {
-            float2 w = tw[j << (logN - logm - logR)];
+            float2 w = tw[j];
             if (INV) w.y = -w.y;
             if constexpr (R == 2) {
                 x[1] = cmul(x[1], w);
@@ -177,11 +194,7 @@ __device__ __forceinline__ void radix_pass(const float2 *__restrict__ a, float2 
                 // z[i] (scaled) plus the old tail gives output i (i < len) or
                 // new tail entry i - len (len <= i < len + M - 1)
                 if (i < io.len + io.T1) {
-                    float v1 = x[q].x * io.scale, v2 = x[q].y * io.scale;
-                    if (i < io.T1) {
-                        v1 += io.told[(long long)io.c1 * io.T1 + i];
-                        if (io.has2) v2 += io.told[(long long)(io.c1 + 1) * io.T1 + i];
-                    }
+                    const float v1 = x[q].x * io.scale + told_q[q].x, v2 = x[q].y * io.scale + told_q[q].y;
                     if (i < io.len) {
                         io.y[(long long)i * io.ldy + io.c1] = v1;
                         if (io.has2) io.y[(long long)i * io.ldy + io.c1 + 1] = v2;
@@ -207,21 +220,23 @@ __device__ __forceinline__ void radix_pass_any(int logR, const float2 *a, float2
 // when io.H is set; the result is left in the returned buffer.
 __device__ float2 *fft_forward(float2 *a, float2 *b, int logN, const float2 *tw, const BlockIO &io) {
     const int rem = logN % 3, npass = logN / 3 + (rem ? 1 : 0);
-    int logm = 0;
+    int logm = 0, toff = 0;
     for (int p = 0; p < npass; ++p) {
         const int logR = (p == 0 && rem) ? rem : 3;
         const bool last = p == npass - 1;
+        const float2 *twp = tw + toff;
         if (p == 0) {
-            if (last && io.H) radix_pass_any<false, SRC_GIN, DST_SMEM_H>(logR, a, b, logN, logm, tw, io);
-            else radix_pass_any<false, SRC_GIN, DST_SMEM>(logR, a, b, logN, logm, tw, io);
+            if (last && io.H) radix_pass_any<false, SRC_GIN, DST_SMEM_H>(logR, a, b, logN, logm, twp, io);
+            else radix_pass_any<false, SRC_GIN, DST_SMEM>(logR, a, b, logN, logm, twp, io);
         } else {
-            if (last && io.H) radix_pass_any<false, SRC_SMEM, DST_SMEM_H>(logR, a, b, logN, logm, tw, io);
-            else radix_pass_any<false, SRC_SMEM, DST_SMEM>(logR, a, b, logN, logm, tw, io);
+            if (last && io.H) radix_pass_any<false, SRC_SMEM, DST_SMEM_H>(logR, a, b, logN, logm, twp, io);
+            else radix_pass_any<false, SRC_SMEM, DST_SMEM>(logR, a, b, logN, logm, twp, io);
         }
         __syncthreads();
         float2 *tmp = a;
         a = b;
         b = tmp;
+        if (logm > 0) toff += 1 << logm;
         logm += logR;
     }
     return a;
@@ -230,18 +245,19 @@ __device__ float2 *fft_forward(float2 *a, float2 *b, int logN, const float2 *tw,
 // Inverse transform of a (unscaled); the last pass writes outputs and tail.
 __device__ void fft_inverse_out(float2 *a, float2 *b, int logN, const float2 *tw, const BlockIO &io) {
     const int rem = logN % 3, npass = logN / 3 + (rem ? 1 : 0);
-    int logm = 0;
+    int logm = 0, toff = 0;
     for (int p = 0; p < npass; ++p) {
         const int logR = (p == 0 && rem) ? rem : 3;
         if (p == npass - 1) {
-            radix_pass_any<true, SRC_SMEM, DST_GOUT>(logR, a, b, logN, logm, tw, io);
+            radix_pass_any<true, SRC_SMEM, DST_GOUT>(logR, a, b, logN, logm, tw + toff, io);
         } else {
-            radix_pass_any<true, SRC_SMEM, DST_SMEM>(logR, a, b, logN, logm, tw, io);
+            radix_pass_any<true, SRC_SMEM, DST_SMEM>(logR, a, b, logN, logm, tw + toff, io);
             __syncthreads();
             float2 *tmp = a;
             a = b;
             b = tmp;
         }
+        if (logm > 0) toff += 1 << logm;
         logm += logR;
     }
 }
@@ -262,7 +278,15 @@ __global__ void __launch_bounds__(kFftMaxThreads) fftfilt_block_kernel(const __g
     extern __shared__ float2 sm[];
     const int NP = pad(fp.N);
     float2 *stw = sm + 2 * NP;
-    for (int i = threadIdx.x; i < fp.N / 2; i += blockDim.x) stw[i] = __ldg(tw + i);
+    for (int i = threadIdx.x; i < fp.twlen; i += blockDim.x) stw[i] = __ldg(tw + i);
+    {
+        // start the old tail of both channels (contiguous) on its way to L2
+        const int T1 = fp.M - 1, c1 = 2 * blockIdx.x;
+        const long long n = (long long)T1 * min(2, C - c1);
+        const long long off = (long long)threadIdx.x * 32;   // one 128-byte line per thread
+        for (long long e = off; e < n; e += (long long)blockDim.x * 32)
+            asm volatile("prefetch.global.L2 [%0];" ::"l"(told + (long long)c1 * T1 + e));
+    }
     BlockIO io;
     io.x = x;
     io.ldx = ldx;
@@ -288,7 +312,7 @@ __global__ void __launch_bounds__(kFftMaxThreads) fft_of_taps_kernel(const __gri
     extern __shared__ float2 sm[];
     const int NP = pad(fp.N);
     float2 *stw = sm + 2 * NP;
-    for (int i = threadIdx.x; i < fp.N / 2; i += blockDim.x) stw[i] = __ldg(tw + i);
+    for (int i = threadIdx.x; i < fp.twlen; i += blockDim.x) stw[i] = __ldg(tw + i);
     __syncthreads();
     BlockIO io{};
     io.x = h;
@@ -376,11 +400,25 @@ filark_status filark_fftfilt_create(int n_channels, int n_taps, const double *ta
     }
     std::vector<float> hf((size_t)n_taps);
     for (int k = 0; k < n_taps; ++k) hf[(size_t)k] = (float)taps[k];
-    std::vector<float2> twh((size_t)f->fp.N / 2);
-    for (int k = 0; k < f->fp.N / 2; ++k) {
-        const double ang = -2.0 * 3.14159265358979323846 * (double)k / (double)f->fp.N;
-        twh[(size_t)k] = make_float2((float)std::cos(ang), (float)std::sin(ang));
+    // per-pass twiddle runs, in the kernels' pass order: w_j = exp(-2 pi i j / (R m)), j < m
+    std::vector<float2> twh;
+    {
+        const int rem = logN % 3, npass = logN / 3 + (rem ? 1 : 0);
+        int logm = 0;
+        for (int p = 0; p < npass; ++p) {
+            const int logR = (p == 0 && rem) ? rem : 3;
+            if (logm > 0) {
+                const int m = 1 << logm, Rm = m << logR;
+                for (int j = 0; j < m; ++j) {
+                    const double ang = -2.0 * 3.14159265358979323846 * (double)j / (double)Rm;
+                    twh.push_back(make_float2((float)std::cos(ang), (float)std::sin(ang)));
+                }
+            }
+            logm += logR;
+        }
     }
+    if (twh.empty()) twh.push_back(make_float2(1.f, 0.f));
+    f->fp.twlen = (int)twh.size();
     float *dh = nullptr;
     cudaError_t e = cudaMalloc(&f->H, sizeof(float2) * (size_t)f->fp.N);
     if (e == cudaSuccess) e = cudaMalloc(&f->tw, sizeof(float2) * twh.size());

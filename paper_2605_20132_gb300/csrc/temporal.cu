@@ -37,7 +37,7 @@ constexpr int kFirRows = 256;       // FIR outputs per CTA
 constexpr int kFirThreads = 256;    // (channel, group of 32 outputs)
 constexpr int kFirMaxTaps = 512;
 constexpr int kScanBlocks = 32;     // blocks of 32 samples per slab (window / EMA kernels)
-constexpr int kScanCh = 8;          // channels per CTA of the window / EMA kernels: 32-byte rows,
+constexpr int kScanCh = 8;          // channels per CTA of the prefix kernel: 32-byte rows,
                                     // and enough CTAs (C / 8) to fill every SM
 constexpr int kScanThreads = kScanCh * kScanBlocks;  // 256
 constexpr int kEmaCh = 32;          // channels per CTA of the EMA kernel (measured faster than 8)
