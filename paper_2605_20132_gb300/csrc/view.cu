@@ -31,7 +31,20 @@ __device__ __forceinline__ float reduce_group(const float *p, long long st, int 
     if (mode == FILARK_VIEW_DROP || n == 1) return p[0];
     if (mode == FILARK_VIEW_PEAK) {
         float best = p[0], mag = fabsf(p[0]);
-        for (int i = 1; i < n; ++i) {
+        int i = 1;
+        // four loads in flight, then the comparisons in order (first on ties)
+        for (; i + 4 <= n; i += 4) {
+            float v[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) v[u] = p[(long long)(i + u) * st];
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                if (fabsf(v[u]) > mag) {
+                    mag = fabsf(v[u]);
+                    best = v[u];
+                }
+        }
+        for (; i < n; ++i) {
             const float v = p[(long long)i * st];
             if (fabsf(v) > mag) {
                 mag = fabsf(v);
@@ -74,7 +87,20 @@ __global__ void view_columns_kernel(const float *__restrict__ carry, const float
     } else if (mode == FILARK_VIEW_PEAK) {
         out = vsample(carry, src, nc, H, v0, r);
         float mag = fabsf(out);
-        for (int k = 1; k < kt; ++k) {
+        int k = 1;
+        // four loads in flight, then the comparisons in order (first on ties)
+        for (; k + 4 <= kt; k += 4) {
+            float v[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) v[u] = vsample(carry, src, nc, H, v0 + k + u, r);
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                if (fabsf(v[u]) > mag) {
+                    mag = fabsf(v[u]);
+                    out = v[u];
+                }
+        }
+        for (; k < kt; ++k) {
             const float v = vsample(carry, src, nc, H, v0 + k, r);
             if (fabsf(v) > mag) {
                 mag = fabsf(v);
