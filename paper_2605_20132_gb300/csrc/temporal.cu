@@ -8,7 +8,8 @@
 //         are carried (overlap-save).  CTA = 32 channels x 256 outputs; the
 //         inputs with M-1 rows of history sit in shared memory; each thread
 //         makes 32 consecutive outputs of one channel from a 63-value register
-//         window per 32 taps (FFMA with the taps as constant-bank operands).
+//         window per 32 taps, the last M mod 32 taps in groups of 8 (FFMA with
+//         the taps as constant-bank operands).
 //   MEAN  y[n] = (1/w) sum_{k<w} x[n-k]
 //   AGC   g[n] = (1/w) sum_{k<w} |x[n-k]|, y[n] = x[n] / g[n] (0 if g = 0)
 //         Window sums are differences of a running prefix P of x (or |x|) kept
@@ -116,7 +117,8 @@ __global__ void __launch_bounds__(kFirThreads) fir_kernel(const __grid_constant_
     float acc[32];
 #pragma unroll
     for (int j = 0; j < 32; ++j) acc[j] = 0.f;
-    for (int k0 = 0; k0 < fp.Mpad; k0 += 32) {
+    const int M32 = fp.M & ~31;
+    for (int k0 = 0; k0 < M32; k0 += 32) {
         // w[q] = input row r0 - k0 - 31 + q, q = 0..62
         float w[63];
         const float *base = xs + (OFF + r0 - k0 - 31) * kTopCh + ch;
@@ -127,6 +129,20 @@ __global__ void __launch_bounds__(kFirThreads) fir_kernel(const __grid_constant_
             const float hk = fp.h[k0 + kk];
 #pragma unroll
             for (int j = 0; j < 32; ++j) acc[j] = fmaf(hk, w[j - kk + 31], acc[j]);
+        }
+    }
+    // the remaining taps in groups of 8 (the taps past M are zero)
+    for (int k0 = M32; k0 < fp.M; k0 += 8) {
+        // w[q] = input row r0 - k0 - 7 + q, q = 0..38
+        float w[39];
+        const float *base = xs + (OFF + r0 - k0 - 7) * kTopCh + ch;
+#pragma unroll
+        for (int q = 0; q < 39; ++q) w[q] = base[q * kTopCh];
+#pragma unroll
+        for (int kk = 0; kk < 8; ++kk) {
+            const float hk = fp.h[k0 + kk];
+#pragma unroll
+            for (int j = 0; j < 32; ++j) acc[j] = fmaf(hk, w[j - kk + 7], acc[j]);
         }
     }
     const int c = c0 + ch;
