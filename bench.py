@@ -295,6 +295,7 @@ def run_gpu(args, rank: int, world: int, dist) -> None:
     e2e_s = max_over_ranks(time.perf_counter() - t0, dist, dev)
     e2e_value = whole_job_rate(C * N * e2e_steps, world, e2e_s)
     chain.close()
+    link = host_link_rates(xh, rh, C * T)
 
     if rank != 0:
         return
@@ -336,7 +337,12 @@ def run_gpu(args, rank: int, world: int, dist) -> None:
         "cpu_baseline": {"value": cpu_value, "unit": UNIT, "cores": cores, "kind": "oracle",
                          "sample": f"{C} channels x {cpu_push} pushes of {T} samples, FP64 oracle, {cores} threads"},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 4 * C * N,
-                "d2h_bytes_per_step": 4 * C * N},
+                "d2h_bytes_per_step": 4 * C * N,
+                # the host link's own rates on this machine, measured right after:
+                # the pipelined e2e moves 4 B in and 4 B out per channel-sample
+                "host_link_gbs": link,
+                "link_bound": link["both"] * 1e9 / 8.0,
+                "frac_of_link_bound": e2e_value / (link["both"] * 1e9 / 8.0)},
         "gpu_launches": launches,
         "clocks": sampler.summary(),
     }
@@ -350,6 +356,36 @@ def kernel_sha() -> str:
         with open(os.path.join(ROOT, "paper_2605_20132_gb300", "csrc", f), "rb") as fh:
             hsh.update(fh.read())
     return hsh.hexdigest()[:16]
+
+
+def host_link_rates(xh, rh, n: int) -> dict:
+    """Copy-engine rates between page-locked host memory and the device for
+    pushes of n floats: H2D alone, D2H alone, both directions at once
+    (GB/s, 8 copies each)."""
+    import torch
+    d1 = torch.empty(n, device="cuda")
+    d2 = torch.empty(n, device="cuda")
+    s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
+    src, dst = xh.view(-1), rh.view(-1)
+    k = max(1, min(8, src.numel() // n))
+
+    def run(h2d, d2h):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for i in range(k):
+            if h2d:
+                with torch.cuda.stream(s1):
+                    d1.copy_(src[i * n:(i + 1) * n], non_blocking=True)
+            if d2h:
+                with torch.cuda.stream(s2):
+                    dst[i * n:(i + 1) * n].copy_(d2, non_blocking=True)
+        torch.cuda.synchronize()
+        return time.perf_counter() - t0
+
+    run(True, True)
+    b = 4.0 * n * k
+    return {"h2d": b / run(True, False) / 1e9, "d2h": b / run(False, True) / 1e9,
+            "both": 2 * b / run(True, True) / 1e9}
 
 
 # ------------------------------------------------- other workloads (lines) --
