@@ -185,6 +185,20 @@ filark_status filark_chain_push_host_async(filark_chain *h, const float *h_in, i
    device status as filark_chain_sync_status does. */
 filark_status filark_chain_host_sync(filark_chain *h, filark_stream_t stream);
 
+/*
+ * Launch geometry (no counterpart in the paper).  Each launch of <= 2048
+ * samples cuts every channel tile's samples into 32-sample blocks and gives
+ * each CTA of the tile's cluster `blocks_per_cta` consecutive blocks (at most
+ * 8 CTAs per tile).  0 selects the default, 8; 1..7 gives a short push more
+ * CTAs per tile (raised to ceil(blocks / 8) where a launch would need more
+ * than 8 CTAs), which can lower the latency of chains with few channel tiles
+ * (512 channels, pushes of 1000 on a GB300: 21.9 -> 17.8 us with 4) and is
+ * slower once the tiles fill the GPU.  The dense carry always uses 8.  The
+ * outputs are equal within rounding for every setting, and bit-identical for
+ * the same setting.  FILARK_EINVAL outside 0..8.
+ */
+filark_status filark_chain_set_blocks_per_cta(filark_chain *h, int blocks_per_cta);
+
 /* Zero the whole state (IIR, detector sums, history, sample count) on
    `stream`, and clear a sticky error. */
 filark_status filark_chain_reset_state(filark_chain *h, filark_stream_t stream);

@@ -40,7 +40,7 @@ FILARK_MAX_SPATIAL_WIDTH = 33
 # Every function the header declares (the tests check the library exports them).
 EXPORTED = (
     "filark_chain_create", "filark_chain_push_chunk", "filark_chain_push_chunk_host",
-    "filark_chain_push_host_async", "filark_chain_host_sync",
+    "filark_chain_push_host_async", "filark_chain_host_sync", "filark_chain_set_blocks_per_cta",
     "filark_chain_reset_state", "filark_chain_destroy", "filark_chain_get_state",
     "filark_chain_set_state", "filark_chain_sync_status", "filark_chain_get_info",
     "filark_butter_bandpass_sos", "filark_last_error_string", "filark_abi_version",
@@ -160,6 +160,7 @@ def load(build_if_missing: bool = True) -> ct.CDLL:
             "filark_chain_push_chunk_host": ([vp, vp, i64, i64, vp, vp, vp, i64, vp], ct.c_int),
             "filark_chain_push_host_async": ([vp, vp, i64, i64, vp, vp, vp, i64, vp], ct.c_int),
             "filark_chain_host_sync": ([vp, vp], ct.c_int),
+            "filark_chain_set_blocks_per_cta": ([vp, ct.c_int], ct.c_int),
             "filark_chain_reset_state": ([vp, vp], ct.c_int),
             "filark_chain_destroy": ([vp], ct.c_int),
             "filark_chain_get_state": ([vp, vp, ct.POINTER(ct.c_size_t), vp], ct.c_int),
@@ -256,6 +257,10 @@ def filark_chain_push_host_async(h, h_in, ld_in, n, h_ratio, h_bp, h_sp, ld_out,
 
 def filark_chain_host_sync(h, stream) -> int:
     return load().filark_chain_host_sync(h, stream)
+
+
+def filark_chain_set_blocks_per_cta(h, blocks_per_cta: int) -> int:
+    return load().filark_chain_set_blocks_per_cta(h, blocks_per_cta)
 
 
 def filark_chain_reset_state(h, stream) -> int:

@@ -119,6 +119,11 @@ class Chain:
                                               ld_out, _stream_handle(stream))
         abi.check(st, "filark_chain_push_host_async")
 
+    def set_blocks_per_cta(self, blocks_per_cta: int) -> None:
+        """0: planned per launch (default); 1..8: fixed (see the C header)."""
+        abi.check(abi.filark_chain_set_blocks_per_cta(self._h, int(blocks_per_cta)),
+                  "filark_chain_set_blocks_per_cta")
+
     def host_sync(self, stream=None) -> None:
         abi.check(abi.filark_chain_host_sync(self._h, _stream_handle(stream)), "filark_chain_host_sync")
 

@@ -159,7 +159,14 @@ filark_status push_device(filark_chain *h, const float *d_in, int64_t ld_in, int
         u.det_in = h->detst[h->parity];
         u.det_out = h->detst[h->parity ^ 1];
         u.n0 = h->n;
-        set_unit_geometry(h->plan, Tl, u);
+        // blocks per CTA: kNB unless the caller set fewer (the modal carry's
+        // cross-CTA powers are tabulated per setting; the dense carry keeps kNB)
+        const int nblk = (Tl + kL - 1) / kL;
+        int nbc = kNB;
+        if (!h->plan.dense && h->nbc_fixed > 0)
+            nbc = std::max(h->nbc_fixed, (nblk + kMaxCluster - 1) / kMaxCluster);
+        set_unit_geometry(h->plan, Tl, nbc, u);
+        if (nbc != kNB) set_cta_powers(h->plan, nbc, p);
         u.slot_n0 = h->Q > 0 ? (int)(h->n % h->Q) : 0;
         p.pdl = h->use_pdl;
         u.x_vec4 = (ld_in % 4 == 0) && (((uintptr_t)u.x & 15u) == 0);
@@ -344,6 +351,7 @@ filark_status filark_chain_create(const filark_chain_config *cfg, int cuda_devic
     b.u.ldr = h->ldr;
     b.u.Q = h->Q > 0 ? (int)h->Q : 1;
     b.u.C = h->C;
+    b.u.nbc = kNB;
 
     st = zero_state(h, nullptr);
     if (st == FILARK_OK) {
@@ -497,6 +505,13 @@ filark_status filark_chain_host_sync(filark_chain *h, filark_stream_t stream) {
         return fail_cuda(e, "host_sync");
     }
     return check_device_status(h);
+}
+
+filark_status filark_chain_set_blocks_per_cta(filark_chain *h, int blocks_per_cta) {
+    if (!h) return fail(FILARK_EINVAL, "chain is NULL");
+    if (blocks_per_cta < 0 || blocks_per_cta > kNB) return fail(FILARK_EINVAL, "blocks_per_cta must be in 0..8");
+    h->nbc_fixed = blocks_per_cta;
+    return FILARK_OK;
 }
 
 filark_status filark_chain_sync_status(filark_chain *h, filark_stream_t stream) {

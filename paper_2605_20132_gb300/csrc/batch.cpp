@@ -187,7 +187,7 @@ int stage_push(filark_batch *b, int k, const filark_chunk_desc *d) {
             u.det_in = h->detst[h->parity];
             u.det_out = h->detst[h->parity ^ 1];
             u.n0 = h->n;
-            set_unit_geometry(h->plan, Tl, u);
+            set_unit_geometry(h->plan, Tl, kNB, u);
             u.slot_n0 = h->Q > 0 ? (int)(h->n % h->Q) : 0;
             u.x_vec4 = (c.ld_in % 4 == 0) && (((uintptr_t)u.x & 15u) == 0);
             bool ov = (c.ld_out % 4 == 0);

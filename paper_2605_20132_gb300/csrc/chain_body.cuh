@@ -10,7 +10,7 @@
 //             of an output channel needs its neighbours' bandpass output, so
 //             the halo channels' IIR is computed again by the neighbour tile --
 //             the overlap-aware halo expansion of Sec. 3.4);
-//   grid.y  = R time ranges of kNB blocks x kL samples; the R CTAs of a tile
+//   grid.y  = R time ranges of nbc <= kNB blocks x kL samples; the R CTAs of a tile
 //             form one thread-block cluster and exchange their IIR carries and
 //             detector sums through distributed shared memory.
 //
@@ -299,8 +299,8 @@ __device__ __forceinline__ void chain_body(const ChainParams &p, const ChainUnit
     const int R = cu.R;
     const int c0 = tx * p.Wout;               // first output channel of the tile
     const int cbase = c0 - p.HP;              // channel of tile column 0
-    const int blk0 = r * kNB;
-    const int nb = min(kNB, cu.nblk - blk0);   // blocks in this CTA (>= 1)
+    const int blk0 = r * cu.nbc;
+    const int nb = min(cu.nbc, cu.nblk - blk0);   // blocks in this CTA (>= 1)
     const int row0 = blk0 * kL;               // first launch row of this CTA
     const int rows = min(nb * kL, cu.T - row0);
     const bool last_cta = (r == R - 1);

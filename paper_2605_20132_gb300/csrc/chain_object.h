@@ -33,6 +33,7 @@ struct filark_chain {
     filark::ChainParams base{};
     int64_t device_bytes = 0;
     int use_pdl = 1;
+    int nbc_fixed = 0;            // blocks per CTA set by the caller, 0 = kNB
 };
 
 namespace filark {

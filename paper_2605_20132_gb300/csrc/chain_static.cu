@@ -151,7 +151,7 @@ extern "C" filark_status filark_chain_run_static(const filark_chain_config *cfg,
         u.det_in = dst[parity];
         u.det_out = dst[parity ^ 1];
         u.n0 = done;
-        set_unit_geometry(plan, Tl, u);
+        set_unit_geometry(plan, Tl, kNB, u);
         u.slot_n0 = (int)(done % Q);
         u.x_vec4 = (ld_in % 4 == 0) && (((uintptr_t)u.x & 15u) == 0);
         bool ov = (ld_out % 4 == 0);

@@ -23,7 +23,7 @@ namespace filark {
 // distributed shared memory.
 // ---------------------------------------------------------------------------
 constexpr int kL = 32;                    // samples per time block
-constexpr int kNB = 8;                    // time blocks per CTA
+constexpr int kNB = 8;                    // time blocks per CTA (at most; a launch may use fewer)
 constexpr int kWT = 64;                   // channels per CTA tile (incl. halo)
 constexpr int kThreads = kWT * kNB;       // 512 threads: one per (channel, block)
 constexpr int kTileRows = kL * kNB;       // 256 samples per CTA
@@ -71,6 +71,7 @@ struct ChainUnit {
     int Q;                              // ring length in samples
     int slot_n0;                        // n0 mod Q
     int C, T, nblk, Lr, R;
+    int nbc;                            // blocks per CTA (<= kNB): CTA r covers blocks [r nbc, r nbc + nbc)
     int x_vec4, o_vec4;                 // float4 access allowed (input, outputs)
     // transition over the launch's last CTA, and PhiTot = PhiLast * Phi^(R-1)
     // (launch start -> launch end), as double-float hi/lo pairs
@@ -82,7 +83,7 @@ struct ChainUnit {
 // Everything else is fixed for a chain (for a batch: shared by its streams).
 struct ChainParams {
     Tables32 tab;
-    float PhiPow32[kMaxCluster][kMaxSlots][4]; // Phi^r = M^(L*kNB*r), FP32
+    float PhiPow32[kMaxCluster][kMaxSlots][4]; // Phi^r = M^(L*nbc*r), FP32, for the launch's nbc
     int hw, HP, Wout;
     int ns, nl;
     float ratio_scale;                  // nl / ns
@@ -124,9 +125,10 @@ struct Plan {
     const double (*power_cached(int n) const)[4];
     mutable std::vector<double> pow_cache;     // (kTileRows + 1) x kMaxSlots x 4
     mutable std::vector<char> pow_have;
-    // Phi^r = M^(L*kNB*r) for 0 <= r < kMaxCluster.
-    const double (*power_cached_cta(int r) const)[4];
-    mutable std::vector<double> cta_cache;
+    // Phi^r = M^(L*nbc*r) for 0 <= r < kMaxCluster, 1 <= nbc <= kNB.
+    const double (*power_cached_cta(int nbc, int r) const)[4];
+    mutable std::vector<double> cta_cache;     // (kNB + 1) x kMaxCluster x kMaxSlots x 4
+    mutable std::vector<char> cta_have;
 };
 
 // Message returned by filark_last_error_string on this thread.
@@ -140,9 +142,13 @@ filark_status make_plan(const double *sos, int S, int precision, Plan *plan, std
 filark_status design_butter_bandpass(int order, double f1, double f2, double fs, double *sos,
                                      std::string *err);
 
-// Fill the launch geometry of a unit of Tl samples (1 <= Tl <= kTileRows * Rmax,
-// Rmax <= kMaxCluster) and its ragged-end transitions from the plan.
-void set_unit_geometry(const Plan &plan, int Tl, ChainUnit &u);
+// Fill the launch geometry of a unit of Tl samples with nbc blocks per CTA
+// (1 <= Tl <= kL * nbc * kMaxCluster) and its ragged-end transitions.
+void set_unit_geometry(const Plan &plan, int Tl, int nbc, ChainUnit &u);
+
+
+// p.PhiPow32 for nbc blocks per CTA.
+void set_cta_powers(const Plan &plan, int nbc, ChainParams &p);
 
 // Static kernel parameters of a chain (tables, transitions, geometry).
 void set_static_params(const Plan &plan, int hw, int HP, int Wout, int ns, int nl, const double *dense_dev,
@@ -155,6 +161,7 @@ cudaError_t launch_chain(const ChainParams &p, int NS, bool detector, bool dense
                          cudaStream_t stream);
 
 size_t chain_smem_bytes(bool dense);
+
 
 // The batched kernel: a persistent grid of `n_clusters` clusters of `cluster`
 // CTAs (time ranges) takes the items in order from a device counter.

@@ -118,7 +118,9 @@ ld frob(const std::vector<ld> &a) {
 // Emulates, on one channel, the FP32/FP64 arithmetic the kernel performs, and
 // returns the normwise error against a long double TDF-II run of the same
 // input.  Used to verify the FP32 modal tables before a chain is accepted.
-double probe_modal(const Plan &pl, const std::vector<Section> &secs) {
+// fewest_blocks: every launch uses the fewest blocks per CTA a caller may set
+// (more CTAs, shorter FP32 chains) instead of kNB.
+double probe_modal(const Plan &pl, const std::vector<Section> &secs, bool fewest_blocks) {
     const int NS = pl.NS, R2 = 2 * NS;
     // deterministic probe: uniform noise with an impulse at the start
     const int launches[] = {2048, 1500, 1, 700, 2048, 33, 2048};
@@ -144,7 +146,8 @@ double probe_modal(const Plan &pl, const std::vector<Section> &secs) {
     for (int T : launches) {
         const int nblk = (T + kL - 1) / kL, Lr = T - (nblk - 1) * kL;
         pl.slot_power(Lr, Mr);
-        const int R = (nblk + kNB - 1) / kNB;
+        const int nbc = fewest_blocks ? std::max(1, (nblk + kMaxCluster - 1) / kMaxCluster) : kNB;
+        const int R = (nblk + nbc - 1) / nbc;
         std::vector<float> e((size_t)nblk * R2), er((size_t)R2, 0.f);
         std::vector<float> yl((size_t)nblk * kL);
         for (int j = 0; j < nblk; ++j) {
@@ -173,12 +176,12 @@ double probe_modal(const Plan &pl, const std::vector<Section> &secs) {
         }
         // carries: FP32 aggregate per CTA (the last CTA's ragged block uses
         // M^Lr and the right-aligned end state), FP64 across CTAs and launches
-        const int nb_last = nblk - (R - 1) * kNB;
+        const int nb_last = nblk - (R - 1) * nbc;
         double PhiLast[kMaxSlots][4];
         pl.slot_power((nb_last - 1) * kL + Lr, PhiLast);
         std::vector<float> agg((size_t)R * R2, 0.f);
         for (int rr = 0; rr < R; ++rr) {
-            int j0 = rr * kNB, nb = std::min(kNB, nblk - j0);
+            int j0 = rr * nbc, nb = std::min(nbc, nblk - j0);
             for (int s = 0; s < NS; ++s) {
                 float a0 = 0.f, a1 = 0.f;
                 for (int jj = 0; jj < nb; ++jj) {
@@ -198,16 +201,16 @@ double probe_modal(const Plan &pl, const std::vector<Section> &secs) {
         }
         std::vector<float> mstart((size_t)nblk * R2);
         std::vector<double> newstate((size_t)R2);
-        const double (*PP)[4] = pl.power_cached_cta(R - 1);
+        const double (*PP)[4] = pl.power_cached_cta(nbc, R - 1);
         for (int rr = 0; rr < R; ++rr) {
-            int j0 = rr * kNB, nb = std::min(kNB, nblk - j0);
-            const double (*Pr)[4] = pl.power_cached_cta(rr);
+            int j0 = rr * nbc, nb = std::min(nbc, nblk - j0);
+            const double (*Pr)[4] = pl.power_cached_cta(nbc, rr);
             for (int s = 0; s < NS; ++s) {
                 // as the kernel: earlier CTAs' aggregates through their own FP32
                 // powers, the carried state's leading float through Phi^rr
                 float g0 = 0.f, g1 = 0.f;
                 for (int q = 0; q < rr; ++q) {
-                    const double (*Pq)[4] = pl.power_cached_cta(rr - 1 - q);
+                    const double (*Pq)[4] = pl.power_cached_cta(nbc, rr - 1 - q);
                     const float a0 = agg[(size_t)q * R2 + 2 * s], a1 = agg[(size_t)q * R2 + 2 * s + 1];
                     g0 = std::fmaf((float)Pq[s][0], a0, std::fmaf((float)Pq[s][1], a1, g0));
                     g1 = std::fmaf((float)Pq[s][2], a0, std::fmaf((float)Pq[s][3], a1, g1));
@@ -403,13 +406,18 @@ const double (*Plan::power_cached(int n) const)[4] {
     return slot;
 }
 
-const double (*Plan::power_cached_cta(int r) const)[4] {
+const double (*Plan::power_cached_cta(int nbc, int r) const)[4] {
     if (cta_cache.empty()) {
-        cta_cache.assign((size_t)kMaxCluster * kMaxSlots * 4, 0.0);
-        for (int q = 0; q < kMaxCluster; ++q)
-            slot_power(kL * kNB * q, reinterpret_cast<double (*)[4]>(&cta_cache[(size_t)q * kMaxSlots * 4]));
+        cta_cache.assign((size_t)(kNB + 1) * kMaxCluster * kMaxSlots * 4, 0.0);
+        cta_have.assign((size_t)(kNB + 1), 0);
     }
-    return reinterpret_cast<const double (*)[4]>(&cta_cache[(size_t)r * kMaxSlots * 4]);
+    double *base = &cta_cache[(size_t)nbc * kMaxCluster * kMaxSlots * 4];
+    if (!cta_have[(size_t)nbc]) {
+        for (int q = 0; q < kMaxCluster; ++q)
+            slot_power(kL * nbc * q, reinterpret_cast<double (*)[4]>(base + (size_t)q * kMaxSlots * 4));
+        cta_have[(size_t)nbc] = 1;
+    }
+    return reinterpret_cast<const double (*)[4]>(base + (size_t)r * kMaxSlots * 4);
 }
 
 filark_status make_plan(const double *sos, int S, int precision, Plan *pl, std::string *err) {
@@ -599,7 +607,7 @@ filark_status make_plan(const double *sos, int S, int precision, Plan *pl, std::
         pl->slot_power(kL, ML);
         for (int s = 0; s < kMaxSlots; ++s)
             for (int q = 0; q < 4; ++q) tb.M[s][q] = (float)ML[s][q];
-        pl->probe_err = probe_modal(*pl, secs);
+        pl->probe_err = std::max(probe_modal(*pl, secs, false), probe_modal(*pl, secs, true));
         use_modal = precision == FILARK_PREC_MODAL32 ||
                     ((precision == FILARK_PREC_AUTO || precision == FILARK_PREC_ALL32) && pl->probe_err < 2e-6);
     } else {
@@ -706,16 +714,17 @@ filark_status design_butter_bandpass(int order, double f1, double f2, double fs,
     return FILARK_OK;
 }
 
-void set_unit_geometry(const Plan &plan, int Tl, ChainUnit &u) {
+void set_unit_geometry(const Plan &plan, int Tl, int nbc, ChainUnit &u) {
     u.T = Tl;
     u.nblk = (Tl + kL - 1) / kL;
     u.Lr = Tl - (u.nblk - 1) * kL;
-    u.R = (u.nblk + kNB - 1) / kNB;
+    u.nbc = nbc;
+    u.R = (u.nblk + nbc - 1) / nbc;
     if (plan.NS > 0) {
-        const int nb_last = u.nblk - (u.R - 1) * kNB;
+        const int nb_last = u.nblk - (u.R - 1) * nbc;
         const double (*pl)[4] = plan.power_cached((nb_last - 1) * kL + u.Lr);
         const double (*pr)[4] = plan.power_cached(u.Lr);
-        const double (*pp)[4] = plan.power_cached_cta(u.R - 1);
+        const double (*pp)[4] = plan.power_cached_cta(nbc, u.R - 1);
         for (int s = 0; s < kMaxSlots; ++s) {
             // PhiTot = PhiLast * Phi^(R-1) (2x2 per slot)
             const double *a = pl[s], *b = pp[s];
@@ -736,11 +745,7 @@ void set_static_params(const Plan &plan, int hw, int HP, int Wout, int ns, int n
                        ChainParams &p) {
     std::memset(&p, 0, sizeof(p));
     p.tab = plan.tab;
-    for (int r = 0; r < kMaxCluster; ++r) {
-        const double (*pr)[4] = plan.power_cached_cta(r);
-        for (int s = 0; s < kMaxSlots; ++s)
-            for (int q = 0; q < 4; ++q) p.PhiPow32[r][s][q] = (float)pr[s][q];
-    }
+    set_cta_powers(plan, kNB, p);
     p.hw = hw;
     p.HP = HP;
     p.Wout = Wout;
@@ -749,6 +754,14 @@ void set_static_params(const Plan &plan, int hw, int HP, int Wout, int ns, int n
     p.ratio_scale = (nl > 0 && ns > 0) ? (float)((double)nl / (double)ns) : 0.f;
     p.all32 = plan.mode == FILARK_PREC_ALL32;
     p.dense = dense_dev;
+}
+
+void set_cta_powers(const Plan &plan, int nbc, ChainParams &p) {
+    for (int r = 0; r < kMaxCluster; ++r) {
+        const double (*pr)[4] = plan.power_cached_cta(nbc, r);
+        for (int s = 0; s < kMaxSlots; ++s)
+            for (int q = 0; q < 4; ++q) p.PhiPow32[r][s][q] = (float)pr[s][q];
+    }
 }
 
 }  // namespace filark

@@ -92,8 +92,9 @@ def test_batch_matches_oracle(small_case, cluster, graph):
 
 
 def test_batch_bitwise_equals_single_chains(small_case):
-    """With 8 time ranges per cluster a batched push does exactly the work of
-    the single-stream pushes: the outputs agree bit for bit."""
+    """With 8 time ranges per cluster, and 8 blocks per CTA on both sides, a
+    batched push does exactly the work of the single-stream pushes: the
+    outputs agree bit for bit."""
     import torch
     from paper_2605_20132_gb300.chain import Batch, Chain
     Cs, T, data, sos, _ = small_case
@@ -103,6 +104,7 @@ def test_batch_bitwise_equals_single_chains(small_case):
     b.close()
     for i, C in enumerate(Cs):
         ch = Chain(C, sos, 1000.0, K, NS_, NL, outputs=ALL_OUT, max_chunk=3000)
+        ch.set_blocks_per_cta(8)   # the batch's CTAs cover 8 blocks each
         x = torch.from_numpy(data[i]).cuda()
         o = {k: torch.empty(data[i].shape, device="cuda") for k in ("ratio", "bp", "sp")}
         t = 0

@@ -143,6 +143,38 @@ def test_step_off_gives_exact_zero_ratio(oracle_mod):
     assert compare(got, ref)["ratio"] <= TOL
 
 
+@pytest.mark.parametrize("nbc", [0, 1, 3, 4, 5, 6, 7, 8])
+def test_blocks_per_cta_choices_match_oracle(oracle_mod, nbc):
+    """Every blocks-per-CTA setting (0 = the default, 8) matches the oracle
+    over launches of many lengths (ragged, one sample, 2048, split pushes) on
+    several channel tiles, and repeats bit for bit."""
+    from paper_2605_20132_gb300.chain import Chain
+    x = synth.small_stream(300, 7000, seed=31)
+    sos = small_sos(oracle_mod)
+    chunks = [1500, 2048, 1, 700, 1751, 1000]
+    ref = run_oracle(oracle_mod, x, sos, K=5, ns=50, nl=1000)
+    outs = []
+    for _ in range(2):
+        ch = Chain(300, sos, 1000.0, 5, 50, 1000, outputs=ALL_OUT, max_chunk=2048)
+        ch.set_blocks_per_cta(nbc)
+        outs.append(run_gpu(x, chunks, sos, K=5, ns=50, nl=1000, chain=ch))
+        ch.close()
+    errs = compare(outs[0], ref)
+    print(nbc, errs)
+    assert all(e <= TOL for e in errs.values()), errs
+    for k in outs[0]:
+        assert np.array_equal(outs[0][k], outs[1][k]), k
+
+
+def test_blocks_per_cta_rejects_out_of_range(oracle_mod):
+    from paper_2605_20132_gb300.chain import Chain
+    ch = Chain(16, small_sos(oracle_mod), 1000.0, 3, 5, 50, outputs=ALL_OUT, max_chunk=100)
+    for bad in (-1, 9):
+        assert abi.filark_chain_set_blocks_per_cta(ch._h, bad) == abi.FILARK_EINVAL
+    assert abi.filark_chain_set_blocks_per_cta(ch._h, 0) == abi.FILARK_OK
+    ch.close()
+
+
 def test_deterministic(oracle_mod):
     x = synth.small_stream(64, 4000, seed=4)
     a = run_gpu(x, [4000], small_sos(oracle_mod), K=5, ns=50, nl=1000)
