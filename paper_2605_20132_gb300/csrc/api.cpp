@@ -28,22 +28,11 @@ filark_status fail(filark_status st, const std::string &msg) {
 }
 
 filark_status fail_cuda(cudaError_t e, const char *what) {
+    cudaGetLastError();
     g_err = std::string(what) + ": " + cudaGetErrorString(e);
     return FILARK_ECUDA;
 }
 
-// Restores the caller's current device on scope exit.
-struct DeviceGuard {
-    int prev = -1;
-    bool ok = false;
-    explicit DeviceGuard(int dev) {
-        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
-        ok = cudaSetDevice(dev) == cudaSuccess;
-    }
-    ~DeviceGuard() {
-        if (prev >= 0) cudaSetDevice(prev);
-    }
-};
 
 std::mutex g_cfg_mu;
 std::set<int> g_configured;

@@ -32,28 +32,8 @@ constexpr int kMaxTuned = 16;
 
 size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
 
-filark_status bfail(filark_status st, const std::string &msg) {
-    set_last_error(msg);
-    return st;
-}
 
-filark_status bfail_cuda(cudaError_t e, const char *what) {
-    cudaGetLastError();
-    set_last_error(std::string(what) + ": " + cudaGetErrorString(e));
-    return FILARK_ECUDA;
-}
 
-struct DeviceGuard {
-    int prev = -1;
-    bool ok = false;
-    explicit DeviceGuard(int dev) {
-        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
-        ok = cudaSetDevice(dev) == cudaSuccess;
-    }
-    ~DeviceGuard() {
-        if (prev >= 0) cudaSetDevice(prev);
-    }
-};
 
 }  // namespace
 
@@ -121,20 +101,20 @@ filark_status build_graphs(filark_batch *b) {
     if (!b->use_graph) return FILARK_OK;
     for (int k = 0; k < 2; ++k) {
         cudaError_t e = cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal);
-        if (e != cudaSuccess) return bfail_cuda(e, "batch: begin capture");
+        if (e != cudaSuccess) return fail_cuda_with(e, "batch: begin capture");
         cudaError_t e1 = cudaMemcpyAsync(b->d_desc, b->h_stage[k], b->desc_bytes, cudaMemcpyHostToDevice, b->cap);
         cudaError_t e2 = e1 == cudaSuccess ? enqueue_launch(b, b->cap) : e1;
         cudaGraph_t g = nullptr;
         e = cudaStreamEndCapture(b->cap, &g);
         if (e2 != cudaSuccess || e != cudaSuccess) {
             if (g) cudaGraphDestroy(g);
-            return bfail_cuda(e2 != cudaSuccess ? e2 : e, "batch: capture of upload + launch");
+            return fail_cuda_with(e2 != cudaSuccess ? e2 : e, "batch: capture of upload + launch");
         }
         e = cudaGraphInstantiate(&b->exec[k], g, 0);
         cudaGraphDestroy(g);
         if (e != cudaSuccess) {
             b->exec[k] = nullptr;
-            return bfail_cuda(e, "batch: graph instantiate");
+            return fail_cuda_with(e, "batch: graph instantiate");
         }
     }
     return FILARK_OK;
@@ -142,10 +122,10 @@ filark_status build_graphs(filark_batch *b) {
 
 filark_status set_launch(filark_batch *b, int cluster, int n_clusters, int use_graph) {
     if (std::find(std::begin(kClusterChoices), std::end(kClusterChoices), cluster) == std::end(kClusterChoices))
-        return bfail(FILARK_EINVAL, "batch: cluster must be 1, 2, 4 or 8");
+        return fail_with(FILARK_EINVAL, "batch: cluster must be 1, 2, 4 or 8");
     int n = n_clusters;
     if (n <= 0) n = batch_max_active_clusters(b->NS, b->det, b->dense, cluster);
-    if (n <= 0) return bfail(FILARK_ENOSYS, "batch: no cluster of this size fits on the device");
+    if (n <= 0) return fail_with(FILARK_ENOSYS, "batch: no cluster of this size fits on the device");
     b->cluster = cluster;
     b->n_clusters = n;
     b->use_graph = use_graph ? 1 : 0;
@@ -217,7 +197,7 @@ int stage_push(filark_batch *b, int k, const filark_chunk_desc *d) {
 }
 
 filark_status push(filark_batch *b, const filark_chunk_desc *descs, cudaStream_t stream) {
-    if (b->sticky != FILARK_OK) return bfail(FILARK_ESTATE, "batch is in an error state; reset it");
+    if (b->sticky != FILARK_OK) return fail_with(FILARK_ESTATE, "batch is in an error state; reset it");
     const int n = (int)b->chains.size();
     for (int i = 0; i < n; ++i) {
         filark_chain *h = b->chains[(size_t)i];
@@ -225,11 +205,11 @@ filark_status push(filark_batch *b, const filark_chunk_desc *descs, cudaStream_t
         if (st != FILARK_OK) return st;
         const filark_chunk_desc &c = descs[i];
         st = chain_validate_push(h, c.d_in, c.ld_in, c.n_samples, c.d_ratio, c.d_bandpass, c.d_spatial, c.ld_out);
-        if (st != FILARK_OK) return bfail(st, "stream " + std::to_string(i) + ": " + filark_last_error_string());
+        if (st != FILARK_OK) return fail_with(st, "stream " + std::to_string(i) + ": " + filark_last_error_string());
     }
     const int k = b->next;
     cudaError_t e = cudaEventSynchronize(b->staged[k]);   // the push before last has uploaded this buffer
-    if (e != cudaSuccess) return bfail_cuda(e, "batch: staging event");
+    if (e != cudaSuccess) return fail_cuda_with(e, "batch: staging event");
     const int ni = stage_push(b, k, descs);
     if (ni == 0) return FILARK_OK;
     if (b->use_graph) {
@@ -242,7 +222,7 @@ filark_status push(filark_batch *b, const filark_chunk_desc *descs, cudaStream_t
     if (e != cudaSuccess) {
         b->sticky = FILARK_ECUDA;
         for (filark_chain *h : b->chains) h->sticky = FILARK_ECUDA;
-        return bfail_cuda(e, "batch: launch");
+        return fail_cuda_with(e, "batch: launch");
     }
     b->next ^= 1;
     return FILARK_OK;
@@ -263,12 +243,12 @@ extern "C" {
 
 filark_status filark_batch_create(const filark_chain_config *cfg, int n_streams, const int32_t *n_channels,
                                   int cuda_device, filark_batch **out) {
-    if (!out) return bfail(FILARK_EINVAL, "out is NULL");
+    if (!out) return fail_with(FILARK_EINVAL, "out is NULL");
     *out = nullptr;
-    if (!cfg || !n_channels) return bfail(FILARK_EINVAL, "config or n_channels is NULL");
-    if (n_streams < 1) return bfail(FILARK_EINVAL, "n_streams must be >= 1");
+    if (!cfg || !n_channels) return fail_with(FILARK_EINVAL, "config or n_channels is NULL");
+    if (n_streams < 1) return fail_with(FILARK_EINVAL, "n_streams must be >= 1");
     filark_batch *b = new (std::nothrow) filark_batch();
-    if (!b) return bfail(FILARK_ENOMEM, "host allocation failed");
+    if (!b) return fail_with(FILARK_ENOMEM, "host allocation failed");
     b->device = cuda_device;
     for (int i = 0; i < n_streams; ++i) {
         filark_chain_config c = *cfg;
@@ -278,7 +258,7 @@ filark_status filark_batch_create(const filark_chain_config *cfg, int n_streams,
         if (st != FILARK_OK) {
             const std::string msg = "stream " + std::to_string(i) + ": " + filark_last_error_string();
             free_batch(b);
-            return bfail(st, msg);
+            return fail_with(st, msg);
         }
         h->use_pdl = 0;
         b->chains.push_back(h);
@@ -290,7 +270,7 @@ filark_status filark_batch_create(const filark_chain_config *cfg, int n_streams,
             if (cudaMalloc(&hs, bytes) != cudaSuccess) {
                 cudaGetLastError();
                 free_batch(b);
-                return bfail(FILARK_ENOMEM, "batch create: halo state allocation");
+                return fail_with(FILARK_ENOMEM, "batch create: halo state allocation");
             }
             b->device_bytes += (int64_t)bytes;
         }
@@ -315,7 +295,7 @@ filark_status filark_batch_create(const filark_chain_config *cfg, int n_streams,
     DeviceGuard dg(cuda_device);
     if (!dg.ok) {
         free_batch(b);
-        return bfail(FILARK_ECUDA, "cudaSetDevice failed for device " + std::to_string(cuda_device));
+        return fail_with(FILARK_ECUDA, "cudaSetDevice failed for device " + std::to_string(cuda_device));
     }
     cudaError_t e = cudaMalloc(&b->d_desc, b->desc_bytes);
     for (int k = 0; k < 2 && e == cudaSuccess; ++k) e = cudaHostAlloc(&b->h_stage[k], b->desc_bytes, cudaHostAllocDefault);
@@ -323,7 +303,7 @@ filark_status filark_batch_create(const filark_chain_config *cfg, int n_streams,
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
     if (e != cudaSuccess) {
         free_batch(b);
-        return bfail_cuda(e, "batch create: allocation");
+        return fail_cuda_with(e, "batch create: allocation");
     }
     b->device_bytes += (int64_t)b->desc_bytes;
     for (int k = 0; k < 2; ++k) std::memset(b->h_stage[k], 0, b->desc_bytes);
@@ -331,45 +311,45 @@ filark_status filark_batch_create(const filark_chain_config *cfg, int n_streams,
     if (st != FILARK_OK) {
         const std::string msg = filark_last_error_string();
         free_batch(b);
-        return bfail(st, msg);
+        return fail_with(st, msg);
     }
     *out = b;
     return FILARK_OK;
 }
 
 filark_status filark_batch_push(filark_batch *b, const filark_chunk_desc *descs, filark_stream_t stream) {
-    if (!b) return bfail(FILARK_EINVAL, "batch is NULL");
-    if (!descs) return bfail(FILARK_EINVAL, "descs is NULL");
+    if (!b) return fail_with(FILARK_EINVAL, "batch is NULL");
+    if (!descs) return fail_with(FILARK_EINVAL, "descs is NULL");
     DeviceGuard dg(b->device);
-    if (!dg.ok) return bfail(FILARK_ECUDA, "cudaSetDevice failed");
+    if (!dg.ok) return fail_with(FILARK_ECUDA, "cudaSetDevice failed");
     return push(b, descs, (cudaStream_t)stream);
 }
 
 filark_status filark_batch_set_launch(filark_batch *b, int cluster, int n_clusters, int use_graph) {
-    if (!b) return bfail(FILARK_EINVAL, "batch is NULL");
+    if (!b) return fail_with(FILARK_EINVAL, "batch is NULL");
     DeviceGuard dg(b->device);
-    if (!dg.ok) return bfail(FILARK_ECUDA, "cudaSetDevice failed");
+    if (!dg.ok) return fail_with(FILARK_ECUDA, "cudaSetDevice failed");
     // the staging buffers may still be read by an earlier upload
     for (cudaEvent_t ev : b->staged) {
         cudaError_t e = cudaEventSynchronize(ev);
-        if (e != cudaSuccess) return bfail_cuda(e, "batch: staging event");
+        if (e != cudaSuccess) return fail_cuda_with(e, "batch: staging event");
     }
     return set_launch(b, cluster, n_clusters, use_graph);
 }
 
 filark_status filark_batch_tune(filark_batch *b, const filark_chunk_desc *descs, int timed_pushes,
                                 filark_stream_t stream) {
-    if (!b || !descs) return bfail(FILARK_EINVAL, "batch or descs is NULL");
-    if (timed_pushes < 1) return bfail(FILARK_EINVAL, "timed_pushes must be >= 1");
+    if (!b || !descs) return fail_with(FILARK_EINVAL, "batch or descs is NULL");
+    if (timed_pushes < 1) return fail_with(FILARK_EINVAL, "timed_pushes must be >= 1");
     DeviceGuard dg(b->device);
-    if (!dg.ok) return bfail(FILARK_ECUDA, "cudaSetDevice failed");
+    if (!dg.ok) return fail_with(FILARK_ECUDA, "cudaSetDevice failed");
     cudaStream_t s = (cudaStream_t)stream;
     cudaEvent_t t0 = nullptr, t1 = nullptr;
     cudaError_t e = cudaEventCreate(&t0);
     if (e == cudaSuccess) e = cudaEventCreate(&t1);
     if (e != cudaSuccess) {
         if (t0) cudaEventDestroy(t0);
-        return bfail_cuda(e, "tune: events");
+        return fail_cuda_with(e, "tune: events");
     }
     filark_status st = FILARK_OK;
     double best = 1e300;
@@ -384,13 +364,13 @@ filark_status filark_batch_tune(filark_batch *b, const filark_chunk_desc *descs,
             st = set_launch(b, cl, occ * mult, 1);
             if (st == FILARK_OK) st = reset(b, s);
             for (int w = 0; w < 2 && st == FILARK_OK; ++w) st = push(b, descs, s);
-            if (st == FILARK_OK && (e = cudaEventRecord(t0, s)) != cudaSuccess) st = bfail_cuda(e, "tune: record");
+            if (st == FILARK_OK && (e = cudaEventRecord(t0, s)) != cudaSuccess) st = fail_cuda_with(e, "tune: record");
             for (int r = 0; r < timed_pushes && st == FILARK_OK; ++r) st = push(b, descs, s);
-            if (st == FILARK_OK && (e = cudaEventRecord(t1, s)) != cudaSuccess) st = bfail_cuda(e, "tune: record");
-            if (st == FILARK_OK && (e = cudaEventSynchronize(t1)) != cudaSuccess) st = bfail_cuda(e, "tune: sync");
+            if (st == FILARK_OK && (e = cudaEventRecord(t1, s)) != cudaSuccess) st = fail_cuda_with(e, "tune: record");
+            if (st == FILARK_OK && (e = cudaEventSynchronize(t1)) != cudaSuccess) st = fail_cuda_with(e, "tune: sync");
             float ms = 0.f;
             if (st == FILARK_OK && (e = cudaEventElapsedTime(&ms, t0, t1)) != cudaSuccess)
-                st = bfail_cuda(e, "tune: elapsed");
+                st = fail_cuda_with(e, "tune: elapsed");
             if (st != FILARK_OK) break;
             const double per = (double)ms / timed_pushes;
             b->tune_cluster[b->n_tuned] = cl;
@@ -411,27 +391,27 @@ filark_status filark_batch_tune(filark_batch *b, const filark_chunk_desc *descs,
     for (cudaEvent_t ev : b->staged) cudaEventSynchronize(ev);
     st = set_launch(b, best_cluster, best_n, 1);
     if (st == FILARK_OK) st = reset(b, s);
-    if (st == FILARK_OK && (e = cudaStreamSynchronize(s)) != cudaSuccess) st = bfail_cuda(e, "tune: sync");
+    if (st == FILARK_OK && (e = cudaStreamSynchronize(s)) != cudaSuccess) st = fail_cuda_with(e, "tune: sync");
     return st;
 }
 
 filark_status filark_batch_reset_state(filark_batch *b, filark_stream_t stream) {
-    if (!b) return bfail(FILARK_EINVAL, "batch is NULL");
+    if (!b) return fail_with(FILARK_EINVAL, "batch is NULL");
     DeviceGuard dg(b->device);
-    if (!dg.ok) return bfail(FILARK_ECUDA, "cudaSetDevice failed");
+    if (!dg.ok) return fail_with(FILARK_ECUDA, "cudaSetDevice failed");
     return reset(b, (cudaStream_t)stream);
 }
 
 filark_status filark_batch_sync_status(filark_batch *b, filark_stream_t stream) {
-    if (!b) return bfail(FILARK_EINVAL, "batch is NULL");
+    if (!b) return fail_with(FILARK_EINVAL, "batch is NULL");
     DeviceGuard dg(b->device);
-    if (!dg.ok) return bfail(FILARK_ECUDA, "cudaSetDevice failed");
+    if (!dg.ok) return fail_with(FILARK_ECUDA, "cudaSetDevice failed");
     cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
     if (e != cudaSuccess) {
         b->sticky = FILARK_ECUDA;
-        return bfail_cuda(e, "batch: synchronize");
+        return fail_cuda_with(e, "batch: synchronize");
     }
-    if (b->sticky != FILARK_OK) return bfail(FILARK_ESTATE, "batch is in an error state; reset it");
+    if (b->sticky != FILARK_OK) return fail_with(FILARK_ESTATE, "batch is in an error state; reset it");
     for (filark_chain *h : b->chains) {
         filark_status st = chain_check_status(h);
         if (st != FILARK_OK) return st;
@@ -440,7 +420,7 @@ filark_status filark_batch_sync_status(filark_batch *b, filark_stream_t stream) 
 }
 
 filark_status filark_batch_get_info(const filark_batch *b, filark_batch_info *out) {
-    if (!b || !out) return bfail(FILARK_EINVAL, "batch or out is NULL");
+    if (!b || !out) return fail_with(FILARK_EINVAL, "batch or out is NULL");
     std::memset(out, 0, sizeof(*out));
     out->n_streams = (int32_t)b->chains.size();
     out->cluster = b->cluster;
@@ -458,8 +438,8 @@ filark_status filark_batch_get_info(const filark_batch *b, filark_batch_info *ou
 }
 
 filark_status filark_batch_stream(filark_batch *b, int i, filark_chain **out) {
-    if (!b || !out) return bfail(FILARK_EINVAL, "batch or out is NULL");
-    if (i < 0 || i >= (int)b->chains.size()) return bfail(FILARK_EINVAL, "stream index out of range");
+    if (!b || !out) return fail_with(FILARK_EINVAL, "batch or out is NULL");
+    if (i < 0 || i >= (int)b->chains.size()) return fail_with(FILARK_EINVAL, "stream index out of range");
     *out = b->chains[(size_t)i];
     return FILARK_OK;
 }

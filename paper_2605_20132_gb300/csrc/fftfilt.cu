@@ -325,28 +325,8 @@ __global__ void __launch_bounds__(kFftMaxThreads) fft_of_taps_kernel(const __gri
     for (int i = threadIdx.x; i < fp.N; i += blockDim.x) H[i] = r[pad(i)];
 }
 
-struct DeviceGuard {
-    int prev = -1;
-    bool ok = false;
-    explicit DeviceGuard(int dev) {
-        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
-        ok = cudaSetDevice(dev) == cudaSuccess;
-    }
-    ~DeviceGuard() {
-        if (prev >= 0) cudaSetDevice(prev);
-    }
-};
 
-filark_status ffail(filark_status st, const std::string &m) {
-    set_last_error(m);
-    return st;
-}
 
-filark_status fcuda(cudaError_t e, const char *what) {
-    cudaGetLastError();
-    set_last_error(std::string(what) + ": " + cudaGetErrorString(e));
-    return FILARK_ECUDA;
-}
 
 // two padded buffers and the twiddle table
 size_t fft_smem(int N) { return sizeof(float2) * (2 * (size_t)(N + (N >> 4)) + (size_t)(N / 2)); }
@@ -367,12 +347,12 @@ extern "C" {
 
 filark_status filark_fftfilt_create(int n_channels, int n_taps, const double *taps, int block_len,
                                     int64_t max_chunk, int cuda_device, filark_fftfilt **out) {
-    if (!out) return ffail(FILARK_EINVAL, "out is NULL");
+    if (!out) return fail_with(FILARK_EINVAL, "out is NULL");
     *out = nullptr;
     if (n_channels < 1 || n_taps < 1 || !taps || max_chunk < 1)
-        return ffail(FILARK_EINVAL, "need n_channels >= 1, n_taps >= 1, taps, max_chunk >= 1");
+        return fail_with(FILARK_EINVAL, "need n_channels >= 1, n_taps >= 1, taps, max_chunk >= 1");
     for (int k = 0; k < n_taps; ++k)
-        if (!std::isfinite(taps[k])) return ffail(FILARK_EINVAL, "non-finite tap");
+        if (!std::isfinite(taps[k])) return fail_with(FILARK_EINVAL, "non-finite tap");
     int L = block_len;
     if (L <= 0) {
         // default: the largest power-of-two block with N = 2 next_pow2(M) or more
@@ -382,9 +362,9 @@ filark_status filark_fftfilt_create(int n_channels, int n_taps, const double *ta
     }
     int logN = 0;
     while ((1 << logN) < L + n_taps - 1) ++logN;
-    if (logN > kFftMaxLog) return ffail(FILARK_ENOSYS, "block_len + n_taps - 1 above the 8192-point FFT");
+    if (logN > kFftMaxLog) return fail_with(FILARK_ENOSYS, "block_len + n_taps - 1 above the 8192-point FFT");
     filark_fftfilt *f = new (std::nothrow) filark_fftfilt();
-    if (!f) return ffail(FILARK_ENOMEM, "host allocation failed");
+    if (!f) return fail_with(FILARK_ENOMEM, "host allocation failed");
     f->device = cuda_device;
     f->C = n_channels;
     f->max_chunk = max_chunk;
@@ -396,7 +376,7 @@ filark_status filark_fftfilt_create(int n_channels, int n_taps, const double *ta
     DeviceGuard dg(cuda_device);
     if (!dg.ok) {
         delete f;
-        return ffail(FILARK_ECUDA, "cudaSetDevice failed");
+        return fail_with(FILARK_ECUDA, "cudaSetDevice failed");
     }
     std::vector<float> hf((size_t)n_taps);
     for (int k = 0; k < n_taps; ++k) hf[(size_t)k] = (float)taps[k];
@@ -447,7 +427,7 @@ filark_status filark_fftfilt_create(int n_channels, int n_taps, const double *ta
         if (f->tail[0]) cudaFree(f->tail[0]);
         if (f->tail[1]) cudaFree(f->tail[1]);
         delete f;
-        return fcuda(e, "fftfilt create");
+        return fail_cuda_with(e, "fftfilt create");
     }
     *out = f;
     return FILARK_OK;
@@ -455,16 +435,16 @@ filark_status filark_fftfilt_create(int n_channels, int n_taps, const double *ta
 
 filark_status filark_fftfilt_push(filark_fftfilt *f, const float *d_in, int64_t ld_in, int64_t n_samples,
                                   float *d_out, int64_t ld_out, filark_stream_t stream) {
-    if (!f) return ffail(FILARK_EINVAL, "filter is NULL");
-    if (n_samples < 0 || n_samples > f->max_chunk) return ffail(FILARK_EINVAL, "n_samples must be in [0, max_chunk]");
+    if (!f) return fail_with(FILARK_EINVAL, "filter is NULL");
+    if (n_samples < 0 || n_samples > f->max_chunk) return fail_with(FILARK_EINVAL, "n_samples must be in [0, max_chunk]");
     if (n_samples == 0) return FILARK_OK;
-    if (!d_in || !d_out || ld_in < f->C || ld_out < f->C) return ffail(FILARK_EINVAL, "buffers NULL or ld < C");
+    if (!d_in || !d_out || ld_in < f->C || ld_out < f->C) return fail_with(FILARK_EINVAL, "buffers NULL or ld < C");
     const size_t in_bytes = sizeof(float) * (size_t)((n_samples - 1) * ld_in + f->C);
     const size_t out_bytes = sizeof(float) * (size_t)((n_samples - 1) * ld_out + f->C);
     const char *pi = (const char *)d_in, *po = (const char *)d_out;
-    if (pi < po + out_bytes && po < pi + in_bytes) return ffail(FILARK_EINVAL, "output overlaps the input");
+    if (pi < po + out_bytes && po < pi + in_bytes) return fail_with(FILARK_EINVAL, "output overlaps the input");
     DeviceGuard dg(f->device);
-    if (!dg.ok) return ffail(FILARK_ECUDA, "cudaSetDevice failed");
+    if (!dg.ok) return fail_with(FILARK_ECUDA, "cudaSetDevice failed");
     cudaStream_t s = (cudaStream_t)stream;
     const unsigned pairs = (unsigned)((f->C + 1) / 2);
     for (int64_t t = 0; t < n_samples; t += f->fp.L) {
@@ -475,21 +455,21 @@ filark_status filark_fftfilt_push(filark_fftfilt *f, const float *d_in, int64_t 
         f->cur = 1 - f->cur;
     }
     const cudaError_t e = cudaGetLastError();
-    return e == cudaSuccess ? FILARK_OK : fcuda(e, "fftfilt push");
+    return e == cudaSuccess ? FILARK_OK : fail_cuda_with(e, "fftfilt push");
 }
 
 filark_status filark_fftfilt_reset(filark_fftfilt *f, filark_stream_t stream) {
-    if (!f) return ffail(FILARK_EINVAL, "filter is NULL");
+    if (!f) return fail_with(FILARK_EINVAL, "filter is NULL");
     DeviceGuard dg(f->device);
-    if (!dg.ok) return ffail(FILARK_ECUDA, "cudaSetDevice failed");
+    if (!dg.ok) return fail_with(FILARK_ECUDA, "cudaSetDevice failed");
     if (!f->tail[0]) return FILARK_OK;
     const cudaError_t e = cudaMemsetAsync(f->tail[f->cur], 0, sizeof(float) * (size_t)f->C * (f->fp.M - 1),
                                           (cudaStream_t)stream);
-    return e == cudaSuccess ? FILARK_OK : fcuda(e, "fftfilt reset");
+    return e == cudaSuccess ? FILARK_OK : fail_cuda_with(e, "fftfilt reset");
 }
 
 filark_status filark_fftfilt_get_info(const filark_fftfilt *f, int *fft_len, int *block_len) {
-    if (!f) return ffail(FILARK_EINVAL, "filter is NULL");
+    if (!f) return fail_with(FILARK_EINVAL, "filter is NULL");
     if (fft_len) *fft_len = f->fp.N;
     if (block_len) *block_len = f->fp.L;
     return FILARK_OK;

@@ -134,6 +134,35 @@ struct Plan {
 // Message returned by filark_last_error_string on this thread.
 void set_last_error(const std::string &msg);
 
+// Records msg as this thread's last error and returns st.
+inline filark_status fail_with(filark_status st, const std::string &msg) {
+    set_last_error(msg);
+    return st;
+}
+
+// Clears the CUDA error state, records "what: <CUDA message>" and returns
+// FILARK_ECUDA.
+inline filark_status fail_cuda_with(cudaError_t e, const char *what) {
+    cudaGetLastError();
+    set_last_error(std::string(what) + ": " + cudaGetErrorString(e));
+    return FILARK_ECUDA;
+}
+
+// Makes `dev` the current device and restores the caller's on scope exit.
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = false;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        ok = cudaSetDevice(dev) == cudaSuccess;
+    }
+    ~DeviceGuard() {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+    DeviceGuard(const DeviceGuard &) = delete;
+    DeviceGuard &operator=(const DeviceGuard &) = delete;
+};
+
 // Validate and normalise the SOS (a0 != 0, finite, stable), and build the
 // plan.  Returns FILARK_OK or an error with a message in *err.
 filark_status make_plan(const double *sos, int S, int precision, Plan *plan, std::string *err);

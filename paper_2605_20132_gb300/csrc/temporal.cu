@@ -304,28 +304,8 @@ __global__ void __launch_bounds__(kEmaThreads) ema_kernel(const __grid_constant_
 
 // ------------------------------------------------------------------ host --
 
-struct DeviceGuard {
-    int prev = -1;
-    bool ok = false;
-    explicit DeviceGuard(int dev) {
-        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
-        ok = cudaSetDevice(dev) == cudaSuccess;
-    }
-    ~DeviceGuard() {
-        if (prev >= 0) cudaSetDevice(prev);
-    }
-};
 
-filark_status tfail(filark_status st, const std::string &m) {
-    set_last_error(m);
-    return st;
-}
 
-filark_status tcuda(cudaError_t e, const char *what) {
-    cudaGetLastError();
-    set_last_error(std::string(what) + ": " + cudaGetErrorString(e));
-    return FILARK_ECUDA;
-}
 
 size_t fir_smem(int Mpad) { return sizeof(float) * (size_t)(Mpad + kFirRows) * kTopCh; }
 
@@ -359,7 +339,7 @@ filark_status zero_top(filark_top *t, cudaStream_t s) {
     for (float *p : t->hist)
         if (p && e == cudaSuccess) e = cudaMemsetAsync(p, 0, sizeof(float) * (size_t)(t->M - 1) * t->C, s);
     if (t->carry && e == cudaSuccess) e = cudaMemsetAsync(t->carry, 0, sizeof(float2) * (size_t)t->C, s);
-    if (e != cudaSuccess) return tcuda(e, "temporal operator: reset");
+    if (e != cudaSuccess) return fail_cuda_with(e, "temporal operator: reset");
     t->n = 0;
     t->parity = 0;
     return FILARK_OK;
@@ -371,13 +351,13 @@ extern "C" {
 
 filark_status filark_top_create(int kind, int n_channels, int length, const double *taps, double alpha,
                                 int64_t max_chunk, int cuda_device, filark_top **out) {
-    if (!out) return tfail(FILARK_EINVAL, "out is NULL");
+    if (!out) return fail_with(FILARK_EINVAL, "out is NULL");
     *out = nullptr;
-    if (kind < FILARK_TOP_FIR || kind > FILARK_TOP_EMA) return tfail(FILARK_EINVAL, "unknown operator kind");
-    if (n_channels < 1) return tfail(FILARK_EINVAL, "n_channels must be >= 1");
-    if (max_chunk < 1 || max_chunk > (int64_t)1 << 30) return tfail(FILARK_EINVAL, "max_chunk out of range");
+    if (kind < FILARK_TOP_FIR || kind > FILARK_TOP_EMA) return fail_with(FILARK_EINVAL, "unknown operator kind");
+    if (n_channels < 1) return fail_with(FILARK_EINVAL, "n_channels must be >= 1");
+    if (max_chunk < 1 || max_chunk > (int64_t)1 << 30) return fail_with(FILARK_EINVAL, "max_chunk out of range");
     filark_top *t = new (std::nothrow) filark_top();
-    if (!t) return tfail(FILARK_ENOMEM, "host allocation failed");
+    if (!t) return fail_with(FILARK_ENOMEM, "host allocation failed");
     t->kind = kind;
     t->device = cuda_device;
     t->C = n_channels;
@@ -385,12 +365,12 @@ filark_status filark_top_create(int kind, int n_channels, int length, const doub
     if (kind == FILARK_TOP_FIR) {
         if (length < 1 || length > kFirMaxTaps || !taps) {
             delete t;
-            return tfail(FILARK_EINVAL, "FIR needs 1 <= taps <= 512 and a taps array");
+            return fail_with(FILARK_EINVAL, "FIR needs 1 <= taps <= 512 and a taps array");
         }
         for (int k = 0; k < length; ++k)
             if (!std::isfinite(taps[k])) {
                 delete t;
-                return tfail(FILARK_EINVAL, "non-finite tap");
+                return fail_with(FILARK_EINVAL, "non-finite tap");
             }
         t->M = length;
         t->fir.M = length;
@@ -399,18 +379,18 @@ filark_status filark_top_create(int kind, int n_channels, int length, const doub
     } else if (kind == FILARK_TOP_MEAN || kind == FILARK_TOP_AGC) {
         if (length < 1 || length > (1 << 24)) {
             delete t;
-            return tfail(FILARK_EINVAL, "window length must be in [1, 2^24]");
+            return fail_with(FILARK_EINVAL, "window length must be in [1, 2^24]");
         }
         t->M = length;
         t->Q = (long long)length + max_chunk;
         if ((double)t->Q * n_channels > 2.0e9) {
             delete t;
-            return tfail(FILARK_ENOSYS, "window ring above 2^31 entries");
+            return fail_with(FILARK_ENOSYS, "window ring above 2^31 entries");
         }
     } else {
         if (!(alpha > 0.0) || !(alpha <= 1.0)) {
             delete t;
-            return tfail(FILARK_EINVAL, "EMA coefficient must be in (0, 1]");
+            return fail_with(FILARK_EINVAL, "EMA coefficient must be in (0, 1]");
         }
         t->M = 1;
         const double ac = 1.0 - alpha;
@@ -426,7 +406,7 @@ filark_status filark_top_create(int kind, int n_channels, int length, const doub
     DeviceGuard dg(cuda_device);
     if (!dg.ok) {
         delete t;
-        return tfail(FILARK_ECUDA, "cudaSetDevice failed");
+        return fail_with(FILARK_ECUDA, "cudaSetDevice failed");
     }
     cudaError_t e = cudaSuccess;
     if (kind == FILARK_TOP_FIR) {
@@ -441,10 +421,10 @@ filark_status filark_top_create(int kind, int n_channels, int length, const doub
     }
     if (e != cudaSuccess) {
         free_top(t);
-        return tcuda(e, "temporal operator create");
+        return fail_cuda_with(e, "temporal operator create");
     }
     filark_status st = zero_top(t, nullptr);
-    if (st == FILARK_OK && (e = cudaStreamSynchronize(nullptr)) != cudaSuccess) st = tcuda(e, "create: sync");
+    if (st == FILARK_OK && (e = cudaStreamSynchronize(nullptr)) != cudaSuccess) st = fail_cuda_with(e, "create: sync");
     if (st != FILARK_OK) {
         free_top(t);
         return st;
@@ -455,16 +435,16 @@ filark_status filark_top_create(int kind, int n_channels, int length, const doub
 
 filark_status filark_top_push(filark_top *t, const float *d_in, int64_t ld_in, int64_t n_samples, float *d_out,
                               int64_t ld_out, filark_stream_t stream) {
-    if (!t) return tfail(FILARK_EINVAL, "operator is NULL");
-    if (n_samples < 0 || n_samples > t->max_chunk) return tfail(FILARK_EINVAL, "n_samples must be in [0, max_chunk]");
+    if (!t) return fail_with(FILARK_EINVAL, "operator is NULL");
+    if (n_samples < 0 || n_samples > t->max_chunk) return fail_with(FILARK_EINVAL, "n_samples must be in [0, max_chunk]");
     if (n_samples == 0) return FILARK_OK;
-    if (!d_in || !d_out || ld_in < t->C || ld_out < t->C) return tfail(FILARK_EINVAL, "buffers NULL or ld < C");
+    if (!d_in || !d_out || ld_in < t->C || ld_out < t->C) return fail_with(FILARK_EINVAL, "buffers NULL or ld < C");
     const size_t in_bytes = sizeof(float) * (size_t)((n_samples - 1) * ld_in + t->C);
     const size_t out_bytes = sizeof(float) * (size_t)((n_samples - 1) * ld_out + t->C);
     const char *pi = (const char *)d_in, *po = (const char *)d_out;
-    if (pi < po + out_bytes && po < pi + in_bytes) return tfail(FILARK_EINVAL, "output overlaps the input");
+    if (pi < po + out_bytes && po < pi + in_bytes) return fail_with(FILARK_EINVAL, "output overlaps the input");
     DeviceGuard dg(t->device);
-    if (!dg.ok) return tfail(FILARK_ECUDA, "cudaSetDevice failed");
+    if (!dg.ok) return fail_with(FILARK_ECUDA, "cudaSetDevice failed");
     cudaStream_t s = (cudaStream_t)stream;
     const int T = (int)n_samples, C = t->C;
     const unsigned gch = (unsigned)((C + kTopCh - 1) / kTopCh);
@@ -494,15 +474,15 @@ filark_status filark_top_push(filark_top *t, const float *d_in, int64_t ld_in, i
         ema_kernel<<<(unsigned)((C + kEmaCh - 1) / kEmaCh), kEmaThreads, 0, s>>>(ep, d_in, ld_in, T, C, t->carry, d_out, ld_out);
     }
     const cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return tcuda(e, "temporal operator push");
+    if (e != cudaSuccess) return fail_cuda_with(e, "temporal operator push");
     t->n += n_samples;
     return FILARK_OK;
 }
 
 filark_status filark_top_reset(filark_top *t, filark_stream_t stream) {
-    if (!t) return tfail(FILARK_EINVAL, "operator is NULL");
+    if (!t) return fail_with(FILARK_EINVAL, "operator is NULL");
     DeviceGuard dg(t->device);
-    if (!dg.ok) return tfail(FILARK_ECUDA, "cudaSetDevice failed");
+    if (!dg.ok) return fail_with(FILARK_ECUDA, "cudaSetDevice failed");
     return zero_top(t, (cudaStream_t)stream);
 }
 

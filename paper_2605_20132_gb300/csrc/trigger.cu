@@ -376,28 +376,8 @@ float float_ceil(double v) {
     return f;
 }
 
-struct DeviceGuard {
-    int prev = -1;
-    bool ok = false;
-    explicit DeviceGuard(int dev) {
-        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
-        ok = cudaSetDevice(dev) == cudaSuccess;
-    }
-    ~DeviceGuard() {
-        if (prev >= 0) cudaSetDevice(prev);
-    }
-};
 
-filark_status tfail(filark_status st, const std::string &m) {
-    set_last_error(m);
-    return st;
-}
 
-filark_status tcuda(cudaError_t e, const char *what) {
-    cudaGetLastError();
-    set_last_error(std::string(what) + ": " + cudaGetErrorString(e));
-    return FILARK_ECUDA;
-}
 
 }  // namespace
 
@@ -430,15 +410,15 @@ extern "C" {
 
 filark_status filark_trigger_create(int n_channels, double on, double off, int64_t max_chunk, int cuda_device,
                                     filark_trigger **out) {
-    if (!out) return tfail(FILARK_EINVAL, "out is NULL");
+    if (!out) return fail_with(FILARK_EINVAL, "out is NULL");
     *out = nullptr;
-    if (n_channels < 1) return tfail(FILARK_EINVAL, "n_channels must be >= 1");
+    if (n_channels < 1) return fail_with(FILARK_EINVAL, "n_channels must be >= 1");
     if (!std::isfinite(on) || !std::isfinite(off) || off > on)
-        return tfail(FILARK_EINVAL, "thresholds must be finite with off <= on");
-    if (std::fabs(on) > 3.0e38 || std::fabs(off) > 3.0e38) return tfail(FILARK_EINVAL, "thresholds out of float range");
-    if (max_chunk < 1 || max_chunk > (int64_t)kSeg * 65535) return tfail(FILARK_EINVAL, "max_chunk out of range");
+        return fail_with(FILARK_EINVAL, "thresholds must be finite with off <= on");
+    if (std::fabs(on) > 3.0e38 || std::fabs(off) > 3.0e38) return fail_with(FILARK_EINVAL, "thresholds out of float range");
+    if (max_chunk < 1 || max_chunk > (int64_t)kSeg * 65535) return fail_with(FILARK_EINVAL, "max_chunk out of range");
     filark_trigger *t = new (std::nothrow) filark_trigger();
-    if (!t) return tfail(FILARK_ENOMEM, "host allocation failed");
+    if (!t) return fail_with(FILARK_ENOMEM, "host allocation failed");
     t->device = cuda_device;
     t->C = n_channels;
     t->on = on;
@@ -450,7 +430,7 @@ filark_status filark_trigger_create(int n_channels, double on, double off, int64
     DeviceGuard dg(cuda_device);
     if (!dg.ok) {
         delete t;
-        return tfail(FILARK_ECUDA, "cudaSetDevice failed");
+        return fail_with(FILARK_ECUDA, "cudaSetDevice failed");
     }
     const size_t C = (size_t)n_channels, G = (size_t)t->nseg_max;
     cudaError_t e = cudaMalloc(&t->st_s, sizeof(int) * C);
@@ -463,7 +443,7 @@ filark_status filark_trigger_create(int n_channels, double on, double off, int64
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     if (e != cudaSuccess) {
         free_trigger(t);
-        return tcuda(e, "trigger create");
+        return fail_cuda_with(e, "trigger create");
     }
     *out = t;
     return FILARK_OK;
@@ -472,14 +452,14 @@ filark_status filark_trigger_create(int n_channels, double on, double off, int64
 filark_status filark_trigger_push(filark_trigger *t, const float *d_ratio, int64_t ld, int64_t n_samples,
                                   filark_trigger_record *d_records, int64_t capacity, unsigned long long *d_count,
                                   filark_stream_t stream) {
-    if (!t) return tfail(FILARK_EINVAL, "trigger is NULL");
-    if (n_samples < 0 || n_samples > t->max_chunk) return tfail(FILARK_EINVAL, "n_samples must be in [0, max_chunk]");
+    if (!t) return fail_with(FILARK_EINVAL, "trigger is NULL");
+    if (n_samples < 0 || n_samples > t->max_chunk) return fail_with(FILARK_EINVAL, "n_samples must be in [0, max_chunk]");
     if (n_samples == 0) return FILARK_OK;
-    if (!d_ratio || ld < t->C) return tfail(FILARK_EINVAL, "ratio is NULL or ld < n_channels");
+    if (!d_ratio || ld < t->C) return fail_with(FILARK_EINVAL, "ratio is NULL or ld < n_channels");
     if (!d_count || capacity < 0 || (capacity > 0 && !d_records))
-        return tfail(FILARK_EINVAL, "records/capacity/count arguments");
+        return fail_with(FILARK_EINVAL, "records/capacity/count arguments");
     DeviceGuard dg(t->device);
-    if (!dg.ok) return tfail(FILARK_ECUDA, "cudaSetDevice failed");
+    if (!dg.ok) return fail_with(FILARK_ECUDA, "cudaSetDevice failed");
     cudaStream_t s = (cudaStream_t)stream;
     const int T = (int)n_samples;
     const int nseg = (T + kSeg - 1) / kSeg;
@@ -491,32 +471,32 @@ filark_status filark_trigger_push(filark_trigger *t, const float *d_ratio, int64
     trig_emit_kernel<<<grid2, kTrigThreads, 0, s>>>(d_ratio, ld, t->C, T, t->on_f, t->off_f, t->n, t->summ,
                                                     t->seg_s, t->seg_t, d_records, capacity, d_count);
     const cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return tcuda(e, "trigger push");
+    if (e != cudaSuccess) return fail_cuda_with(e, "trigger push");
     t->n += n_samples;
     return FILARK_OK;
 }
 
 filark_status filark_trigger_flush(filark_trigger *t, filark_trigger_record *d_records, int64_t capacity,
                                    unsigned long long *d_count, filark_stream_t stream) {
-    if (!t) return tfail(FILARK_EINVAL, "trigger is NULL");
+    if (!t) return fail_with(FILARK_EINVAL, "trigger is NULL");
     if (!d_count || capacity < 0 || (capacity > 0 && !d_records))
-        return tfail(FILARK_EINVAL, "records/capacity/count arguments");
+        return fail_with(FILARK_EINVAL, "records/capacity/count arguments");
     DeviceGuard dg(t->device);
-    if (!dg.ok) return tfail(FILARK_ECUDA, "cudaSetDevice failed");
+    if (!dg.ok) return fail_with(FILARK_ECUDA, "cudaSetDevice failed");
     trig_flush_kernel<<<(unsigned)((t->C + kTrigThreads - 1) / kTrigThreads), kTrigThreads, 0,
                         (cudaStream_t)stream>>>(t->st_s, t->st_t, t->C, t->n, d_records, capacity, d_count);
     const cudaError_t e = cudaGetLastError();
-    return e == cudaSuccess ? FILARK_OK : tcuda(e, "trigger flush");
+    return e == cudaSuccess ? FILARK_OK : fail_cuda_with(e, "trigger flush");
 }
 
 filark_status filark_trigger_reset(filark_trigger *t, filark_stream_t stream) {
-    if (!t) return tfail(FILARK_EINVAL, "trigger is NULL");
+    if (!t) return fail_with(FILARK_EINVAL, "trigger is NULL");
     DeviceGuard dg(t->device);
-    if (!dg.ok) return tfail(FILARK_ECUDA, "cudaSetDevice failed");
+    if (!dg.ok) return fail_with(FILARK_ECUDA, "cudaSetDevice failed");
     cudaStream_t s = (cudaStream_t)stream;
     cudaError_t e = cudaMemsetAsync(t->st_s, 0, sizeof(int) * (size_t)t->C, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(t->st_t, 0, sizeof(long long) * (size_t)t->C, s);
-    if (e != cudaSuccess) return tcuda(e, "trigger reset");
+    if (e != cudaSuccess) return fail_cuda_with(e, "trigger reset");
     t->n = 0;
     return FILARK_OK;
 }
@@ -537,27 +517,27 @@ size_t filark_events_work_bytes(int64_t n_triggers, int n_channels) {
 filark_status filark_events_merge(const filark_trigger_record *d_triggers, int64_t n_triggers, int n_channels,
                                   filark_event *d_events, int64_t capacity, unsigned long long *d_n_events,
                                   void *d_work, size_t work_bytes, filark_stream_t stream) {
-    if (n_triggers < 0 || n_channels < 1) return tfail(FILARK_EINVAL, "n_triggers < 0 or n_channels < 1");
+    if (n_triggers < 0 || n_channels < 1) return fail_with(FILARK_EINVAL, "n_triggers < 0 or n_channels < 1");
     if (!d_n_events || capacity < 0 || (capacity > 0 && !d_events))
-        return tfail(FILARK_EINVAL, "events/capacity/count arguments");
+        return fail_with(FILARK_EINVAL, "events/capacity/count arguments");
     if (n_triggers == 0) return FILARK_OK;
     if (!d_triggers || !d_work || work_bytes < filark_events_work_bytes(n_triggers, n_channels) ||
         ((uintptr_t)d_work & 255))
-        return tfail(FILARK_EINVAL, "triggers NULL, or work buffer too small / not 256-byte aligned");
+        return fail_with(FILARK_EINVAL, "triggers NULL, or work buffer too small / not 256-byte aligned");
     cudaStream_t s = (cudaStream_t)stream;
     MergeWork w;
     merge_layout(n_triggers, n_channels, &w, (char *)d_work);
     int *bad = w.bad;
     cudaError_t e = cudaMemsetAsync(w.bucket, 0, sizeof(long long) * ((size_t)n_channels + 1), s);
     if (e == cudaSuccess) e = cudaMemsetAsync(bad, 0, sizeof(int), s);
-    if (e != cudaSuccess) return tcuda(e, "events merge: clear");
+    if (e != cudaSuccess) return fail_cuda_with(e, "events merge: clear");
     const unsigned gn = (unsigned)((n_triggers + 255) / 256);
     merge_count_kernel<<<gn, 256, 0, s>>>(d_triggers, n_triggers, n_channels, w.bucket, bad);
     int bad_h = 0;
     e = cudaMemcpyAsync(&bad_h, bad, sizeof(int), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    if (e != cudaSuccess) return tcuda(e, "events merge: check");
-    if (bad_h) return tfail(FILARK_EINVAL, "a trigger's channel is outside [0, n_channels)");
+    if (e != cudaSuccess) return fail_cuda_with(e, "events merge: check");
+    if (bad_h) return fail_with(FILARK_EINVAL, "a trigger's channel is outside [0, n_channels)");
     merge_scan_kernel<<<1, 1024, 0, s>>>(w.bucket, w.cursor, n_channels);
     merge_scatter_kernel<<<gn, 256, 0, s>>>(d_triggers, n_triggers, w);
     merge_sort_kernel<<<(unsigned)((n_channels + 127) / 128), 128, 0, s>>>(w, n_channels);
@@ -566,8 +546,8 @@ filark_status filark_events_merge(const filark_trigger_record *d_triggers, int64
     merge_emit_kernel<<<gn, 256, 0, s>>>(w, n_triggers, d_events, capacity, d_n_events);
     e = cudaMemcpyAsync(&bad_h, bad, sizeof(int), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    if (e != cudaSuccess) return tcuda(e, "events merge");
-    if (bad_h) return tfail(FILARK_ETIMEOUT, "events merge: union-find gave up");
+    if (e != cudaSuccess) return fail_cuda_with(e, "events merge");
+    if (bad_h) return fail_with(FILARK_ETIMEOUT, "events merge: union-find gave up");
     return FILARK_OK;
 }
 

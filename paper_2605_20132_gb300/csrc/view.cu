@@ -133,28 +133,8 @@ __global__ void view_image_kernel(const float *__restrict__ ring, int H, int W, 
     img[(long long)r * ldi + c] = j >= 0 ? ring[(long long)r * W + j % W] : 0.f;
 }
 
-struct DeviceGuard {
-    int prev = -1;
-    bool ok = false;
-    explicit DeviceGuard(int dev) {
-        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
-        ok = cudaSetDevice(dev) == cudaSuccess;
-    }
-    ~DeviceGuard() {
-        if (prev >= 0) cudaSetDevice(prev);
-    }
-};
 
-filark_status vfail(filark_status st, const std::string &m) {
-    set_last_error(m);
-    return st;
-}
 
-filark_status vcuda(cudaError_t e, const char *what) {
-    cudaGetLastError();
-    set_last_error(std::string(what) + ": " + cudaGetErrorString(e));
-    return FILARK_ECUDA;
-}
 
 unsigned blocks_for(long long n) { return (unsigned)((n + 255) / 256); }
 
@@ -187,14 +167,14 @@ extern "C" {
 filark_status filark_view_create(int n_channels, int channels_per_row, int samples_per_column, int width, int mode,
                                  int n_sections, const double *sos, int64_t max_chunk, int cuda_device,
                                  filark_view **out) {
-    if (!out) return vfail(FILARK_EINVAL, "out is NULL");
+    if (!out) return fail_with(FILARK_EINVAL, "out is NULL");
     *out = nullptr;
     if (n_channels < 1 || channels_per_row < 1 || samples_per_column < 1 || width < 1 || max_chunk < 1)
-        return vfail(FILARK_EINVAL, "sizes must be >= 1");
-    if (mode < FILARK_VIEW_DROP || mode > FILARK_VIEW_LINEAR) return vfail(FILARK_EINVAL, "unknown view mode");
-    if (n_sections < 0 || (n_sections > 0 && !sos)) return vfail(FILARK_EINVAL, "display filter sections");
+        return fail_with(FILARK_EINVAL, "sizes must be >= 1");
+    if (mode < FILARK_VIEW_DROP || mode > FILARK_VIEW_LINEAR) return fail_with(FILARK_EINVAL, "unknown view mode");
+    if (n_sections < 0 || (n_sections > 0 && !sos)) return fail_with(FILARK_EINVAL, "display filter sections");
     filark_view *v = new (std::nothrow) filark_view();
-    if (!v) return vfail(FILARK_ENOMEM, "host allocation failed");
+    if (!v) return fail_with(FILARK_ENOMEM, "host allocation failed");
     v->device = cuda_device;
     v->C = n_channels;
     v->kc = channels_per_row;
@@ -218,13 +198,13 @@ filark_status filark_view_create(int n_channels, int channels_per_row, int sampl
         if (st != FILARK_OK) {
             const std::string msg = std::string("display filter: ") + filark_last_error_string();
             delete v;
-            return vfail(st, msg);
+            return fail_with(st, msg);
         }
     }
     DeviceGuard dg(cuda_device);
     if (!dg.ok) {
         free_view(v);
-        return vfail(FILARK_ECUDA, "cudaSetDevice failed");
+        return fail_with(FILARK_ECUDA, "cudaSetDevice failed");
     }
     const size_t H = (size_t)v->H;
     cudaError_t e = cudaMalloc(&v->rows, sizeof(float) * (size_t)max_chunk * H);
@@ -235,7 +215,7 @@ filark_status filark_view_create(int n_channels, int channels_per_row, int sampl
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     if (e != cudaSuccess) {
         free_view(v);
-        return vcuda(e, "view create");
+        return fail_cuda_with(e, "view create");
     }
     *out = v;
     return FILARK_OK;
@@ -243,12 +223,12 @@ filark_status filark_view_create(int n_channels, int channels_per_row, int sampl
 
 filark_status filark_view_push(filark_view *v, const float *d_in, int64_t ld_in, int64_t n_samples,
                                filark_stream_t stream) {
-    if (!v) return vfail(FILARK_EINVAL, "view is NULL");
-    if (n_samples < 0 || n_samples > v->max_chunk) return vfail(FILARK_EINVAL, "n_samples must be in [0, max_chunk]");
+    if (!v) return fail_with(FILARK_EINVAL, "view is NULL");
+    if (n_samples < 0 || n_samples > v->max_chunk) return fail_with(FILARK_EINVAL, "n_samples must be in [0, max_chunk]");
     if (n_samples == 0) return FILARK_OK;
-    if (!d_in || ld_in < v->C) return vfail(FILARK_EINVAL, "input NULL or ld < n_channels");
+    if (!d_in || ld_in < v->C) return fail_with(FILARK_EINVAL, "input NULL or ld < n_channels");
     DeviceGuard dg(v->device);
-    if (!dg.ok) return vfail(FILARK_ECUDA, "cudaSetDevice failed");
+    if (!dg.ok) return fail_with(FILARK_ECUDA, "cudaSetDevice failed");
     cudaStream_t s = (cudaStream_t)stream;
     const int T = (int)n_samples, H = v->H;
     view_rows_kernel<<<blocks_for((long long)T * H), 256, 0, s>>>(d_in, ld_in, T, v->C, v->kc, H, v->mode, v->rows);
@@ -271,7 +251,7 @@ filark_status filark_view_push(filark_view *v, const float *d_in, int64_t ld_in,
                                                                            nq * v->kt, nrest,
                                                                            v->carry[v->parity ^ 1]);
     const cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return vcuda(e, "view push");
+    if (e != cudaSuccess) return fail_cuda_with(e, "view push");
     v->parity ^= 1;
     v->carry_n = nrest;
     v->ncols += nq;
@@ -280,19 +260,19 @@ filark_status filark_view_push(filark_view *v, const float *d_in, int64_t ld_in,
 }
 
 filark_status filark_view_image(const filark_view *v, float *d_image, int64_t ld_image, filark_stream_t stream) {
-    if (!v) return vfail(FILARK_EINVAL, "view is NULL");
-    if (!d_image || ld_image < v->W) return vfail(FILARK_EINVAL, "image NULL or ld < width");
+    if (!v) return fail_with(FILARK_EINVAL, "view is NULL");
+    if (!d_image || ld_image < v->W) return fail_with(FILARK_EINVAL, "image NULL or ld < width");
     DeviceGuard dg(v->device);
-    if (!dg.ok) return vfail(FILARK_ECUDA, "cudaSetDevice failed");
+    if (!dg.ok) return fail_with(FILARK_ECUDA, "cudaSetDevice failed");
     view_image_kernel<<<blocks_for((long long)v->H * v->W), 256, 0, (cudaStream_t)stream>>>(v->ring, v->H, v->W,
                                                                                             v->ncols, d_image,
                                                                                             ld_image);
     const cudaError_t e = cudaGetLastError();
-    return e == cudaSuccess ? FILARK_OK : vcuda(e, "view image");
+    return e == cudaSuccess ? FILARK_OK : fail_cuda_with(e, "view image");
 }
 
 filark_status filark_view_get_info(const filark_view *v, int *rows, int64_t *columns, int *ring_offset) {
-    if (!v) return vfail(FILARK_EINVAL, "view is NULL");
+    if (!v) return fail_with(FILARK_EINVAL, "view is NULL");
     if (rows) *rows = v->H;
     if (columns) *columns = v->ncols;
     if (ring_offset) *ring_offset = (int)(v->ncols % v->W);
@@ -300,15 +280,15 @@ filark_status filark_view_get_info(const filark_view *v, int *rows, int64_t *col
 }
 
 filark_status filark_view_reset(filark_view *v, filark_stream_t stream) {
-    if (!v) return vfail(FILARK_EINVAL, "view is NULL");
+    if (!v) return fail_with(FILARK_EINVAL, "view is NULL");
     DeviceGuard dg(v->device);
-    if (!dg.ok) return vfail(FILARK_ECUDA, "cudaSetDevice failed");
+    if (!dg.ok) return fail_with(FILARK_ECUDA, "cudaSetDevice failed");
     if (v->filt) {
         filark_status st = filark_chain_reset_state(v->filt, stream);
         if (st != FILARK_OK) return st;
     }
     const cudaError_t e = cudaMemsetAsync(v->ring, 0, sizeof(float) * (size_t)v->W * v->H, (cudaStream_t)stream);
-    if (e != cudaSuccess) return vcuda(e, "view reset");
+    if (e != cudaSuccess) return fail_cuda_with(e, "view reset");
     v->n = v->ncols = 0;
     v->carry_n = 0;
     return FILARK_OK;
