@@ -6,25 +6,29 @@
 //
 // Each push is cut into blocks of at most L samples per channel.  A block b
 // of len samples gives z = x_b * h (length len + M - 1) through an FFT of size
-// N >= L + M - 1: Z = FFT(x_b) . H, z = IFFT(Z).  The outputs of the block are
-// z[0, len) + tail[0, len); the tail becomes tail[len, ...) + z[len, ...).
-// Two channels share one complex transform (x1 + i x2; h is real, so the
-// real and imaginary parts of the result are the two convolutions).
+// N >= len + M - 1: Z = FFT(x_b) . H_N, z = IFFT(Z).  The outputs of the block
+// are z[0, len) + tail[0, len); the tail becomes tail[len, ...) + z[len, ...).
+// Two channels share one complex transform (x1 + i x2; h is real, so the real
+// and imaginary parts of the result are the two convolutions).  N is the
+// smallest size 2^k or 3 * 2^k that holds the block's convolution (a
+// 1,500-sample push with 4,001 taps: 6144 rather than 8192), and H_N, the
+// spectrum of the taps, is kept for every such size up to the largest.
 //
-// FFT: Stockham autosort in shared memory, one CTA per channel pair and
-// block.  The log2(N) radix-2 steps are grouped into passes of radix 8 (one
-// radix 2 or radix 4 pass first when log2(N) is not a multiple of 3); each
-// thread does whole radix-R butterflies in registers.  The first forward pass
-// reads the input block straight from global memory, the last forward pass
-// multiplies by H, and the last inverse pass writes the outputs and the new
-// tail straight to global memory.  The tail is double-buffered (read from one
-// buffer, written to the other), so the epilogue needs no barrier.  Twiddles
-// come from a host table made in double precision, one run of m values per
-// pass (w_j = exp(-2 pi i j / (R m)), j < m, contiguous in j so that a warp
-// reads consecutive entries), staged in shared memory; a butterfly's powers
-// w^2 .. w^7 are products of at most three table values' roundings.  Shared arrays are padded by one element per 16 (element i at
-// i + i/16), which spreads the strided stores of the early passes over the
-// banks.  N <= 8192 (2 x 68 KB of complex floats plus 32 KB of twiddles).
+// FFT: mixed-radix Stockham autosort in shared memory, one CTA per channel
+// pair and block.  Passes: radix 3 first when 3 divides N, then one radix-2
+// or radix-4 pass when log2 of the power-of-two part is not a multiple of 3,
+// then radix 8; each thread does whole radix-R butterflies in registers.  The
+// first forward pass reads the input block straight from global memory, the
+// last forward pass multiplies by H_N, and the last inverse pass writes the
+// outputs and the new tail straight to global memory.  The tail is
+// double-buffered (read from one buffer, written to the other), so the
+// epilogue needs no barrier.  Twiddles come from a host table made in double
+// precision, one run of m values per pass (w_j = exp(-2 pi i j / (R m)),
+// j < m, contiguous in j), staged in shared memory; a butterfly's powers
+// w^2 .. w^7 are products of at most three table values' roundings.  Shared
+// arrays are padded by one element per 16 (element i at i + i/16), which
+// spreads the strided stores of the early passes over the banks.
+// N <= 8192; up to 6144 two CTAs of N / 16 threads share an SM.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -39,10 +43,13 @@ using namespace filark;
 namespace {
 
 constexpr int kFftMaxThreads = 1024;
-constexpr int kFftMaxLog = 13;     // N <= 8192
+constexpr int kFftMaxN = 8192;
+constexpr int kMaxPass = 6;
+constexpr size_t kTwoCtaSmem = 110 * 1024;   // at most this much shared memory: two CTAs per SM
 
 // padded shared-memory position of element i
 __device__ __forceinline__ int pad(int i) { return i + (i >> 4); }
+int pad_h(int i) { return i + (i >> 4); }
 
 __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
     return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
@@ -71,6 +78,15 @@ __device__ __forceinline__ void dft(float2 (&x)[R]) {
         const float2 u = x[0];
         x[0] = cadd(u, x[1]);
         x[1] = csub(u, x[1]);
+    } else if constexpr (R == 3) {
+        // y0 = x0 + (x1 + x2), y1,2 = x0 - (x1 + x2)/2 +- d i (sqrt(3)/2)(x1 - x2)
+        const float h = 0.86602540378443865f;
+        const float2 s = cadd(x[1], x[2]);
+        const float2 t = make_float2(x[0].x - 0.5f * s.x, x[0].y - 0.5f * s.y);
+        const float2 u = rot<INV>(csub(x[1], x[2]));
+        x[0] = cadd(x[0], s);
+        x[1] = make_float2(t.x + h * u.x, t.y + h * u.y);
+        x[2] = make_float2(t.x - h * u.x, t.y - h * u.y);
     } else if constexpr (R == 4) {
         dft4<INV>(x[0], x[1], x[2], x[3]);
     } else {
@@ -94,9 +110,39 @@ __device__ __forceinline__ void dft(float2 (&x)[R]) {
     }
 }
 
+// x_r *= w^r (w conjugated for the inverse)
+template <int R, bool INV>
+__device__ __forceinline__ void twiddle(float2 (&x)[R], float2 w) {
+    if (INV) w.y = -w.y;
+    if constexpr (R == 2) {
+        x[1] = cmul(x[1], w);
+    } else if constexpr (R == 3) {
+        x[1] = cmul(x[1], w);
+        x[2] = cmul(x[2], cmul(w, w));
+    } else if constexpr (R == 4) {
+        const float2 w2 = cmul(w, w);
+        x[1] = cmul(x[1], w);
+        x[2] = cmul(x[2], w2);
+        x[3] = cmul(x[3], cmul(w2, w));
+    } else {
+        const float2 w2 = cmul(w, w), w4 = cmul(w2, w2), w3 = cmul(w2, w);
+        x[1] = cmul(x[1], w);
+        x[2] = cmul(x[2], w2);
+        x[3] = cmul(x[3], w3);
+        x[4] = cmul(x[4], w4);
+        x[5] = cmul(x[5], cmul(w4, w));
+        x[6] = cmul(x[6], cmul(w4, w2));
+        x[7] = cmul(x[7], cmul(w4, w3));
+    }
+}
+
+// One transform size: its passes (radix R[p] combining sub-transforms of
+// length m[p]; twiddle run at toff[p]).
 struct FftParams {
-    int N, logN, L, M;
-    int twlen;          // entries of the per-pass twiddle table (<= N / 2)
+    int N, M;
+    int npass;
+    int R[kMaxPass], m[kMaxPass], toff[kMaxPass];
+    int twlen;          // entries of the per-pass twiddle table
     float scale;        // 1 / N
 };
 
@@ -119,25 +165,24 @@ struct BlockIO {
     float scale;
 };
 
-// One Stockham pass of radix R: sub-transforms of length m = 2^logm are
-// combined R at a time.  Butterfly t (< N/R) reads elements t + r N/R, scales
-// them by w^r with w = exp(d 2 pi i j / (R m)) = tw[j] (this pass's run of
-// the table), j = t mod m, and writes the radix-R DFT to (t - j) R + j + q m.
+// One Stockham pass of radix R: sub-transforms of length m are combined R at
+// a time.  Butterfly t (< N/R) reads elements t + r N/R, scales them by w^r
+// with w = exp(d 2 pi i j / (R m)) = tw[j] (this pass's run of the table),
+// j = t mod m, and writes the radix-R DFT to (t - j) R + j + q m.
 template <int R, bool INV, int SRC, int DST>
-__device__ __forceinline__ void radix_pass(const float2 *__restrict__ a, float2 *__restrict__ b, int logN, int logm,
+__device__ __forceinline__ void radix_pass(const float2 *__restrict__ a, float2 *__restrict__ b, int N, int m,
                                            const float2 *tw, const BlockIO &io) {
-    constexpr int logR = R == 2 ? 1 : (R == 4 ? 2 : 3);
-    const int N = 1 << logN, stride = N >> logR, m = 1 << logm;
+    const int stride = N / R;
     for (int t = threadIdx.x; t < stride; t += blockDim.x) {
-        const int j = t & (m - 1);
+        const int k = t / m, j = t - k * m;
+        const int base = k * R * m + j;
         // the old tail values this butterfly's outputs add (issued first: they
         // do not depend on the transform)
         float2 told_q[DST == DST_GOUT ? R : 1];
         if constexpr (DST == DST_GOUT) {
-            const int base = ((t - j) << logR) + j;
 #pragma unroll
             for (int q = 0; q < R; ++q) {
-                const int i = base + (q << logm);
+                const int i = base + q * m;
                 told_q[q] = make_float2(0.f, 0.f);
                 if (i < io.T1) {
                     told_q[q].x = __ldg(io.told + (long long)io.c1 * io.T1 + i);
@@ -160,32 +205,11 @@ __device__ __forceinline__ void radix_pass(const float2 *__restrict__ a, float2 
                 x[r] = a[pad(i)];
             }
         }
-        if (logm > 0) {
-            float2 w = tw[j];
-            if (INV) w.y = -w.y;
-            if constexpr (R == 2) {
-                x[1] = cmul(x[1], w);
-            } else if constexpr (R == 4) {
-                const float2 w2 = cmul(w, w);
-                x[1] = cmul(x[1], w);
-                x[2] = cmul(x[2], w2);
-                x[3] = cmul(x[3], cmul(w2, w));
-            } else {
-                const float2 w2 = cmul(w, w), w4 = cmul(w2, w2), w3 = cmul(w2, w);
-                x[1] = cmul(x[1], w);
-                x[2] = cmul(x[2], w2);
-                x[3] = cmul(x[3], w3);
-                x[4] = cmul(x[4], w4);
-                x[5] = cmul(x[5], cmul(w4, w));
-                x[6] = cmul(x[6], cmul(w4, w2));
-                x[7] = cmul(x[7], cmul(w4, w3));
-            }
-        }
+        if (m > 1) twiddle<R, INV>(x, tw[j]);
         dft<R, INV>(x);
-        const int base = ((t - j) << logR) + j;
 #pragma unroll
         for (int q = 0; q < R; ++q) {
-            const int i = base + (q << logm);
+            const int i = base + q * m;
             if constexpr (DST == DST_SMEM) {
                 b[pad(i)] = x[q];
             } else if constexpr (DST == DST_SMEM_H) {
@@ -209,60 +233,52 @@ __device__ __forceinline__ void radix_pass(const float2 *__restrict__ a, float2 
 }
 
 template <bool INV, int SRC, int DST>
-__device__ __forceinline__ void radix_pass_any(int logR, const float2 *a, float2 *b, int logN, int logm,
-                                               const float2 *tw, const BlockIO &io) {
-    if (logR == 1) radix_pass<2, INV, SRC, DST>(a, b, logN, logm, tw, io);
-    else if (logR == 2) radix_pass<4, INV, SRC, DST>(a, b, logN, logm, tw, io);
-    else radix_pass<8, INV, SRC, DST>(a, b, logN, logm, tw, io);
+__device__ __forceinline__ void radix_pass_any(int R, const float2 *a, float2 *b, int N, int m, const float2 *tw,
+                                               const BlockIO &io) {
+    switch (R) {
+    case 2: radix_pass<2, INV, SRC, DST>(a, b, N, m, tw, io); break;
+    case 3: radix_pass<3, INV, SRC, DST>(a, b, N, m, tw, io); break;
+    case 4: radix_pass<4, INV, SRC, DST>(a, b, N, m, tw, io); break;
+    default: radix_pass<8, INV, SRC, DST>(a, b, N, m, tw, io); break;
+    }
 }
 
 // Forward transform of the input block (read from global memory), times H
 // when io.H is set; the result is left in the returned buffer.
-__device__ float2 *fft_forward(float2 *a, float2 *b, int logN, const float2 *tw, const BlockIO &io) {
-    const int rem = logN % 3, npass = logN / 3 + (rem ? 1 : 0);
-    int logm = 0, toff = 0;
-    for (int p = 0; p < npass; ++p) {
-        const int logR = (p == 0 && rem) ? rem : 3;
-        const bool last = p == npass - 1;
-        const float2 *twp = tw + toff;
+__device__ float2 *fft_forward(const FftParams &fp, float2 *a, float2 *b, const float2 *tw, const BlockIO &io) {
+    for (int p = 0; p < fp.npass; ++p) {
+        const bool last = p == fp.npass - 1;
+        const float2 *twp = tw + fp.toff[p];
         if (p == 0) {
-            if (last && io.H) radix_pass_any<false, SRC_GIN, DST_SMEM_H>(logR, a, b, logN, logm, twp, io);
-            else radix_pass_any<false, SRC_GIN, DST_SMEM>(logR, a, b, logN, logm, twp, io);
+            if (last && io.H) radix_pass_any<false, SRC_GIN, DST_SMEM_H>(fp.R[p], a, b, fp.N, fp.m[p], twp, io);
+            else radix_pass_any<false, SRC_GIN, DST_SMEM>(fp.R[p], a, b, fp.N, fp.m[p], twp, io);
         } else {
-            if (last && io.H) radix_pass_any<false, SRC_SMEM, DST_SMEM_H>(logR, a, b, logN, logm, twp, io);
-            else radix_pass_any<false, SRC_SMEM, DST_SMEM>(logR, a, b, logN, logm, twp, io);
+            if (last && io.H) radix_pass_any<false, SRC_SMEM, DST_SMEM_H>(fp.R[p], a, b, fp.N, fp.m[p], twp, io);
+            else radix_pass_any<false, SRC_SMEM, DST_SMEM>(fp.R[p], a, b, fp.N, fp.m[p], twp, io);
         }
         __syncthreads();
         float2 *tmp = a;
         a = b;
         b = tmp;
-        if (logm > 0) toff += 1 << logm;
-        logm += logR;
     }
     return a;
 }
 
 // Inverse transform of a (unscaled); the last pass writes outputs and tail.
-__device__ void fft_inverse_out(float2 *a, float2 *b, int logN, const float2 *tw, const BlockIO &io) {
-    const int rem = logN % 3, npass = logN / 3 + (rem ? 1 : 0);
-    int logm = 0, toff = 0;
-    for (int p = 0; p < npass; ++p) {
-        const int logR = (p == 0 && rem) ? rem : 3;
-        if (p == npass - 1) {
-            radix_pass_any<true, SRC_SMEM, DST_GOUT>(logR, a, b, logN, logm, tw + toff, io);
+__device__ void fft_inverse_out(const FftParams &fp, float2 *a, float2 *b, const float2 *tw, const BlockIO &io) {
+    for (int p = 0; p < fp.npass; ++p) {
+        const float2 *twp = tw + fp.toff[p];
+        if (p == fp.npass - 1) {
+            radix_pass_any<true, SRC_SMEM, DST_GOUT>(fp.R[p], a, b, fp.N, fp.m[p], twp, io);
         } else {
-            radix_pass_any<true, SRC_SMEM, DST_SMEM>(logR, a, b, logN, logm, tw + toff, io);
+            radix_pass_any<true, SRC_SMEM, DST_SMEM>(fp.R[p], a, b, fp.N, fp.m[p], twp, io);
             __syncthreads();
             float2 *tmp = a;
             a = b;
             b = tmp;
         }
-        if (logm > 0) toff += 1 << logm;
-        logm += logR;
     }
 }
-
-int fft_threads(int N) { return std::max(64, std::min(kFftMaxThreads, N / 8)); }
 
 // One CTA per (channel pair, block) of a launch; the blocks of one launch are
 // consecutive and independent given the tail, so a launch covers exactly one
@@ -301,8 +317,8 @@ __global__ void __launch_bounds__(kFftMaxThreads) fftfilt_block_kernel(const __g
     io.T1 = fp.M - 1;
     io.scale = fp.scale;
     __syncthreads();
-    float2 *X = fft_forward(sm, sm + NP, fp.logN, stw, io);
-    fft_inverse_out(X, X == sm ? sm + NP : sm, fp.logN, stw, io);
+    float2 *X = fft_forward(fp, sm, sm + NP, stw, io);
+    fft_inverse_out(fp, X, X == sm ? sm + NP : sm, stw, io);
 }
 
 __global__ void __launch_bounds__(kFftMaxThreads) fft_of_taps_kernel(const __grid_constant__ FftParams fp,
@@ -321,27 +337,99 @@ __global__ void __launch_bounds__(kFftMaxThreads) fft_of_taps_kernel(const __gri
     io.c1 = 0;
     io.has2 = false;
     io.H = nullptr;
-    const float2 *r = fft_forward(sm, sm + NP, fp.logN, stw, io);
+    const float2 *r = fft_forward(fp, sm, sm + NP, stw, io);
     for (int i = threadIdx.x; i < fp.N; i += blockDim.x) H[i] = r[pad(i)];
 }
 
-
-
-
 // two padded buffers and the twiddle table
-size_t fft_smem(int N) { return sizeof(float2) * (2 * (size_t)(N + (N >> 4)) + (size_t)(N / 2)); }
+size_t fft_smem(int N, int twlen) { return sizeof(float2) * (2 * (size_t)pad_h(N) + (size_t)twlen); }
+
+// sizes 2^k and 3 * 2^k, 2 <= N <= kFftMaxN
+bool fft_size_ok(int N) {
+    if (N < 2 || N > kFftMaxN) return false;
+    const int p = N % 3 == 0 ? N / 3 : N;
+    return (p & (p - 1)) == 0;
+}
+
+// smallest such size >= n (0 if none)
+int fft_size_at_least(int n) {
+    for (int N = std::max(n, 2); N <= kFftMaxN; ++N)
+        if (fft_size_ok(N)) return N;
+    return 0;
+}
+
+// Passes, twiddle runs and launch shape of one size.
+struct FftSize {
+    FftParams fp{};
+    std::vector<float2> tw;
+    int threads = 0;
+    size_t smem = 0;
+    float2 *d_H = nullptr, *d_tw = nullptr;
+};
+
+void make_size(int N, int M, FftSize &z) {
+    FftParams &fp = z.fp;
+    std::memset(&fp, 0, sizeof(fp));
+    fp.N = N;
+    fp.M = M;
+    fp.scale = 1.0f / (float)N;
+    int rest = N;
+    std::vector<int> radices;
+    if (rest % 3 == 0) {
+        radices.push_back(3);
+        rest /= 3;
+    }
+    int a = 0;
+    while ((1 << a) < rest) ++a;
+    if (a % 3) radices.push_back(1 << (a % 3));
+    for (int i = 0; i < a / 3; ++i) radices.push_back(8);
+    fp.npass = (int)radices.size();
+    int m = 1;
+    z.tw.clear();
+    for (int p = 0; p < fp.npass; ++p) {
+        fp.R[p] = radices[(size_t)p];
+        fp.m[p] = m;
+        fp.toff[p] = (int)z.tw.size();
+        if (m > 1) {
+            const int Rm = m * fp.R[p];
+            for (int j = 0; j < m; ++j) {
+                const double ang = -2.0 * 3.14159265358979323846 * (double)j / (double)Rm;
+                z.tw.push_back(make_float2((float)std::cos(ang), (float)std::sin(ang)));
+            }
+        }
+        m *= fp.R[p];
+    }
+    if (z.tw.empty()) z.tw.push_back(make_float2(1.f, 0.f));
+    fp.twlen = (int)z.tw.size();
+    z.smem = fft_smem(N, fp.twlen);
+    // two CTAs of N / 16 threads per SM where their shared memory fits, else
+    // one CTA of up to N / 8 threads
+    z.threads = z.smem <= kTwoCtaSmem ? std::max(32, N / 16) : std::max(32, std::min(kFftMaxThreads, N / 8));
+}
 
 }  // namespace
 
 struct filark_fftfilt {
-    int device = 0, C = 0;
+    int device = 0, C = 0, M = 0, L = 0, Nmax = 0;
     long long max_chunk = 0;
-    FftParams fp{};
-    float2 *H = nullptr;
-    float2 *tw = nullptr;       // exp(-2 pi i k / N), k < N/2
+    std::vector<FftSize> sizes;     // ascending N: every size from the first >= M up to Nmax
     float *tail[2] = {nullptr, nullptr};   // [C][M-1] each; tail[cur] is current
     int cur = 0;
 };
+
+namespace {
+
+void free_fftfilt(filark_fftfilt *f) {
+    for (FftSize &z : f->sizes) {
+        if (z.d_H) cudaFree(z.d_H);
+        if (z.d_tw) cudaFree(z.d_tw);
+    }
+    if (f->tail[0]) cudaFree(f->tail[0]);
+    if (f->tail[1]) cudaFree(f->tail[1]);
+    delete f;
+}
+
+}  // namespace
 
 extern "C" {
 
@@ -353,26 +441,26 @@ filark_status filark_fftfilt_create(int n_channels, int n_taps, const double *ta
         return fail_with(FILARK_EINVAL, "need n_channels >= 1, n_taps >= 1, taps, max_chunk >= 1");
     for (int k = 0; k < n_taps; ++k)
         if (!std::isfinite(taps[k])) return fail_with(FILARK_EINVAL, "non-finite tap");
-    int L = block_len;
+    long long L = block_len;
     if (L <= 0) {
-        // default: the largest power-of-two block with N = 2 next_pow2(M) or more
-        int n = 1;
-        while (n < 2 * n_taps) n <<= 1;
+        // default: the largest block with N = 2 next_pow2(M) or more
+        long long n = 1;
+        while (n < 2LL * n_taps) n <<= 1;
         L = n - n_taps + 1;
     }
-    int logN = 0;
-    while ((1 << logN) < L + n_taps - 1) ++logN;
-    if (logN > kFftMaxLog) return fail_with(FILARK_ENOSYS, "block_len + n_taps - 1 above the 8192-point FFT");
+    if (L + n_taps - 1 > kFftMaxN) return fail_with(FILARK_ENOSYS, "block_len + n_taps - 1 above the 8192-point FFT");
     filark_fftfilt *f = new (std::nothrow) filark_fftfilt();
     if (!f) return fail_with(FILARK_ENOMEM, "host allocation failed");
     f->device = cuda_device;
     f->C = n_channels;
+    f->M = n_taps;
+    f->L = (int)L;
     f->max_chunk = max_chunk;
-    f->fp.logN = logN;
-    f->fp.N = 1 << logN;
-    f->fp.L = L;
-    f->fp.M = n_taps;
-    f->fp.scale = 1.0f / (float)f->fp.N;
+    f->Nmax = fft_size_at_least((int)L + n_taps - 1);
+    for (int N = fft_size_at_least(n_taps); N > 0 && N <= f->Nmax; N = fft_size_at_least(N + 1)) {
+        f->sizes.emplace_back();
+        make_size(N, n_taps, f->sizes.back());
+    }
     DeviceGuard dg(cuda_device);
     if (!dg.ok) {
         delete f;
@@ -380,53 +468,32 @@ filark_status filark_fftfilt_create(int n_channels, int n_taps, const double *ta
     }
     std::vector<float> hf((size_t)n_taps);
     for (int k = 0; k < n_taps; ++k) hf[(size_t)k] = (float)taps[k];
-    // per-pass twiddle runs, in the kernels' pass order: w_j = exp(-2 pi i j / (R m)), j < m
-    std::vector<float2> twh;
-    {
-        const int rem = logN % 3, npass = logN / 3 + (rem ? 1 : 0);
-        int logm = 0;
-        for (int p = 0; p < npass; ++p) {
-            const int logR = (p == 0 && rem) ? rem : 3;
-            if (logm > 0) {
-                const int m = 1 << logm, Rm = m << logR;
-                for (int j = 0; j < m; ++j) {
-                    const double ang = -2.0 * 3.14159265358979323846 * (double)j / (double)Rm;
-                    twh.push_back(make_float2((float)std::cos(ang), (float)std::sin(ang)));
-                }
-            }
-            logm += logR;
-        }
-    }
-    if (twh.empty()) twh.push_back(make_float2(1.f, 0.f));
-    f->fp.twlen = (int)twh.size();
     float *dh = nullptr;
-    cudaError_t e = cudaMalloc(&f->H, sizeof(float2) * (size_t)f->fp.N);
-    if (e == cudaSuccess) e = cudaMalloc(&f->tw, sizeof(float2) * twh.size());
-    if (e == cudaSuccess) e = cudaMemcpy(f->tw, twh.data(), sizeof(float2) * twh.size(), cudaMemcpyHostToDevice);
+    cudaError_t e = cudaMalloc(&dh, sizeof(float) * (size_t)n_taps);
+    if (e == cudaSuccess) e = cudaMemcpy(dh, hf.data(), sizeof(float) * hf.size(), cudaMemcpyHostToDevice);
     const size_t tail_bytes = sizeof(float) * (size_t)n_channels * (size_t)(n_taps - 1);
     if (e == cudaSuccess && n_taps > 1) e = cudaMalloc(&f->tail[0], tail_bytes);
     if (e == cudaSuccess && n_taps > 1) e = cudaMalloc(&f->tail[1], tail_bytes);
-    if (e == cudaSuccess) e = cudaMalloc(&dh, sizeof(float) * (size_t)n_taps);
-    if (e == cudaSuccess) e = cudaMemcpy(dh, hf.data(), sizeof(float) * hf.size(), cudaMemcpyHostToDevice);
+    const int max_smem = (int)fft_smem(kFftMaxN, kFftMaxN / 2);
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(fftfilt_block_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)fft_smem(1 << kFftMaxLog));
+        e = cudaFuncSetAttribute(fftfilt_block_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(fft_of_taps_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)fft_smem(1 << kFftMaxLog));
-    if (e == cudaSuccess) {
-        fft_of_taps_kernel<<<1, fft_threads(f->fp.N), fft_smem(f->fp.N)>>>(f->fp, dh, f->tw, f->H);
-        e = cudaGetLastError();
+        e = cudaFuncSetAttribute(fft_of_taps_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
+    for (FftSize &z : f->sizes) {
+        if (e == cudaSuccess) e = cudaMalloc(&z.d_H, sizeof(float2) * (size_t)z.fp.N);
+        if (e == cudaSuccess) e = cudaMalloc(&z.d_tw, sizeof(float2) * z.tw.size());
+        if (e == cudaSuccess)
+            e = cudaMemcpy(z.d_tw, z.tw.data(), sizeof(float2) * z.tw.size(), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) {
+            fft_of_taps_kernel<<<1, z.threads, z.smem>>>(z.fp, dh, z.d_tw, z.d_H);
+            e = cudaGetLastError();
+        }
     }
     if (e == cudaSuccess && f->tail[0]) e = cudaMemset(f->tail[0], 0, tail_bytes);
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     if (dh) cudaFree(dh);
     if (e != cudaSuccess) {
-        if (f->H) cudaFree(f->H);
-        if (f->tw) cudaFree(f->tw);
-        if (f->tail[0]) cudaFree(f->tail[0]);
-        if (f->tail[1]) cudaFree(f->tail[1]);
-        delete f;
+        free_fftfilt(f);
         return fail_cuda_with(e, "fftfilt create");
     }
     *out = f;
@@ -447,11 +514,18 @@ filark_status filark_fftfilt_push(filark_fftfilt *f, const float *d_in, int64_t 
     if (!dg.ok) return fail_with(FILARK_ECUDA, "cudaSetDevice failed");
     cudaStream_t s = (cudaStream_t)stream;
     const unsigned pairs = (unsigned)((f->C + 1) / 2);
-    for (int64_t t = 0; t < n_samples; t += f->fp.L) {
-        const int len = (int)std::min<int64_t>(f->fp.L, n_samples - t);
-        fftfilt_block_kernel<<<pairs, fft_threads(f->fp.N), fft_smem(f->fp.N), s>>>(
-            f->fp, d_in + t * ld_in, ld_in, len, f->C, f->H, f->tw, f->tail[f->cur], f->tail[1 - f->cur],
-            d_out + t * ld_out, ld_out);
+    for (int64_t t = 0; t < n_samples; t += f->L) {
+        const int len = (int)std::min<int64_t>(f->L, n_samples - t);
+        // the smallest size that holds this block's convolution
+        const FftSize *z = &f->sizes.back();
+        for (const FftSize &c : f->sizes)
+            if (c.fp.N >= len + f->M - 1) {
+                z = &c;
+                break;
+            }
+        fftfilt_block_kernel<<<pairs, z->threads, z->smem, s>>>(z->fp, d_in + t * ld_in, ld_in, len, f->C, z->d_H,
+                                                                  z->d_tw, f->tail[f->cur], f->tail[1 - f->cur],
+                                                                  d_out + t * ld_out, ld_out);
         f->cur = 1 - f->cur;
     }
     const cudaError_t e = cudaGetLastError();
@@ -463,15 +537,15 @@ filark_status filark_fftfilt_reset(filark_fftfilt *f, filark_stream_t stream) {
     DeviceGuard dg(f->device);
     if (!dg.ok) return fail_with(FILARK_ECUDA, "cudaSetDevice failed");
     if (!f->tail[0]) return FILARK_OK;
-    const cudaError_t e = cudaMemsetAsync(f->tail[f->cur], 0, sizeof(float) * (size_t)f->C * (f->fp.M - 1),
+    const cudaError_t e = cudaMemsetAsync(f->tail[f->cur], 0, sizeof(float) * (size_t)f->C * (f->M - 1),
                                           (cudaStream_t)stream);
     return e == cudaSuccess ? FILARK_OK : fail_cuda_with(e, "fftfilt reset");
 }
 
 filark_status filark_fftfilt_get_info(const filark_fftfilt *f, int *fft_len, int *block_len) {
     if (!f) return fail_with(FILARK_EINVAL, "filter is NULL");
-    if (fft_len) *fft_len = f->fp.N;
-    if (block_len) *block_len = f->fp.L;
+    if (fft_len) *fft_len = f->Nmax;
+    if (block_len) *block_len = f->L;
     return FILARK_OK;
 }
 
@@ -479,11 +553,7 @@ filark_status filark_fftfilt_destroy(filark_fftfilt *f) {
     if (!f) return FILARK_OK;
     DeviceGuard dg(f->device);
     cudaDeviceSynchronize();
-    if (f->H) cudaFree(f->H);
-    if (f->tw) cudaFree(f->tw);
-    if (f->tail[0]) cudaFree(f->tail[0]);
-    if (f->tail[1]) cudaFree(f->tail[1]);
-    delete f;
+    free_fftfilt(f);
     return FILARK_OK;
 }
 

@@ -54,6 +54,23 @@ def test_fftfilt_matches_direct_fir(oracle_mod, M, block_len):
     assert err <= TOL
 
 
+@pytest.mark.parametrize("M", [1, 2, 3, 5, 17, 100, 700])
+def test_fftfilt_every_transform_size(oracle_mod, M):
+    """Pushes of many lengths make every transform size 2^k and 3 * 2^k
+    between M and the largest appear (each block uses the smallest size that
+    holds its convolution)."""
+    C = 5
+    lens = [1, 2, 3, 4, 5, 6, 7, 9, 10, 13, 20, 30, 50, 64, 97, 128, 200, 300, 513, 1000, 1537, 2100]
+    N = sum(lens)
+    x = synth.small_stream(C, N, seed=150 + M)
+    h = synth.windowed_sinc_bandpass(M, 1.0, 50.0, 1000.0) if M > 2 else np.array([0.6, -0.3][:M])
+    got, info = run(x, h, lens)
+    ref = oracle_mod.TemporalOp(C, oracle_mod.TOP_FIR, M, h.astype(np.float32).astype(np.float64)).push(x)
+    err = normwise(got, ref)
+    print("sizes", M, info, err)
+    assert err <= TOL
+
+
 def test_fftfilt_reset_and_errors(oracle_mod):
     import torch
     from paper_2605_20132_gb300.chain import FFTFilter
