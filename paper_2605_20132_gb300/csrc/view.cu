@@ -15,6 +15,7 @@
 //   4. each completed column j is written to ring column j mod W -- only the
 //      newly exposed columns move, whatever the length of the recording.
 // filark_view_image unrolls the ring into [H][W], oldest column at the left.
+#include <cstdint>
 #include <cstring>
 #include <new>
 #include <string>
@@ -65,6 +66,68 @@ __global__ void view_rows_kernel(const float *__restrict__ x, long long ldx, int
     const int t = (int)(i / H), r = (int)(i % H);
     const int c0 = r * kc, n = min(C, c0 + kc) - c0;
     rows[i] = reduce_group(x + (long long)t * ldx + c0, 1, n, mode);
+}
+
+// reduce_group on values held in registers (n known at compile time)
+__device__ __forceinline__ float reduce_vals(const float *v, int n, int mode) {
+    if (mode == FILARK_VIEW_DROP || n == 1) return v[0];
+    if (mode == FILARK_VIEW_PEAK) {
+        float best = v[0], mag = fabsf(v[0]);
+        for (int i = 1; i < n; ++i)
+            if (fabsf(v[i]) > mag) {
+                mag = fabsf(v[i]);
+                best = v[i];
+            }
+        return best;
+    }
+    const int i0 = (n - 1) >> 1;
+    if (n & 1) return v[i0];
+    return 0.5f * v[i0] + 0.5f * v[i0 + 1];
+}
+
+// The same with G rows per thread read as 16-byte vectors (G * KC a multiple
+// of 4, KC <= 8 channels per row known at compile time), rows of x 16-byte
+// aligned; threads at the array's end take the scalar path.
+template <int KC>
+__host__ __device__ constexpr int rows_per_thread() {
+    return KC % 4 == 0 ? 1 : (KC % 2 == 0 ? 2 : 4);
+}
+
+template <int KC>
+__global__ void view_rows_vec_kernel(const float *__restrict__ x, long long ldx, int T, int C, int H, int mode,
+                                     float *__restrict__ rows) {
+    constexpr int G = rows_per_thread<KC>(), NF = G * KC;
+    const int ng = (H + G - 1) / G;
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (long long)T * ng) return;
+    const int t = (int)(i / ng), r0 = (int)(i % ng) * G;
+    const int c0 = r0 * KC;
+    const float *xr = x + (long long)t * ldx;
+    if (c0 + NF <= C && r0 + G <= H) {
+        float v[NF];
+#pragma unroll
+        for (int q = 0; q < NF / 4; ++q) {
+            const float4 f = __ldg(reinterpret_cast<const float4 *>(xr + c0) + q);
+            v[4 * q] = f.x;
+            v[4 * q + 1] = f.y;
+            v[4 * q + 2] = f.z;
+            v[4 * q + 3] = f.w;
+        }
+#pragma unroll
+        for (int rr = 0; rr < G; ++rr) rows[(long long)t * H + r0 + rr] = reduce_vals(v + rr * KC, KC, mode);
+    } else {
+        for (int r = r0; r < min(H, r0 + G); ++r) {
+            const int c = r * KC, n = min(C, c + KC) - c;
+            rows[(long long)t * H + r] = reduce_group(xr + c, 1, n, mode);
+        }
+    }
+}
+
+template <int KC>
+void launch_rows_vec(const float *x, long long ldx, int T, int C, int H, int mode, float *rows, cudaStream_t s) {
+    const long long ng = (H + rows_per_thread<KC>() - 1) / rows_per_thread<KC>();
+    const long long n = (long long)T * ng;
+    view_rows_vec_kernel<KC><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(x, ldx, T, C, H, mode, rows);
 }
 
 // Column q of this push covers virtual samples q*kt .. q*kt + kt - 1, where
@@ -231,7 +294,21 @@ filark_status filark_view_push(filark_view *v, const float *d_in, int64_t ld_in,
     if (!dg.ok) return fail_with(FILARK_ECUDA, "cudaSetDevice failed");
     cudaStream_t s = (cudaStream_t)stream;
     const int T = (int)n_samples, H = v->H;
-    view_rows_kernel<<<blocks_for((long long)T * H), 256, 0, s>>>(d_in, ld_in, T, v->C, v->kc, H, v->mode, v->rows);
+    if (ld_in % 4 == 0 && ((uintptr_t)d_in & 15u) == 0 && v->kc <= 8) {
+        switch (v->kc) {
+        case 1: launch_rows_vec<1>(d_in, ld_in, T, v->C, H, v->mode, v->rows, s); break;
+        case 2: launch_rows_vec<2>(d_in, ld_in, T, v->C, H, v->mode, v->rows, s); break;
+        case 3: launch_rows_vec<3>(d_in, ld_in, T, v->C, H, v->mode, v->rows, s); break;
+        case 4: launch_rows_vec<4>(d_in, ld_in, T, v->C, H, v->mode, v->rows, s); break;
+        case 5: launch_rows_vec<5>(d_in, ld_in, T, v->C, H, v->mode, v->rows, s); break;
+        case 6: launch_rows_vec<6>(d_in, ld_in, T, v->C, H, v->mode, v->rows, s); break;
+        case 7: launch_rows_vec<7>(d_in, ld_in, T, v->C, H, v->mode, v->rows, s); break;
+        default: launch_rows_vec<8>(d_in, ld_in, T, v->C, H, v->mode, v->rows, s); break;
+        }
+    } else {
+        view_rows_kernel<<<blocks_for((long long)T * H), 256, 0, s>>>(d_in, ld_in, T, v->C, v->kc, H, v->mode,
+                                                                      v->rows);
+    }
     const float *src = v->rows;
     if (v->filt) {
         filark_status st = filark_chain_push_chunk(v->filt, v->rows, H, T, nullptr, v->frows, nullptr, H, stream);

@@ -64,6 +64,18 @@ def test_view_matches_oracle(oracle_mod, mode, kc, kt, W):
 
 
 @pytest.mark.parametrize("mode", [0, 1, 2])
+@pytest.mark.parametrize("kc", [1, 2, 3, 5, 6, 8])
+def test_view_vector_rows_match_oracle(oracle_mod, mode, kc):
+    """Channel counts and row strides that are multiples of 4 (16-byte row
+    loads, several rows per thread) with a ragged last group of rows."""
+    rng = np.random.default_rng(170 + 10 * mode + kc)
+    x = synth.small_stream(44, 3000, seed=170 + kc)
+    chunks = chunking(rng, 3000, 500)
+    worst = run_both(oracle_mod, x, chunks, kc, 9, 40, mode)
+    assert worst <= 1e-6, worst
+
+
+@pytest.mark.parametrize("mode", [0, 1, 2])
 def test_view_display_filter(oracle_mod, mode):
     """Render-time causal display filter (order-4 1-50 Hz bandpass at 1 kHz)
     with its state kept across pushes."""
