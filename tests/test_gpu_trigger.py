@@ -71,12 +71,13 @@ def run_oracle_trigger(ora, R, chunks, on, off, flush=True):
     return closed, opened
 
 
-def test_triggers_match_oracle_random_chunks(oracle_mod):
-    """Blob-shaped ratio images on 300 channels, pushed in 1..700-sample
+@pytest.mark.parametrize("C", [300, 301])
+def test_triggers_match_oracle_random_chunks(oracle_mod, C):
+    """Blob-shaped ratio images on 300 and 301 channels, pushed in 1..700-sample
     chunks (segments of every phase, pushes shorter than a segment);
     thresholds that are not floats (exact comparison by rounding up)."""
     rng = np.random.default_rng(80)
-    N, C = 5000, 300
+    N = 5000
     R = blob_ratio(rng, N, C)
     on, off = 4.0000001, 1.0000001
     R[10, :5] = np.float32(on)      # equal to neither threshold as a float
