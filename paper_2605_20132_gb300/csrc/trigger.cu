@@ -13,9 +13,10 @@
 //   summary  each segment's effect for both incoming states (final state,
 //            last rise, whether a run ends inside) -- reads R once;
 //   scan     one thread per channel chains the segments (state and the start
-//            of the open run) and carries the result to the next push;
-//   emit     only segments in which a run ends read R again and append their
-//            triggers to the caller's list (one atomic per trigger).
+//            of the open run), carries the result to the next push, and lists
+//            the segments in which a run ends (one atomic per listed segment);
+//   emit     one thread per listed segment reads its 32 samples of R again and
+//            appends the triggers that end there (one atomic per trigger).
 //
 // Events are the connected components of the triggers, two triggers being
 // joined when their channels are neighbours and their intervals share a
@@ -23,6 +24,7 @@
 // orders each channel's triggers by time, joins overlapping neighbours with a
 // lock-free union-find whose roots are the smallest indices, and reduces each
 // component to (t_on, t_off, c_min, c_max, n_triggers).
+#include <algorithm>
 #include <climits>
 #include <cmath>
 #include <cstring>
@@ -71,12 +73,21 @@ __global__ void __launch_bounds__(kTrigThreads) trig_summary_kernel(const float 
     summ[(size_t)seg * C + c] = pack_summary(s0, s1, e0, e1, r0, r1);
 }
 
-// One thread per channel: state at each segment start, and the carried state.
+// A segment in which a run ends: its channel, index, entry state and the
+// start of the run open at its entry.
+struct EmitItem {
+    long long t_open;
+    int c;
+    int seg_s;          // segment << 1 | entry state
+};
+
+// One thread per channel: chains the segments (the state at each segment
+// start), lists the segments in which a run ends, and carries the state.
 __global__ void __launch_bounds__(kScanThreads) trig_scan_kernel(const unsigned *__restrict__ summ, int C, int nseg,
                                                                  long long n0, int *__restrict__ st_s,
                                                                  long long *__restrict__ st_t,
-                                                                 int *__restrict__ seg_s,
-                                                                 long long *__restrict__ seg_t) {
+                                                                 EmitItem *__restrict__ list,
+                                                                 unsigned *__restrict__ list_n) {
     const int c = blockIdx.x * kScanThreads + threadIdx.x;
     if (c >= C) return;
     int s = st_s[c];
@@ -91,8 +102,14 @@ __global__ void __launch_bounds__(kScanThreads) trig_scan_kernel(const unsigned 
         for (int q = 0; q < kScanBatch; ++q) {
             const int g = g0 + q;
             if (g < nseg) {
-                seg_s[(size_t)g * C + c] = s;
-                seg_t[(size_t)g * C + c] = t;
+                if ((m[q] >> (2 + s)) & 1) {
+                    const unsigned i = atomicAdd(list_n, 1u);
+                    EmitItem it;
+                    it.t_open = t;
+                    it.c = c;
+                    it.seg_s = (g << 1) | s;
+                    list[i] = it;
+                }
                 const int f = (m[q] >> s) & 1;
                 const int rise = (int)((m[q] >> (s ? 10 : 4)) & 63) - 1;
                 if (f) t = rise >= 0 ? n0 + (long long)g * kSeg + rise : t;
@@ -118,33 +135,36 @@ __device__ __forceinline__ void append_record(filark_trigger_record *recs, long 
     }
 }
 
-__global__ void __launch_bounds__(kTrigThreads) trig_emit_kernel(const float *__restrict__ R, long long ld, int C,
-                                                                 int T, float on, float off, long long n0,
-                                                                 const unsigned *__restrict__ summ,
-                                                                 const int *__restrict__ seg_s,
-                                                                 const long long *__restrict__ seg_t,
+// The listed segments: their samples in flight at once, then the automaton
+// from the entry state, appending the triggers that end there.  Grid-stride
+// over the list; the first thread also clears the other list counter, which
+// the next push uses.
+__global__ void __launch_bounds__(kTrigThreads) trig_emit_kernel(const float *__restrict__ R, long long ld, int T,
+                                                                 float on, float off, long long n0,
+                                                                 const EmitItem *__restrict__ list,
+                                                                 unsigned *__restrict__ list_n, int par,
                                                                  filark_trigger_record *__restrict__ recs,
                                                                  long long cap, unsigned long long *count) {
-    const int c = blockIdx.x * kTrigThreads + threadIdx.x;
-    const int seg = blockIdx.y;
-    if (c >= C) return;
-    const size_t idx = (size_t)seg * C + c;
-    int s = seg_s[idx];
-    if (!((summ[idx] >> (2 + s)) & 1)) return;   // no run ends in this segment
-    long long t = seg_t[idx];
-    const int a = seg * kSeg, nk = min(kSeg, T - a);
-    // all of the segment's samples in flight at once, then the automaton
-    float rv[kSeg];
+    const unsigned n = list_n[par];
+    if (blockIdx.x == 0 && threadIdx.x == 0) list_n[par ^ 1] = 0u;
+    for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const EmitItem it = list[i];
+        const int c = it.c, seg = it.seg_s >> 1;
+        int s = it.seg_s & 1;
+        long long t = it.t_open;
+        const int a = seg * kSeg, nk = min(kSeg, T - a);
+        float rv[kSeg];
 #pragma unroll
-    for (int k = 0; k < kSeg; ++k) rv[k] = k < nk ? __ldg(R + (long long)(a + k) * ld + c) : 0.f;
+        for (int k = 0; k < kSeg; ++k) rv[k] = k < nk ? __ldg(R + (long long)(a + k) * ld + c) : 0.f;
 #pragma unroll
-    for (int k = 0; k < kSeg; ++k) {
-        if (k < nk) {
-            const float r = rv[k];
-            const int n = r >= on ? 1 : (r < off ? 0 : s);
-            if (n && !s) t = n0 + a + k;
-            if (!n && s) append_record(recs, cap, count, t, n0 + a + k, c, 0);
-            s = n;
+        for (int k = 0; k < kSeg; ++k) {
+            if (k < nk) {
+                const float r = rv[k];
+                const int nx = r >= on ? 1 : (r < off ? 0 : s);
+                if (nx && !s) t = n0 + a + k;
+                if (!nx && s) append_record(recs, cap, count, t, n0 + a + k, c, 0);
+                s = nx;
+            }
         }
     }
 }
@@ -391,15 +411,17 @@ struct filark_trigger {
     int *st_s = nullptr;
     long long *st_t = nullptr;
     unsigned *summ = nullptr;
-    int *seg_s = nullptr;
-    long long *seg_t = nullptr;
+    EmitItem *list = nullptr;       // [C * nseg_max] segments in which a run ends
+    unsigned *list_n = nullptr;     // [2] list lengths, alternating between pushes
+    int par = 0;
+    int emit_ctas = 0;
 };
 
 namespace {
 
 void free_trigger(filark_trigger *t) {
     if (!t) return;
-    for (void *p : {(void *)t->st_s, (void *)t->st_t, (void *)t->summ, (void *)t->seg_s, (void *)t->seg_t})
+    for (void *p : {(void *)t->st_s, (void *)t->st_t, (void *)t->summ, (void *)t->list, (void *)t->list_n})
         if (p) cudaFree(p);
     delete t;
 }
@@ -433,11 +455,19 @@ filark_status filark_trigger_create(int n_channels, double on, double off, int64
         return fail_with(FILARK_ECUDA, "cudaSetDevice failed");
     }
     const size_t C = (size_t)n_channels, G = (size_t)t->nseg_max;
-    cudaError_t e = cudaMalloc(&t->st_s, sizeof(int) * C);
+    if (C * G > 0xFFFFFFFFull) {
+        delete t;
+        return fail_with(FILARK_ENOSYS, "n_channels x ceil(max_chunk / 32) above 2^32 segments");
+    }
+    int sms = 0;
+    cudaError_t e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, cuda_device);
+    t->emit_ctas = 2 * std::max(sms, 1);
+    if (e == cudaSuccess) e = cudaMalloc(&t->st_s, sizeof(int) * C);
     if (e == cudaSuccess) e = cudaMalloc(&t->st_t, sizeof(long long) * C);
     if (e == cudaSuccess) e = cudaMalloc(&t->summ, sizeof(unsigned) * C * G);
-    if (e == cudaSuccess) e = cudaMalloc(&t->seg_s, sizeof(int) * C * G);
-    if (e == cudaSuccess) e = cudaMalloc(&t->seg_t, sizeof(long long) * C * G);
+    if (e == cudaSuccess) e = cudaMalloc(&t->list, sizeof(EmitItem) * C * G);
+    if (e == cudaSuccess) e = cudaMalloc(&t->list_n, 2 * sizeof(unsigned));
+    if (e == cudaSuccess) e = cudaMemset(t->list_n, 0, 2 * sizeof(unsigned));
     if (e == cudaSuccess) e = cudaMemset(t->st_s, 0, sizeof(int) * C);
     if (e == cudaSuccess) e = cudaMemset(t->st_t, 0, sizeof(long long) * C);
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
@@ -466,12 +496,13 @@ filark_status filark_trigger_push(filark_trigger *t, const float *d_ratio, int64
     const dim3 grid2((unsigned)((t->C + kTrigThreads - 1) / kTrigThreads), (unsigned)nseg);
     const unsigned grid1 = (unsigned)((t->C + kScanThreads - 1) / kScanThreads);
     trig_summary_kernel<<<grid2, kTrigThreads, 0, s>>>(d_ratio, ld, t->C, T, t->on_f, t->off_f, t->summ);
-    trig_scan_kernel<<<grid1, kScanThreads, 0, s>>>(t->summ, t->C, nseg, t->n, t->st_s, t->st_t, t->seg_s,
-                                                    t->seg_t);
-    trig_emit_kernel<<<grid2, kTrigThreads, 0, s>>>(d_ratio, ld, t->C, T, t->on_f, t->off_f, t->n, t->summ,
-                                                    t->seg_s, t->seg_t, d_records, capacity, d_count);
+    trig_scan_kernel<<<grid1, kScanThreads, 0, s>>>(t->summ, t->C, nseg, t->n, t->st_s, t->st_t, t->list,
+                                                    t->list_n + t->par);
+    trig_emit_kernel<<<(unsigned)t->emit_ctas, kTrigThreads, 0, s>>>(d_ratio, ld, T, t->on_f, t->off_f, t->n, t->list,
+                                                                     t->list_n, t->par, d_records, capacity, d_count);
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return fail_cuda_with(e, "trigger push");
+    t->par ^= 1;
     t->n += n_samples;
     return FILARK_OK;
 }
@@ -496,6 +527,7 @@ filark_status filark_trigger_reset(filark_trigger *t, filark_stream_t stream) {
     cudaStream_t s = (cudaStream_t)stream;
     cudaError_t e = cudaMemsetAsync(t->st_s, 0, sizeof(int) * (size_t)t->C, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(t->st_t, 0, sizeof(long long) * (size_t)t->C, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(t->list_n, 0, 2 * sizeof(unsigned), s);
     if (e != cudaSuccess) return fail_cuda_with(e, "trigger reset");
     t->n = 0;
     return FILARK_OK;
