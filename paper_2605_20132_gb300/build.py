@@ -24,6 +24,7 @@ CU_SOURCES = ["chain_kernel.cu", "chain_batch.cu", "chain_static.cu", "sos_adjoi
               "temporal.cu", "fftfilt.cu", "view.cu"]
 CPP_SOURCES = ["plan.cpp", "api.cpp", "batch.cpp"]
 HEADERS = [os.path.join(CSRC, "filark_internal.h"), os.path.join(CSRC, "chain_body.cuh"), os.path.join(CSRC, "chain_object.h"),
+           os.path.join(CSRC, "host_trace.h"),
            os.path.join(INCLUDE, "filark.h")]
 
 

@@ -15,6 +15,7 @@
 #include <vector>
 
 #include "chain_object.h"
+#include "host_trace.h"
 
 using namespace filark;
 
@@ -372,6 +373,7 @@ filark_status filark_chain_reset_state(filark_chain *h, filark_stream_t stream) 
 filark_status filark_chain_push_chunk(filark_chain *h, const float *d_in, int64_t ld_in, int64_t n_samples,
                                       float *d_ratio, float *d_bandpass, float *d_spatial, int64_t ld_out,
                                       filark_stream_t stream) {
+    filark::NvtxRange nvtx_range("filark_chain_push_chunk");
     filark_status st = validate_push(h, d_in, ld_in, n_samples, d_ratio, d_bandpass, d_spatial, ld_out);
     if (st != FILARK_OK) return st;
     st = check_device_status(h);
@@ -384,6 +386,7 @@ filark_status filark_chain_push_chunk(filark_chain *h, const float *d_in, int64_
 filark_status filark_chain_push_chunk_host(filark_chain *h, const float *h_in, int64_t ld_in, int64_t n_samples,
                                            float *h_ratio, float *h_bandpass, float *h_spatial, int64_t ld_out,
                                            filark_stream_t stream) {
+    filark::NvtxRange nvtx_range("filark_chain_push_chunk_host");
     filark_status st = validate_push(h, h_in, ld_in, n_samples, h_ratio, h_bandpass, h_spatial, ld_out);
     if (st != FILARK_OK) return st;
     st = check_device_status(h);
@@ -423,6 +426,7 @@ filark_status filark_chain_push_chunk_host(filark_chain *h, const float *h_in, i
 filark_status filark_chain_push_host_async(filark_chain *h, const float *h_in, int64_t ld_in, int64_t n_samples,
                                            float *h_ratio, float *h_bandpass, float *h_spatial, int64_t ld_out,
                                            filark_stream_t stream) {
+    filark::NvtxRange nvtx_range("filark_chain_push_host_async");
     filark_status st = validate_push(h, h_in, ld_in, n_samples, h_ratio, h_bandpass, h_spatial, ld_out);
     if (st != FILARK_OK) return st;
     st = check_device_status(h);
@@ -483,6 +487,7 @@ filark_status filark_chain_push_host_async(filark_chain *h, const float *h_in, i
 }
 
 filark_status filark_chain_host_sync(filark_chain *h, filark_stream_t stream) {
+    filark::NvtxRange nvtx_range("filark_chain_host_sync");
     if (!h) return fail(FILARK_EINVAL, "chain is NULL");
     DeviceGuard dg(h->device);
     cudaError_t e = cudaSuccess;

@@ -20,6 +20,7 @@
 #include <vector>
 
 #include "chain_object.h"
+#include "host_trace.h"
 
 using namespace filark;
 
@@ -318,6 +319,7 @@ filark_status filark_batch_create(const filark_chain_config *cfg, int n_streams,
 }
 
 filark_status filark_batch_push(filark_batch *b, const filark_chunk_desc *descs, filark_stream_t stream) {
+    filark::NvtxRange nvtx_range("filark_batch_push");
     if (!b) return fail_with(FILARK_EINVAL, "batch is NULL");
     if (!descs) return fail_with(FILARK_EINVAL, "descs is NULL");
     DeviceGuard dg(b->device);

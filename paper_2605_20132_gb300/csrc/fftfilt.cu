@@ -37,6 +37,7 @@
 #include <vector>
 
 #include "filark_internal.h"
+#include "host_trace.h"
 
 using namespace filark;
 
@@ -502,6 +503,7 @@ filark_status filark_fftfilt_create(int n_channels, int n_taps, const double *ta
 
 filark_status filark_fftfilt_push(filark_fftfilt *f, const float *d_in, int64_t ld_in, int64_t n_samples,
                                   float *d_out, int64_t ld_out, filark_stream_t stream) {
+    filark::NvtxRange nvtx_range("filark_fftfilt_push");
     if (!f) return fail_with(FILARK_EINVAL, "filter is NULL");
     if (n_samples < 0 || n_samples > f->max_chunk) return fail_with(FILARK_EINVAL, "n_samples must be in [0, max_chunk]");
     if (n_samples == 0) return FILARK_OK;

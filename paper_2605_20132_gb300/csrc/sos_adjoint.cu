@@ -45,6 +45,7 @@
 #include <string>
 
 #include "filark_internal.h"
+#include "host_trace.h"
 
 namespace {
 
@@ -598,6 +599,7 @@ extern "C" filark_status filark_iir_forward_ckpt(const double *sos, int n_sectio
                                                  const float *d_x, int64_t ld_x, int64_t n_samples, float *d_y,
                                                  int64_t ld_y, int64_t ckpt_every, void *d_ckpt, size_t ckpt_size,
                                                  filark_stream_t stream) {
+    filark::NvtxRange nvtx_range("filark_iir_forward_ckpt");
     Geometry g;
     if (!make_geometry(n_sections, n_channels, n_samples, ckpt_every, g)) {
         set_last_error("need 1 <= n_sections <= FILARK_MAX_SECTIONS, n_channels >= 1, n_samples >= 1, ckpt_every >= 1");
@@ -631,6 +633,7 @@ extern "C" filark_status filark_iir_backward(const double *sos, int n_sections, 
                                              int64_t ckpt_every, const void *d_ckpt, size_t ckpt_size, void *d_work,
                                              size_t work_size, float *d_gx, int64_t ld_gx, double *d_gsos,
                                              filark_stream_t stream) {
+    filark::NvtxRange nvtx_range("filark_iir_backward");
     Geometry g;
     if (!make_geometry(n_sections, n_channels, n_samples, ckpt_every, g)) {
         set_last_error("need 1 <= n_sections <= FILARK_MAX_SECTIONS, n_channels >= 1, n_samples >= 1, ckpt_every >= 1");

@@ -28,6 +28,7 @@
 #include <string>
 
 #include "filark_internal.h"
+#include "host_trace.h"
 
 using namespace filark;
 
@@ -435,6 +436,7 @@ filark_status filark_top_create(int kind, int n_channels, int length, const doub
 
 filark_status filark_top_push(filark_top *t, const float *d_in, int64_t ld_in, int64_t n_samples, float *d_out,
                               int64_t ld_out, filark_stream_t stream) {
+    filark::NvtxRange nvtx_range("filark_top_push");
     if (!t) return fail_with(FILARK_EINVAL, "operator is NULL");
     if (n_samples < 0 || n_samples > t->max_chunk) return fail_with(FILARK_EINVAL, "n_samples must be in [0, max_chunk]");
     if (n_samples == 0) return FILARK_OK;

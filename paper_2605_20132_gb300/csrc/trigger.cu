@@ -27,11 +27,13 @@
 #include <algorithm>
 #include <climits>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <string>
 
 #include "filark_internal.h"
+#include "host_trace.h"
 
 using namespace filark;
 
@@ -320,9 +322,10 @@ __device__ __forceinline__ long long uf_find(long long *parent, long long i) {
 
 // Lock-free union; a failed hook means another thread hooked that root first.
 // Every failure is matched by a successful hook elsewhere (at most n - 1), so
-// the bound below is never reached by a correct run; if it is, *bad is set.
-__device__ void uf_union(long long *parent, long long a, long long b, int *bad) {
-    for (int tries = 0; tries < (1 << 22); ++tries) {
+// the bound (2^22 unless a test lowers it) is never reached by a correct run;
+// if it is, *bad is set and the merge reports FILARK_ETIMEOUT.
+__device__ void uf_union(long long *parent, long long a, long long b, int *bad, int max_tries) {
+    for (int tries = 0; tries < max_tries; ++tries) {
         a = uf_find(parent, a);
         b = uf_find(parent, b);
         if (a == b) return;
@@ -338,7 +341,7 @@ __device__ void uf_union(long long *parent, long long a, long long b, int *bad) 
 }
 
 // each trigger joins the overlapping triggers of the next channel
-__global__ void merge_union_kernel(MergeWork w, long long n, int C, int *bad) {
+__global__ void merge_union_kernel(MergeWork w, long long n, int C, int *bad, int max_tries) {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const int c = w.ch[i];
@@ -352,7 +355,7 @@ __global__ void merge_union_kernel(MergeWork w, long long n, int C, int *bad) {
         if (w.toff[mid] > a) hi = mid;
         else lo = mid + 1;
     }
-    for (long long j = lo; j < w.bucket[c + 2] && w.ton[j] < b; ++j) uf_union(w.parent, i, j, bad);
+    for (long long j = lo; j < w.bucket[c + 2] && w.ton[j] < b; ++j) uf_union(w.parent, i, j, bad, max_tries);
 }
 
 __global__ void merge_reduce_kernel(MergeWork w, long long n) {
@@ -482,6 +485,7 @@ filark_status filark_trigger_create(int n_channels, double on, double off, int64
 filark_status filark_trigger_push(filark_trigger *t, const float *d_ratio, int64_t ld, int64_t n_samples,
                                   filark_trigger_record *d_records, int64_t capacity, unsigned long long *d_count,
                                   filark_stream_t stream) {
+    filark::NvtxRange nvtx_range("filark_trigger_push");
     if (!t) return fail_with(FILARK_EINVAL, "trigger is NULL");
     if (n_samples < 0 || n_samples > t->max_chunk) return fail_with(FILARK_EINVAL, "n_samples must be in [0, max_chunk]");
     if (n_samples == 0) return FILARK_OK;
@@ -509,6 +513,7 @@ filark_status filark_trigger_push(filark_trigger *t, const float *d_ratio, int64
 
 filark_status filark_trigger_flush(filark_trigger *t, filark_trigger_record *d_records, int64_t capacity,
                                    unsigned long long *d_count, filark_stream_t stream) {
+    filark::NvtxRange nvtx_range("filark_trigger_flush");
     if (!t) return fail_with(FILARK_EINVAL, "trigger is NULL");
     if (!d_count || capacity < 0 || (capacity > 0 && !d_records))
         return fail_with(FILARK_EINVAL, "records/capacity/count arguments");
@@ -549,6 +554,7 @@ size_t filark_events_work_bytes(int64_t n_triggers, int n_channels) {
 filark_status filark_events_merge(const filark_trigger_record *d_triggers, int64_t n_triggers, int n_channels,
                                   filark_event *d_events, int64_t capacity, unsigned long long *d_n_events,
                                   void *d_work, size_t work_bytes, filark_stream_t stream) {
+    filark::NvtxRange nvtx_range("filark_events_merge");
     if (n_triggers < 0 || n_channels < 1) return fail_with(FILARK_EINVAL, "n_triggers < 0 or n_channels < 1");
     if (!d_n_events || capacity < 0 || (capacity > 0 && !d_events))
         return fail_with(FILARK_EINVAL, "events/capacity/count arguments");
@@ -573,7 +579,11 @@ filark_status filark_events_merge(const filark_trigger_record *d_triggers, int64
     merge_scan_kernel<<<1, 1024, 0, s>>>(w.bucket, w.cursor, n_channels);
     merge_scatter_kernel<<<gn, 256, 0, s>>>(d_triggers, n_triggers, w);
     merge_sort_kernel<<<(unsigned)((n_channels + 127) / 128), 128, 0, s>>>(w, n_channels);
-    merge_union_kernel<<<gn, 256, 0, s>>>(w, n_triggers, n_channels, bad);
+    // FILARK_TEST_UNION_TRIES lowers the retry bound so that a test can see
+    // the bounded loop give up and the merge report it (never set otherwise)
+    int max_tries = 1 << 22;
+    if (const char *ev = std::getenv("FILARK_TEST_UNION_TRIES")) max_tries = std::max(0, std::atoi(ev));
+    merge_union_kernel<<<gn, 256, 0, s>>>(w, n_triggers, n_channels, bad, max_tries);
     merge_reduce_kernel<<<gn, 256, 0, s>>>(w, n_triggers);
     merge_emit_kernel<<<gn, 256, 0, s>>>(w, n_triggers, d_events, capacity, d_n_events);
     e = cudaMemcpyAsync(&bad_h, bad, sizeof(int), cudaMemcpyDeviceToHost, s);

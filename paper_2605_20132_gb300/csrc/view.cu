@@ -21,6 +21,7 @@
 #include <string>
 
 #include "filark_internal.h"
+#include "host_trace.h"
 
 using namespace filark;
 
@@ -286,6 +287,7 @@ filark_status filark_view_create(int n_channels, int channels_per_row, int sampl
 
 filark_status filark_view_push(filark_view *v, const float *d_in, int64_t ld_in, int64_t n_samples,
                                filark_stream_t stream) {
+    filark::NvtxRange nvtx_range("filark_view_push");
     if (!v) return fail_with(FILARK_EINVAL, "view is NULL");
     if (n_samples < 0 || n_samples > v->max_chunk) return fail_with(FILARK_EINVAL, "n_samples must be in [0, max_chunk]");
     if (n_samples == 0) return FILARK_OK;
@@ -337,6 +339,7 @@ filark_status filark_view_push(filark_view *v, const float *d_in, int64_t ld_in,
 }
 
 filark_status filark_view_image(const filark_view *v, float *d_image, int64_t ld_image, filark_stream_t stream) {
+    filark::NvtxRange nvtx_range("filark_view_image");
     if (!v) return fail_with(FILARK_EINVAL, "view is NULL");
     if (!d_image || ld_image < v->W) return fail_with(FILARK_EINVAL, "image NULL or ld < width");
     DeviceGuard dg(v->device);

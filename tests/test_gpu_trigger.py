@@ -131,6 +131,34 @@ def test_events_match_oracle(oracle_mod):
     tr.close()
 
 
+def test_events_merge_bounded_retry_reports_timeout(oracle_mod, monkeypatch):
+    """The union-find's retry loop is bounded: with the bound lowered to 0 by
+    the test override every union gives up, the merge returns FILARK_ETIMEOUT
+    (no hang, no fault), and the next merge with the normal bound is correct."""
+    import torch
+    rng = np.random.default_rng(83)
+    N, C = 2000, 64
+    R = blob_ratio(rng, N, C, n_blobs=30)
+    tr, _, n = run_gpu_trigger(R, [N], 3.0, 1.5)
+    assert n > 10
+    wb = abi.filark_events_work_bytes(n, C)
+    work = torch.empty(wb + 256, dtype=torch.uint8, device="cuda")
+    wp = (work.data_ptr() + 255) // 256 * 256
+    ev = torch.zeros((n, 4), dtype=torch.int64, device="cuda")
+    n_ev = torch.zeros(1, dtype=torch.int64, device="cuda")
+    monkeypatch.setenv("FILARK_TEST_UNION_TRIES", "0")
+    st = abi.filark_events_merge(tr.records.data_ptr(), n, C, ev.data_ptr(), n, n_ev.data_ptr(), wp, wb, None)
+    assert st == abi.FILARK_ETIMEOUT
+    monkeypatch.delenv("FILARK_TEST_UNION_TRIES")
+    from paper_2605_20132_gb300.chain import merge_events
+    got, m = merge_events(tr.records, n, C)
+    closed, opened = run_oracle_trigger(oracle_mod, R, [N], 3.0, 1.5)
+    want = oracle_mod.events_merge(np.concatenate([closed, opened]))
+    assert m == len(want)
+    assert np.array_equal(sort_events(got[:, :5]), sort_events(want))
+    tr.close()
+
+
 def test_trigger_capacity_overflow_counts_everything(oracle_mod):
     rng = np.random.default_rng(82)
     R = blob_ratio(rng, 2000, 64, n_blobs=40)
