@@ -30,6 +30,9 @@ import numpy as np  # noqa: E402
 
 METRIC = "channel-samples/s of chunked filter chain (device-timed), % of HBM roofline"
 UNIT = "channel-samples/s"
+# channel-tile groups pushed on the chain's own streams (filark_chain_set_lanes);
+# each step's outputs are joined into the timing stream at the step's end
+LANES = 2
 
 
 def workload():
@@ -228,12 +231,14 @@ def run_gpu(args, rank: int, world: int, dist) -> None:
     S = sos.shape[0]
     lib = abi.load()
     chain = Chain(C, sos, w["fs"], K, ns, nl, outputs=abi.FILARK_OUT_RATIO, max_chunk=T, device=local)
+    chain.set_lanes(LANES)
     info = chain.info()
     stream = torch.cuda.Stream(device=dev)
     sh = stream.cuda_stream
     xd = torch.from_numpy(x_host).to(dev)
     rd = torch.empty((N, C), dtype=torch.float32, device=dev)
     push = lib.filark_chain_push_chunk
+    join = lib.filark_chain_join
     h = chain._h
     row = 4 * C
     xp, rp = xd.data_ptr(), rd.data_ptr()
@@ -244,6 +249,10 @@ def run_gpu(args, rank: int, world: int, dist) -> None:
             st = push(h, xi, C, T, ri, None, None, C, sh)
             if st:
                 abi.check(st, "push")
+        # every push of the step is complete on `stream` after this
+        st = join(h, sh)
+        if st:
+            abi.check(st, "join")
 
     torch.cuda.synchronize()
     with torch.cuda.stream(stream):
@@ -267,8 +276,29 @@ def run_gpu(args, rank: int, world: int, dist) -> None:
     ms = max_over_ranks(ev0.elapsed_time(ev1), dist, dev)
     abi.check(abi.filark_chain_sync_status(h, sh), "sync")
     launches_per_push = (T + 2047) // 2048
-    launches = args.steps * n_push * launches_per_push
+    lanes = min(LANES, -(-C // info["tile_channels"]))
+    launches = args.steps * n_push * launches_per_push * lanes
     value = whole_job_rate(C * N * args.steps, world, ms / 1e3)
+
+    # ---- the same pushes in one lane: each push complete on `stream` when
+    # its launch ends (the stream-ordered mode, the API's default)
+    chain.set_lanes(1)
+    so_steps = max(3, min(args.steps, 20))
+    with torch.cuda.stream(stream):
+        for _ in range(3):
+            step()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    ev2 = torch.cuda.Event(enable_timing=True)
+    ev3 = torch.cuda.Event(enable_timing=True)
+    ev2.record(stream)
+    for _ in range(so_steps):
+        step()
+    ev3.record(stream)
+    ev3.synchronize()
+    ms_so = max_over_ranks(ev2.elapsed_time(ev3), dist, dev)
+    so_value = whole_job_rate(C * N * so_steps, world, ms_so / 1e3)
 
     # ---- end to end through the host-buffer entry point (pinned host memory)
     e2e_steps = max(1, min(args.steps, 3))
@@ -301,8 +331,11 @@ def run_gpu(args, rank: int, world: int, dist) -> None:
         return
     # ---- roofline of the (only) kernel
     bytes_push = algorithmic_bytes_per_push(C, T, S, ns, nl)
-    ms_launch = ms / launches
-    achieved = bytes_push / launches_per_push / (ms_launch / 1e3) / 1e9
+    # the lanes' launches overlap: achieved = algorithmic bytes of every push
+    # of the timed region / the timed region (= bytes per push / time per push)
+    ms_push = ms / (args.steps * n_push)
+    achieved = bytes_push / (ms_push / 1e3) / 1e9
+    ms_push_so = ms_so / (so_steps * n_push)
     peak, peak_kind = measured_peak_hbm()
     traffic = None
     tp = os.path.join(ROOT, "profiles", "chain_fwd_paper_scale_traffic.json")
@@ -310,8 +343,8 @@ def run_gpu(args, rank: int, world: int, dist) -> None:
         try:
             with open(tp) as f:
                 tj = json.load(f)
-            if tj.get("kernel_source_sha") == kernel_sha():
-                traffic = tj.get("dram_bytes_per_launch")
+            if tj.get("kernel_source_sha") == kernel_sha() and tj.get("lanes") == lanes:
+                traffic = tj.get("dram_bytes_per_push")
         except (OSError, ValueError):
             traffic = None
 
@@ -329,14 +362,20 @@ def run_gpu(args, rank: int, world: int, dist) -> None:
             "workload": w["name"], "channels": C, "samples_per_step": N, "fs": w["fs"], "chunk": T,
             "pushes_per_step": n_push, "sections": S, "spatial_width": K, "sta": ns, "lta": nl,
             "precision": {1: "modal32", 2: "dense64", 3: "all32"}.get(info["precision"], "?"),
-            "l2": "inputs larger than L2 (2.16 GB per step)", "parallelism": "replicas" if world > 1 else "1 GPU"},
+            "l2": "inputs larger than L2 (2.16 GB per step)", "parallelism": "replicas" if world > 1 else "1 GPU",
+            "lanes": lanes,
+            "completion": "each step's 60 pushes complete on the timing stream at the step's end (filark_chain_join)"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
-                     "bytes_per_launch": bytes_push // launches_per_push,
-                     "ms_per_launch": ms_launch},
+                     "unit_of_work": f"one push of {T} x {C} ({lanes} overlapping launches, one per lane)",
+                     "bytes_per_push": bytes_push, "ms_per_push": ms_push},
+        "stream_ordered": {"value": so_value, "unit": UNIT, "lanes": 1, "steps": so_steps,
+                           "ms_per_push": ms_push_so,
+                           "frac": bytes_push / (ms_push_so / 1e3) / 1e9 / peak,
+                           "note": "every push complete on its stream when its launch ends"},
         "cpu_baseline": {"value": cpu_value, "unit": UNIT, "cores": cores, "kind": "oracle",
                          "sample": f"{C} channels x {cpu_push} pushes of {T} samples, FP64 oracle, {cores} threads"},
-        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 4 * C * N,
+        "e2e": {"value": e2e_value, "unit": UNIT, "lanes": 1, "h2d_bytes_per_step": 4 * C * N,
                 "d2h_bytes_per_step": 4 * C * N,
                 # the host link's own rates on this machine, measured right after:
                 # the pipelined e2e moves 4 B in and 4 B out per channel-sample
@@ -664,10 +703,80 @@ def run_ops_workload(args) -> None:
                    "display_filter": "order-8 0.5-100 Hz bandpass"}}), flush=True)
 
 
+def run_waves_workload(args) -> None:
+    """Grid-fill staircase of the chain kernel: the paper-scale chain (order-8
+    bandpass, K = 9, STA/LTA 150/3000) on n x 56 channels (n channel tiles of
+    56 outputs, one cluster of time ranges each) for pushes of 1,500 and 2,048
+    samples; device time per push over 30 consecutive pushes.  One line per
+    push length, with the tile counts at which a new wave of clusters starts
+    visible as steps; then the paper-scale chain in 1 to 4 lanes."""
+    import torch
+
+    from paper_2605_20132_gb300 import abi
+    from paper_2605_20132_gb300.chain import Chain, butter_bandpass
+    w = workload()
+    sos = butter_bandpass(w["order"], *w["band"], w["fs"])
+    tiles = (24, 36, 44, 48, 56, 72, 84, 90, 94, 96, 100, 108, 112, 120, 132, 144)
+    n_push = 30
+    wout = 56
+    for T in (w["chunk"], 2048):
+        g = torch.Generator(device="cuda").manual_seed(0)
+        x = torch.randn((n_push * T, wout * max(tiles)), device="cuda", generator=g)
+        r = torch.empty_like(x)
+        rows = []
+        for nt in tiles:
+            C = wout * nt
+            xs, rs = x[:, :C], r[:, :C]
+            ch = Chain(C, sos, w["fs"], w["spatial_width"], w["sta"], w["lta"],
+                       outputs=abi.FILARK_OUT_RATIO, max_chunk=T)
+
+            def step():
+                for t in range(0, n_push * T, T):
+                    ch.push(xs[t:t + T], ratio=rs[t:t + T])
+
+            for _ in range(3):
+                step()
+            ms = _event_ms(step, max(1, min(args.steps, 5)))
+            ch.close()
+            us = ms / n_push * 1e3
+            rows.append({"tiles": nt, "channels": C, "us_per_push": round(us, 2),
+                         "channel_samples_per_s": C * T / (us / 1e6)})
+        nblk = (T + 31) // 32
+        print(json.dumps({"workload": f"chain-grid-fill-T{T}", "metric": "device time per push",
+                          "push_samples": T, "ctas_per_cluster": (nblk + 7) // 8, "outputs_per_tile": wout,
+                          "rows": rows, "dtype": "f32", "data": "synthetic N(0,1) on the device"}), flush=True)
+        del x, r
+    # the paper-scale chain in 1-4 lanes: 60 pushes, joined at the end
+    C, T = w["n_channels"], w["chunk"]
+    n_push = 60
+    g = torch.Generator(device="cuda").manual_seed(0)
+    x = torch.randn((n_push * T, C), device="cuda", generator=g)
+    r = torch.empty_like(x)
+    ch = Chain(C, sos, w["fs"], w["spatial_width"], w["sta"], w["lta"], outputs=abi.FILARK_OUT_RATIO, max_chunk=T)
+    rows = []
+    for lanes in range(1, abi.FILARK_MAX_LANES + 1):
+        ch.set_lanes(lanes)
+
+        def lstep():
+            for t in range(0, n_push * T, T):
+                ch.push(x[t:t + T], ratio=r[t:t + T])
+            ch.join()
+
+        for _ in range(3):
+            lstep()
+        ms = _event_ms(lstep, max(1, min(args.steps, 5)))
+        us = ms / n_push * 1e3
+        rows.append({"lanes": lanes, "us_per_push": round(us, 2), "channel_samples_per_s": C * T / (us / 1e6)})
+    ch.close()
+    print(json.dumps({"workload": f"chain-lanes-{C}ch-T{T}", "metric": "device time per push", "rows": rows,
+                      "dtype": "f32", "data": "synthetic N(0,1) on the device"}), flush=True)
+
+
 def ncu_case() -> None:
     """Small profiling case for ncu captures: the paper-scale chain on 6,000
-    channels, 4 pushes of 1,500 samples of Gaussian noise (144 MB of input,
-    larger than L2), ratio output only."""
+    channels in the benchmark's lanes (one launch per lane and push), 4 pushes
+    of 1,500 samples of Gaussian noise (144 MB of input, larger than L2), ratio
+    output only."""
     import torch
 
     from paper_2605_20132_gb300 import abi
@@ -679,6 +788,7 @@ def ncu_case() -> None:
     r = torch.empty_like(x)
     ch = Chain(C, butter_bandpass(w["order"], *w["band"], w["fs"]), w["fs"], w["spatial_width"], w["sta"],
                w["lta"], outputs=abi.FILARK_OUT_RATIO, max_chunk=T)
+    ch.set_lanes(LANES)
     for i in range(n_push):
         ch.push(x[i * T:(i + 1) * T], ratio=r[i * T:(i + 1) * T])
     ch.sync()
@@ -693,7 +803,7 @@ def main() -> None:
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="filark", choices=["filark", "reference"])
     ap.add_argument("--ncu-case", action="store_true", help="run the small profiling case only")
-    ap.add_argument("--workload", default="chain", choices=["chain", "batch", "adjoint", "trigger", "ops"],
+    ap.add_argument("--workload", default="chain", choices=["chain", "batch", "adjoint", "trigger", "ops", "waves"],
                     help="chain: the paper-scale chain (the benchmark line); the others print their own line")
     args = ap.parse_args()
     if args.ncu_case:
@@ -703,7 +813,8 @@ def main() -> None:
         import torch
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
         {"batch": run_batch_workload, "adjoint": run_adjoint_workload,
-         "trigger": run_trigger_workload, "ops": run_ops_workload}[args.workload](args)
+         "trigger": run_trigger_workload, "ops": run_ops_workload,
+         "waves": run_waves_workload}[args.workload](args)
         return
     args.warmup = max(args.warmup, 3) if args.impl == "filark" else args.warmup
     world = int(os.environ.get("WORLD_SIZE", "1"))

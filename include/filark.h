@@ -199,6 +199,36 @@ filark_status filark_chain_host_sync(filark_chain *h, filark_stream_t stream);
  */
 filark_status filark_chain_set_blocks_per_cta(filark_chain *h, int blocks_per_cta);
 
+/*
+ * Lanes (no counterpart in the paper: a throughput mode for pushes that are
+ * queued back to back, e.g. a recording replayed from storage).  A launch
+ * waits for the whole previous launch before it touches the carried state, so
+ * when a push's clusters of channel tiles fill the GPU's SMs 2.4 times over,
+ * the third, partly filled wave runs with most SMs idle.  With lanes >= 2 the
+ * channel tiles are split into `lanes` contiguous groups, each pushed on an
+ * internal stream of the chain, and each tile carries the state of its halo
+ * columns itself; the groups do not wait for one another, so one group's
+ * pushes fill the other's partial waves.  A push still starts after the work
+ * already enqueued on its `stream` (the lanes fork from it), but it does NOT
+ * complete on `stream`: its input must stay unmodified, and its outputs are
+ * valid, only once a stream made to wait by filark_chain_join has reached that
+ * point (or after filark_chain_sync_status / filark_chain_host_sync).  The
+ * outputs and the state are bit-identical to lanes = 1.  get_state, set_state,
+ * reset_state, sync_status, host_sync and the host-buffer pushes join the
+ * lanes into their `stream` first (the host-buffer pushes after each push).
+ * Changing the setting waits for the lanes' pending work on the host.
+ * lanes = 1 (the default) runs every push on the caller's stream.
+ * FILARK_EINVAL outside 1..FILARK_MAX_LANES; FILARK_ECUDA / FILARK_ENOMEM if
+ * the streams or the per-tile state (2 x tiles x 64 x 2S doubles) cannot be
+ * created.  With fewer channel tiles than lanes, the tiles run one per lane.
+ */
+#define FILARK_MAX_LANES 4
+filark_status filark_chain_set_lanes(filark_chain *h, int lanes);
+
+/* Make `stream` wait (asynchronously) for every push enqueued on the chain's
+   lanes; a no-op when none is pending. */
+filark_status filark_chain_join(filark_chain *h, filark_stream_t stream);
+
 /* Zero the whole state (IIR, detector sums, history, sample count) on
    `stream`, and clear a sticky error. */
 filark_status filark_chain_reset_state(filark_chain *h, filark_stream_t stream);

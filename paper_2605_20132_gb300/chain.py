@@ -124,6 +124,16 @@ class Chain:
         abi.check(abi.filark_chain_set_blocks_per_cta(self._h, int(blocks_per_cta)),
                   "filark_chain_set_blocks_per_cta")
 
+    def set_lanes(self, lanes: int) -> None:
+        """1 (default): every push completes on its stream.  2..FILARK_MAX_LANES:
+        channel-tile groups on internal streams; a push's outputs are valid
+        only after join(stream) / sync() (see the C header)."""
+        abi.check(abi.filark_chain_set_lanes(self._h, int(lanes)), "filark_chain_set_lanes")
+
+    def join(self, stream=None) -> None:
+        """Make `stream` (default: the current stream) wait for the lanes."""
+        abi.check(abi.filark_chain_join(self._h, _stream_handle(stream)), "filark_chain_join")
+
     def host_sync(self, stream=None) -> None:
         abi.check(abi.filark_chain_host_sync(self._h, _stream_handle(stream)), "filark_chain_host_sync")
 

@@ -76,6 +76,13 @@ void free_chain(filark_chain *h) {
     }
     if (h->hcopy_in) cudaStreamDestroy(h->hcopy_in);
     if (h->hcopy_out) cudaStreamDestroy(h->hcopy_out);
+    for (int l = 0; l < FILARK_MAX_LANES; ++l) {
+        if (h->lane_s[l]) cudaStreamDestroy(h->lane_s[l]);
+        if (h->ev_lane[l]) cudaEventDestroy(h->ev_lane[l]);
+    }
+    if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+    for (double *p : h->halo)
+        if (p) cudaFree(p);
     delete h;
 }
 
@@ -98,6 +105,7 @@ filark_status zero_state(filark_chain *h, cudaStream_t stream) {
     h->parity = 0;
     h->n = 0;
     h->sticky = FILARK_OK;
+    h->halo_valid = false;
     return FILARK_OK;
 }
 
@@ -130,9 +138,41 @@ filark_status check_device_status(filark_chain *h) {
     return FILARK_OK;
 }
 
+// Make `stream` wait for every lane's enqueued work.
+filark_status join_lanes(filark_chain *h, cudaStream_t stream) {
+    if (!h->lanes_pending) return FILARK_OK;
+    for (int l = 0; l < FILARK_MAX_LANES; ++l) {
+        if (!h->lane_s[l]) continue;
+        cudaError_t e = cudaEventRecord(h->ev_lane[l], h->lane_s[l]);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(stream, h->ev_lane[l], 0);
+        if (e != cudaSuccess) {
+            h->sticky = FILARK_ECUDA;
+            return fail_cuda(e, "join: event");
+        }
+    }
+    h->lanes_pending = false;
+    return FILARK_OK;
+}
+
+// Enqueue one push.  With lanes, every launch of the push runs each tile group
+// on its lane stream after the work already on `stream`; join_after makes
+// `stream` wait for the lanes at the end (the host-buffer paths need their
+// outputs on `stream`).
 filark_status push_device(filark_chain *h, const float *d_in, int64_t ld_in, int64_t T, float *d_ratio,
-                          float *d_bp, float *d_sp, int64_t ld_out, cudaStream_t stream) {
+                          float *d_bp, float *d_sp, int64_t ld_out, cudaStream_t stream, bool join_after = false) {
     const int NS = h->plan.NS;
+    const int L = std::min(h->lanes, h->n_tiles);
+    if (L > 1) {
+        cudaError_t e = cudaEventRecord(h->ev_fork, stream);
+        for (int l = 0; l < L && e == cudaSuccess; ++l) e = cudaStreamWaitEvent(h->lane_s[l], h->ev_fork, 0);
+        if (e != cudaSuccess) {
+            h->sticky = FILARK_ECUDA;
+            return fail_cuda(e, "push: lane fork");
+        }
+    } else {
+        filark_status st = join_lanes(h, stream);
+        if (st != FILARK_OK) return st;
+    }
     int64_t done = 0;
     while (done < T) {
         const int Tl = (int)std::min<int64_t>(T - done, kMaxLaunchSamples);
@@ -164,7 +204,22 @@ filark_status push_device(filark_chain *h, const float *d_in, int64_t ld_in, int
         for (float *o : {u.ratio, u.bp, u.sp})
             if (o && ((uintptr_t)o & 15u)) ov = false;
         u.o_vec4 = ov;
-        cudaError_t e = launch_chain(p, NS, h->det, h->plan.dense, h->n_tiles, stream);
+        cudaError_t e = cudaSuccess;
+        if (L > 1) {
+            // each group reads and writes the state of its own tiles' columns
+            u.halo_in = h->halo_valid ? h->halo[h->parity] : nullptr;
+            u.halo_out = h->halo[h->parity ^ 1];
+            for (int l = 0; l < L && e == cudaSuccess; ++l) {
+                const int t0 = (int)((long long)h->n_tiles * l / L), t1 = (int)((long long)h->n_tiles * (l + 1) / L);
+                u.tx0 = t0;
+                e = launch_chain(p, NS, h->det, h->plan.dense, t1 - t0, h->lane_s[l]);
+            }
+            h->halo_valid = true;
+            h->lanes_pending = true;
+        } else {
+            e = launch_chain(p, NS, h->det, h->plan.dense, h->n_tiles, stream);
+            h->halo_valid = false;
+        }
         if (e != cudaSuccess) {
             h->sticky = FILARK_ECUDA;
             return fail_cuda(e, "push: kernel launch");
@@ -173,6 +228,7 @@ filark_status push_device(filark_chain *h, const float *d_in, int64_t ld_in, int
         h->n += Tl;
         done += Tl;
     }
+    if (join_after) return join_lanes(h, stream);
     return FILARK_OK;
 }
 
@@ -367,6 +423,8 @@ filark_status filark_chain_destroy(filark_chain *h) {
 filark_status filark_chain_reset_state(filark_chain *h, filark_stream_t stream) {
     if (!h) return fail(FILARK_EINVAL, "chain is NULL");
     DeviceGuard dg(h->device);
+    const filark_status st = join_lanes(h, (cudaStream_t)stream);
+    if (st != FILARK_OK) return st;
     return zero_state(h, (cudaStream_t)stream);
 }
 
@@ -410,7 +468,7 @@ filark_status filark_chain_push_chunk_host(filark_chain *h, const float *h_in, i
                                       (size_t)n_samples, cudaMemcpyHostToDevice, s);
     if (e != cudaSuccess) return fail_cuda(e, "push_host: input copy");
     st = push_device(h, h->stage[0], h->C, n_samples, h_ratio ? h->stage[1] : nullptr,
-                     h_bandpass ? h->stage[2] : nullptr, h_spatial ? h->stage[3] : nullptr, h->C, s);
+                     h_bandpass ? h->stage[2] : nullptr, h_spatial ? h->stage[3] : nullptr, h->C, s, true);
     if (st != FILARK_OK) return st;
     for (int i = 1; i < 4; ++i) {
         if (!hosts[i]) continue;
@@ -469,7 +527,8 @@ filark_status filark_chain_push_host_async(filark_chain *h, const float *h_in, i
     if (e == cudaSuccess && h->slot_used[k]) e = cudaStreamWaitEvent(s, h->ev_out[k], 0);
     if (e != cudaSuccess) return fail_cuda(e, "push_host_async: input copy");
     st = push_device(h, h->astage[k][0], h->C, n_samples, h_ratio ? h->astage[k][1] : nullptr,
-                     h_bandpass ? h->astage[k][2] : nullptr, h_spatial ? h->astage[k][3] : nullptr, h->C, s);
+                     h_bandpass ? h->astage[k][2] : nullptr, h_spatial ? h->astage[k][3] : nullptr, h->C, s,
+                     true);
     if (st != FILARK_OK) return st;
     e = cudaEventRecord(h->ev_comp[k], s);
     // output copies
@@ -490,6 +549,8 @@ filark_status filark_chain_host_sync(filark_chain *h, filark_stream_t stream) {
     filark::NvtxRange nvtx_range("filark_chain_host_sync");
     if (!h) return fail(FILARK_EINVAL, "chain is NULL");
     DeviceGuard dg(h->device);
+    const filark_status jst = join_lanes(h, (cudaStream_t)stream);
+    if (jst != FILARK_OK) return jst;
     cudaError_t e = cudaSuccess;
     if (h->hcopy_in) e = cudaStreamSynchronize(h->hcopy_in);
     if (e == cudaSuccess) e = cudaStreamSynchronize((cudaStream_t)stream);
@@ -508,9 +569,54 @@ filark_status filark_chain_set_blocks_per_cta(filark_chain *h, int blocks_per_ct
     return FILARK_OK;
 }
 
+filark_status filark_chain_set_lanes(filark_chain *h, int lanes) {
+    if (!h) return fail(FILARK_EINVAL, "chain is NULL");
+    if (lanes < 1 || lanes > FILARK_MAX_LANES) return fail(FILARK_EINVAL, "lanes must be in 1..FILARK_MAX_LANES");
+    DeviceGuard dg(h->device);
+    // a tile may move to another lane: let the lanes' pending work finish
+    for (int l = 0; l < FILARK_MAX_LANES && h->lanes_pending; ++l) {
+        if (!h->lane_s[l]) continue;
+        const cudaError_t e = cudaStreamSynchronize(h->lane_s[l]);
+        if (e != cudaSuccess) {
+            h->sticky = FILARK_ECUDA;
+            return fail_cuda(e, "set_lanes: synchronize");
+        }
+    }
+    h->lanes_pending = false;
+    if (lanes > 1) {
+        cudaError_t e = cudaSuccess;
+        if (!h->ev_fork) e = cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming);
+        for (int l = 0; l < lanes && e == cudaSuccess; ++l) {
+            if (!h->lane_s[l]) e = cudaStreamCreateWithFlags(&h->lane_s[l], cudaStreamNonBlocking);
+            if (e == cudaSuccess && !h->ev_lane[l]) e = cudaEventCreateWithFlags(&h->ev_lane[l], cudaEventDisableTiming);
+        }
+        if (e != cudaSuccess) return fail_cuda(e, "set_lanes: stream/event creation");
+        const int NS = h->plan.NS;
+        const size_t bytes = sizeof(double) * (size_t)h->n_tiles * kWT * (size_t)(2 * NS);
+        for (int i = 0; i < 2 && bytes > 0; ++i) {
+            if (h->halo[i]) continue;
+            if (cudaMalloc((void **)&h->halo[i], bytes) != cudaSuccess) {
+                cudaGetLastError();
+                return fail(FILARK_ENOMEM, "set_lanes: halo state allocation failed");
+            }
+            h->device_bytes += (int64_t)bytes;
+        }
+    }
+    h->lanes = lanes;
+    return FILARK_OK;
+}
+
+filark_status filark_chain_join(filark_chain *h, filark_stream_t stream) {
+    if (!h) return fail(FILARK_EINVAL, "chain is NULL");
+    DeviceGuard dg(h->device);
+    return join_lanes(h, (cudaStream_t)stream);
+}
+
 filark_status filark_chain_sync_status(filark_chain *h, filark_stream_t stream) {
     if (!h) return fail(FILARK_EINVAL, "chain is NULL");
     DeviceGuard dg(h->device);
+    const filark_status jst = join_lanes(h, (cudaStream_t)stream);
+    if (jst != FILARK_OK) return jst;
     cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
     if (e != cudaSuccess) {
         h->sticky = FILARK_ECUDA;
@@ -549,6 +655,8 @@ filark_status filark_chain_get_state(filark_chain *h, void *host_buf, size_t *by
     if (*bytes < need) return fail(FILARK_EINVAL, "state buffer too small");
     DeviceGuard dg(h->device);
     cudaStream_t s = (cudaStream_t)stream;
+    filark_status jst = join_lanes(h, s);
+    if (jst != FILARK_OK) return jst;
     cudaError_t e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return fail_cuda(e, "get_state: synchronize");
     filark_status st = check_device_status(h);
@@ -608,7 +716,9 @@ filark_status filark_chain_set_state(filark_chain *h, const void *host_buf, size
     if (bytes < need) return fail(FILARK_EINVAL, "state buffer too small");
     DeviceGuard dg(h->device);
     cudaStream_t s = (cudaStream_t)stream;
-    filark_status st = zero_state(h, s);
+    filark_status st = join_lanes(h, s);
+    if (st != FILARK_OK) return st;
+    st = zero_state(h, s);
     if (st != FILARK_OK) return st;
     cudaError_t e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return fail_cuda(e, "set_state: synchronize");

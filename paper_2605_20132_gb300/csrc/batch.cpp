@@ -155,6 +155,7 @@ int stage_push(filark_batch *b, int k, const filark_chunk_desc *d) {
             u = h->base.u;   // ring, ldr, Q, C
             // tile-private state between the units of this push (unit j reads
             // what unit j-1 wrote; the first reads the per-channel state)
+            u.tx0 = 0;   // the batched kernel passes each unit's tile itself
             u.halo_in = (hs && j > 0) ? hs + (size_t)((j - 1) & 1) * hstride : nullptr;
             u.halo_out = (hs && done + Tl < c.n_samples) ? hs + (size_t)(j & 1) * hstride : nullptr;
             u.x = c.d_in + done * c.ld_in;

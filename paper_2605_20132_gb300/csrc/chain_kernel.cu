@@ -1,6 +1,7 @@
 // Single-stream launch of the fused chain kernel (device code in
-// chain_body.cuh): one launch per <= 2048 samples of a push, grid.x =
-// channel tiles, grid.y = the cluster of time ranges.
+// chain_body.cuh): one launch per <= 2048 samples of a push (and per tile
+// group when the chain runs its tiles in lanes), grid.x = channel tiles from
+// u.tx0 on, grid.y = the cluster of time ranges.
 #include "chain_body.cuh"
 
 namespace filark {
@@ -10,7 +11,7 @@ namespace {
 template <int NS, bool DET, bool DENSE>
 __global__ void __launch_bounds__(kThreads, kCTAsPerSM) chain_fwd_kernel(const __grid_constant__ ChainParams p) {
     if (p.pdl) pdl_launch_dependents();
-    chain_body<NS, DET, DENSE>(p, p.u, blockIdx.x, blockIdx.y);
+    chain_body<NS, DET, DENSE>(p, p.u, p.u.tx0 + (int)blockIdx.x, blockIdx.y);
 }
 
 template <int NS, bool DET, bool DENSE>

@@ -34,6 +34,19 @@ struct filark_chain {
     int64_t device_bytes = 0;
     int use_pdl = 1;
     int nbc_fixed = 0;            // blocks per CTA set by the caller, 0 = kNB
+    // lanes: the channel tiles split into `lanes` contiguous groups, each
+    // pushed on an internal stream of its own; a push forks from the caller's
+    // stream, and filark_chain_join (or any call that reads or resets the
+    // state) joins the lanes back into a caller's stream
+    int lanes = 1;
+    cudaStream_t lane_s[FILARK_MAX_LANES] = {};
+    cudaEvent_t ev_fork = nullptr, ev_lane[FILARK_MAX_LANES] = {};
+    bool lanes_pending = false;   // lane work not yet joined into a caller's stream
+    // per-tile carried IIR state of all kWT columns, [tiles][kWT][2*NS] per
+    // parity, so that a tile never reads a neighbouring tile's (possibly
+    // other lane's) state; valid once a lane launch has written it
+    double *halo[2] = {nullptr, nullptr};
+    bool halo_valid = false;
 };
 
 namespace filark {

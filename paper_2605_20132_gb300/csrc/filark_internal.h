@@ -72,6 +72,7 @@ struct ChainUnit {
     int slot_n0;                        // n0 mod Q
     int C, T, nblk, Lr, R;
     int nbc;                            // blocks per CTA (<= kNB): CTA r covers blocks [r nbc, r nbc + nbc)
+    int tx0;                            // channel tile of grid.x = 0 (a launch may cover a tile range)
     int x_vec4, o_vec4;                 // float4 access allowed (input, outputs)
     // transition over the launch's last CTA, and PhiTot = PhiLast * Phi^(R-1)
     // (launch start -> launch end), as double-float hi/lo pairs
