@@ -18,9 +18,13 @@
 //         x 32 samples: block sums, per-channel prefix over the blocks, the
 //         samples' prefixes) and an output kernel over all samples.
 //   EMA   e[n] = (1-a) e[n-1] + a x[n]^2, y[n] = x[n] / sqrt(e[n]) (0 if e = 0)
-//         One CTA per 32 channels: per 32-sample block the response from a
-//         zero start (FP32), block starts from the carried state through the
-//         powers (1-a)^(32 j), the carried state itself in double-float.
+//         One CTA per 16 channels x 32 time segments; a push is one slab of
+//         32 segments of ceil(T / 32) samples (<= 64; longer pushes take
+//         several slabs), so every SM holds several CTAs and the push is one
+//         wave.  Per segment the response from a zero start (FP32), segment
+//         starts from the carried state through the powers (1-a)^(seg j), the
+//         carried state itself in double-float; the input is read twice
+//         (the second time from L2) instead of being held in registers.
 #include <cmath>
 #include <cstdint>
 #include <cstring>
@@ -42,9 +46,11 @@ constexpr int kScanBlocks = 32;     // blocks of 32 samples per slab (window / E
 constexpr int kScanCh = 8;          // channels per CTA of the prefix kernel: 32-byte rows,
                                     // and enough CTAs (C / 8) to fill every SM
 constexpr int kScanThreads = kScanCh * kScanBlocks;  // 256
-constexpr int kEmaCh = 32;          // channels per CTA of the EMA kernel (measured faster than 8)
-constexpr int kEmaThreads = kEmaCh * kScanBlocks;    // 1024
 constexpr int kSlab = 32 * kScanBlocks;              // 1024 samples
+constexpr int kEmaCh = 16;          // channels per CTA of the EMA kernel
+constexpr int kEmaSegs = 32;        // time segments per slab
+constexpr int kEmaThreads = kEmaCh * kEmaSegs;       // 512
+constexpr int kEmaMaxSeg = 64;      // samples per segment at most (slabs <= 2048 samples)
 
 struct DF2 {
     float hi, lo;
@@ -241,66 +247,66 @@ struct EmaParams {
     float alpha;                  // a
     float ac, ac_lo;              // 1 - a as a float pair: a float alone would move
                                   // a slow EMA's time constant (1-a = 0.9999 to ~6e-8)
-    float pw32[kScanBlocks + 1];  // (1-a)^(32 j), FP32
-    float pw1[32];                // (1-a)^j, FP32
-    float p1024_hi, p1024_lo;     // (1-a)^1024, double-float (full slabs)
+    int seg;                      // samples per segment for this push
+    float pwseg[kEmaSegs + 1];    // (1-a)^(seg j), FP32
+    float pw1[kEmaMaxSeg + 1];    // (1-a)^j, FP32
+    float pslab_hi, pslab_lo;     // (1-a)^(32 seg), double-float (full slabs)
     float plast_hi, plast_lo;     // (1-a)^(length of the push's last slab), double-float
 };
 
-__device__ __forceinline__ float ema_pow(const EmaParams &ep, int m) { return ep.pw32[m >> 5] * ep.pw1[m & 31]; }
-
-__global__ void __launch_bounds__(kEmaThreads) ema_kernel(const __grid_constant__ EmaParams ep,
-                                                           const float *__restrict__ x, long long ldx, int T, int C,
-                                                           float2 *__restrict__ state, float *__restrict__ y,
-                                                           long long ldy) {
-    __shared__ float ls[kScanBlocks][kEmaCh];
+__global__ void __launch_bounds__(kEmaThreads, 3) ema_kernel(const __grid_constant__ EmaParams ep,
+                                                              const float *__restrict__ x, long long ldx, int T,
+                                                              int C, float2 *__restrict__ state,
+                                                              float *__restrict__ y, long long ldy) {
+    __shared__ float ls[kEmaSegs][kEmaCh];
     __shared__ DF2 es[kEmaCh];
-    const int ch = threadIdx.x % kEmaCh, blk = threadIdx.x / kEmaCh;
+    const int ch = threadIdx.x % kEmaCh, sg = threadIdx.x / kEmaCh;
     const int c = blockIdx.x * kEmaCh + ch;
-    if (blk == 0) es[ch] = c < C ? DF2{state[c].x, state[c].y} : DF2{0.f, 0.f};
+    const int seg = ep.seg, slab_len = kEmaSegs * seg;
+    if (sg == 0) es[ch] = c < C ? DF2{state[c].x, state[c].y} : DF2{0.f, 0.f};
     __syncthreads();
-    for (int s0 = 0; s0 < T; s0 += kSlab) {
-        const int slab = min(kSlab, T - s0);
-        const int a = s0 + blk * 32;
-        float v[32];
-        // this block's response at its last sample from a zero start (FP32)
+    for (int s0 = 0; s0 < T; s0 += slab_len) {
+        const int slab = min(slab_len, T - s0);
+        const int a = s0 + sg * seg;
+        const int n_here = c < C ? max(0, min(seg, T - a)) : 0;   // samples of this segment
+        const float *xp = x + (long long)a * ldx + c;
+        // this segment's response at its last sample from a zero start (FP32)
         float l = 0.f;
-#pragma unroll
-        for (int i = 0; i < 32; ++i) {
-            const bool in = c < C && a + i < T;
-            v[i] = in ? x[(long long)(a + i) * ldx + c] : 0.f;
-            if (in) l = fmaf(ep.ac, l, fmaf(ep.ac_lo, l, ep.alpha * v[i] * v[i]));
+#pragma unroll 8
+        for (int i = 0; i < n_here; ++i) {
+            const float v = __ldg(xp + (long long)i * ldx);
+            l = fmaf(ep.ac, l, fmaf(ep.ac_lo, l, ep.alpha * v * v));
         }
-        ls[blk][ch] = l;
+        ls[sg][ch] = l;
         __syncthreads();
-        // start of this block: (1-a)^(32 blk) E + sum_{j<blk} (1-a)^(32(blk-1-j)) l_j
+        // start of this segment: (1-a)^(seg sg) E + sum_{j<sg} (1-a)^(seg (sg-1-j)) l_j
         const DF2 E = es[ch];
-        float e = ep.pw32[blk] * E.hi;
-        for (int j = 0; j < blk; ++j) e = fmaf(ep.pw32[blk - 1 - j], ls[j][ch], e);
-        if (c < C) {
-#pragma unroll
-            for (int i = 0; i < 32; ++i) {
-                if (a + i >= T) break;
-                e = fmaf(ep.ac, e, fmaf(ep.ac_lo, e, ep.alpha * v[i] * v[i]));
-                y[(long long)(a + i) * ldy + c] = e > 0.f ? v[i] * rsqrtf(e) : 0.f;
-            }
+        float e = ep.pwseg[sg] * E.hi;
+        for (int j = 0; j < sg; ++j) e = fmaf(ep.pwseg[sg - 1 - j], ls[j][ch], e);
+        float *yp = y + (long long)a * ldy + c;
+#pragma unroll 8
+        for (int i = 0; i < n_here; ++i) {
+            const float v = __ldg(xp + (long long)i * ldx);
+            e = fmaf(ep.ac, e, fmaf(ep.ac_lo, e, ep.alpha * v * v));
+            yp[(long long)i * ldy] = e > 0.f ? v * rsqrtf(e) : 0.f;
         }
         __syncthreads();
-        if (blk == 0) {
+        if (sg == 0) {
             // state after the slab's last sample, double-float:
-            // (1-a)^slab E + sum_j (1-a)^(samples after block j) l_j
-            const int nb = (slab + 31) / 32;
-            DF2 t = d_mul(E, slab == kSlab ? DF2{ep.p1024_hi, ep.p1024_lo} : DF2{ep.plast_hi, ep.plast_lo});
+            // (1-a)^slab E + sum_j (1-a)^(samples after segment j) l_j
+            const int nb = (slab + seg - 1) / seg;
+            const int tail = slab - seg * (nb - 1);      // samples of the last segment
+            DF2 t = d_mul(E, slab == slab_len ? DF2{ep.pslab_hi, ep.pslab_lo} : DF2{ep.plast_hi, ep.plast_lo});
             float add = 0.f;
             for (int j = 0; j < nb; ++j) {
-                const int after = j < nb - 1 ? slab - 32 * (j + 1) : 0;
-                add = fmaf(ema_pow(ep, after), ls[j][ch], add);
+                const float pw = j < nb - 1 ? ep.pw1[tail] * ep.pwseg[nb - 2 - j] : 1.f;
+                add = fmaf(pw, ls[j][ch], add);
             }
             es[ch] = d_add_f(t, add);
         }
         __syncthreads();
     }
-    if (blk == 0 && c < C) state[c] = make_float2(es[ch].hi, es[ch].lo);
+    if (sg == 0 && c < C) state[c] = make_float2(es[ch].hi, es[ch].lo);
 }
 
 // ------------------------------------------------------------------ host --
@@ -398,11 +404,8 @@ filark_status filark_top_create(int kind, int n_channels, int length, const doub
         t->ema.alpha = (float)alpha;
         t->ema.ac = (float)ac;
         t->ema.ac_lo = (float)(ac - (double)t->ema.ac);
-        for (int j = 0; j <= kScanBlocks; ++j) t->ema.pw32[j] = (float)std::pow(ac, 32.0 * j);
-        for (int j = 0; j < 32; ++j) t->ema.pw1[j] = (float)std::pow(ac, (double)j);
-        const double p1024 = std::pow(ac, 1024.0);
-        t->ema.p1024_hi = (float)p1024;
-        t->ema.p1024_lo = (float)(p1024 - (double)t->ema.p1024_hi);
+        for (int j = 0; j <= kEmaMaxSeg; ++j) t->ema.pw1[j] = (float)std::pow(ac, (double)j);
+        t->ema.seg = 0;   // segment tables filled at the first push
     }
     DeviceGuard dg(cuda_device);
     if (!dg.ok) {
@@ -468,9 +471,20 @@ filark_status filark_top_push(filark_top *t, const float *d_in, int64_t ld_in, i
         window_out_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(d_in, ld_in, T, C, t->M, agc, t->n,
                                                                       (int)t->Q, t->ring, d_out, ld_out);
     } else {
+        // one slab of 32 segments per push where it fits in 32 x 64 samples
+        const int seg = std::min(kEmaMaxSeg, (T + kEmaSegs - 1) / kEmaSegs);
+        const double acd = (double)t->ema.ac + (double)t->ema.ac_lo;
+        if (t->ema.seg != seg) {
+            t->ema.seg = seg;
+            for (int j = 0; j <= kEmaSegs; ++j) t->ema.pwseg[j] = (float)std::pow(acd, (double)seg * j);
+            const double ps = std::pow(acd, (double)seg * kEmaSegs);
+            t->ema.pslab_hi = (float)ps;
+            t->ema.pslab_lo = (float)(ps - (double)t->ema.pslab_hi);
+        }
         EmaParams ep = t->ema;
-        const int last = T - (T - 1) / kSlab * kSlab;   // length of the last slab
-        const double pl = std::pow((double)ep.ac + (double)ep.ac_lo, (double)last);
+        const int slab_len = kEmaSegs * seg;
+        const int last = T - (T - 1) / slab_len * slab_len;   // length of the last slab
+        const double pl = std::pow(acd, (double)last);
         ep.plast_hi = (float)pl;
         ep.plast_lo = (float)(pl - (double)ep.plast_hi);
         ema_kernel<<<(unsigned)((C + kEmaCh - 1) / kEmaCh), kEmaThreads, 0, s>>>(ep, d_in, ld_in, T, C, t->carry, d_out, ld_out);
