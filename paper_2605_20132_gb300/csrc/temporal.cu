@@ -162,23 +162,24 @@ __global__ void __launch_bounds__(kFirThreads) fir_kernel(const __grid_constant_
     }
 }
 
-// next history = the last M-1 samples of (history, push)
+// next history = the last M-1 samples of (history, push); grid (channel
+// groups of 256, history rows)
 __global__ void fir_history_kernel(const float *__restrict__ x, long long ldx, int T, int C, int M,
                                    const float *__restrict__ hist, float *__restrict__ hist_next) {
-    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    const long long n = (long long)(M - 1) * C;
-    if (i >= n) return;
-    const int j = (int)(i / C), c = (int)(i % C);
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y;
+    if (c >= C) return;
     const long long src = (long long)j + T;   // position in (history, push)
-    hist_next[i] = src >= M - 1 ? x[(src - (M - 1)) * ldx + c] : hist[src * C + c];
+    hist_next[(long long)j * C + c] = src >= M - 1 ? x[(src - (M - 1)) * ldx + c] : hist[src * C + c];
 }
 
 // ------------------------------------------------------ window sums (P) --
 
 // One CTA per 8 channels walks the push in slabs of 1024 samples and writes
 // the running prefix P[n] (double-float) of u = x (MEAN) or |x| (AGC).
+// slot0 = n0 mod Q, the ring row of the push's first sample.
 __global__ void __launch_bounds__(kScanThreads, 5) prefix_kernel(const float *__restrict__ x, long long ldx, int T,
-                                                              int C, int absval, long long n0, int Q,
+                                                              int C, int absval, int slot0, int Q,
                                                               float2 *__restrict__ ring,
                                                               float2 *__restrict__ carry) {
     __shared__ DF2 bs[kScanBlocks][kScanCh];
@@ -202,12 +203,16 @@ __global__ void __launch_bounds__(kScanThreads, 5) prefix_kernel(const float *__
         __syncthreads();
         DF2 p = cin[ch];
         for (int j = 0; j < blk; ++j) p = d_add(p, bs[j][ch]);
-        if (c < C) {
+        if (c < C && a < T) {
+            int slot = slot0 + a;                // slot0 < Q and a < T < Q: at most one wrap
+            if (slot >= Q) slot -= Q;
+            float2 *rc = ring + c;
 #pragma unroll
             for (int i = 0; i < 32; ++i) {
                 if (a + i >= T) break;
                 p = d_add_f(p, u[i]);
-                ring[(size_t)((n0 + a + i) % Q) * C + c] = make_float2(p.hi, p.lo);
+                rc[(size_t)slot * C] = make_float2(p.hi, p.lo);
+                slot = slot + 1 == Q ? 0 : slot + 1;
             }
         }
         __syncthreads();
@@ -221,24 +226,31 @@ __global__ void __launch_bounds__(kScanThreads, 5) prefix_kernel(const float *__
     if (blk == 0 && c < C) carry[c] = make_float2(cin[ch].hi, cin[ch].lo);
 }
 
+// grid (channel groups of 256, rows; rows past gridDim.y loop); slot0 = n0 mod Q
 __global__ void window_out_kernel(const float *__restrict__ x, long long ldx, int T, int C, int w, int agc,
-                                  long long n0, int Q, const float2 *__restrict__ ring, float *__restrict__ y,
-                                  long long ldy) {
-    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= (long long)T * C) return;
-    const int t = (int)(i / C), c = (int)(i % C);
-    const long long n = n0 + t;
-    const float2 pn = ring[(size_t)(n % Q) * C + c];
-    float2 pw = make_float2(0.f, 0.f);
-    if (n - w >= 0) pw = ring[(size_t)((n - w) % Q) * C + c];
-    const DF2 d = d_add(DF2{pn.x, pn.y}, DF2{-pw.x, -pw.y});
-    const float g = (d.hi + d.lo) / (float)w;
-    float out = g;
-    if (agc) {
-        const float v = x[(long long)t * ldx + c];
-        out = g > 0.f ? v / g : 0.f;
+                                  long long n0, int slot0, int Q, const float2 *__restrict__ ring,
+                                  float *__restrict__ y, long long ldy) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= C) return;
+    for (int t = blockIdx.y; t < T; t += gridDim.y) {
+        int sn = slot0 + t;                          // t < T < Q: at most one wrap
+        if (sn >= Q) sn -= Q;
+        const float2 pn = ring[(size_t)sn * C + c];
+        float2 pw = make_float2(0.f, 0.f);
+        if (n0 + t - w >= 0) {
+            int sw = sn - w;                         // w < Q
+            if (sw < 0) sw += Q;
+            pw = ring[(size_t)sw * C + c];
+        }
+        const DF2 d = d_add(DF2{pn.x, pn.y}, DF2{-pw.x, -pw.y});
+        const float g = (d.hi + d.lo) / (float)w;
+        float out = g;
+        if (agc) {
+            const float v = x[(long long)t * ldx + c];
+            out = g > 0.f ? v / g : 0.f;
+        }
+        y[(long long)t * ldy + c] = out;
     }
-    y[(long long)t * ldy + c] = out;
 }
 
 // ------------------------------------------------------------------- EMA --
@@ -459,17 +471,17 @@ filark_status filark_top_push(filark_top *t, const float *d_in, int64_t ld_in, i
         const float *h = t->M > 1 ? t->hist[t->parity] : nullptr;
         fir_kernel<<<grid, kFirThreads, fir_smem(t->fir.Mpad), s>>>(t->fir, d_in, ld_in, T, C, h, d_out, ld_out);
         if (t->M > 1) {
-            const long long n = (long long)(t->M - 1) * C;
-            fir_history_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(d_in, ld_in, T, C, t->M, h,
-                                                                           t->hist[t->parity ^ 1]);
+            const dim3 gh((unsigned)((C + 255) / 256), (unsigned)(t->M - 1));
+            fir_history_kernel<<<gh, 256, 0, s>>>(d_in, ld_in, T, C, t->M, h, t->hist[t->parity ^ 1]);
             t->parity ^= 1;
         }
     } else if (t->kind == FILARK_TOP_MEAN || t->kind == FILARK_TOP_AGC) {
         const int agc = t->kind == FILARK_TOP_AGC;
-        prefix_kernel<<<gscan, kScanThreads, 0, s>>>(d_in, ld_in, T, C, agc, t->n, (int)t->Q, t->ring, t->carry);
-        const long long n = (long long)T * C;
-        window_out_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(d_in, ld_in, T, C, t->M, agc, t->n,
-                                                                      (int)t->Q, t->ring, d_out, ld_out);
+        const int slot0 = (int)(t->n % t->Q);
+        prefix_kernel<<<gscan, kScanThreads, 0, s>>>(d_in, ld_in, T, C, agc, slot0, (int)t->Q, t->ring, t->carry);
+        const dim3 gout((unsigned)((C + 255) / 256), (unsigned)std::min(T, 65535));
+        window_out_kernel<<<gout, 256, 0, s>>>(d_in, ld_in, T, C, t->M, agc, t->n, slot0, (int)t->Q, t->ring,
+                                               d_out, ld_out);
     } else {
         // one slab of 32 segments per push where it fits in 32 x 64 samples
         const int seg = std::min(kEmaMaxSeg, (T + kEmaSegs - 1) / kEmaSegs);
