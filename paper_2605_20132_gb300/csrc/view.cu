@@ -60,13 +60,15 @@ __device__ __forceinline__ float reduce_group(const float *p, long long st, int 
     return 0.5f * p[(long long)i0 * st] + 0.5f * p[(long long)(i0 + 1) * st];
 }
 
+// grid (row groups of 256, samples; samples past gridDim.y loop)
 __global__ void view_rows_kernel(const float *__restrict__ x, long long ldx, int T, int C, int kc, int H, int mode,
                                  float *__restrict__ rows) {
-    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= (long long)T * H) return;
-    const int t = (int)(i / H), r = (int)(i % H);
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= H) return;
     const int c0 = r * kc, n = min(C, c0 + kc) - c0;
-    rows[i] = reduce_group(x + (long long)t * ldx + c0, 1, n, mode);
+#pragma unroll 1
+    for (int t = blockIdx.y; t < T; t += gridDim.y)
+        rows[(long long)t * H + r] = reduce_group(x + (long long)t * ldx + c0, 1, n, mode);
 }
 
 // reduce_group on values held in registers (n known at compile time)
@@ -95,14 +97,14 @@ __host__ __device__ constexpr int rows_per_thread() {
 }
 
 template <int KC>
-__global__ void view_rows_vec_kernel(const float *__restrict__ x, long long ldx, int T, int C, int H, int mode,
+__global__ void view_rows_vec_kernel(const float *__restrict__ x, long long ldx, int t0, int C, int H, int mode,
                                      float *__restrict__ rows) {
     constexpr int G = rows_per_thread<KC>(), NF = G * KC;
     const int ng = (H + G - 1) / G;
-    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= (long long)T * ng) return;
-    const int t = (int)(i / ng), r0 = (int)(i % ng) * G;
-    const int c0 = r0 * KC;
+    const int gi = blockIdx.x * blockDim.x + threadIdx.x;     // group of G rows
+    if (gi >= ng) return;
+    const int r0 = gi * G, c0 = r0 * KC;
+    const int t = t0 + blockIdx.y;     // grid (groups of 256 x G rows, samples from t0)
     const float *xr = x + (long long)t * ldx;
     if (c0 + NF <= C && r0 + G <= H) {
         float v[NF];
@@ -126,9 +128,11 @@ __global__ void view_rows_vec_kernel(const float *__restrict__ x, long long ldx,
 
 template <int KC>
 void launch_rows_vec(const float *x, long long ldx, int T, int C, int H, int mode, float *rows, cudaStream_t s) {
-    const long long ng = (H + rows_per_thread<KC>() - 1) / rows_per_thread<KC>();
-    const long long n = (long long)T * ng;
-    view_rows_vec_kernel<KC><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(x, ldx, T, C, H, mode, rows);
+    const int ng = (H + rows_per_thread<KC>() - 1) / rows_per_thread<KC>();
+    for (int t0 = 0; t0 < T; t0 += 65535) {
+        const dim3 grid((unsigned)((ng + 255) / 256), (unsigned)std::min(T - t0, 65535));
+        view_rows_vec_kernel<KC><<<grid, 256, 0, s>>>(x, ldx, t0, C, H, mode, rows);
+    }
 }
 
 // Column q of this push covers virtual samples q*kt .. q*kt + kt - 1, where
@@ -137,14 +141,15 @@ __device__ __forceinline__ float vsample(const float *carry, const float *src, i
     return v < nc ? carry[v * H + r] : src[(v - nc) * H + r];
 }
 
+// grid (row groups of 256, new columns): new column qi = blockIdx.y of the
+// columns q0, q0 + 1, ... goes to ring column colq0 + qi (colq0 < W, qi < W)
 __global__ void view_columns_kernel(const float *__restrict__ carry, const float *__restrict__ src, int nc,
-                                    int H, int kt, int mode, long long q0, long long nq, long long col0, int W,
+                                    int H, int kt, int mode, long long q0, int colq0, int W,
                                     float *__restrict__ ring) {
-    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= nq * H) return;
-    const long long q = q0 + i / H;
-    const int r = (int)(i % H);
-    const long long v0 = q * kt;
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= H) return;
+    const int qi = blockIdx.y;
+    const long long v0 = (q0 + qi) * kt;
     float out;
     if (mode == FILARK_VIEW_DROP || kt == 1) {
         out = vsample(carry, src, nc, H, v0, r);
@@ -176,7 +181,9 @@ __global__ void view_columns_kernel(const float *__restrict__ carry, const float
         const float a = vsample(carry, src, nc, H, v0 + i0, r);
         out = (kt & 1) ? a : 0.5f * a + 0.5f * vsample(carry, src, nc, H, v0 + i0 + 1, r);
     }
-    ring[(long long)r * W + (col0 + q) % W] = out;
+    int col = colq0 + qi;
+    if (col >= W) col -= W;
+    ring[(long long)r * W + col] = out;
 }
 
 // new carry = virtual samples [from, from + n)
@@ -188,13 +195,18 @@ __global__ void view_carry_kernel(const float *__restrict__ carry, const float *
     carry_next[i] = vsample(carry, src, nc, H, from + k, r);
 }
 
-__global__ void view_image_kernel(const float *__restrict__ ring, int H, int W, long long ncols,
+// grid (image column groups of 256, rows; rows past gridDim.y loop); ncmod =
+// ncols mod W
+__global__ void view_image_kernel(const float *__restrict__ ring, int H, int W, long long ncols, int ncmod,
                                   float *__restrict__ img, long long ldi) {
-    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= (long long)H * W) return;
-    const int r = (int)(i / W), c = (int)(i % W);
-    const long long j = ncols - W + c;   // global column shown at image column c
-    img[(long long)r * ldi + c] = j >= 0 ? ring[(long long)r * W + j % W] : 0.f;
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= W) return;
+    const bool shown = ncols - W + c >= 0;    // global column ncols - W + c exists
+    int j = ncmod + c;                        // its ring column, (ncols - W + c) mod W
+    if (j >= W) j -= W;
+#pragma unroll 1
+    for (int r = blockIdx.y; r < H; r += gridDim.y)
+        img[(long long)r * ldi + c] = shown ? ring[(long long)r * W + j] : 0.f;
 }
 
 
@@ -308,8 +320,8 @@ filark_status filark_view_push(filark_view *v, const float *d_in, int64_t ld_in,
         default: launch_rows_vec<8>(d_in, ld_in, T, v->C, H, v->mode, v->rows, s); break;
         }
     } else {
-        view_rows_kernel<<<blocks_for((long long)T * H), 256, 0, s>>>(d_in, ld_in, T, v->C, v->kc, H, v->mode,
-                                                                      v->rows);
+        const dim3 grid((unsigned)((H + 255) / 256), (unsigned)std::min(T, 65535));
+        view_rows_kernel<<<grid, 256, 0, s>>>(d_in, ld_in, T, v->C, v->kc, H, v->mode, v->rows);
     }
     const float *src = v->rows;
     if (v->filt) {
@@ -321,9 +333,14 @@ filark_status filark_view_push(filark_view *v, const float *d_in, int64_t ld_in,
     const long long nq = avail / v->kt;
     // only the last W new columns survive in the ring
     const long long q0 = nq > v->W ? nq - v->W : 0;
-    if (nq > q0)
-        view_columns_kernel<<<blocks_for((nq - q0) * H), 256, 0, s>>>(v->carry[v->parity], src, v->carry_n, H, v->kt,
-                                                                      v->mode, q0, nq - q0, v->ncols, v->W, v->ring);
+    // new columns q0 .. nq - 1 (at most W), up to 65535 per launch
+    for (long long qa = q0; qa < nq; qa += 65535) {
+        const int nnew = (int)std::min<long long>(nq - qa, 65535);
+        const int colq0 = (int)((v->ncols + qa) % v->W);
+        const dim3 grid((unsigned)((H + 255) / 256), (unsigned)nnew);
+        view_columns_kernel<<<grid, 256, 0, s>>>(v->carry[v->parity], src, v->carry_n, H, v->kt, v->mode, qa, colq0,
+                                                 v->W, v->ring);
+    }
     const int nrest = (int)(avail - nq * v->kt);
     if (nrest > 0)
         view_carry_kernel<<<blocks_for((long long)nrest * H), 256, 0, s>>>(v->carry[v->parity], src, v->carry_n, H,
@@ -344,9 +361,9 @@ filark_status filark_view_image(const filark_view *v, float *d_image, int64_t ld
     if (!d_image || ld_image < v->W) return fail_with(FILARK_EINVAL, "image NULL or ld < width");
     DeviceGuard dg(v->device);
     if (!dg.ok) return fail_with(FILARK_ECUDA, "cudaSetDevice failed");
-    view_image_kernel<<<blocks_for((long long)v->H * v->W), 256, 0, (cudaStream_t)stream>>>(v->ring, v->H, v->W,
-                                                                                            v->ncols, d_image,
-                                                                                            ld_image);
+    const dim3 grid((unsigned)((v->W + 255) / 256), (unsigned)std::min(v->H, 65535));
+    view_image_kernel<<<grid, 256, 0, (cudaStream_t)stream>>>(v->ring, v->H, v->W, v->ncols, (int)(v->ncols % v->W),
+                                                              d_image, ld_image);
     const cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? FILARK_OK : fail_cuda_with(e, "view image");
 }
