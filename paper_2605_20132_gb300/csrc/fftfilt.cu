@@ -143,6 +143,7 @@ struct FftParams {
     int N, M;
     int npass;
     int R[kMaxPass], m[kMaxPass], toff[kMaxPass];
+    unsigned mdiv[kMaxPass];   // ceil(2^32 / m): t / m = umulhi(t, mdiv) for t, m < 2^16 (m > 1)
     int twlen;          // entries of the per-pass twiddle table
     float scale;        // 1 / N
 };
@@ -157,6 +158,7 @@ struct BlockIO {
     int len;                // samples in this block
     int c1;                 // first channel of the pair (c1 + 1 the second, if has2)
     bool has2;
+    bool pair_in, pair_out; // both channels as one 8-byte access (even ld, 8-byte aligned rows)
     const float2 *H;        // [N] spectrum of the taps
     const float *told;      // [C][M-1] tail before this block (NULL if M = 1)
     float *tnew;            // [C][M-1] tail after this block
@@ -172,10 +174,10 @@ struct BlockIO {
 // j = t mod m, and writes the radix-R DFT to (t - j) R + j + q m.
 template <int R, bool INV, int SRC, int DST>
 __device__ __forceinline__ void radix_pass(const float2 *__restrict__ a, float2 *__restrict__ b, int N, int m,
-                                           const float2 *tw, const BlockIO &io) {
+                                           unsigned mdiv, const float2 *tw, const BlockIO &io) {
     const int stride = N / R;
     for (int t = threadIdx.x; t < stride; t += blockDim.x) {
-        const int k = t / m, j = t - k * m;
+        const int k = m == 1 ? t : (int)__umulhi((unsigned)t, mdiv), j = t - k * m;
         const int base = k * R * m + j;
         // the old tail values this butterfly's outputs add (issued first: they
         // do not depend on the transform)
@@ -198,8 +200,15 @@ __device__ __forceinline__ void radix_pass(const float2 *__restrict__ a, float2 
             if constexpr (SRC == SRC_GIN) {
                 float re = 0.f, im = 0.f;
                 if (i < io.len) {
-                    re = __ldg(io.x + (long long)i * io.ldx + io.c1);
-                    if (io.has2) im = __ldg(io.x + (long long)i * io.ldx + io.c1 + 1);
+                    const float *src = io.x + (long long)i * io.ldx + io.c1;
+                    if (io.pair_in) {
+                        const float2 v = __ldg(reinterpret_cast<const float2 *>(src));
+                        re = v.x;
+                        im = v.y;
+                    } else {
+                        re = __ldg(src);
+                        if (io.has2) im = __ldg(src + 1);
+                    }
                 }
                 x[r] = make_float2(re, im);
             } else {
@@ -221,8 +230,13 @@ __device__ __forceinline__ void radix_pass(const float2 *__restrict__ a, float2 
                 if (i < io.len + io.T1) {
                     const float v1 = x[q].x * io.scale + told_q[q].x, v2 = x[q].y * io.scale + told_q[q].y;
                     if (i < io.len) {
-                        io.y[(long long)i * io.ldy + io.c1] = v1;
-                        if (io.has2) io.y[(long long)i * io.ldy + io.c1 + 1] = v2;
+                        float *dst = io.y + (long long)i * io.ldy + io.c1;
+                        if (io.pair_out) {
+                            *reinterpret_cast<float2 *>(dst) = make_float2(v1, v2);
+                        } else {
+                            dst[0] = v1;
+                            if (io.has2) dst[1] = v2;
+                        }
                     } else {
                         io.tnew[(long long)io.c1 * io.T1 + (i - io.len)] = v1;
                         if (io.has2) io.tnew[(long long)(io.c1 + 1) * io.T1 + (i - io.len)] = v2;
@@ -234,13 +248,13 @@ __device__ __forceinline__ void radix_pass(const float2 *__restrict__ a, float2 
 }
 
 template <bool INV, int SRC, int DST>
-__device__ __forceinline__ void radix_pass_any(int R, const float2 *a, float2 *b, int N, int m, const float2 *tw,
-                                               const BlockIO &io) {
+__device__ __forceinline__ void radix_pass_any(int R, const float2 *a, float2 *b, int N, int m, unsigned mdiv,
+                                               const float2 *tw, const BlockIO &io) {
     switch (R) {
-    case 2: radix_pass<2, INV, SRC, DST>(a, b, N, m, tw, io); break;
-    case 3: radix_pass<3, INV, SRC, DST>(a, b, N, m, tw, io); break;
-    case 4: radix_pass<4, INV, SRC, DST>(a, b, N, m, tw, io); break;
-    default: radix_pass<8, INV, SRC, DST>(a, b, N, m, tw, io); break;
+    case 2: radix_pass<2, INV, SRC, DST>(a, b, N, m, mdiv, tw, io); break;
+    case 3: radix_pass<3, INV, SRC, DST>(a, b, N, m, mdiv, tw, io); break;
+    case 4: radix_pass<4, INV, SRC, DST>(a, b, N, m, mdiv, tw, io); break;
+    default: radix_pass<8, INV, SRC, DST>(a, b, N, m, mdiv, tw, io); break;
     }
 }
 
@@ -250,12 +264,14 @@ __device__ float2 *fft_forward(const FftParams &fp, float2 *a, float2 *b, const 
     for (int p = 0; p < fp.npass; ++p) {
         const bool last = p == fp.npass - 1;
         const float2 *twp = tw + fp.toff[p];
+        const int R = fp.R[p], m = fp.m[p];
+        const unsigned md = fp.mdiv[p];
         if (p == 0) {
-            if (last && io.H) radix_pass_any<false, SRC_GIN, DST_SMEM_H>(fp.R[p], a, b, fp.N, fp.m[p], twp, io);
-            else radix_pass_any<false, SRC_GIN, DST_SMEM>(fp.R[p], a, b, fp.N, fp.m[p], twp, io);
+            if (last && io.H) radix_pass_any<false, SRC_GIN, DST_SMEM_H>(R, a, b, fp.N, m, md, twp, io);
+            else radix_pass_any<false, SRC_GIN, DST_SMEM>(R, a, b, fp.N, m, md, twp, io);
         } else {
-            if (last && io.H) radix_pass_any<false, SRC_SMEM, DST_SMEM_H>(fp.R[p], a, b, fp.N, fp.m[p], twp, io);
-            else radix_pass_any<false, SRC_SMEM, DST_SMEM>(fp.R[p], a, b, fp.N, fp.m[p], twp, io);
+            if (last && io.H) radix_pass_any<false, SRC_SMEM, DST_SMEM_H>(R, a, b, fp.N, m, md, twp, io);
+            else radix_pass_any<false, SRC_SMEM, DST_SMEM>(R, a, b, fp.N, m, md, twp, io);
         }
         __syncthreads();
         float2 *tmp = a;
@@ -270,9 +286,9 @@ __device__ void fft_inverse_out(const FftParams &fp, float2 *a, float2 *b, const
     for (int p = 0; p < fp.npass; ++p) {
         const float2 *twp = tw + fp.toff[p];
         if (p == fp.npass - 1) {
-            radix_pass_any<true, SRC_SMEM, DST_GOUT>(fp.R[p], a, b, fp.N, fp.m[p], twp, io);
+            radix_pass_any<true, SRC_SMEM, DST_GOUT>(fp.R[p], a, b, fp.N, fp.m[p], fp.mdiv[p], twp, io);
         } else {
-            radix_pass_any<true, SRC_SMEM, DST_SMEM>(fp.R[p], a, b, fp.N, fp.m[p], twp, io);
+            radix_pass_any<true, SRC_SMEM, DST_SMEM>(fp.R[p], a, b, fp.N, fp.m[p], fp.mdiv[p], twp, io);
             __syncthreads();
             float2 *tmp = a;
             a = b;
@@ -310,6 +326,9 @@ __global__ void __launch_bounds__(kFftMaxThreads) fftfilt_block_kernel(const __g
     io.len = len;
     io.c1 = 2 * blockIdx.x;
     io.has2 = io.c1 + 1 < C;
+    // c1 is even: with an even row stride and 8-byte aligned bases the pair is one float2
+    io.pair_in = io.has2 && (ldx & 1) == 0 && ((uintptr_t)x & 7u) == 0;
+    io.pair_out = io.has2 && (ldy & 1) == 0 && ((uintptr_t)y & 7u) == 0;
     io.H = H;
     io.told = told;
     io.tnew = tnew;
@@ -390,6 +409,7 @@ void make_size(int N, int M, FftSize &z) {
     for (int p = 0; p < fp.npass; ++p) {
         fp.R[p] = radices[(size_t)p];
         fp.m[p] = m;
+        fp.mdiv[p] = m > 1 ? (unsigned)((((uint64_t)1 << 32) + (uint64_t)m - 1) / (uint64_t)m) : 0u;
         fp.toff[p] = (int)z.tw.size();
         if (m > 1) {
             const int Rm = m * fp.R[p];
