@@ -93,6 +93,24 @@ def test_triggers_match_oracle_random_chunks(oracle_mod, C):
     tr.close()
 
 
+def test_dense_triggers_match_oracle(oracle_mod):
+    """Runs ending in almost every 32-sample segment of every channel (uniform
+    ratio around thresholds 1.0 / 0.9): nearly every (channel, segment) pair
+    is on the emit list; pushes of mixed lengths."""
+    rng = np.random.default_rng(81)
+    N, C = 3000, 97
+    R = (rng.random((N, C)) * 2.0).astype(np.float32)
+    on, off = 1.0, 0.9
+    chunks = [1500, 1, 700, 799]
+    tr, got, n = run_gpu_trigger(R, chunks, on, off, capacity=1 << 20)
+    closed, opened = run_oracle_trigger(oracle_mod, R, chunks, on, off)
+    want = np.concatenate([np.c_[closed, np.zeros(len(closed), np.int64)],
+                           np.c_[opened, np.ones(len(opened), np.int64)]])
+    assert n == len(want) > 50 * C
+    assert np.array_equal(sort_records(got), sort_records(want))
+    tr.close()
+
+
 def test_trigger_threshold_edges(oracle_mod):
     """R equal to the on threshold sets, equal to off keeps, the float just
     below off resets; hysteresis across a push boundary of one sample."""
