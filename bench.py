@@ -30,6 +30,8 @@ import numpy as np  # noqa: E402
 
 METRIC = "channel-samples/s of chunked filter chain (device-timed), % of HBM roofline"
 UNIT = "channel-samples/s"
+# GB300 HBM3e nominal bandwidth, quoted beside the measured copy peak
+NOMINAL_HBM_GBS = 7900.0
 # channel-tile groups pushed on the chain's own streams (filark_chain_set_lanes);
 # each step's outputs are joined into the timing stream at the step's end
 LANES = 2
@@ -367,6 +369,7 @@ def run_gpu(args, rank: int, world: int, dist) -> None:
             "completion": "each step's 60 pushes complete on the timing stream at the step's end (filark_chain_join)"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
+                     "frac_of_nominal": achieved / NOMINAL_HBM_GBS,
                      "unit_of_work": f"one push of {T} x {C} ({lanes} overlapping launches, one per lane)",
                      "bytes_per_push": bytes_push, "ms_per_push": ms_push},
         "stream_ordered": {"value": so_value, "unit": UNIT, "lanes": 1, "steps": so_steps,
