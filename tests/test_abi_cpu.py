@@ -152,6 +152,21 @@ def test_destroy_null_is_ok():
     assert abi.filark_chain_destroy(None) == abi.FILARK_OK
 
 
+def test_chain_calls_reject_a_null_handle():
+    """Every chain call that takes a handle reports FILARK_EINVAL for NULL
+    before touching a device (lanes, join, geometry, status, state, resets)."""
+    import ctypes as ct
+    assert abi.filark_chain_set_lanes(None, 2) == abi.FILARK_EINVAL
+    assert abi.filark_chain_join(None, None) == abi.FILARK_EINVAL
+    assert abi.filark_chain_set_blocks_per_cta(None, 4) == abi.FILARK_EINVAL
+    assert abi.filark_chain_sync_status(None, None) == abi.FILARK_EINVAL
+    assert abi.filark_chain_host_sync(None, None) == abi.FILARK_EINVAL
+    assert abi.filark_chain_reset_state(None, None) == abi.FILARK_EINVAL
+    assert abi.filark_chain_get_state(None, None, ct.c_size_t(0), None) == abi.FILARK_EINVAL
+    assert abi.filark_chain_set_state(None, None, 0, None) == abi.FILARK_EINVAL
+    assert "NULL" in abi.filark_last_error_string()
+
+
 # ---- differentiable bandpass: host-side sizes and argument checks ----------
 
 def _piece(ckpt):
