@@ -10,7 +10,6 @@
 #include <cstring>
 #include <mutex>
 #include <new>
-#include <set>
 #include <string>
 #include <vector>
 
@@ -36,7 +35,6 @@ filark_status fail_cuda(cudaError_t e, const char *what) {
 
 
 std::mutex g_cfg_mu;
-std::set<int> g_configured;
 
 constexpr uint32_t kStateMagic = 0x4B524C46u;   // "FLRK"
 constexpr uint32_t kStateVersion = 1u;
@@ -158,18 +156,29 @@ filark_status join_lanes(filark_chain *h, cudaStream_t stream) {
 // on its lane stream after the work already on `stream`; join_after makes
 // `stream` wait for the lanes at the end (the host-buffer paths need their
 // outputs on `stream`).
+//
+// Lane launches read only per-tile state (`halo`), which a tile alone writes.
+// Until that state exists (after create, reset, set_state, a one-lane push or
+// a lane change) a tile's halo columns would have to come from the
+// neighbouring tiles' per-channel state, which another lane may already be
+// overwriting; so the first launch in that case runs every tile at once on
+// `stream` and writes the per-tile state, and the lanes fork after it.
 filark_status push_device(filark_chain *h, const float *d_in, int64_t ld_in, int64_t T, float *d_ratio,
                           float *d_bp, float *d_sp, int64_t ld_out, cudaStream_t stream, bool join_after = false) {
     const int NS = h->plan.NS;
     const int L = std::min(h->lanes, h->n_tiles);
-    if (L > 1) {
+    bool forked = false;
+    auto fork_lanes = [&]() -> filark_status {
         cudaError_t e = cudaEventRecord(h->ev_fork, stream);
         for (int l = 0; l < L && e == cudaSuccess; ++l) e = cudaStreamWaitEvent(h->lane_s[l], h->ev_fork, 0);
         if (e != cudaSuccess) {
             h->sticky = FILARK_ECUDA;
             return fail_cuda(e, "push: lane fork");
         }
-    } else {
+        forked = true;
+        return FILARK_OK;
+    };
+    if (L <= 1 || !h->halo_valid) {
         filark_status st = join_lanes(h, stream);
         if (st != FILARK_OK) return st;
     }
@@ -205,16 +214,27 @@ filark_status push_device(filark_chain *h, const float *d_in, int64_t ld_in, int
             if (o && ((uintptr_t)o & 15u)) ov = false;
         u.o_vec4 = ov;
         cudaError_t e = cudaSuccess;
-        if (L > 1) {
+        if (L > 1 && !h->halo_valid) {
+            // every tile in one launch on the caller's stream: halo columns
+            // from the per-channel state, per-tile state written for the lanes
+            u.halo_in = nullptr;
+            u.halo_out = h->halo[h->parity ^ 1];
+            u.tx0 = 0;
+            e = launch_chain(p, NS, h->det, h->plan.dense, h->n_tiles, stream);
+            h->halo_valid = true;
+        } else if (L > 1) {
+            if (!forked) {
+                const filark_status st = fork_lanes();
+                if (st != FILARK_OK) return st;
+            }
             // each group reads and writes the state of its own tiles' columns
-            u.halo_in = h->halo_valid ? h->halo[h->parity] : nullptr;
+            u.halo_in = h->halo[h->parity];
             u.halo_out = h->halo[h->parity ^ 1];
             for (int l = 0; l < L && e == cudaSuccess; ++l) {
                 const int t0 = (int)((long long)h->n_tiles * l / L), t1 = (int)((long long)h->n_tiles * (l + 1) / L);
                 u.tx0 = t0;
                 e = launch_chain(p, NS, h->det, h->plan.dense, t1 - t0, h->lane_s[l]);
             }
-            h->halo_valid = true;
             h->lanes_pending = true;
         } else {
             e = launch_chain(p, NS, h->det, h->plan.dense, h->n_tiles, stream);
@@ -337,14 +357,13 @@ filark_status filark_chain_create(const filark_chain_config *cfg, int cuda_devic
         return fail(FILARK_ECUDA, "cudaSetDevice failed for device " + std::to_string(cuda_device));
     }
     {
+        // set on every create: attributes set once would not survive a
+        // cudaDeviceReset of the device
         std::lock_guard<std::mutex> lk(g_cfg_mu);
-        if (!g_configured.count(cuda_device)) {
-            cudaError_t e = configure_chain_kernels();
-            if (e != cudaSuccess) {
-                delete h;
-                return fail_cuda(e, "create: kernel attributes");
-            }
-            g_configured.insert(cuda_device);
+        cudaError_t e = configure_chain_kernels();
+        if (e != cudaSuccess) {
+            delete h;
+            return fail_cuda(e, "create: kernel attributes");
         }
     }
     const int NS = h->plan.NS;

@@ -354,6 +354,59 @@ def test_paper_scale_parity_sampled(oracle_mod, paper_scale):
     assert normwise(outs["sp"][rows].double().cpu().numpy(), mean.cpu().numpy()) <= TOL
 
 
+def test_paper_scale_benchmark_configuration(oracle_mod, paper_scale):
+    """The benchmark's own configuration: the paper-scale stream pushed as 60
+    chunks of 1,500 samples in two lanes (tiles 0-53 and 54-107) with the SOS
+    from the library's Butterworth designer and the ratio as the only output,
+    as the benchmark line times it.  Its ratio is compared with the FP64
+    oracle on sampled channel windows: both array ends, the middle, and the
+    boundary between the two lanes' tile groups (channel 54 x 56 = 3024).  A
+    second run with every output enabled gives the identical ratio and its
+    bandpass and spatial outputs are compared there too."""
+    import torch
+    from paper_2605_20132_gb300.chain import Chain, butter_bandpass
+    x = paper_scale
+    N, C = x.shape
+    cfg = synth.PAPER_SCALE
+    sos = butter_bandpass(cfg["order"], *cfg["band"], cfg["fs"])
+    K, ns, nl, T = cfg["spatial_width"], cfg["sta"], cfg["lta"], cfg["chunk"]
+    xd = torch.from_numpy(x).cuda()
+
+    def run(outputs):
+        ch = Chain(C, sos, cfg["fs"], K, ns, nl, outputs=outputs, max_chunk=T)
+        ch.set_lanes(2)
+        assert ch.info()["tile_channels"] == 56
+        names = ["ratio"] + (["bp", "sp"] if outputs != abi.FILARK_OUT_RATIO else [])
+        outs = {k: torch.full((N, C), float("nan"), device="cuda") for k in names}
+        for t in range(0, N, T):
+            ch.push(xd[t:t + T], ratio=outs["ratio"][t:t + T],
+                    bandpass=outs["bp"][t:t + T] if "bp" in outs else None,
+                    spatial=outs["sp"][t:t + T] if "sp" in outs else None)
+        ch.join()
+        ch.sync()
+        ch.close()
+        return outs
+
+    bench = run(abi.FILARK_OUT_RATIO)
+    full = run(ALL_OUT)
+    assert torch.equal(bench["ratio"], full["ratio"])
+    h = (K - 1) // 2
+    worst = {}
+    for lo, hi in [(0, 24), (2988, 3012), (3008, 3040), (5976, 6000)]:
+        a, b = max(0, lo - h), min(C, hi + h)
+        ref = run_oracle(oracle_mod, np.ascontiguousarray(x[:, a:b]), sos, K=K, ns=ns, nl=nl)
+        sel = slice(lo - a, hi - a)
+        got = {k: full[k][:, lo:hi].cpu().numpy() for k in full}
+        errs = compare(got, {k: ref[k][:, sel] for k in ref})
+        for k, v in errs.items():
+            worst[k] = max(worst.get(k, 0.0), v)
+    print("benchmark configuration, sampled errors:", worst)
+    assert set(worst) == {"ratio", "bp", "sp"}
+    assert all(e <= TOL for e in worst.values()), worst
+    r = bench["ratio"]
+    assert torch.isfinite(r).all() and (r >= 0).all() and (r[: nl - 1] == 0).all()
+
+
 # --------------------------------------------------------------------------
 # Dense FP64 carry (canonical basis): forced on the small workload, chosen
 # automatically for a defective cascade (repeated poles) and for the

@@ -190,3 +190,37 @@ def test_set_lanes_rejects_out_of_range(oracle_mod):
     assert abi.filark_chain_set_lanes(ch._h, abi.FILARK_MAX_LANES) == abi.FILARK_OK
     assert abi.filark_chain_join(ch._h, None) == abi.FILARK_OK
     ch.close()
+
+
+def test_lanes_paper_scale_first_pushes_bitwise(oracle_mod):
+    """The paper-scale chain (6,000 channels = 108 tiles, two lanes of 54
+    tiles; order-8 0.5-100 Hz bandpass from the library's designer, K = 9,
+    STA/LTA 150/3000) with pushes longer than one launch right after create
+    and right after a reset, where the per-tile state does not exist yet:
+    every output equals one lane bit for bit, in both runs."""
+    import torch
+    from paper_2605_20132_gb300.chain import Chain, butter_bandpass
+    cfg = synth.PAPER_SCALE
+    C, fs = cfg["n_channels"], cfg["fs"]
+    chunks = [3000, 1500, 2500, 1500, 3500]
+    N = sum(chunks)
+    x = synth.paper_scale_stream(C, N, seed=48)
+    sos = butter_bandpass(cfg["order"], *cfg["band"], fs)
+    K, ns, nl = cfg["spatial_width"], cfg["sta"], cfg["lta"]
+    one = run_gpu(x, chunks, sos, fs=fs, K=K, ns=ns, nl=nl, max_chunk=max(chunks))
+    ch = Chain(C, sos, fs, K, ns, nl, outputs=ALL_OUT, max_chunk=max(chunks))
+    ch.set_lanes(2)
+    xd = torch.from_numpy(x).cuda()
+    for rep in range(2):
+        outs = {k: torch.full(xd.shape, float("nan"), device="cuda") for k in ("ratio", "bp", "sp")}
+        t = 0
+        for T in chunks:
+            sl = slice(t, t + T)
+            ch.push(xd[sl], ratio=outs["ratio"][sl], bandpass=outs["bp"][sl], spatial=outs["sp"][sl])
+            t += T
+        ch.join()
+        ch.sync()
+        for k in one:
+            assert np.array_equal(outs[k].cpu().numpy(), one[k]), (rep, k)
+        ch.reset()
+    ch.close()
