@@ -276,21 +276,28 @@ filark_status filark_butter_bandpass_sos(int order, double f1, double f2, double
  *
  * Runs the whole chain over ONE recording of n_samples samples, from a zero
  * state, writing the requested outputs (same layouts and rules as
- * filark_chain_push_chunk; any n_samples >= 0, inputs must not overlap
- * outputs).  The chain's working memory (carried IIR and detector state, cf
- * history ring, dense-carry matrices) lives in a 32 MiB file-scope device array
- * that every GPU which loads the library holds until the process exits; no
- * device memory is allocated or freed (host-side planning uses ordinary heap
- * memory).  A recording whose working memory would exceed the array -- roughly
+ * filark_chain_push_chunk; any n_samples >= 0).  An output pointer whose bit is
+ * not set in cfg->outputs, an output that overlaps the input or another output,
+ * or a stride below n_channels is rejected with FILARK_EINVAL.  The chain's
+ * working memory (carried IIR and detector state, cf history ring, dense-carry
+ * matrices) lives in a 32 MiB file-scope device array that every GPU which
+ * loads the library holds until the process exits; no device memory is
+ * allocated or freed (host-side planning uses ordinary heap memory).  A
+ * recording whose working memory would exceed the array -- roughly
  * 4 * n_channels * (lta_len + min(n_samples, 2048)) bytes plus the state -- is
  * rejected with FILARK_EINVAL and a message.
  *
- * The device address of the array is looked up, and the kernels' attributes are
- * set, on the first call on each device (with that device current); make that
- * first call before any stream capture.  All calls share the array and each
- * call clears the state it starts from, so calls that overlap on the GPU (other
- * streams or host threads) race with each other; serialise them.  Work is
- * enqueued on `stream` on the current CUDA device.
+ * Every call looks up the array's device address and sets the kernels'
+ * attributes on the current device (neither allocates); the first call on a
+ * device also loads the library's device code there, so make that first call
+ * before any stream capture.  When the plan uses the dense FP64 carry
+ * (FILARK_PREC_DENSE64, or FILARK_PREC_AUTO for poles very close to z = 1, see
+ * filark_chain_get_info of an equivalent chain), the call copies the carry
+ * matrices from host memory and waits for `stream` before it returns.  All
+ * calls share the array and each call clears the state it starts from, so
+ * calls that overlap on the GPU (other streams or host threads) race with each
+ * other; serialise them.  Work is enqueued on `stream` on the current CUDA
+ * device.
  */
 filark_status filark_chain_run_static(const filark_chain_config *cfg, const float *d_in, int64_t ld_in,
                                       int64_t n_samples, float *d_ratio, float *d_bandpass,

@@ -12,6 +12,7 @@
 // holds it until the process exits.  All calls share it: each call clears what
 // must start at zero, and calls that overlap on the GPU (different streams,
 // or different host threads) race on it.
+#include <algorithm>
 #include <cstring>
 #include <mutex>
 #include <string>
@@ -25,10 +26,12 @@ constexpr size_t kStaticScratchBytes = size_t(32) << 20;
 
 static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
 
-constexpr int kMaxDevices = 64;
 std::mutex g_static_mu;
-void *g_static_ptr[kMaxDevices] = {};     // device address of g_static_scratch, per device
-bool g_static_configured[kMaxDevices] = {};
+
+bool ranges_overlap(const void *a, size_t an, const void *b, size_t bn) {
+    const char *pa = (const char *)a, *pb = (const char *)b;
+    return pa < pb + bn && pb < pa + an;
+}
 
 size_t align256(size_t b) { return (b + 255) / 256 * 256; }
 
@@ -69,6 +72,22 @@ extern "C" filark_status filark_chain_run_static(const filark_chain_config *cfg,
     if (ld_in < C) return fail(FILARK_EINVAL, "ld_in < n_channels");
     if ((d_ratio || d_bandpass || d_spatial) && ld_out < C) return fail(FILARK_EINVAL, "ld_out < n_channels");
     if (d_ratio && !det) return fail(FILARK_EINVAL, "ratio output needs the detector");
+    if (d_ratio && !(cfg->outputs & FILARK_OUT_RATIO)) return fail(FILARK_EINVAL, "ratio output not enabled");
+    if (d_bandpass && !(cfg->outputs & FILARK_OUT_BANDPASS))
+        return fail(FILARK_EINVAL, "bandpass output not enabled");
+    if (d_spatial && !(cfg->outputs & FILARK_OUT_SPATIAL)) return fail(FILARK_EINVAL, "spatial output not enabled");
+    if (n_samples > 0) {
+        const size_t in_bytes = sizeof(float) * (size_t)((n_samples - 1) * ld_in + C);
+        const size_t out_bytes = sizeof(float) * (size_t)((n_samples - 1) * std::max<int64_t>(ld_out, 0) + C);
+        const void *outs[3] = {d_ratio, d_bandpass, d_spatial};
+        for (int a = 0; a < 3; ++a) {
+            if (outs[a] && ranges_overlap(d_in, in_bytes, outs[a], out_bytes))
+                return fail(FILARK_EINVAL, "an output overlaps the input");
+            for (int b = a + 1; b < 3; ++b)
+                if (outs[a] && outs[b] && ranges_overlap(outs[a], out_bytes, outs[b], out_bytes))
+                    return fail(FILARK_EINVAL, "two outputs overlap");
+        }
+    }
     if (cfg->precision < FILARK_PREC_AUTO || cfg->precision > FILARK_PREC_ALL32)
         return fail(FILARK_EINVAL, "unknown precision mode");
 
@@ -95,25 +114,25 @@ extern "C" filark_status filark_chain_run_static(const filark_chain_config *cfg,
                     "array holds " + std::to_string(kStaticScratchBytes) + " (lower n_channels or lta_len)");
     if (n_samples == 0) return FILARK_OK;
 
-    int dev = -1;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices)
-        return fail(FILARK_ECUDA, "no current CUDA device");
+    // The array's device address and the kernels' attributes are taken on
+    // every call, on the current device: a cached address would outlive a
+    // cudaDeviceReset (the module, and the array with it, is loaded again in
+    // the new context).  Neither call allocates.
     char *base = nullptr;
     {
         std::lock_guard<std::mutex> lk(g_static_mu);
-        if (!g_static_ptr[dev]) {
-            void *ptr = nullptr;
-            cudaError_t e = cudaGetSymbolAddress(&ptr, g_static_scratch);
-            if (e != cudaSuccess || !ptr)
-                return fail(FILARK_ECUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
-            g_static_ptr[dev] = ptr;
+        void *ptr = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&ptr, g_static_scratch);
+        if (e != cudaSuccess || !ptr) {
+            cudaGetLastError();
+            return fail(FILARK_ECUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
         }
-        if (!g_static_configured[dev]) {
-            cudaError_t e = configure_chain_kernels();
-            if (e != cudaSuccess) return fail(FILARK_ECUDA, std::string("kernel attributes: ") + cudaGetErrorString(e));
-            g_static_configured[dev] = true;
+        e = configure_chain_kernels();
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return fail(FILARK_ECUDA, std::string("kernel attributes: ") + cudaGetErrorString(e));
         }
-        base = (char *)g_static_ptr[dev];
+        base = (char *)ptr;
     }
     cudaStream_t s = (cudaStream_t)stream;
     double *iir[2] = {(double *)base, (double *)(base + b_iir)};
