@@ -591,8 +591,8 @@ static long uf_find(long *parent, long i)
  * when their channels differ by one and their intervals share a sample.
  * ev receives 5 longs per event {t_on, t_off, c_min, c_max, n_triggers};
  * events are returned sorted by (t_on, c_min, t_off, c_max).  Returns the
- * number of events.  Only triggers of neighbouring channels are compared
- * (pairwise within the two channels), after grouping by channel. */
+ * number of events.  Every pair of triggers is tested (quadratic in n: the
+ * plain statement of the rule, kept for its clarity, not its speed). */
 static int ev_cmp(const void *a, const void *b)
 {
     const long *x = (const long *)a, *y = (const long *)b;
@@ -604,45 +604,21 @@ static int ev_cmp(const void *a, const void *b)
     return 0;
 }
 
-static const long *g_sort_c, *g_sort_on;
-static int idx_cmp(const void *a, const void *b)
-{
-    const long i = *(const long *)a, j = *(const long *)b;
-    if (g_sort_c[i] != g_sort_c[j]) return g_sort_c[i] < g_sort_c[j] ? -1 : 1;
-    if (g_sort_on[i] != g_sort_on[j]) return g_sort_on[i] < g_sort_on[j] ? -1 : 1;
-    return i < j ? -1 : (i > j);
-}
-
 long ora_events_merge(const long *rc, const long *ron, const long *roff, long n, long *ev)
 {
     long *parent = (long *)malloc(sizeof(long) * (size_t)(n > 0 ? n : 1));
-    long *ord = (long *)malloc(sizeof(long) * (size_t)(n > 0 ? n : 1));
     long *root_ev = (long *)malloc(sizeof(long) * (size_t)(n > 0 ? n : 1));
-    for (long i = 0; i < n; ++i) {
-        parent[i] = i;
-        ord[i] = i;
-    }
-    /* group the triggers by channel: only neighbouring channels can join */
-    g_sort_c = rc;
-    g_sort_on = ron;
-    qsort(ord, (size_t)n, sizeof(long), idx_cmp);
-    long next = 0;   /* start of the next channel's group in ord */
-    for (long a = 0; a < n; a = next) {
-        next = a;
-        while (next < n && rc[ord[next]] == rc[ord[a]]) ++next;
-        if (next >= n || rc[ord[next]] != rc[ord[a]] + 1) continue;
-        long end = next;
-        while (end < n && rc[ord[end]] == rc[ord[next]]) ++end;
-        for (long p = a; p < next; ++p)
-            for (long q = next; q < end; ++q) {
-                const long i = ord[p], j = ord[q];
-                const long lo = ron[i] > ron[j] ? ron[i] : ron[j];
-                const long hi = roff[i] < roff[j] ? roff[i] : roff[j];
-                if (lo >= hi) continue;
-                const long x = uf_find(parent, i), y = uf_find(parent, j);
-                if (x != y) parent[x < y ? y : x] = x < y ? x : y;
-            }
-    }
+    for (long i = 0; i < n; ++i) parent[i] = i;
+    for (long i = 0; i < n; ++i)
+        for (long j = i + 1; j < n; ++j) {
+            const long dc = rc[i] - rc[j];
+            if (dc != 1 && dc != -1) continue;
+            const long lo = ron[i] > ron[j] ? ron[i] : ron[j];
+            const long hi = roff[i] < roff[j] ? roff[i] : roff[j];
+            if (lo >= hi) continue;
+            const long x = uf_find(parent, i), y = uf_find(parent, j);
+            if (x != y) parent[x < y ? y : x] = x < y ? x : y;
+        }
     long m = 0;
     for (long i = 0; i < n; ++i)
         if (uf_find(parent, i) == i) {
@@ -660,7 +636,6 @@ long ora_events_merge(const long *rc, const long *ron, const long *roff, long n,
     }
     qsort(ev, (size_t)m, 5 * sizeof(long), ev_cmp);
     free(parent);
-    free(ord);
     free(root_ev);
     return m;
 }

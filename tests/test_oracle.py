@@ -96,8 +96,8 @@ MUTANTS = [
     ("trigger_no_hysteresis", "else if (r < t->off) s = 0;", "else s = 0;"),
     ("trigger_flush_end", "roff[k] = t->n;", "roff[k] = t->n - 1;"),
     ("events_touching_merge", "if (lo >= hi) continue;", "if (lo > hi) continue;"),
-    ("events_skip_a_channel", "if (next >= n || rc[ord[next]] != rc[ord[a]] + 1) continue;",
-     "if (next >= n || rc[ord[next]] != rc[ord[a]] + 2) continue;"),
+    ("events_skip_a_channel", "if (dc != 1 && dc != -1) continue;", "if (dc != 2 && dc != -2) continue;"),
+    ("events_one_side_only", "if (dc != 1 && dc != -1) continue;", "if (dc != 1) continue;"),
     ("fir_skip_current", "for (int k = 0; k < t->M; ++k) acc += t->h[k] * top_hist(t, c, n - k);",
      "for (int k = 0; k < t->M; ++k) acc += t->h[k] * top_hist(t, c, n - k - 1);"),
     ("window_exit_early", "const double old = top_hist(t, c, n - t->M);",
