@@ -54,23 +54,29 @@ def algorithmic_bytes_per_push(C: int, T: int, S: int, ns: int, nl: int) -> int:
 
 
 class ClockSampler:
-    """nvidia-smi sampling of SM clocks and throttle reasons while it runs."""
+    """nvidia-smi sampling of SM clocks and throttle reasons.  Start it before
+    the warm-up (nvidia-smi takes a moment to print its first line) and mark
+    the timed region with begin()/end(): the summary keeps the samples that
+    arrived inside it (host receive time)."""
 
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    PERIOD_MS = 20
 
     def __init__(self, gpu_index: int):
         self.gpu = gpu_index
         self.proc = None
-        self.lines: list[str] = []
+        self.lines: list[tuple[float, str]] = []
         self._t = None
+        self.t_begin = None
+        self.t_end = None
 
     def __enter__(self):
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+                 "-lms", str(self.PERIOD_MS)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self._t = threading.Thread(target=self._read, daemon=True)
             self._t.start()
         except (OSError, ValueError):
@@ -79,7 +85,13 @@ class ClockSampler:
 
     def _read(self):
         for line in self.proc.stdout:
-            self.lines.append(line.strip())
+            self.lines.append((time.perf_counter(), line.strip()))
+
+    def begin(self):
+        self.t_begin = time.perf_counter()
+
+    def end(self):
+        self.t_end = time.perf_counter()
 
     def __exit__(self, *exc):
         if self.proc is not None:
@@ -95,7 +107,12 @@ class ClockSampler:
     def summary(self) -> dict:
         sm, smax, reasons = [], None, set()
         names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
-        for ln in self.lines:
+        lo = self.t_begin if self.t_begin is not None else -float("inf")
+        # a line can lag its sample by up to one period
+        hi = (self.t_end + self.PERIOD_MS / 1e3) if self.t_end is not None else float("inf")
+        for t, ln in self.lines:
+            if not (lo <= t <= hi):
+                continue
             parts = [p.strip() for p in ln.split(",")]
             if len(parts) < 9:
                 continue
@@ -108,7 +125,7 @@ class ClockSampler:
                 if val.lower().startswith("active"):
                     reasons.add(name)
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
-                "reasons": sorted(reasons), "samples": len(sm)}
+                "reasons": sorted(reasons), "samples": len(sm), "period_ms": self.PERIOD_MS}
 
 
 def measured_peak_hbm() -> tuple[float, str]:
@@ -257,24 +274,24 @@ def run_gpu(args, rank: int, world: int, dist) -> None:
             abi.check(st, "join")
 
     torch.cuda.synchronize()
-    with torch.cuda.stream(stream):
-        for _ in range(args.warmup):
-            step()
-    torch.cuda.synchronize()
-    if dist:
-        dist.barrier()
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
     sampler = ClockSampler(local)
     with sampler:
+        with torch.cuda.stream(stream):
+            for _ in range(args.warmup):
+                step()
         torch.cuda.synchronize()
         if dist:
             dist.barrier()
+        torch.cuda.synchronize()
+        sampler.begin()
         ev0.record(stream)
         for _ in range(args.steps):
             step()
         ev1.record(stream)
         ev1.synchronize()
+        sampler.end()
     ms = max_over_ranks(ev0.elapsed_time(ev1), dist, dev)
     abi.check(abi.filark_chain_sync_status(h, sh), "sync")
     launches_per_push = (T + 2047) // 2048
@@ -282,27 +299,8 @@ def run_gpu(args, rank: int, world: int, dist) -> None:
     launches = args.steps * n_push * launches_per_push * lanes
     value = whole_job_rate(C * N * args.steps, world, ms / 1e3)
 
-    # ---- the same pushes in one lane: each push complete on `stream` when
-    # its launch ends (the stream-ordered mode, the API's default)
-    chain.set_lanes(1)
-    so_steps = max(3, min(args.steps, 20))
-    with torch.cuda.stream(stream):
-        for _ in range(3):
-            step()
-    torch.cuda.synchronize()
-    if dist:
-        dist.barrier()
-    ev2 = torch.cuda.Event(enable_timing=True)
-    ev3 = torch.cuda.Event(enable_timing=True)
-    ev2.record(stream)
-    for _ in range(so_steps):
-        step()
-    ev3.record(stream)
-    ev3.synchronize()
-    ms_so = max_over_ranks(ev2.elapsed_time(ev3), dist, dev)
-    so_value = whole_job_rate(C * N * so_steps, world, ms_so / 1e3)
-
-    # ---- end to end through the host-buffer entry point (pinned host memory)
+    # ---- end to end through the host-buffer entry point (pinned host memory),
+    # in the same lanes as the timed region
     e2e_steps = max(1, min(args.steps, 3))
     xh = torch.from_numpy(x_host).pin_memory()
     rh = torch.empty((N, C), dtype=torch.float32).pin_memory()
@@ -326,6 +324,27 @@ def run_gpu(args, rank: int, world: int, dist) -> None:
         step_host()
     e2e_s = max_over_ranks(time.perf_counter() - t0, dist, dev)
     e2e_value = whole_job_rate(C * N * e2e_steps, world, e2e_s)
+
+    # ---- the same pushes in one lane: each push complete on `stream` when
+    # its launch ends (the stream-ordered mode, the API's default)
+    chain.set_lanes(1)
+    so_steps = max(3, min(args.steps, 20))
+    with torch.cuda.stream(stream):
+        for _ in range(3):
+            step()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    ev2 = torch.cuda.Event(enable_timing=True)
+    ev3 = torch.cuda.Event(enable_timing=True)
+    ev2.record(stream)
+    for _ in range(so_steps):
+        step()
+    ev3.record(stream)
+    ev3.synchronize()
+    ms_so = max_over_ranks(ev2.elapsed_time(ev3), dist, dev)
+    so_value = whole_job_rate(C * N * so_steps, world, ms_so / 1e3)
+
     chain.close()
     link = host_link_rates(xh, rh, C * T)
 
@@ -369,6 +388,9 @@ def run_gpu(args, rank: int, world: int, dist) -> None:
             "completion": "each step's 60 pushes complete on the timing stream at the step's end (filark_chain_join)"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
+                     "traffic_source": ("ncu DRAM read + write of one push, profiles/chain_fwd_paper_scale_traffic.json "
+                                        "(taken on this kernel source; not measured in this run)")
+                     if traffic is not None else "no capture on this kernel source",
                      "frac_of_nominal": achieved / NOMINAL_HBM_GBS,
                      "unit_of_work": f"one push of {T} x {C} ({lanes} overlapping launches, one per lane)",
                      "bytes_per_push": bytes_push, "ms_per_push": ms_push},
@@ -378,7 +400,7 @@ def run_gpu(args, rank: int, world: int, dist) -> None:
                            "note": "every push complete on its stream when its launch ends"},
         "cpu_baseline": {"value": cpu_value, "unit": UNIT, "cores": cores, "kind": "oracle",
                          "sample": f"{C} channels x {cpu_push} pushes of {T} samples, FP64 oracle, {cores} threads"},
-        "e2e": {"value": e2e_value, "unit": UNIT, "lanes": 1, "h2d_bytes_per_step": 4 * C * N,
+        "e2e": {"value": e2e_value, "unit": UNIT, "lanes": lanes, "h2d_bytes_per_step": 4 * C * N,
                 "d2h_bytes_per_step": 4 * C * N,
                 # the host link's own rates on this machine, measured right after:
                 # the pipelined e2e moves 4 B in and 4 B out per channel-sample
