@@ -61,6 +61,7 @@ struct filark_batch {
     std::vector<int> order;
     std::vector<int> unit0, nunits;
     std::vector<double *> halo;   // per stream: [2][tiles][kWT][2*NS] tile-private IIR state
+    std::vector<double *> detx;   // per stream: [C][4] detector state between the units of one push
 };
 
 namespace {
@@ -83,6 +84,8 @@ void free_batch(filark_batch *b) {
         if (p) cudaFreeHost(p);
     if (b->d_desc) cudaFree(b->d_desc);
     for (double *p : b->halo)
+        if (p) cudaFree(p);
+    for (double *p : b->detx)
         if (p) cudaFree(p);
     for (filark_chain *h : b->chains) filark_chain_destroy(h);
     delete b;
@@ -148,6 +151,19 @@ int stage_push(filark_batch *b, int k, const filark_chunk_desc *d) {
         b->nunits[(size_t)i] = 0;
         const size_t hstride = (size_t)h->n_tiles * kWT * (size_t)(2 * b->NS);
         double *hs = b->halo[(size_t)i];
+        // Every unit of this push runs in the same launch, and a tile's first
+        // unit reads its halo columns from the neighbouring tiles' per-channel
+        // state iir[P0]; so no unit writes iir[P0]: the intermediate units
+        // carry the IIR state in the tile-private halo buffers only, the last
+        // writes iir[P0 ^ 1].  The detector state (each tile's own channels)
+        // steps through det[P0] -> ... -> det[P0 ^ 1], alternating with a
+        // spare buffer so that the last unit lands in det[P0 ^ 1].
+        const int P0 = h->parity;
+        const int n_u = (int)((c.n_samples + span - 1) / span);
+        auto det_buf = [&](int j) -> double * {
+            if (j == 0) return h->detst[P0];
+            return ((n_u - j) % 2 == 0) ? h->detst[P0 ^ 1] : b->detx[(size_t)i];
+        };
         for (int64_t done = 0; done < c.n_samples;) {
             const int Tl = (int)std::min<int64_t>(c.n_samples - done, span);
             const int j = b->nunits[(size_t)i];
@@ -164,10 +180,10 @@ int stage_push(filark_batch *b, int k, const filark_chunk_desc *d) {
             u.bp = c.d_bandpass ? c.d_bandpass + done * c.ld_out : nullptr;
             u.sp = c.d_spatial ? c.d_spatial + done * c.ld_out : nullptr;
             u.ldo = c.ld_out;
-            u.iir_in = h->iir[h->parity];
-            u.iir_out = h->iir[h->parity ^ 1];
-            u.det_in = h->detst[h->parity];
-            u.det_out = h->detst[h->parity ^ 1];
+            u.iir_in = h->iir[P0];
+            u.iir_out = j == n_u - 1 ? h->iir[P0 ^ 1] : nullptr;
+            u.det_in = det_buf(j);
+            u.det_out = det_buf(j + 1);
             u.n0 = h->n;
             set_unit_geometry(h->plan, Tl, kNB, u);
             u.slot_n0 = h->Q > 0 ? (int)(h->n % h->Q) : 0;
@@ -176,11 +192,11 @@ int stage_push(filark_batch *b, int k, const filark_chunk_desc *d) {
             for (float *o : {u.ratio, u.bp, u.sp})
                 if (o && ((uintptr_t)o & 15u)) ov = false;
             u.o_vec4 = ov;
-            h->parity ^= 1;
             h->n += Tl;
             done += Tl;
             b->nunits[(size_t)i]++;
         }
+        if (n_u > 0) h->parity = P0 ^ 1;
     }
     // longest chunk first, then stream order
     std::vector<int> &ord = b->order;
@@ -277,6 +293,17 @@ filark_status filark_batch_create(const filark_chain_config *cfg, int n_streams,
             b->device_bytes += (int64_t)bytes;
         }
         b->halo.push_back(hs);
+        double *dx = nullptr;
+        if (h->det) {
+            DeviceGuard g(cuda_device);
+            if (cudaMalloc(&dx, sizeof(double) * 4 * (size_t)h->C) != cudaSuccess) {
+                cudaGetLastError();
+                free_batch(b);
+                return fail_with(FILARK_ENOMEM, "batch create: detector state allocation");
+            }
+            b->device_bytes += (int64_t)(sizeof(double) * 4 * (size_t)h->C);
+        }
+        b->detx.push_back(dx);
         b->max_units += (std::min<int64_t>(cfg->max_chunk, INT32_MAX) + kTileRows - 1) / kTileRows;
         b->max_items += h->n_tiles;
     }

@@ -495,7 +495,7 @@ __device__ __forceinline__ void chain_body(const ChainParams &p, const ChainUnit
                 }
                 if (last_cta || j < nb - 1) dense_step<NS>(MV, cur, rag ? Ar : AL, c, r0, add, p.all32);
             }
-            if (last_cta && c >= p.HP && c < p.HP + p.Wout && cgs < cu.C) {
+            if (last_cta && cu.iir_out && c >= p.HP && c < p.HP + p.Wout && cgs < cu.C) {
 #pragma unroll
                 for (int t = 0; t < RT; ++t)
                     if (r0 + t < n)
@@ -580,7 +580,7 @@ __device__ __forceinline__ void chain_body(const ChainParams &p, const ChainUnit
                     u0 = DF{u0.hi, 0.f};
                     u1 = DF{u1.hi, 0.f};
                 }
-                if (own) {
+                if (own && cu.iir_out) {
                     float2 *dst = reinterpret_cast<float2 *>(cu.iir_out + (long long)cgs * (2 * NS));
                     dst[2 * s] = make_float2(u0.hi, u0.lo);
                     dst[2 * s + 1] = make_float2(u1.hi, u1.lo);

@@ -56,7 +56,8 @@ struct ChainUnit {
     // modal carries store double-float {hi, lo} float pairs, the dense carry
     // stores FP64
     const double *iir_in;
-    double *iir_out;
+    double *iir_out;                    // NULL: the owned channels' state is not written (a batched
+                                        // push's units before its last)
     const double *det_in;               // [C][4] {sta_sum, lta_sum, 1 + index of last nonzero cf (0 = none), 0}
     double *det_out;
     // Batched pushes run a stream's units back to back in one cluster, so a

@@ -118,6 +118,40 @@ def test_batch_bitwise_equals_single_chains(small_case):
             assert np.array_equal(o[k].cpu().numpy(), got[i][k]), (i, k)
 
 
+def test_batch_one_cluster_multi_unit_pushes(oracle_mod):
+    """One persistent cluster runs every item of a push one after another, so
+    a tile's later units finish before its neighbouring tile's first unit
+    reads the halo columns' carried state: pushes of 2,500..3,000 samples
+    (two units each) must still equal single-stream chains bit for bit, i.e.
+    no unit may overwrite the per-channel state that the first units of the
+    same launch read."""
+    import torch
+    from paper_2605_20132_gb300.chain import Batch, Chain
+    rng = np.random.default_rng(71)
+    Cs = [300, 130]
+    T = rng.integers(2500, 3001, (3, len(Cs)))
+    data = [synth.small_stream(C, int(T[:, i].sum()), seed=72 + i) for i, C in enumerate(Cs)]
+    sos = small_sos(oracle_mod)
+    b = Batch(Cs, sos, 1000.0, K, NS_, NL, outputs=ALL_OUT, max_chunk=3000)
+    b.set_launch(8, 1, True)
+    got = run_batch(b, data, T)
+    b.close()
+    for i, C in enumerate(Cs):
+        ch = Chain(C, sos, 1000.0, K, NS_, NL, outputs=ALL_OUT, max_chunk=3000)
+        ch.set_blocks_per_cta(8)
+        x = torch.from_numpy(data[i]).cuda()
+        o = {k: torch.empty(data[i].shape, device="cuda") for k in ("ratio", "bp", "sp")}
+        t = 0
+        for row in T:
+            n = int(row[i])
+            ch.push(x[t:t + n], ratio=o["ratio"][t:t + n], bandpass=o["bp"][t:t + n], spatial=o["sp"][t:t + n])
+            t += n
+        ch.sync()
+        ch.close()
+        for k in o:
+            assert np.array_equal(o[k].cpu().numpy(), got[i][k]), (i, k)
+
+
 def test_batch_tune_then_stream(small_case):
     """The tuner times every geometry, keeps the fastest, and leaves every
     stream reset: streaming afterwards starts from a zero state."""
