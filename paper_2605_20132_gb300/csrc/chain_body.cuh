@@ -51,6 +51,26 @@ __device__ __forceinline__ void cluster_sync_release_acquire() {
     asm volatile("barrier.cluster.wait.acquire.aligned;\n" ::: "memory");
 }
 
+// The two halves of a cluster barrier, for work in between: arrive (release:
+// this CTA's earlier writes become visible to the cluster; relaxed: no
+// ordering) and wait (acquire).  Every thread of the CTA executes each.
+__device__ __forceinline__ void cluster_arrive_release() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n" ::: "memory");
+}
+__device__ __forceinline__ void cluster_arrive_relaxed() {
+    asm volatile("barrier.cluster.arrive.relaxed.aligned;\n" ::: "memory");
+}
+__device__ __forceinline__ void cluster_wait_acquire() {
+    asm volatile("barrier.cluster.wait.acquire.aligned;\n" ::: "memory");
+}
+
+// 1 / x to about one ulp (the hardware approximation, subnormals flushed)
+__device__ __forceinline__ float rcp_approx(float x) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
 __device__ __forceinline__ void pdl_launch_dependents() {
     asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
 }
@@ -536,7 +556,22 @@ __device__ __forceinline__ void chain_body(const ChainParams &p, const ChainUnit
             AGG[(2 * s) * kWT + sc] = a0;
             AGG[(2 * s + 1) * kWT + sc] = a1;
         }
-        cluster_sync_release_acquire();
+        // publish the aggregates; meanwhile read the launch's carried state
+        // (double-float hi/lo pairs) of this thread's slot
+        static_assert(NS <= kSlotStep, "one slot per thread");
+        cluster_arrive_release();
+        float2 c0 = make_float2(0.f, 0.f), c1 = make_float2(0.f, 0.f);
+        {
+            const int s = tid / kWT, cgs = cbase + sc;
+            if (s < NS && cgs >= 0 && cgs < cu.C) {
+                const float2 *src = reinterpret_cast<const float2 *>(
+                    cu.halo_in ? cu.halo_in + ((long long)tx * kWT + sc) * (2 * NS)
+                               : cu.iir_in + (long long)cgs * (2 * NS));
+                c0 = src[2 * s];
+                c1 = src[2 * s + 1];
+            }
+        }
+        cluster_wait_acquire();
         for (int s = tid / kWT; s < NS; s += kSlotStep) {
             const int cgs = cbase + sc;
             // earlier CTAs of the cluster: g = sum_q Phi^(r-1-q) agg_q, each
@@ -549,16 +584,8 @@ __device__ __forceinline__ void chain_body(const ChainParams &p, const ChainUnit
                 g0 = fmaf(Pq[0], a0, fmaf(Pq[1], a1, g0));
                 g1 = fmaf(Pq[2], a0, fmaf(Pq[3], a1, g1));
             }
-            // carried state of the launch (double-float hi/lo pairs); the
-            // start of this CTA, Phi^r c + g, only feeds the FP32 block carries
-            float2 c0 = make_float2(0.f, 0.f), c1 = make_float2(0.f, 0.f);
-            if (cgs >= 0 && cgs < cu.C) {
-                const float2 *src = reinterpret_cast<const float2 *>(
-                    cu.halo_in ? cu.halo_in + ((long long)tx * kWT + sc) * (2 * NS)
-                               : cu.iir_in + (long long)cgs * (2 * NS));
-                c0 = src[2 * s];
-                c1 = src[2 * s + 1];
-            }
+            // the start of this CTA, Phi^r c + g, only feeds the FP32 block
+            // carries
             const float *Pr = p.PhiPow32[r][s];
             const float d0 = fmaf(Pr[0], c0.x, fmaf(Pr[1], c1.x, g0));
             const float d1 = fmaf(Pr[2], c0.x, fmaf(Pr[3], c1.x, g1));
@@ -833,6 +860,9 @@ __device__ __forceinline__ void chain_body(const ChainParams &p, const ChainUnit
             }
         }
         __syncthreads();
+        // every read of another CTA's shared memory is done: the closing
+        // cluster barrier's arrive (its wait is at the end of the body)
+        cluster_arrive_relaxed();
         // pass b: running sums inside the block, ratio
         if (dact) {
             float fs = BS[jb * kWT + col].hi + BS[jb * kWT + col].lo;
@@ -858,7 +888,7 @@ __device__ __forceinline__ void chain_body(const ChainParams &p, const ChainUnit
                         const float cf = tile[(rbeg + kb + u) * kWT + col];
                         fs += cf - vs[u];
                         fl += cf - vl[u];
-                        rq[(long long)u * cu.ldo] = __fdividef(fs * scale, fl);
+                        rq[(long long)u * cu.ldo] = (fs * scale) * rcp_approx(fl);
                     }
                 }
             } else {
@@ -875,7 +905,7 @@ __device__ __forceinline__ void chain_body(const ChainParams &p, const ChainUnit
                         fl += cf - vl[u];
                         lz = cf != 0.f ? row : lz;
                         const bool valid = (row >= warm) & (lz > row - p.nl);
-                        const float Rv = valid ? __fdividef(fs * scale, fl) : 0.f;
+                        const float Rv = valid ? (fs * scale) * rcp_approx(fl) : 0.f;
                         if (rp && row < rows) rp[(long long)(kb + u) * cu.ldo] = Rv;
                     }
                 }
@@ -883,7 +913,8 @@ __device__ __forceinline__ void chain_body(const ChainParams &p, const ChainUnit
         }
     }
     // no CTA may exit while a peer can still read its shared memory
-    if (NS > 0 || DET) cluster_sync_release_acquire();
+    if constexpr (DET) cluster_wait_acquire();
+    else if (NS > 0) cluster_sync_release_acquire();
 }
 
 template <int NS, bool DET>
