@@ -601,6 +601,59 @@ def run_adjoint_workload(args) -> None:
     print(json.dumps(line), flush=True)
 
 
+def run_precision_workload(args) -> None:
+    """The precision-stress shape: order-8 Butterworth 0.01-1 Hz at 1.5 kHz
+    (poles within 1e-4 of z = 1) on 10,000 channels, pushes of 1,500 samples,
+    bandpass output (N(0,1) noise plus a 0.05 Hz sine generated on the device,
+    16 pushes = 960 MB per step, larger than L2).  The planner's choice (the
+    dense double-float carry for this filter) against the modal FP32 carry and the
+    all-FP32 carry forced on the same filter; their accuracy over the whole
+    600 s record is in profiles/precision_stress_10000ch_600s.md."""
+    import torch
+
+    from paper_2605_20132_gb300 import abi, synth
+    from paper_2605_20132_gb300.chain import Chain, butter_bandpass
+    cfg = synth.PRECISION
+    C, T, P = cfg["n_channels"], cfg["chunk"], 16
+    sos = butter_bandpass(cfg["order"], *cfg["band"], cfg["fs"])
+    g = torch.Generator(device="cuda").manual_seed(cfg["seed"])
+    x = torch.randn((T * P, C), device="cuda", generator=g)
+    t = torch.arange(T * P, device="cuda", dtype=torch.float64).unsqueeze(1) / cfg["fs"]
+    ph = torch.rand((1, C), device="cuda", generator=g, dtype=torch.float64) * 2 * np.pi
+    x += (cfg["sine_amp"] * torch.sin(2 * np.pi * cfg["sine_hz"] * t + ph)).float()
+    del t
+    y = torch.empty_like(x)
+    peak, peak_kind = measured_peak_hbm()
+    rows = []
+    for name, prec in [("planner", abi.FILARK_PREC_AUTO), ("modal32", abi.FILARK_PREC_MODAL32),
+                       ("all32", abi.FILARK_PREC_ALL32)]:
+        try:
+            ch = Chain(C, sos, cfg["fs"], 1, 0, 0, outputs=abi.FILARK_OUT_BANDPASS, precision=prec, max_chunk=T)
+        except abi.FilarkError as e:
+            rows.append({"mode": name, "unavailable": str(e)})
+            continue
+        mode = {1: "modal32", 2: "dense64", 3: "all32"}.get(ch.info()["precision"], "?")
+
+        def step():
+            for i in range(P):
+                ch.push(x[i * T:(i + 1) * T], bandpass=y[i * T:(i + 1) * T])
+
+        for _ in range(max(args.warmup, 3)):
+            step()
+        ms = _event_ms(step, args.steps)
+        ch.close()
+        # input read + bandpass written + the carried state read and written
+        byts = 8.0 * C * T * P + 2 * 2 * 8.0 * 2 * sos.shape[0] * C * P
+        rows.append({"mode": name, "carry": mode, "channel_samples_per_s": C * T * P / (ms / 1e3),
+                     "us_per_push": 1e3 * ms / P, "frac_of_hbm": byts / (ms / 1e3) / 1e9 / peak})
+    print(json.dumps({
+        "workload": "precision-stress-10000ch-1500Hz", "metric": "channel-samples/s of the bandpass (device-timed)",
+        "rows": rows, "peak_gbs": peak, "peak_kind": peak_kind, "steps": args.steps, "pushes_per_step": P,
+        "dtype": "f32 scan, carries as named", "data": "synthetic N(0,1) + 0.05 Hz sine on the device",
+        "config": {"channels": C, "chunk": T, "fs": cfg["fs"], "sections": int(sos.shape[0]),
+                   "band": list(cfg["band"])}}), flush=True)
+
+
 def run_trigger_workload(args) -> None:
     """Triggers (hysteresis 6 / 2) on the paper-scale chain's ratio, 60 pushes
     of 1,500 samples x 6,000 channels, and the event merge of all of them."""
@@ -828,7 +881,8 @@ def main() -> None:
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="filark", choices=["filark", "reference"])
     ap.add_argument("--ncu-case", action="store_true", help="run the small profiling case only")
-    ap.add_argument("--workload", default="chain", choices=["chain", "batch", "adjoint", "trigger", "ops", "waves"],
+    ap.add_argument("--workload", default="chain",
+                    choices=["chain", "batch", "adjoint", "trigger", "ops", "waves", "precision"],
                     help="chain: the paper-scale chain (the benchmark line); the others print their own line")
     args = ap.parse_args()
     if args.ncu_case:
@@ -839,7 +893,7 @@ def main() -> None:
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
         {"batch": run_batch_workload, "adjoint": run_adjoint_workload,
          "trigger": run_trigger_workload, "ops": run_ops_workload,
-         "waves": run_waves_workload}[args.workload](args)
+         "waves": run_waves_workload, "precision": run_precision_workload}[args.workload](args)
         return
     args.warmup = max(args.warmup, 3) if args.impl == "filark" else args.warmup
     world = int(os.environ.get("WORLD_SIZE", "1"))

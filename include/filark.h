@@ -76,8 +76,10 @@ enum {
     FILARK_PREC_AUTO = 0,      /* planner picks and verifies a mode          */
     FILARK_PREC_MODAL32 = 1,   /* per-pole 2x2 carries in FP32, FP64 across
                                   thread blocks and chunks                   */
-    FILARK_PREC_DENSE64 = 2,   /* dense carry in FP64 (poles very near 1 or
-                                  repeated poles)                            */
+    FILARK_PREC_DENSE64 = 2,   /* dense carry in the cascade's own basis,
+                                  double-float (~48-bit) arithmetic at every
+                                  block, FP64 between chunks (poles very
+                                  near 1 or repeated poles)                  */
     FILARK_PREC_ALL32 = 3      /* modal carries in FP32 everywhere, including
                                   the state kept between chunks (comparison
                                   only)                                      */
@@ -290,7 +292,7 @@ filark_status filark_butter_bandpass_sos(int order, double f1, double f2, double
  * Every call looks up the array's device address and sets the kernels'
  * attributes on the current device (neither allocates); the first call on a
  * device also loads the library's device code there, so make that first call
- * before any stream capture.  When the plan uses the dense FP64 carry
+ * before any stream capture.  When the plan uses the dense carry
  * (FILARK_PREC_DENSE64, or FILARK_PREC_AUTO for poles very close to z = 1, see
  * filark_chain_get_info of an equivalent chain), the call copies the carry
  * matrices from host memory and waits for `stream` before it returns.  All

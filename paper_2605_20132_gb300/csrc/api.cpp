@@ -391,8 +391,8 @@ filark_status filark_chain_create(const filark_chain_config *cfg, int cuda_devic
         ok = alloc((void **)&h->ring, sizeof(float) * (size_t)h->Q * (size_t)h->ldr);
     }
     if (ok && h->plan.dense) {
-        ok = alloc((void **)&h->dense, sizeof(double) * h->plan.dense_mats.size());
-        if (ok && cudaMemcpy(h->dense, h->plan.dense_mats.data(), sizeof(double) * h->plan.dense_mats.size(),
+        ok = alloc((void **)&h->dense, sizeof(float) * h->plan.dense_mats.size());
+        if (ok && cudaMemcpy(h->dense, h->plan.dense_mats.data(), sizeof(float) * h->plan.dense_mats.size(),
                              cudaMemcpyHostToDevice) != cudaSuccess) {
             cudaGetLastError();
             ok = false;

@@ -132,11 +132,11 @@ constexpr int kEFloats = kNB * 2 * kMaxSlots * kWT;          // 8192
 constexpr int kERFloats = 2 * kMaxSlots * kWT;               // 1024
 constexpr int kAggFloats = 2 * kMaxSlots * kWT;              // 1024 (also holds 3 x 64 doubles)
 constexpr int kSmemFloats = kTileFloats + kEFloats + kERFloats + kAggFloats;
-// the dense carry needs an FP64 aggregate [16][kWT] (in place of AGG) and a
-// double-buffered FP64 state [2][16][kWT] after it
+// the dense carry needs a double-float aggregate [16][kWT] in place of AGG
+// (its running state lives in registers)
 constexpr int kAggDenseFloats = kDenseDim * kWT * 2;          // 2048
-constexpr int kMVFloats = 2 * kDenseDim * kWT * 2;            // 4096
-constexpr int kSmemFloatsDense = kTileFloats + kEFloats + kERFloats + kAggDenseFloats + kMVFloats;
+constexpr int kSmemFloatsDense = kTileFloats + kEFloats + kERFloats + kAggDenseFloats;
+static_assert(2 * (kSmemFloatsDense * 4 + 1024) <= 228 * 1024, "two dense CTAs per SM");
 
 // detector overlays on the E region (free after the IIR fix-up); offsets in floats
 constexpr int kDetDS = 0;                                    // DF [kNB][kWT]
@@ -268,39 +268,72 @@ __device__ __forceinline__ void spatial_rows_generic(const ChainParams &p, const
     store_cf_in_place<DET>(tile, ro, rows, q0, gact, cfv);
 }
 
-// One step of the dense carry for the column c and the rows r0, r0+1 this
-// thread owns: out = Mx * MV[cur] + add, written to MV[cur ^ 1].  All threads
-// of the block call it (it ends with a barrier).
-// rows of the dense state owned by one thread
-template <int NS>
-__host__ __device__ constexpr int dense_rows_per_thread() {
-    return (2 * NS + kThreads / kWT - 1) / (kThreads / kWT);
+// Dense carry.  The state of one tile column (n = 2NS rows in the canonical
+// basis) is held as double-float pairs by 8 lanes of one warp: lane w < NS
+// holds rows w and n-1-w (lanes w >= NS hold zeros).  The transition powers
+// are block lower triangular, so row w < NS needs the state rows q < NS and
+// row n-1-w all n of them: 3NS products per lane and step, whatever w is.
+struct DenseRows {
+    DF lo, hi;   // rows w and n-1-w
+};
+
+// s + t += m * v for double-float m and v, the sum kept unnormalised: the
+// leading products are split exactly (TwoProduct by FMA) and summed exactly
+// (TwoSum) into s; their rounding errors and the cross terms go into t, as in
+// the compensated dot product of Ogita, Rump and Oishi (2005).  The _rn forms
+// keep the compiler from fusing the steps whose rounding is meant.
+__device__ __forceinline__ void df_dot_step(float &s, float &t, float mh, float ml, float vh, float vl) {
+    const float p = __fmul_rn(mh, vh);
+    const float pe = fmaf(mh, vh, -p);
+    const float s2 = __fadd_rn(s, p);
+    const float bb = __fsub_rn(s2, s);
+    const float err = __fadd_rn(__fsub_rn(s, __fsub_rn(s2, bb)), __fsub_rn(p, bb));
+    t = fmaf(mh, vl, t);
+    t = fmaf(ml, vh, t);
+    t = __fadd_rn(t, __fadd_rn(pe, err));
+    s = s2;
+}
+__device__ __forceinline__ DF df_norm(float s, float t) {
+    const float hi = __fadd_rn(s, t);
+    return DF{hi, __fsub_rn(t, __fsub_rn(hi, s))};
+}
+__device__ __forceinline__ DF df_from_double(double v) {
+    const float hi = __double2float_rn(v);
+    return DF{hi, __double2float_rn(v - (double)hi)};
 }
 
+// One step of the dense carry for the 8 lanes of a column: state <- Mx state
+// + add, Mx one matrix in the lane layout [n][8] float4 (row w: hi, lo; row
+// n-1-w: hi, lo).  The state rows travel by warp shuffles; every lane of the
+// warp executes it.  With all32 the result is rounded to FP32 (comparison).
 template <int NS>
-__device__ __forceinline__ void dense_step(double *MV, int &cur, const double *Mx, int c, int r0,
-                                           const double (&add)[dense_rows_per_thread<NS>()], bool all32) {
+__device__ __forceinline__ void dense_step(const float4 *__restrict__ Mx, DenseRows &st, DF add_lo, DF add_hi,
+                                           int w, int lane_base, bool all32) {
     constexpr int n = 2 * NS;
-    constexpr int RT = dense_rows_per_thread<NS>();
-    if (r0 < n) {
-        const double *v = MV + (size_t)cur * kDenseDim * kWT;
-        double a[RT];
-#pragma unroll
-        for (int t = 0; t < RT; ++t) a[t] = add[t];
-#pragma unroll
-        for (int q = 0; q < n; ++q) {
-            const double vq = v[q * kWT + c];
-#pragma unroll
-            for (int t = 0; t < RT; ++t)
-                if (r0 + t < n) a[t] = fma(__ldg(Mx + (size_t)(r0 + t) * kDenseDim + q), vq, a[t]);
-        }
-        double *o = MV + (size_t)(cur ^ 1) * kDenseDim * kWT;
-#pragma unroll
-        for (int t = 0; t < RT; ++t)
-            if (r0 + t < n) o[(r0 + t) * kWT + c] = all32 ? (double)(float)a[t] : a[t];
+    float sl = add_lo.hi, tl = add_lo.lo, sh = add_hi.hi, th = add_hi.lo;
+    // state rows q < NS are the lanes' first rows, q >= NS their second ones
+#pragma unroll 4
+    for (int q = 0; q < NS; ++q) {
+        const float vh = __shfl_sync(0xffffffffu, st.lo.hi, lane_base + q);
+        const float vl = __shfl_sync(0xffffffffu, st.lo.lo, lane_base + q);
+        const float4 m = __ldg(Mx + q * 8 + w);
+        df_dot_step(sh, th, m.z, m.w, vh, vl);
+        df_dot_step(sl, tl, m.x, m.y, vh, vl);
     }
-    cur ^= 1;
-    __syncthreads();
+    const float2 *Mh = reinterpret_cast<const float2 *>(Mx);
+#pragma unroll 4
+    for (int q = NS; q < n; ++q) {
+        const float vh = __shfl_sync(0xffffffffu, st.hi.hi, lane_base + n - 1 - q);
+        const float vl = __shfl_sync(0xffffffffu, st.hi.lo, lane_base + n - 1 - q);
+        const float2 m = __ldg(Mh + (q * 8 + w) * 2 + 1);
+        df_dot_step(sh, th, m.x, m.y, vh, vl);
+    }
+    st.lo = df_norm(sl, tl);
+    st.hi = df_norm(sh, th);
+    if (all32) {
+        st.lo.lo = 0.f;
+        st.hi.lo = 0.f;
+    }
 }
 
 // The work of one CTA: time range r (its rank in the cluster) of channel tile
@@ -432,102 +465,79 @@ __device__ __forceinline__ void chain_body(const ChainParams &p, const ChainUnit
     if constexpr (NS > 0) {
         // ------------------------------------------------ 2. carry scan
         if constexpr (DENSE) {
-            // canonical basis, FP64 carry at every block; thread (c, rp) owns
-            // state rows rp*RT .. rp*RT+RT-1 of column c
+            // canonical basis, double-float carry at every block; lanes
+            // 8k..8k+7 of warp v hold column 4v + k
             constexpr int n = 2 * NS;
-            constexpr int RT = dense_rows_per_thread<NS>();
-            double *AGGD = reinterpret_cast<double *>(AGG);                        // [16][kWT]
-            double *MV = AGGD + kDenseDim * kWT;                                   // [2][16][kWT]
-            const int c = tid % kWT, rp = tid / kWT, r0 = rp * RT;
+            constexpr int kMat = kDenseDim * 8;                                   // float4 per matrix
+            DF *AGGD = reinterpret_cast<DF *>(AGG);                               // [n][kWT]
+            const int w = lane & 7, lane_base = lane & ~7;
+            const int c = (warp << 2) | (lane >> 3);
+            const bool act = w < NS;
+            const int rlo = act ? w : 0, rhi = act ? n - 1 - w : 0;
             const int cgs = cbase + c;
             const bool ragged_last = last_cta && cu.Lr < kL;
-            const double *AL = p.dense + (size_t)(kL - 1) * kDenseDim * kDenseDim;
-            const double *Ar = p.dense + (size_t)(cu.Lr - 1) * kDenseDim * kDenseDim;
-            const double *Phi = p.dense + (size_t)(kL + 1) * kDenseDim * kDenseDim;
-            const double *PhiR = p.dense + (size_t)(kL + r) * kDenseDim * kDenseDim;
-            int cur = 0;
-            double add[RT];
-            auto set_rows = [&](const double (&v)[RT]) {
-#pragma unroll
-                for (int t = 0; t < RT; ++t)
-                    if (r0 + t < n) MV[(size_t)cur * kDenseDim * kWT + (r0 + t) * kWT + c] = v[t];
-            };
-            auto get_rows = [&](double (&v)[RT]) {
-#pragma unroll
-                for (int t = 0; t < RT; ++t)
-                    v[t] = r0 + t < n ? MV[(size_t)cur * kDenseDim * kWT + (r0 + t) * kWT + c] : 0.0;
-            };
-#pragma unroll
-            for (int t = 0; t < RT; ++t) add[t] = 0.0;
+            const float4 *Md = reinterpret_cast<const float4 *>(p.dense);
+            const float4 *AL = Md + (kL - 1) * kMat;
+            const float4 *Ar = Md + (cu.Lr - 1) * kMat;
+            const float4 *Phi = Md + (kL + 1) * kMat;
+            const float4 *PhiR = Md + (kL + r) * kMat;
+            const DF zero{0.f, 0.f};
+            DenseRows st{zero, zero};
             // (a) aggregate of this CTA from a zero start (not needed by the last)
-            set_rows(add);
-            __syncthreads();
             if (!last_cta) {
                 for (int j = 0; j < nb; ++j) {
-#pragma unroll
-                    for (int t = 0; t < RT; ++t)
-                        add[t] = r0 + t < n ? (double)E[(j * 2 * NS + r0 + t) * kWT + c] : 0.0;
-                    dense_step<NS>(MV, cur, AL, c, r0, add, p.all32);
+                    const DF al{act ? E[(j * n + rlo) * kWT + c] : 0.f, 0.f};
+                    const DF ah{act ? E[(j * n + rhi) * kWT + c] : 0.f, 0.f};
+                    dense_step<NS>(AL, st, al, ah, w, lane_base, p.all32);
                 }
-                get_rows(add);
-#pragma unroll
-                for (int t = 0; t < RT; ++t)
-                    if (r0 + t < n) AGGD[(r0 + t) * kWT + c] = add[t];
+                if (act) {
+                    AGGD[rlo * kWT + c] = st.lo;
+                    AGGD[rhi * kWT + c] = st.hi;
+                }
             }
             cluster_sync_release_acquire();
             // (b) g = sum over earlier CTAs q of Phi^(r-1-q) agg_q
-#pragma unroll
-            for (int t = 0; t < RT; ++t) add[t] = 0.0;
-            set_rows(add);
-            __syncthreads();
+            st = DenseRows{zero, zero};
             for (int q = 0; q < r; ++q) {
-                const double *ragg = cluster.map_shared_rank(AGGD, q);
-#pragma unroll
-                for (int t = 0; t < RT; ++t) add[t] = r0 + t < n ? ragg[(r0 + t) * kWT + c] : 0.0;
-                dense_step<NS>(MV, cur, Phi, c, r0, add, p.all32);
+                const DF *ragg = cluster.map_shared_rank(AGGD, q);
+                const DF al = act ? ragg[rlo * kWT + c] : zero;
+                const DF ah = act ? ragg[rhi * kWT + c] : zero;
+                dense_step<NS>(Phi, st, al, ah, w, lane_base, p.all32);
             }
-            double g[RT];
-            get_rows(g);
-            __syncthreads();
-            // (c) state at this CTA's start: Phi^r s_launch + g
+            const DenseRows g = st;
+            // (c) state at this CTA's start: Phi^r s_launch + g (FP64 in memory)
             {
-                double sv[RT];
-                const double *src = cu.halo_in ? cu.halo_in + ((long long)tx * kWT + c) * (2 * NS)
-                                               : cu.iir_in + (long long)cgs * (2 * NS);
-#pragma unroll
-                for (int t = 0; t < RT; ++t)
-                    sv[t] = (r0 + t < n && cgs >= 0 && cgs < cu.C) ? src[r0 + t] : 0.0;
-                set_rows(sv);
-                __syncthreads();
-                dense_step<NS>(MV, cur, PhiR, c, r0, g, p.all32);
+                const double *src = cu.halo_in ? cu.halo_in + ((long long)tx * kWT + c) * n
+                                               : cu.iir_in + (long long)cgs * n;
+                const bool ok = act && cgs >= 0 && cgs < cu.C;
+                st.lo = ok ? df_from_double(src[rlo]) : zero;
+                st.hi = ok ? df_from_double(src[rhi]) : zero;
+                dense_step<NS>(PhiR, st, g.lo, g.hi, w, lane_base, p.all32);
             }
             // (d) block start states (FP32 into E) and, in the last CTA, the end state
             for (int j = 0; j < nb; ++j) {
                 const bool rag = ragged_last && j == nb - 1;
-#pragma unroll
-                for (int t = 0; t < RT; ++t) {
-                    add[t] = 0.0;
-                    if (r0 + t < n) {
-                        float *pe = &E[(j * 2 * NS + r0 + t) * kWT + c];
-                        add[t] = rag ? (double)ER[(r0 + t) * kWT + c] : (double)*pe;
-                        *pe = (float)MV[(size_t)cur * kDenseDim * kWT + (r0 + t) * kWT + c];
-                    }
+                DF al = zero, ah = zero;
+                if (act) {
+                    float *pl = &E[(j * n + rlo) * kWT + c], *ph = &E[(j * n + rhi) * kWT + c];
+                    al.hi = rag ? ER[rlo * kWT + c] : *pl;
+                    ah.hi = rag ? ER[rhi * kWT + c] : *ph;
+                    *pl = st.lo.hi;
+                    *ph = st.hi.hi;
                 }
-                if (last_cta || j < nb - 1) dense_step<NS>(MV, cur, rag ? Ar : AL, c, r0, add, p.all32);
+                if (last_cta || j < nb - 1) dense_step<NS>(rag ? Ar : AL, st, al, ah, w, lane_base, p.all32);
             }
-            if (last_cta && cu.iir_out && c >= p.HP && c < p.HP + p.Wout && cgs < cu.C) {
-#pragma unroll
-                for (int t = 0; t < RT; ++t)
-                    if (r0 + t < n)
-                        cu.iir_out[(long long)cgs * (2 * NS) + r0 + t] =
-                            MV[(size_t)cur * kDenseDim * kWT + (r0 + t) * kWT + c];
-            }
-            if (last_cta && cu.halo_out && cgs >= 0 && cgs < cu.C) {
-#pragma unroll
-                for (int t = 0; t < RT; ++t)
-                    if (r0 + t < n)
-                        cu.halo_out[((long long)tx * kWT + c) * (2 * NS) + r0 + t] =
-                            MV[(size_t)cur * kDenseDim * kWT + (r0 + t) * kWT + c];
+            if (last_cta && act && cgs >= 0 && cgs < cu.C) {
+                const double vlo = (double)st.lo.hi + (double)st.lo.lo;
+                const double vhi = (double)st.hi.hi + (double)st.hi.lo;
+                if (cu.iir_out && c >= p.HP && c < p.HP + p.Wout) {
+                    cu.iir_out[(long long)cgs * n + rlo] = vlo;
+                    cu.iir_out[(long long)cgs * n + rhi] = vhi;
+                }
+                if (cu.halo_out) {
+                    cu.halo_out[((long long)tx * kWT + c) * n + rlo] = vlo;
+                    cu.halo_out[((long long)tx * kWT + c) * n + rhi] = vhi;
+                }
             }
         } else {
         const int sc = tid % kWT;

@@ -29,7 +29,7 @@ struct filark_chain {
     cudaEvent_t ev_in[FILARK_HOST_SLOTS] = {}, ev_comp[FILARK_HOST_SLOTS] = {}, ev_out[FILARK_HOST_SLOTS] = {};
     bool slot_used[FILARK_HOST_SLOTS] = {};
     int aslot = 0;
-    double *dense = nullptr;      // dense carry matrices (device)
+    float *dense = nullptr;       // dense carry matrices (device)
     filark::ChainParams base{};
     int64_t device_bytes = 0;
     int use_pdl = 1;

@@ -107,7 +107,7 @@ extern "C" filark_status filark_chain_run_static(const filark_chain_config *cfg,
     const size_t b_iir = align256(sizeof(double) * (size_t)C * (size_t)(2 * NS));
     const size_t b_det = align256(sizeof(double) * (size_t)C * 4);
     const size_t b_ring = det ? align256(sizeof(float) * (size_t)Q * (size_t)ldr) : 0;
-    const size_t b_dense = plan.dense ? align256(sizeof(double) * plan.dense_mats.size()) : 0;
+    const size_t b_dense = plan.dense ? align256(sizeof(float) * plan.dense_mats.size()) : 0;
     const size_t need = 2 * b_iir + 2 * b_det + b_ring + b_dense;
     if (need > kStaticScratchBytes || (double)Q * (double)ldr >= 2147483647.0)
         return fail(FILARK_EINVAL, "recording needs " + std::to_string(need) + " bytes of working memory; the static "
@@ -138,12 +138,12 @@ extern "C" filark_status filark_chain_run_static(const filark_chain_config *cfg,
     double *iir[2] = {(double *)base, (double *)(base + b_iir)};
     double *dst[2] = {(double *)(base + 2 * b_iir), (double *)(base + 2 * b_iir + b_det)};
     float *ring = det ? (float *)(base + 2 * b_iir + 2 * b_det) : nullptr;
-    double *dense = plan.dense ? (double *)(base + 2 * b_iir + 2 * b_det + b_ring) : nullptr;
+    float *dense = plan.dense ? (float *)(base + 2 * b_iir + 2 * b_det + b_ring) : nullptr;
     // zero state (the ring needs no clearing: every value read was written
     // earlier in this call, or lies before the first sample and reads as 0)
     cudaError_t e = cudaMemsetAsync(base, 0, 2 * b_iir + 2 * b_det, s);
     if (e == cudaSuccess && dense)
-        e = cudaMemcpyAsync(dense, plan.dense_mats.data(), sizeof(double) * plan.dense_mats.size(),
+        e = cudaMemcpyAsync(dense, plan.dense_mats.data(), sizeof(float) * plan.dense_mats.size(),
                             cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess && dense) e = cudaStreamSynchronize(s);   // the host copy source is pageable
     if (e != cudaSuccess) return fail(FILARK_ECUDA, std::string("scratch clear: ") + cudaGetErrorString(e));

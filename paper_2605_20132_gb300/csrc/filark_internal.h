@@ -92,8 +92,10 @@ struct ChainParams {
     int all32;                          // keep carries in FP32 everywhere (comparison)
     int pdl;                            // launched with programmatic stream serialization
     // dense carry (FILARK_PREC_DENSE64, or ALL32 without a modal basis):
-    // [kDenseMats][16][16] FP64, entries 0..31 = A^1..A^32, 32..39 = Phi^0..Phi^7
-    const double *dense;
+    // matrices 0..31 = A^1..A^32, 32..39 = Phi^0..Phi^7, each as double-float
+    // entries in the lane layout [kDenseDim][8] float4 (plan.cpp,
+    // dense_lane_layout)
+    const float *dense;
     ChainUnit u;                        // the launch (single-stream kernel)
 };
 
@@ -110,9 +112,9 @@ struct Plan {
     int S = 0;                // sections
     int NS = 0;               // slots the kernel runs (S padded to 2, 4 or 8; 0 = no IIR)
     int mode = FILARK_PREC_MODAL32;
-    bool dense = false;       // dense FP64 carry in the canonical basis
+    bool dense = false;       // dense double-float carry in the canonical basis
     // dense matrices (see ChainParams::dense), host copy
-    std::vector<double> dense_mats;
+    std::vector<float> dense_mats;
     double kappa = 0.0;       // condition number estimate of the modal basis
     double probe_err = 0.0;   // FP32 emulation error on the probe signal
     Tables32 tab{};
@@ -182,7 +184,7 @@ void set_unit_geometry(const Plan &plan, int Tl, int nbc, ChainUnit &u);
 void set_cta_powers(const Plan &plan, int nbc, ChainParams &p);
 
 // Static kernel parameters of a chain (tables, transitions, geometry).
-void set_static_params(const Plan &plan, int hw, int HP, int Wout, int ns, int nl, const double *dense_dev,
+void set_static_params(const Plan &plan, int hw, int HP, int Wout, int ns, int nl, const float *dense_dev,
                        ChainParams &p);
 
 // ---------------------------------------------------------------------------

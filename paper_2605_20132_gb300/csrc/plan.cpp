@@ -359,6 +359,38 @@ std::vector<double> dense_matrices(const std::vector<ld> &A, int n) {
     return out;
 }
 
+// The kernel's layout of the dense matrices.  A column's state (n = 2NS rows)
+// lives in 8 lanes of a warp, lane w < NS holding rows w and n-1-w; at step q
+// of a matrix-vector product every lane takes the entries (w, q) and
+// (n-1-w, q) as one float4 {hi, lo of row w; hi, lo of row n-1-w}, a
+// double-float split of the FP64 entry.  Output [kDenseMats][kDenseDim][8]
+// float4.  The powers of the cascade's transition matrix are block lower
+// triangular (section k depends only on sections <= k), so row w needs the
+// columns q < NS only and the kernel reads no other entry of it; false if an
+// entry it would skip is not zero.
+bool dense_lane_layout(const std::vector<double> &mats, int NS, std::vector<float> &out) {
+    const int D = kDenseDim, n = 2 * NS;
+    out.assign((size_t)kDenseMats * D * 8 * 4, 0.f);
+    auto split = [](double v, float *dst) {
+        const float hi = (float)v;
+        dst[0] = hi;
+        dst[1] = (float)(v - (double)hi);
+    };
+    for (int m = 0; m < kDenseMats; ++m) {
+        const double *M = mats.data() + (size_t)m * D * D;
+        for (int w = 0; w < NS; ++w)
+            for (int q = NS; q < n; ++q)
+                if (M[(size_t)w * D + q] != 0.0) return false;
+        for (int q = 0; q < n; ++q)
+            for (int w = 0; w < NS; ++w) {
+                float *f = out.data() + (((size_t)m * D + q) * 8 + w) * 4;
+                if (q < NS) split(M[(size_t)w * D + q], f);
+                split(M[(size_t)(n - 1 - w) * D + q], f + 2);
+            }
+    }
+    return true;
+}
+
 }  // namespace
 
 void Plan::slot_power(int n, double out[kMaxSlots][4]) const {
@@ -631,7 +663,10 @@ filark_status make_plan(const double *sos, int S, int precision, Plan *pl, std::
     pl->Winv.assign((size_t)n * n, 0);
     for (int i = 0; i < n; ++i) pl->W[(size_t)i * n + i] = pl->Winv[(size_t)i * n + i] = 1;
     fill_tables(Kf, Gf);
-    pl->dense_mats = dense_matrices(A, n);
+    if (!dense_lane_layout(dense_matrices(A, n), pl->NS, pl->dense_mats)) {
+        *err = "dense carry: a transition power is not block lower triangular";
+        return FILARK_EINVAL;
+    }
     pl->probe_err = probe_dense(*pl, secs, A);
     return FILARK_OK;
 }
@@ -741,7 +776,7 @@ void set_unit_geometry(const Plan &plan, int Tl, int nbc, ChainUnit &u) {
     }
 }
 
-void set_static_params(const Plan &plan, int hw, int HP, int Wout, int ns, int nl, const double *dense_dev,
+void set_static_params(const Plan &plan, int hw, int HP, int Wout, int ns, int nl, const float *dense_dev,
                        ChainParams &p) {
     std::memset(&p, 0, sizeof(p));
     p.tab = plan.tab;

@@ -131,7 +131,7 @@ def test_create_rejects_bad_sections(row, expect):
 
 def test_create_accepts_repeated_poles():
     """Two identical sections make the cascade matrix defective (no modal
-    basis); the planner falls back to the dense FP64 carry instead of failing
+    basis); the planner falls back to the dense carry instead of failing
     (without a GPU the call then stops at the device step)."""
     sec = [1.0, 0.0, -1.0, 1.0, -1.2, 0.5]
     cfg, _keep = _cfg(sos=np.array([sec, sec]))

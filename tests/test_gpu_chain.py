@@ -408,7 +408,7 @@ def test_paper_scale_benchmark_configuration(oracle_mod, paper_scale):
 
 
 # --------------------------------------------------------------------------
-# Dense FP64 carry (canonical basis): forced on the small workload, chosen
+# Dense double-float carry (canonical basis): forced on the small workload, chosen
 # automatically for a defective cascade (repeated poles) and for the
 # precision-stress bandpass 0.01-1 Hz at 1.5 kHz (poles 8e-6 from z = 1).
 # --------------------------------------------------------------------------
@@ -439,7 +439,7 @@ def test_repeated_poles_use_dense_carry(oracle_mod):
 def test_precision_stress_sampled(oracle_mod):
     """Order-8 0.01-1 Hz bandpass at 1.5 kHz on 48 channels of the stress
     stream (noise + 0.05 Hz sine), 120 pushes of 1 s: the planner picks the
-    dense FP64 carry and stays within 1e-5 of the FP64 oracle; carrying in
+    dense double-float carry and stays within 1e-5 of the FP64 oracle; carrying in
     FP32 instead (the all-FP32 comparison mode) does not."""
     from paper_2605_20132_gb300.chain import Chain
     cfg = synth.PRECISION
@@ -459,6 +459,6 @@ def test_precision_stress_sampled(oracle_mod):
     err32 = normwise(got32["bp"], ref["bp"])
     # per-chunk report (max over channels) of both modes
     per_chunk = [normwise(got["bp"][i * 1500:(i + 1) * 1500], ref["bp"][i * 1500:(i + 1) * 1500]) for i in range(n_push)]
-    print(f"precision stress: dense FP64 carry {err:.2e} (worst chunk {max(per_chunk):.2e}), all-FP32 {err32:.2e}")
+    print(f"precision stress: dense carry {err:.2e} (worst chunk {max(per_chunk):.2e}), all-FP32 {err32:.2e}")
     assert err <= TOL
     assert err32 > err

@@ -2,7 +2,7 @@
 0.01-1 Hz at 1.5 kHz (poles within 1e-4 of z = 1) on 10,000 channels of
 N(0,1) noise plus a 0.05 Hz sine of amplitude 0.1, pushed in 1 s chunks.
 
-The planner's path (FP32 block scan with FP64 carries -- the dense carry for
+The planner's path (FP32 block scan with double-float carries -- the dense carry for
 this filter) and the all-FP32 comparison mode run on all 10,000 channels; the
 FP64 oracle runs on 64 evenly spaced channels.  For every chunk the max
 relative error (normwise per channel, over the 64 channels) of both modes is
@@ -37,12 +37,12 @@ def test_precision_stress_per_chunk_report(oracle_mod):
     sel = np.linspace(0, C - 1, 64).round().astype(np.int64)
     sel_t = torch.from_numpy(sel).cuda()
     chains = {
-        "fp32_scan_fp64_carry": Chain(C, sos, cfg["fs"], outputs=abi.FILARK_OUT_BANDPASS, max_chunk=T),
+        "fp32_scan_df_carry": Chain(C, sos, cfg["fs"], outputs=abi.FILARK_OUT_BANDPASS, max_chunk=T),
         "all_fp32": Chain(C, sos, cfg["fs"], outputs=abi.FILARK_OUT_BANDPASS, max_chunk=T,
                           precision=abi.FILARK_PREC_ALL32),
     }
     modes = {k: {1: "modal32", 2: "dense64", 3: "all32"}[c.info()["precision"]] for k, c in chains.items()}
-    assert modes["fp32_scan_fp64_carry"] == "dense64"
+    assert modes["fp32_scan_df_carry"] == "dense64"
     ora = oracle_mod.Chain(len(sel), sos, 1, 0, 0)
     got = {k: np.empty((n_push * T, len(sel))) for k in chains}
     ref = np.empty((n_push * T, len(sel)))
@@ -82,6 +82,6 @@ def test_precision_stress_per_chunk_report(oracle_mod):
         os.makedirs(out_dir, exist_ok=True)
         with open(os.path.join(out_dir, "precision_stress_report.json"), "w") as f:
             json.dump(report, f)
-    assert per["fp32_scan_fp64_carry"].max() <= TOL
+    assert per["fp32_scan_df_carry"].max() <= TOL
     # the comparison mode drifts: its worst chunk is far above the planner's
-    assert per["all_fp32"].max() > 10 * per["fp32_scan_fp64_carry"].max()
+    assert per["all_fp32"].max() > 10 * per["fp32_scan_df_carry"].max()

@@ -113,7 +113,7 @@ def test_static_calls_in_a_row_match_the_chain_bitwise(oracle_mod):
 
 
 def test_static_dense_carry_and_short_recording(oracle_mod):
-    """The dense FP64 carry (forced) and a recording shorter than one launch
+    """The dense carry (forced) and a recording shorter than one launch
     (700 samples: history ring of lta_len + 700 rows), each bitwise equal to
     the regular chain."""
     st, sos = abi.filark_butter_bandpass_sos(4, 1.0, 50.0, 1000.0)
