@@ -528,7 +528,9 @@ def run_batch_workload(args) -> None:
                           "launches_per_step": int(sum(-(-int(t) // 2048) for t in T.ravel() if t))},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "peak_kind": peak_kind},
-        "tuner": {"cluster": info["cluster"], "n_clusters": info["n_clusters"], "candidates": info["tuned"]},
+        "tuner": {"cluster": info["cluster"], "n_clusters": info["n_clusters"],
+                  "blocks_per_cta": info["blocks_per_cta"], "use_graph": info["use_graph"],
+                  "stream_path_ms": info["stream_ms"], "candidates": info["tuned"]},
         "gpu_launches": args.steps * P, "dtype": "f32", "data": "synthetic N(0,1) noise generated on the device",
         "config": {"streams": len(Cs), "channels": int(sum(Cs)), "chunk_range": list(cfg["chunk"]),
                    "sections": int(sos.shape[0]), "spatial_width": K, "sta": ns, "lta": nl},

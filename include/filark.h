@@ -368,10 +368,12 @@ filark_status filark_iir_backward(const double *sos, int n_sections, int n_chann
  * with the same arithmetic as filark_chain_push_chunk.  The descriptor upload
  * and the launch are captured once in a CUDA graph and replayed per push.
  *
- * The launch geometry -- time ranges per cluster (the scan blocks one cluster
- * combines, 1, 2, 4 or 8 x 256 samples) and the number of resident clusters --
- * is chosen by filark_batch_tune, which times the candidates on a caller-given
- * push; until then a fixed default is used.
+ * The launch geometry -- time ranges per cluster (1, 2, 4 or 8 CTAs), the
+ * scan segment of one CTA (4 .. 8 blocks of 32 samples) and the number of
+ * resident clusters -- is chosen by filark_batch_tune, which times the
+ * candidates on a caller-given push; until then a fixed default is used.  A
+ * stream whose push needs fewer time ranges than the cluster has (a short
+ * chunk) shares each cluster among several of its channel tiles.
  */
 typedef struct filark_batch filark_batch;
 
@@ -396,6 +398,9 @@ typedef struct {
     int32_t tune_cluster[16];
     int32_t tune_clusters[16];
     double tune_ms[16];       /* mean ms per push of each candidate            */
+    int32_t blocks_per_cta;   /* scan blocks of 32 samples per CTA (4 .. 8)     */
+    int32_t tune_blocks[16];  /* blocks per CTA of each candidate              */
+    double tune_stream_ms;    /* the fastest candidate without the graph       */
 } filark_batch_info;
 
 /* cfg is the configuration every stream shares; its n_channels is ignored and
@@ -411,15 +416,28 @@ filark_status filark_batch_create(const filark_chain_config *cfg, int n_streams,
 filark_status filark_batch_push(filark_batch *b, const filark_chunk_desc *descs, filark_stream_t stream);
 
 /* Time each launch geometry on the push `descs` (warm-up pushes, then
-   timed_pushes >= 1 timed ones, CUDA events on `stream`), keep the fastest,
-   and reset every stream's state (the trial pushes advance it).  Blocks until
-   done.  The outputs of descs are overwritten. */
+   timed_pushes >= 1 timed ones, CUDA events on `stream`), then the fastest
+   once more without the graph; keep the fastest of all and reset every
+   stream's state (the trial pushes advance it).  Blocks until done.  The
+   outputs of descs are overwritten. */
 filark_status filark_batch_tune(filark_batch *b, const filark_chunk_desc *descs, int timed_pushes,
                                 filark_stream_t stream);
 
 /* Set the launch geometry by hand: cluster in {1, 2, 4, 8}; n_clusters <= 0
-   takes the occupancy limit; use_graph 0 launches without a graph. */
+   takes the occupancy limit.  use_graph 1: each push replays a captured graph
+   (upload + launch); 0: each push uploads its descriptors on a side stream,
+   which overlaps the previous push, and launches with programmatic dependent
+   launch, so that its clusters start while the previous push's last items
+   drain (the same rule as for filark_chain_push_chunk: work enqueued on
+   `stream` between two pushes then runs before the second push's kernel,
+   which only reads the caller's input before that push's state is needed). */
 filark_status filark_batch_set_launch(filark_batch *b, int cluster, int n_clusters, int use_graph);
+
+/* Scan blocks of 32 samples per CTA, 4 .. 8 (default 8): a unit then spans
+   cluster x blocks x 32 samples.  FILARK_EINVAL outside 4 .. 8; FILARK_ENOSYS
+   for anything but 8 when the plan uses the dense carry.  Waits for the
+   staging buffers' uploads like filark_batch_set_launch. */
+filark_status filark_batch_set_blocks_per_cta(filark_batch *b, int blocks);
 
 filark_status filark_batch_reset_state(filark_batch *b, filark_stream_t stream);
 filark_status filark_batch_sync_status(filark_batch *b, filark_stream_t stream);

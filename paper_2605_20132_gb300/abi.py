@@ -50,6 +50,7 @@ EXPORTED = (
     "filark_chain_run_static", "filark_iir_ckpt_bytes", "filark_iir_work_bytes",
     "filark_iir_forward_ckpt", "filark_iir_backward",
     "filark_batch_create", "filark_batch_push", "filark_batch_tune", "filark_batch_set_launch",
+    "filark_batch_set_blocks_per_cta",
     "filark_batch_reset_state", "filark_batch_sync_status", "filark_batch_get_info", "filark_batch_stream",
     "filark_batch_destroy",
     "filark_trigger_create", "filark_trigger_push", "filark_trigger_flush", "filark_trigger_reset",
@@ -124,6 +125,9 @@ class filark_batch_info(ct.Structure):
         ("tune_cluster", ct.c_int32 * 16),
         ("tune_clusters", ct.c_int32 * 16),
         ("tune_ms", ct.c_double * 16),
+        ("blocks_per_cta", ct.c_int32),
+        ("tune_blocks", ct.c_int32 * 16),
+        ("tune_stream_ms", ct.c_double),
     ]
 
 
@@ -183,6 +187,7 @@ def load(build_if_missing: bool = True) -> ct.CDLL:
             "filark_batch_push": ([vp, ct.POINTER(filark_chunk_desc), vp], ct.c_int),
             "filark_batch_tune": ([vp, ct.POINTER(filark_chunk_desc), ct.c_int, vp], ct.c_int),
             "filark_batch_set_launch": ([vp, ct.c_int, ct.c_int, ct.c_int], ct.c_int),
+            "filark_batch_set_blocks_per_cta": ([vp, ct.c_int], ct.c_int),
             "filark_batch_reset_state": ([vp, vp], ct.c_int),
             "filark_batch_sync_status": ([vp, vp], ct.c_int),
             "filark_batch_get_info": ([vp, ct.POINTER(filark_batch_info)], ct.c_int),
@@ -354,6 +359,10 @@ def filark_batch_tune(b, descs, timed_pushes: int, stream) -> int:
 
 def filark_batch_set_launch(b, cluster: int, n_clusters: int, use_graph: int) -> int:
     return load().filark_batch_set_launch(b, int(cluster), int(n_clusters), int(use_graph))
+
+
+def filark_batch_set_blocks_per_cta(b, blocks: int) -> int:
+    return load().filark_batch_set_blocks_per_cta(b, int(blocks))
 
 
 def filark_batch_reset_state(b, stream) -> int:

@@ -235,6 +235,9 @@ class Batch:
         abi.check(abi.filark_batch_set_launch(self._h, cluster, n_clusters, int(use_graph)),
                   "filark_batch_set_launch")
 
+    def set_blocks_per_cta(self, blocks: int) -> None:
+        abi.check(abi.filark_batch_set_blocks_per_cta(self._h, blocks), "filark_batch_set_blocks_per_cta")
+
     def reset(self, stream=None) -> None:
         abi.check(abi.filark_batch_reset_state(self._h, _stream_handle(stream)), "filark_batch_reset_state")
 
@@ -245,9 +248,10 @@ class Batch:
         st, inf = abi.filark_batch_get_info(self._h)
         abi.check(st, "filark_batch_get_info")
         out = {k: getattr(inf, k) for k, _ in inf._fields_ if not k.startswith("tune_")}
+        out["stream_ms"] = inf.tune_stream_ms
         n = inf.n_tuned
-        out["tuned"] = [dict(cluster=inf.tune_cluster[i], n_clusters=inf.tune_clusters[i], ms=inf.tune_ms[i])
-                        for i in range(n)]
+        out["tuned"] = [dict(cluster=inf.tune_cluster[i], n_clusters=inf.tune_clusters[i],
+                             blocks_per_cta=inf.tune_blocks[i], ms=inf.tune_ms[i]) for i in range(n)]
         return out
 
 

@@ -29,6 +29,7 @@ namespace {
 constexpr size_t kAlign = 256;
 constexpr int kClusterChoices[] = {1, 2, 4, 8};
 constexpr int kDefaultCluster = 8;   // the single-stream kernel's time split
+constexpr int kMinBlocksPerCta = 4;  // smallest scan segment per CTA (x 32 samples)
 constexpr int kMaxTuned = 16;
 
 size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
@@ -45,18 +46,25 @@ struct filark_batch {
     int NS = 0;
     bool det = false, dense = false;
     int cluster = kDefaultCluster, n_clusters = 0, use_graph = 1;
+    int nbc = kNB;               // scan blocks of 32 samples per CTA
     int64_t max_units = 0, max_items = 0, n_tiles = 0;
     size_t off_items = 0, off_units = 0, desc_bytes = 0;
-    char *d_desc = nullptr;                 // [count | items | units] on the device
+    size_t staged_bytes = 0;                // bytes of the descriptor block the last push filled
+    char *d_desc[2] = {nullptr, nullptr};   // [count | items | units] on the device, per staging buffer
     char *h_stage[2] = {nullptr, nullptr};  // the same, pinned host staging
-    cudaEvent_t staged[2] = {nullptr, nullptr};
+    cudaEvent_t staged[2] = {nullptr, nullptr};     // staging buffer k uploaded
+    cudaEvent_t done[2] = {nullptr, nullptr};       // the kernel that read d_desc[k] finished
     int next = 0;
     cudaStream_t cap = nullptr;             // capture stream (graphs are built here)
+    cudaStream_t up = nullptr;              // descriptor uploads of the stream path
+    cudaGraph_t graph[2] = {nullptr, nullptr};
     cudaGraphExec_t exec[2] = {nullptr, nullptr};
+    cudaGraphNode_t upload[2] = {nullptr, nullptr};   // each graph's descriptor copy
     filark_status sticky = FILARK_OK;
     int64_t device_bytes = 0;
     int n_tuned = 0;
-    int tune_cluster[kMaxTuned] = {}, tune_clusters[kMaxTuned] = {};
+    int tune_cluster[kMaxTuned] = {}, tune_clusters[kMaxTuned] = {}, tune_nbc[kMaxTuned] = {};
+    double stream_ms = 0.0;     // the best geometry without the graph (last tune)
     double tune_ms[kMaxTuned] = {};
     std::vector<int> order;
     std::vector<int> unit0, nunits;
@@ -67,11 +75,13 @@ struct filark_batch {
 namespace {
 
 void destroy_graphs(filark_batch *b) {
-    for (cudaGraphExec_t &g : b->exec)
-        if (g) {
-            cudaGraphExecDestroy(g);
-            g = nullptr;
-        }
+    for (int k = 0; k < 2; ++k) {
+        if (b->exec[k]) cudaGraphExecDestroy(b->exec[k]);
+        if (b->graph[k]) cudaGraphDestroy(b->graph[k]);
+        b->exec[k] = nullptr;
+        b->graph[k] = nullptr;
+        b->upload[k] = nullptr;
+    }
 }
 
 void free_batch(filark_batch *b) {
@@ -79,10 +89,14 @@ void free_batch(filark_batch *b) {
     destroy_graphs(b);
     for (cudaEvent_t &e : b->staged)
         if (e) cudaEventDestroy(e);
+    for (cudaEvent_t &e : b->done)
+        if (e) cudaEventDestroy(e);
     if (b->cap) cudaStreamDestroy(b->cap);
+    if (b->up) cudaStreamDestroy(b->up);
     for (char *p : b->h_stage)
         if (p) cudaFreeHost(p);
-    if (b->d_desc) cudaFree(b->d_desc);
+    for (char *p : b->d_desc)
+        if (p) cudaFree(p);
     for (double *p : b->halo)
         if (p) cudaFree(p);
     for (double *p : b->detx)
@@ -91,13 +105,23 @@ void free_batch(filark_batch *b) {
     delete b;
 }
 
-const BatchItem *dev_items(const filark_batch *b) { return (const BatchItem *)(b->d_desc + b->off_items); }
-const ChainUnit *dev_units(const filark_batch *b) { return (const ChainUnit *)(b->d_desc + b->off_units); }
-int *dev_ctr(const filark_batch *b) { return (int *)b->d_desc; }
+const BatchItem *dev_items(const filark_batch *b, int k) { return (const BatchItem *)(b->d_desc[k] + b->off_items); }
+const ChainUnit *dev_units(const filark_batch *b, int k) { return (const ChainUnit *)(b->d_desc[k] + b->off_units); }
+int *dev_ctr(const filark_batch *b, int k) { return (int *)b->d_desc[k]; }
 
-cudaError_t enqueue_launch(filark_batch *b, cudaStream_t s) {
-    return launch_chain_batch(b->base, b->NS, b->det, b->dense, b->cluster, b->n_clusters, dev_items(b),
-                              dev_ctr(b), dev_units(b), s);
+// pdl: launched with programmatic stream serialization (the stream path), so
+// that its clusters start while the previous push's last items drain
+cudaError_t enqueue_launch(filark_batch *b, int k, cudaStream_t s, bool pdl) {
+    ChainParams p = b->base;
+    p.pdl = pdl ? 1 : 0;
+    return (b->cluster == 1 ? launch_chain_batch_solo : launch_chain_batch)(
+        p, b->NS, b->det, b->dense, b->cluster, b->n_clusters, dev_items(b, k),
+                              dev_ctr(b, k), dev_units(b, k), s);
+}
+
+int max_clusters(const filark_batch *b, int cluster) {
+    return cluster == 1 ? batch_max_active_clusters_solo(b->NS, b->det, b->dense, cluster)
+                        : batch_max_active_clusters(b->NS, b->det, b->dense, cluster);
 }
 
 filark_status build_graphs(filark_batch *b) {
@@ -106,16 +130,27 @@ filark_status build_graphs(filark_batch *b) {
     for (int k = 0; k < 2; ++k) {
         cudaError_t e = cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal);
         if (e != cudaSuccess) return fail_cuda_with(e, "batch: begin capture");
-        cudaError_t e1 = cudaMemcpyAsync(b->d_desc, b->h_stage[k], b->desc_bytes, cudaMemcpyHostToDevice, b->cap);
-        cudaError_t e2 = e1 == cudaSuccess ? enqueue_launch(b, b->cap) : e1;
+        cudaError_t e1 = cudaMemcpyAsync(b->d_desc[k], b->h_stage[k], b->desc_bytes, cudaMemcpyHostToDevice, b->cap);
+        cudaError_t e2 = e1 == cudaSuccess ? enqueue_launch(b, k, b->cap, false) : e1;
         cudaGraph_t g = nullptr;
         e = cudaStreamEndCapture(b->cap, &g);
         if (e2 != cudaSuccess || e != cudaSuccess) {
             if (g) cudaGraphDestroy(g);
             return fail_cuda_with(e2 != cudaSuccess ? e2 : e, "batch: capture of upload + launch");
         }
-        e = cudaGraphInstantiate(&b->exec[k], g, 0);
-        cudaGraphDestroy(g);
+        b->graph[k] = g;
+        // the copy node, whose length each push sets to the bytes it filled
+        size_t n = 0;
+        e = cudaGraphGetNodes(g, nullptr, &n);
+        std::vector<cudaGraphNode_t> nodes(n);
+        if (e == cudaSuccess && n > 0) e = cudaGraphGetNodes(g, nodes.data(), &n);
+        for (size_t i = 0; e == cudaSuccess && i < n; ++i) {
+            cudaGraphNodeType t;
+            e = cudaGraphNodeGetType(nodes[i], &t);
+            if (e == cudaSuccess && t == cudaGraphNodeTypeMemcpy) b->upload[k] = nodes[i];
+        }
+        if (e == cudaSuccess && !b->upload[k]) return fail_with(FILARK_ECUDA, "batch: no copy node in the graph");
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec[k], g, 0);
         if (e != cudaSuccess) {
             b->exec[k] = nullptr;
             return fail_cuda_with(e, "batch: graph instantiate");
@@ -124,15 +159,21 @@ filark_status build_graphs(filark_batch *b) {
     return FILARK_OK;
 }
 
-filark_status set_launch(filark_batch *b, int cluster, int n_clusters, int use_graph) {
+filark_status set_launch(filark_batch *b, int cluster, int n_clusters, int use_graph, int nbc) {
     if (std::find(std::begin(kClusterChoices), std::end(kClusterChoices), cluster) == std::end(kClusterChoices))
         return fail_with(FILARK_EINVAL, "batch: cluster must be 1, 2, 4 or 8");
+    if (nbc < kMinBlocksPerCta || nbc > kNB)
+        return fail_with(FILARK_EINVAL, "batch: blocks per CTA must be 4 .. 8");
+    if (b->dense && nbc != kNB) return fail_with(FILARK_ENOSYS, "batch: the dense carry uses 8 blocks per CTA");
     int n = n_clusters;
-    if (n <= 0) n = batch_max_active_clusters(b->NS, b->det, b->dense, cluster);
+    if (n <= 0) n = max_clusters(b, cluster);
     if (n <= 0) return fail_with(FILARK_ENOSYS, "batch: no cluster of this size fits on the device");
     b->cluster = cluster;
     b->n_clusters = n;
     b->use_graph = use_graph ? 1 : 0;
+    b->nbc = nbc;
+    // the cross-CTA powers Phi^r of the modal carry depend on the segment
+    set_cta_powers(b->chains[0]->plan, nbc, b->base);
     return build_graphs(b);
 }
 
@@ -142,7 +183,7 @@ int stage_push(filark_batch *b, int k, const filark_chunk_desc *d) {
     BatchItem *items = (BatchItem *)(base + b->off_items);
     ChainUnit *units = (ChainUnit *)(base + b->off_units);
     const int n = (int)b->chains.size();
-    const int span = kTileRows * b->cluster;
+    const int span = kL * b->nbc * b->cluster;
     int nu = 0;
     for (int i = 0; i < n; ++i) {
         filark_chain *h = b->chains[(size_t)i];
@@ -185,7 +226,7 @@ int stage_push(filark_batch *b, int k, const filark_chunk_desc *d) {
             u.det_in = det_buf(j);
             u.det_out = det_buf(j + 1);
             u.n0 = h->n;
-            set_unit_geometry(h->plan, Tl, kNB, u);
+            set_unit_geometry(h->plan, Tl, b->nbc, u);
             u.slot_n0 = h->Q > 0 ? (int)(h->n % h->Q) : 0;
             u.x_vec4 = (c.ld_in % 4 == 0) && (((uintptr_t)u.x & 15u) == 0);
             bool ov = (c.ld_out % 4 == 0);
@@ -203,14 +244,26 @@ int stage_push(filark_batch *b, int k, const filark_chunk_desc *d) {
     ord.resize((size_t)n);
     for (int i = 0; i < n; ++i) ord[(size_t)i] = i;
     std::stable_sort(ord.begin(), ord.end(), [&](int a, int c) { return d[a].n_samples > d[c].n_samples; });
+    // a push of one unit that needs R < cluster time ranges shares the
+    // cluster among cluster / reff tiles, reff = R rounded up to a power of two
     int ni = 0;
     for (int i : ord) {
-        if (b->nunits[(size_t)i] == 0) continue;
+        const int nu_i = b->nunits[(size_t)i];
+        if (nu_i == 0) continue;
         const filark_chain *h = b->chains[(size_t)i];
-        for (int t = 0; t < h->n_tiles; ++t) items[ni++] = BatchItem{b->unit0[(size_t)i], b->nunits[(size_t)i], t, 0};
+        int reff = b->cluster;
+        if (nu_i == 1) {
+            const int R = units[b->unit0[(size_t)i]].R;
+            reff = 1;
+            while (reff < R) reff <<= 1;
+        }
+        const int g = b->cluster / reff;
+        for (int t = 0; t < h->n_tiles; t += g)
+            items[ni++] = BatchItem{b->unit0[(size_t)i], nu_i, t, std::min(g, h->n_tiles - t), reff, {0, 0, 0}};
     }
     ((int *)base)[0] = ni;
     ((int *)base)[1] = 0;   // the kernel's work counter
+    b->staged_bytes = b->off_units + sizeof(ChainUnit) * (size_t)nu;
     return ni;
 }
 
@@ -230,13 +283,25 @@ filark_status push(filark_batch *b, const filark_chunk_desc *descs, cudaStream_t
     if (e != cudaSuccess) return fail_cuda_with(e, "batch: staging event");
     const int ni = stage_push(b, k, descs);
     if (ni == 0) return FILARK_OK;
+    // upload only the part of the descriptor block this push filled
     if (b->use_graph) {
-        e = cudaGraphLaunch(b->exec[k], stream);
+        e = cudaGraphExecMemcpyNodeSetParams1D(b->exec[k], b->upload[k], b->d_desc[k], b->h_stage[k],
+                                               b->staged_bytes, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaGraphLaunch(b->exec[k], stream);
+        if (e == cudaSuccess) e = cudaEventRecord(b->staged[k], stream);
     } else {
-        e = cudaMemcpyAsync(b->d_desc, b->h_stage[k], b->desc_bytes, cudaMemcpyHostToDevice, stream);
-        if (e == cudaSuccess) e = enqueue_launch(b, stream);
+        // the upload runs on the side stream once the kernel that last read
+        // d_desc[k] (the push before last) is done, so it overlaps the
+        // previous push; the launch waits for it and overlaps the previous
+        // kernel's tail through programmatic dependent launch
+        e = cudaStreamWaitEvent(b->up, b->done[k], 0);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(b->d_desc[k], b->h_stage[k], b->staged_bytes, cudaMemcpyHostToDevice, b->up);
+        if (e == cudaSuccess) e = cudaEventRecord(b->staged[k], b->up);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(stream, b->staged[k], 0);
+        if (e == cudaSuccess) e = enqueue_launch(b, k, stream, true);
+        if (e == cudaSuccess) e = cudaEventRecord(b->done[k], stream);
     }
-    if (e == cudaSuccess) e = cudaEventRecord(b->staged[k], stream);
     if (e != cudaSuccess) {
         b->sticky = FILARK_ECUDA;
         for (filark_chain *h : b->chains) h->sticky = FILARK_ECUDA;
@@ -244,6 +309,20 @@ filark_status push(filark_batch *b, const filark_chunk_desc *descs, cudaStream_t
     }
     b->next ^= 1;
     return FILARK_OK;
+}
+
+// Wait until no upload reads a staging buffer and no kernel reads a device
+// descriptor block (before the launch settings change).
+cudaError_t wait_idle(filark_batch *b) {
+    for (cudaEvent_t ev : b->staged) {
+        const cudaError_t e = cudaEventSynchronize(ev);
+        if (e != cudaSuccess) return e;
+    }
+    for (cudaEvent_t ev : b->done) {
+        const cudaError_t e = cudaEventSynchronize(ev);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 filark_status reset(filark_batch *b, cudaStream_t stream) {
@@ -304,7 +383,9 @@ filark_status filark_batch_create(const filark_chain_config *cfg, int n_streams,
             b->device_bytes += (int64_t)(sizeof(double) * 4 * (size_t)h->C);
         }
         b->detx.push_back(dx);
-        b->max_units += (std::min<int64_t>(cfg->max_chunk, INT32_MAX) + kTileRows - 1) / kTileRows;
+        // units are at least kMinBlocksPerCta x 32 samples
+        b->max_units += (std::min<int64_t>(cfg->max_chunk, INT32_MAX) + kL * kMinBlocksPerCta - 1) /
+                        (kL * kMinBlocksPerCta);
         b->max_items += h->n_tiles;
     }
     b->n_tiles = b->max_items;
@@ -326,17 +407,20 @@ filark_status filark_batch_create(const filark_chain_config *cfg, int n_streams,
         free_batch(b);
         return fail_with(FILARK_ECUDA, "cudaSetDevice failed for device " + std::to_string(cuda_device));
     }
-    cudaError_t e = cudaMalloc(&b->d_desc, b->desc_bytes);
+    cudaError_t e = cudaSuccess;
+    for (int k = 0; k < 2 && e == cudaSuccess; ++k) e = cudaMalloc(&b->d_desc[k], b->desc_bytes);
     for (int k = 0; k < 2 && e == cudaSuccess; ++k) e = cudaHostAlloc(&b->h_stage[k], b->desc_bytes, cudaHostAllocDefault);
     for (int k = 0; k < 2 && e == cudaSuccess; ++k) e = cudaEventCreateWithFlags(&b->staged[k], cudaEventDisableTiming);
+    for (int k = 0; k < 2 && e == cudaSuccess; ++k) e = cudaEventCreateWithFlags(&b->done[k], cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->up, cudaStreamNonBlocking);
     if (e != cudaSuccess) {
         free_batch(b);
         return fail_cuda_with(e, "batch create: allocation");
     }
-    b->device_bytes += (int64_t)b->desc_bytes;
+    b->device_bytes += 2 * (int64_t)b->desc_bytes;
     for (int k = 0; k < 2; ++k) std::memset(b->h_stage[k], 0, b->desc_bytes);
-    filark_status st = set_launch(b, kDefaultCluster, 0, 1);
+    filark_status st = set_launch(b, kDefaultCluster, 0, 1, kNB);
     if (st != FILARK_OK) {
         const std::string msg = filark_last_error_string();
         free_batch(b);
@@ -360,11 +444,18 @@ filark_status filark_batch_set_launch(filark_batch *b, int cluster, int n_cluste
     DeviceGuard dg(b->device);
     if (!dg.ok) return fail_with(FILARK_ECUDA, "cudaSetDevice failed");
     // the staging buffers may still be read by an earlier upload
-    for (cudaEvent_t ev : b->staged) {
-        cudaError_t e = cudaEventSynchronize(ev);
-        if (e != cudaSuccess) return fail_cuda_with(e, "batch: staging event");
-    }
-    return set_launch(b, cluster, n_clusters, use_graph);
+    const cudaError_t e = wait_idle(b);
+    if (e != cudaSuccess) return fail_cuda_with(e, "batch: staging event");
+    return set_launch(b, cluster, n_clusters, use_graph, b->nbc);
+}
+
+filark_status filark_batch_set_blocks_per_cta(filark_batch *b, int blocks) {
+    if (!b) return fail_with(FILARK_EINVAL, "batch is NULL");
+    DeviceGuard dg(b->device);
+    if (!dg.ok) return fail_with(FILARK_ECUDA, "cudaSetDevice failed");
+    const cudaError_t e = wait_idle(b);
+    if (e != cudaSuccess) return fail_cuda_with(e, "batch: staging event");
+    return set_launch(b, b->cluster, b->n_clusters, b->use_graph, blocks);
 }
 
 filark_status filark_batch_tune(filark_batch *b, const filark_chunk_desc *descs, int timed_pushes,
@@ -383,43 +474,71 @@ filark_status filark_batch_tune(filark_batch *b, const filark_chunk_desc *descs,
     }
     filark_status st = FILARK_OK;
     double best = 1e300;
-    int best_cluster = b->cluster, best_n = b->n_clusters;
+    int best_cluster = b->cluster, best_n = b->n_clusters, best_nbc = b->nbc;
     b->n_tuned = 0;
-    for (int cl : kClusterChoices) {
-        const int occ = batch_max_active_clusters(b->NS, b->det, b->dense, cl);
-        if (occ <= 0) continue;
-        for (int mult : {1, 2}) {
-            if (b->n_tuned >= kMaxTuned) break;
-            for (cudaEvent_t ev : b->staged) cudaEventSynchronize(ev);
-            st = set_launch(b, cl, occ * mult, 1);
-            if (st == FILARK_OK) st = reset(b, s);
-            for (int w = 0; w < 2 && st == FILARK_OK; ++w) st = push(b, descs, s);
-            if (st == FILARK_OK && (e = cudaEventRecord(t0, s)) != cudaSuccess) st = fail_cuda_with(e, "tune: record");
-            for (int r = 0; r < timed_pushes && st == FILARK_OK; ++r) st = push(b, descs, s);
-            if (st == FILARK_OK && (e = cudaEventRecord(t1, s)) != cudaSuccess) st = fail_cuda_with(e, "tune: record");
-            if (st == FILARK_OK && (e = cudaEventSynchronize(t1)) != cudaSuccess) st = fail_cuda_with(e, "tune: sync");
-            float ms = 0.f;
-            if (st == FILARK_OK && (e = cudaEventElapsedTime(&ms, t0, t1)) != cudaSuccess)
-                st = fail_cuda_with(e, "tune: elapsed");
-            if (st != FILARK_OK) break;
-            const double per = (double)ms / timed_pushes;
-            b->tune_cluster[b->n_tuned] = cl;
-            b->tune_clusters[b->n_tuned] = occ * mult;
-            b->tune_ms[b->n_tuned] = per;
-            b->n_tuned++;
-            if (per < best) {
-                best = per;
-                best_cluster = cl;
-                best_n = occ * mult;
+    // reset, 2 warm-up pushes, then the mean ms of timed_pushes pushes
+    auto time_pushes = [&](double &per) -> filark_status {
+        filark_status r = reset(b, s);
+        for (int w = 0; w < 2 && r == FILARK_OK; ++w) r = push(b, descs, s);
+        if (r == FILARK_OK && (e = cudaEventRecord(t0, s)) != cudaSuccess) r = fail_cuda_with(e, "tune: record start");
+        for (int q = 0; q < timed_pushes && r == FILARK_OK; ++q) r = push(b, descs, s);
+        if (r == FILARK_OK && (e = cudaEventRecord(t1, s)) != cudaSuccess) r = fail_cuda_with(e, "tune: record end");
+        if (r == FILARK_OK && (e = cudaEventSynchronize(t1)) != cudaSuccess) r = fail_cuda_with(e, "tune: sync");
+        float ms = 0.f;
+        if (r == FILARK_OK && (e = cudaEventElapsedTime(&ms, t0, t1)) != cudaSuccess)
+            r = fail_cuda_with(e, "tune: elapsed");
+        per = (double)ms / timed_pushes;
+        return r;
+    };
+    // scan segments of 8 and 4 blocks per CTA (the dense carry: 8 only) x
+    // cluster sizes x one or two grids' worth of resident clusters
+    for (int nbc : {kNB, kMinBlocksPerCta}) {
+        if (b->dense && nbc != kNB) continue;
+        for (int cl : kClusterChoices) {
+            const int occ = max_clusters(b, cl);
+            if (occ <= 0) continue;
+            for (int mult : {1, 2}) {
+                if (b->n_tuned >= kMaxTuned) break;
+                wait_idle(b);
+                st = set_launch(b, cl, occ * mult, 1, nbc);
+                double per = 0.0;
+                if (st == FILARK_OK) st = time_pushes(per);
+                if (st != FILARK_OK) break;
+                b->tune_cluster[b->n_tuned] = cl;
+                b->tune_clusters[b->n_tuned] = occ * mult;
+                b->tune_nbc[b->n_tuned] = nbc;
+                b->tune_ms[b->n_tuned] = per;
+                b->n_tuned++;
+                if (per < best) {
+                    best = per;
+                    best_cluster = cl;
+                    best_n = occ * mult;
+                    best_nbc = nbc;
+                }
             }
+            if (st != FILARK_OK) break;
         }
         if (st != FILARK_OK) break;
     }
+    // the fastest geometry once more without the graph: uploads on a side
+    // stream and programmatic launches that overlap consecutive pushes
+    int best_graph = 1;
+    if (st == FILARK_OK) {
+        wait_idle(b);
+        st = set_launch(b, best_cluster, best_n, 0, best_nbc);
+        double per_stream = 0.0;
+        if (st == FILARK_OK) st = time_pushes(per_stream);
+        if (st == FILARK_OK) {
+            b->stream_ms = per_stream;
+            if (per_stream < best) best_graph = 0;
+        }
+    }
+    // the timing events are used by time_pushes up to here
     cudaEventDestroy(t0);
     cudaEventDestroy(t1);
     if (st != FILARK_OK) return st;
-    for (cudaEvent_t ev : b->staged) cudaEventSynchronize(ev);
-    st = set_launch(b, best_cluster, best_n, 1);
+    wait_idle(b);
+    if (st == FILARK_OK) st = set_launch(b, best_cluster, best_n, best_graph, best_nbc);
     if (st == FILARK_OK) st = reset(b, s);
     if (st == FILARK_OK && (e = cudaStreamSynchronize(s)) != cudaSuccess) st = fail_cuda_with(e, "tune: sync");
     return st;
@@ -463,7 +582,10 @@ filark_status filark_batch_get_info(const filark_batch *b, filark_batch_info *ou
         out->tune_cluster[i] = b->tune_cluster[i];
         out->tune_clusters[i] = b->tune_clusters[i];
         out->tune_ms[i] = b->tune_ms[i];
+        out->tune_blocks[i] = b->tune_nbc[i];
     }
+    out->blocks_per_cta = b->nbc;
+    out->tune_stream_ms = b->stream_ms;
     return FILARK_OK;
 }
 
@@ -477,8 +599,7 @@ filark_status filark_batch_stream(filark_batch *b, int i, filark_chain **out) {
 filark_status filark_batch_destroy(filark_batch *b) {
     if (!b) return FILARK_OK;
     DeviceGuard dg(b->device);
-    for (cudaEvent_t ev : b->staged)
-        if (ev) cudaEventSynchronize(ev);
+    wait_idle(b);
     free_batch(b);
     return FILARK_OK;
 }

@@ -64,6 +64,30 @@ __device__ __forceinline__ void cluster_wait_acquire() {
     asm volatile("barrier.cluster.wait.acquire.aligned;\n" ::: "memory");
 }
 
+// The body's barriers.  A tile whose time ranges are a whole cluster of one
+// CTA (SOLO: the batched kernel with clusters of 1) exchanges nothing through
+// distributed shared memory, so a block barrier does: the split arrive is
+// dropped and the wait becomes the barrier.  (The batched kernel fences
+// global memory once per unit instead; see chain_batch.cu.)
+template <bool SOLO>
+__device__ __forceinline__ void body_sync() {
+    if constexpr (SOLO) __syncthreads();
+    else cluster_sync_release_acquire();
+}
+template <bool SOLO>
+__device__ __forceinline__ void body_arrive_release() {
+    if constexpr (!SOLO) cluster_arrive_release();
+}
+template <bool SOLO>
+__device__ __forceinline__ void body_arrive_relaxed() {
+    if constexpr (!SOLO) cluster_arrive_relaxed();
+}
+template <bool SOLO>
+__device__ __forceinline__ void body_wait() {
+    if constexpr (SOLO) __syncthreads();
+    else cluster_wait_acquire();
+}
+
 // 1 / x to about one ulp (the hardware approximation, subnormals flushed)
 __device__ __forceinline__ float rcp_approx(float x) {
     float r;
@@ -336,10 +360,18 @@ __device__ __forceinline__ void dense_step(const float4 *__restrict__ Mx, DenseR
     }
 }
 
-// The work of one CTA: time range r (its rank in the cluster) of channel tile
-// `tx` for the launch `cu`.  Every CTA of the cluster calls it with the same
-// unit; it executes chain_cluster_barriers<NS, DET>() cluster barriers.
-template <int NS, bool DET, bool DENSE>
+// Cluster rank of time range q of this CTA's tile: the tile's time ranges are
+// consecutive ranks, this CTA (time range r) among them (the single-stream
+// kernel gives a tile the whole cluster; the batched kernel may put several
+// tiles of a short push in one cluster).
+__device__ __forceinline__ unsigned tile_rank(const cg::cluster_group &cluster, int r, int q) {
+    return cluster.block_rank() - (unsigned)r + (unsigned)q;
+}
+
+// The work of one CTA: time range r of channel tile `tx` for the launch `cu`.
+// Every CTA of the cluster calls it with the same unit; it executes
+// chain_cluster_barriers<NS, DET>() cluster barriers.
+template <int NS, bool DET, bool DENSE, bool SOLO = false>
 __device__ __forceinline__ void chain_body(const ChainParams &p, const ChainUnit &cu, const int tx, const int r) {
     extern __shared__ __align__(16) float smem[];
     float *tile = smem;                       // [kTileRows][kWT]
@@ -495,11 +527,11 @@ __device__ __forceinline__ void chain_body(const ChainParams &p, const ChainUnit
                     AGGD[rhi * kWT + c] = st.hi;
                 }
             }
-            cluster_sync_release_acquire();
+            body_sync<SOLO>();
             // (b) g = sum over earlier CTAs q of Phi^(r-1-q) agg_q
             st = DenseRows{zero, zero};
             for (int q = 0; q < r; ++q) {
-                const DF *ragg = cluster.map_shared_rank(AGGD, q);
+                const DF *ragg = cluster.map_shared_rank(AGGD, tile_rank(cluster, r, q));
                 const DF al = act ? ragg[rlo * kWT + c] : zero;
                 const DF ah = act ? ragg[rhi * kWT + c] : zero;
                 dense_step<NS>(Phi, st, al, ah, w, lane_base, p.all32);
@@ -569,7 +601,7 @@ __device__ __forceinline__ void chain_body(const ChainParams &p, const ChainUnit
         // publish the aggregates; meanwhile read the launch's carried state
         // (double-float hi/lo pairs) of this thread's slot
         static_assert(NS <= kSlotStep, "one slot per thread");
-        cluster_arrive_release();
+        body_arrive_release<SOLO>();
         float2 c0 = make_float2(0.f, 0.f), c1 = make_float2(0.f, 0.f);
         {
             const int s = tid / kWT, cgs = cbase + sc;
@@ -581,14 +613,14 @@ __device__ __forceinline__ void chain_body(const ChainParams &p, const ChainUnit
                 c1 = src[2 * s + 1];
             }
         }
-        cluster_wait_acquire();
+        body_wait<SOLO>();
         for (int s = tid / kWT; s < NS; s += kSlotStep) {
             const int cgs = cbase + sc;
             // earlier CTAs of the cluster: g = sum_q Phi^(r-1-q) agg_q, each
             // term from its own power (independent loads, FP32)
             float g0 = 0.f, g1 = 0.f;
             for (int q = 0; q < r; ++q) {
-                const float *ragg = cluster.map_shared_rank(AGG, q);
+                const float *ragg = cluster.map_shared_rank(AGG, tile_rank(cluster, r, q));
                 const float a0 = ragg[(2 * s) * kWT + sc], a1 = ragg[(2 * s + 1) * kWT + sc];
                 const float *Pq = p.PhiPow32[r - 1 - q][s];
                 g0 = fmaf(Pq[0], a0, fmaf(Pq[1], a1, g0));
@@ -708,7 +740,7 @@ __device__ __forceinline__ void chain_body(const ChainParams &p, const ChainUnit
         // ring writes of every CTA of the cluster become visible to the others
         // (release/acquire at cluster scope orders the global stores too; the
         // next launch sees them at the kernel boundary)
-        cluster_sync_release_acquire();
+        body_sync<SOLO>();
 
         // ------------------------------------------------ 5. STA/LTA
         DF *DS = reinterpret_cast<DF *>(E + kDetDS);
@@ -826,7 +858,7 @@ __device__ __forceinline__ void chain_body(const ChainParams &p, const ChainUnit
                 AGG2[4 * kWT + c] = __int_as_float(bz == kNoNonzero ? kNoNonzero : row0 + bz);
             }
         }
-        cluster_sync_release_acquire();
+        body_sync<SOLO>();
         if (tid < kWT) {
             const int c = tid;
             const int cgl = cbase + c;
@@ -846,7 +878,7 @@ __device__ __forceinline__ void chain_body(const ChainParams &p, const ChainUnit
                     zl = rel < (long long)kNoNonzero ? kNoNonzero : (int)rel;
                 }
                 for (int q = 0; q < r; ++q) {
-                    const float *ra = cluster.map_shared_rank(AGG2, q);
+                    const float *ra = cluster.map_shared_rank(AGG2, tile_rank(cluster, r, q));
                     bS = df_add(bS, DF{ra[0 * kWT + c], ra[1 * kWT + c]});
                     bL = df_add(bL, DF{ra[2 * kWT + c], ra[3 * kWT + c]});
                     zl = max(zl, __float_as_int(ra[4 * kWT + c]));
@@ -872,7 +904,7 @@ __device__ __forceinline__ void chain_body(const ChainParams &p, const ChainUnit
         __syncthreads();
         // every read of another CTA's shared memory is done: the closing
         // cluster barrier's arrive (its wait is at the end of the body)
-        cluster_arrive_relaxed();
+        body_arrive_relaxed<SOLO>();
         // pass b: running sums inside the block, ratio
         if (dact) {
             float fs = BS[jb * kWT + col].hi + BS[jb * kWT + col].lo;
@@ -923,8 +955,8 @@ __device__ __forceinline__ void chain_body(const ChainParams &p, const ChainUnit
         }
     }
     // no CTA may exit while a peer can still read its shared memory
-    if constexpr (DET) cluster_wait_acquire();
-    else if (NS > 0) cluster_sync_release_acquire();
+    if constexpr (DET) body_wait<SOLO>();
+    else if (NS > 0) body_sync<SOLO>();
 }
 
 template <int NS, bool DET>

@@ -57,6 +57,7 @@ cudaError_t configure_chain_kernels() {
     FILARK_CFG(8, false, false) FILARK_CFG(8, true, false) FILARK_CFG(8, false, true) FILARK_CFG(8, true, true)
 #undef FILARK_CFG
     if (e == cudaSuccess) e = configure_batch_kernels();
+    if (e == cudaSuccess) e = configure_batch_kernels_solo();
     return e;
 }
 

@@ -99,10 +99,14 @@ struct ChainParams {
     ChainUnit u;                        // the launch (single-stream kernel)
 };
 
-// One work item of the batched kernel: tile `tile` of one stream, whose push
-// is the units [unit0, unit0 + n_units) run in order by one cluster.
+// One work item of the batched kernel: n_tiles channel tiles of one stream,
+// whose push is the units [unit0, unit0 + n_units) run in order by one
+// cluster; cluster ranks [k reff, (k + 1) reff) run tile `tile + k`.
 struct BatchItem {
-    int unit0, n_units, tile, pad;
+    int unit0, n_units;
+    int tile, n_tiles;   // tiles tile .. tile + n_tiles - 1 of the stream
+    int reff;            // cluster ranks per tile (a power of two dividing the cluster)
+    int pad[3];
 };
 
 // ---------------------------------------------------------------------------
@@ -200,15 +204,22 @@ size_t chain_smem_bytes(bool dense);
 // CTAs (time ranges) takes the items in order from a device counter.
 // d_ctr[0] = item count, d_ctr[1] = next item (0 at launch); both live in
 // device memory so that a captured graph can be replayed with other tables.
+// The _solo forms run clusters of one CTA with block barriers in the body
+// (chain_batch_solo.cu); batch.cpp uses them whenever cluster == 1.
 cudaError_t launch_chain_batch(const ChainParams &p, int NS, bool detector, bool dense, int cluster,
                                int n_clusters, const BatchItem *d_items, int *d_ctr,
                                const ChainUnit *d_units, cudaStream_t stream);
+cudaError_t launch_chain_batch_solo(const ChainParams &p, int NS, bool detector, bool dense, int cluster,
+                                    int n_clusters, const BatchItem *d_items, int *d_ctr,
+                                    const ChainUnit *d_units, cudaStream_t stream);
 
 // Function attributes of the batched kernels (called by configure_chain_kernels).
 cudaError_t configure_batch_kernels();
+cudaError_t configure_batch_kernels_solo();
 
 // Clusters of `cluster` CTAs that can be resident at once (0 if unknown).
 int batch_max_active_clusters(int NS, bool detector, bool dense, int cluster);
+int batch_max_active_clusters_solo(int NS, bool detector, bool dense, int cluster);
 
 // Set the kernels' function attributes on the current device (call once per
 // device before the first launch).

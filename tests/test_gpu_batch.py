@@ -152,6 +152,77 @@ def test_batch_one_cluster_multi_unit_pushes(oracle_mod):
             assert np.array_equal(o[k].cpu().numpy(), got[i][k]), (i, k)
 
 
+def _single_chain_outputs(C, sos, data_i, T_i, blocks):
+    import torch
+    from paper_2605_20132_gb300.chain import Chain
+    ch = Chain(C, sos, 1000.0, K, NS_, NL, outputs=ALL_OUT, max_chunk=3000)
+    ch.set_blocks_per_cta(blocks)
+    x = torch.from_numpy(data_i).cuda()
+    o = {k: torch.empty(data_i.shape, device="cuda") for k in ("ratio", "bp", "sp")}
+    t = 0
+    for n in T_i:
+        n = int(n)
+        ch.push(x[t:t + n], ratio=o["ratio"][t:t + n], bandpass=o["bp"][t:t + n], spatial=o["sp"][t:t + n])
+        t += n
+    ch.sync()
+    ch.close()
+    return {k: v.cpu().numpy() for k, v in o.items()}
+
+
+@pytest.mark.parametrize("blocks", [8, 4])
+def test_batch_short_pushes_share_clusters(oracle_mod, blocks):
+    """Pushes of at most 1,024 samples need fewer time ranges than a cluster
+    of 8 CTAs has, so the batched kernel runs 2, 4 or 8 channel tiles of a
+    stream in one cluster (ragged tile groups at the array end included).
+    With 8 or 4 blocks per CTA on both sides, every stream equals its
+    single-stream chain bit for bit; one stream is also held against the
+    oracle."""
+    from paper_2605_20132_gb300.chain import Batch
+    rng = np.random.default_rng(74)
+    Cs = [1000, 450, 57, 391]
+    # 1..40 samples: one time range; 300: 2 (8 blocks) or 3 (4 blocks); 1024: 4 or 8
+    T = np.array([[37, 300, 1024, 129], [1024, 7, 300, 640], [300, 640, 40, 1024], [129, 1024, 700, 1]])
+    data = [synth.small_stream(C, int(T[:, i].sum()), seed=75 + i) * np.float32(1.5) for i, C in enumerate(Cs)]
+    sos = small_sos(oracle_mod)
+    b = Batch(Cs, sos, 1000.0, K, NS_, NL, outputs=ALL_OUT, max_chunk=3000)
+    b.set_launch(8, 0, True)
+    b.set_blocks_per_cta(blocks)
+    assert b.info()["blocks_per_cta"] == blocks
+    got = run_batch(b, data, T)
+    b.close()
+    for i, C in enumerate(Cs):
+        ref = _single_chain_outputs(C, sos, data[i], T[:, i], blocks)
+        for k in ref:
+            assert np.array_equal(ref[k], got[i][k]), (blocks, i, k)
+    o = run_oracle(oracle_mod, data[2], sos, K=K, ns=NS_, nl=NL)
+    errs = compare(got[2], o)
+    assert all(e <= TOL for e in errs.values()), errs
+
+
+def test_batch_dense_carry_short_pushes():
+    """The dense carry (poles next to z = 1) in the batched kernel with tile
+    groups: bitwise equal to single-stream chains; it keeps 8 blocks per
+    CTA."""
+    from paper_2605_20132_gb300.chain import Batch
+    st, sos = abi.filark_butter_bandpass_sos(8, 0.01, 1.0, 1500.0)
+    assert st == abi.FILARK_OK
+    Cs = [300, 61]
+    T = np.array([[200, 900], [1024, 33], [500, 1024]])
+    data = [synth.small_stream(C, int(T[:, i].sum()), seed=80 + i) for i, C in enumerate(Cs)]
+    b = Batch(Cs, sos, 1000.0, K, NS_, NL, outputs=ALL_OUT, max_chunk=3000)
+    st, h = abi.filark_batch_stream(b._h, 0)
+    st, inf = abi.filark_chain_get_info(h)
+    assert inf.precision == abi.FILARK_PREC_DENSE64
+    assert abi.filark_batch_set_blocks_per_cta(b._h, 4) == abi.FILARK_ENOSYS
+    b.set_launch(8, 0, True)
+    got = run_batch(b, data, T)
+    b.close()
+    for i, C in enumerate(Cs):
+        ref = _single_chain_outputs(C, sos, data[i], T[:, i], 8)
+        for k in ref:
+            assert np.array_equal(ref[k], got[i][k]), (i, k)
+
+
 def test_batch_tune_then_stream(small_case):
     """The tuner times every geometry, keeps the fastest, and leaves every
     stream reset: streaming afterwards starts from a zero state."""
@@ -163,8 +234,10 @@ def test_batch_tune_then_stream(small_case):
     info = b.tune(scratch, ratios=[torch.empty_like(s) for s in scratch], timed_pushes=2)
     tuned = info["tuned"]
     assert {t["cluster"] for t in tuned} == {1, 2, 4, 8}
+    assert {t["blocks_per_cta"] for t in tuned} == {4, 8}
     best = min(tuned, key=lambda t: t["ms"])
     assert info["cluster"] == best["cluster"] and info["n_clusters"] == best["n_clusters"]
+    assert info["blocks_per_cta"] == best["blocks_per_cta"]
     got = run_batch(b, data, T)
     b.close()
     for i in range(len(Cs)):
@@ -205,6 +278,8 @@ def test_batch_rejects_bad_descriptor(small_case):
     d[1].n_samples = 3001
     assert abi.filark_batch_push(b._h, d, None) == abi.FILARK_EINVAL
     assert abi.filark_batch_set_launch(b._h, 3, 0, 1) == abi.FILARK_EINVAL
+    assert abi.filark_batch_set_blocks_per_cta(b._h, 3) == abi.FILARK_EINVAL
+    assert abi.filark_batch_set_blocks_per_cta(b._h, 9) == abi.FILARK_EINVAL
     b.close()
 
 
