@@ -554,8 +554,14 @@ filark_status filark_top_destroy(filark_top *t);   /* NULL ok */
  * with h through an FFT of N >= block_len + M - 1 points (hand-written Stockham
  * transform, two channels per complex transform), and the M-1 sample overlap
  * tail is carried across blocks and pushes.  block_len <= 0 picks N = the
- * power of two >= 2M.  N is limited to 8192 (FILARK_ENOSYS above).  taps: host,
- * M doubles, rounded to float.  Buffers as for filark_top_push.
+ * power of two >= 2M.  N is limited to 8192: up to M = 4096 a block_len that
+ * does not fit is shortened to 8193 - M; longer filters (M <= 2^24) are cut
+ * into partitions of 4096 taps, each block (at most 4096 samples) is
+ * transformed once and every partition's product with it is inverse
+ * transformed and added at the partition's offset (uniformly partitioned
+ * convolution).  filark_fftfilt_get_info reports the largest N and the block
+ * length in use.  taps: host, M doubles, rounded to float.  Buffers as for
+ * filark_top_push.
  */
 typedef struct filark_fftfilt filark_fftfilt;
 

@@ -29,6 +29,17 @@
 // arrays are padded by one element per 16 (element i at i + i/16), which
 // spreads the strided stores of the early passes over the banks.
 // N <= 8192; up to 6144 two CTAs of N / 16 threads share an SM.
+//
+// Filters longer than 4096 taps whose block would not fit the 8192-point
+// transform use a partitioned convolution: the taps are cut into P partitions
+// of B = 4096 (the last shorter), h_p = h[pB, pB + B), with one spectrum per
+// partition and transform size; a block of len <= B samples is transformed
+// once (its spectrum X stays in shared memory) and each partition adds
+// IFFT(X H_p), the block convolved with h_p, at block position pB.  The
+// partitions run in order inside the CTA: positions [pB, (p+1)B) are owned by
+// partition p (it adds the old tail there), and p's overhang past (p+1)B
+// (len - 1 positions) goes to the new tail as a partial sum that p + 1
+// completes.  Outputs are positions < len, which only partition 0 reaches.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -149,8 +160,8 @@ struct FftParams {
 };
 
 // Where a pass reads from and writes to.
-enum { SRC_SMEM = 0, SRC_GIN = 1 };
-enum { DST_SMEM = 0, DST_SMEM_H = 1, DST_GOUT = 2 };
+enum { SRC_SMEM = 0, SRC_GIN = 1, SRC_SMEM_H = 2 };
+enum { DST_SMEM = 0, DST_SMEM_H = 1, DST_GOUT = 2, DST_GOUT_PART = 3 };
 
 struct BlockIO {
     const float *x;         // input block, time-major, row stride ldx
@@ -166,6 +177,11 @@ struct BlockIO {
     long long ldy;
     int T1;                 // M - 1
     float scale;
+    // partitioned convolution (M + block length - 1 above the largest FFT):
+    // this transform is the block convolved with taps [off, off + lenp) of
+    // partition `part`; partitions are B taps long (the last may be shorter)
+    int off, lenp, B, part;
+    bool last_part;
 };
 
 // One Stockham pass of radix R: sub-transforms of length m are combined R at
@@ -181,7 +197,7 @@ __device__ __forceinline__ void radix_pass(const float2 *__restrict__ a, float2 
         const int base = k * R * m + j;
         // the old tail values this butterfly's outputs add (issued first: they
         // do not depend on the transform)
-        float2 told_q[DST == DST_GOUT ? R : 1];
+        float2 told_q[DST == DST_GOUT || DST == DST_GOUT_PART ? R : 1];
         if constexpr (DST == DST_GOUT) {
 #pragma unroll
             for (int q = 0; q < R; ++q) {
@@ -190,6 +206,27 @@ __device__ __forceinline__ void radix_pass(const float2 *__restrict__ a, float2 
                 if (i < io.T1) {
                     told_q[q].x = __ldg(io.told + (long long)io.c1 * io.T1 + i);
                     if (io.has2) told_q[q].y = __ldg(io.told + (long long)(io.c1 + 1) * io.T1 + i);
+                }
+            }
+        } else if constexpr (DST == DST_GOUT_PART) {
+            // what block position j = off + i already holds: the old tail,
+            // added by the partition that owns j (j in [part B, (part + 1) B),
+            // or the last partition), and the previous partition's overhang
+            // into [part B, part B + len - 1), which it left in the new tail
+#pragma unroll
+            for (int q = 0; q < R; ++q) {
+                const int i = base + q * m, j = io.off + i;
+                told_q[q] = make_float2(0.f, 0.f);
+                if (i < io.len + io.lenp - 1) {
+                    if ((i < io.B || io.last_part) && j < io.T1) {
+                        told_q[q].x = __ldg(io.told + (long long)io.c1 * io.T1 + j);
+                        if (io.has2) told_q[q].y = __ldg(io.told + (long long)(io.c1 + 1) * io.T1 + j);
+                    }
+                    if (io.part > 0 && i < io.len - 1) {
+                        // written by this CTA in the previous partition (plain loads)
+                        told_q[q].x += io.tnew[(long long)io.c1 * io.T1 + (j - io.len)];
+                        if (io.has2) told_q[q].y += io.tnew[(long long)(io.c1 + 1) * io.T1 + (j - io.len)];
+                    }
                 }
             }
         }
@@ -211,6 +248,8 @@ __device__ __forceinline__ void radix_pass(const float2 *__restrict__ a, float2 
                     }
                 }
                 x[r] = make_float2(re, im);
+            } else if constexpr (SRC == SRC_SMEM_H) {
+                x[r] = cmul(a[pad(i)], __ldg(io.H + i));
             } else {
                 x[r] = a[pad(i)];
             }
@@ -224,6 +263,25 @@ __device__ __forceinline__ void radix_pass(const float2 *__restrict__ a, float2 
                 b[pad(i)] = x[q];
             } else if constexpr (DST == DST_SMEM_H) {
                 b[pad(i)] = cmul(x[q], __ldg(io.H + i));
+            } else if constexpr (DST == DST_GOUT_PART) {
+                // block position j = off + i: an output (j < len, partition 0
+                // only, as B >= len) or new tail entry j - len
+                if (i < io.len + io.lenp - 1) {
+                    const int j = io.off + i;
+                    const float v1 = x[q].x * io.scale + told_q[q].x, v2 = x[q].y * io.scale + told_q[q].y;
+                    if (j < io.len) {
+                        float *dst = io.y + (long long)j * io.ldy + io.c1;
+                        if (io.pair_out) {
+                            *reinterpret_cast<float2 *>(dst) = make_float2(v1, v2);
+                        } else {
+                            dst[0] = v1;
+                            if (io.has2) dst[1] = v2;
+                        }
+                    } else {
+                        io.tnew[(long long)io.c1 * io.T1 + (j - io.len)] = v1;
+                        if (io.has2) io.tnew[(long long)(io.c1 + 1) * io.T1 + (j - io.len)] = v2;
+                    }
+                }
             } else {
                 // z[i] (scaled) plus the old tail gives output i (i < len) or
                 // new tail entry i - len (len <= i < len + M - 1)
@@ -297,6 +355,28 @@ __device__ void fft_inverse_out(const FftParams &fp, float2 *a, float2 *b, const
     }
 }
 
+// Inverse transform of X times io.H (the first pass multiplies as it reads, so
+// X is kept for the next partition), through the work buffers w1 and w2; the
+// last pass adds this partition's convolution into the outputs and the new
+// tail.  Needs at least two passes.
+__device__ void fft_inverse_part(const FftParams &fp, const float2 *X, float2 *w1, float2 *w2, const float2 *tw,
+                                 const BlockIO &io) {
+    const float2 *a = X;
+    float2 *b = w1;
+    for (int p = 0; p < fp.npass; ++p) {
+        const float2 *twp = tw + fp.toff[p];
+        if (p == fp.npass - 1) {
+            radix_pass_any<true, SRC_SMEM, DST_GOUT_PART>(fp.R[p], a, b, fp.N, fp.m[p], fp.mdiv[p], twp, io);
+        } else {
+            if (p == 0) radix_pass_any<true, SRC_SMEM_H, DST_SMEM>(fp.R[p], a, b, fp.N, fp.m[p], fp.mdiv[p], twp, io);
+            else radix_pass_any<true, SRC_SMEM, DST_SMEM>(fp.R[p], a, b, fp.N, fp.m[p], fp.mdiv[p], twp, io);
+            __syncthreads();
+            a = b;
+            b = (b == w1) ? w2 : w1;
+        }
+    }
+}
+
 // One CTA per (channel pair, block) of a launch; the blocks of one launch are
 // consecutive and independent given the tail, so a launch covers exactly one
 // block per channel pair and the host launches the blocks of a push in order.
@@ -341,8 +421,57 @@ __global__ void __launch_bounds__(kFftMaxThreads) fftfilt_block_kernel(const __g
     fft_inverse_out(fp, X, X == sm ? sm + NP : sm, stw, io);
 }
 
+// Partitioned convolution of one (channel pair, block): the block's spectrum X
+// stays in shared memory and each partition p of the taps adds X H_p, inverse
+// transformed, at block position p B; partitions run in order, so the
+// overhang of partition p into the next one (len - 1 positions) is left in
+// the new tail and completed by p + 1.  Three padded buffers.
+__global__ void __launch_bounds__(kFftMaxThreads) fftfilt_part_kernel(const __grid_constant__ FftParams fp,
+                                                                      const float *__restrict__ x, long long ldx,
+                                                                      int len, int C, int n_parts, int B,
+                                                                      const float2 *__restrict__ Hparts,
+                                                                      const float2 *__restrict__ tw,
+                                                                      const float *__restrict__ told,
+                                                                      float *__restrict__ tnew,
+                                                                      float *__restrict__ y, long long ldy) {
+    extern __shared__ float2 sm[];
+    const int NP = pad(fp.N);
+    float2 *stw = sm + 3 * NP;
+    for (int i = threadIdx.x; i < fp.twlen; i += blockDim.x) stw[i] = __ldg(tw + i);
+    BlockIO io;
+    io.x = x;
+    io.ldx = ldx;
+    io.len = len;
+    io.c1 = 2 * blockIdx.x;
+    io.has2 = io.c1 + 1 < C;
+    io.pair_in = io.has2 && (ldx & 1) == 0 && ((uintptr_t)x & 7u) == 0;
+    io.pair_out = io.has2 && (ldy & 1) == 0 && ((uintptr_t)y & 7u) == 0;
+    io.H = nullptr;
+    io.told = told;
+    io.tnew = tnew;
+    io.y = y;
+    io.ldy = ldy;
+    io.T1 = fp.M - 1;
+    io.scale = fp.scale;
+    io.B = B;
+    __syncthreads();
+    const float2 *X = fft_forward(fp, sm, sm + NP, stw, io);
+    float2 *w1 = X == sm ? sm + NP : sm, *w2 = sm + 2 * NP;
+    for (int part = 0; part < n_parts; ++part) {
+        io.H = Hparts + (long long)part * fp.N;
+        io.part = part;
+        io.off = part * B;
+        io.lenp = min(B, fp.M - part * B);
+        io.last_part = part == n_parts - 1;
+        fft_inverse_part(fp, X, w1, w2, stw, io);
+        // the next partition reads this one's overhang from the new tail and
+        // reuses the work buffers
+        __syncthreads();
+    }
+}
+
 __global__ void __launch_bounds__(kFftMaxThreads) fft_of_taps_kernel(const __grid_constant__ FftParams fp,
-                                                                     const float *__restrict__ h,
+                                                                     const float *__restrict__ h, int n,
                                                                      const float2 *__restrict__ tw,
                                                                      float2 *__restrict__ H) {
     extern __shared__ float2 sm[];
@@ -353,7 +482,7 @@ __global__ void __launch_bounds__(kFftMaxThreads) fft_of_taps_kernel(const __gri
     BlockIO io{};
     io.x = h;
     io.ldx = 1;
-    io.len = fp.M;
+    io.len = n;
     io.c1 = 0;
     io.has2 = false;
     io.H = nullptr;
@@ -361,8 +490,10 @@ __global__ void __launch_bounds__(kFftMaxThreads) fft_of_taps_kernel(const __gri
     for (int i = threadIdx.x; i < fp.N; i += blockDim.x) H[i] = r[pad(i)];
 }
 
-// two padded buffers and the twiddle table
-size_t fft_smem(int N, int twlen) { return sizeof(float2) * (2 * (size_t)pad_h(N) + (size_t)twlen); }
+// two padded buffers and the twiddle table (three for the partitioned kernel)
+size_t fft_smem(int N, int twlen, int buffers = 2) {
+    return sizeof(float2) * ((size_t)buffers * (size_t)pad_h(N) + (size_t)twlen);
+}
 
 // sizes 2^k and 3 * 2^k, 2 <= N <= kFftMaxN
 bool fft_size_ok(int N) {
@@ -387,7 +518,7 @@ struct FftSize {
     float2 *d_H = nullptr, *d_tw = nullptr;
 };
 
-void make_size(int N, int M, FftSize &z) {
+void make_size(int N, int M, FftSize &z, int buffers) {
     FftParams &fp = z.fp;
     std::memset(&fp, 0, sizeof(fp));
     fp.N = N;
@@ -422,18 +553,25 @@ void make_size(int N, int M, FftSize &z) {
     }
     if (z.tw.empty()) z.tw.push_back(make_float2(1.f, 0.f));
     fp.twlen = (int)z.tw.size();
-    z.smem = fft_smem(N, fp.twlen);
+    z.smem = fft_smem(N, fp.twlen, buffers);
     // two CTAs of N / 16 threads per SM where their shared memory fits, else
     // one CTA of up to N / 8 threads
     z.threads = z.smem <= kTwoCtaSmem ? std::max(32, N / 16) : std::max(32, std::min(kFftMaxThreads, N / 8));
 }
 
+// Partition length of the partitioned mode: blocks of at most this many
+// samples and partitions of this many taps fit the largest transform.
+constexpr int kPartB = kFftMaxN / 2;
+constexpr int kMaxTaps = 1 << 24;
+
 }  // namespace
 
 struct filark_fftfilt {
     int device = 0, C = 0, M = 0, L = 0, Nmax = 0;
+    int P = 0;                      // partitions of kPartB taps (0: one transform holds block + taps)
     long long max_chunk = 0;
-    std::vector<FftSize> sizes;     // ascending N: every size from the first >= M up to Nmax
+    std::vector<FftSize> sizes;     // ascending N: every size from the first >= M (or >= kPartB) up to Nmax;
+                                    // d_H holds P spectra of N points each in the partitioned mode
     float *tail[2] = {nullptr, nullptr};   // [C][M-1] each; tail[cur] is current
     int cur = 0;
 };
@@ -462,6 +600,7 @@ filark_status filark_fftfilt_create(int n_channels, int n_taps, const double *ta
         return fail_with(FILARK_EINVAL, "need n_channels >= 1, n_taps >= 1, taps, max_chunk >= 1");
     for (int k = 0; k < n_taps; ++k)
         if (!std::isfinite(taps[k])) return fail_with(FILARK_EINVAL, "non-finite tap");
+    if (n_taps > kMaxTaps) return fail_with(FILARK_EINVAL, "n_taps above 2^24");
     long long L = block_len;
     if (L <= 0) {
         // default: the largest block with N = 2 next_pow2(M) or more
@@ -469,7 +608,13 @@ filark_status filark_fftfilt_create(int n_channels, int n_taps, const double *ta
         while (n < 2LL * n_taps) n <<= 1;
         L = n - n_taps + 1;
     }
-    if (L + n_taps - 1 > kFftMaxN) return fail_with(FILARK_ENOSYS, "block_len + n_taps - 1 above the 8192-point FFT");
+    // Block and taps above the largest transform: up to kPartB taps the block
+    // is shortened to fit (at least kFftMaxN - kPartB + 1 samples); longer
+    // filters use the partitioned convolution, partitions of kPartB taps and
+    // blocks of at most kPartB samples.
+    const bool parted = L + n_taps - 1 > kFftMaxN && n_taps > kPartB;
+    if (parted) L = std::min<long long>(block_len > 0 ? block_len : kPartB, kPartB);
+    else if (L + n_taps - 1 > kFftMaxN) L = kFftMaxN - n_taps + 1;
     filark_fftfilt *f = new (std::nothrow) filark_fftfilt();
     if (!f) return fail_with(FILARK_ENOMEM, "host allocation failed");
     f->device = cuda_device;
@@ -477,10 +622,12 @@ filark_status filark_fftfilt_create(int n_channels, int n_taps, const double *ta
     f->M = n_taps;
     f->L = (int)L;
     f->max_chunk = max_chunk;
-    f->Nmax = fft_size_at_least((int)L + n_taps - 1);
-    for (int N = fft_size_at_least(n_taps); N > 0 && N <= f->Nmax; N = fft_size_at_least(N + 1)) {
+    f->P = parted ? (n_taps + kPartB - 1) / kPartB : 0;
+    const int span = parted ? kPartB : n_taps;   // taps one transform convolves with
+    f->Nmax = fft_size_at_least((int)L + span - 1);
+    for (int N = fft_size_at_least(span); N > 0 && N <= f->Nmax; N = fft_size_at_least(N + 1)) {
         f->sizes.emplace_back();
-        make_size(N, n_taps, f->sizes.back());
+        make_size(N, n_taps, f->sizes.back(), parted ? 3 : 2);
     }
     DeviceGuard dg(cuda_device);
     if (!dg.ok) {
@@ -495,18 +642,26 @@ filark_status filark_fftfilt_create(int n_channels, int n_taps, const double *ta
     const size_t tail_bytes = sizeof(float) * (size_t)n_channels * (size_t)(n_taps - 1);
     if (e == cudaSuccess && n_taps > 1) e = cudaMalloc(&f->tail[0], tail_bytes);
     if (e == cudaSuccess && n_taps > 1) e = cudaMalloc(&f->tail[1], tail_bytes);
-    const int max_smem = (int)fft_smem(kFftMaxN, kFftMaxN / 2);
+    size_t max_smem = 0;
+    for (const FftSize &z : f->sizes) max_smem = std::max(max_smem, z.smem);
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(fftfilt_block_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
+        e = parted ? cudaFuncSetAttribute(fftfilt_part_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)max_smem)
+                   : cudaFuncSetAttribute(fftfilt_block_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)max_smem);
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(fft_of_taps_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
+        e = cudaFuncSetAttribute(fft_of_taps_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)max_smem);
+    const int n_spec = parted ? f->P : 1;
     for (FftSize &z : f->sizes) {
-        if (e == cudaSuccess) e = cudaMalloc(&z.d_H, sizeof(float2) * (size_t)z.fp.N);
+        if (e == cudaSuccess) e = cudaMalloc(&z.d_H, sizeof(float2) * (size_t)z.fp.N * (size_t)n_spec);
         if (e == cudaSuccess) e = cudaMalloc(&z.d_tw, sizeof(float2) * z.tw.size());
         if (e == cudaSuccess)
             e = cudaMemcpy(z.d_tw, z.tw.data(), sizeof(float2) * z.tw.size(), cudaMemcpyHostToDevice);
-        if (e == cudaSuccess) {
-            fft_of_taps_kernel<<<1, z.threads, z.smem>>>(z.fp, dh, z.d_tw, z.d_H);
+        // the spectrum of the taps, or of each partition of kPartB taps
+        for (int q = 0; q < n_spec && e == cudaSuccess; ++q) {
+            const int n = parted ? std::min(kPartB, n_taps - q * kPartB) : n_taps;
+            fft_of_taps_kernel<<<1, z.threads, z.smem>>>(z.fp, dh + (size_t)q * kPartB, n, z.d_tw,
+                                                        z.d_H + (size_t)q * z.fp.N);
             e = cudaGetLastError();
         }
     }
@@ -538,16 +693,23 @@ filark_status filark_fftfilt_push(filark_fftfilt *f, const float *d_in, int64_t 
     const unsigned pairs = (unsigned)((f->C + 1) / 2);
     for (int64_t t = 0; t < n_samples; t += f->L) {
         const int len = (int)std::min<int64_t>(f->L, n_samples - t);
-        // the smallest size that holds this block's convolution
+        // the smallest size that holds this block's convolution (with the
+        // taps, or with one partition of them)
+        const int span = f->P ? kPartB : f->M;
         const FftSize *z = &f->sizes.back();
         for (const FftSize &c : f->sizes)
-            if (c.fp.N >= len + f->M - 1) {
+            if (c.fp.N >= len + span - 1) {
                 z = &c;
                 break;
             }
-        fftfilt_block_kernel<<<pairs, z->threads, z->smem, s>>>(z->fp, d_in + t * ld_in, ld_in, len, f->C, z->d_H,
-                                                                  z->d_tw, f->tail[f->cur], f->tail[1 - f->cur],
-                                                                  d_out + t * ld_out, ld_out);
+        if (f->P)
+            fftfilt_part_kernel<<<pairs, z->threads, z->smem, s>>>(z->fp, d_in + t * ld_in, ld_in, len, f->C, f->P,
+                                                                     kPartB, z->d_H, z->d_tw, f->tail[f->cur],
+                                                                     f->tail[1 - f->cur], d_out + t * ld_out, ld_out);
+        else
+            fftfilt_block_kernel<<<pairs, z->threads, z->smem, s>>>(z->fp, d_in + t * ld_in, ld_in, len, f->C,
+                                                                      z->d_H, z->d_tw, f->tail[f->cur],
+                                                                      f->tail[1 - f->cur], d_out + t * ld_out, ld_out);
         f->cur = 1 - f->cur;
     }
     const cudaError_t e = cudaGetLastError();

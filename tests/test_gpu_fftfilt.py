@@ -85,5 +85,35 @@ def test_fftfilt_reset_and_errors(oracle_mod):
     assert torch.equal(y1, y2)
     assert abi.filark_fftfilt_push(f._h, x.data_ptr(), 4, 5001, y1.data_ptr(), 4, None) == abi.FILARK_EINVAL
     f.close()
-    st, _ = abi.filark_fftfilt_create(4, np.ones(9000), 0, 100, 0)
-    assert st == abi.FILARK_ENOSYS
+    # a block that does not fit the 8192-point transform is shortened
+    g = FFTFilter(4, h, block_len=9000, max_chunk=100)
+    assert g.block_len == 8192 - 401 + 1 and g.fft_len == 8192
+    g.close()
+    st, _ = abi.filark_fftfilt_create(4, np.array([1.0, np.nan]), 0, 100, 0)
+    assert st == abi.FILARK_EINVAL
+
+
+@pytest.mark.parametrize("M,block_len,N", [(4097, 0, 30000), (5000, 0, 30000), (9000, 1000, 30000),
+                                           (12289, 0, 24000), (20001, 0, 16000), (3000, 7000, 30000)])
+def test_fftfilt_long_filters(oracle_mod, M, block_len, N):
+    """Filters beyond the single 8192-point transform: partitions of 4096
+    taps (the block transformed once, one inverse transform per partition,
+    overhangs completed by the next partition), against the direct FIR; and
+    a block too long for a 3000-tap filter, shortened to fit.  Five channels
+    (the last pair has one channel), chunks of 1 to 9000 samples, so blocks
+    of every length up to 4096 occur."""
+    rng = np.random.default_rng(160 + M)
+    C = 5
+    x = synth.small_stream(C, N, seed=160 + M)
+    h = synth.windowed_sinc_bandpass(M, 0.5, 50.0, 1000.0)
+    chunks = [1, 4096, 4097]
+    while sum(chunks) < N:
+        chunks.append(int(min(rng.integers(1, 9000), N - sum(chunks))))
+    got, info = run(x, h, chunks, block_len)
+    ref = oracle_mod.TemporalOp(C, oracle_mod.TOP_FIR, M, h.astype(np.float32).astype(np.float64)).push(x)
+    err = normwise(got, ref)
+    print("fftfilt long", M, block_len, info, err)
+    assert info[0] <= 8192
+    if M > 4096:
+        assert info[1] == (block_len or 4096)
+    assert err <= TOL
