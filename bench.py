@@ -35,6 +35,11 @@ NOMINAL_HBM_GBS = 7900.0
 # channel-tile groups pushed on the chain's own streams (filark_chain_set_lanes);
 # each step's outputs are joined into the timing stream at the step's end
 LANES = 2
+# a push is cut into launches of at most this many samples
+# (filark_chain_set_launch_samples); with pushes enqueued back to back, one
+# launch per push and lane is fastest here (1,024-sample launches in three
+# lanes: 94.9 against 85.6 us per push)
+LAUNCH_SAMPLES = 2048
 
 
 def workload():
@@ -251,6 +256,7 @@ def run_gpu(args, rank: int, world: int, dist) -> None:
     lib = abi.load()
     chain = Chain(C, sos, w["fs"], K, ns, nl, outputs=abi.FILARK_OUT_RATIO, max_chunk=T, device=local)
     chain.set_lanes(LANES)
+    chain.set_launch_samples(LAUNCH_SAMPLES)
     info = chain.info()
     stream = torch.cuda.Stream(device=dev)
     sh = stream.cuda_stream
@@ -294,7 +300,7 @@ def run_gpu(args, rank: int, world: int, dist) -> None:
         sampler.end()
     ms = max_over_ranks(ev0.elapsed_time(ev1), dist, dev)
     abi.check(abi.filark_chain_sync_status(h, sh), "sync")
-    launches_per_push = (T + 2047) // 2048
+    launches_per_push = -(-T // LAUNCH_SAMPLES)
     lanes = min(LANES, -(-C // info["tile_channels"]))
     launches = args.steps * n_push * launches_per_push * lanes
     value = whole_job_rate(C * N * args.steps, world, ms / 1e3)
@@ -364,7 +370,8 @@ def run_gpu(args, rank: int, world: int, dist) -> None:
         try:
             with open(tp) as f:
                 tj = json.load(f)
-            if tj.get("kernel_source_sha") == kernel_sha() and tj.get("lanes") == lanes:
+            if (tj.get("kernel_source_sha") == kernel_sha() and tj.get("lanes") == lanes
+                    and tj.get("launch_samples") == LAUNCH_SAMPLES):
                 traffic = tj.get("dram_bytes_per_push")
         except (OSError, ValueError):
             traffic = None
@@ -384,7 +391,7 @@ def run_gpu(args, rank: int, world: int, dist) -> None:
             "pushes_per_step": n_push, "sections": S, "spatial_width": K, "sta": ns, "lta": nl,
             "precision": {1: "modal32", 2: "dense64", 3: "all32"}.get(info["precision"], "?"),
             "l2": "inputs larger than L2 (2.16 GB per step)", "parallelism": "replicas" if world > 1 else "1 GPU",
-            "lanes": lanes,
+            "lanes": lanes, "launch_samples": LAUNCH_SAMPLES,
             "completion": "each step's 60 pushes complete on the timing stream at the step's end (filark_chain_join)"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
@@ -392,7 +399,8 @@ def run_gpu(args, rank: int, world: int, dist) -> None:
                                         "(taken on this kernel source; not measured in this run)")
                      if traffic is not None else "no capture on this kernel source",
                      "frac_of_nominal": achieved / NOMINAL_HBM_GBS,
-                     "unit_of_work": f"one push of {T} x {C} ({lanes} overlapping launches, one per lane)",
+                     "unit_of_work": f"one push of {T} x {C} ({lanes * launches_per_push} launches: "
+                                     f"{launches_per_push} per lane, the lanes overlapping)",
                      "bytes_per_push": bytes_push, "ms_per_push": ms_push},
         "stream_ordered": {"value": so_value, "unit": UNIT, "lanes": 1, "steps": so_steps,
                            "ms_per_push": ms_push_so,
@@ -826,7 +834,8 @@ def run_waves_workload(args) -> None:
                           "push_samples": T, "ctas_per_cluster": (nblk + 7) // 8, "outputs_per_tile": wout,
                           "rows": rows, "dtype": "f32", "data": "synthetic N(0,1) on the device"}), flush=True)
         del x, r
-    # the paper-scale chain in 1-4 lanes: 60 pushes, joined at the end
+    # the paper-scale chain in 1-4 lanes and launches of at most 2048, 1024 and
+    # 512 samples: 60 pushes, joined at the end
     C, T = w["n_channels"], w["chunk"]
     n_push = 60
     g = torch.Generator(device="cuda").manual_seed(0)
@@ -834,19 +843,22 @@ def run_waves_workload(args) -> None:
     r = torch.empty_like(x)
     ch = Chain(C, sos, w["fs"], w["spatial_width"], w["sta"], w["lta"], outputs=abi.FILARK_OUT_RATIO, max_chunk=T)
     rows = []
-    for lanes in range(1, abi.FILARK_MAX_LANES + 1):
-        ch.set_lanes(lanes)
+    for launch in (2048, 1024, 512):
+        ch.set_launch_samples(launch)
+        for lanes in range(1, abi.FILARK_MAX_LANES + 1):
+            ch.set_lanes(lanes)
 
-        def lstep():
-            for t in range(0, n_push * T, T):
-                ch.push(x[t:t + T], ratio=r[t:t + T])
-            ch.join()
+            def lstep():
+                for t in range(0, n_push * T, T):
+                    ch.push(x[t:t + T], ratio=r[t:t + T])
+                ch.join()
 
-        for _ in range(3):
-            lstep()
-        ms = _event_ms(lstep, max(1, min(args.steps, 5)))
-        us = ms / n_push * 1e3
-        rows.append({"lanes": lanes, "us_per_push": round(us, 2), "channel_samples_per_s": C * T / (us / 1e6)})
+            for _ in range(3):
+                lstep()
+            ms = _event_ms(lstep, max(1, min(args.steps, 5)))
+            us = ms / n_push * 1e3
+            rows.append({"launch_samples": launch, "lanes": lanes, "us_per_push": round(us, 2),
+                         "channel_samples_per_s": C * T / (us / 1e6)})
     ch.close()
     print(json.dumps({"workload": f"chain-lanes-{C}ch-T{T}", "metric": "device time per push", "rows": rows,
                       "dtype": "f32", "data": "synthetic N(0,1) on the device"}), flush=True)
@@ -854,7 +866,7 @@ def run_waves_workload(args) -> None:
 
 def ncu_case() -> None:
     """Small profiling case for ncu captures: the paper-scale chain on 6,000
-    channels in the benchmark's lanes (one launch per lane and push), 4 pushes
+    channels in the benchmark's lanes and launch length, 4 pushes
     of 1,500 samples of Gaussian noise (144 MB of input, larger than L2), ratio
     output only."""
     import torch
@@ -869,6 +881,7 @@ def ncu_case() -> None:
     ch = Chain(C, butter_bandpass(w["order"], *w["band"], w["fs"]), w["fs"], w["spatial_width"], w["sta"],
                w["lta"], outputs=abi.FILARK_OUT_RATIO, max_chunk=T)
     ch.set_lanes(LANES)
+    ch.set_launch_samples(LAUNCH_SAMPLES)
     for i in range(n_push):
         ch.push(x[i * T:(i + 1) * T], ratio=r[i * T:(i + 1) * T])
     ch.sync()

@@ -202,6 +202,23 @@ filark_status filark_chain_host_sync(filark_chain *h, filark_stream_t stream);
 filark_status filark_chain_set_blocks_per_cta(filark_chain *h, int blocks_per_cta);
 
 /*
+ * Samples per launch (no counterpart in the paper): a push is cut into
+ * launches of at most `samples` samples, a multiple of 256 in 256..2048
+ * (0 selects the default, 2048).  A launch's tile runs as a cluster of
+ * ceil(samples / 256) CTAs; clusters of 4 pack the SMs more tightly than
+ * clusters of 6 or 8, but a push then takes more, smaller launches, and
+ * which wins depends on how the lanes' launches interleave.  GB300, 6,000
+ * channels, pushes of 1,500: enqueued back to back, one launch per push in
+ * two lanes is fastest (85.6 us per push; 1,024 + 476 in three lanes:
+ * 94.9 us); with the pushes enqueued about 40 us apart, 1,024 + 476 in three
+ * lanes measured 83.3 us against 86.3 us.  The carried state crosses launch
+ * boundaries in FP64 / double-float, so outputs are equal within rounding for
+ * every setting and bit-identical for the same setting.  FILARK_EINVAL
+ * otherwise.  Takes effect at the next push.
+ */
+filark_status filark_chain_set_launch_samples(filark_chain *h, int samples);
+
+/*
  * Lanes (no counterpart in the paper: a throughput mode for pushes that are
  * queued back to back, e.g. a recording replayed from storage).  A launch
  * waits for the whole previous launch before it touches the carried state, so

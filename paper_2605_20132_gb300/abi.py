@@ -43,7 +43,7 @@ FILARK_HOST_SLOTS = 3
 EXPORTED = (
     "filark_chain_create", "filark_chain_push_chunk", "filark_chain_push_chunk_host",
     "filark_chain_push_host_async", "filark_chain_host_sync", "filark_chain_set_blocks_per_cta",
-    "filark_chain_set_lanes", "filark_chain_join",
+    "filark_chain_set_lanes", "filark_chain_join", "filark_chain_set_launch_samples",
     "filark_chain_reset_state", "filark_chain_destroy", "filark_chain_get_state",
     "filark_chain_set_state", "filark_chain_sync_status", "filark_chain_get_info",
     "filark_butter_bandpass_sos", "filark_last_error_string", "filark_abi_version",
@@ -169,6 +169,7 @@ def load(build_if_missing: bool = True) -> ct.CDLL:
             "filark_chain_host_sync": ([vp, vp], ct.c_int),
             "filark_chain_set_blocks_per_cta": ([vp, ct.c_int], ct.c_int),
             "filark_chain_set_lanes": ([vp, ct.c_int], ct.c_int),
+            "filark_chain_set_launch_samples": ([vp, ct.c_int], ct.c_int),
             "filark_chain_join": ([vp, vp], ct.c_int),
             "filark_chain_reset_state": ([vp, vp], ct.c_int),
             "filark_chain_destroy": ([vp], ct.c_int),
@@ -271,6 +272,10 @@ def filark_chain_host_sync(h, stream) -> int:
 
 def filark_chain_set_blocks_per_cta(h, blocks_per_cta: int) -> int:
     return load().filark_chain_set_blocks_per_cta(h, blocks_per_cta)
+
+
+def filark_chain_set_launch_samples(h, samples: int) -> int:
+    return load().filark_chain_set_launch_samples(h, samples)
 
 
 def filark_chain_set_lanes(h, lanes: int) -> int:

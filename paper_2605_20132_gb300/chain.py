@@ -124,6 +124,9 @@ class Chain:
         abi.check(abi.filark_chain_set_blocks_per_cta(self._h, int(blocks_per_cta)),
                   "filark_chain_set_blocks_per_cta")
 
+    def set_launch_samples(self, samples: int) -> None:
+        abi.check(abi.filark_chain_set_launch_samples(self._h, int(samples)), "filark_chain_set_launch_samples")
+
     def set_lanes(self, lanes: int) -> None:
         """1 (default): every push completes on its stream.  2..FILARK_MAX_LANES:
         channel-tile groups on internal streams; a push's outputs are valid

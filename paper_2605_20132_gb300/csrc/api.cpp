@@ -184,7 +184,7 @@ filark_status push_device(filark_chain *h, const float *d_in, int64_t ld_in, int
     }
     int64_t done = 0;
     while (done < T) {
-        const int Tl = (int)std::min<int64_t>(T - done, kMaxLaunchSamples);
+        const int Tl = (int)std::min<int64_t>(T - done, h->launch_samples);
         ChainParams p = h->base;
         ChainUnit &u = p.u;
         u.x = d_in + done * ld_in;
@@ -585,6 +585,15 @@ filark_status filark_chain_set_blocks_per_cta(filark_chain *h, int blocks_per_ct
     if (!h) return fail(FILARK_EINVAL, "chain is NULL");
     if (blocks_per_cta < 0 || blocks_per_cta > kNB) return fail(FILARK_EINVAL, "blocks_per_cta must be in 0..8");
     h->nbc_fixed = blocks_per_cta;
+    return FILARK_OK;
+}
+
+filark_status filark_chain_set_launch_samples(filark_chain *h, int samples) {
+    if (!h) return fail(FILARK_EINVAL, "chain is NULL");
+    if (samples == 0) samples = kMaxLaunchSamples;
+    if (samples < kTileRows || samples > kMaxLaunchSamples || samples % kTileRows != 0)
+        return fail(FILARK_EINVAL, "samples per launch must be a multiple of 256 in 256..2048");
+    h->launch_samples = samples;
     return FILARK_OK;
 }
 

@@ -34,6 +34,7 @@ struct filark_chain {
     int64_t device_bytes = 0;
     int use_pdl = 1;
     int nbc_fixed = 0;            // blocks per CTA set by the caller, 0 = kNB
+    int launch_samples = filark::kMaxLaunchSamples;   // a push is cut into launches of at most this many samples
     // lanes: the channel tiles split into `lanes` contiguous groups, each
     // pushed on an internal stream of its own; a push forks from the caller's
     // stream, and filark_chain_join (or any call that reads or resets the

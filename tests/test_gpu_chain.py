@@ -356,14 +356,16 @@ def test_paper_scale_parity_sampled(oracle_mod, paper_scale):
 
 def test_paper_scale_benchmark_configuration(oracle_mod, paper_scale):
     """The benchmark's own configuration: the paper-scale stream pushed as 60
-    chunks of 1,500 samples in two lanes (tiles 0-53 and 54-107) with the SOS
+    chunks of 1,500 samples in the benchmark's lanes and launch length (each
+    push cut into launches of at most LAUNCH_SAMPLES samples) with the SOS
     from the library's Butterworth designer and the ratio as the only output,
     as the benchmark line times it.  Its ratio is compared with the FP64
-    oracle on sampled channel windows: both array ends, the middle, and the
-    boundary between the two lanes' tile groups (channel 54 x 56 = 3024).  A
-    second run with every output enabled gives the identical ratio and its
-    bandpass and spatial outputs are compared there too."""
+    oracle on sampled channel windows: both array ends, the middle, and every
+    boundary between two lanes' tile groups.  A second run with every output
+    enabled gives the identical ratio and its bandpass and spatial outputs are
+    compared there too."""
     import torch
+    from bench import LANES, LAUNCH_SAMPLES
     from paper_2605_20132_gb300.chain import Chain, butter_bandpass
     x = paper_scale
     N, C = x.shape
@@ -374,7 +376,8 @@ def test_paper_scale_benchmark_configuration(oracle_mod, paper_scale):
 
     def run(outputs):
         ch = Chain(C, sos, cfg["fs"], K, ns, nl, outputs=outputs, max_chunk=T)
-        ch.set_lanes(2)
+        ch.set_lanes(LANES)
+        ch.set_launch_samples(LAUNCH_SAMPLES)
         assert ch.info()["tile_channels"] == 56
         names = ["ratio"] + (["bp", "sp"] if outputs != abi.FILARK_OUT_RATIO else [])
         outs = {k: torch.full((N, C), float("nan"), device="cuda") for k in names}
@@ -392,7 +395,9 @@ def test_paper_scale_benchmark_configuration(oracle_mod, paper_scale):
     assert torch.equal(bench["ratio"], full["ratio"])
     h = (K - 1) // 2
     worst = {}
-    for lo, hi in [(0, 24), (2988, 3012), (3008, 3040), (5976, 6000)]:
+    n_tiles = -(-C // 56)
+    bounds = [(n_tiles * l // LANES) * 56 for l in range(1, LANES)]
+    for lo, hi in [(0, 24), (2988, 3012), (5976, 6000)] + [(b - 16, b + 16) for b in bounds]:
         a, b = max(0, lo - h), min(C, hi + h)
         ref = run_oracle(oracle_mod, np.ascontiguousarray(x[:, a:b]), sos, K=K, ns=ns, nl=nl)
         sel = slice(lo - a, hi - a)

@@ -224,3 +224,48 @@ def test_lanes_paper_scale_first_pushes_bitwise(oracle_mod):
             assert np.array_equal(outs[k].cpu().numpy(), one[k]), (rep, k)
         ch.reset()
     ch.close()
+
+
+def test_launch_samples_lanes_bitwise():
+    """Pushes cut into launches of at most 1,024 (and 512) samples: three
+    lanes equal one lane bit for bit for the same launch length, on the
+    paper-scale chain with pushes of 3,000 / 1,500 / 2,500 / 1,024 / 1,500
+    samples (ragged last launches); the length must be a multiple of 256 in
+    256..2048 (0 restores 2048)."""
+    import torch
+    from paper_2605_20132_gb300.chain import Chain, butter_bandpass
+    cfg = synth.PAPER_SCALE
+    C, fs = cfg["n_channels"], cfg["fs"]
+    chunks = [3000, 1500, 2500, 1024, 1500]
+    N = sum(chunks)
+    x = torch.from_numpy(synth.paper_scale_stream(C, N, seed=49)).cuda()
+    sos = butter_bandpass(cfg["order"], *cfg["band"], fs)
+    K, ns, nl = cfg["spatial_width"], cfg["sta"], cfg["lta"]
+
+    def run(lanes, launch):
+        ch = Chain(C, sos, fs, K, ns, nl, outputs=ALL_OUT, max_chunk=max(chunks))
+        ch.set_lanes(lanes)
+        ch.set_launch_samples(launch)
+        outs = {k: torch.full(x.shape, float("nan"), device="cuda") for k in ("ratio", "bp", "sp")}
+        t = 0
+        for T in chunks:
+            sl = slice(t, t + T)
+            ch.push(x[sl], ratio=outs["ratio"][sl], bandpass=outs["bp"][sl], spatial=outs["sp"][sl])
+            t += T
+        ch.join()
+        ch.sync()
+        ch.close()
+        return outs
+
+    for launch in (1024, 512):
+        one, three = run(1, launch), run(3, launch)
+        for k in one:
+            assert torch.equal(one[k], three[k]), (launch, k)
+            assert torch.isfinite(one[k]).all(), (launch, k)
+    ch = Chain(16, sos, fs, K, ns, nl, outputs=ALL_OUT, max_chunk=100)
+    for bad in (-256, 100, 300, 2304):
+        assert abi.filark_chain_set_launch_samples(ch._h, bad) == abi.FILARK_EINVAL
+    for good in (0, 256, 2048):
+        assert abi.filark_chain_set_launch_samples(ch._h, good) == abi.FILARK_OK
+    ch.close()
+
