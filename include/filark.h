@@ -342,18 +342,19 @@ filark_status filark_chain_run_static(const filark_chain_config *cfg, const floa
  * (buf[t * ld + c], ld >= n_channels).  Arithmetic is double-float (FP32 pairs, ~48 bits) on the device.
  *
  * Checkpointing: the forward stores only the cascade state (2 * n_sections
- * doubles per channel) at the start of every segment, in the caller's d_ckpt
- * buffer of filark_iir_ckpt_bytes(...) bytes.  Segments are ckpt_every
- * samples long unless n_channels x ceil(n_samples / ckpt_every) is below
- * 2^17 (too few (segment, channel) threads to fill the GPU): then they are
- * shortened to ceil(ckpt_every / f), f = ceil(2^17 / that product), but not
- * below min(ckpt_every, 128) samples.  The backward recomputes the section
- * signals from those checkpoints, a piece of about sqrt(2 * L) samples at a
- * time (L the segment length), in the caller's d_work buffer of
- * filark_iir_work_bytes(...) bytes -- about (L / P * 2S + P * S + 8S) doubles
- * per channel per segment, P the piece length, rather than n_samples *
- * n_sections doubles per channel for all intermediates.  Both size queries
- * return 0 for invalid sizes and depend only on their arguments.
+ * doubles per channel) at the start of every piece of P ~ sqrt(2 * L) samples
+ * of every segment (L the segment length), in the caller's d_ckpt buffer of
+ * filark_iir_ckpt_bytes(...) bytes -- about L / P * 2S doubles per channel and
+ * segment.  Segments are ckpt_every samples long unless n_channels x
+ * ceil(n_samples / ckpt_every) is below 2^17 (too few (segment, channel)
+ * threads to fill the GPU): then they are shortened to ceil(ckpt_every / f),
+ * f = ceil(2^17 / that product), but not below min(ckpt_every, 128) samples.
+ * The backward recomputes the section signals from those checkpoints, one
+ * piece at a time, in the caller's d_work buffer of filark_iir_work_bytes(...)
+ * bytes -- about (P * S + 8S) doubles per channel and segment -- rather than
+ * n_samples * n_sections doubles per channel for all intermediates.  Both
+ * size queries return 0 for invalid sizes and depend only on their
+ * arguments.
  *
  * Buffers are 8-byte aligned device memory owned by the caller; d_ckpt must
  * hold the checkpoints of a forward with the same sos, sizes and input when the

@@ -3,9 +3,11 @@
 The forward and the backward are the library's CUDA kernels
 (filark_iir_forward_ckpt / filark_iir_backward); this module only allocates
 the checkpoint and work buffers with torch and marshals pointers.  The
-forward keeps the cascade state at most ``ckpt_every`` samples apart (closer
-when the channels are too few to fill the GPU) and nothing else; the backward recomputes the section signals from those checkpoints and
-runs the reverse-time adjoint (Sec. 3.4, the SOS filter, differentiated).
+forward keeps the cascade state at the start of every piece of about
+sqrt(2 L) samples of segments of at most ``ckpt_every`` samples (shorter when
+the channels are too few to fill the GPU) and nothing else; the backward
+recomputes the section signals piece by piece from those checkpoints and runs
+the reverse-time adjoint (Sec. 3.4, the SOS filter, differentiated).
 
 x: (n_samples, n_channels) float32 CUDA tensor, time-major (row stride >=
 n_channels, unit channel stride).  sos: (n_sections, 6) float64 tensor of raw

@@ -239,12 +239,14 @@ __global__ void __launch_bounds__(kChainThreads) chain_segments_kernel(const __g
     }
 }
 
-// F3: rerun every segment from its checkpoint, writing y.
+// F3: rerun every segment from its checkpoint, writing y (if asked for) and
+// the state at the start of every later piece of P samples (the pieces the
+// backward recomputes one at a time), checkpoint rows p * 2S + r.
 template <int S>
 __global__ void __launch_bounds__(kAdjThreads) fwd_run_kernel(const __grid_constant__ SosCoef k,
                                                               const __grid_constant__ Geometry g,
                                                               const float *__restrict__ x, long long ldx,
-                                                              const double *__restrict__ ckpt,
+                                                              double *__restrict__ ckpt,
                                                               float *__restrict__ y, long long ldy) {
     const long long T = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (T >= g.NT) return;
@@ -258,11 +260,21 @@ __global__ void __launch_bounds__(kAdjThreads) fwd_run_kernel(const __grid_const
         z[s][0] = ld_dd(ckpt + ix(2 * s, g.NT, T));
         z[s][1] = ld_dd(ckpt + ix(2 * s + 1, g.NT, T));
     }
+    long long next = t0 + g.P, p = 1;
     for (long long n = t0; n < t1; ++n) {
+        if (n == next) {
+#pragma unroll
+            for (int s = 0; s < S; ++s) {
+                st_dd(ckpt + ix(p * (2 * S) + 2 * s, g.NT, T), z[s][0]);
+                st_dd(ckpt + ix(p * (2 * S) + 2 * s + 1, g.NT, T), z[s][1]);
+            }
+            ++p;
+            next += g.P;
+        }
         dd u = dd_f(x[n * ldx + c]);
 #pragma unroll
         for (int s = 0; s < S; ++s) u = tdf2_dd(k, s, u, z[s][0], z[s][1]);
-        y[n * ldy + c] = dd_to_f(u);
+        if (y) y[n * ldy + c] = dd_to_f(u);
     }
 }
 
@@ -297,10 +309,27 @@ __global__ void __launch_bounds__(kAdjThreads) adj_local_kernel(const __grid_con
     }
 }
 
-// B3: gradients.  Sweep 1 stores the forward state every P samples; then the
-// pieces are handled last to first: recompute the piece's section outputs
-// into `sig` ([p][s][NT]), run the adjoint over it backwards from the true
-// adjoint state, accumulate the coefficient gradients, write dL/dx.
+// acc += a * b for double-float a, b, the accumulator kept unnormalised: the
+// leading product split exactly (TwoProduct by FMA) and summed exactly into
+// acc.hi (TwoSum), its rounding error and the cross terms gathered in acc.lo
+// (as in the compensated dot product of Ogita, Rump and Oishi, 2005).
+__device__ __forceinline__ void dd_acc_mul(dd &acc, dd a, dd b) {
+    const float p = __fmul_rn(a.hi, b.hi);
+    float e = fmaf(a.hi, b.hi, -p);
+    e = fmaf(a.hi, b.lo, e);
+    e = fmaf(a.lo, b.hi, e);
+    const float s = __fadd_rn(acc.hi, p);
+    const float bb = __fsub_rn(s, acc.hi);
+    const float err = __fadd_rn(__fsub_rn(acc.hi, __fsub_rn(s, bb)), __fsub_rn(p, bb));
+    acc.lo = __fadd_rn(acc.lo, __fadd_rn(err, e));
+    acc.hi = s;
+}
+
+// B3: gradients.  The pieces (the forward left the state at each piece start
+// in the checkpoints) are handled last to first: recompute the piece's
+// section outputs into `sig` ([p][s][NT]), run the adjoint over it backwards
+// from the true adjoint state, accumulate the coefficient gradients, write
+// dL/dx.
 template <int S>
 __global__ void __launch_bounds__(kAdjThreads) adj_run_kernel(const __grid_constant__ SosCoef k,
                                                               const __grid_constant__ Geometry g,
@@ -308,7 +337,7 @@ __global__ void __launch_bounds__(kAdjThreads) adj_run_kernel(const __grid_const
                                                               const float *__restrict__ gy, long long ldg,
                                                               const double *__restrict__ ckpt,
                                                               const double *__restrict__ beta,
-                                                              double *__restrict__ sub, double *__restrict__ sig,
+                                                              double *__restrict__ sig,
                                                               float *__restrict__ gx, long long ldgx,
                                                               double *__restrict__ gpart) {
     const long long T = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -319,30 +348,6 @@ __global__ void __launch_bounds__(kAdjThreads) adj_run_kernel(const __grid_const
     long long t0, t1;
     seg_range(g, seg, t0, t1);
     const long long npiece = (t1 - t0 + g.P - 1) / g.P;
-
-    // sweep 1: piece start states
-    {
-        dd z[S][2];
-#pragma unroll
-        for (int s = 0; s < S; ++s) {
-            z[s][0] = ld_dd(ckpt + ix(2 * s, NT, T));
-            z[s][1] = ld_dd(ckpt + ix(2 * s + 1, NT, T));
-        }
-        for (long long p = 0; p < npiece; ++p) {
-#pragma unroll
-            for (int s = 0; s < S; ++s) {
-                st_dd(sub + ix(p * (2 * S) + 2 * s, NT, T), z[s][0]);
-                st_dd(sub + ix(p * (2 * S) + 2 * s + 1, NT, T), z[s][1]);
-            }
-            if (p == npiece - 1) break;
-            const long long a = t0 + p * g.P;
-            for (long long n = a; n < a + g.P; ++n) {
-                dd u = dd_f(x[n * ldx + c]);
-#pragma unroll
-                for (int s = 0; s < S; ++s) u = tdf2_dd(k, s, u, z[s][0], z[s][1]);
-            }
-        }
-    }
 
     dd w1[S], w2[S], gb[S][3], ga[S][3];
 #pragma unroll
@@ -359,8 +364,8 @@ __global__ void __launch_bounds__(kAdjThreads) adj_run_kernel(const __grid_const
             dd z[S][2];
 #pragma unroll
             for (int s = 0; s < S; ++s) {
-                z[s][0] = ld_dd(sub + ix(p * (2 * S) + 2 * s, NT, T));
-                z[s][1] = ld_dd(sub + ix(p * (2 * S) + 2 * s + 1, NT, T));
+                z[s][0] = ld_dd(ckpt + ix(p * (2 * S) + 2 * s, NT, T));
+                z[s][1] = ld_dd(ckpt + ix(p * (2 * S) + 2 * s + 1, NT, T));
             }
             for (long long n = a; n < b; ++n) {
                 dd u = dd_f(x[n * ldx + c]);
@@ -380,12 +385,12 @@ __global__ void __launch_bounds__(kAdjThreads) adj_run_kernel(const __grid_const
                 const dd wn1 = w1[s], wn2 = w2[s];
                 dd w;
                 gg = adj_dd(k, s, gg, w1[s], w2[s], w);
-                gb[s][0] = gb[s][0] + us * w;
-                gb[s][1] = gb[s][1] + us * wn1;
-                gb[s][2] = gb[s][2] + us * wn2;
-                ga[s][0] = ga[s][0] - ys * w;
-                ga[s][1] = ga[s][1] - ys * wn1;
-                ga[s][2] = ga[s][2] - ys * wn2;
+                dd_acc_mul(gb[s][0], us, w);
+                dd_acc_mul(gb[s][1], us, wn1);
+                dd_acc_mul(gb[s][2], us, wn2);
+                dd_acc_mul(ga[s][0], ys, w);     // negated at the end
+                dd_acc_mul(ga[s][1], ys, wn1);
+                dd_acc_mul(ga[s][2], ys, wn2);
             }
             if (gx) gx[n * ldgx + c] = dd_to_f(gg);
         }
@@ -395,7 +400,7 @@ __global__ void __launch_bounds__(kAdjThreads) adj_run_kernel(const __grid_const
 #pragma unroll
         for (int i = 0; i < 3; ++i) {
             gpart[ix(6 * s + i, NT, T)] = (double)gb[s][i].hi + (double)gb[s][i].lo;
-            gpart[ix(6 * s + 3 + i, NT, T)] = (double)ga[s][i].hi + (double)ga[s][i].lo;
+            gpart[ix(6 * s + 3 + i, NT, T)] = -((double)ga[s][i].hi + (double)ga[s][i].lo);
         }
 }
 
@@ -531,12 +536,11 @@ bool make_geometry(int S, int C, long long N, long long ckpt, Geometry &g) {
     return true;
 }
 
-size_t ckpt_doubles(const Geometry &g, int S) { return (size_t)g.NT * (size_t)(2 * S); }
+// checkpoints: the state at every piece start, [npiece * 2S][NT]
+size_t ckpt_doubles(const Geometry &g, int S) { return (size_t)g.NT * (size_t)(g.npiece * 2 * S); }
 
-// workspace: beta [2S][NT], sub [npiece*2S][NT], sig [P*S][NT], gpart [6S][NT]
-size_t work_doubles(const Geometry &g, int S) {
-    return (size_t)g.NT * (size_t)(2 * S + g.npiece * 2 * S + g.P * S + 6 * S);
-}
+// workspace: beta [2S][NT], sig [P*S][NT], gpart [6S][NT]
+size_t work_doubles(const Geometry &g, int S) { return (size_t)g.NT * (size_t)(2 * S + g.P * S + 6 * S); }
 
 bool check_sos(const double *sos, int S, SosCoef &k) {
     if (!sos || !load_coef(sos, S, k)) {
@@ -562,7 +566,7 @@ void launch_forward(const SosCoef &k, const Transition &tr, const Geometry &g, c
     const unsigned nc = (unsigned)((g.C * chain_group<S>() + kChainThreads - 1) / kChainThreads);
     fwd_local_kernel<S><<<nb, kAdjThreads, 0, st>>>(k, g, x, ldx, ckpt);
     chain_segments_kernel<S><<<nc, kChainThreads, 0, st>>>(tr, g, ckpt, 0);
-    if (y) fwd_run_kernel<S><<<nb, kAdjThreads, 0, st>>>(k, g, x, ldx, ckpt, y, ldy);
+    fwd_run_kernel<S><<<nb, kAdjThreads, 0, st>>>(k, g, x, ldx, ckpt, y, ldy);
 }
 
 template <int S>
@@ -572,12 +576,11 @@ void launch_backward(const SosCoef &k, const Transition &tr, const Geometry &g, 
     const unsigned nb = (unsigned)((g.NT + kAdjThreads - 1) / kAdjThreads);
     const unsigned nc = (unsigned)((g.C * chain_group<S>() + kChainThreads - 1) / kChainThreads);
     double *beta = work;
-    double *sub = beta + (size_t)g.NT * (2 * S);
-    double *sig = sub + (size_t)g.NT * (size_t)(g.npiece * 2 * S);
+    double *sig = beta + (size_t)g.NT * (2 * S);
     double *gpart = sig + (size_t)g.NT * (size_t)(g.P * S);
     adj_local_kernel<S><<<nb, kAdjThreads, 0, st>>>(k, g, gy, ldg, beta);
     chain_segments_kernel<S><<<nc, kChainThreads, 0, st>>>(tr, g, beta, 1);
-    adj_run_kernel<S><<<nb, kAdjThreads, 0, st>>>(k, g, x, ldx, gy, ldg, ckpt, beta, sub, sig, gx, ldgx, gpart);
+    adj_run_kernel<S><<<nb, kAdjThreads, 0, st>>>(k, g, x, ldx, gy, ldg, ckpt, beta, sig, gx, ldgx, gpart);
     sum_partials_kernel<<<6 * S, kSumThreads, 0, st>>>(gpart, g.NT, gsos);
 }
 

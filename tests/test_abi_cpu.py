@@ -188,16 +188,16 @@ def _segment(C, N, ckpt):
 @pytest.mark.parametrize("S,C,N,ckpt", [(4, 2048, 30000, 3000), (1, 1, 1, 1), (8, 37, 777, 100), (4, 16, 2000, 5000),
                                         (4, 6000, 90000, 3000), (2, 100, 10**6, 1000)])
 def test_iir_buffer_sizes(S, C, N, ckpt):
-    """Checkpoints: 2S doubles per channel per segment; work: the adjoint
-    states, piece states, one piece of section signals and the gradient
-    partials per (segment, channel)."""
+    """Checkpoints: 2S doubles per channel at every piece start of every
+    segment; work: the adjoint states, one piece of section signals and the
+    gradient partials per (segment, channel)."""
     seg = _segment(C, N, ckpt)
     assert seg <= ckpt
     nseg = -(-N // seg)
     P = _piece(seg)
     npiece = -(-min(seg, N) // P)
-    assert abi.filark_iir_ckpt_bytes(S, C, N, ckpt) == 8 * nseg * C * 2 * S
-    assert abi.filark_iir_work_bytes(S, C, N, ckpt) == 8 * nseg * C * (2 * S + npiece * 2 * S + P * S + 6 * S)
+    assert abi.filark_iir_ckpt_bytes(S, C, N, ckpt) == 8 * nseg * C * npiece * 2 * S
+    assert abi.filark_iir_work_bytes(S, C, N, ckpt) == 8 * nseg * C * (2 * S + P * S + 6 * S)
 
 
 def test_iir_segments_fill_the_gpu_only_when_needed():
@@ -205,8 +205,9 @@ def test_iir_segments_fill_the_gpu_only_when_needed():
     differentiation workload (2048 x 30,000, every 3000) is cut finer."""
     assert _segment(6000, 90000, 3000) == 3000
     assert _segment(2048, 30000, 3000) == 429
-    assert abi.filark_iir_ckpt_bytes(4, 6000, 90000, 3000) == 8 * 30 * 6000 * 8
-    assert abi.filark_iir_ckpt_bytes(4, 2048, 30000, 3000) == 8 * 70 * 2048 * 8
+    # pieces of ceil(sqrt(2 L)) samples: 78 for L = 3000 (39 pieces), 30 for 429 (15)
+    assert abi.filark_iir_ckpt_bytes(4, 6000, 90000, 3000) == 8 * 30 * 6000 * 39 * 8
+    assert abi.filark_iir_ckpt_bytes(4, 2048, 30000, 3000) == 8 * 70 * 2048 * 15 * 8
 
 
 @pytest.mark.parametrize("args", [(0, 4, 10, 5), (9, 4, 10, 5), (4, 0, 10, 5), (4, 4, 0, 5), (4, 4, 10, 0)])
