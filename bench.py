@@ -688,7 +688,14 @@ def run_trigger_workload(args) -> None:
         tr.reset()
         for t in range(0, N, T):
             tr.push(r[t:t + T])
+        tr.join()
 
+    # stream-ordered pushes, then the overlap mode (a push's summaries beside
+    # the previous push's scan and emission; the step's triggers joined at its end)
+    for _ in range(max(args.warmup, 3)):
+        step()
+    ms_so = _event_ms(step, args.steps)
+    tr.set_overlap(True)
     for _ in range(max(args.warmup, 3)):
         step()
     ms = _event_ms(step, args.steps)
@@ -707,7 +714,9 @@ def run_trigger_workload(args) -> None:
     line = {
         "workload": "trigger-" + w["name"], "metric": "channel-samples/s of trigger extraction (device-timed)",
         "value": C * N / (ms / 1e3), "unit": UNIT, "ms_per_step": ms, "steps": args.steps,
-        "triggers": n, "events": m, "event_merge_ms": ms_merge,
+        "triggers": n, "events": m, "event_merge_ms": ms_merge, "overlap": True,
+        "stream_ordered": {"value": C * N / (ms_so / 1e3), "unit": UNIT, "ms_per_step": ms_so,
+                           "frac": byts / (ms_so / 1e3) / 1e9 / peak},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "peak_kind": peak_kind, "bytes_per_step": byts},
         "gpu_launches": 3 * (N // T) * args.steps, "dtype": "u8/i64 (comparisons, indices)",

@@ -522,6 +522,24 @@ filark_status filark_trigger_push(filark_trigger *t, const float *d_ratio, int64
 filark_status filark_trigger_flush(filark_trigger *t, filark_trigger_record *d_records, int64_t capacity,
                                    unsigned long long *d_count, filark_stream_t stream);
 filark_status filark_trigger_reset(filark_trigger *t, filark_stream_t stream);
+
+/*
+ * Overlap mode (no counterpart in the paper: a throughput mode for pushes
+ * queued back to back).  A push is three short dependent kernels: the segment
+ * summaries (which read the ratio and depend on nothing else), the per-channel
+ * scan (which carries the state from push to push) and the emission of the
+ * triggers.  With overlap = 1 they run on two internal streams, so that the
+ * summaries of one push run beside the scan and emission of the previous one.
+ * A push still starts after the work already enqueued on its `stream` (it
+ * forks from it) but does NOT complete on `stream`: the ratio must stay
+ * unmodified, and *d_count / d_records are not final, until
+ * filark_trigger_join(t, stream) has made `stream` wait for every push so far
+ * (flush and reset join first by themselves).  Triggers and their order per
+ * channel are the same as without overlap.  Switching the mode waits for the
+ * work enqueued so far.  overlap: 0 or 1, else FILARK_EINVAL.
+ */
+filark_status filark_trigger_set_overlap(filark_trigger *t, int overlap);
+filark_status filark_trigger_join(filark_trigger *t, filark_stream_t stream);
 filark_status filark_trigger_destroy(filark_trigger *t);   /* NULL ok */
 
 size_t filark_events_work_bytes(int64_t n_triggers, int n_channels);

@@ -54,6 +54,7 @@ EXPORTED = (
     "filark_batch_reset_state", "filark_batch_sync_status", "filark_batch_get_info", "filark_batch_stream",
     "filark_batch_destroy",
     "filark_trigger_create", "filark_trigger_push", "filark_trigger_flush", "filark_trigger_reset",
+    "filark_trigger_set_overlap", "filark_trigger_join",
     "filark_trigger_destroy", "filark_events_work_bytes", "filark_events_merge",
     "filark_top_create", "filark_top_push", "filark_top_reset", "filark_top_destroy",
     "filark_fftfilt_create", "filark_fftfilt_push", "filark_fftfilt_reset", "filark_fftfilt_get_info",
@@ -199,6 +200,8 @@ def load(build_if_missing: bool = True) -> ct.CDLL:
             "filark_trigger_push": ([vp, vp, i64, i64, vp, i64, vp, vp], ct.c_int),
             "filark_trigger_flush": ([vp, vp, i64, vp, vp], ct.c_int),
             "filark_trigger_reset": ([vp, vp], ct.c_int),
+            "filark_trigger_set_overlap": ([vp, ct.c_int], ct.c_int),
+            "filark_trigger_join": ([vp, vp], ct.c_int),
             "filark_trigger_destroy": ([vp], ct.c_int),
             "filark_events_work_bytes": ([i64, ct.c_int], ct.c_size_t),
             "filark_events_merge": ([vp, i64, ct.c_int, vp, i64, vp, vp, ct.c_size_t, vp], ct.c_int),
@@ -411,6 +414,14 @@ def filark_trigger_flush(t, d_records, capacity, d_count, stream) -> int:
 
 def filark_trigger_reset(t, stream) -> int:
     return load().filark_trigger_reset(t, stream)
+
+
+def filark_trigger_set_overlap(t, overlap: int) -> int:
+    return load().filark_trigger_set_overlap(t, int(overlap))
+
+
+def filark_trigger_join(t, stream) -> int:
+    return load().filark_trigger_join(t, stream)
 
 
 def filark_trigger_destroy(t) -> int:

@@ -303,8 +303,15 @@ class Trigger:
         abi.check(abi.filark_trigger_reset(self._h, _stream_handle(stream)), "filark_trigger_reset")
         self.count.zero_()
 
+    def set_overlap(self, overlap: bool) -> None:
+        abi.check(abi.filark_trigger_set_overlap(self._h, int(bool(overlap))), "filark_trigger_set_overlap")
+
+    def join(self, stream=None) -> None:
+        abi.check(abi.filark_trigger_join(self._h, _stream_handle(stream)), "filark_trigger_join")
+
     def triggers(self) -> np.ndarray:
         """[k][3] = (channel, t_on, t_off, flags folded out) as numpy int64."""
+        self.join()
         n = int(self.count.item())
         if n > self.capacity:
             raise RuntimeError(f"{n} triggers exceeded the capacity {self.capacity}")

@@ -413,17 +413,28 @@ struct filark_trigger {
     int nseg_max = 0;
     int *st_s = nullptr;
     long long *st_t = nullptr;
-    unsigned *summ = nullptr;
+    unsigned *summ = nullptr;       // [2][nseg_max][C]: the summaries of this push (summ + par * C * nseg_max)
     EmitItem *list = nullptr;       // [C * nseg_max] segments in which a run ends
     unsigned *list_n = nullptr;     // [2] list lengths, alternating between pushes
     int par = 0;
     int emit_ctas = 0;
+    // overlap mode: the summaries of a push on s_sum, its scan and emit on
+    // s_run, so that the summaries of one push run beside the scan and emit
+    // of the previous one; the caller's stream only forks (ev_in) and joins
+    int overlap = 0;
+    bool pending = false;
+    cudaStream_t s_sum = nullptr, s_run = nullptr;
+    cudaEvent_t ev_in = nullptr, ev_done = nullptr, ev_sum[2] = {nullptr, nullptr}, ev_scan[2] = {nullptr, nullptr};
 };
 
 namespace {
 
 void free_trigger(filark_trigger *t) {
     if (!t) return;
+    for (cudaEvent_t e : {t->ev_in, t->ev_done, t->ev_sum[0], t->ev_sum[1], t->ev_scan[0], t->ev_scan[1]})
+        if (e) cudaEventDestroy(e);
+    for (cudaStream_t q : {t->s_sum, t->s_run})
+        if (q) cudaStreamDestroy(q);
     for (void *p : {(void *)t->st_s, (void *)t->st_t, (void *)t->summ, (void *)t->list, (void *)t->list_n})
         if (p) cudaFree(p);
     delete t;
@@ -467,7 +478,7 @@ filark_status filark_trigger_create(int n_channels, double on, double off, int64
     t->emit_ctas = 2 * std::max(sms, 1);
     if (e == cudaSuccess) e = cudaMalloc(&t->st_s, sizeof(int) * C);
     if (e == cudaSuccess) e = cudaMalloc(&t->st_t, sizeof(long long) * C);
-    if (e == cudaSuccess) e = cudaMalloc(&t->summ, sizeof(unsigned) * C * G);
+    if (e == cudaSuccess) e = cudaMalloc(&t->summ, 2 * sizeof(unsigned) * C * G);
     if (e == cudaSuccess) e = cudaMalloc(&t->list, sizeof(EmitItem) * C * G);
     if (e == cudaSuccess) e = cudaMalloc(&t->list_n, 2 * sizeof(unsigned));
     if (e == cudaSuccess) e = cudaMemset(t->list_n, 0, 2 * sizeof(unsigned));
@@ -499,15 +510,85 @@ filark_status filark_trigger_push(filark_trigger *t, const float *d_ratio, int64
     const int nseg = (T + kSeg - 1) / kSeg;
     const dim3 grid2((unsigned)((t->C + kTrigThreads - 1) / kTrigThreads), (unsigned)nseg);
     const unsigned grid1 = (unsigned)((t->C + kScanThreads - 1) / kScanThreads);
-    trig_summary_kernel<<<grid2, kTrigThreads, 0, s>>>(d_ratio, ld, t->C, T, t->on_f, t->off_f, t->summ);
-    trig_scan_kernel<<<grid1, kScanThreads, 0, s>>>(t->summ, t->C, nseg, t->n, t->st_s, t->st_t, t->list,
-                                                    t->list_n + t->par);
-    trig_emit_kernel<<<(unsigned)t->emit_ctas, kTrigThreads, 0, s>>>(d_ratio, ld, T, t->on_f, t->off_f, t->n, t->list,
-                                                                     t->list_n, t->par, d_records, capacity, d_count);
-    const cudaError_t e = cudaGetLastError();
+    unsigned *summ = t->summ + (size_t)t->par * (size_t)t->C * (size_t)t->nseg_max;
+    cudaError_t e = cudaSuccess;
+    cudaStream_t q_sum = s, q_run = s;
+    if (t->overlap) {
+        // fork from the caller's stream; the summaries wait for the scan
+        // that last read this parity's buffer (two pushes ago)
+        q_sum = t->s_sum;
+        q_run = t->s_run;
+        e = cudaEventRecord(t->ev_in, s);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(q_sum, t->ev_in, 0);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(q_sum, t->ev_scan[t->par], 0);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(q_run, t->ev_in, 0);
+        if (e != cudaSuccess) return fail_cuda_with(e, "trigger push: fork");
+    }
+    trig_summary_kernel<<<grid2, kTrigThreads, 0, q_sum>>>(d_ratio, ld, t->C, T, t->on_f, t->off_f, summ);
+    if (t->overlap) {
+        e = cudaEventRecord(t->ev_sum[t->par], q_sum);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(q_run, t->ev_sum[t->par], 0);
+        if (e != cudaSuccess) return fail_cuda_with(e, "trigger push: summaries");
+    }
+    trig_scan_kernel<<<grid1, kScanThreads, 0, q_run>>>(summ, t->C, nseg, t->n, t->st_s, t->st_t, t->list,
+                                                        t->list_n + t->par);
+    if (t->overlap) {
+        e = cudaEventRecord(t->ev_scan[t->par], q_run);
+        if (e != cudaSuccess) return fail_cuda_with(e, "trigger push: scan");
+        t->pending = true;
+    }
+    trig_emit_kernel<<<(unsigned)t->emit_ctas, kTrigThreads, 0, q_run>>>(d_ratio, ld, T, t->on_f, t->off_f, t->n,
+                                                                         t->list, t->list_n, t->par, d_records,
+                                                                         capacity, d_count);
+    e = cudaGetLastError();
     if (e != cudaSuccess) return fail_cuda_with(e, "trigger push");
     t->par ^= 1;
     t->n += n_samples;
+    return FILARK_OK;
+}
+
+namespace {
+
+// The caller's stream waits for every overlapped push enqueued so far.
+filark_status trigger_join(filark_trigger *t, cudaStream_t s) {
+    if (!t->pending) return FILARK_OK;
+    cudaError_t e = cudaEventRecord(t->ev_done, t->s_run);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, t->ev_done, 0);
+    if (e != cudaSuccess) return fail_cuda_with(e, "trigger join");
+    t->pending = false;
+    return FILARK_OK;
+}
+
+}  // namespace
+
+filark_status filark_trigger_join(filark_trigger *t, filark_stream_t stream) {
+    if (!t) return fail_with(FILARK_EINVAL, "trigger is NULL");
+    DeviceGuard dg(t->device);
+    if (!dg.ok) return fail_with(FILARK_ECUDA, "cudaSetDevice failed");
+    return trigger_join(t, (cudaStream_t)stream);
+}
+
+filark_status filark_trigger_set_overlap(filark_trigger *t, int overlap) {
+    if (!t) return fail_with(FILARK_EINVAL, "trigger is NULL");
+    if (overlap != 0 && overlap != 1) return fail_with(FILARK_EINVAL, "overlap must be 0 or 1");
+    DeviceGuard dg(t->device);
+    if (!dg.ok) return fail_with(FILARK_ECUDA, "cudaSetDevice failed");
+    cudaError_t e = cudaSuccess;
+    if (overlap && !t->s_sum) {
+        e = cudaStreamCreateWithFlags(&t->s_sum, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&t->s_run, cudaStreamNonBlocking);
+        for (cudaEvent_t *ev : {&t->ev_in, &t->ev_done, &t->ev_sum[0], &t->ev_sum[1], &t->ev_scan[0], &t->ev_scan[1]})
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming);
+        if (e != cudaSuccess) return fail_cuda_with(e, "trigger overlap: streams");
+    }
+    // work already enqueued in the other mode finishes first
+    if (t->s_run) {
+        e = cudaStreamSynchronize(t->s_run);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(t->s_sum);
+        if (e != cudaSuccess) return fail_cuda_with(e, "trigger overlap: synchronize");
+    }
+    t->pending = false;
+    t->overlap = overlap;
     return FILARK_OK;
 }
 
@@ -519,6 +600,8 @@ filark_status filark_trigger_flush(filark_trigger *t, filark_trigger_record *d_r
         return fail_with(FILARK_EINVAL, "records/capacity/count arguments");
     DeviceGuard dg(t->device);
     if (!dg.ok) return fail_with(FILARK_ECUDA, "cudaSetDevice failed");
+    const filark_status js = trigger_join(t, (cudaStream_t)stream);
+    if (js != FILARK_OK) return js;
     trig_flush_kernel<<<(unsigned)((t->C + kTrigThreads - 1) / kTrigThreads), kTrigThreads, 0,
                         (cudaStream_t)stream>>>(t->st_s, t->st_t, t->C, t->n, d_records, capacity, d_count);
     const cudaError_t e = cudaGetLastError();
@@ -530,6 +613,8 @@ filark_status filark_trigger_reset(filark_trigger *t, filark_stream_t stream) {
     DeviceGuard dg(t->device);
     if (!dg.ok) return fail_with(FILARK_ECUDA, "cudaSetDevice failed");
     cudaStream_t s = (cudaStream_t)stream;
+    const filark_status js = trigger_join(t, s);
+    if (js != FILARK_OK) return js;
     cudaError_t e = cudaMemsetAsync(t->st_s, 0, sizeof(int) * (size_t)t->C, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(t->st_t, 0, sizeof(long long) * (size_t)t->C, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(t->list_n, 0, 2 * sizeof(unsigned), s);

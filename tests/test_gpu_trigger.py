@@ -41,11 +41,13 @@ def blob_ratio(rng, N, C, n_blobs=30, level=5.0):
     return R
 
 
-def run_gpu_trigger(R, chunks, on, off, capacity=1 << 18, flush=True):
+def run_gpu_trigger(R, chunks, on, off, capacity=1 << 18, flush=True, overlap=False):
     import torch
     from paper_2605_20132_gb300.chain import Trigger
     N, C = R.shape
     tr = Trigger(C, on, off, max_chunk=max(chunks), capacity=capacity)
+    if overlap:
+        tr.set_overlap(True)
     Rd = torch.from_numpy(R).cuda()
     t = 0
     for k in chunks:
@@ -54,6 +56,7 @@ def run_gpu_trigger(R, chunks, on, off, capacity=1 << 18, flush=True):
     assert t == N
     if flush:
         tr.flush()
+    tr.join()
     torch.cuda.synchronize()
     n = int(tr.count.item())
     recs = tr.triggers() if n <= capacity else None
@@ -71,11 +74,14 @@ def run_oracle_trigger(ora, R, chunks, on, off, flush=True):
     return closed, opened
 
 
+@pytest.mark.parametrize("overlap", [False, True])
 @pytest.mark.parametrize("C", [300, 301])
-def test_triggers_match_oracle_random_chunks(oracle_mod, C):
+def test_triggers_match_oracle_random_chunks(oracle_mod, C, overlap):
     """Blob-shaped ratio images on 300 and 301 channels, pushed in 1..700-sample
     chunks (segments of every phase, pushes shorter than a segment);
-    thresholds that are not floats (exact comparison by rounding up)."""
+    thresholds that are not floats (exact comparison by rounding up); with
+    and without the overlap mode (summaries of one push beside the scan and
+    emission of the previous one, on the trigger's own streams)."""
     rng = np.random.default_rng(80)
     N = 5000
     R = blob_ratio(rng, N, C)
@@ -84,12 +90,44 @@ def test_triggers_match_oracle_random_chunks(oracle_mod, C):
     chunks = []
     while sum(chunks) < N:
         chunks.append(int(min(rng.integers(1, 701), N - sum(chunks))))
-    tr, got, n = run_gpu_trigger(R, chunks, on, off)
+    tr, got, n = run_gpu_trigger(R, chunks, on, off, overlap=overlap)
     closed, opened = run_oracle_trigger(oracle_mod, R, chunks, on, off)
     want = np.concatenate([np.c_[closed, np.zeros(len(closed), np.int64)],
                            np.c_[opened, np.ones(len(opened), np.int64)]])
     assert n == len(want)
     assert np.array_equal(sort_records(got), sort_records(want))
+    tr.close()
+
+
+def test_trigger_overlap_mode_switches_and_reset(oracle_mod):
+    """Pushes in overlap mode, a switch back to stream order in the middle of
+    the record and a reset with overlapped pushes pending give the oracle's
+    triggers; set_overlap rejects anything but 0 and 1."""
+    import torch
+    from paper_2605_20132_gb300.chain import Trigger
+    rng = np.random.default_rng(81)
+    N, C = 4000, 257
+    R = blob_ratio(rng, N, C)
+    on, off = 4.0, 1.0
+    chunks = [500] * 8
+    tr = Trigger(C, on, off, max_chunk=500)
+    Rd = torch.from_numpy(R).cuda()
+    for rep in range(2):
+        tr.set_overlap(True)
+        for i, k in enumerate(chunks):
+            if i == 4:
+                tr.set_overlap(False)
+            tr.push(Rd[500 * i:500 * i + k])
+        tr.flush()
+        got = tr.triggers()
+        closed, opened = run_oracle_trigger(oracle_mod, R, chunks, on, off)
+        want = np.concatenate([np.c_[closed, np.zeros(len(closed), np.int64)],
+                               np.c_[opened, np.ones(len(opened), np.int64)]])
+        assert np.array_equal(sort_records(got), sort_records(want)), rep
+        tr.set_overlap(True)
+        tr.push(Rd[:500])                 # pending when reset joins
+        tr.reset()
+    assert abi.filark_trigger_set_overlap(tr._h, 2) == abi.FILARK_EINVAL
     tr.close()
 
 
