@@ -868,9 +868,11 @@ def run_waves_workload(args) -> None:
             us = ms / n_push * 1e3
             rows.append({"launch_samples": launch, "lanes": lanes, "us_per_push": round(us, 2),
                          "channel_samples_per_s": C * T / (us / 1e6)})
+    # the chain's own autotuner on the same push (enqueued back to back)
+    tuned = ch.tune(x[:T], ratio=r[:T], timed_pushes=20)
     ch.close()
     print(json.dumps({"workload": f"chain-lanes-{C}ch-T{T}", "metric": "device time per push", "rows": rows,
-                      "dtype": "f32", "data": "synthetic N(0,1) on the device"}), flush=True)
+                      "tuner": tuned, "dtype": "f32", "data": "synthetic N(0,1) on the device"}), flush=True)
 
 
 def ncu_case() -> None:

@@ -219,6 +219,30 @@ filark_status filark_chain_set_blocks_per_cta(filark_chain *h, int blocks_per_ct
 filark_status filark_chain_set_launch_samples(filark_chain *h, int samples);
 
 /*
+ * Autotuner for the launch geometry above (no counterpart in the paper):
+ * times every combination of lanes 1..min(FILARK_MAX_LANES, channel tiles),
+ * samples per launch {2048, 1024} and blocks per CTA {8, 4} (the dense carry:
+ * 8 only; at most 16 candidates) on the caller's push -- two warm-up pushes,
+ * then timed_pushes >= 1 pushes of the same chunk back to back, joined, CUDA
+ * events on `stream` -- keeps the fastest and resets the chain's state (the
+ * trial pushes advance it).  The outputs are overwritten.  Blocks until done.
+ * Arguments as for filark_chain_push_chunk (n_samples >= 1).
+ */
+filark_status filark_chain_tune(filark_chain *h, const float *d_in, int64_t ld_in, int64_t n_samples, float *d_ratio,
+                                float *d_bandpass, float *d_spatial, int64_t ld_out, int timed_pushes,
+                                filark_stream_t stream);
+
+typedef struct {
+    int32_t n_tuned;              /* candidates timed by the last filark_chain_tune */
+    int32_t chosen;               /* index of the one kept (-1: none)               */
+    int32_t lanes[16];
+    int32_t launch_samples[16];
+    int32_t blocks_per_cta[16];   /* 0 = the default, 8                             */
+    double ms_per_push[16];
+} filark_chain_tuning;
+filark_status filark_chain_get_tuning(const filark_chain *h, filark_chain_tuning *out);
+
+/*
  * Lanes (no counterpart in the paper: a throughput mode for pushes that are
  * queued back to back, e.g. a recording replayed from storage).  A launch
  * waits for the whole previous launch before it touches the carried state, so

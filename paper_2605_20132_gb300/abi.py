@@ -43,7 +43,8 @@ FILARK_HOST_SLOTS = 3
 EXPORTED = (
     "filark_chain_create", "filark_chain_push_chunk", "filark_chain_push_chunk_host",
     "filark_chain_push_host_async", "filark_chain_host_sync", "filark_chain_set_blocks_per_cta",
-    "filark_chain_set_lanes", "filark_chain_join", "filark_chain_set_launch_samples",
+    "filark_chain_set_lanes", "filark_chain_join", "filark_chain_set_launch_samples", "filark_chain_tune",
+    "filark_chain_get_tuning",
     "filark_chain_reset_state", "filark_chain_destroy", "filark_chain_get_state",
     "filark_chain_set_state", "filark_chain_sync_status", "filark_chain_get_info",
     "filark_butter_bandpass_sos", "filark_last_error_string", "filark_abi_version",
@@ -114,6 +115,17 @@ class filark_chunk_desc(ct.Structure):
     ]
 
 
+class filark_chain_tuning(ct.Structure):
+    _fields_ = [
+        ("n_tuned", ct.c_int32),
+        ("chosen", ct.c_int32),
+        ("lanes", ct.c_int32 * 16),
+        ("launch_samples", ct.c_int32 * 16),
+        ("blocks_per_cta", ct.c_int32 * 16),
+        ("ms_per_push", ct.c_double * 16),
+    ]
+
+
 class filark_batch_info(ct.Structure):
     _fields_ = [
         ("n_streams", ct.c_int32),
@@ -171,6 +183,8 @@ def load(build_if_missing: bool = True) -> ct.CDLL:
             "filark_chain_set_blocks_per_cta": ([vp, ct.c_int], ct.c_int),
             "filark_chain_set_lanes": ([vp, ct.c_int], ct.c_int),
             "filark_chain_set_launch_samples": ([vp, ct.c_int], ct.c_int),
+            "filark_chain_tune": ([vp, vp, i64, i64, vp, vp, vp, i64, ct.c_int, vp], ct.c_int),
+            "filark_chain_get_tuning": ([vp, ct.POINTER(filark_chain_tuning)], ct.c_int),
             "filark_chain_join": ([vp, vp], ct.c_int),
             "filark_chain_reset_state": ([vp, vp], ct.c_int),
             "filark_chain_destroy": ([vp], ct.c_int),
@@ -279,6 +293,17 @@ def filark_chain_set_blocks_per_cta(h, blocks_per_cta: int) -> int:
 
 def filark_chain_set_launch_samples(h, samples: int) -> int:
     return load().filark_chain_set_launch_samples(h, samples)
+
+
+def filark_chain_tune(h, d_in, ld_in: int, n_samples: int, d_ratio, d_bp, d_sp, ld_out: int, timed_pushes: int,
+                      stream) -> int:
+    return load().filark_chain_tune(h, d_in, ld_in, n_samples, d_ratio, d_bp, d_sp, ld_out, int(timed_pushes), stream)
+
+
+def filark_chain_get_tuning(h) -> tuple[int, filark_chain_tuning]:
+    out = filark_chain_tuning()
+    st = load().filark_chain_get_tuning(h, ct.byref(out))
+    return st, out
 
 
 def filark_chain_set_lanes(h, lanes: int) -> int:

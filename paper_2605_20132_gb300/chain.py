@@ -127,6 +127,21 @@ class Chain:
     def set_launch_samples(self, samples: int) -> None:
         abi.check(abi.filark_chain_set_launch_samples(self._h, int(samples)), "filark_chain_set_launch_samples")
 
+    def tune(self, x, ratio=None, bandpass=None, spatial=None, timed_pushes: int = 5, stream=None) -> dict:
+        """Time the launch geometries on pushes of x (outputs overwritten), keep
+        the fastest, reset the state; returns the candidates and the choice."""
+        T = int(x.shape[0])
+        outs = [o for o in (ratio, bandpass, spatial) if o is not None]
+        ld_out = int(outs[0].stride(0)) if outs else self.n_channels
+        abi.check(abi.filark_chain_tune(self._h, _ptr(x), int(x.stride(0)), T, _ptr(ratio), _ptr(bandpass),
+                                        _ptr(spatial), ld_out, timed_pushes, _stream_handle(stream)),
+                  "filark_chain_tune")
+        st, t = abi.filark_chain_get_tuning(self._h)
+        abi.check(st, "filark_chain_get_tuning")
+        rows = [dict(lanes=t.lanes[i], launch_samples=t.launch_samples[i], blocks_per_cta=t.blocks_per_cta[i],
+                     ms_per_push=t.ms_per_push[i]) for i in range(t.n_tuned)]
+        return {"candidates": rows, "chosen": rows[t.chosen] if t.chosen >= 0 else None}
+
     def set_lanes(self, lanes: int) -> None:
         """1 (default): every push completes on its stream.  2..FILARK_MAX_LANES:
         channel-tile groups on internal streams; a push's outputs are valid

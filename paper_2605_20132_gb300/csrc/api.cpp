@@ -634,6 +634,95 @@ filark_status filark_chain_set_lanes(filark_chain *h, int lanes) {
     return FILARK_OK;
 }
 
+filark_status filark_chain_tune(filark_chain *h, const float *d_in, int64_t ld_in, int64_t n_samples, float *d_ratio,
+                                float *d_bandpass, float *d_spatial, int64_t ld_out, int timed_pushes,
+                                filark_stream_t stream) {
+    filark::NvtxRange nvtx_range("filark_chain_tune");
+    filark_status st = validate_push(h, d_in, ld_in, n_samples, d_ratio, d_bandpass, d_spatial, ld_out);
+    if (st != FILARK_OK) return st;
+    if (n_samples < 1 || timed_pushes < 1) return fail(FILARK_EINVAL, "tune needs n_samples >= 1 and timed_pushes >= 1");
+    st = check_device_status(h);
+    if (st != FILARK_OK) return st;
+    DeviceGuard dg(h->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaEvent_t t0 = nullptr, t1 = nullptr;
+    cudaError_t e = cudaEventCreate(&t0);
+    if (e == cudaSuccess) e = cudaEventCreate(&t1);
+    if (e != cudaSuccess) {
+        if (t0) cudaEventDestroy(t0);
+        return fail_cuda(e, "tune: events");
+    }
+    // lanes x samples per launch x blocks per CTA (the dense carry keeps 8)
+    struct Cand {
+        int lanes, launch, blocks;
+    };
+    std::vector<Cand> cands;
+    for (int blocks : {0, 4}) {
+        if (blocks && h->plan.dense) continue;
+        for (int launch : {kMaxLaunchSamples, kMaxLaunchSamples / 2})
+            for (int lanes = 1; lanes <= std::min(FILARK_MAX_LANES, h->n_tiles); ++lanes)
+                if ((int)cands.size() < 16) cands.push_back(Cand{lanes, launch, blocks});
+    }
+    h->n_tuned = 0;
+    h->tuned_choice = -1;
+    double best = 1e300;
+    for (const Cand &c : cands) {
+        st = filark_chain_set_lanes(h, c.lanes);
+        if (st != FILARK_OK) break;
+        h->launch_samples = c.launch;
+        h->nbc_fixed = c.blocks;
+        st = filark_chain_reset_state(h, stream);
+        // two warm-up pushes, then timed_pushes back to back, joined at the end
+        for (int w = 0; w < 2 && st == FILARK_OK; ++w)
+            st = push_device(h, d_in, ld_in, n_samples, d_ratio, d_bandpass, d_spatial, ld_out, s);
+        if (st == FILARK_OK && (e = cudaEventRecord(t0, s)) != cudaSuccess) st = fail_cuda(e, "tune: record");
+        for (int q = 0; q < timed_pushes && st == FILARK_OK; ++q)
+            st = push_device(h, d_in, ld_in, n_samples, d_ratio, d_bandpass, d_spatial, ld_out, s);
+        if (st == FILARK_OK) st = join_lanes(h, s);
+        if (st == FILARK_OK && (e = cudaEventRecord(t1, s)) != cudaSuccess) st = fail_cuda(e, "tune: record");
+        if (st == FILARK_OK && (e = cudaEventSynchronize(t1)) != cudaSuccess) st = fail_cuda(e, "tune: sync");
+        float ms = 0.f;
+        if (st == FILARK_OK && (e = cudaEventElapsedTime(&ms, t0, t1)) != cudaSuccess)
+            st = fail_cuda(e, "tune: elapsed");
+        if (st != FILARK_OK) break;
+        const double per = (double)ms / timed_pushes;
+        const int k = h->n_tuned++;
+        h->tune_lanes[k] = c.lanes;
+        h->tune_launch[k] = c.launch;
+        h->tune_blocks[k] = c.blocks;
+        h->tune_ms[k] = per;
+        if (per < best) {
+            best = per;
+            h->tuned_choice = k;
+        }
+    }
+    cudaEventDestroy(t0);
+    cudaEventDestroy(t1);
+    if (st != FILARK_OK) return st;
+    const int k = h->tuned_choice;
+    st = filark_chain_set_lanes(h, h->tune_lanes[k]);
+    if (st != FILARK_OK) return st;
+    h->launch_samples = h->tune_launch[k];
+    h->nbc_fixed = h->tune_blocks[k];
+    st = filark_chain_reset_state(h, stream);
+    if (st == FILARK_OK && (e = cudaStreamSynchronize(s)) != cudaSuccess) st = fail_cuda(e, "tune: sync");
+    return st;
+}
+
+filark_status filark_chain_get_tuning(const filark_chain *h, filark_chain_tuning *out) {
+    if (!h || !out) return fail(FILARK_EINVAL, "chain or out is NULL");
+    std::memset(out, 0, sizeof(*out));
+    out->n_tuned = h->n_tuned;
+    out->chosen = h->tuned_choice;
+    for (int i = 0; i < h->n_tuned; ++i) {
+        out->lanes[i] = h->tune_lanes[i];
+        out->launch_samples[i] = h->tune_launch[i];
+        out->blocks_per_cta[i] = h->tune_blocks[i];
+        out->ms_per_push[i] = h->tune_ms[i];
+    }
+    return FILARK_OK;
+}
+
 filark_status filark_chain_join(filark_chain *h, filark_stream_t stream) {
     if (!h) return fail(FILARK_EINVAL, "chain is NULL");
     DeviceGuard dg(h->device);

@@ -35,6 +35,10 @@ struct filark_chain {
     int use_pdl = 1;
     int nbc_fixed = 0;            // blocks per CTA set by the caller, 0 = kNB
     int launch_samples = filark::kMaxLaunchSamples;   // a push is cut into launches of at most this many samples
+    // the last filark_chain_tune: candidates and their ms per push
+    int n_tuned = 0, tuned_choice = -1;
+    int tune_lanes[16] = {}, tune_launch[16] = {}, tune_blocks[16] = {};
+    double tune_ms[16] = {};
     // lanes: the channel tiles split into `lanes` contiguous groups, each
     // pushed on an internal stream of its own; a push forks from the caller's
     // stream, and filark_chain_join (or any call that reads or resets the

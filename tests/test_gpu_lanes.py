@@ -269,3 +269,52 @@ def test_launch_samples_lanes_bitwise():
         assert abi.filark_chain_set_launch_samples(ch._h, good) == abi.FILARK_OK
     ch.close()
 
+
+def test_chain_tune_picks_a_candidate_and_resets():
+    """The chain's autotuner times lanes x samples per launch x blocks per
+    CTA on a push, keeps the fastest and resets the state: a run after tuning
+    equals a fresh chain with the chosen settings bit for bit, and within
+    rounding (the oracle's bar) the default chain."""
+    import torch
+    from paper_2605_20132_gb300.chain import Chain, butter_bandpass
+    C, fs = 700, 1000.0
+    sos = butter_bandpass(4, 1.0, 50.0, fs)
+    chunks = [1500, 1500, 700]
+    x = torch.from_numpy(synth.small_stream(C, sum(chunks), seed=51)).cuda()
+
+    def run(ch):
+        outs = {k: torch.full(x.shape, float("nan"), device="cuda") for k in ("ratio", "bp", "sp")}
+        t = 0
+        for T in chunks:
+            sl = slice(t, t + T)
+            ch.push(x[sl], ratio=outs["ratio"][sl], bandpass=outs["bp"][sl], spatial=outs["sp"][sl])
+            t += T
+        ch.join()
+        ch.sync()
+        return outs
+
+    tuned = Chain(C, sos, fs, 5, 50, 1000, outputs=ALL_OUT, max_chunk=1500)
+    scratch = {k: torch.empty((1500, C), device="cuda") for k in ("ratio", "bp", "sp")}
+    res = tuned.tune(x[:1500], ratio=scratch["ratio"], bandpass=scratch["bp"], spatial=scratch["sp"],
+                     timed_pushes=2)
+    cands, best = res["candidates"], res["chosen"]
+    n_tiles = -(-C // tuned.info()["tile_channels"])
+    assert len(cands) == min(16, 2 * 2 * min(abi.FILARK_MAX_LANES, n_tiles))
+    assert best == min(cands, key=lambda c: c["ms_per_push"])
+    got = run(tuned)
+    tuned.close()
+    ref = Chain(C, sos, fs, 5, 50, 1000, outputs=ALL_OUT, max_chunk=1500)
+    ref.set_lanes(best["lanes"])
+    ref.set_launch_samples(best["launch_samples"])
+    ref.set_blocks_per_cta(best["blocks_per_cta"])
+    want = run(ref)
+    ref.close()
+    for k in want:
+        assert torch.equal(got[k], want[k]), k
+    plain = Chain(C, sos, fs, 5, 50, 1000, outputs=ALL_OUT, max_chunk=1500)
+    base = run(plain)
+    plain.close()
+    for k in base:
+        d = (got[k] - base[k]).abs().max().item()
+        assert d <= TOL * base[k].abs().max().item(), (k, d)
+
