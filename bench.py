@@ -681,7 +681,6 @@ def run_trigger_workload(args) -> None:
         ch.push(x[t:t + T], ratio=r[t:t + T])
     ch.sync()
     ch.close()
-    del x
     tr = Trigger(C, 6.0, 2.0, max_chunk=T, capacity=1 << 22)
 
     def step():
@@ -708,6 +707,40 @@ def run_trigger_workload(args) -> None:
     e1.synchronize()
     ms_merge = e0.elapsed_time(e1)
     tr.close()
+    # the chain and the triggers per push, in the benchmark's lanes: a chain
+    # push, its lanes joined, then a trigger push -- against the chain push with
+    # the trigger summaries fused into its detector (filark_chain_push_triggers)
+    sos = butter_bandpass(w["order"], *w["band"], w["fs"])
+    cf = Chain(C, sos, w["fs"], w["spatial_width"], w["sta"], w["lta"], outputs=abi.FILARK_OUT_RATIO, max_chunk=T)
+    cf.set_lanes(LANES)
+    tf = Trigger(C, 6.0, 2.0, max_chunk=T, capacity=1 << 22)
+
+    def step_sep():
+        cf.reset()
+        tf.reset()
+        for t in range(0, N, T):
+            cf.push(x[t:t + T], ratio=r[t:t + T])
+            cf.join()
+            tf.push(r[t:t + T])
+
+    def step_fused():
+        cf.reset()
+        tf.reset()
+        for t in range(0, N, T):
+            cf.push_triggers(x[t:t + T], r[t:t + T], tf)
+        cf.join()
+        tf.join()
+
+    pipe = {}
+    for name, fn, ov in (("separate", step_sep, False), ("fused", step_fused, False),
+                         ("fused_overlap", step_fused, True)):
+        tf.set_overlap(ov)
+        for _ in range(3):
+            fn()
+        pipe[name] = _event_ms(fn, max(1, min(args.steps, 5)))
+    cf.close()
+    tf.close()
+    del x
     peak, peak_kind = measured_peak_hbm()
     byts = 4.0 * C * N   # the ratio is read once; the triggers are a few MB
     achieved = byts / (ms / 1e3) / 1e9
@@ -715,6 +748,8 @@ def run_trigger_workload(args) -> None:
         "workload": "trigger-" + w["name"], "metric": "channel-samples/s of trigger extraction (device-timed)",
         "value": C * N / (ms / 1e3), "unit": UNIT, "ms_per_step": ms, "steps": args.steps,
         "triggers": n, "events": m, "event_merge_ms": ms_merge, "overlap": True,
+        "chain_and_triggers": {k: {"ms_per_step": v, "us_per_push": v / (N // T) * 1e3,
+                                   "channel_samples_per_s": C * N / (v / 1e3)} for k, v in pipe.items()},
         "stream_ordered": {"value": C * N / (ms_so / 1e3), "unit": UNIT, "ms_per_step": ms_so,
                            "frac": byts / (ms_so / 1e3) / 1e9 / peak},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,

@@ -564,6 +564,26 @@ filark_status filark_trigger_reset(filark_trigger *t, filark_stream_t stream);
  */
 filark_status filark_trigger_set_overlap(filark_trigger *t, int overlap);
 filark_status filark_trigger_join(filark_trigger *t, filark_stream_t stream);
+
+/*
+ * Chain push with the triggers fused into its detector: the same push as
+ * filark_chain_push_chunk with the ratio output (d_ratio required; no
+ * bandpass or spatial output), during which the detector also writes the
+ * trigger's per-segment summaries from the ratio values it computes, followed
+ * by the trigger's scan and emission (filark_trigger_push without its own pass
+ * over the ratio).  The ratio and the triggers are the same as those of the
+ * two calls made one after the other.  t must have the chain's channel count
+ * and n_samples <= its max_chunk.  The scan needs every tile's summaries:
+ * with the trigger's overlap mode its scan and emission run on the trigger's
+ * stream and wait for this push's launches (in every lane), so a chain in
+ * lanes goes on with its next push meanwhile (join both, filark_chain_join
+ * and filark_trigger_join, before using the ratio or the triggers); without
+ * it the chain's lanes join back into `stream` at the end of the push.
+ */
+filark_status filark_chain_push_triggers(filark_chain *h, filark_trigger *t, const float *d_in, int64_t ld_in,
+                                        int64_t n_samples, float *d_ratio, int64_t ld_out,
+                                        filark_trigger_record *d_records, int64_t capacity,
+                                        unsigned long long *d_count, filark_stream_t stream);
 filark_status filark_trigger_destroy(filark_trigger *t);   /* NULL ok */
 
 size_t filark_events_work_bytes(int64_t n_triggers, int n_channels);

@@ -55,7 +55,7 @@ EXPORTED = (
     "filark_batch_reset_state", "filark_batch_sync_status", "filark_batch_get_info", "filark_batch_stream",
     "filark_batch_destroy",
     "filark_trigger_create", "filark_trigger_push", "filark_trigger_flush", "filark_trigger_reset",
-    "filark_trigger_set_overlap", "filark_trigger_join",
+    "filark_trigger_set_overlap", "filark_trigger_join", "filark_chain_push_triggers",
     "filark_trigger_destroy", "filark_events_work_bytes", "filark_events_merge",
     "filark_top_create", "filark_top_push", "filark_top_reset", "filark_top_destroy",
     "filark_fftfilt_create", "filark_fftfilt_push", "filark_fftfilt_reset", "filark_fftfilt_get_info",
@@ -216,6 +216,7 @@ def load(build_if_missing: bool = True) -> ct.CDLL:
             "filark_trigger_reset": ([vp, vp], ct.c_int),
             "filark_trigger_set_overlap": ([vp, ct.c_int], ct.c_int),
             "filark_trigger_join": ([vp, vp], ct.c_int),
+            "filark_chain_push_triggers": ([vp, vp, vp, i64, i64, vp, i64, vp, i64, vp, vp], ct.c_int),
             "filark_trigger_destroy": ([vp], ct.c_int),
             "filark_events_work_bytes": ([i64, ct.c_int], ct.c_size_t),
             "filark_events_merge": ([vp, i64, ct.c_int, vp, i64, vp, vp, ct.c_size_t, vp], ct.c_int),
@@ -447,6 +448,12 @@ def filark_trigger_set_overlap(t, overlap: int) -> int:
 
 def filark_trigger_join(t, stream) -> int:
     return load().filark_trigger_join(t, stream)
+
+
+def filark_chain_push_triggers(h, t, d_in, ld_in: int, n_samples: int, d_ratio, ld_out: int, d_records,
+                               capacity: int, d_count, stream) -> int:
+    return load().filark_chain_push_triggers(h, t, d_in, ld_in, n_samples, d_ratio, ld_out, d_records, capacity,
+                                             d_count, stream)
 
 
 def filark_trigger_destroy(t) -> int:

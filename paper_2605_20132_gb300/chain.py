@@ -91,6 +91,16 @@ class Chain:
                                          _ptr(spatial), ld_out, _stream_handle(stream))
         abi.check(st, "filark_chain_push_chunk")
 
+    def push_triggers(self, x, ratio, trigger, stream=None) -> None:
+        """Push x with the ratio output and the triggers of `trigger` (a
+        Trigger) fused into the detector (filark_chain_push_triggers)."""
+        T = int(x.shape[0])
+        st = abi.filark_chain_push_triggers(self._h, trigger._h, _ptr(x), int(x.stride(0)) if T else self.n_channels,
+                                            T, _ptr(ratio), int(ratio.stride(0)) if T else self.n_channels,
+                                            _ptr(trigger.records), trigger.capacity, _ptr(trigger.count),
+                                            _stream_handle(stream))
+        abi.check(st, "filark_chain_push_triggers")
+
     def push_host(self, x: np.ndarray, ratio: np.ndarray | None = None,
                   bandpass: np.ndarray | None = None, spatial: np.ndarray | None = None,
                   stream=None) -> None:

@@ -164,7 +164,8 @@ filark_status join_lanes(filark_chain *h, cudaStream_t stream) {
 // overwriting; so the first launch in that case runs every tile at once on
 // `stream` and writes the per-tile state, and the lanes fork after it.
 filark_status push_device(filark_chain *h, const float *d_in, int64_t ld_in, int64_t T, float *d_ratio,
-                          float *d_bp, float *d_sp, int64_t ld_out, cudaStream_t stream, bool join_after = false) {
+                          float *d_bp, float *d_sp, int64_t ld_out, cudaStream_t stream, bool join_after = false,
+                          const TriggerFusion *tf = nullptr) {
     const int NS = h->plan.NS;
     const int L = std::min(h->lanes, h->n_tiles);
     bool forked = false;
@@ -213,6 +214,16 @@ filark_status push_device(filark_chain *h, const float *d_in, int64_t ld_in, int
         for (float *o : {u.ratio, u.bp, u.sp})
             if (o && ((uintptr_t)o & 15u)) ov = false;
         u.o_vec4 = ov;
+        // fused trigger summaries: the launch's blocks start at push block done / 32
+        u.trig_summ = tf ? tf->summ + (size_t)(done / kL) * (size_t)h->C : nullptr;
+        if (tf) {
+            p.trig_on = tf->on;
+            p.trig_off = tf->off;
+        }
+        auto launch = [&](int n_tiles, cudaStream_t q) {
+            return tf ? launch_chain_trig(p, NS, h->plan.dense, n_tiles, q)
+                      : launch_chain(p, NS, h->det, h->plan.dense, n_tiles, q);
+        };
         cudaError_t e = cudaSuccess;
         if (L > 1 && !h->halo_valid) {
             // every tile in one launch on the caller's stream: halo columns
@@ -220,7 +231,7 @@ filark_status push_device(filark_chain *h, const float *d_in, int64_t ld_in, int
             u.halo_in = nullptr;
             u.halo_out = h->halo[h->parity ^ 1];
             u.tx0 = 0;
-            e = launch_chain(p, NS, h->det, h->plan.dense, h->n_tiles, stream);
+            e = launch(h->n_tiles, stream);
             h->halo_valid = true;
         } else if (L > 1) {
             if (!forked) {
@@ -233,11 +244,11 @@ filark_status push_device(filark_chain *h, const float *d_in, int64_t ld_in, int
             for (int l = 0; l < L && e == cudaSuccess; ++l) {
                 const int t0 = (int)((long long)h->n_tiles * l / L), t1 = (int)((long long)h->n_tiles * (l + 1) / L);
                 u.tx0 = t0;
-                e = launch_chain(p, NS, h->det, h->plan.dense, t1 - t0, h->lane_s[l]);
+                e = launch(t1 - t0, h->lane_s[l]);
             }
             h->lanes_pending = true;
         } else {
-            e = launch_chain(p, NS, h->det, h->plan.dense, h->n_tiles, stream);
+            e = launch(h->n_tiles, stream);
             h->halo_valid = false;
         }
         if (e != cudaSuccess) {
@@ -458,6 +469,49 @@ filark_status filark_chain_push_chunk(filark_chain *h, const float *d_in, int64_
     if (n_samples == 0) return FILARK_OK;
     DeviceGuard dg(h->device);
     return push_device(h, d_in, ld_in, n_samples, d_ratio, d_bandpass, d_spatial, ld_out, (cudaStream_t)stream);
+}
+
+filark_status filark_chain_push_triggers(filark_chain *h, filark_trigger *t, const float *d_in, int64_t ld_in,
+                                        int64_t n_samples, float *d_ratio, int64_t ld_out,
+                                        filark_trigger_record *d_records, int64_t capacity,
+                                        unsigned long long *d_count, filark_stream_t stream) {
+    filark::NvtxRange nvtx_range("filark_chain_push_triggers");
+    if (!t) return fail(FILARK_EINVAL, "trigger is NULL");
+    if (!d_ratio) return fail(FILARK_EINVAL, "push_triggers needs the ratio output");
+    filark_status st = validate_push(h, d_in, ld_in, n_samples, d_ratio, nullptr, nullptr, ld_out);
+    if (st != FILARK_OK) return st;
+    if (!d_count || capacity < 0 || (capacity > 0 && !d_records))
+        return fail(FILARK_EINVAL, "records/capacity/count arguments");
+    st = check_device_status(h);
+    if (st != FILARK_OK) return st;
+    if (n_samples == 0) return FILARK_OK;
+    DeviceGuard dg(h->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    TriggerFusion tf;
+    st = trigger_fusion_begin(t, s, tf);
+    if (st != FILARK_OK) return st;
+    if (tf.C != h->C) return fail(FILARK_EINVAL, "trigger and chain have different channel counts");
+    if (n_samples > tf.max_chunk) return fail(FILARK_EINVAL, "n_samples above the trigger's max_chunk");
+    // The scan reads every tile's summaries: with the trigger on its own
+    // stream it waits for this push's lane launches (the lanes go on with the
+    // next push); otherwise the lanes join back into `stream`.
+    const int L = std::min(h->lanes, h->n_tiles);
+    const bool direct = tf.overlap && L > 1;
+    st = push_device(h, d_in, ld_in, n_samples, d_ratio, nullptr, nullptr, ld_out, s, !direct, &tf);
+    if (st != FILARK_OK) return st;
+    cudaEvent_t deps[FILARK_MAX_LANES];
+    int n_deps = 0;
+    if (direct && h->lanes_pending) {
+        for (int l = 0; l < L; ++l) {
+            const cudaError_t e = cudaEventRecord(h->ev_lane[l], h->lane_s[l]);
+            if (e != cudaSuccess) {
+                h->sticky = FILARK_ECUDA;
+                return fail_cuda(e, "push_triggers: lane event");
+            }
+            deps[n_deps++] = h->ev_lane[l];
+        }
+    }
+    return trigger_push_summarized(t, d_ratio, ld_out, n_samples, d_records, capacity, d_count, s, deps, n_deps);
 }
 
 filark_status filark_chain_push_chunk_host(filark_chain *h, const float *h_in, int64_t ld_in, int64_t n_samples,

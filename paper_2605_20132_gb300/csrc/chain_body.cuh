@@ -371,7 +371,29 @@ __device__ __forceinline__ unsigned tile_rank(const cg::cluster_group &cluster, 
 // The work of one CTA: time range r of channel tile `tx` for the launch `cu`.
 // Every CTA of the cluster calls it with the same unit; it executes
 // chain_cluster_barriers<NS, DET>() cluster barriers.
-template <int NS, bool DET, bool DENSE, bool SOLO = false>
+// Trigger summary of one channel's 32-sample segment (TRIG): the hysteresis
+// state s(n) = 1 if R(n) >= on, 0 if R(n) < off, else s(n-1), run from both
+// possible entry states on the ratio as it is written; packed as the trigger
+// pipeline's scan reads it (bits 0/1 final state from 0/1, bits 2/3 a run
+// ends inside when entering with 0/1, bits 4-9 / 10-15 last rise + 1).
+struct TrigAuto {
+    // kept directly in the packed form (one register): entry 1's state starts at 1
+    unsigned w = 2u;
+    __device__ __forceinline__ void step(float r, float on, float off, int k) {
+        const unsigned set = r >= on, keep = !(r < off);
+        const unsigned s0 = w & 1u, s1 = (w >> 1) & 1u;
+        const unsigned n0 = set | (keep & s0), n1 = set | (keep & s1);
+        const unsigned rise0 = n0 & (s0 ^ 1u), rise1 = n1 & (s1 ^ 1u);
+        const unsigned end0 = s0 & (n0 ^ 1u), end1 = s1 & (n1 ^ 1u);
+        const unsigned k1 = (unsigned)(k + 1);
+        w = (w & ~3u) | n0 | (n1 << 1) | (end0 << 2) | (end1 << 3);
+        if (rise0) w = (w & ~(63u << 4)) | (k1 << 4);
+        if (rise1) w = (w & ~(63u << 10)) | (k1 << 10);
+    }
+    __device__ __forceinline__ unsigned packed() const { return w; }
+};
+
+template <int NS, bool DET, bool DENSE, bool SOLO = false, bool TRIG = false>
 __device__ __forceinline__ void chain_body(const ChainParams &p, const ChainUnit &cu, const int tx, const int r) {
     extern __shared__ __align__(16) float smem[];
     float *tile = smem;                       // [kTileRows][kWT]
@@ -918,6 +940,7 @@ __device__ __forceinline__ void chain_body(const ChainParams &p, const ChainUnit
             // past the warm-up, with a nonzero cf inside every window of the
             // block already known, no sample needs the validity test
             const bool all_valid = full_blk && rbeg >= warm && lz > rbeg + kL - 1 - p.nl;
+            TrigAuto ta;
             if (all_valid && rp) {
 #pragma unroll 1
                 for (int kb = 0; kb < kL; kb += 8) {
@@ -930,7 +953,9 @@ __device__ __forceinline__ void chain_body(const ChainParams &p, const ChainUnit
                         const float cf = tile[(rbeg + kb + u) * kWT + col];
                         fs += cf - vs[u];
                         fl += cf - vl[u];
-                        rq[(long long)u * cu.ldo] = (fs * scale) * rcp_approx(fl);
+                        const float Rv = (fs * scale) * rcp_approx(fl);
+                        rq[(long long)u * cu.ldo] = Rv;
+                        if constexpr (TRIG) ta.step(Rv, p.trig_on, p.trig_off, kb + u);
                     }
                 }
             } else {
@@ -949,9 +974,12 @@ __device__ __forceinline__ void chain_body(const ChainParams &p, const ChainUnit
                         const bool valid = (row >= warm) & (lz > row - p.nl);
                         const float Rv = valid ? (fs * scale) * rcp_approx(fl) : 0.f;
                         if (rp && row < rows) rp[(long long)(kb + u) * cu.ldo] = Rv;
+                        if constexpr (TRIG)
+                            if (row < rows) ta.step(Rv, p.trig_on, p.trig_off, kb + u);
                     }
                 }
             }
+            if constexpr (TRIG) cu.trig_summ[(long long)(blk0 + jb) * cu.C + cgc] = ta.packed();
         }
     }
     // no CTA may exit while a peer can still read its shared memory

@@ -75,6 +75,10 @@ struct ChainUnit {
     int nbc;                            // blocks per CTA (<= kNB): CTA r covers blocks [r nbc, r nbc + nbc)
     int tx0;                            // channel tile of grid.x = 0 (a launch may cover a tile range)
     int x_vec4, o_vec4;                 // float4 access allowed (input, outputs)
+    // trigger summaries fused into the detector (chain_fwd_kernel<..., TRIG>):
+    // [blocks of the launch][C] packed segment summaries, row 0 = the launch's
+    // first 32-sample block
+    unsigned *trig_summ;
     // transition over the launch's last CTA, and PhiTot = PhiLast * Phi^(R-1)
     // (launch start -> launch end), as double-float hi/lo pairs
     float PhiLastHi[kMaxSlots][4], PhiLastLo[kMaxSlots][4];
@@ -89,6 +93,7 @@ struct ChainParams {
     int hw, HP, Wout;
     int ns, nl;
     float ratio_scale;                  // nl / ns
+    float trig_on, trig_off;            // trigger thresholds (floats >= the doubles) for TRIG launches
     int all32;                          // keep carries in FP32 everywhere (comparison)
     int pdl;                            // launched with programmatic stream serialization
     // dense carry (FILARK_PREC_DENSE64, or ALL32 without a modal basis):
@@ -198,6 +203,30 @@ cudaError_t launch_chain(const ChainParams &p, int NS, bool detector, bool dense
                          cudaStream_t stream);
 
 size_t chain_smem_bytes(bool dense);
+// The same launch with the detector writing the trigger summaries too
+// (p.u.trig_summ, p.trig_on / trig_off); detector chains only.
+cudaError_t launch_chain_trig(const ChainParams &p, int NS, bool dense, int n_tiles, cudaStream_t stream);
+
+// A trigger as the chain's detector sees it when it writes the trigger
+// summaries itself (trigger.cu): the summary buffer the next push fills
+// ([ceil(max_chunk / 32)][C]), the thresholds as floats, the sizes.
+struct TriggerFusion {
+    unsigned *summ;
+    float on, off;
+    int C;
+    long long max_chunk;
+    int overlap;        // the trigger's scan and emission run on its own stream
+};
+// Makes `stream` wait until the summary buffer of the next push is free and
+// describes it.
+filark_status trigger_fusion_begin(filark_trigger *t, cudaStream_t stream, TriggerFusion &out);
+// The rest of filark_trigger_push after the summaries: scan and emission.
+// In the overlap mode the scan also waits for deps[0 .. n_deps) (the lanes of
+// a chain push whose detector wrote the summaries).
+filark_status trigger_push_summarized(filark_trigger *t, const float *d_ratio, long long ld, long long n_samples,
+                                      filark_trigger_record *d_records, long long capacity,
+                                      unsigned long long *d_count, cudaStream_t stream,
+                                      const cudaEvent_t *deps = nullptr, int n_deps = 0);
 
 
 // The batched kernel: a persistent grid of `n_clusters` clusters of `cluster`

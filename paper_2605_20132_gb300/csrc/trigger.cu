@@ -509,26 +509,64 @@ filark_status filark_trigger_push(filark_trigger *t, const float *d_ratio, int64
     const int T = (int)n_samples;
     const int nseg = (T + kSeg - 1) / kSeg;
     const dim3 grid2((unsigned)((t->C + kTrigThreads - 1) / kTrigThreads), (unsigned)nseg);
-    const unsigned grid1 = (unsigned)((t->C + kScanThreads - 1) / kScanThreads);
     unsigned *summ = t->summ + (size_t)t->par * (size_t)t->C * (size_t)t->nseg_max;
     cudaError_t e = cudaSuccess;
-    cudaStream_t q_sum = s, q_run = s;
+    cudaStream_t q_sum = s;
     if (t->overlap) {
-        // fork from the caller's stream; the summaries wait for the scan
+        // the summaries fork from the caller's stream and wait for the scan
         // that last read this parity's buffer (two pushes ago)
         q_sum = t->s_sum;
-        q_run = t->s_run;
         e = cudaEventRecord(t->ev_in, s);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(q_sum, t->ev_in, 0);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(q_sum, t->ev_scan[t->par], 0);
-        if (e == cudaSuccess) e = cudaStreamWaitEvent(q_run, t->ev_in, 0);
         if (e != cudaSuccess) return fail_cuda_with(e, "trigger push: fork");
     }
     trig_summary_kernel<<<grid2, kTrigThreads, 0, q_sum>>>(d_ratio, ld, t->C, T, t->on_f, t->off_f, summ);
+    if (t->overlap && (e = cudaEventRecord(t->ev_sum[t->par], q_sum)) != cudaSuccess)
+        return fail_cuda_with(e, "trigger push: summaries");
+    return trigger_push_summarized(t, d_ratio, ld, n_samples, d_records, capacity, d_count, s);
+}
+
+}  // extern "C"
+
+namespace filark {
+
+filark_status trigger_fusion_begin(filark_trigger *t, cudaStream_t stream, TriggerFusion &out) {
     if (t->overlap) {
-        e = cudaEventRecord(t->ev_sum[t->par], q_sum);
+        const cudaError_t e = cudaStreamWaitEvent(stream, t->ev_scan[t->par], 0);
+        if (e != cudaSuccess) return fail_cuda_with(e, "trigger fusion: wait");
+    }
+    out.summ = t->summ + (size_t)t->par * (size_t)t->C * (size_t)t->nseg_max;
+    out.on = t->on_f;
+    out.off = t->off_f;
+    out.C = t->C;
+    out.max_chunk = t->max_chunk;
+    out.overlap = t->overlap;
+    return FILARK_OK;
+}
+
+// Scan and emission of a push whose summaries are in the current parity's
+// buffer (written on `stream`, or on s_sum with ev_sum recorded, in the
+// overlap mode by filark_trigger_push).
+filark_status trigger_push_summarized(filark_trigger *t, const float *d_ratio, long long ld, long long n_samples,
+                                      filark_trigger_record *d_records, long long capacity,
+                                      unsigned long long *d_count, cudaStream_t s, const cudaEvent_t *deps,
+                                      int n_deps) {
+    const int T = (int)n_samples;
+    const int nseg = (T + kSeg - 1) / kSeg;
+    const unsigned grid1 = (unsigned)((t->C + kScanThreads - 1) / kScanThreads);
+    unsigned *summ = t->summ + (size_t)t->par * (size_t)t->C * (size_t)t->nseg_max;
+    cudaError_t e = cudaSuccess;
+    cudaStream_t q_run = s;
+    if (t->overlap) {
+        q_run = t->s_run;
+        // after the caller's work (the fused summaries, outputs' zeroing) and,
+        // when filark_trigger_push made them, after the summaries on s_sum
+        e = cudaEventRecord(t->ev_in, s);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(q_run, t->ev_in, 0);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(q_run, t->ev_sum[t->par], 0);
-        if (e != cudaSuccess) return fail_cuda_with(e, "trigger push: summaries");
+        for (int i = 0; i < n_deps && e == cudaSuccess; ++i) e = cudaStreamWaitEvent(q_run, deps[i], 0);
+        if (e != cudaSuccess) return fail_cuda_with(e, "trigger push: fork");
     }
     trig_scan_kernel<<<grid1, kScanThreads, 0, q_run>>>(summ, t->C, nseg, t->n, t->st_s, t->st_t, t->list,
                                                         t->list_n + t->par);
@@ -546,6 +584,10 @@ filark_status filark_trigger_push(filark_trigger *t, const float *d_ratio, int64
     t->n += n_samples;
     return FILARK_OK;
 }
+
+}  // namespace filark
+
+extern "C" {
 
 namespace {
 

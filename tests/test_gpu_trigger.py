@@ -313,3 +313,53 @@ def test_paper_scale_triggers_and_events(oracle_mod):
     assert np.array_equal(sort_events(ev[:, :5]), sort_events(ref))
     ch.close()
     tr.close()
+
+
+@pytest.mark.parametrize("lanes,overlap", [(1, False), (2, False), (2, True), (3, True), (1, True)])
+def test_chain_push_triggers_equals_separate_calls(lanes, overlap):
+    """Triggers fused into the chain's detector: the ratio and the trigger
+    list equal a chain push followed by a trigger push, on a stream with
+    events (the small-workload chain at amplitude 6, thresholds 3 / 1.5),
+    pushes of 1..3000 samples (several launches per push, ragged segments),
+    in one and two lanes, with and without the trigger's overlap mode."""
+    import torch
+    from paper_2605_20132_gb300.chain import Chain, Trigger, butter_bandpass
+    rng = np.random.default_rng(85)
+    C, N = 300, 12000
+    x = torch.from_numpy(synth.small_stream(C, N, seed=86) * np.float32(6.0)).cuda()
+    sos = butter_bandpass(4, 1.0, 50.0, 1000.0)
+    chunks = [1, 3000, 2049, 37] + chunking_fixed(rng, N - 5087, 3000)
+    ra, rb = torch.full_like(x, float("nan")), torch.full_like(x, float("nan"))
+    ca = Chain(C, sos, 1000.0, 5, 50, 1000, outputs=abi.FILARK_OUT_RATIO, max_chunk=3000)
+    cb = Chain(C, sos, 1000.0, 5, 50, 1000, outputs=abi.FILARK_OUT_RATIO, max_chunk=3000)
+    cb.set_lanes(lanes)
+    ta = Trigger(C, 3.0, 1.5, max_chunk=3000)
+    tb = Trigger(C, 3.0, 1.5, max_chunk=3000)
+    if overlap:
+        tb.set_overlap(True)
+    t = 0
+    for k in chunks:
+        ca.push(x[t:t + k], ratio=ra[t:t + k])
+        ta.push(ra[t:t + k])
+        cb.push_triggers(x[t:t + k], rb[t:t + k], tb)
+        t += k
+    assert t == N
+    ta.flush()
+    tb.flush()
+    ca.sync()
+    cb.join()
+    cb.sync()
+    assert torch.equal(ra, rb)
+    got, want = tb.triggers(), ta.triggers()
+    assert len(want) > 50
+    assert np.array_equal(sort_records(got), sort_records(want))
+    for o in (ca, cb, ta, tb):
+        o.close()
+
+
+def chunking_fixed(rng, n, hi):
+    out = []
+    while sum(out) < n:
+        out.append(int(min(rng.integers(1, hi + 1), n - sum(out))))
+    return out
+
