@@ -20,7 +20,7 @@ LIB = os.path.join(OUT, "libfilark.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-CU_SOURCES = ["chain_kernel.cu", "chain_batch.cu", "chain_batch_solo.cu", "chain_static.cu", "sos_adjoint.cu", "trigger.cu",
+CU_SOURCES = ["chain_kernel.cu", "chain_kernel_trig.cu", "chain_batch.cu", "chain_batch_solo.cu", "chain_static.cu", "sos_adjoint.cu", "trigger.cu",
               "temporal.cu", "fftfilt.cu", "view.cu"]
 CPP_SOURCES = ["plan.cpp", "api.cpp", "batch.cpp"]
 HEADERS = [os.path.join(CSRC, "filark_internal.h"), os.path.join(CSRC, "chain_body.cuh"), os.path.join(CSRC, "chain_object.h"),

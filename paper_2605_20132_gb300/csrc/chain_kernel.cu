@@ -8,25 +8,22 @@ namespace filark {
 
 namespace {
 
-// TRIG: the detector also writes the trigger summary of every (channel,
-// 32-sample block) (filark_chain_push_triggers); DET only.
-template <int NS, bool DET, bool DENSE, bool TRIG = false>
+template <int NS, bool DET, bool DENSE>
 __global__ void __launch_bounds__(kThreads, kCTAsPerSM) chain_fwd_kernel(const __grid_constant__ ChainParams p) {
     if (p.pdl) pdl_launch_dependents();
-    chain_body<NS, DET, DENSE, false, TRIG>(p, p.u, p.u.tx0 + (int)blockIdx.x, blockIdx.y);
+    chain_body<NS, DET, DENSE>(p, p.u, p.u.tx0 + (int)blockIdx.x, blockIdx.y);
 }
 
-template <int NS, bool DET, bool DENSE, bool TRIG = false>
+template <int NS, bool DET, bool DENSE>
 cudaError_t configure_t() {
-    cudaError_t e = cudaFuncSetAttribute(chain_fwd_kernel<NS, DET, DENSE, TRIG>,
+    cudaError_t e = cudaFuncSetAttribute(chain_fwd_kernel<NS, DET, DENSE>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)chain_smem_bytes(DENSE));
     if (e == cudaSuccess && kMaxCluster > 8)
-        e = cudaFuncSetAttribute(chain_fwd_kernel<NS, DET, DENSE, TRIG>, cudaFuncAttributeNonPortableClusterSizeAllowed,
-                                 1);
+        e = cudaFuncSetAttribute(chain_fwd_kernel<NS, DET, DENSE>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     return e;
 }
 
-template <int NS, bool DET, bool DENSE, bool TRIG = false>
+template <int NS, bool DET, bool DENSE>
 cudaError_t launch_t(const ChainParams &p, int n_tiles, cudaStream_t stream) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)n_tiles, (unsigned)p.u.R, 1);
@@ -42,7 +39,7 @@ cudaError_t launch_t(const ChainParams &p, int n_tiles, cudaStream_t stream) {
     attr[1].val.programmaticStreamSerializationAllowed = p.pdl ? 1 : 0;
     cfg.attrs = attr;
     cfg.numAttrs = 2;
-    return cudaLaunchKernelEx(&cfg, chain_fwd_kernel<NS, DET, DENSE, TRIG>, p);
+    return cudaLaunchKernelEx(&cfg, chain_fwd_kernel<NS, DET, DENSE>, p);
 }
 
 }  // namespace
@@ -59,23 +56,10 @@ cudaError_t configure_chain_kernels() {
     FILARK_CFG(4, false, false) FILARK_CFG(4, true, false) FILARK_CFG(4, false, true) FILARK_CFG(4, true, true)
     FILARK_CFG(8, false, false) FILARK_CFG(8, true, false) FILARK_CFG(8, false, true) FILARK_CFG(8, true, true)
 #undef FILARK_CFG
-#define FILARK_CFG_T(NS, X) if (e == cudaSuccess) e = configure_t<NS, true, X, true>();
-    FILARK_CFG_T(0, false) FILARK_CFG_T(2, false) FILARK_CFG_T(2, true) FILARK_CFG_T(4, false) FILARK_CFG_T(4, true)
-    FILARK_CFG_T(8, false) FILARK_CFG_T(8, true)
-#undef FILARK_CFG_T
+    if (e == cudaSuccess) e = configure_chain_trig_kernels();
     if (e == cudaSuccess) e = configure_batch_kernels();
     if (e == cudaSuccess) e = configure_batch_kernels_solo();
     return e;
-}
-
-cudaError_t launch_chain_trig(const ChainParams &p, int NS, bool dense, int n_tiles, cudaStream_t stream) {
-    switch (NS) {
-    case 0: return launch_t<0, true, false, true>(p, n_tiles, stream);
-    case 2: return dense ? launch_t<2, true, true, true>(p, n_tiles, stream) : launch_t<2, true, false, true>(p, n_tiles, stream);
-    case 4: return dense ? launch_t<4, true, true, true>(p, n_tiles, stream) : launch_t<4, true, false, true>(p, n_tiles, stream);
-    case 8: return dense ? launch_t<8, true, true, true>(p, n_tiles, stream) : launch_t<8, true, false, true>(p, n_tiles, stream);
-    default: return cudaErrorInvalidValue;
-    }
 }
 
 cudaError_t launch_chain(const ChainParams &p, int NS, bool det, bool dense, int n_tiles, cudaStream_t stream) {

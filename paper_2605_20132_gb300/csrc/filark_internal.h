@@ -206,6 +206,7 @@ size_t chain_smem_bytes(bool dense);
 // The same launch with the detector writing the trigger summaries too
 // (p.u.trig_summ, p.trig_on / trig_off); detector chains only.
 cudaError_t launch_chain_trig(const ChainParams &p, int NS, bool dense, int n_tiles, cudaStream_t stream);
+cudaError_t configure_chain_trig_kernels();   // chain_kernel_trig.cu
 
 // A trigger as the chain's detector sees it when it writes the trigger
 // summaries itself (trigger.cu): the summary buffer the next push fills
