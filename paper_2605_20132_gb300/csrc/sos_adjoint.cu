@@ -58,30 +58,39 @@ constexpr long long kTargetThreads = 1LL << 17;   // (segment, channel) pairs th
 constexpr long long kMinSegment = 128;
 constexpr int kChainThreads = 64;   // small CTAs: the chaining has only C x (2S rounded up) threads
 
-// A double-float number (hi + lo, ~48 significant bits) on the FP32 pipe:
-// FMA-exact products and TwoSum additions (the "sloppy" sum: error ~2^-44 of
-// the operands, far below what the recursions amplify to).
+// A double-float number (hi + lo, ~48 significant bits) on the FP32 pipe.
+// The recursions are sums of products, so their one primitive is a fused
+// acc + a * b: the leading product split exactly (TwoProduct by FMA), added
+// to acc.hi exactly (Knuth's TwoSum), the rounding errors and the cross terms
+// a.hi * b.lo, a.lo * b.hi gathered in the low word (as in the compensated dot
+// product of Ogita, Rump and Oishi, 2005).  The sum is left unnormalised
+// between the terms of one expression and renormalised (Dekker's Fast2Sum)
+// once per value the recursion keeps.  Explicit-rounding intrinsics keep the
+// compiler from contracting the error-free steps into FMAs.
 struct dd {
     float hi, lo;
 };
 __device__ __forceinline__ dd dd_norm(float s, float e) {
-    const float hi = s + e;
-    return dd{hi, e - (hi - s)};
+    const float hi = __fadd_rn(s, e);
+    return dd{hi, __fsub_rn(e, __fsub_rn(hi, s))};
 }
-__device__ __forceinline__ dd operator+(dd a, dd b) {
-    const float s = a.hi + b.hi;
-    const float bb = s - a.hi;
-    const float e = (a.hi - (s - bb)) + (b.hi - bb) + a.lo + b.lo;
-    return dd_norm(s, e);
-}
+__device__ __forceinline__ dd dd_renorm(dd v) { return dd_norm(v.hi, v.lo); }
 __device__ __forceinline__ dd operator-(dd a) { return dd{-a.hi, -a.lo}; }
-__device__ __forceinline__ dd operator-(dd a, dd b) { return a + (-b); }
-__device__ __forceinline__ dd operator*(dd a, dd b) {
-    const float p = a.hi * b.hi;
+// a * b, unnormalised
+__device__ __forceinline__ dd dd_mul_raw(dd a, dd b) {
+    const float p = __fmul_rn(a.hi, b.hi);
     float e = fmaf(a.hi, b.hi, -p);
     e = fmaf(a.hi, b.lo, e);
     e = fmaf(a.lo, b.hi, e);
-    return dd_norm(p, e);
+    return dd{p, e};
+}
+// acc + a * b, unnormalised (acc may be unnormalised too)
+__device__ __forceinline__ dd dd_fma(dd acc, dd a, dd b) {
+    const dd m = dd_mul_raw(a, b);
+    const float s = __fadd_rn(acc.hi, m.hi);
+    const float bb = __fsub_rn(s, acc.hi);
+    const float err = __fadd_rn(__fsub_rn(acc.hi, __fsub_rn(s, bb)), __fsub_rn(m.hi, bb));
+    return dd{s, __fadd_rn(acc.lo, __fadd_rn(err, m.lo))};
 }
 __device__ __forceinline__ dd dd_f(float v) { return dd{v, 0.f}; }
 __device__ __forceinline__ float dd_to_f(dd v) { return v.hi + v.lo; }
@@ -141,16 +150,21 @@ __host__ __device__ __forceinline__ R adj_step(const SosCoef &k, int s, R g, R &
 
 __device__ __forceinline__ dd cf(const DDC &c) { return dd{c.hi, c.lo}; }
 
+// tdf2_step in double-float: three fused sums of products, each renormalised
+// once (y, and the two states the next step reads).
 __device__ __forceinline__ dd tdf2_dd(const SosCoef &k, int s, dd u, dd &z1, dd &z2) {
-    const dd y = cf(k.dnb[s][0]) * u + z1;
-    z1 = cf(k.dnb[s][1]) * u - cf(k.dna[s][0]) * y + z2;
-    z2 = cf(k.dnb[s][2]) * u - cf(k.dna[s][1]) * y;
+    const dd y = dd_renorm(dd_fma(z1, cf(k.dnb[s][0]), u));
+    z1 = dd_renorm(dd_fma(dd_fma(z2, cf(k.dnb[s][1]), u), -cf(k.dna[s][0]), y));
+    z2 = dd_renorm(dd_fma(dd_mul_raw(cf(k.dnb[s][2]), u), -cf(k.dna[s][1]), y));
     return y;
 }
 
+// adj_step in double-float, with the denominator divided through:
+// w = g / a0 - (a1 / a0) w1 - (a2 / a0) w2.
 __device__ __forceinline__ dd adj_dd(const SosCoef &k, int s, dd g, dd &w1, dd &w2, dd &w) {
-    w = (g - cf(k.da[s][1]) * w1 - cf(k.da[s][2]) * w2) * cf(k.dia0[s]);
-    const dd gprev = cf(k.db[s][0]) * w + cf(k.db[s][1]) * w1 + cf(k.db[s][2]) * w2;
+    w = dd_renorm(dd_fma(dd_fma(dd_mul_raw(cf(k.dia0[s]), g), -cf(k.dna[s][0]), w1), -cf(k.dna[s][1]), w2));
+    const dd gprev =
+        dd_renorm(dd_fma(dd_fma(dd_mul_raw(cf(k.db[s][0]), w), cf(k.db[s][1]), w1), cf(k.db[s][2]), w2));
     w2 = w1;
     w1 = w;
     return gprev;
@@ -309,21 +323,10 @@ __global__ void __launch_bounds__(kAdjThreads) adj_local_kernel(const __grid_con
     }
 }
 
-// acc += a * b for double-float a, b, the accumulator kept unnormalised: the
-// leading product split exactly (TwoProduct by FMA) and summed exactly into
-// acc.hi (TwoSum), its rounding error and the cross terms gathered in acc.lo
-// (as in the compensated dot product of Ogita, Rump and Oishi, 2005).
-__device__ __forceinline__ void dd_acc_mul(dd &acc, dd a, dd b) {
-    const float p = __fmul_rn(a.hi, b.hi);
-    float e = fmaf(a.hi, b.hi, -p);
-    e = fmaf(a.hi, b.lo, e);
-    e = fmaf(a.lo, b.hi, e);
-    const float s = __fadd_rn(acc.hi, p);
-    const float bb = __fsub_rn(s, acc.hi);
-    const float err = __fadd_rn(__fsub_rn(acc.hi, __fsub_rn(s, bb)), __fsub_rn(p, bb));
-    acc.lo = __fadd_rn(acc.lo, __fadd_rn(err, e));
-    acc.hi = s;
-}
+// acc += a * b for double-float a, b, the accumulator kept unnormalised
+// over the whole run (its low word gathers every rounding error and cross
+// term).
+__device__ __forceinline__ void dd_acc_mul(dd &acc, dd a, dd b) { acc = dd_fma(acc, a, b); }
 
 // B3: gradients.  The pieces (the forward left the state at each piece start
 // in the checkpoints) are handled last to first: recompute the piece's
@@ -378,9 +381,10 @@ __global__ void __launch_bounds__(kAdjThreads) adj_run_kernel(const __grid_const
         }
         for (long long n = b - 1; n >= a; --n) {
             dd gg = dd_f(gy[n * ldg + c]);
+            dd ys = ld_dd(sig + ix((n - a) * S + S - 1, NT, T));
 #pragma unroll
             for (int s = S - 1; s >= 0; --s) {
-                const dd ys = ld_dd(sig + ix((n - a) * S + s, NT, T));
+                // section s maps u_s = y_{s-1} (x for s = 0) to y_s
                 const dd us = s == 0 ? dd_f(x[n * ldx + c]) : ld_dd(sig + ix((n - a) * S + s - 1, NT, T));
                 const dd wn1 = w1[s], wn2 = w2[s];
                 dd w;
@@ -391,6 +395,7 @@ __global__ void __launch_bounds__(kAdjThreads) adj_run_kernel(const __grid_const
                 dd_acc_mul(ga[s][0], ys, w);     // negated at the end
                 dd_acc_mul(ga[s][1], ys, wn1);
                 dd_acc_mul(ga[s][2], ys, wn2);
+                ys = us;
             }
             if (gx) gx[n * ldgx + c] = dd_to_f(gg);
         }
