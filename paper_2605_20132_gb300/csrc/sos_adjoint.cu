@@ -119,6 +119,15 @@ struct Transition {
     double T[kMaxState][kMaxState];  // row-major, first 2S x 2S used
 };
 
+// Block form of the local passes: over a block of kLocalL samples the state
+// (zero-input step A, e = the state one step after a unit input from a zero
+// state) moves as z <- A^L z + sum_m K[m] u[m] with K[m] = A^(L-1-m) e.
+constexpr int kLocalL = 32;
+struct LocalTables {
+    DDC AL[kMaxState][kMaxState];  // A^L, first D x D used
+    DDC K[kLocalL][kMaxState];     // K[m][i], first D columns used
+};
+
 struct Geometry {
     long long N, ckpt, P;  // samples, segment length (<= the requested interval), piece length
     long long nseg, npiece;
@@ -179,34 +188,82 @@ __device__ __forceinline__ void seg_range(const Geometry &g, long long seg, long
 // (coalesced); each 8-byte entry holds a double-float.
 __device__ __forceinline__ long long ix(long long row, long long NT, long long T) { return row * NT + T; }
 
-// F1: final state of each segment (except the last) from a zero start, stored
-// in the checkpoint slot of the next segment.
-template <int S>
-__global__ void __launch_bounds__(kAdjThreads) fwd_local_kernel(const __grid_constant__ SosCoef k,
-                                                                const __grid_constant__ Geometry g,
-                                                                const float *__restrict__ x, long long ldx,
-                                                                double *__restrict__ ckpt) {
+// acc + a * v for a double-float a and a float v, unnormalised
+__device__ __forceinline__ dd dd_fma_f(dd acc, const DDC &a, float v) {
+    const float p = __fmul_rn(a.hi, v);
+    float e = fmaf(a.hi, v, -p);
+    e = fmaf(a.lo, v, e);
+    const float s = __fadd_rn(acc.hi, p);
+    const float bb = __fsub_rn(s, acc.hi);
+    const float err = __fadd_rn(__fsub_rn(acc.hi, __fsub_rn(s, bb)), __fsub_rn(p, bb));
+    return dd{s, __fadd_rn(acc.lo, __fadd_rn(err, e))};
+}
+
+// F1 / B1: the state each segment ends in from a zero start (the forward:
+// every segment but the last, stored in the checkpoint slot of the next one;
+// the adjoint, which runs backwards in time: every segment but the first, its
+// adjoint state (w_s[n+1], w_s[n+2]) at the segment start stored in the slot of
+// the previous one).  From a zero start that state is linear in the segment's
+// input, so it is formed block by block from the tables (z <- A^L z +
+// sum_m K[m] u[m]): D + D^2 / L double-float products per sample instead of the
+// S sections' recursions.  Samples are taken in the recursion's order (the
+// adjoint from the segment's end); the first block is the partial one, its
+// len mod L samples at positions L - r .. L - 1.
+template <int S, bool ADJ>
+__global__ void __launch_bounds__(kAdjThreads) local_block_kernel(const __grid_constant__ LocalTables tb,
+                                                                  const __grid_constant__ Geometry g,
+                                                                  const float *__restrict__ in, long long ld,
+                                                                  double *__restrict__ out) {
+    constexpr int D = 2 * S;
     const long long T = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (T >= g.NT) return;
     const long long seg = T / g.C;
     const int c = (int)(T - seg * g.C);
-    if (seg == g.nseg - 1) return;
+    if (ADJ ? seg == 0 : seg == g.nseg - 1) return;
     long long t0, t1;
     seg_range(g, seg, t0, t1);
-    dd z[S][2];
+    const long long len = t1 - t0;
+    // sample q of the recursion's order
+    const float *src = in + (ADJ ? (t1 - 1) * ld : t0 * ld) + c;
+    const long long step = ADJ ? -ld : ld;
+    dd z[D];
 #pragma unroll
-    for (int s = 0; s < S; ++s) z[s][0] = z[s][1] = dd_f(0.f);
-    for (long long n = t0; n < t1; ++n) {
-        dd u = dd_f(x[n * ldx + c]);
+    for (int i = 0; i < D; ++i) z[i] = dd_f(0.f);
+    long long q = 0;
+    const int r = (int)(len % kLocalL);
+    if (r) {
+        dd acc[D];
 #pragma unroll
-        for (int s = 0; s < S; ++s) u = tdf2_dd(k, s, u, z[s][0], z[s][1]);
+        for (int i = 0; i < D; ++i) acc[i] = dd_f(0.f);
+        for (int m = kLocalL - r; m < kLocalL; ++m, ++q) {
+            const float v = src[q * step];
+#pragma unroll
+            for (int i = 0; i < D; ++i) acc[i] = dd_fma_f(acc[i], tb.K[m][i], v);
+        }
+#pragma unroll
+        for (int i = 0; i < D; ++i) z[i] = dd_renorm(acc[i]);
     }
-    const long long Tn = T + g.C;  // (seg + 1, c)
+    for (; q < len; q += kLocalL) {
+        dd acc[D];
 #pragma unroll
-    for (int s = 0; s < S; ++s) {
-        st_dd(ckpt + ix(2 * s, g.NT, Tn), z[s][0]);
-        st_dd(ckpt + ix(2 * s + 1, g.NT, Tn), z[s][1]);
+        for (int i = 0; i < D; ++i) {
+            acc[i] = dd_mul_raw(cf(tb.AL[i][0]), z[0]);
+#pragma unroll
+            for (int j = 1; j < D; ++j) acc[i] = dd_fma(acc[i], cf(tb.AL[i][j]), z[j]);
+        }
+        const float *blk = src + q * step;
+#pragma unroll 8
+        for (int m = 0; m < kLocalL; ++m) {
+            const float v = blk[m * step];
+#pragma unroll
+            for (int i = 0; i < D; ++i) acc[i] = dd_fma_f(acc[i], tb.K[m][i], v);
+        }
+#pragma unroll
+        for (int i = 0; i < D; ++i) z[i] = dd_renorm(acc[i]);
     }
+    const long long To = ADJ ? T - g.C : T + g.C;
+#pragma unroll
+    for (int i = 0; i < D; ++i) st_dd(out + ix(i, g.NT, To), z[i]);
 }
 
 // F2 / B2: per channel, chain the segments (FP64: one D x D product per
@@ -289,37 +346,6 @@ __global__ void __launch_bounds__(kAdjThreads) fwd_run_kernel(const __grid_const
 #pragma unroll
         for (int s = 0; s < S; ++s) u = tdf2_dd(k, s, u, z[s][0], z[s][1]);
         if (y) y[n * ldy + c] = dd_to_f(u);
-    }
-}
-
-// B1: adjoint state at the start of each segment (except the first) from a
-// zero adjoint state at its end, stored in the slot of the previous segment.
-// The adjoint state of section s is (w_s[n+1], w_s[n+2]).
-template <int S>
-__global__ void __launch_bounds__(kAdjThreads) adj_local_kernel(const __grid_constant__ SosCoef k,
-                                                                const __grid_constant__ Geometry g,
-                                                                const float *__restrict__ gy, long long ldg,
-                                                                double *__restrict__ beta) {
-    const long long T = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (T >= g.NT) return;
-    const long long seg = T / g.C;
-    const int c = (int)(T - seg * g.C);
-    if (seg == 0) return;
-    long long t0, t1;
-    seg_range(g, seg, t0, t1);
-    dd w1[S], w2[S];
-#pragma unroll
-    for (int s = 0; s < S; ++s) w1[s] = w2[s] = dd_f(0.f);
-    for (long long n = t1 - 1; n >= t0; --n) {
-        dd gg = dd_f(gy[n * ldg + c]), w;
-#pragma unroll
-        for (int s = S - 1; s >= 0; --s) gg = adj_dd(k, s, gg, w1[s], w2[s], w);
-    }
-    const long long Tp = T - g.C;  // (seg - 1, c)
-#pragma unroll
-    for (int s = 0; s < S; ++s) {
-        st_dd(beta + ix(2 * s, g.NT, Tp), w1[s]);
-        st_dd(beta + ix(2 * s + 1, g.NT, Tp), w2[s]);
     }
 }
 
@@ -517,6 +543,45 @@ void transition(const SosCoef &k, int S, bool adjoint, long long n, Transition &
         for (int j = 0; j < D; ++j) out.T[i][j] = (double)R[i][j];
 }
 
+// The local passes' tables (A^L and K[m] = A^(L-1-m) e) from the kernels' own
+// one-step recursion, in long double, split into double-float pairs.
+void local_tables(const SosCoef &k, int S, bool adjoint, LocalTables &tb) {
+    const int D = 2 * S;
+    long double A[kMaxState][kMaxState], AL[kMaxState][kMaxState];
+    one_step_matrix(k, S, adjoint, A);
+    long double e[kMaxState] = {};
+    if (!adjoint) {
+        long double u = 1.0L;
+        for (int s = 0; s < S; ++s) u = tdf2_step<long double>(k, s, u, e[2 * s], e[2 * s + 1]);
+    } else {
+        long double gg = 1.0L, w;
+        for (int s = S - 1; s >= 0; --s) gg = adj_step<long double>(k, s, gg, e[2 * s], e[2 * s + 1], w);
+    }
+    long double K[kLocalL][kMaxState] = {};
+    for (int i = 0; i < D; ++i) K[kLocalL - 1][i] = e[i];
+    for (int m = kLocalL - 2; m >= 0; --m)
+        for (int i = 0; i < D; ++i) {
+            long double acc = 0.0L;
+            for (int j = 0; j < D; ++j) acc += A[i][j] * K[m + 1][j];
+            K[m][i] = acc;
+        }
+    for (int i = 0; i < D; ++i)
+        for (int j = 0; j < D; ++j) AL[i][j] = A[i][j];
+    for (int n = 1; n < kLocalL; n *= 2) mat_mul(D, AL, AL, AL);  // kLocalL is a power of two
+    auto split = [](long double v) {
+        DDC d;
+        d.hi = (float)v;
+        d.lo = (float)(v - (long double)d.hi);
+        return d;
+    };
+    std::memset(&tb, 0, sizeof(tb));
+    for (int i = 0; i < D; ++i)
+        for (int j = 0; j < D; ++j) tb.AL[i][j] = split(AL[i][j]);
+    for (int m = 0; m < kLocalL; ++m)
+        for (int i = 0; i < D; ++i) tb.K[m][i] = split(K[m][i]);
+}
+static_assert((kLocalL & (kLocalL - 1)) == 0, "kLocalL: a power of two");
+
 long long piece_len(long long ckpt) {
     long long P = (long long)std::ceil(std::sqrt(2.0 * (double)ckpt));
     return std::max(1LL, std::min(P, ckpt));
@@ -565,25 +630,25 @@ filark_status launch_status(const char *where) {
 }
 
 template <int S>
-void launch_forward(const SosCoef &k, const Transition &tr, const Geometry &g, const float *x, long long ldx,
-                    float *y, long long ldy, double *ckpt, cudaStream_t st) {
+void launch_forward(const SosCoef &k, const LocalTables &tb, const Transition &tr, const Geometry &g,
+                    const float *x, long long ldx, float *y, long long ldy, double *ckpt, cudaStream_t st) {
     const unsigned nb = (unsigned)((g.NT + kAdjThreads - 1) / kAdjThreads);
     const unsigned nc = (unsigned)((g.C * chain_group<S>() + kChainThreads - 1) / kChainThreads);
-    fwd_local_kernel<S><<<nb, kAdjThreads, 0, st>>>(k, g, x, ldx, ckpt);
+    local_block_kernel<S, false><<<nb, kAdjThreads, 0, st>>>(tb, g, x, ldx, ckpt);
     chain_segments_kernel<S><<<nc, kChainThreads, 0, st>>>(tr, g, ckpt, 0);
     fwd_run_kernel<S><<<nb, kAdjThreads, 0, st>>>(k, g, x, ldx, ckpt, y, ldy);
 }
 
 template <int S>
-void launch_backward(const SosCoef &k, const Transition &tr, const Geometry &g, const float *x, long long ldx,
-                     const float *gy, long long ldg, const double *ckpt, double *work, float *gx, long long ldgx,
-                     double *gsos, cudaStream_t st) {
+void launch_backward(const SosCoef &k, const LocalTables &tb, const Transition &tr, const Geometry &g,
+                     const float *x, long long ldx, const float *gy, long long ldg, const double *ckpt, double *work,
+                     float *gx, long long ldgx, double *gsos, cudaStream_t st) {
     const unsigned nb = (unsigned)((g.NT + kAdjThreads - 1) / kAdjThreads);
     const unsigned nc = (unsigned)((g.C * chain_group<S>() + kChainThreads - 1) / kChainThreads);
     double *beta = work;
     double *sig = beta + (size_t)g.NT * (2 * S);
     double *gpart = sig + (size_t)g.NT * (size_t)(g.P * S);
-    adj_local_kernel<S><<<nb, kAdjThreads, 0, st>>>(k, g, gy, ldg, beta);
+    local_block_kernel<S, true><<<nb, kAdjThreads, 0, st>>>(tb, g, gy, ldg, beta);
     chain_segments_kernel<S><<<nc, kChainThreads, 0, st>>>(tr, g, beta, 1);
     adj_run_kernel<S><<<nb, kAdjThreads, 0, st>>>(k, g, x, ldx, gy, ldg, ckpt, beta, sig, gx, ldgx, gpart);
     sum_partials_kernel<<<6 * S, kSumThreads, 0, st>>>(gpart, g.NT, gsos);
@@ -625,11 +690,13 @@ extern "C" filark_status filark_iir_forward_ckpt(const double *sos, int n_sectio
     }
     Transition tr;
     transition(k, n_sections, false, g.ckpt, tr);
+    LocalTables tb;
+    local_tables(k, n_sections, false, tb);
     cudaStream_t st = (cudaStream_t)stream;
     double *ck = (double *)d_ckpt;
     switch (n_sections) {
 #define FWD_CASE(S_) \
-    case S_: launch_forward<S_>(k, tr, g, d_x, ld_x, d_y, ld_y, ck, st); break;
+    case S_: launch_forward<S_>(k, tb, tr, g, d_x, ld_x, d_y, ld_y, ck, st); break;
         FWD_CASE(1) FWD_CASE(2) FWD_CASE(3) FWD_CASE(4) FWD_CASE(5) FWD_CASE(6) FWD_CASE(7) FWD_CASE(8)
 #undef FWD_CASE
     }
@@ -663,12 +730,14 @@ extern "C" filark_status filark_iir_backward(const double *sos, int n_sections, 
     }
     Transition tr;
     transition(k, n_sections, true, g.ckpt, tr);
+    LocalTables tb;
+    local_tables(k, n_sections, true, tb);
     cudaStream_t st = (cudaStream_t)stream;
     const double *ck = (const double *)d_ckpt;
     double *wk = (double *)d_work;
     switch (n_sections) {
 #define BWD_CASE(S_) \
-    case S_: launch_backward<S_>(k, tr, g, d_x, ld_x, d_gy, ld_gy, ck, wk, d_gx, ld_gx, d_gsos, st); break;
+    case S_: launch_backward<S_>(k, tb, tr, g, d_x, ld_x, d_gy, ld_gy, ck, wk, d_gx, ld_gx, d_gsos, st); break;
         BWD_CASE(1) BWD_CASE(2) BWD_CASE(3) BWD_CASE(4) BWD_CASE(5) BWD_CASE(6) BWD_CASE(7) BWD_CASE(8)
 #undef BWD_CASE
     }
