@@ -215,6 +215,14 @@ __global__ void __launch_bounds__(kAdjThreads) local_block_kernel(const __grid_c
                                                                   const float *__restrict__ in, long long ld,
                                                                   double *__restrict__ out) {
     constexpr int D = 2 * S;
+    // K in shared memory, row m as D / 2 float4 (two double-float entries
+    // each): every thread reads the same row, a broadcast
+    __shared__ float4 sK[kLocalL][D / 2];
+    for (int e = threadIdx.x; e < kLocalL * (D / 2); e += blockDim.x) {
+        const int m = e / (D / 2), i = 2 * (e % (D / 2));
+        sK[m][i / 2] = make_float4(tb.K[m][i].hi, tb.K[m][i].lo, tb.K[m][i + 1].hi, tb.K[m][i + 1].lo);
+    }
+    __syncthreads();
     const long long T = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (T >= g.NT) return;
     const long long seg = T / g.C;
@@ -223,6 +231,15 @@ __global__ void __launch_bounds__(kAdjThreads) local_block_kernel(const __grid_c
     long long t0, t1;
     seg_range(g, seg, t0, t1);
     const long long len = t1 - t0;
+    // acc[i] += K[m][i] v for all i
+    auto add_sample = [&](dd(&acc)[D], int m, float v) {
+#pragma unroll
+        for (int h = 0; h < D / 2; ++h) {
+            const float4 k2 = sK[m][h];
+            acc[2 * h] = dd_fma_f(acc[2 * h], DDC{k2.x, k2.y}, v);
+            acc[2 * h + 1] = dd_fma_f(acc[2 * h + 1], DDC{k2.z, k2.w}, v);
+        }
+    };
     // sample q of the recursion's order
     const float *src = in + (ADJ ? (t1 - 1) * ld : t0 * ld) + c;
     const long long step = ADJ ? -ld : ld;
@@ -235,11 +252,7 @@ __global__ void __launch_bounds__(kAdjThreads) local_block_kernel(const __grid_c
         dd acc[D];
 #pragma unroll
         for (int i = 0; i < D; ++i) acc[i] = dd_f(0.f);
-        for (int m = kLocalL - r; m < kLocalL; ++m, ++q) {
-            const float v = src[q * step];
-#pragma unroll
-            for (int i = 0; i < D; ++i) acc[i] = dd_fma_f(acc[i], tb.K[m][i], v);
-        }
+        for (int m = kLocalL - r; m < kLocalL; ++m, ++q) add_sample(acc, m, src[q * step]);
 #pragma unroll
         for (int i = 0; i < D; ++i) z[i] = dd_renorm(acc[i]);
     }
@@ -253,11 +266,7 @@ __global__ void __launch_bounds__(kAdjThreads) local_block_kernel(const __grid_c
         }
         const float *blk = src + q * step;
 #pragma unroll 8
-        for (int m = 0; m < kLocalL; ++m) {
-            const float v = blk[m * step];
-#pragma unroll
-            for (int i = 0; i < D; ++i) acc[i] = dd_fma_f(acc[i], tb.K[m][i], v);
-        }
+        for (int m = 0; m < kLocalL; ++m) add_sample(acc, m, blk[m * step]);
 #pragma unroll
         for (int i = 0; i < D; ++i) z[i] = dd_renorm(acc[i]);
     }
