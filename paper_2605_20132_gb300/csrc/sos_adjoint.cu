@@ -169,11 +169,13 @@ __device__ __forceinline__ dd tdf2_dd(const SosCoef &k, int s, dd u, dd &z1, dd 
 }
 
 // adj_step in double-float, with the denominator divided through:
-// w = g / a0 - (a1 / a0) w1 - (a2 / a0) w2.
+// w = g / a0 - (a1 / a0) w1 - (a2 / a0) w2.  The value passed down the
+// sections (g, then w) enters each sum last: the terms of the state are
+// summed while it is still on its way.
 __device__ __forceinline__ dd adj_dd(const SosCoef &k, int s, dd g, dd &w1, dd &w2, dd &w) {
-    w = dd_renorm(dd_fma(dd_fma(dd_mul_raw(cf(k.dia0[s]), g), -cf(k.dna[s][0]), w1), -cf(k.dna[s][1]), w2));
+    w = dd_renorm(dd_fma(dd_fma(dd_mul_raw(-cf(k.dna[s][0]), w1), -cf(k.dna[s][1]), w2), cf(k.dia0[s]), g));
     const dd gprev =
-        dd_renorm(dd_fma(dd_fma(dd_mul_raw(cf(k.db[s][0]), w), cf(k.db[s][1]), w1), cf(k.db[s][2]), w2));
+        dd_renorm(dd_fma(dd_fma(dd_mul_raw(cf(k.db[s][1]), w1), cf(k.db[s][2]), w2), cf(k.db[s][0]), w));
     w2 = w1;
     w1 = w;
     return gprev;
@@ -405,8 +407,10 @@ __global__ void __launch_bounds__(kAdjThreads) adj_run_kernel(const __grid_const
                 z[s][0] = ld_dd(ckpt + ix(p * (2 * S) + 2 * s, NT, T));
                 z[s][1] = ld_dd(ckpt + ix(p * (2 * S) + 2 * s + 1, NT, T));
             }
+            float xn = x[a * ldx + c];  // loaded one sample ahead
             for (long long n = a; n < b; ++n) {
-                dd u = dd_f(x[n * ldx + c]);
+                dd u = dd_f(xn);
+                if (n + 1 < b) xn = x[(n + 1) * ldx + c];
 #pragma unroll
                 for (int s = 0; s < S; ++s) {
                     u = tdf2_dd(k, s, u, z[s][0], z[s][1]);
@@ -414,13 +418,29 @@ __global__ void __launch_bounds__(kAdjThreads) adj_run_kernel(const __grid_const
                 }
             }
         }
+        // the loads of sample n (y_s for every section, x, dL/dy) are issued
+        // one sample ahead
+        float gyn = gy[(b - 1) * ldg + c], xn = x[(b - 1) * ldx + c];
+        dd sn[S];
+#pragma unroll
+        for (int s = 0; s < S; ++s) sn[s] = ld_dd(sig + ix((b - 1 - a) * S + s, NT, T));
         for (long long n = b - 1; n >= a; --n) {
-            dd gg = dd_f(gy[n * ldg + c]);
-            dd ys = ld_dd(sig + ix((n - a) * S + S - 1, NT, T));
+            dd gg = dd_f(gyn);
+            const float xc = xn;
+            dd yv[S];
+#pragma unroll
+            for (int s = 0; s < S; ++s) yv[s] = sn[s];
+            if (n > a) {
+                gyn = gy[(n - 1) * ldg + c];
+                xn = x[(n - 1) * ldx + c];
+#pragma unroll
+                for (int s = 0; s < S; ++s) sn[s] = ld_dd(sig + ix((n - 1 - a) * S + s, NT, T));
+            }
+            dd ys = yv[S - 1];
 #pragma unroll
             for (int s = S - 1; s >= 0; --s) {
                 // section s maps u_s = y_{s-1} (x for s = 0) to y_s
-                const dd us = s == 0 ? dd_f(x[n * ldx + c]) : ld_dd(sig + ix((n - a) * S + s - 1, NT, T));
+                const dd us = s == 0 ? dd_f(xc) : yv[s - 1];
                 const dd wn1 = w1[s], wn2 = w2[s];
                 dd w;
                 gg = adj_dd(k, s, gg, w1[s], w2[s], w);
