@@ -375,7 +375,8 @@ filark_status filark_chain_run_static(const filark_chain_config *cfg, const floa
  * f = ceil(2^17 / that product), but not below min(ckpt_every, 128) samples.
  * The backward recomputes the section signals from those checkpoints, one
  * piece at a time, in the caller's d_work buffer of filark_iir_work_bytes(...)
- * bytes -- about (P * S + 8S) doubles per channel and segment -- rather than
+ * bytes -- (P * S + 8S) doubles per channel and segment plus 48S for the
+ * reduction of the coefficient gradients -- rather than
  * n_samples * n_sections doubles per channel for all intermediates.  Both
  * size queries return 0 for invalid sizes and depend only on their
  * arguments.

@@ -122,7 +122,7 @@ struct Transition {
 // Block form of the local passes: over a block of kLocalL samples the state
 // (zero-input step A, e = the state one step after a unit input from a zero
 // state) moves as z <- A^L z + sum_m K[m] u[m] with K[m] = A^(L-1-m) e.
-constexpr int kLocalL = 32;
+constexpr int kLocalL = 64;
 struct LocalTables {
     DDC AL[kMaxState][kMaxState];  // A^L, first D x D used
     DDC K[kLocalL][kMaxState];     // K[m][i], first D columns used
@@ -277,14 +277,23 @@ __global__ void __launch_bounds__(kAdjThreads) local_block_kernel(const __grid_c
     for (int i = 0; i < D; ++i) st_dd(out + ix(i, g.NT, To), z[i]);
 }
 
-// F2 / B2: per channel, chain the segments (FP64: one D x D product per
-// segment).  A group of G >= D lanes serves one channel, lane i owning state
-// row i; the state vector is read across the group with shuffles.
+// F2 / B2: per channel, chain the segments (one D x D product per segment,
+// double-float on the FP32 pipe).  A group of G >= D lanes serves one channel,
+// lane i owning state row i; the state vector is read across the group with
+// shuffles.
 //   forward : st[0] = 0,         st[j+1] += T st[j]        (j ascending)
 //   backward: st[nseg-1] = 0,    st[j-1] += T st[j]        (j descending)
 template <int S>
 __host__ __device__ constexpr int chain_group() {
     return 2 * S <= 2 ? 2 : (2 * S <= 4 ? 4 : (2 * S <= 8 ? 8 : 16));
+}
+
+// a + b for unnormalised double-float a, b (TwoSum of the leading words)
+__device__ __forceinline__ dd dd_add_raw(dd a, dd b) {
+    const float s = __fadd_rn(a.hi, b.hi);
+    const float bb = __fsub_rn(s, a.hi);
+    const float err = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, bb)), __fsub_rn(b.hi, bb));
+    return dd{s, __fadd_rn(__fadd_rn(a.lo, b.lo), err)};
 }
 
 template <int S>
@@ -297,10 +306,14 @@ __global__ void __launch_bounds__(kChainThreads) chain_segments_kernel(const __g
     const int gbase = (threadIdx.x & 31) - i;                // first lane of the group
     const long long c = ((long long)blockIdx.x * blockDim.x + threadIdx.x) / G;
     const bool row = c < g.C && i < D;                       // lanes past D or C only shuffle
-    double Trow[D];
+    dd Trow[D];
 #pragma unroll
-    for (int q = 0; q < D; ++q) Trow[q] = i < D ? tr.T[i][q] : 0.0;
-    double v = 0.0;
+    for (int q = 0; q < D; ++q) {
+        const double t = i < D ? tr.T[i][q] : 0.0;
+        const float hi = (float)t;
+        Trow[q] = dd{hi, (float)(t - (double)hi)};
+    }
+    dd v = dd_f(0.f);
     const long long first = backward ? g.nseg - 1 : 0;
     if (row) st_dd(st + ix(i, g.NT, first * g.C + c), dd_f(0.f));
     // the local state of step j + 1 is loaded while step j is combined
@@ -310,14 +323,19 @@ __global__ void __launch_bounds__(kChainThreads) chain_segments_kernel(const __g
         const long long seg = backward ? g.nseg - 1 - j : j;
         const dd loc = next;
         if (row && j + 1 < g.nseg) next = ld_dd(st + ix(i, g.NT, (backward ? g.nseg - 2 - j : j + 1) * g.C + c));
-        double acc = (double)loc.hi + (double)loc.lo;
+        // two interleaved sums halve the dependent chain
+        dd acc0 = loc, acc1 = dd_f(0.f);
 #pragma unroll
-        for (int q = 0; q < D; ++q) acc += Trow[q] * __shfl_sync(0xffffffffu, v, gbase + q);
-        v = row ? acc : 0.0;
-        if (row) {
-            const float hi = (float)acc;
-            st_dd(st + ix(i, g.NT, seg * g.C + c), dd{hi, (float)(acc - (double)hi)});
+        for (int q = 0; q < D; ++q) {
+            const dd vq{__shfl_sync(0xffffffffu, v.hi, gbase + q), __shfl_sync(0xffffffffu, v.lo, gbase + q)};
+            if (q & 1)
+                acc1 = dd_fma(acc1, Trow[q], vq);
+            else
+                acc0 = dd_fma(acc0, Trow[q], vq);
         }
+        const dd acc = dd_renorm(dd_add_raw(acc0, acc1));
+        v = row ? acc : dd_f(0.f);
+        if (row) st_dd(st + ix(i, g.NT, seg * g.C + c), acc);
     }
 }
 
@@ -343,6 +361,7 @@ __global__ void __launch_bounds__(kAdjThreads) fwd_run_kernel(const __grid_const
         z[s][1] = ld_dd(ckpt + ix(2 * s + 1, g.NT, T));
     }
     long long next = t0 + g.P, p = 1;
+    float xn = x[t0 * ldx + c];  // loaded one sample ahead
     for (long long n = t0; n < t1; ++n) {
         if (n == next) {
 #pragma unroll
@@ -353,7 +372,8 @@ __global__ void __launch_bounds__(kAdjThreads) fwd_run_kernel(const __grid_const
             ++p;
             next += g.P;
         }
-        dd u = dd_f(x[n * ldx + c]);
+        dd u = dd_f(xn);
+        if (n + 1 < t1) xn = x[(n + 1) * ldx + c];
 #pragma unroll
         for (int s = 0; s < S; ++s) u = tdf2_dd(k, s, u, z[s][0], z[s][1]);
         if (y) y[n * ldy + c] = dd_to_f(u);
@@ -464,29 +484,35 @@ __global__ void __launch_bounds__(kAdjThreads) adj_run_kernel(const __grid_const
         }
 }
 
-// B4: dL/dsos[j] = sum over all (segment, channel) partials, FP64, fixed order
-// (each thread keeps 4 interleaved sums, combined in a fixed tree).
+// B4: dL/dsos[j] = sum over all (segment, channel) partials, FP64, in a fixed
+// order, by two launches of this kernel: CTA (j, q) sums chunk q of the n
+// entries of row j (each thread 4 interleaved sums, combined in a fixed tree)
+// into out[j * gridDim.y + q]; the second launch sums each row's chunk sums.
 constexpr int kSumThreads = 1024;
-__global__ void __launch_bounds__(kSumThreads) sum_partials_kernel(const double *__restrict__ gpart, long long NT,
-                                                                   double *__restrict__ gsos) {
+constexpr int kSumSplit = 8;  // chunks per row in the first launch: 6 S x 8 CTAs
+__global__ void __launch_bounds__(kSumThreads) sum_rows_kernel(const double *__restrict__ in, long long n,
+                                                               long long ld, double *__restrict__ out) {
     __shared__ double part[kSumThreads];
-    const int j = blockIdx.x;
-    const double *src = gpart + (long long)j * NT;
+    const int j = blockIdx.x, q = blockIdx.y, nq = gridDim.y;
+    const long long chunk = (n + nq - 1) / nq;
+    const long long lo = (long long)q * chunk;
+    const long long len = lo < n ? (n - lo < chunk ? n - lo : chunk) : 0;
+    const double *src = in + (long long)j * ld + lo;
     double acc[4] = {0.0, 0.0, 0.0, 0.0};
     long long t = threadIdx.x;
-    for (; t + 3 * kSumThreads < NT; t += 4 * kSumThreads) {
+    for (; t + 3 * kSumThreads < len; t += 4 * kSumThreads) {
 #pragma unroll
-        for (int q = 0; q < 4; ++q) acc[q] += src[t + q * kSumThreads];
+        for (int r = 0; r < 4; ++r) acc[r] += src[t + r * kSumThreads];
     }
-    for (int q = 0; q < 4; ++q, t += kSumThreads)
-        if (t < NT) acc[q] += src[t];
+    for (int r = 0; r < 4; ++r, t += kSumThreads)
+        if (t < len) acc[r] += src[t];
     part[threadIdx.x] = (acc[0] + acc[1]) + (acc[2] + acc[3]);
     __syncthreads();
     for (int w = kSumThreads / 2; w > 0; w >>= 1) {
         if ((int)threadIdx.x < w) part[threadIdx.x] += part[threadIdx.x + w];
         __syncthreads();
     }
-    if (threadIdx.x == 0) gsos[j] = part[0];
+    if (threadIdx.x == 0) out[(long long)j * nq + q] = part[0];
 }
 
 // ---- host side ---------------------------------------------------------------
@@ -638,8 +664,10 @@ bool make_geometry(int S, int C, long long N, long long ckpt, Geometry &g) {
 // checkpoints: the state at every piece start, [npiece * 2S][NT]
 size_t ckpt_doubles(const Geometry &g, int S) { return (size_t)g.NT * (size_t)(g.npiece * 2 * S); }
 
-// workspace: beta [2S][NT], sig [P*S][NT], gpart [6S][NT]
-size_t work_doubles(const Geometry &g, int S) { return (size_t)g.NT * (size_t)(2 * S + g.P * S + 6 * S); }
+// workspace: beta [2S][NT], sig [P*S][NT], gpart [6S][NT], chunk sums [6S][kSumSplit]
+size_t work_doubles(const Geometry &g, int S) {
+    return (size_t)g.NT * (size_t)(2 * S + g.P * S + 6 * S) + (size_t)(6 * S * kSumSplit);
+}
 
 bool check_sos(const double *sos, int S, SosCoef &k) {
     if (!sos || !load_coef(sos, S, k)) {
@@ -677,10 +705,12 @@ void launch_backward(const SosCoef &k, const LocalTables &tb, const Transition &
     double *beta = work;
     double *sig = beta + (size_t)g.NT * (2 * S);
     double *gpart = sig + (size_t)g.NT * (size_t)(g.P * S);
+    double *chunks = gpart + (size_t)g.NT * (size_t)(6 * S);
     local_block_kernel<S, true><<<nb, kAdjThreads, 0, st>>>(tb, g, gy, ldg, beta);
     chain_segments_kernel<S><<<nc, kChainThreads, 0, st>>>(tr, g, beta, 1);
     adj_run_kernel<S><<<nb, kAdjThreads, 0, st>>>(k, g, x, ldx, gy, ldg, ckpt, beta, sig, gx, ldgx, gpart);
-    sum_partials_kernel<<<6 * S, kSumThreads, 0, st>>>(gpart, g.NT, gsos);
+    sum_rows_kernel<<<dim3(6 * S, kSumSplit), kSumThreads, 0, st>>>(gpart, g.NT, g.NT, chunks);
+    sum_rows_kernel<<<dim3(6 * S, 1), kSumThreads, 0, st>>>(chunks, kSumSplit, kSumSplit, gsos);
 }
 
 }  // namespace

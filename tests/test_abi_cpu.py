@@ -190,14 +190,15 @@ def _segment(C, N, ckpt):
 def test_iir_buffer_sizes(S, C, N, ckpt):
     """Checkpoints: 2S doubles per channel at every piece start of every
     segment; work: the adjoint states, one piece of section signals and the
-    gradient partials per (segment, channel)."""
+    gradient partials per (segment, channel), and 6S x 8 chunk sums of the
+    gradient reduction."""
     seg = _segment(C, N, ckpt)
     assert seg <= ckpt
     nseg = -(-N // seg)
     P = _piece(seg)
     npiece = -(-min(seg, N) // P)
     assert abi.filark_iir_ckpt_bytes(S, C, N, ckpt) == 8 * nseg * C * npiece * 2 * S
-    assert abi.filark_iir_work_bytes(S, C, N, ckpt) == 8 * nseg * C * (2 * S + P * S + 6 * S)
+    assert abi.filark_iir_work_bytes(S, C, N, ckpt) == 8 * (nseg * C * (2 * S + P * S + 6 * S) + 6 * S * 8)
 
 
 def test_iir_segments_fill_the_gpu_only_when_needed():
