@@ -467,8 +467,9 @@ __global__ void __launch_bounds__(kAdjThreads) adj_run_kernel(const __grid_const
                 dd_acc_mul(gb[s][0], us, w);
                 dd_acc_mul(gb[s][1], us, wn1);
                 dd_acc_mul(gb[s][2], us, wn2);
-                dd_acc_mul(ga[s][0], ys, w);     // negated at the end
-                dd_acc_mul(ga[s][1], ys, wn1);
+                // ga[s][0] (dL/da0) follows from the other five after the
+                // reduction (finish_a0_kernel)
+                dd_acc_mul(ga[s][1], ys, wn1);     // negated at the end
                 dd_acc_mul(ga[s][2], ys, wn2);
                 ys = us;
             }
@@ -480,7 +481,7 @@ __global__ void __launch_bounds__(kAdjThreads) adj_run_kernel(const __grid_const
 #pragma unroll
         for (int i = 0; i < 3; ++i) {
             gpart[ix(6 * s + i, NT, T)] = (double)gb[s][i].hi + (double)gb[s][i].lo;
-            gpart[ix(6 * s + 3 + i, NT, T)] = -((double)ga[s][i].hi + (double)ga[s][i].lo);
+            gpart[ix(6 * s + 3 + i, NT, T)] = i == 0 ? 0.0 : -((double)ga[s][i].hi + (double)ga[s][i].lo);
         }
 }
 
@@ -513,6 +514,19 @@ __global__ void __launch_bounds__(kSumThreads) sum_rows_kernel(const double *__r
         __syncthreads();
     }
     if (threadIdx.x == 0) out[(long long)j * nq + q] = part[0];
+}
+
+// B5: dL/da0 of each section.  Scaling a section's six coefficients by the
+// same factor leaves the cascade unchanged, so the loss is homogeneous of
+// degree 0 in them and (Euler) sum_k c_k dL/dc_k = 0: dL/da0 =
+// -(b0 gb0 + b1 gb1 + b2 gb2 + a1 ga1 + a2 ga2) / a0, from the reduced FP64
+// sums -- one product per section and sample fewer in adj_run.
+__global__ void finish_a0_kernel(const __grid_constant__ SosCoef k, int S, double *__restrict__ gsos) {
+    const int s = threadIdx.x;
+    if (s >= S) return;
+    double *g = gsos + 6 * s;
+    const double acc = k.b[s][0] * g[0] + k.b[s][1] * g[1] + k.b[s][2] * g[2] + k.a[s][1] * g[4] + k.a[s][2] * g[5];
+    g[3] = -acc / k.a[s][0];
 }
 
 // ---- host side ---------------------------------------------------------------
@@ -711,6 +725,7 @@ void launch_backward(const SosCoef &k, const LocalTables &tb, const Transition &
     adj_run_kernel<S><<<nb, kAdjThreads, 0, st>>>(k, g, x, ldx, gy, ldg, ckpt, beta, sig, gx, ldgx, gpart);
     sum_rows_kernel<<<dim3(6 * S, kSumSplit), kSumThreads, 0, st>>>(gpart, g.NT, g.NT, chunks);
     sum_rows_kernel<<<dim3(6 * S, 1), kSumThreads, 0, st>>>(chunks, kSumSplit, kSumSplit, gsos);
+    finish_a0_kernel<<<1, 32, 0, st>>>(k, S, gsos);
 }
 
 }  // namespace

@@ -663,6 +663,25 @@ def pin_adjoint_identity(ora):
     return abs(a - b) / max(abs(a), 1e-30), 1e-10
 
 
+def pin_adjoint_scale_invariance(ora):
+    """Scaling all six coefficients of one section by the same factor leaves
+    the cascade unchanged, so the loss is homogeneous of degree 0 in each
+    section's coefficients and (Euler) sum_k c_k dL/dc_k = 0 per section.
+    Checked relative to sum_k |c_k dL/dc_k|; a wrong sign, a swapped lag or a
+    dropped term in any of the six gradients breaks it."""
+    rng = np.random.default_rng(19)
+    sos = ora.butter_bandpass(4, 1.0, 50.0, 1000.0) * np.array([[1.0], [2.5], [0.4], [1.0]])
+    target_sos = synth.perturb_sos(sos, 0.02, 20)
+    x = rng.standard_normal(2500)
+    target, _ = ora.sosfilt(target_sos, x)
+    _, _, gs = _loss_and_grads(ora, sos, x, target)
+    worst = 0.0
+    for s in range(sos.shape[0]):
+        terms = sos[s] * gs[s]
+        worst = _worst(worst, abs(float(np.sum(terms))) / float(np.sum(np.abs(terms))))
+    return worst, 1e-10
+
+
 def pin_stalta_naive_closed_forms(ora):
     """The literal-window helper itself: constant cf gives R = 1 after the
     warm-up; a single spike of height a at k0 gives STA = a/ns, LTA = a/nl
@@ -700,6 +719,7 @@ ALL_PINS = [
     pin_stalta_naive_closed_forms,
     pin_adjoint_finite_differences,
     pin_adjoint_identity,
+    pin_adjoint_scale_invariance,
     pin_trigger_closed_forms,
     pin_trigger_last_forcing_sample,
     pin_events_vs_flood_fill,
