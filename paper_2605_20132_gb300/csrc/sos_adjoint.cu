@@ -296,12 +296,30 @@ __device__ __forceinline__ dd dd_add_raw(dd a, dd b) {
     return dd{s, __fadd_rn(__fadd_rn(a.lo, b.lo), err)};
 }
 
+// asynchronous 8-byte global -> shared copies (cp.async), own copies only
+__device__ __forceinline__ void cp_async8(void *smem, const void *gmem) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+// The local states of kChainStage steps are copied into the thread's own
+// column of a shared-memory stage while the previous kChainStage steps are
+// combined (double-buffered), so the loads of a whole stage are in flight
+// together instead of one step ahead.
+constexpr int kChainStage = 32;
+
 template <int S>
 __global__ void __launch_bounds__(kChainThreads) chain_segments_kernel(const __grid_constant__ Transition tr,
                                                                        const __grid_constant__ Geometry g,
                                                                        double *__restrict__ st, int backward) {
     constexpr int D = 2 * S;
     constexpr int G = chain_group<S>();
+    __shared__ float2 stage[2][kChainStage][kChainThreads];
     const int i = threadIdx.x % G;                          // state row of this lane
     const int gbase = (threadIdx.x & 31) - i;                // first lane of the group
     const long long c = ((long long)blockIdx.x * blockDim.x + threadIdx.x) / G;
@@ -316,27 +334,40 @@ __global__ void __launch_bounds__(kChainThreads) chain_segments_kernel(const __g
     dd v = dd_f(0.f);
     const long long first = backward ? g.nseg - 1 : 0;
     if (row) st_dd(st + ix(i, g.NT, first * g.C + c), dd_f(0.f));
-    // the local state of step j + 1 is loaded while step j is combined
-    dd next = dd_f(0.f);
-    if (row && g.nseg > 1) next = ld_dd(st + ix(i, g.NT, (backward ? g.nseg - 2 : 1) * g.C + c));
-    for (long long j = 1; j < g.nseg; ++j) {
-        const long long seg = backward ? g.nseg - 1 - j : j;
-        const dd loc = next;
-        if (row && j + 1 < g.nseg) next = ld_dd(st + ix(i, g.NT, (backward ? g.nseg - 2 - j : j + 1) * g.C + c));
-        // two interleaved sums halve the dependent chain
-        dd acc0 = loc, acc1 = dd_f(0.f);
+    // steps j0 .. j0 + kChainStage - 1 (those < nseg) into stage[buf]
+    auto issue = [&](int buf, long long j0) {
+        if (row)
+            for (int q = 0; q < kChainStage && j0 + q < g.nseg; ++q) {
+                const long long seg = backward ? g.nseg - 1 - (j0 + q) : j0 + q;
+                cp_async8(&stage[buf][q][threadIdx.x], st + ix(i, g.NT, seg * g.C + c));
+            }
+        cp_async_commit();
+    };
+    issue(0, 1);
+    for (long long j0 = 1, sb = 0; j0 < g.nseg; j0 += kChainStage, sb ^= 1) {
+        issue((int)sb ^ 1, j0 + kChainStage);
+        cp_async_wait<1>();  // this thread's copies of stage sb have landed
+        const int nq = g.nseg - j0 < kChainStage ? (int)(g.nseg - j0) : kChainStage;
+        for (int q = 0; q < nq; ++q) {
+            const long long j = j0 + q;
+            const long long seg = backward ? g.nseg - 1 - j : j;
+            const float2 lv = stage[sb][q][threadIdx.x];
+            // two interleaved sums halve the dependent chain
+            dd acc0 = row ? dd{lv.x, lv.y} : dd_f(0.f), acc1 = dd_f(0.f);
 #pragma unroll
-        for (int q = 0; q < D; ++q) {
-            const dd vq{__shfl_sync(0xffffffffu, v.hi, gbase + q), __shfl_sync(0xffffffffu, v.lo, gbase + q)};
-            if (q & 1)
-                acc1 = dd_fma(acc1, Trow[q], vq);
-            else
-                acc0 = dd_fma(acc0, Trow[q], vq);
+            for (int r = 0; r < D; ++r) {
+                const dd vr{__shfl_sync(0xffffffffu, v.hi, gbase + r), __shfl_sync(0xffffffffu, v.lo, gbase + r)};
+                if (r & 1)
+                    acc1 = dd_fma(acc1, Trow[r], vr);
+                else
+                    acc0 = dd_fma(acc0, Trow[r], vr);
+            }
+            const dd acc = dd_renorm(dd_add_raw(acc0, acc1));
+            v = row ? acc : dd_f(0.f);
+            if (row) st_dd(st + ix(i, g.NT, seg * g.C + c), acc);
         }
-        const dd acc = dd_renorm(dd_add_raw(acc0, acc1));
-        v = row ? acc : dd_f(0.f);
-        if (row) st_dd(st + ix(i, g.NT, seg * g.C + c), acc);
     }
+    cp_async_wait<0>();
 }
 
 // F3: rerun every segment from its checkpoint, writing y (if asked for) and
