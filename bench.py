@@ -547,6 +547,12 @@ def run_batch_workload(args) -> None:
     print(json.dumps(line), flush=True)
 
 
+# warp instructions executed by one forward + backward of the adjoint workload
+# (2,048 ch x 30,000 samples, order-4 bandpass, checkpoints every 3,000),
+# summed over its kernels from one ncu capture
+ADJOINT_WARP_INSTRUCTIONS = 2.653e9
+
+
 def run_adjoint_workload(args) -> None:
     """Forward with checkpoints + reverse-time adjoint through the order-4
     bandpass on 2,048 channels x 30,000 samples (checkpoints every 3,000),
@@ -597,6 +603,14 @@ def run_adjoint_workload(args) -> None:
     ms_plain = _event_ms(plain, args.steps)
     chain.close()
     units = C * N
+    clocks = sampler.summary()
+    # FP32-issue roofline: the warp instructions of one forward + backward
+    # (ncu smsp__inst_executed.sum summed over its kernels on this workload)
+    # over the timed forward + backward, against one instruction per cycle on
+    # all 4 schedulers of the 152 SMs at the sampled SM clock
+    mhz = clocks.get("sm_mhz") or 2070.0
+    peak_ginst = 4 * 152 * mhz / 1e3
+    got_ginst = ADJOINT_WARP_INSTRUCTIONS / (ms_both / 1e3) / 1e9
     line = {
         "workload": cfg["name"], "metric": "channel-samples/s of forward + adjoint (device-timed)",
         "value": units / (ms_both / 1e3), "unit": UNIT, "ms_per_step": ms_both, "steps": args.steps,
@@ -606,7 +620,12 @@ def run_adjoint_workload(args) -> None:
         "memory": {"checkpoint_bytes": nb, "work_bytes": wb, "all_intermediates_fp64_bytes": 8 * S * C * N},
         "dtype": "f32x2 (double-float)", "data": "synthetic noise + Ricker events (seeded)",
         "config": {"channels": C, "samples": N, "sections": S, "checkpoint": ck},
-        "clocks": sampler.summary(),
+        "roofline": {"bound": "alu", "achieved": got_ginst, "peak": peak_ginst,
+                     "unit": "G warp instructions/s (FP32 issue)", "frac": got_ginst / peak_ginst,
+                     "instructions": ADJOINT_WARP_INSTRUCTIONS,
+                     "instructions_source": "ncu smsp__inst_executed.sum of one forward + backward, "
+                                            "profiles/iir_adjoint_2048x30000.md"},
+        "clocks": clocks,
     }
     print(json.dumps(line), flush=True)
 
