@@ -93,18 +93,20 @@ __global__ void __launch_bounds__(kFirThreads) fir_kernel(const __grid_constant_
     // 16-byte loads when every row of input and history starts 16-byte aligned
     const bool vec4 = ((ldx | C) & 3) == 0 && (((uintptr_t)x | (uintptr_t)hist) & 15) == 0;
     if (vec4) {
+        // asynchronous 16-byte copies, all in flight together; quads out of
+        // range are zero-filled (source size 0)
         for (int f = tid; f < nrows * (kTopCh / 4); f += kFirThreads) {
             const int s = f / (kTopCh / 4), q = f % (kTopCh / 4);
             const int r = s - OFF;
             const long long g = (long long)t0 + r;
             const int c = c0 + 4 * q;
-            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (c < C && r > -fp.M && g < T) {   // C % 4 == 0: the whole quad is in range
-                if (g >= 0) v = __ldg(reinterpret_cast<const float4 *>(x + g * ldx + c));
-                else v = __ldg(reinterpret_cast<const float4 *>(hist + (g + fp.M - 1) * (long long)C + c));
-            }
-            *reinterpret_cast<float4 *>(&xs[s * kTopCh + 4 * q]) = v;
+            const bool in = c < C && r > -fp.M && g < T;   // C % 4 == 0: the whole quad is in range
+            const float *src = !in ? x : (g >= 0 ? x + g * ldx + c : hist + (g + fp.M - 1) * (long long)C + c);
+            const unsigned dst = (unsigned)__cvta_generic_to_shared(&xs[s * kTopCh + 4 * q]);
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(dst), "l"(src), "r"(in ? 16 : 0)
+                         : "memory");
         }
+        asm volatile("cp.async.wait_all;\n" ::: "memory");
     } else {
         for (int f = tid; f < nrows * kTopCh; f += kFirThreads) {
             const int s = f / kTopCh, ch = f % kTopCh;
