@@ -170,6 +170,24 @@ def precision_chunk(chunk_index: int, n_channels: int = 10_000, chunk: int = 150
     return x
 
 
+def precision_chunk_device(chunk_index: int, n_channels: int = 10_000, chunk: int = 1500,
+                           fs: float = 1500.0, seed: int = 5, sine_hz: float = 0.05,
+                           sine_amp: float = 0.1, generator=None):
+    """The same stream's chunk made on the CUDA device, so that the whole
+    600 s record is quick to produce: the noise comes from torch's seeded
+    generator (the same N(0,1) distribution as precision_chunk, other
+    samples), the sinusoid's phases are precision_chunk's.  Returns a float32
+    CUDA tensor of shape (chunk, n_channels)."""
+    import torch
+    g = generator if generator is not None else torch.Generator(device="cuda")
+    g.manual_seed(seed * 1_000_003 + chunk_index)
+    x = torch.randn((chunk, n_channels), device="cuda", generator=g, dtype=torch.float32)
+    phase = torch.from_numpy(np.random.default_rng([seed, 0]).uniform(0, 2 * np.pi, n_channels)).cuda()
+    t = (chunk_index * chunk + torch.arange(chunk, device="cuda", dtype=torch.float64)) / fs
+    x += (sine_amp * torch.sin(2 * np.pi * sine_hz * t[:, None] + phase[None, :])).float()
+    return x
+
+
 def batch_streams(seed: int = 3, n_streams: int = 32, channels=(500, 10_000),
                   chunk=(200, 3000)) -> list[dict]:
     """Specs of the independent streams of the batching workload: a channel
