@@ -17,28 +17,29 @@
 // Arithmetic is double-float (FP32 pairs, ~48 significant bits) on the FP32
 // pipe -- GB300 runs FP64 at 1/64 of the FP32 rate.  Plain FP32 is not enough:
 // for poles a few 1e-3 from z = 1, rounding the coefficients alone moves the
-// poles by ~1e-5 and the resonance gain by ~1e-3.  The per-channel chaining of
-// segment states (a few steps) and the final reductions run in FP64.
+// poles by ~1e-5 and the resonance gain by ~1e-3.  Only the final reduction of
+// the coefficient gradients runs in FP64.
 //
 // Parallelism over time as well as channels.  The record is cut into segments
 // of at most `ckpt` samples; one thread owns one (segment, channel) pair.  When
 // the channels times the segments of `ckpt` samples are too few threads to
 // fill the GPU (kTargetThreads), the segments are shortened (to no fewer than
 // kMinSegment samples) until they are enough: the checkpoints are then closer
-// than asked for, which the size queries account for.  Both the
-// forward state and the adjoint state are linear in their inputs, so each
-// pass runs in three steps: every thread runs its segment from a zero state
-// and keeps only the final state; one thread per channel chains the segments,
-// state_next = T * state + local (T = the transition over ckpt samples of
-// zero input, computed on the host in long double); every thread reruns its
-// segment from the true state.
+// than asked for, which the size queries account for.  Both the forward state
+// and the adjoint state are linear in their inputs, so each pass runs in three
+// steps: every thread forms the state its segment ends in from a zero start
+// (in block form, local_block_kernel); one group of lanes per channel chains
+// the segments, state_next = T * state + local (T = the transition over a
+// segment of zero input, computed on the host in long double); every thread
+// reruns its segment from the true state.
 //
-// Memory: the forward keeps only the cascade state at each segment start (the
-// checkpoints).  The backward recomputes a segment's section signals piece by
-// piece: a first sweep stores the state every P ~ sqrt(2 ckpt) samples, then
-// the pieces are recomputed in reverse order into a P-sample buffer and
-// consumed by the adjoint.  The workspace holds ~(ckpt/P * 2S + P * S) doubles
-// per (segment, channel) instead of ckpt * S.
+// Memory: the forward's rerun keeps the cascade state at the start of every
+// piece of P ~ sqrt(2 ckpt) samples (the checkpoints).  The backward
+// recomputes a segment's section signals piece by piece, last to first, from
+// those states into a P-sample buffer and consumes them in the adjoint.  The
+// workspace holds (2S + P * S + 6S) doubles per (segment, channel) -- adjoint
+// states, one piece of section signals, gradient partials -- instead of
+// ckpt * S.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
