@@ -359,6 +359,9 @@ filark_status filark_chain_run_static(const filark_chain_config *cfg, const floa
  *     dL/db_i = sum_m u_s[m] w_s[m+i],  dL/da_i = -sum_m y_s[m] w_s[m+i]
  *     (i = 0, 1, 2; a0 included, through the division by a0),
  *     dL/dx = g_0,  g_{s-1}[n] = b0 w_s[n] + b1 w_s[n+1] + b2 w_s[n+2].
+ * dL/da0 is formed from the other five of its section: scaling a section's
+ * six coefficients by one factor leaves the cascade unchanged, so
+ * sum_k c_k dL/dc_k = 0 per section.
  *
  * sos: host, n_sections rows {b0,b1,b2,a0,a1,a2} (raw, not normalised), read
  * during the call only; all finite, a0 != 0; 1 <= n_sections <=
